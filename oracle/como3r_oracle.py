@@ -1,0 +1,393 @@
+"""Plain FP64 CPU oracle of the unified multi-agent Sim(3) Gauss-Newton refinement.
+
+TEST INFRASTRUCTURE ONLY.  This module is the independent reference that the CUDA
+library is checked against.  Only the test suite, the package smoke check and the
+benchmark's CPU-baseline / reference legs may import it; the library never does, and
+it shares no code with the library (its only inputs are the arrays of a problem).
+
+It follows CoMo3R-SLAM (arXiv 2605.30488), Section III, step by step, with dense
+matrices and no blocking or fusion:
+
+* pose T = [sR t; 0 1] in Sim(3) maps camera to world; T_ij = T_i^{-1} T_j (Sec. III-A);
+* ray operator psi(X) = X / ||X|| and the 4-vector ray-plus-range residual (Eq. residual);
+* whitening Sigma_mn = Sigma / q_mn, Sigma = diag(sigma_r^2 I_3, sigma_d^2), and a
+  component-wise Huber kernel with IRLS weight w(r) = min(1, kappa / |r|) (Sec. III-A);
+* the global cost over intra- and inter-agent edges with the first anchor fixed
+  (Eq. global);
+* left perturbation T <- Exp(tau) T, tau = (v, omega, zeta), analytic Jacobians
+  (Eq. jacobian) chained to both endpoints by -/+ Ad_{T_i^{-1}} (Sec. III-D);
+* the regularised normal equations (Eq. normal) with the epsilon escalation
+  eps_r = eps_0 * 100^r, at most six attempts, zero update if all fail (Sec. III-D);
+* closed-form Umeyama alignment (Eq. align, Eq. umeyama).
+
+Readings where the paper is silent (each also listed in the design notes):
+
+* q_mn = sqrt(c_i,m * c_j,n) from the per-pixel confidences supplied with the pointmaps
+  (they play the role of the descriptor confidences Q);
+* rho(r) = r^2 / 2 for |r| <= kappa, kappa |r| - kappa^2 / 2 beyond, so rho'(r) = w(r) r;
+* g = sum J^T W e is the gradient of E_global and the step solves (...) tau = -g;
+* W_c = w(r_c) q / sigma_c^2, H = sum J^T W J (Gauss-Newton with IRLS weights);
+* back-end lambda defaults to 0; a factorisation "fails" when a pivot is not > 0 or is
+  not finite; attempts r = 0..5 use eps_r = 1e-6 * 100^r;
+* a match is skipped when ||X_i,m|| or ||T_ij X_j,n|| is not > 1e-12, when
+  c_i,m * c_j,n is negative, or when any of them is not finite;
+* the anchor is removed from the unknowns (all seven of its degrees of freedom).
+"""
+from __future__ import annotations
+
+import math
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+import scipy.linalg
+
+DEGENERATE = 1e-12
+
+
+# =============================================================== Sim(3) (Sec. III-A, III-D)
+def quat_to_rot(q: np.ndarray) -> np.ndarray:
+    """Rotation matrix of a unit quaternion stored (x, y, z, w)."""
+    x, y, z, w = [float(v) for v in q]
+    n = math.sqrt(x * x + y * y + z * z + w * w)
+    x, y, z, w = x / n, y / n, z / n, w / n
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+def pose_to_matrix(p: np.ndarray) -> np.ndarray:
+    """4x4 similarity [sR t; 0 1] of a pose stored (tx, ty, tz, qx, qy, qz, qw, s) (Sec. III-A)."""
+    T = np.eye(4)
+    T[:3, :3] = p[7] * quat_to_rot(p[3:7])
+    T[:3, 3] = p[:3]
+    return T
+
+
+def matrix_to_pose(T: np.ndarray) -> np.ndarray:
+    """Inverse of pose_to_matrix: s = det(sR)^(1/3), R projected to SO(3) by SVD, q with w >= 0."""
+    sR = T[:3, :3]
+    s = np.cbrt(np.linalg.det(sR))
+    U, _, Vt = np.linalg.svd(sR / s)
+    R = U @ Vt
+    from scipy.spatial.transform import Rotation
+    q = Rotation.from_matrix(R).as_quat()  # (x, y, z, w)
+    if q[3] < 0:
+        q = -q
+    return np.concatenate([T[:3, 3], q, [s]])
+
+
+def sim3_inverse(T: np.ndarray) -> np.ndarray:
+    return np.linalg.inv(T)
+
+
+def skew(w: np.ndarray) -> np.ndarray:
+    return np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+
+
+def hat(tau: np.ndarray) -> np.ndarray:
+    """sim(3) generator of tau = (v, omega, zeta): [[omega^ + zeta I, v], [0, 0]] (Sec. III-D)."""
+    X = np.zeros((4, 4))
+    X[:3, :3] = skew(tau[3:6]) + tau[6] * np.eye(3)
+    X[:3, 3] = tau[:3]
+    return X
+
+
+def exp_sim3(tau: np.ndarray) -> np.ndarray:
+    """Exp(tau) as the matrix exponential of hat(tau) (library expm, scaling and squaring)."""
+    return scipy.linalg.expm(hat(np.asarray(tau, dtype=np.float64)))
+
+
+def log_sim3(T: np.ndarray) -> np.ndarray:
+    """Inverse of exp_sim3 through the principal matrix logarithm (error reports only)."""
+    L = np.real(scipy.linalg.logm(T))
+    A = L[:3, :3]
+    zeta = np.trace(A) / 3.0
+    W = 0.5 * (A - A.T)
+    return np.array([L[0, 3], L[1, 3], L[2, 3], W[2, 1], W[0, 2], W[1, 0], zeta])
+
+
+def adjoint(T: np.ndarray) -> np.ndarray:
+    """7x7 Ad_T with T hat(tau) T^{-1} = hat(Ad_T tau) for tau = (v, omega, zeta).
+
+    With T = (sR, t): v' = sR v + [t]x R omega - zeta t, omega' = R omega, zeta' = zeta.
+    """
+    sR = T[:3, :3]
+    s = np.cbrt(np.linalg.det(sR))
+    R = sR / s
+    t = T[:3, 3]
+    Ad = np.zeros((7, 7))
+    Ad[:3, :3] = sR
+    Ad[:3, 3:6] = skew(t) @ R
+    Ad[:3, 6] = -t
+    Ad[3:6, 3:6] = R
+    Ad[6, 6] = 1.0
+    return Ad
+
+
+# ============================================== residual, whitening, Huber (Sec. III-A)
+def psi(X: np.ndarray) -> np.ndarray:
+    """Ray operator psi(X) = X / ||X|| (row-wise)."""
+    return X / np.linalg.norm(X, axis=-1, keepdims=True)
+
+
+def transform(T: np.ndarray, X: np.ndarray) -> np.ndarray:
+    return X @ T[:3, :3].T + T[:3, 3]
+
+
+def residual(Tij: np.ndarray, Xi: np.ndarray, Xj: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """e_mn = [psi(T_ij X_j,n) - psi(X_i,m); ||T_ij X_j,n|| - ||X_i,m||] (Eq. residual)."""
+    x = transform(Tij, Xj)
+    e = np.empty((x.shape[0], 4))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        e[:, :3] = psi(x) - psi(Xi)
+    e[:, 3] = np.linalg.norm(x, axis=1) - np.linalg.norm(Xi, axis=1)
+    return e, x
+
+
+def whiten(e: np.ndarray, q: np.ndarray, sigma_ray: float, sigma_dist: float) -> np.ndarray:
+    """r = Sigma_mn^{-1/2} e with Sigma_mn = diag(sigma_r^2, sigma_r^2, sigma_r^2, sigma_d^2) / q."""
+    sig = np.array([sigma_ray, sigma_ray, sigma_ray, sigma_dist])
+    return np.sqrt(q)[:, None] * e / sig[None, :]
+
+
+def huber_rho(r: np.ndarray, kappa: float) -> np.ndarray:
+    a = np.abs(r)
+    return np.where(a <= kappa, 0.5 * r * r, kappa * a - 0.5 * kappa * kappa)
+
+
+def huber_weight(r: np.ndarray, kappa: float) -> np.ndarray:
+    """IRLS weight w(r) = min(1, kappa / |r|), equal to 1 at r = 0."""
+    a = np.abs(r)
+    with np.errstate(divide="ignore"):
+        return np.where(a <= kappa, 1.0, kappa / np.where(a > 0, a, 1.0))
+
+
+# ========================================================== Jacobians (Eq. jacobian)
+def jacobian_rel(x: np.ndarray) -> np.ndarray:
+    """d e / d tau for the left perturbation x <- Exp(tau) x, one 4x7 block per row of x.
+
+    Product of the printed factors: Dx/Dtau = [I, -[x]x, x], Dpsi/Dx = (I - x x^T / d^2) / d,
+    Dd/Dx = x^T / d.
+    """
+    M = x.shape[0]
+    d = np.linalg.norm(x, axis=1)
+    Dx = np.zeros((M, 3, 7))
+    Dx[:, :, 0:3] = np.eye(3)
+    Dx[:, 0, 4], Dx[:, 0, 5] = x[:, 2], -x[:, 1]   # -[x]x
+    Dx[:, 1, 3], Dx[:, 1, 5] = -x[:, 2], x[:, 0]
+    Dx[:, 2, 3], Dx[:, 2, 4] = x[:, 1], -x[:, 0]
+    Dx[:, :, 6] = x
+    outer = x[:, :, None] * x[:, None, :]
+    Dpsi = (np.eye(3)[None] - outer / (d * d)[:, None, None]) / d[:, None, None]
+    Dd = (x / d[:, None])[:, None, :]
+    J = np.empty((M, 4, 7))
+    J[:, :3, :] = Dpsi @ Dx
+    J[:, 3:, :] = Dd @ Dx
+    return J
+
+
+# ========================================================== problem access helpers
+def problem_arrays(prob) -> Dict[str, np.ndarray]:
+    """The arrays of a problem as FP64 views (storage values upcast exactly)."""
+    pix = prob.pixels_of()
+    return dict(points=np.asarray(prob.points, dtype=np.float64),
+                pix_off=np.concatenate([[0], np.cumsum(pix)]).astype(np.int64),
+                idx_off=np.concatenate([[0], np.cumsum(pix[prob.edge_i])]).astype(np.int64))
+
+
+def edge_matches(prob, arrs, e: int):
+    """Valid (m, n) pairs of edge e and the points/confidences they touch."""
+    i, j = int(prob.edge_i[e]), int(prob.edge_j[e])
+    idx = prob.match_idx[arrs["idx_off"][e]:arrs["idx_off"][e + 1]]
+    m = np.nonzero(idx >= 0)[0]
+    n = idx[m].astype(np.int64)
+    Pi = arrs["points"][arrs["pix_off"][i] + m]
+    Pj = arrs["points"][arrs["pix_off"][j] + n]
+    return i, j, m, n, Pi, Pj
+
+
+# ======================================== one edge, linearised (Eq. global, jacobian)
+def linearize_edge(Ti: np.ndarray, Tj: np.ndarray, Pi: np.ndarray, Pj: np.ndarray,
+                   params: Dict[str, float]) -> Dict[str, np.ndarray]:
+    """Residuals, IRLS weights, edge Jacobians and the blocks one edge adds.
+
+    Returns the relative-pose blocks H_rel = sum J^T W J, g_rel = sum J^T W e (J w.r.t. a
+    left perturbation of T_ij), the endpoint blocks H_ii, H_jj, H_ij, g_i, g_j built from
+    per-match J_i = -J Ad, J_j = J Ad with Ad = Ad_{T_i^{-1}}, the cost and the counts.
+    """
+    Tij = sim3_inverse(Ti) @ Tj
+    Xi, ci = Pi[:, :3], Pi[:, 3]
+    Xj, cj = Pj[:, :3], Pj[:, 3]
+    e, x = residual(Tij, Xi, Xj)
+    di = np.linalg.norm(Xi, axis=1)
+    d = np.linalg.norm(x, axis=1)
+    cc = ci * cj
+    with np.errstate(invalid="ignore"):
+        ok = (di > DEGENERATE) & (d > DEGENERATE) & (cc >= 0) & np.isfinite(di) & np.isfinite(d) & np.isfinite(cc)
+    ok &= np.all(np.isfinite(e), axis=1)
+    e, x, cc = e[ok], x[ok], cc[ok]
+    q = np.sqrt(cc)
+    r = whiten(e, q, params["sigma_ray"], params["sigma_dist"])
+    w = huber_weight(r, params["huber_k"])
+    sig = np.array([params["sigma_ray"]] * 3 + [params["sigma_dist"]])
+    W = w * q[:, None] / (sig * sig)[None, :]
+    cost = float(huber_rho(r, params["huber_k"]).sum())
+    J = jacobian_rel(x)
+    Ad = adjoint(sim3_inverse(Ti))
+    Ji = -J @ Ad
+    Jj = J @ Ad
+    ein = lambda A, B: np.einsum("mci,mc,mcj->ij", A, W, B, optimize=True)
+    return dict(
+        H_rel=ein(J, J), g_rel=np.einsum("mci,mc,mc->i", J, W, e, optimize=True),
+        H_ii=ein(Ji, Ji), H_jj=ein(Jj, Jj), H_ij=ein(Ji, Jj),
+        g_i=np.einsum("mci,mc,mc->i", Ji, W, e, optimize=True),
+        g_j=np.einsum("mci,mc,mc->i", Jj, W, e, optimize=True),
+        cost=cost, n_valid=int(ok.size), n_skipped=int((~ok).sum()), Ad=Ad)
+
+
+def build_system(prob, poses: np.ndarray, graph: int = 0, arrs=None):
+    """Dense normal equations of one graph: H (7N x 7N), g (7N), cost, per-edge records.
+
+    Keyframes of the graph are numbered locally from 0; the anchor is still included.
+    """
+    arrs = arrs or problem_arrays(prob)
+    params = prob.params()
+    k0, k1 = int(prob.kf_offset[graph]), int(prob.kf_offset[graph + 1])
+    N = k1 - k0
+    H = np.zeros((7 * N, 7 * N))
+    g = np.zeros(7 * N)
+    cost = 0.0
+    records = []
+    T = [pose_to_matrix(poses[k]) for k in range(k0, k1)]
+    for e in range(int(prob.edge_offset[graph]), int(prob.edge_offset[graph + 1])):
+        i, j, m, n, Pi, Pj = edge_matches(prob, arrs, e)
+        li, lj = i - k0, j - k0
+        rec = linearize_edge(T[li], T[lj], Pi, Pj, params)
+        si, sj = slice(7 * li, 7 * li + 7), slice(7 * lj, 7 * lj + 7)
+        H[si, si] += rec["H_ii"]
+        H[sj, sj] += rec["H_jj"]
+        H[si, sj] += rec["H_ij"]
+        H[sj, si] += rec["H_ij"].T
+        g[si] += rec["g_i"]
+        g[sj] += rec["g_j"]
+        cost += rec["cost"]
+        records.append(rec)
+    return H, g, cost, records
+
+
+# ============================= regularised normal equations (Eq. normal, Sec. III-D)
+def cholesky(A: np.ndarray) -> Optional[np.ndarray]:
+    """Textbook Cholesky-Crout A = L L^T; None when a pivot is not > 0 or not finite."""
+    n = A.shape[0]
+    L = np.zeros_like(A)
+    for j in range(n):
+        piv = A[j, j] - L[j, :j] @ L[j, :j]
+        if not (np.isfinite(piv) and piv > 0.0):
+            return None
+        L[j, j] = math.sqrt(piv)
+        L[j + 1:, j] = (A[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
+    return L
+
+
+def damped_solve(H: np.ndarray, g: np.ndarray, anchor: int, lam: float, eps0: float,
+                 max_attempts: int) -> Tuple[np.ndarray, int, bool]:
+    """Solve (H + lam diag(H) + eps_r I) tau = -g over all keyframes but the anchor.
+
+    eps_r = eps0 * 100^r for r = 0 .. max_attempts-1; the first successful
+    factorisation is used; if none succeeds the update is zero.  Returns (tau [N, 7],
+    attempts made, success).
+    """
+    N = H.shape[0] // 7
+    keep = np.array([k for k in range(7 * N) if k // 7 != anchor], dtype=np.int64)
+    Hr = H[np.ix_(keep, keep)]
+    gr = g[keep]
+    tau = np.zeros(7 * N)
+    for r in range(max_attempts):
+        eps = eps0 * 100.0 ** r
+        A = Hr + lam * np.diag(np.diag(Hr)) + eps * np.eye(Hr.shape[0])
+        L = cholesky(A)
+        if L is None:
+            continue
+        y = scipy.linalg.solve_triangular(L, -gr, lower=True)
+        tau[keep] = scipy.linalg.solve_triangular(L.T, y, lower=False)
+        return tau.reshape(N, 7), r + 1, True
+    return tau.reshape(N, 7), max_attempts, False
+
+
+# ======================================================= Gauss-Newton (Sec. III-D)
+def retract(poses: np.ndarray, tau: np.ndarray, k0: int = 0) -> np.ndarray:
+    """T_i <- Exp(tau_i) T_i for the keyframes k0 .. k0 + len(tau) - 1."""
+    out = poses.copy()
+    for l in range(tau.shape[0]):
+        if not np.any(tau[l]):
+            continue
+        out[k0 + l] = matrix_to_pose(exp_sim3(tau[l]) @ pose_to_matrix(poses[k0 + l]))
+    return out
+
+
+def gn_step(prob, poses: np.ndarray, arrs=None) -> Tuple[np.ndarray, List[dict]]:
+    """One iteration for every graph: linearise, solve the damped system, retract."""
+    arrs = arrs or problem_arrays(prob)
+    out = poses.copy()
+    infos = []
+    for gidx in range(prob.num_graphs):
+        k0 = int(prob.kf_offset[gidx])
+        H, g, cost, recs = build_system(prob, poses, gidx, arrs)
+        tau, attempts, ok = damped_solve(H, g, int(prob.anchor[gidx]) - k0, prob.lam, prob.eps0, prob.max_attempts)
+        out = retract(out, tau, k0)
+        infos.append(dict(cost=cost, attempts=attempts, ok=ok, H=H, g=g, tau=tau,
+                          n_skipped=sum(r["n_skipped"] for r in recs)))
+    return out, infos
+
+
+def gn_solve(prob, poses: np.ndarray, iters: int) -> Tuple[np.ndarray, np.ndarray]:
+    """`iters` GN iterations; returns the poses and the cost trace [iters + 1, G]."""
+    arrs = problem_arrays(prob)
+    trace = np.zeros((iters + 1, prob.num_graphs))
+    for k in range(iters):
+        poses, infos = gn_step(prob, poses, arrs)
+        trace[k] = [inf["cost"] for inf in infos]
+    trace[iters] = [build_system(prob, poses, gidx, arrs)[2] for gidx in range(prob.num_graphs)]
+    return poses, trace
+
+
+def total_cost(prob, poses: np.ndarray) -> np.ndarray:
+    arrs = problem_arrays(prob)
+    return np.array([build_system(prob, poses, gidx, arrs)[2] for gidx in range(prob.num_graphs)])
+
+
+# ================================================== Umeyama (Eq. align, Eq. umeyama)
+def umeyama(x: np.ndarray, y: np.ndarray) -> Tuple[float, np.ndarray, np.ndarray]:
+    """(s, R, t) minimising sum ||x_l - (s R y_l + t)||^2 in closed form."""
+    mx, my = x.mean(axis=0), y.mean(axis=0)
+    xc, yc = x - mx, y - my
+    A = xc.T @ yc / x.shape[0]
+    U, lam, Vt = np.linalg.svd(A)
+    S = np.diag([1.0, 1.0, np.sign(np.linalg.det(U @ Vt)) or 1.0])
+    R = U @ S @ Vt
+    s = float(np.trace(S @ np.diag(lam)) / ((yc * yc).sum() / x.shape[0]))
+    t = mx - s * R @ my
+    return s, R, t
+
+
+# =================================================================== error reports
+def pose_errors(pa: np.ndarray, pb: np.ndarray, ref_scale: Optional[float] = None) -> Dict[str, float]:
+    """Max over keyframes of rotation angle (rad), relative translation and relative scale error.
+
+    Translation error is ||t_a - t_b|| / max(||t_b||, ref), ref = RMS distance of the
+    reference camera centres from their mean unless given.
+    """
+    tb = pb[:, :3]
+    ref = ref_scale if ref_scale is not None else float(np.sqrt(((tb - tb.mean(0)) ** 2).sum(1).mean()))
+    rot, tra, sca = 0.0, 0.0, 0.0
+    for a, b in zip(pa, pb):
+        Ra, Rb = quat_to_rot(a[3:7]), quat_to_rot(b[3:7])
+        c = (np.trace(Ra @ Rb.T) - 1.0) / 2.0
+        rot = max(rot, math.acos(max(-1.0, min(1.0, c))) if c < 0.999999 else
+                  np.linalg.norm(0.5 * np.array([(Ra @ Rb.T)[2, 1] - (Ra @ Rb.T)[1, 2],
+                                                 (Ra @ Rb.T)[0, 2] - (Ra @ Rb.T)[2, 0],
+                                                 (Ra @ Rb.T)[1, 0] - (Ra @ Rb.T)[0, 1]])))
+        tra = max(tra, float(np.linalg.norm(a[:3] - b[:3]) / max(np.linalg.norm(b[:3]), ref, 1e-300)))
+        sca = max(sca, abs(a[7] / b[7] - 1.0))
+    return dict(rot=rot, trans=tra, scale=sca)

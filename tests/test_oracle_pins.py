@@ -1,0 +1,370 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by the mathematics.
+
+Each test checks the oracle against something other than itself: hand-derived values
+of Eq. (jacobian) / Eq. (residual), central finite differences, Lie-group identities,
+the Sim(3) gauge symmetry of Eq. (global), noise-free recovery, closed-form Umeyama
+(Eq. umeyama) against brute force, and the escalation schedule of Sec. III-D.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import como3r_oracle as O
+from synth import make_problem, make_workload
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rand_sim3(rng, rot=1.0, trans=2.0, logs=0.5):
+    tau = np.concatenate([rng.normal(size=3) * trans, rng.normal(size=3) * rot, [rng.normal() * logs]])
+    return O.exp_sim3(tau)
+
+
+# ------------------------------------------------------------------ golden fixtures
+def load_jacobian_golden():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "jacobian_rel.txt")) if l.strip() and not l.startswith("#")]
+    cases = []
+    for k in range(0, len(rows), 5):
+        x = np.array([float(v) for v in rows[k]])
+        J = np.array([[float(v) for v in r] for r in rows[k + 1:k + 5]])
+        cases.append((x, J))
+    return cases
+
+
+def test_jacobian_matches_hand_derivation():
+    """Eq. (jacobian): the 4x7 block written out by hand for two points."""
+    for x, J in load_jacobian_golden():
+        got = O.jacobian_rel(x[None, :])[0]
+        np.testing.assert_allclose(got, J, rtol=0, atol=1e-15)
+
+
+def test_residual_matches_hand_values():
+    """Eq. (residual) on hand-picked poses and points."""
+    for line in open(os.path.join(GOLDEN, "residual.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        pose, xj, xi, e = [np.array([float(v) for v in part.split()]) for part in line.split("|")]
+        s, q, t = pose[0], pose[1:5], pose[5:8]
+        T = O.pose_to_matrix(np.concatenate([t, q, [s]]))
+        got, _ = O.residual(T, xi[None, :], xj[None, :])
+        np.testing.assert_allclose(got[0], e, rtol=0, atol=1e-13)
+
+
+# ------------------------------------------------------------------ Lie group identities
+def test_exp_special_cases():
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=3)
+    np.testing.assert_allclose(O.exp_sim3(np.r_[v, 0, 0, 0, 0]), np.block([[np.eye(3), v[:, None]], [np.zeros((1, 3)), 1]]), atol=1e-15)
+    z = 0.37
+    np.testing.assert_allclose(O.exp_sim3(np.r_[0, 0, 0, 0, 0, 0, z])[:3, :3], math.exp(z) * np.eye(3), rtol=1e-15)
+    w = rng.normal(size=3)
+    th = np.linalg.norm(w)
+    K = O.skew(w / th)
+    Rrod = np.eye(3) + math.sin(th) * K + (1 - math.cos(th)) * K @ K  # Rodrigues
+    np.testing.assert_allclose(O.exp_sim3(np.r_[0, 0, 0, w, 0])[:3, :3], Rrod, atol=1e-14)
+    tau = rng.normal(size=7)
+    np.testing.assert_allclose(O.exp_sim3(tau) @ O.exp_sim3(-tau), np.eye(4), atol=1e-13)
+    h = 1e-6
+    dE = (O.exp_sim3(tau * (1 + h)) - O.exp_sim3(tau * (1 - h))) / (2 * h)
+    np.testing.assert_allclose(dE, O.hat(tau) @ O.exp_sim3(tau), rtol=1e-6, atol=1e-8)
+
+
+def test_adjoint_conjugation():
+    """Ad_T tau satisfies Exp(Ad_T tau) = T Exp(tau) T^{-1}."""
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        T = rand_sim3(rng)
+        tau = rng.normal(size=7) * 0.3
+        lhs = O.exp_sim3(O.adjoint(T) @ tau)
+        rhs = T @ O.exp_sim3(tau) @ np.linalg.inv(T)
+        np.testing.assert_allclose(lhs, rhs, rtol=1e-11, atol=1e-11)
+
+
+def test_edge_chain_rule_signs():
+    """T_ij under left perturbations of T_i and T_j moves by -Ad / +Ad of T_i^{-1} (Sec. III-D)."""
+    rng = np.random.default_rng(3)
+    Ti, Tj = rand_sim3(rng), rand_sim3(rng)
+    Tij = np.linalg.inv(Ti) @ Tj
+    Ad = O.adjoint(np.linalg.inv(Ti))
+    h = 1e-6
+    for k in range(7):
+        d = np.zeros(7); d[k] = h
+        for which, sign in (("i", -1.0), ("j", 1.0)):
+            def rel(dd):
+                A = O.exp_sim3(dd) @ Ti if which == "i" else Ti
+                B = O.exp_sim3(dd) @ Tj if which == "j" else Tj
+                return O.log_sim3(np.linalg.inv(A) @ B @ np.linalg.inv(Tij))
+            fd = (rel(d) - rel(-d)) / (2 * h)
+            np.testing.assert_allclose(fd, sign * Ad[:, k], rtol=1e-5, atol=1e-6)
+
+
+# ------------------------------------------------------------------ Jacobians by FD
+def test_edge_jacobians_central_fd():
+    """J_i = -J Ad, J_j = J Ad agree with central FD of e to 1e-6 relative (Eq. jacobian)."""
+    rng = np.random.default_rng(4)
+    Ti, Tj = rand_sim3(rng, trans=1.0), rand_sim3(rng, trans=1.0)
+    Xj = rng.normal(size=(50, 3)) + np.array([0, 0, 5.0])
+    Xi = O.transform(np.linalg.inv(Ti) @ Tj, Xj) * (1 + 0.01 * rng.normal(size=(50, 1)))
+    e0, x = O.residual(np.linalg.inv(Ti) @ Tj, Xi, Xj)
+    J = O.jacobian_rel(x)
+    Ad = O.adjoint(np.linalg.inv(Ti))
+    Ji, Jj = -J @ Ad, J @ Ad
+    h = 1e-6
+    for k in range(7):
+        d = np.zeros(7); d[k] = h
+        for Jan, which in ((Ji, "i"), (Jj, "j")):
+            def ev(dd):
+                A = O.exp_sim3(dd) @ Ti if which == "i" else Ti
+                B = O.exp_sim3(dd) @ Tj if which == "j" else Tj
+                return O.residual(np.linalg.inv(A) @ B, Xi, Xj)[0]
+            fd = (ev(d) - ev(-d)) / (2 * h)
+            scale = np.abs(Jan[:, :, k]).max()
+            assert np.abs(fd - Jan[:, :, k]).max() <= 1e-6 * scale
+
+
+# ------------------------------------------------------------------ Huber
+def test_huber_derivative_and_continuity():
+    k = 1.345
+    r = np.linspace(-5, 5, 1001)
+    h = 1e-6
+    fd = (O.huber_rho(r + h, k) - O.huber_rho(r - h, k)) / (2 * h)
+    np.testing.assert_allclose(fd, O.huber_weight(r, k) * r, atol=1e-8)
+    for s in (1, -1):  # C1 at the breakpoint
+        a, b = s * (k - 1e-9), s * (k + 1e-9)
+        assert abs(O.huber_rho(np.array([a]), k) - O.huber_rho(np.array([b]), k))[0] < 1e-8
+        assert abs(O.huber_weight(np.array([a]), k)[0] - O.huber_weight(np.array([b]), k)[0]) < 1e-8
+    assert O.huber_weight(np.array([0.0]), k)[0] == 1.0
+
+
+# ------------------------------------------------------------------ system-level pins
+@pytest.fixture(scope="module")
+def tiny():
+    return make_workload("two_agent_6kf_64x48", seed=0)
+
+
+@pytest.fixture(scope="module")
+def tiny_exact():
+    return make_problem(3, noise=0.0, outlier=0.0, exact=True, name="noise-free")
+
+
+def perturb_one(poses, k, tau):
+    out = poses.copy()
+    out[k] = O.matrix_to_pose(O.exp_sim3(tau) @ O.pose_to_matrix(poses[k]))
+    return out
+
+
+def test_gradient_is_derivative_of_cost(tiny):
+    """g = sum J^T W e is dE/dtau for left perturbations (pins sign, W and whitening)."""
+    poses = tiny.poses_init
+    H, g, E, _ = O.build_system(tiny, poses, 0)
+    rng = np.random.default_rng(5)
+    h = 1e-6
+    for k in rng.choice(tiny.num_kf, size=4, replace=False):
+        for c in range(7):
+            d = np.zeros(7); d[c] = h
+            fd = (O.total_cost(tiny, perturb_one(poses, k, d))[0] - O.total_cost(tiny, perturb_one(poses, k, -d))[0]) / (2 * h)
+            assert abs(fd - g[7 * k + c]) <= 1e-5 * max(1.0, abs(g).max() * 1e-2)
+
+
+def test_hessian_exact_at_zero_residual(tiny_exact):
+    """With all residuals zero the GN matrix is the exact Hessian: H = d g / d tau."""
+    poses = tiny_exact.poses_gt
+    H, g, E, _ = O.build_system(tiny_exact, poses, 0)
+    assert E < 1e-18
+    h = 1e-6
+    for k in (1, 7):
+        for c in range(7):
+            d = np.zeros(7); d[c] = h
+            gp = O.build_system(tiny_exact, perturb_one(poses, k, d), 0)[1]
+            gm = O.build_system(tiny_exact, perturb_one(poses, k, -d), 0)[1]
+            col = (gp - gm) / (2 * h)
+            np.testing.assert_allclose(col, H[:, 7 * k + c], rtol=0, atol=2e-5 * np.abs(H).max())
+
+
+def test_gauge_invariance(tiny):
+    """E(G T) = E(T); H annihilates a common left perturbation; sum_i g_i = 0 (Eq. global)."""
+    poses = tiny.poses_init
+    H, g, E, _ = O.build_system(tiny, poses, 0)
+    rng = np.random.default_rng(6)
+    G = rand_sim3(rng)
+    moved = np.array([O.matrix_to_pose(G @ O.pose_to_matrix(p)) for p in poses])
+    E2 = O.total_cost(tiny, moved)[0]
+    assert abs(E2 - E) <= 1e-9 * E
+    delta = rng.normal(size=7)
+    common = np.tile(delta, tiny.num_kf)
+    assert np.abs(H @ common).max() <= 1e-9 * np.abs(H).max() * np.abs(delta).max()
+    np.testing.assert_allclose(g.reshape(-1, 7).sum(0), 0.0, atol=1e-9 * np.abs(g).max())
+
+
+def test_edge_block_structure(tiny):
+    """Each edge adds H_ii = H_jj = -H_ij and g_i = -g_j (two diagonal + one off-diagonal block)."""
+    _, _, _, recs = O.build_system(tiny, tiny.poses_init, 0)
+    for r in recs:
+        s = np.abs(r["H_ii"]).max()
+        np.testing.assert_allclose(r["H_ii"], r["H_jj"], atol=1e-10 * s)
+        np.testing.assert_allclose(r["H_ij"], -r["H_ii"], atol=1e-10 * s)
+        np.testing.assert_allclose(r["g_i"], -r["g_j"], atol=1e-10 * max(1.0, np.abs(r["g_i"]).max()))
+        Ad = r["Ad"]
+        np.testing.assert_allclose(r["H_jj"], Ad.T @ r["H_rel"] @ Ad, atol=1e-9 * s)
+
+
+def test_confidence_and_sigma_scaling(tiny_exact):
+    """Quadratic regime: E scales with q (c -> 4c gives x4) and with 1/sigma^2 per block."""
+    poses = tiny_exact.poses_init.copy()
+    # tiny perturbation keeps every |r| below kappa
+    poses = np.array([O.matrix_to_pose(O.exp_sim3(np.r_[1e-6, 0, 0, 0, 1e-7, 0, 1e-7]) @ O.pose_to_matrix(p)) if k else p
+                      for k, p in enumerate(tiny_exact.poses_gt)])
+    E = O.total_cost(tiny_exact, poses)[0]
+    p4 = make_problem(3, noise=0.0, outlier=0.0, exact=True)
+    p4.points = p4.points.copy(); p4.points[:, 3] *= 4.0
+    E4 = O.total_cost(p4, poses)[0]
+    assert abs(E4 / E - 4.0) < 1e-9
+    pd = make_problem(3, noise=0.0, outlier=0.0, exact=True)
+    pd.sigma_dist = 1e9  # range block off: only the ray block remains
+    pr = make_problem(3, noise=0.0, outlier=0.0, exact=True)
+    pr.sigma_ray = 1e9
+    Er, Ed = O.total_cost(pd, poses)[0], O.total_cost(pr, poses)[0]
+    assert abs((Er + Ed) / E - 1.0) < 1e-9
+    pd.sigma_ray = tiny_exact.sigma_ray / 2
+    assert abs(O.total_cost(pd, poses)[0] / Er - 4.0) < 1e-9
+
+
+def test_noise_free_recovery(tiny_exact):
+    """Exact correspondences, no noise: GN returns to the ground truth (anchor fixes the gauge)."""
+    poses, trace = O.gn_solve(tiny_exact, tiny_exact.poses_init, 10)
+    err = O.pose_errors(poses, tiny_exact.poses_gt)
+    assert err["rot"] < 1e-10 and err["trans"] < 1e-10 and err["scale"] < 1e-10, err
+    assert trace[-1, 0] < 1e-16 and trace[0, 0] > 1.0
+
+
+def test_two_view_equals_umeyama():
+    """One edge, noise-free: the GN pose of j equals Umeyama on the matched points."""
+    p = make_problem(11, agents=1, n_kf=2, noise=0.0, outlier=0.0, n_inter=0, exact=True)
+    poses, _ = O.gn_solve(p, p.poses_init, 10)
+    arrs = O.problem_arrays(p)
+    i, j, m, n, Pi, Pj = O.edge_matches(p, arrs, 0)
+    x = O.transform(O.pose_to_matrix(p.poses_gt[0]), Pi[:, :3])
+    s, R, t = O.umeyama(x, Pj[:, :3])
+    T = np.eye(4); T[:3, :3] = s * R; T[:3, 3] = t
+    np.testing.assert_allclose(O.pose_to_matrix(poses[1]), T, atol=1e-10)
+    np.testing.assert_allclose(T, O.pose_to_matrix(p.poses_gt[1]), atol=1e-10)
+
+
+# ------------------------------------------------------------------ Umeyama vs brute force
+def _brute_force_alignment(x, y):
+    """Best (s, R, t) by a rotation grid (<= 1 deg) plus local GN refinement; s, t closed form per R."""
+    xc, yc = x - x.mean(0), y - y.mean(0)
+
+    def cost_R(R):
+        Ry = yc @ R.T
+        s = max((xc * Ry).sum() / (yc * yc).sum(), 0.0)
+        return ((xc - s * Ry) ** 2).sum(), s
+
+    best = (np.inf, None)
+    axes = []
+    for a in np.linspace(0, math.pi, 13):
+        for b in np.linspace(0, 2 * math.pi, 25, endpoint=False):
+            axes.append([math.sin(a) * math.cos(b), math.sin(a) * math.sin(b), math.cos(a)])
+    for ax in axes:
+        for ang in np.linspace(0, math.pi, 19):
+            R = O.exp_sim3(np.r_[0, 0, 0, np.array(ax) * ang, 0])[:3, :3]
+            c, _ = cost_R(R)
+            if c < best[0]:
+                best = (c, R)
+    R = best[1]
+    for _ in range(200):  # refine with small rotations (finite-difference Newton on so(3))
+        c0, _ = cost_R(R)
+        h = 1e-5
+        g = np.zeros(3); Hm = np.zeros((3, 3))
+        for a in range(3):
+            ea = np.zeros(3); ea[a] = h
+            cp, cm = cost_R(O.exp_sim3(np.r_[0, 0, 0, ea, 0])[:3, :3] @ R)[0], cost_R(O.exp_sim3(np.r_[0, 0, 0, -ea, 0])[:3, :3] @ R)[0]
+            g[a] = (cp - cm) / (2 * h)
+            Hm[a, a] = (cp - 2 * c0 + cm) / h ** 2
+            for b in range(a):
+                eb = np.zeros(3); eb[b] = h
+                cpp = cost_R(O.exp_sim3(np.r_[0, 0, 0, ea + eb, 0])[:3, :3] @ R)[0]
+                cmm = cost_R(O.exp_sim3(np.r_[0, 0, 0, -ea - eb, 0])[:3, :3] @ R)[0]
+                cpm = cost_R(O.exp_sim3(np.r_[0, 0, 0, ea - eb, 0])[:3, :3] @ R)[0]
+                cmp_ = cost_R(O.exp_sim3(np.r_[0, 0, 0, -ea + eb, 0])[:3, :3] @ R)[0]
+                Hm[a, b] = Hm[b, a] = (cpp - cpm - cmp_ + cmm) / (4 * h * h)
+        step = -np.linalg.solve(Hm + 1e-12 * np.eye(3), g)
+        if np.linalg.norm(step) > 0.05:
+            step *= 0.05 / np.linalg.norm(step)
+        Rn = O.exp_sim3(np.r_[0, 0, 0, step, 0])[:3, :3] @ R
+        if cost_R(Rn)[0] <= c0:
+            R = Rn
+        if np.linalg.norm(step) < 1e-12:
+            break
+    c, s = cost_R(R)
+    return c, s, R
+
+
+@pytest.mark.parametrize("npts,seed", [(3, 0), (4, 1), (5, 2), (8, 3), (6, 4)])
+def test_umeyama_matches_brute_force(npts, seed):
+    rng = np.random.default_rng(seed)
+    y = rng.normal(size=(npts, 3))
+    T = rand_sim3(rng)
+    x = O.transform(T, y) + 0.05 * rng.normal(size=(npts, 3))
+    s, R, t = O.umeyama(x, y)
+    c_closed = ((x - (s * y @ R.T + t)) ** 2).sum()
+    c_bf, s_bf, R_bf = _brute_force_alignment(x, y)
+    assert c_closed <= c_bf + 1e-12
+    assert abs(c_closed - c_bf) <= 1e-9 * max(1.0, c_bf)
+    np.testing.assert_allclose(R, R_bf, atol=1e-5)
+    assert abs(np.linalg.det(R) - 1) < 1e-12
+
+
+def test_umeyama_reflection_case():
+    """Points related by a reflection: det(U V^T) = -1 and S flips the last singular direction."""
+    rng = np.random.default_rng(9)
+    y = rng.normal(size=(6, 3))
+    x = y * np.array([1.0, 1.0, -1.0])
+    A = (x - x.mean(0)).T @ (y - y.mean(0))
+    U, _, Vt = np.linalg.svd(A)
+    assert np.linalg.det(U @ Vt) < 0
+    s, R, t = O.umeyama(x, y)
+    assert abs(np.linalg.det(R) - 1) < 1e-12
+    c_closed = ((x - (s * y @ R.T + t)) ** 2).sum()
+    c_bf, _, _ = _brute_force_alignment(x, y)
+    assert abs(c_closed - c_bf) <= 1e-8 * max(1.0, c_bf)
+
+
+# ------------------------------------------------------------------ escalation (Sec. III-D)
+def test_cholesky_matches_library_and_detects_indefinite():
+    rng = np.random.default_rng(10)
+    B = rng.normal(size=(30, 30))
+    A = B @ B.T + 30 * np.eye(30)
+    np.testing.assert_allclose(O.cholesky(A), np.linalg.cholesky(A), rtol=1e-12, atol=1e-12)
+    A[5, 5] = -1.0
+    assert O.cholesky(A) is None
+
+
+def test_escalation_schedule():
+    """An eigenvalue of -0.5 fails at eps = 1e-6, 1e-4, 1e-2 and succeeds at eps = 1 (attempt 4)."""
+    rng = np.random.default_rng(11)
+    Q, _ = np.linalg.qr(rng.normal(size=(14, 14)))
+    lam = np.r_[-0.5, np.linspace(1, 3, 13)]
+    H = Q @ np.diag(lam) @ Q.T
+    Hfull = np.zeros((21, 21)); Hfull[7:, 7:] = H   # keyframe 0 is the anchor
+    g = np.r_[np.zeros(7), rng.normal(size=14)]
+    tau, attempts, ok = O.damped_solve(Hfull, g, 0, 0.0, 1e-6, 6)
+    assert ok and attempts == 4
+    np.testing.assert_allclose((H + 1.0 * np.eye(14)) @ tau[1:].ravel(), -g[7:], atol=1e-10)
+    assert np.all(tau[0] == 0)
+    Hbad = np.zeros((21, 21)); Hbad[7:, 7:] = Q @ np.diag(np.r_[-1e6, lam[1:]]) @ Q.T
+    tau, attempts, ok = O.damped_solve(Hbad, g, 0, 0.0, 1e-6, 6)
+    assert not ok and attempts == 6 and np.all(tau == 0)
+
+
+def test_degenerate_matches_are_skipped():
+    rng = np.random.default_rng(12)
+    Pi = np.c_[rng.normal(size=(10, 3)) + [0, 0, 4], np.ones(10)]
+    Pj = Pi.copy()
+    Pi[3, :3] = 0.0           # zero-range streamed point
+    Pj[5, :3] = np.nan        # non-finite gathered point
+    rec = O.linearize_edge(np.eye(4), np.eye(4), Pi, Pj, make_problem.__defaults__ and dict(
+        sigma_ray=0.003, sigma_dist=10.0, huber_k=1.345, lam=0.0, eps0=1e-6, max_attempts=6))
+    assert rec["n_skipped"] == 2 and rec["n_valid"] == 10 and rec["cost"] < 1e-20
