@@ -1,0 +1,193 @@
+/*
+ * como3r.h -- C ABI of the B300 (sm_103a) unified multi-agent Sim(3) graph refinement.
+ *
+ * The library evaluates and minimises, by Gauss-Newton, the global cost of CoMo3R-SLAM
+ * (arXiv 2605.30488), Sec. III-D, Eq. (global):
+ *
+ *   E = sum_{(i,j) in E} sum_{(m,n) in M_ij} sum_{c=1..4} rho([Sigma_mn^{-1/2} e_mn(T_ij)]_c)
+ *
+ * with the ray-plus-range residual of Eq. (residual), e = [psi(T_ij X_j,n) - psi(X_i,m);
+ * ||T_ij X_j,n|| - ||X_i,m||], psi(X) = X/||X||, T_ij = T_i^{-1} T_j, Sigma_mn = Sigma/q_mn,
+ * Sigma = diag(sigma_r^2 I_3, sigma_d^2), q_mn = sqrt(c_i,m c_j,n) and a component-wise
+ * Huber kernel rho of breakpoint kappa with IRLS weights min(1, kappa/|r|) (Sec. III-A).
+ * Every iteration linearises all edges with the analytic Jacobians of Eq. (jacobian)
+ * chained to both endpoints by -/+ Ad_{T_i^{-1}}, assembles the block-sparse normal
+ * matrix (two diagonal and one off-diagonal 7x7 block per edge), solves Eq. (normal)
+ * (H + lambda diag(H) + eps_r I) tau = -g with eps_r = eps0 * 100^r escalated on
+ * factorisation failure (zero update after max_attempts failures), and retracts
+ * T_i <- Exp(tau_i) T_i with tau = (v, omega, zeta) (Sec. III-D).  The first keyframe
+ * of agent 0 (or the keyframe given as anchor) is held fixed.
+ *
+ * Conventions shared by every call:
+ *   Poses:   double [N][8] = (tx, ty, tz, qx, qy, qz, qw, s): T = [s R(q) t; 0 1] maps
+ *            camera coordinates to world coordinates (Sec. III-A).  Pose arguments may be
+ *            host or device pointers; the library detects which.
+ *   Points:  per keyframe k a row-major H_g x W_g pointmap in k's own camera frame, each
+ *            pixel packed as (x, y, z, confidence) in the storage type of the graph
+ *            (FP16: 8 B, FP32: 16 B, FP64: 32 B per pixel); keyframes concatenated in
+ *            global keyframe order.  Pixels of keyframe k start at sum_{k'<k} P_k'.
+ *   Matches: for edge e = (i, j), int32 [P_i]: the pixel n of keyframe j matched to pixel
+ *            m of keyframe i, or -1 (masked / invalid).  Edges concatenated in edge order.
+ *   Ownership: device input buffers passed at create are borrowed (zero copy) and must
+ *            stay alive and unchanged until como3r_graph_destroy, unless
+ *            desc.copy_inputs = 1, in which case the library copies them into buffers it
+ *            owns (source may then be host or device memory).  The library owns all
+ *            workspaces, the ordering / symbolic factorisation and the captured CUDA
+ *            graphs.
+ *   Streams: all work is enqueued on the stream given at create (0 = legacy default).
+ *            Calls return after the results they write to host memory are available;
+ *            device outputs are complete when the stream reaches the call's end.
+ *   Errors:  0 = OK; > 0 = warning bit set (COMO3R_WARN_*), results valid;
+ *            < 0 = error (COMO3R_ERR_*), outputs untouched unless stated.  No call aborts
+ *            the process or traps on the device.  Handles are not thread-safe: one
+ *            host thread at a time per handle.
+ */
+#ifndef COMO3R_H
+#define COMO3R_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct como3r_graph* como3r_graph_t;
+
+/* Storage type of the packed (x, y, z, confidence) pixels. */
+typedef enum { COMO3R_F16 = 0, COMO3R_F32 = 1, COMO3R_F64 = 2 } como3r_dtype;
+
+/* Arithmetic of the per-match residual / Jacobian / reduction.
+ * PLAIN_FP64: every step in FP64.
+ * MIXED: residuals, Jacobians and per-thread Hessian-block accumulation in FP32 with
+ *        compensated warp merges and FP64 beyond the warp; edge preparation, assembly,
+ *        Cholesky factorisation, solve and Sim(3) retraction stay FP64. */
+typedef enum { COMO3R_PLAIN_FP64 = 0, COMO3R_MIXED = 1 } como3r_mode;
+
+#define COMO3R_OK 0
+#define COMO3R_WARN_SOLVE_FAILED 1   /* all eps attempts failed in >= 1 graph: zero update there */
+#define COMO3R_WARN_SKIPPED 2        /* >= 1 degenerate / non-finite match was skipped */
+#define COMO3R_ERR_INVALID_ARG (-1)
+#define COMO3R_ERR_CUDA (-2)
+#define COMO3R_ERR_OOM (-3)
+#define COMO3R_ERR_UNSUPPORTED (-4)
+
+/* Size of one exported edge record (doubles), see como3r_linearize. */
+#define COMO3R_EDGE_RECORD 64
+
+/* One batch of independent graphs in a flat keyframe index space (Sec. III-D: all
+ * keyframes of all agents in one global index with a side map a(i)). */
+typedef struct {
+  int32_t num_graphs;            /* G >= 1 */
+  const int32_t* kf_offset;      /* host [G+1]: keyframes of graph g are [kf_offset[g], kf_offset[g+1]) */
+  const int32_t* height;         /* host [G]: pointmap rows of graph g (> 0) */
+  const int32_t* width;          /* host [G]: pointmap columns of graph g (> 0) */
+  const int32_t* agent_of;       /* host [N] or NULL: originating agent a(i) of each keyframe */
+  const void* points_conf;       /* [sum_k P_k][4] packed pixels, see Points above */
+  int32_t dtype;                 /* como3r_dtype of points_conf */
+  const int32_t* edge_offset;    /* host [G+1]: edges of graph g are [edge_offset[g], edge_offset[g+1]) */
+  const int32_t* edge_i;         /* host [E]: streamed keyframe (global id) */
+  const int32_t* edge_j;         /* host [E]: gathered keyframe (global id), same graph, != edge_i */
+  const int32_t* match_idx;      /* [sum_e P_{edge_i[e]}] pixel of j or -1, see Matches above */
+  const int32_t* anchor;         /* host [G] or NULL: fixed keyframe of each graph (default:
+                                    the first keyframe of the graph's lowest agent) */
+  double sigma_ray;              /* sigma_r > 0, paper: 0.003 */
+  double sigma_dist;             /* sigma_d > 0, paper: 10 */
+  double huber_k;                /* kappa > 0, paper: 1.345 */
+  double lambda;                 /* lambda >= 0 of Eq. (normal); back-end default 0 */
+  double eps0;                   /* eps_0 > 0, paper: 1e-6 */
+  int32_t max_attempts;          /* 1..16, paper: 6 */
+  int32_t mode;                  /* como3r_mode */
+  int32_t copy_inputs;           /* 0: borrow device buffers; 1: copy points/matches (host or device) */
+} como3r_graph_desc;
+
+/* Per-graph result of one linearisation / iteration. */
+typedef struct {
+  double cost;                   /* E at the linearisation point (Eq. global) */
+  int32_t attempts;              /* factorisation attempts made (1..max_attempts) */
+  int32_t solved;                /* 1: a factorisation succeeded; 0: zero update applied */
+  int64_t valid_matches;         /* matches with match_idx >= 0 */
+  int64_t skipped_matches;       /* of those, skipped as degenerate / non-finite */
+} como3r_graph_info;
+
+/* Validate the description, plan the solve (fill-reducing ordering, symbolic block
+ * factorisation, work lists), allocate workspaces and check every match index on the
+ * device (-1 <= n < P_j).  Synchronises the stream once.  On error *out is NULL.
+ * Errors: INVALID_ARG (bad sizes / ids / indices / parameters), OOM, CUDA. */
+int como3r_graph_create(const como3r_graph_desc* desc, void* cuda_stream, como3r_graph_t* out);
+
+/* Release every resource of the handle (NULL is allowed). */
+void como3r_graph_destroy(como3r_graph_t graph);
+
+/* One Gauss-Newton iteration for every graph: linearise all edges at `poses`, assemble,
+ * solve Eq. (normal) with eps escalation, retract `poses` in place (Sec. III-D).
+ *   poses  [N][8] in/out (host or device).
+ *   H_out  device [7N][7N] row-major or NULL: the assembled H before damping, on the
+ *          flat keyframe index; rows/columns of anchors and every pair without a block
+ *          are zero.  g_out device [7N] or NULL: the assembled gradient (anchors zero).
+ *   info   host [G] or NULL.
+ * Returns OK or a warning bitmask, or an error. */
+int como3r_gn_step(como3r_graph_t graph, double* poses, double* H_out, double* g_out,
+                   como3r_graph_info* info);
+
+/* `iters` Gauss-Newton iterations (>= 0), replayed from a captured CUDA graph.
+ *   poses       [N][8] in/out (host or device).
+ *   cost_trace  host [(iters+1) * G] or NULL: cost of graph g before iteration k at
+ *               [k*G + g], and after the last retraction at [iters*G + g].
+ *   info        host [G] or NULL: result of the last iteration.
+ * Returns OK or the OR of the warnings of all iterations, or an error. */
+int como3r_solve(como3r_graph_t graph, double* poses, int32_t iters, double* cost_trace,
+                 como3r_graph_info* info);
+
+/* Linearise every edge at `poses` without solving.
+ *   edge_out device [E][COMO3R_EDGE_RECORD] or NULL: per edge e = (i, j) the blocks with
+ *            respect to a left perturbation of T_ij: [0..48] H_rel = sum J^T W J row-major,
+ *            [49..55] g_rel = sum J^T W e, [56] cost, [57] valid matches, [58] skipped.
+ *            (The endpoint blocks follow as H_jj = H_ii = -H_ij = Ad^T H_rel Ad,
+ *            g_j = -g_i = Ad^T g_rel with Ad = Ad_{T_i^{-1}}.)
+ *   cost_out host [G] or NULL. */
+int como3r_linearize(como3r_graph_t graph, const double* poses, double* edge_out, double* cost_out);
+
+/* Left retraction T_k <- Exp(tau_k) T_k (Sec. III-D) of n poses, tau_k = (v, omega, zeta).
+ *   tau   device [n][7]; poses device [n][8] in/out; stream as at create (may be NULL).
+ * Independent of any graph handle. */
+int como3r_sim3_retract(const double* tau, double* poses, int32_t n, void* cuda_stream);
+
+/* Replace the pointmaps and matches of a graph created with copy_inputs = 1 (same sizes);
+ * sources may be host or device memory.  Either pointer may be NULL (kept).  The copy is
+ * enqueued on the graph's stream; host sources must stay valid until the stream passes it
+ * (pinned host memory makes the copy asynchronous). */
+int como3r_update_inputs(como3r_graph_t graph, const void* points_conf, const int32_t* match_idx);
+
+/* Number of kernels the last gn_step / solve / linearize call enqueued (for accounting). */
+int64_t como3r_last_launch_count(como3r_graph_t graph);
+
+/* Static description of the planned work (see COMO3R_STAT_* indices). */
+#define COMO3R_STAT_GRAPHS 0
+#define COMO3R_STAT_KEYFRAMES 1
+#define COMO3R_STAT_EDGES 2
+#define COMO3R_STAT_ITEMS 3          /* K1 work items */
+#define COMO3R_STAT_COLUMNS 4        /* block columns of the factor (all graphs) */
+#define COMO3R_STAT_BLOCKS 5         /* stored 7x7 blocks of the factor, incl. diagonal */
+#define COMO3R_STAT_FILL 6           /* of those, fill blocks (no edge) */
+#define COMO3R_STAT_UPDATES 7        /* 7x7 block updates of one factorisation */
+#define COMO3R_STAT_LEVELS 8         /* max elimination-tree levels of one graph */
+#define COMO3R_STAT_VALID 9          /* valid matches (all edges) */
+#define COMO3R_STAT_CHUNK 10         /* K1 pixels per work item */
+#define COMO3R_STAT_BLOCK 11         /* K1 threads per CTA */
+#define COMO3R_STAT_GRID 12          /* K1 CTAs */
+#define COMO3R_STAT_SMEM_SOLVE 13    /* 1 if the factor of every graph fits in shared memory */
+#define COMO3R_STAT_COUNT 16
+int como3r_graph_stats(como3r_graph_t graph, int64_t* stats /* [COMO3R_STAT_COUNT] */);
+
+/* Plan a description on the host only (no device memory touched): fills the same stats
+ * as como3r_graph_stats (K1 launch fields 0).  For inspecting orderings without a GPU. */
+int como3r_plan_stats(const como3r_graph_desc* desc, int64_t* stats /* [COMO3R_STAT_COUNT] */);
+
+/* Human-readable text of a status code. */
+const char* como3r_status_str(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COMO3R_H */

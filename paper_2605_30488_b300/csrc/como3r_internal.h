@@ -1,0 +1,89 @@
+// Internal declarations shared by the host planner, the C ABI and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace como3r {
+
+// Doubles per K1 work-item partial: [0..24] H_rel unique entries, [25..31] g_rel,
+// [32] cost, [33] skipped matches, [34..35] unused.
+constexpr int kPartial = 36;
+// Unique nonzero H_rel entries kept by K1 (the (omega, zeta) block is identically zero):
+// vv (00 01 02 11 12 22), v-omega (3x3 row-major), omega-omega (00 01 02 11 12 22),
+// v-zeta (3), zeta-zeta (1).
+constexpr int kHUnique = 25;
+constexpr int kEdgeRec = 64;   // exported edge record (doubles)
+
+struct Item {                  // one K1 work item: pixels [begin, end) of edge `edge`
+  int32_t edge, begin, end, pad;
+};
+
+struct EdgeStatic {            // per edge, fixed at create
+  int64_t pix_i;               // first pixel of keyframe i in the packed points
+  int64_t pix_j;               // first pixel of keyframe j
+  int64_t idx_off;             // first entry of the edge in match_idx
+  int32_t i, j;                // global keyframe ids
+  int32_t npix_i, npix_j;      // pixel counts of i and j
+};
+
+struct RobustParams {          // whitening and Huber constants (Sec. III-A)
+  double inv_sigma_ray, inv_sigma_dist;      // 1/sigma_r, 1/sigma_d
+  double inv_var_ray, inv_var_dist;          // 1/sigma_r^2, 1/sigma_d^2
+  double kappa;
+};
+
+struct GraphInfoDev {          // per graph, written on the device
+  double cost;
+  int32_t attempts;
+  int32_t solved;
+  long long skipped;
+};
+
+// Solver plan of all graphs, flattened (device arrays).  Block columns are numbered
+// globally; the columns of graph g are [col_begin[g], col_begin[g+1]) in elimination
+// order.  Slot s is one stored 7x7 block (row-major) of the factor.
+struct SolverPlan {
+  const int32_t* col_begin;    // [G+1]
+  const int32_t* col_kf;       // [C] keyframe of each column
+  const int32_t* col_slot;     // [C+1] slots of column c: diagonal at col_slot[c], then its rows
+  const int32_t* slot_row;     // [S] block row (global column id) of each slot
+  const int32_t* tri_off;      // [C+1] left-looking update triplets of column c
+  const int4* tri;             // [T] (src_r, src_k, dst, 0): L[dst] -= L[src_r] L[src_k]^T
+  const int32_t* rs_off;       // [C+1] row structure of column c
+  const int2* rs;              // [R] (slot of block (c, j), j) for the columns j < c with L_cj != 0
+  const int32_t* sched;        // [C] columns of each graph sorted by elimination-tree level
+  const int32_t* lvl_begin;    // [G+1] level range of graph g in lvl_off
+  const int32_t* lvl_off;      // [L+1] offsets of the levels in sched
+};
+
+// ---- kernel launchers (defined in the .cu files) ----
+cudaError_t launch_edge_prep(const double* poses, const EdgeStatic* es, int E, double* T64, float* T32,
+                             double* Ad, cudaStream_t s);
+cudaError_t launch_residual_reduce(int mode, int dtype, int block, int grid, const void* points,
+                                   const int32_t* midx, const Item* items, int num_items,
+                                   const EdgeStatic* es, const double* T64, const float* T32,
+                                   RobustParams rp, double* partials, cudaStream_t s);
+int residual_reduce_max_blocks_per_sm(int mode, int dtype, int block);
+cudaError_t launch_edge_reduce(const double* partials, const int32_t* item_off, int E, const double* Ad,
+                               double* edge_M, double* edge_b, double* edge_cost, double* edge_skip,
+                               double* edge_rec, const long long* edge_valid, cudaStream_t s);
+cudaError_t launch_assemble(int num_slots, const int32_t* slot_contrib_off, const int32_t* slot_contrib,
+                            const double* edge_M, double* A, int N, const int32_t* kf_contrib_off,
+                            const int32_t* kf_contrib, const double* edge_b, double* gvec, int G,
+                            const int32_t* edge_offset, const double* edge_cost, const double* edge_skip,
+                            GraphInfoDev* ginfo, double* cost_hist, const int* iter_counter, int* warn,
+                            cudaStream_t s);
+cudaError_t launch_export_dense(int num_slots, const int32_t* slot_kf_r, const int32_t* slot_kf_c,
+                                const double* A, int N, const double* gvec, double* H_out, double* g_out,
+                                cudaStream_t s);
+cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t smem_bytes, const double* A,
+                                double* L, double* Dinv, const double* gvec, double* y, double* tau,
+                                double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
+                                cudaStream_t s);
+size_t factor_solve_max_smem();
+cudaError_t launch_retract(const double* tau, double* poses, const uint8_t* frozen, int N, int* iter_counter,
+                           cudaStream_t s);
+cudaError_t launch_check_matches(const int32_t* midx, const EdgeStatic* es, int E, unsigned long long* bad,
+                                 long long* edge_valid, cudaStream_t s);
+
+}  // namespace como3r
