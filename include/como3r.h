@@ -186,6 +186,9 @@ int como3r_plan_stats(const como3r_graph_desc* desc, int64_t* stats /* [COMO3R_S
 /* Human-readable text of a status code. */
 const char* como3r_status_str(int code);
 
+/* Message of the last error returned to the calling host thread ("" if none). */
+const char* como3r_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

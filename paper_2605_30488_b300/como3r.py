@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libcomo3r.so (the C ABI in include/como3r.h).
+
+Argument marshalling only: every step of the refinement runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the current stream.  If the shared library
+is missing the import of this module raises, so there is no silent fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcomo3r.so")
+
+OK = 0
+WARN_SOLVE_FAILED = 1
+WARN_SKIPPED = 2
+ERR_INVALID_ARG = -1
+ERR_CUDA = -2
+ERR_OOM = -3
+ERR_UNSUPPORTED = -4
+F16, F32, F64 = 0, 1, 2
+PLAIN_FP64, MIXED = 0, 1
+EDGE_RECORD = 64
+STAT_NAMES = ["graphs", "keyframes", "edges", "items", "columns", "blocks", "fill", "updates", "levels",
+              "valid", "chunk", "block", "grid", "smem_solve", "r14", "r15"]
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [
+        ("num_graphs", ctypes.c_int32),
+        ("kf_offset", _i32p), ("height", _i32p), ("width", _i32p), ("agent_of", _i32p),
+        ("points_conf", ctypes.c_void_p), ("dtype", ctypes.c_int32),
+        ("edge_offset", _i32p), ("edge_i", _i32p), ("edge_j", _i32p),
+        ("match_idx", ctypes.c_void_p), ("anchor", _i32p),
+        ("sigma_ray", ctypes.c_double), ("sigma_dist", ctypes.c_double), ("huber_k", ctypes.c_double),
+        ("lam", ctypes.c_double), ("eps0", ctypes.c_double),
+        ("max_attempts", ctypes.c_int32), ("mode", ctypes.c_int32), ("copy_inputs", ctypes.c_int32),
+    ]
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("cost", ctypes.c_double), ("attempts", ctypes.c_int32), ("solved", ctypes.c_int32),
+                ("valid_matches", ctypes.c_int64), ("skipped_matches", ctypes.c_int64)]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcomo3r.so not built ({path}); run `python -m paper_2605_30488_b300.build`")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.como3r_graph_create.argtypes = [ctypes.POINTER(GraphDesc), vp, ctypes.POINTER(vp)]
+    lib.como3r_graph_destroy.argtypes = [vp]
+    lib.como3r_graph_destroy.restype = None
+    lib.como3r_gn_step.argtypes = [vp, vp, vp, vp, ctypes.POINTER(GraphInfo)]
+    lib.como3r_solve.argtypes = [vp, vp, ctypes.c_int32, _f64p, ctypes.POINTER(GraphInfo)]
+    lib.como3r_linearize.argtypes = [vp, vp, vp, _f64p]
+    lib.como3r_sim3_retract.argtypes = [vp, vp, ctypes.c_int32, vp]
+    lib.como3r_update_inputs.argtypes = [vp, vp, vp]
+    lib.como3r_last_launch_count.argtypes = [vp]
+    lib.como3r_last_launch_count.restype = ctypes.c_int64
+    lib.como3r_graph_stats.argtypes = [vp, _i64p]
+    lib.como3r_plan_stats.argtypes = [ctypes.POINTER(GraphDesc), _i64p]
+    lib.como3r_status_str.argtypes = [ctypes.c_int]
+    lib.como3r_status_str.restype = ctypes.c_char_p
+    lib.como3r_last_error.argtypes = []
+    lib.como3r_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+class Como3rError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().como3r_last_error().decode() or lib().como3r_status_str(code).decode()
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+def _check(code: int, where: str) -> int:
+    if code < 0:
+        raise Como3rError(code, where)
+    return code
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or a numpy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _dtype_code(np_dtype) -> int:
+    return {np.dtype(np.float16): F16, np.dtype(np.float32): F32, np.dtype(np.float64): F64}[np.dtype(np_dtype)]
+
+
+def _torch_stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _build_desc(prob, points_ptr, midx_ptr, mode: int, copy_inputs: bool, keep: list) -> GraphDesc:
+    arrs = dict(kf_offset=_i32(prob.kf_offset), height=_i32(prob.height), width=_i32(prob.width),
+                agent_of=_i32(prob.agent_of), edge_offset=_i32(prob.edge_offset), edge_i=_i32(prob.edge_i),
+                edge_j=_i32(prob.edge_j), anchor=_i32(prob.anchor))
+    keep.append(arrs)
+    d = GraphDesc()
+    d.num_graphs = len(arrs["kf_offset"]) - 1
+    for k in ("kf_offset", "height", "width", "agent_of", "edge_offset", "edge_i", "edge_j", "anchor"):
+        setattr(d, k, arrs[k].ctypes.data_as(_i32p))
+    d.points_conf = points_ptr
+    d.dtype = _dtype_code(prob.points.dtype)
+    d.match_idx = midx_ptr
+    d.sigma_ray, d.sigma_dist, d.huber_k = prob.sigma_ray, prob.sigma_dist, prob.huber_k
+    d.lam, d.eps0, d.max_attempts = prob.lam, prob.eps0, prob.max_attempts
+    d.mode = mode
+    d.copy_inputs = 1 if copy_inputs else 0
+    return d
+
+
+def plan_stats(prob) -> dict:
+    """Host-only plan of a problem (ordering, factor pattern); no GPU needed."""
+    keep = []
+    pts = np.zeros(4, dtype=prob.points.dtype)  # non-NULL placeholder; never dereferenced
+    d = _build_desc(prob, _ptr(pts), _ptr(np.zeros(1, np.int32)), MIXED, False, keep)
+    out = (ctypes.c_int64 * 16)()
+    _check(lib().como3r_plan_stats(ctypes.byref(d), out), "plan_stats")
+    return dict(zip(STAT_NAMES, list(out)))
+
+
+class Graph:
+    """One handle of como3r_graph_create over a problem's arrays (synth.Problem-like).
+
+    `points` / `match_idx` default to device copies of the problem's arrays held by this
+    object (borrowed by the library); with copy_inputs=True the library copies them (host
+    or device sources) into its own buffers.
+    """
+
+    def __init__(self, prob, mode: int = MIXED, points=None, match_idx=None, copy_inputs: bool = False,
+                 stream=None, device: str = "cuda"):
+        import torch
+        self.prob = prob
+        self.N = prob.num_kf
+        self.G = prob.num_graphs
+        self.E = prob.num_edges
+        self._keep = []
+        if points is None:
+            points = torch.from_numpy(np.ascontiguousarray(prob.points))
+            points = points.pin_memory() if copy_inputs else points.to(device)
+        if match_idx is None:
+            match_idx = torch.from_numpy(np.ascontiguousarray(prob.match_idx.astype(np.int32)))
+            match_idx = match_idx.pin_memory() if copy_inputs else match_idx.to(device)
+        self.points, self.match_idx = points, match_idx
+        self._stream = _torch_stream(stream)
+        d = _build_desc(prob, _ptr(points), _ptr(match_idx), mode, copy_inputs, self._keep)
+        h = ctypes.c_void_p()
+        _check(lib().como3r_graph_create(ctypes.byref(d), self._stream, ctypes.byref(h)), "graph_create")
+        self.handle = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().como3r_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls
+    def gn_step(self, poses, H_out=None, g_out=None):
+        info = (GraphInfo * self.G)()
+        st = _check(lib().como3r_gn_step(self.handle, _ptr(poses), _ptr(H_out), _ptr(g_out), info), "gn_step")
+        return st, [_info_dict(x) for x in info]
+
+    def solve(self, poses, iters: int, trace: bool = True):
+        info = (GraphInfo * self.G)()
+        tr = np.zeros((iters + 1) * self.G) if trace else None
+        st = _check(lib().como3r_solve(self.handle, _ptr(poses), int(iters),
+                                       tr.ctypes.data_as(_f64p) if trace else None, info), "solve")
+        return st, (tr.reshape(iters + 1, self.G) if trace else None), [_info_dict(x) for x in info]
+
+    def linearize(self, poses, edge_out=None):
+        cost = np.zeros(self.G)
+        st = _check(lib().como3r_linearize(self.handle, _ptr(poses), _ptr(edge_out), cost.ctypes.data_as(_f64p)),
+                    "linearize")
+        return st, cost
+
+    def update_inputs(self, points=None, match_idx=None):
+        _check(lib().como3r_update_inputs(self.handle, _ptr(points), _ptr(match_idx)), "update_inputs")
+
+    def last_launch_count(self) -> int:
+        return int(lib().como3r_last_launch_count(self.handle))
+
+    def stats(self) -> dict:
+        out = (ctypes.c_int64 * 16)()
+        _check(lib().como3r_graph_stats(self.handle, out), "graph_stats")
+        return dict(zip(STAT_NAMES, list(out)))
+
+
+def _info_dict(x: GraphInfo) -> dict:
+    return dict(cost=x.cost, attempts=x.attempts, solved=bool(x.solved), valid_matches=x.valid_matches,
+                skipped_matches=x.skipped_matches)
+
+
+def sim3_retract(tau, poses, stream=None) -> None:
+    """poses[k] <- Exp(tau[k]) poses[k] on the device (tau [n, 7], poses [n, 8], float64 CUDA tensors)."""
+    n = int(poses.shape[0])
+    _check(lib().como3r_sim3_retract(_ptr(tau), _ptr(poses), n, _torch_stream(stream)), "sim3_retract")
+
+
+def exported_symbols(header: str) -> Sequence[str]:
+    """Names of the functions a header declares (used by the ABI-load test)."""
+    import re
+    txt = open(header).read()
+    return re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(como3r_[a-z_0-9]+)\s*\(", txt, flags=re.M)

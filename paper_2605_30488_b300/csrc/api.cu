@@ -1,0 +1,451 @@
+// C ABI of the library (declared in include/como3r.h): graph handles, workspaces,
+// per-iteration launch sequence and its CUDA-graph replay.
+//
+// One iteration is six launches on the handle's stream:
+//   K0 edge_prep -> K1 residual_reduce -> K2 edge_reduce -> assemble -> K3 factor_solve -> K4 retract
+// como3r_solve captures them once into a CUDA graph (on a private capture stream) and
+// replays it; a device counter indexes the per-iteration cost trace.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/como3r.h"
+#include "como3r_internal.h"
+#include "plan.h"
+
+using namespace como3r;
+
+namespace {
+thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation) return set_error(COMO3R_ERR_OOM, std::string(where) + ": out of device memory");
+  return set_error(COMO3R_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                      \
+  do {                                       \
+    cudaError_t e_ = (expr);                 \
+    if (e_ != cudaSuccess) return cuda_error(e_, where); \
+  } while (0)
+
+constexpr int kDefaultBlock = 256;
+constexpr int kDefaultChunk = 8192;
+}  // namespace
+
+struct como3r_graph {
+  HostPlan plan;
+  int device = 0, sms = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  RobustParams rp{};
+  double lambda = 0.0, eps0 = 1e-6;
+  int max_attempts = 6;
+  int k1_block = kDefaultBlock, k1_chunk = kDefaultChunk, k1_grid = 0, num_items = 0;
+  std::vector<void*> allocs;
+  const void* points = nullptr;
+  const int32_t* midx = nullptr;
+  void* own_points = nullptr;
+  int32_t* own_midx = nullptr;
+  size_t points_bytes = 0, idx_bytes = 0;
+  EdgeStatic* d_es = nullptr;
+  Item* d_items = nullptr;
+  int32_t* d_item_off = nullptr;
+  double *d_T64 = nullptr, *d_Ad = nullptr, *d_partials = nullptr;
+  float* d_T32 = nullptr;
+  double *d_edge_M = nullptr, *d_edge_b = nullptr, *d_edge_cost = nullptr, *d_edge_skip = nullptr;
+  long long* d_edge_valid = nullptr;
+  int32_t *d_slot_kf_r = nullptr, *d_slot_kf_c = nullptr, *d_slot_contrib_off = nullptr, *d_slot_contrib = nullptr;
+  int32_t *d_kf_contrib_off = nullptr, *d_kf_contrib = nullptr, *d_edge_offset = nullptr;
+  double *d_A = nullptr, *d_L = nullptr, *d_Dinv = nullptr, *d_y = nullptr, *d_gvec = nullptr, *d_tau = nullptr;
+  uint8_t* d_frozen = nullptr;
+  GraphInfoDev* d_ginfo = nullptr;
+  int *d_iter = nullptr, *d_warn = nullptr;
+  double* d_cost_hist = nullptr;
+  int64_t cost_hist_cap = 0;
+  double* d_poses = nullptr;
+  GraphInfoDev* h_ginfo = nullptr;
+  int* h_warn = nullptr;
+  unsigned long long* d_bad = nullptr;
+  bool smem_solve = false;
+  size_t solve_smem = 0;
+  SolverPlan sp{};
+  cudaGraphExec_t iter_exec = nullptr, eval_exec = nullptr;
+  int64_t last_launches = 0;
+  std::vector<long long> edge_valid;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(como3r_graph* g, T** p, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc");
+  g->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return COMO3R_OK;
+}
+
+template <typename T>
+int upload(como3r_graph* g, T** p, const std::vector<T>& v) {
+  int rc = dalloc(g, p, v.size());
+  if (rc) return rc;
+  if (!v.empty()) CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, g->stream), "upload");
+  return COMO3R_OK;
+}
+
+void free_all(como3r_graph* g) {
+  if (g->iter_exec) cudaGraphExecDestroy(g->iter_exec);
+  if (g->eval_exec) cudaGraphExecDestroy(g->eval_exec);
+  for (void* p : g->allocs) cudaFree(p);
+  g->allocs.clear();
+  if (g->h_ginfo) cudaFreeHost(g->h_ginfo);
+  if (g->h_warn) cudaFreeHost(g->h_warn);
+  if (g->cap) cudaStreamDestroy(g->cap);
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int enqueue_linearize(como3r_graph* g, cudaStream_t s, double* cost_hist, const int* iter, double* edge_rec) {
+  const HostPlan& p = g->plan;
+  CK(launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, s), "edge_prep");
+  CK(launch_residual_reduce(p.mode, p.dtype, g->k1_block, g->k1_grid, g->points, g->midx, g->d_items, g->num_items,
+                            g->d_es, g->d_T64, g->d_T32, g->rp, g->d_partials, s),
+     "residual_reduce");
+  CK(launch_edge_reduce(g->d_partials, g->d_item_off, p.E, g->d_Ad, g->d_edge_M, g->d_edge_b, g->d_edge_cost,
+                        g->d_edge_skip, edge_rec, g->d_edge_valid, s),
+     "edge_reduce");
+  const int nslots = p.col_slot.back();
+  CK(launch_assemble(nslots, g->d_slot_contrib_off, g->d_slot_contrib, g->d_edge_M, g->d_A, p.N, g->d_kf_contrib_off,
+                     g->d_kf_contrib, g->d_edge_b, g->d_gvec, p.G, g->d_edge_offset, g->d_edge_cost, g->d_edge_skip,
+                     g->d_ginfo, cost_hist, iter, g->d_warn, s),
+     "assemble");
+  return COMO3R_OK;
+}
+
+int enqueue_solve(como3r_graph* g, cudaStream_t s, int* iter) {
+  const HostPlan& p = g->plan;
+  CK(launch_factor_solve(p.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_Dinv, g->d_gvec, g->d_y,
+                         g->d_tau, g->lambda, g->eps0, g->max_attempts, g->d_ginfo, g->d_warn, s),
+     "factor_solve");
+  CK(launch_retract(g->d_tau, g->d_poses, g->d_frozen, p.N, iter, s), "retract");
+  return COMO3R_OK;
+}
+
+int finish_info(como3r_graph* g, como3r_graph_info* info) {
+  const HostPlan& p = g->plan;
+  if (info) {
+    for (int k = 0; k < p.G; ++k) {
+      info[k].cost = g->h_ginfo[k].cost;
+      info[k].attempts = g->h_ginfo[k].attempts;
+      info[k].solved = g->h_ginfo[k].solved;
+      info[k].skipped_matches = g->h_ginfo[k].skipped;
+      int64_t v = 0;
+      for (int e = p.edge_offset[k]; e < p.edge_offset[k + 1]; ++e) v += g->edge_valid[e];
+      info[k].valid_matches = v;
+    }
+  }
+  return *g->h_warn;
+}
+
+int capture(como3r_graph* g, bool with_solve, cudaGraphExec_t* exec) {
+  CK(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal), "capture begin");
+  int rc = enqueue_linearize(g, g->cap, g->d_cost_hist, g->d_iter, nullptr);
+  if (!rc && with_solve) rc = enqueue_solve(g, g->cap, g->d_iter);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(g->cap, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_error(e, "capture end");
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_error(e, "graph instantiate");
+  return COMO3R_OK;
+}
+
+int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
+  HostPlan& p = g->plan;
+  int rc = build_plan(d, p);
+  if (rc) return set_error(rc, p.error);
+  CK(cudaGetDevice(&g->device), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device), "attribute");
+  CK(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking), "stream create");
+  g->rp.inv_sigma_ray = 1.0 / d->sigma_ray;
+  g->rp.inv_sigma_dist = 1.0 / d->sigma_dist;
+  g->rp.inv_var_ray = 1.0 / (d->sigma_ray * d->sigma_ray);
+  g->rp.inv_var_dist = 1.0 / (d->sigma_dist * d->sigma_dist);
+  g->rp.kappa = d->huber_k;
+  g->lambda = d->lambda;
+  g->eps0 = d->eps0;
+  g->max_attempts = d->max_attempts;
+  const size_t bpp = d->dtype == COMO3R_F16 ? 8 : (d->dtype == COMO3R_F32 ? 16 : 32);
+  g->points_bytes = (size_t)p.total_px * bpp;
+  g->idx_bytes = (size_t)p.total_idx * sizeof(int32_t);
+  if (d->copy_inputs) {
+    if ((rc = dalloc(g, (char**)&g->own_points, g->points_bytes))) return rc;
+    if ((rc = dalloc(g, &g->own_midx, p.total_idx))) return rc;
+    CK(cudaMemcpyAsync(g->own_points, d->points_conf, g->points_bytes, cudaMemcpyDefault, g->stream), "copy points");
+    if (p.total_idx)
+      CK(cudaMemcpyAsync(g->own_midx, d->match_idx, g->idx_bytes, cudaMemcpyDefault, g->stream), "copy matches");
+    g->points = g->own_points;
+    g->midx = g->own_midx;
+  } else {
+    if (!is_device_pointer(d->points_conf) || (p.total_idx && !is_device_pointer(d->match_idx)))
+      return set_error(COMO3R_ERR_INVALID_ARG, "points_conf / match_idx must be device memory unless copy_inputs = 1");
+    if (reinterpret_cast<uintptr_t>(d->points_conf) % 16 || reinterpret_cast<uintptr_t>(d->match_idx) % 4)
+      return set_error(COMO3R_ERR_INVALID_ARG, "points_conf must be 16-byte and match_idx 4-byte aligned");
+    g->points = d->points_conf;
+    g->midx = d->match_idx;
+  }
+  // K1 launch shape
+  std::vector<Item> items;
+  std::vector<int32_t> item_off;
+  build_items(p, g->k1_chunk, items, item_off);
+  g->num_items = (int)items.size();
+  const int occ = residual_reduce_max_blocks_per_sm(p.mode, p.dtype, g->k1_block);
+  g->k1_grid = std::max(1, std::min(g->num_items, g->sms * std::max(occ, 1)));
+  const int E = p.E, N = p.N, G = p.G;
+  const int nslots = p.col_slot.back(), ncols = p.col_begin.back();
+  if ((rc = upload(g, &g->d_es, p.es)) || (rc = upload(g, &g->d_items, items)) ||
+      (rc = upload(g, &g->d_item_off, item_off)) || (rc = dalloc(g, &g->d_T64, (size_t)E * 12)) ||
+      (rc = dalloc(g, &g->d_T32, (size_t)E * 16)) || (rc = dalloc(g, &g->d_Ad, (size_t)E * 49)) ||
+      (rc = dalloc(g, &g->d_partials, (size_t)g->num_items * kPartial)) ||
+      (rc = dalloc(g, &g->d_edge_M, (size_t)E * 49)) || (rc = dalloc(g, &g->d_edge_b, (size_t)E * 7)) ||
+      (rc = dalloc(g, &g->d_edge_cost, E)) || (rc = dalloc(g, &g->d_edge_skip, E)) ||
+      (rc = dalloc(g, &g->d_edge_valid, E)) || (rc = upload(g, &g->d_slot_kf_r, p.slot_kf_r)) ||
+      (rc = upload(g, &g->d_slot_kf_c, p.slot_kf_c)) || (rc = upload(g, &g->d_slot_contrib_off, p.slot_contrib_off)) ||
+      (rc = upload(g, &g->d_slot_contrib, p.slot_contrib)) ||
+      (rc = upload(g, &g->d_kf_contrib_off, p.kf_contrib_off)) || (rc = upload(g, &g->d_kf_contrib, p.kf_contrib)) ||
+      (rc = upload(g, &g->d_edge_offset, p.edge_offset)) || (rc = dalloc(g, &g->d_A, (size_t)nslots * 49)) ||
+      (rc = dalloc(g, &g->d_L, (size_t)nslots * 49)) || (rc = dalloc(g, &g->d_Dinv, (size_t)ncols * 7)) ||
+      (rc = dalloc(g, &g->d_y, (size_t)ncols * 7)) || (rc = dalloc(g, &g->d_gvec, (size_t)N * 7)) ||
+      (rc = dalloc(g, &g->d_tau, (size_t)N * 7)) || (rc = upload(g, &g->d_frozen, p.frozen)) ||
+      (rc = dalloc(g, &g->d_ginfo, G)) || (rc = dalloc(g, &g->d_iter, 1)) || (rc = dalloc(g, &g->d_warn, 1)) ||
+      (rc = dalloc(g, &g->d_poses, (size_t)N * 8)) || (rc = dalloc(g, &g->d_bad, 1)))
+    return rc;
+  // solver plan
+  int32_t *col_begin, *col_kf, *col_slot, *slot_row, *tri_off, *rs_off, *sched, *lvl_begin, *lvl_off;
+  int4* tri;
+  int2* rs;
+  if ((rc = upload(g, &col_begin, p.col_begin)) || (rc = upload(g, &col_kf, p.col_kf)) ||
+      (rc = upload(g, &col_slot, p.col_slot)) || (rc = upload(g, &slot_row, p.slot_row)) ||
+      (rc = upload(g, &tri_off, p.tri_off)) || (rc = upload(g, &tri, p.tri)) || (rc = upload(g, &rs_off, p.rs_off)) ||
+      (rc = upload(g, &rs, p.rs)) || (rc = upload(g, &sched, p.sched)) || (rc = upload(g, &lvl_begin, p.lvl_begin)) ||
+      (rc = upload(g, &lvl_off, p.lvl_off)))
+    return rc;
+  g->sp = SolverPlan{col_begin, col_kf, col_slot, slot_row, tri_off, tri, rs_off, rs, sched, lvl_begin, lvl_off};
+  CK(cudaMallocHost(&g->h_ginfo, sizeof(GraphInfoDev) * G), "cudaMallocHost");
+  CK(cudaMallocHost(&g->h_warn, sizeof(int)), "cudaMallocHost");
+  CK(cudaMemsetAsync(g->d_tau, 0, sizeof(double) * 7 * (size_t)N, g->stream), "memset");
+  CK(cudaMemsetAsync(g->d_ginfo, 0, sizeof(GraphInfoDev) * G, g->stream), "memset");
+  // shared-memory factor when every graph fits
+  const size_t smax = factor_solve_max_smem();
+  g->smem_solve = p.max_graph_smem <= smax;
+  if (g->smem_solve) {
+    g->solve_smem = p.max_graph_smem;
+    CK(factor_solve_prepare(g->solve_smem), "solver smem attribute");
+  }
+  // match index check and valid counts
+  CK(cudaMemsetAsync(g->d_bad, 0, sizeof(unsigned long long), g->stream), "memset");
+  CK(cudaMemsetAsync(g->d_edge_valid, 0, sizeof(long long) * std::max(E, 1), g->stream), "memset");
+  CK(launch_check_matches(g->midx, g->d_es, E, g->d_bad, g->d_edge_valid, g->stream), "check_matches");
+  unsigned long long bad = 0;
+  g->edge_valid.assign(E, 0);
+  CK(cudaMemcpyAsync(&bad, g->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, g->stream), "readback");
+  if (E) CK(cudaMemcpyAsync(g->edge_valid.data(), g->d_edge_valid, sizeof(long long) * E, cudaMemcpyDeviceToHost, g->stream), "readback");
+  CK(cudaStreamSynchronize(g->stream), "create sync");
+  if (bad) return set_error(COMO3R_ERR_INVALID_ARG, std::to_string(bad) + " match indices outside [-1, P_j)");
+  return COMO3R_OK;
+}
+
+int begin_call(como3r_graph* g, const double* poses) {
+  if (!g) return set_error(COMO3R_ERR_INVALID_ARG, "graph handle is NULL");
+  if (!poses) return set_error(COMO3R_ERR_INVALID_ARG, "poses is NULL");
+  CK(cudaMemcpyAsync(g->d_poses, poses, sizeof(double) * 8 * (size_t)g->plan.N, cudaMemcpyDefault, g->stream),
+     "poses in");
+  CK(cudaMemsetAsync(g->d_warn, 0, sizeof(int), g->stream), "memset");
+  return COMO3R_OK;
+}
+
+int end_call(como3r_graph* g, double* poses_out) {
+  if (poses_out)
+    CK(cudaMemcpyAsync(poses_out, g->d_poses, sizeof(double) * 8 * (size_t)g->plan.N, cudaMemcpyDefault, g->stream),
+       "poses out");
+  CK(cudaMemcpyAsync(g->h_ginfo, g->d_ginfo, sizeof(GraphInfoDev) * g->plan.G, cudaMemcpyDeviceToHost, g->stream),
+     "info");
+  CK(cudaMemcpyAsync(g->h_warn, g->d_warn, sizeof(int), cudaMemcpyDeviceToHost, g->stream), "info");
+  CK(cudaStreamSynchronize(g->stream), "sync");
+  return COMO3R_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int como3r_graph_create(const como3r_graph_desc* desc, void* cuda_stream, como3r_graph_t* out) {
+  if (!out) return set_error(COMO3R_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  como3r_graph* g = new (std::nothrow) como3r_graph();
+  if (!g) return set_error(COMO3R_ERR_OOM, "host allocation failed");
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  const int rc = create_impl(g, desc);
+  if (rc) {
+    cudaStreamSynchronize(g->stream);
+    free_all(g);
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return COMO3R_OK;
+}
+
+void como3r_graph_destroy(como3r_graph_t g) {
+  if (!g) return;
+  cudaStreamSynchronize(g->stream);
+  free_all(g);
+  delete g;
+}
+
+int como3r_gn_step(como3r_graph_t g, double* poses, double* H_out, double* g_out, como3r_graph_info* info) {
+  int rc = begin_call(g, poses);
+  if (rc) return rc;
+  const HostPlan& p = g->plan;
+  if ((rc = enqueue_linearize(g, g->stream, nullptr, nullptr, nullptr))) return rc;
+  int64_t launches = 4;
+  if (H_out || g_out) {
+    if (H_out)
+      CK(cudaMemsetAsync(H_out, 0, sizeof(double) * 49 * (size_t)p.N * p.N, g->stream), "memset H_out");
+    CK(launch_export_dense(p.col_slot.back(), g->d_slot_kf_r, g->d_slot_kf_c, g->d_A, p.N, g->d_gvec, H_out, g_out,
+                           g->stream),
+       "export");
+    ++launches;
+  }
+  if ((rc = enqueue_solve(g, g->stream, nullptr))) return rc;
+  g->last_launches = launches + 2;
+  if ((rc = end_call(g, poses))) return rc;
+  return finish_info(g, info);
+}
+
+int como3r_solve(como3r_graph_t g, double* poses, int32_t iters, double* cost_trace, como3r_graph_info* info) {
+  if (g && iters < 0) return set_error(COMO3R_ERR_INVALID_ARG, "iters must be >= 0");
+  int rc = begin_call(g, poses);
+  if (rc) return rc;
+  const int64_t need = (int64_t)(iters + 1) * g->plan.G;
+  if (need > g->cost_hist_cap) {
+    // graphs hold the trace pointer: rebuild them around a larger buffer
+    cudaStreamSynchronize(g->stream);
+    if (g->iter_exec) cudaGraphExecDestroy(g->iter_exec);
+    if (g->eval_exec) cudaGraphExecDestroy(g->eval_exec);
+    g->iter_exec = g->eval_exec = nullptr;
+    const int64_t cap = std::max<int64_t>(need, 64 * (int64_t)g->plan.G);
+    if ((rc = dalloc(g, &g->d_cost_hist, (size_t)cap))) return rc;
+    g->cost_hist_cap = cap;
+  }
+  if (!g->iter_exec && (rc = capture(g, true, &g->iter_exec))) return rc;
+  if (!g->eval_exec && (rc = capture(g, false, &g->eval_exec))) return rc;
+  CK(cudaMemsetAsync(g->d_iter, 0, sizeof(int), g->stream), "memset");
+  for (int k = 0; k < iters; ++k) CK(cudaGraphLaunch(g->iter_exec, g->stream), "graph launch");
+  CK(cudaGraphLaunch(g->eval_exec, g->stream), "graph launch");
+  g->last_launches = 6 * (int64_t)iters + 4;
+  if (cost_trace)
+    CK(cudaMemcpyAsync(cost_trace, g->d_cost_hist, sizeof(double) * need, cudaMemcpyDeviceToHost, g->stream),
+       "trace");
+  if ((rc = end_call(g, poses))) return rc;
+  return finish_info(g, info);
+}
+
+int como3r_linearize(como3r_graph_t g, const double* poses, double* edge_out, double* cost_out) {
+  int rc = begin_call(g, poses);
+  if (rc) return rc;
+  if ((rc = enqueue_linearize(g, g->stream, nullptr, nullptr, edge_out))) return rc;
+  g->last_launches = 4;
+  if ((rc = end_call(g, nullptr))) return rc;
+  if (cost_out)
+    for (int k = 0; k < g->plan.G; ++k) cost_out[k] = g->h_ginfo[k].cost;
+  return *g->h_warn & COMO3R_WARN_SKIPPED;
+}
+
+int como3r_sim3_retract(const double* tau, double* poses, int32_t n, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!tau || !poses))) return set_error(COMO3R_ERR_INVALID_ARG, "bad retract arguments");
+  CK(launch_retract(tau, poses, nullptr, n, nullptr, static_cast<cudaStream_t>(cuda_stream)), "retract");
+  return COMO3R_OK;
+}
+
+int como3r_update_inputs(como3r_graph_t g, const void* points_conf, const int32_t* match_idx) {
+  if (!g) return set_error(COMO3R_ERR_INVALID_ARG, "graph handle is NULL");
+  if (!g->own_points) return set_error(COMO3R_ERR_INVALID_ARG, "graph was created with copy_inputs = 0");
+  if (points_conf)
+    CK(cudaMemcpyAsync(g->own_points, points_conf, g->points_bytes, cudaMemcpyDefault, g->stream), "copy points");
+  if (match_idx && g->idx_bytes)
+    CK(cudaMemcpyAsync(g->own_midx, match_idx, g->idx_bytes, cudaMemcpyDefault, g->stream), "copy matches");
+  return COMO3R_OK;
+}
+
+int64_t como3r_last_launch_count(como3r_graph_t g) { return g ? g->last_launches : 0; }
+
+int como3r_graph_stats(como3r_graph_t g, int64_t* stats) {
+  if (!g || !stats) return set_error(COMO3R_ERR_INVALID_ARG, "NULL argument");
+  plan_stats(g->plan, stats);
+  stats[COMO3R_STAT_ITEMS] = g->num_items;
+  int64_t v = 0;
+  for (long long x : g->edge_valid) v += x;
+  stats[COMO3R_STAT_VALID] = v;
+  stats[COMO3R_STAT_CHUNK] = g->k1_chunk;
+  stats[COMO3R_STAT_BLOCK] = g->k1_block;
+  stats[COMO3R_STAT_GRID] = g->k1_grid;
+  stats[COMO3R_STAT_SMEM_SOLVE] = g->smem_solve ? 1 : 0;
+  return COMO3R_OK;
+}
+
+int como3r_plan_stats(const como3r_graph_desc* desc, int64_t* stats) {
+  if (!stats) return set_error(COMO3R_ERR_INVALID_ARG, "stats is NULL");
+  HostPlan p;
+  const int rc = build_plan(desc, p);
+  if (rc) return set_error(rc, p.error);
+  plan_stats(p, stats);
+  std::vector<Item> items;
+  std::vector<int32_t> item_off;
+  build_items(p, kDefaultChunk, items, item_off);
+  stats[COMO3R_STAT_ITEMS] = (int64_t)items.size();
+  stats[COMO3R_STAT_CHUNK] = kDefaultChunk;
+  return COMO3R_OK;
+}
+
+const char* como3r_status_str(int code) {
+  switch (code) {
+    case COMO3R_OK: return "ok";
+    case COMO3R_WARN_SOLVE_FAILED: return "warning: every factorisation attempt failed in >= 1 graph (zero update)";
+    case COMO3R_WARN_SKIPPED: return "warning: degenerate or non-finite matches were skipped";
+    case COMO3R_WARN_SOLVE_FAILED | COMO3R_WARN_SKIPPED: return "warning: solve failed and matches skipped";
+    case COMO3R_ERR_INVALID_ARG: return "error: invalid argument";
+    case COMO3R_ERR_CUDA: return "error: CUDA runtime error";
+    case COMO3R_ERR_OOM: return "error: out of device memory";
+    case COMO3R_ERR_UNSUPPORTED: return "error: unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* como3r_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

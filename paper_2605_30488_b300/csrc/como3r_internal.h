@@ -81,6 +81,7 @@ cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t
                                 double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
                                 cudaStream_t s);
 size_t factor_solve_max_smem();
+cudaError_t factor_solve_prepare(size_t smem_bytes);  // once, before any capture
 cudaError_t launch_retract(const double* tau, double* poses, const uint8_t* frozen, int N, int* iter_counter,
                            cudaStream_t s);
 cudaError_t launch_check_matches(const int32_t* midx, const EdgeStatic* es, int E, unsigned long long* bad,

@@ -1,0 +1,44 @@
+// Host-side planning of a batch of pose graphs: validation, fill-reducing ordering,
+// symbolic block factorisation, level schedule, assembly lists and K1 work items.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/como3r.h"
+#include "como3r_internal.h"
+
+namespace como3r {
+
+struct HostPlan {
+  int G = 0, N = 0, E = 0;
+  int mode = 1, dtype = 1;
+  int64_t total_px = 0, total_idx = 0, valid_hint = 0;
+  std::vector<int32_t> kf_offset, edge_offset, anchor;
+  std::vector<int64_t> pix_off;   // [N+1]
+  std::vector<int32_t> npix;      // [N]
+  std::vector<EdgeStatic> es;     // [E]
+  std::vector<uint8_t> frozen;    // [N] anchors
+  // solver plan (see SolverPlan)
+  std::vector<int32_t> col_begin, col_kf, col_slot, slot_row, tri_off, rs_off, sched, lvl_begin, lvl_off;
+  std::vector<int4> tri;
+  std::vector<int2> rs;
+  std::vector<int32_t> slot_kf_r, slot_kf_c;
+  // assembly (entries edge * 2 + negate, in edge order)
+  std::vector<int32_t> slot_contrib_off, slot_contrib, kf_contrib_off, kf_contrib;
+  int max_levels = 0;
+  int64_t fill_blocks = 0;
+  size_t max_graph_smem = 0;      // bytes of the largest graph's factor + vectors
+  std::string error;
+};
+
+// Validates `d` and fills `p`; returns COMO3R_OK or COMO3R_ERR_INVALID_ARG (message in p.error).
+int build_plan(const como3r_graph_desc* d, HostPlan& p);
+
+// Splits every edge's streamed pixels into items of at most `chunk` pixels.
+void build_items(const HostPlan& p, int chunk, std::vector<Item>& items, std::vector<int32_t>& item_off);
+
+// Fills the COMO3R_STAT_* entries that depend on the plan only.
+void plan_stats(const HostPlan& p, int64_t* stats);
+
+}  // namespace como3r

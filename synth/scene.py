@@ -7,8 +7,9 @@ Recipe (all draws from one ``numpy.random.Generator(PCG64(seed))``):
   sides in [1, 5] m, all inside the cube [-10, 10]^3; hit points outside the cube are
   discarded, so a ray that leaves the cube without a hit yields no point.
 * Agents: each walks ``n_kf`` keyframes in the central cube [-5, 5]^3 at constant height,
-  0.5 m per step with a yaw change uniform in +-10 deg, keeping >= 0.5 m clearance from
-  every surface.  Agent a > 0 starts within 1.5 m of a keyframe of an earlier agent with a
+  0.5 m per step with a yaw change uniform in +-10 deg (+-25 deg when no such step is
+  admissible), keeping >= 0.5 m clearance from every surface; when less than 4 m of
+  free path lies ahead it turns (<= 25 deg per step) towards the most open heading.  Agent a > 0 starts within 1.5 m of a keyframe of an earlier agent with a
   heading within +-45 deg of it, so that the agents' views overlap somewhere.
 * Pinhole camera (x right, y down, z forward), principal point at the image centre,
   pixel (u, v) looks along ((u + 0.5 - W/2)/f, (v + 0.5 - H/2)/f, 1).
@@ -155,17 +156,39 @@ def pixel_rays(H: int, W: int, f: float) -> np.ndarray:
 # ----------------------------------------------------------------------------- walks
 def walk(geom: Geometry, rng: np.random.Generator, n_kf: int, start: np.ndarray, yaw: float,
          step: float = 0.5, yaw_step_deg: float = 10.0) -> List[Tuple[np.ndarray, float]]:
+    """Random walk with bounded turns that steers towards open space before it is cornered."""
+    def ok(r: np.ndarray) -> bool:
+        return bool(np.all(np.abs(r) <= CENTRAL) and clearance(geom, r) >= CLEARANCE)
+
+    def free_ahead(q: np.ndarray, y: float, limit: float = 8.0) -> float:
+        d = np.array([math.cos(y), math.sin(y), 0.0])
+        s = 0.0
+        while s < limit and ok(q + (s + step) * d):
+            s += step
+        return s
+
+    def wrap(a: float) -> float:
+        return (a + math.pi) % (2 * math.pi) - math.pi
+
     out = [(start.copy(), yaw)]
     p = start.copy()
+    max_turn = math.radians(2.5 * yaw_step_deg)
     for _ in range(n_kf - 1):
-        for attempt in range(400):
-            span = yaw_step_deg if attempt < 40 else 180.0
-            y = yaw + math.radians(rng.uniform(-span, span))
+        if free_ahead(p, yaw) >= 4.0:
+            base = [yaw + math.radians(rng.uniform(-yaw_step_deg, yaw_step_deg)) for _ in range(12)]
+        else:  # turn towards the most open heading, at most 25 deg per step
+            heads = np.linspace(-math.pi, math.pi, 36, endpoint=False)
+            target = heads[int(np.argmax([free_ahead(p, h) for h in heads]))]
+            turn = max(-max_turn, min(max_turn, wrap(target - yaw)))
+            base = [yaw + turn + math.radians(rng.uniform(-2, 2)) for _ in range(4)]
+            base += [yaw + rng.uniform(-max_turn, max_turn) for _ in range(12)]
+        moved = False
+        for y in base:
             q = p + step * np.array([math.cos(y), math.sin(y), 0.0])
-            if np.all(np.abs(q) <= CENTRAL) and clearance(geom, q) >= CLEARANCE:
-                p, yaw = q, y
+            if ok(q):
+                p, yaw, moved = q, y, True
                 break
-        else:
+        if not moved:
             raise RuntimeError("walk: no admissible step")
         out.append((p.copy(), yaw))
     return out
