@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the unified multi-agent Sim(3) Gauss-Newton refinement on one B300.
+
+Workload: 2 agents x 40 keyframes, 512x384 FP32 pointmaps (196,608 px each), 120 edges
+(78 sequential, 34 (k, k+2), 8 inter-agent), 1 % depth noise, lognormal confidences,
+15 % outlier correspondences, 15 GN iterations (synthetic, seeded; see synth/).
+
+A step is one como3r_solve: 15 full GN iterations (edge prep, residual / Jacobian /
+reduction, per-edge reduction, assembly, damped block Cholesky solve with eps
+escalation, retraction) from the perturbed initial poses.  `value` is GN iterations/s of
+the mixed form with inputs resident in HBM; the plain FP64 form is timed beside it.
+`e2e` repeats the mixed measurement through the C ABI with host (pinned) buffers: every
+step uploads the pointmaps and matches and reads the poses back.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica of the workload (the graphs of a
+batch are independent; there is no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "two_agent_40kf_512x384"
+METRIC = "Sim(3) GN iters/s & Mresiduals/s, mixed vs FP64 form, % of HBM peak"
+UNIT = "GN iters/s"
+FALLBACK_HBM_GBS = 6400.0
+PROFILE = os.path.join(ROOT, "profiles", "residual_reduce_two_agent_40kf_512x384.txt")
+K1_SOURCE = os.path.join(ROOT, "paper_2605_30488_b300", "csrc", "k_residual.cu")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-sample-edges", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def algorithmic_bytes(prob) -> int:
+    """Bytes K1 must move per launch: all match indices of every edge (4 B per streamed
+    pixel) plus, per valid match, the streamed and the gathered packed pixel."""
+    pix = prob.pixels_of()
+    b_px = prob.storage_bytes_per_pixel()
+    return int(4 * pix[prob.edge_i].sum() + 2 * b_px * prob.valid_matches())
+
+
+def k1_traffic_from_profile():
+    """DRAM bytes per K1 launch from the committed ncu summary, if it was taken on the
+    current K1 source (sha256 recorded in the summary); else None."""
+    try:
+        txt = open(PROFILE).read()
+        src = hashlib.sha256(open(K1_SOURCE, "rb").read()).hexdigest()
+        fields = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l)
+        if fields.get("source_sha256", "").strip() != src:
+            return None
+        return float(fields["traffic_bytes_per_launch"].strip())
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples (200 ms) with host timestamps."""
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        inside = [s for t, s in self.samples if t0 <= t <= t1]
+        if not inside:  # very short timed region: nearest samples around it
+            near = sorted(self.samples, key=lambda ts: min(abs(ts[0] - t0), abs(ts[0] - t1)))[:3]
+            inside = [s for _, s in near]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(s[0]) for s in inside if s[0].replace(".", "").isdigit()]
+        smax = [float(s[1]) for s in inside if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for s in inside for n, v in zip(names, s[4:8]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(inside)}
+
+
+def oracle_sample(prob, n_edges: int):
+    """Time the FP64 oracle on a bounded sample of one iteration and extrapolate.
+
+    Sample: `n_edges` edges (evenly spread) linearised with dense per-match Jacobians,
+    plus the dense damped Cholesky solve and retraction of a system of the full size 7N.
+    One iteration = sampled edge time x E / n_edges + solve + retraction.
+    """
+    import threadpoolctl
+    from oracle import como3r_oracle as O
+    arrs = O.problem_arrays(prob)
+    T = [O.pose_to_matrix(p) for p in prob.poses_init]
+    sel = np.unique(np.linspace(0, prob.num_edges - 1, n_edges).astype(int))
+    t0 = time.perf_counter()
+    for e in sel:
+        i, j, m, n, Pi, Pj = O.edge_matches(prob, arrs, int(e))
+        O.linearize_edge(T[i], T[j], Pi, Pj, prob.params())
+    t_edges = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    n7 = 7 * prob.num_kf
+    B = rng.normal(size=(n7, n7))
+    Hs = B @ B.T / n7 + np.eye(n7)
+    gs = rng.normal(size=n7)
+    t1 = time.perf_counter()
+    tau, _, _ = O.damped_solve(Hs, gs, int(prob.anchor[0]), prob.lam, prob.eps0, prob.max_attempts)
+    O.retract(prob.poses_init, 1e-3 * tau)
+    t_solve = time.perf_counter() - t1
+    t_iter = t_edges * prob.num_edges / len(sel) + t_solve
+    threads = max([p.get("num_threads", 1) for p in threadpoolctl.threadpool_info()] + [1])
+    return {"value": 1.0 / t_iter, "unit": UNIT, "cores": int(threads), "kind": "oracle",
+            "sample": (f"{len(sel)} of {prob.num_edges} edges linearised + full {n7}x{n7} dense solve and "
+                       f"retraction ({t_edges + t_solve:.1f} s CPU), extrapolated to one GN iteration"),
+            "seconds_per_iteration": t_iter}
+
+
+# ----------------------------------------------------------------------------- arms
+def run_reference(args):
+    rank, local_rank, world = rank_info()
+    if rank != 0:
+        return
+    from synth import make_workload
+    prob = make_workload(args.workload, seed=args.seed)
+    n_edges = max(2, min(8, args.cpu_sample_edges))
+    for _ in range(args.warmup):
+        oracle_sample(prob, n_edges)
+    t0 = time.perf_counter()
+    its = []
+    for _ in range(args.steps):
+        its.append(oracle_sample(prob, n_edges)["seconds_per_iteration"])
+    wall = time.perf_counter() - t0
+    value = 1.0 / float(np.mean(its))
+    cb = oracle_sample(prob, n_edges)
+    cb["value"] = value
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "iters": prob.iters, "keyframes": prob.num_kf,
+                      "edges": prob.num_edges, "valid_matches": prob.valid_matches(), "seed": args.seed},
+           "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                       "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, local_rank, world = rank_info()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local_rank))
+    from paper_2605_30488_b300 import build as b
+    if rank == 0 or world == 1:
+        b.build()
+    if dist:
+        dist.barrier()
+    from paper_2605_30488_b300 import como3r as C
+    from synth import make_workload
+
+    prob = make_workload(args.workload, seed=args.seed)
+    iters = prob.iters
+    dev = torch.device("cuda", local_rank)
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = str(getattr(props, "uuid", local_rank))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) == 36:
+        gpu_id = "GPU-" + gpu_id
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    poses0 = torch.tensor(prob.poses_init, dtype=torch.float64, device=dev)
+    work = torch.empty_like(poses0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # ---- mixed form, inputs resident in HBM (headline)
+    g = C.Graph(prob, mode=C.MIXED)
+    for _ in range(args.warmup):
+        work.copy_(poses0)
+        g.solve(work, iters, trace=False)
+    barrier()
+    launches = 0
+    tw0 = time.time()
+    ev0.record()
+    for _ in range(args.steps):
+        work.copy_(poses0)
+        st, _, info = g.solve(work, iters, trace=False)
+        launches += g.last_launch_count()
+    ev1.record()
+    barrier()
+    tw1 = time.time()
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    final_cost = info[0]["cost"]
+    stages = g.time_stages(poses0, reps=20)
+    stats = g.stats()
+    g.close()
+    value = world * args.steps * iters / (ms / 1e3)
+    valid = prob.valid_matches()
+
+    # ---- plain FP64 form (same storage, same bytes)
+    gp = C.Graph(prob, mode=C.PLAIN_FP64)
+    work.copy_(poses0)
+    gp.solve(work, iters, trace=False)
+    barrier()
+    psteps = max(2, min(args.steps, 5))
+    ev0.record()
+    for _ in range(psteps):
+        work.copy_(poses0)
+        gp.solve(work, iters, trace=False)
+    ev1.record()
+    barrier()
+    pms = max_over_ranks(ev0.elapsed_time(ev1))
+    pstages = gp.time_stages(poses0, reps=3)
+    gp.close()
+    plain_value = world * psteps * iters / (pms / 1e3)
+
+    # ---- e2e: C ABI with pinned host buffers, uploads and readback inside the timed region
+    pts_h = torch.from_numpy(np.ascontiguousarray(prob.points)).pin_memory()
+    idx_h = torch.from_numpy(np.ascontiguousarray(prob.match_idx)).pin_memory()
+    poses_h = torch.tensor(prob.poses_init, dtype=torch.float64).pin_memory()
+    ge = C.Graph(prob, mode=C.MIXED, points=pts_h, match_idx=idx_h, copy_inputs=True)
+    esteps = max(3, min(args.steps, 50))
+    for _ in range(max(1, min(args.warmup, 3))):
+        poses_h.copy_(torch.from_numpy(prob.poses_init))
+        ge.update_inputs(pts_h, idx_h)
+        ge.solve(poses_h, iters, trace=False)
+    barrier()
+    ev0.record()
+    for _ in range(esteps):
+        poses_h.copy_(torch.from_numpy(prob.poses_init))
+        ge.update_inputs(pts_h, idx_h)
+        ge.solve(poses_h, iters, trace=True)
+    ev1.record()
+    barrier()
+    ems = max_over_ranks(ev0.elapsed_time(ev1))
+    ge.close()
+    e2e_value = world * esteps * iters / (ems / 1e3)
+    h2d = pts_h.numel() * pts_h.element_size() + idx_h.numel() * idx_h.element_size() + poses_h.numel() * 8
+    d2h = poses_h.numel() * 8 + (iters + 1) * prob.num_graphs * 8
+
+    clocks.stop()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_src = measured_hbm_peak()
+    bytes_alg = algorithmic_bytes(prob)
+    k1_ms = stages["residual_reduce"]
+    achieved = bytes_alg / (k1_ms / 1e3) / 1e9
+    traffic = k1_traffic_from_profile()
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = oracle_sample(prob, args.cpu_sample_edges)
+        cpu.pop("seconds_per_iteration", None)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "agents": 2, "keyframes": prob.num_kf, "edges": prob.num_edges,
+                   "pointmap": "512x384 FP32", "iters_per_step": iters, "valid_matches_per_iter": valid,
+                   "seed": args.seed, "l2": "inputs larger than L2 (points+matches %.0f MB > 126 MB)"
+                   % ((prob.points.nbytes + prob.match_idx.nbytes) / 1e6),
+                   "parallelism": f"replicas x{world}"},
+        "mresiduals_per_s": value * valid / 1e6,
+        "plain_fp64": {"value": plain_value, "unit": UNIT, "ms_per_step": pms / psteps,
+                       "mresiduals_per_s": plain_value * valid / 1e6,
+                       "k1_ms": pstages["residual_reduce"], "stages_ms": pstages},
+        "mixed_over_plain": value / plain_value,
+        "stages_ms": stages,
+        "final_cost": final_cost,
+        "roofline": {"kernel": "residual_reduce (K1, mixed)", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_source": f"{peak_src} hbm_gbs (copy)", "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": bytes_alg,
+                     "k1_ms_per_launch": k1_ms},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "steps": esteps},
+        "gpu_launches": int(launches),
+        "clocks": clocks.summary(tw0, tw1),
+        "plan": {k: stats[k] for k in ("items", "chunk", "block", "grid", "blocks", "updates", "levels",
+                                       "smem_solve")},
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

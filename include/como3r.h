@@ -158,6 +158,14 @@ int como3r_sim3_retract(const double* tau, double* poses, int32_t n, void* cuda_
  * (pinned host memory makes the copy asynchronous). */
 int como3r_update_inputs(como3r_graph_t graph, const void* points_conf, const int32_t* match_idx);
 
+/* Per-stage timing of `reps` full iterations from `poses` (host or device; not modified):
+ * the six kernels of an iteration are launched individually on the graph's stream with
+ * CUDA events recorded between them, and ms[k] receives the mean duration of stage k:
+ * 0 edge prep, 1 residual/Jacobian/reduction (K1), 2 per-edge reduction, 3 assembly,
+ * 4 factorisation + solve, 5 retraction; ms[6] = mean time of a whole iteration. */
+#define COMO3R_STAGES 7
+int como3r_time_stages(como3r_graph_t graph, const double* poses, int32_t reps, float* ms /* [COMO3R_STAGES] */);
+
 /* Number of kernels the last gn_step / solve / linearize call enqueued (for accounting). */
 int64_t como3r_last_launch_count(como3r_graph_t graph);
 

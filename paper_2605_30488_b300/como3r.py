@@ -28,6 +28,8 @@ EDGE_RECORD = 64
 STAT_NAMES = ["graphs", "keyframes", "edges", "items", "columns", "blocks", "fill", "updates", "levels",
               "valid", "chunk", "block", "grid", "smem_solve", "r14", "r15"]
 
+STAGE_NAMES = ["edge_prep", "residual_reduce", "edge_reduce", "assemble", "factor_solve", "retract", "iteration"]
+
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _f64p = ctypes.POINTER(ctypes.c_double)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -64,6 +66,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.como3r_linearize.argtypes = [vp, vp, vp, _f64p]
     lib.como3r_sim3_retract.argtypes = [vp, vp, ctypes.c_int32, vp]
     lib.como3r_update_inputs.argtypes = [vp, vp, vp]
+    lib.como3r_time_stages.argtypes = [vp, vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
     lib.como3r_last_launch_count.argtypes = [vp]
     lib.como3r_last_launch_count.restype = ctypes.c_int64
     lib.como3r_graph_stats.argtypes = [vp, _i64p]
@@ -219,6 +222,12 @@ class Graph:
 
     def update_inputs(self, points=None, match_idx=None):
         _check(lib().como3r_update_inputs(self.handle, _ptr(points), _ptr(match_idx)), "update_inputs")
+
+    def time_stages(self, poses, reps: int = 10) -> dict:
+        """Mean per-kernel durations (ms) from CUDA events on the library's stream."""
+        ms = (ctypes.c_float * 7)()
+        _check(lib().como3r_time_stages(self.handle, _ptr(poses), int(reps), ms), "time_stages")
+        return dict(zip(STAGE_NAMES, [float(x) for x in ms]))
 
     def last_launch_count(self) -> int:
         return int(lib().como3r_last_launch_count(self.handle))

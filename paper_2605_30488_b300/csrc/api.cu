@@ -402,6 +402,58 @@ int como3r_update_inputs(como3r_graph_t g, const void* points_conf, const int32_
   return COMO3R_OK;
 }
 
+int como3r_time_stages(como3r_graph_t g, const double* poses, int32_t reps, float* ms) {
+  if (!g || !ms || reps < 1) return set_error(COMO3R_ERR_INVALID_ARG, "bad time_stages arguments");
+  int rc = begin_call(g, poses);
+  if (rc) return rc;
+  const HostPlan& p = g->plan;
+  cudaEvent_t ev[7];
+  for (auto& e : ev) CK(cudaEventCreate(&e), "event create");
+  double acc[COMO3R_STAGES] = {0};
+  cudaStream_t s = g->stream;
+  const int nslots = p.col_slot.back();
+  for (int r = 0; r < reps && !rc; ++r) {
+    cudaError_t err = cudaEventRecord(ev[0], s);
+    if (!err) err = launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, s);
+    if (!err) err = cudaEventRecord(ev[1], s);
+    if (!err) err = launch_residual_reduce(p.mode, p.dtype, g->k1_block, g->k1_grid, g->points, g->midx, g->d_items,
+                                           g->num_items, g->d_es, g->d_T64, g->d_T32, g->rp, g->d_partials, s);
+    if (!err) err = cudaEventRecord(ev[2], s);
+    if (!err) err = launch_edge_reduce(g->d_partials, g->d_item_off, p.E, g->d_Ad, g->d_edge_M, g->d_edge_b,
+                                       g->d_edge_cost, g->d_edge_skip, nullptr, g->d_edge_valid, s);
+    if (!err) err = cudaEventRecord(ev[3], s);
+    if (!err) err = launch_assemble(nslots, g->d_slot_contrib_off, g->d_slot_contrib, g->d_edge_M, g->d_A, p.N,
+                                    g->d_kf_contrib_off, g->d_kf_contrib, g->d_edge_b, g->d_gvec, p.G,
+                                    g->d_edge_offset, g->d_edge_cost, g->d_edge_skip, g->d_ginfo, nullptr, nullptr,
+                                    g->d_warn, s);
+    if (!err) err = cudaEventRecord(ev[4], s);
+    if (!err) err = launch_factor_solve(p.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_Dinv,
+                                        g->d_gvec, g->d_y, g->d_tau, g->lambda, g->eps0, g->max_attempts, g->d_ginfo,
+                                        g->d_warn, s);
+    if (!err) err = cudaEventRecord(ev[5], s);
+    if (!err) err = launch_retract(g->d_tau, g->d_poses, g->d_frozen, p.N, nullptr, s);
+    if (!err) err = cudaEventRecord(ev[6], s);
+    if (!err) err = cudaEventSynchronize(ev[6]);
+    if (err) {
+      rc = cuda_error(err, "time_stages");
+      break;
+    }
+    for (int k = 0; k < 6; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
+    float tot = 0.f;
+    cudaEventElapsedTime(&tot, ev[0], ev[6]);
+    acc[6] += tot;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  for (int k = 0; k < COMO3R_STAGES; ++k) ms[k] = (float)(acc[k] / reps);
+  g->last_launches = 6 * (int64_t)reps;
+  return COMO3R_OK;
+}
+
 int64_t como3r_last_launch_count(como3r_graph_t g) { return g ? g->last_launches : 0; }
 
 int como3r_graph_stats(como3r_graph_t g, int64_t* stats) {
