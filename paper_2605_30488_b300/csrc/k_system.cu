@@ -192,6 +192,9 @@ __global__ void retract_kernel(const double* __restrict__ tau, double* __restric
   if (k == 0 && iter_counter) *iter_counter += 1;
   if (k >= N) return;
   if (frozen && frozen[k]) return;
+  const double* t = tau + 7 * k;
+  // a zero update leaves the pose bitwise unchanged (no renormalisation)
+  if (t[0] == 0.0 && t[1] == 0.0 && t[2] == 0.0 && t[3] == 0.0 && t[4] == 0.0 && t[5] == 0.0 && t[6] == 0.0) return;
   double p[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) p[q] = poses[8 * k + q];

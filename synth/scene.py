@@ -34,7 +34,9 @@ Recipe (all draws from one ``numpy.random.Generator(PCG64(seed))``):
 from __future__ import annotations
 
 import dataclasses
+import hashlib
 import math
+import os
 from typing import Dict, List, Optional, Tuple
 
 import numpy as np
@@ -502,7 +504,31 @@ WORKLOADS: Dict[str, dict] = {
 }
 
 
+def _cache_path(name: str, seed: int, overrides: dict) -> Optional[str]:
+    root = os.environ.get("COMO3R_SYNTH_CACHE", "")
+    if not root:
+        return None
+    src = open(__file__, "rb").read()
+    key = hashlib.sha256(src + repr((name, seed, sorted(overrides.items()))).encode()).hexdigest()[:20]
+    return os.path.join(root, f"{name}-{seed}-{key}.npz")
+
+
 def make_workload(name: str, seed: int = 0, **overrides) -> Problem:
+    """A named workload; cached as .npz under $COMO3R_SYNTH_CACHE when that is set."""
+    path = _cache_path(name, seed, overrides)
+    if path and os.path.exists(path):
+        z = np.load(path)
+        fields = {f.name: z[f.name] for f in dataclasses.fields(Problem) if f.name in z.files}
+        scal = {k: v.item() for k, v in fields.items() if v.ndim == 0}
+        fields.update(scal)
+        fields["name"] = str(fields["name"])
+        return Problem(**fields)
     spec = dict(WORKLOADS[name])
     spec.update(overrides)
-    return make_problem(seed, name=name, **spec)
+    prob = make_problem(seed, name=name, **spec)
+    if path:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".{os.getpid()}.tmp.npz"
+        np.savez(tmp, **{f.name: getattr(prob, f.name) for f in dataclasses.fields(Problem)})
+        os.replace(tmp, path)
+    return prob
