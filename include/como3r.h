@@ -110,8 +110,10 @@ typedef struct {
 } como3r_graph_info;
 
 /* Validate the description, plan the solve (fill-reducing ordering, symbolic block
- * factorisation, work lists), allocate workspaces and check every match index on the
- * device (-1 <= n < P_j).  Synchronises the stream once.  On error *out is NULL.
+ * factorisation, work lists), allocate workspaces, check every match index on the
+ * device (-1 <= n < P_j) and autotune the residual kernel's work-item size and launch
+ * configuration on this graph's data (a few milliseconds of timed trial launches).
+ * Synchronises the stream.  On error *out is NULL.
  * Errors: INVALID_ARG (bad sizes / ids / indices / parameters), OOM, CUDA. */
 int como3r_graph_create(const como3r_graph_desc* desc, void* cuda_stream, como3r_graph_t* out);
 
@@ -181,9 +183,10 @@ int64_t como3r_last_launch_count(como3r_graph_t graph);
 #define COMO3R_STAT_LEVELS 8         /* max elimination-tree levels of one graph */
 #define COMO3R_STAT_VALID 9          /* valid matches (all edges) */
 #define COMO3R_STAT_CHUNK 10         /* K1 pixels per work item */
-#define COMO3R_STAT_BLOCK 11         /* K1 threads per CTA */
+#define COMO3R_STAT_BLOCK 11         /* K1 threads per CTA * 100 + chosen register/residency config */
 #define COMO3R_STAT_GRID 12          /* K1 CTAs */
 #define COMO3R_STAT_SMEM_SOLVE 13    /* 1 if the factor of every graph fits in shared memory */
+#define COMO3R_STAT_ND_GRAPHS 14     /* graphs ordered by nested dissection (others: minimum degree) */
 #define COMO3R_STAT_COUNT 16
 int como3r_graph_stats(como3r_graph_t graph, int64_t* stats /* [COMO3R_STAT_COUNT] */);
 

@@ -26,7 +26,7 @@ F16, F32, F64 = 0, 1, 2
 PLAIN_FP64, MIXED = 0, 1
 EDGE_RECORD = 64
 STAT_NAMES = ["graphs", "keyframes", "edges", "items", "columns", "blocks", "fill", "updates", "levels",
-              "valid", "chunk", "block", "grid", "smem_solve", "r14", "r15"]
+              "valid", "chunk", "block", "grid", "smem_solve", "nd_graphs", "r15"]
 
 STAGE_NAMES = ["edge_prep", "residual_reduce", "edge_reduce", "assemble", "factor_solve", "retract", "iteration"]
 

@@ -39,8 +39,8 @@ int cuda_error(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_error(e_, where); \
   } while (0)
 
-constexpr int kDefaultBlock = 256;
-constexpr int kDefaultChunk = 8192;
+constexpr int kDefaultChunk = 2048;
+constexpr int kChunks[] = {1024, 2048, 4096};  // K1 pixels per warp work item (autotuned)
 }  // namespace
 
 struct como3r_graph {
@@ -51,7 +51,8 @@ struct como3r_graph {
   RobustParams rp{};
   double lambda = 0.0, eps0 = 1e-6;
   int max_attempts = 6;
-  int k1_block = kDefaultBlock, k1_chunk = kDefaultChunk, k1_grid = 0, num_items = 0;
+  int k1_cfg = 0, k1_chunk = kDefaultChunk, k1_grid = 0, num_items = 0, max_items = 0;
+  float k1_tuned_ms = 0.f;
   std::vector<void*> allocs;
   const void* points = nullptr;
   const int32_t* midx = nullptr;
@@ -67,7 +68,7 @@ struct como3r_graph {
   long long* d_edge_valid = nullptr;
   int32_t *d_slot_kf_r = nullptr, *d_slot_kf_c = nullptr, *d_slot_contrib_off = nullptr, *d_slot_contrib = nullptr;
   int32_t *d_kf_contrib_off = nullptr, *d_kf_contrib = nullptr, *d_edge_offset = nullptr;
-  double *d_A = nullptr, *d_L = nullptr, *d_Dinv = nullptr, *d_y = nullptr, *d_gvec = nullptr, *d_tau = nullptr;
+  double *d_A = nullptr, *d_L = nullptr, *d_colscratch = nullptr, *d_gvec = nullptr, *d_tau = nullptr;
   uint8_t* d_frozen = nullptr;
   GraphInfoDev* d_ginfo = nullptr;
   int *d_iter = nullptr, *d_warn = nullptr;
@@ -128,10 +129,10 @@ bool is_device_pointer(const void* p) {
 int enqueue_linearize(como3r_graph* g, cudaStream_t s, double* cost_hist, const int* iter, double* edge_rec) {
   const HostPlan& p = g->plan;
   CK(launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, s), "edge_prep");
-  CK(launch_residual_reduce(p.mode, p.dtype, g->k1_block, g->k1_grid, g->points, g->midx, g->d_items, g->num_items,
+  CK(launch_residual_reduce(p.mode, p.dtype, g->k1_cfg, g->k1_grid, g->points, g->midx, g->d_items, g->num_items,
                             g->d_es, g->d_T64, g->d_T32, g->rp, g->d_partials, s),
      "residual_reduce");
-  CK(launch_edge_reduce(g->d_partials, g->d_item_off, p.E, g->d_Ad, g->d_edge_M, g->d_edge_b, g->d_edge_cost,
+  CK(launch_edge_reduce(p.mode, g->d_partials, g->d_item_off, p.E, g->d_Ad, g->d_edge_M, g->d_edge_b, g->d_edge_cost,
                         g->d_edge_skip, edge_rec, g->d_edge_valid, s),
      "edge_reduce");
   const int nslots = p.col_slot.back();
@@ -144,7 +145,7 @@ int enqueue_linearize(como3r_graph* g, cudaStream_t s, double* cost_hist, const 
 
 int enqueue_solve(como3r_graph* g, cudaStream_t s, int* iter) {
   const HostPlan& p = g->plan;
-  CK(launch_factor_solve(p.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_Dinv, g->d_gvec, g->d_y,
+  CK(launch_factor_solve(p.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_colscratch, g->d_gvec,
                          g->d_tau, g->lambda, g->eps0, g->max_attempts, g->d_ginfo, g->d_warn, s),
      "factor_solve");
   CK(launch_retract(g->d_tau, g->d_poses, g->d_frozen, p.N, iter, s), "retract");
@@ -184,6 +185,8 @@ int capture(como3r_graph* g, bool with_solve, cudaGraphExec_t* exec) {
   return COMO3R_OK;
 }
 
+int autotune_k1(como3r_graph* g);
+
 int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   HostPlan& p = g->plan;
   int rc = build_plan(d, p);
@@ -218,19 +221,17 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
     g->points = d->points_conf;
     g->midx = d->match_idx;
   }
-  // K1 launch shape
+  // K1 work items: allocated for the smallest candidate chunk, chosen by autotune_k1()
   std::vector<Item> items;
   std::vector<int32_t> item_off;
-  build_items(p, g->k1_chunk, items, item_off);
-  g->num_items = (int)items.size();
-  const int occ = residual_reduce_max_blocks_per_sm(p.mode, p.dtype, g->k1_block);
-  g->k1_grid = std::max(1, std::min(g->num_items, g->sms * std::max(occ, 1)));
+  build_items(p, kChunks[0], items, item_off);
+  g->max_items = (int)items.size();
   const int E = p.E, N = p.N, G = p.G;
   const int nslots = p.col_slot.back(), ncols = p.col_begin.back();
   if ((rc = upload(g, &g->d_es, p.es)) || (rc = upload(g, &g->d_items, items)) ||
       (rc = upload(g, &g->d_item_off, item_off)) || (rc = dalloc(g, &g->d_T64, (size_t)E * 12)) ||
       (rc = dalloc(g, &g->d_T32, (size_t)E * 16)) || (rc = dalloc(g, &g->d_Ad, (size_t)E * 49)) ||
-      (rc = dalloc(g, &g->d_partials, (size_t)g->num_items * kPartial)) ||
+      (rc = dalloc(g, &g->d_partials, (size_t)g->max_items * kPartial)) ||
       (rc = dalloc(g, &g->d_edge_M, (size_t)E * 49)) || (rc = dalloc(g, &g->d_edge_b, (size_t)E * 7)) ||
       (rc = dalloc(g, &g->d_edge_cost, E)) || (rc = dalloc(g, &g->d_edge_skip, E)) ||
       (rc = dalloc(g, &g->d_edge_valid, E)) || (rc = upload(g, &g->d_slot_kf_r, p.slot_kf_r)) ||
@@ -238,23 +239,24 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
       (rc = upload(g, &g->d_slot_contrib, p.slot_contrib)) ||
       (rc = upload(g, &g->d_kf_contrib_off, p.kf_contrib_off)) || (rc = upload(g, &g->d_kf_contrib, p.kf_contrib)) ||
       (rc = upload(g, &g->d_edge_offset, p.edge_offset)) || (rc = dalloc(g, &g->d_A, (size_t)nslots * 49)) ||
-      (rc = dalloc(g, &g->d_L, (size_t)nslots * 49)) || (rc = dalloc(g, &g->d_Dinv, (size_t)ncols * 7)) ||
-      (rc = dalloc(g, &g->d_y, (size_t)ncols * 7)) || (rc = dalloc(g, &g->d_gvec, (size_t)N * 7)) ||
+      (rc = dalloc(g, &g->d_L, (size_t)nslots * 49)) ||
+      (rc = dalloc(g, &g->d_colscratch, (size_t)ncols * kColScratch)) || (rc = dalloc(g, &g->d_gvec, (size_t)N * 7)) ||
       (rc = dalloc(g, &g->d_tau, (size_t)N * 7)) || (rc = upload(g, &g->d_frozen, p.frozen)) ||
       (rc = dalloc(g, &g->d_ginfo, G)) || (rc = dalloc(g, &g->d_iter, 1)) || (rc = dalloc(g, &g->d_warn, 1)) ||
       (rc = dalloc(g, &g->d_poses, (size_t)N * 8)) || (rc = dalloc(g, &g->d_bad, 1)))
     return rc;
   // solver plan
-  int32_t *col_begin, *col_kf, *col_slot, *slot_row, *tri_off, *rs_off, *sched, *lvl_begin, *lvl_off;
-  int4* tri;
-  int2* rs;
+  int32_t *col_begin, *col_kf, *col_slot, *slot_row, *utask_off, *sched, *lvl_off, *ttask_off, *lvl_begin;
+  int4 *tri, *utask;
+  int2* ttask;
   if ((rc = upload(g, &col_begin, p.col_begin)) || (rc = upload(g, &col_kf, p.col_kf)) ||
       (rc = upload(g, &col_slot, p.col_slot)) || (rc = upload(g, &slot_row, p.slot_row)) ||
-      (rc = upload(g, &tri_off, p.tri_off)) || (rc = upload(g, &tri, p.tri)) || (rc = upload(g, &rs_off, p.rs_off)) ||
-      (rc = upload(g, &rs, p.rs)) || (rc = upload(g, &sched, p.sched)) || (rc = upload(g, &lvl_begin, p.lvl_begin)) ||
-      (rc = upload(g, &lvl_off, p.lvl_off)))
+      (rc = upload(g, &tri, p.tri)) || (rc = upload(g, &utask, p.utask)) || (rc = upload(g, &utask_off, p.utask_off)) ||
+      (rc = upload(g, &sched, p.sched)) || (rc = upload(g, &lvl_off, p.lvl_off)) || (rc = upload(g, &ttask, p.ttask)) ||
+      (rc = upload(g, &ttask_off, p.ttask_off)) || (rc = upload(g, &lvl_begin, p.lvl_begin)))
     return rc;
-  g->sp = SolverPlan{col_begin, col_kf, col_slot, slot_row, tri_off, tri, rs_off, rs, sched, lvl_begin, lvl_off};
+  g->sp = SolverPlan{col_begin, col_kf, col_slot, slot_row, tri, utask, utask_off, sched, lvl_off, ttask, ttask_off,
+                     lvl_begin};
   CK(cudaMallocHost(&g->h_ginfo, sizeof(GraphInfoDev) * G), "cudaMallocHost");
   CK(cudaMallocHost(&g->h_warn, sizeof(int)), "cudaMallocHost");
   CK(cudaMemsetAsync(g->d_tau, 0, sizeof(double) * 7 * (size_t)N, g->stream), "memset");
@@ -276,6 +278,77 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   if (E) CK(cudaMemcpyAsync(g->edge_valid.data(), g->d_edge_valid, sizeof(long long) * E, cudaMemcpyDeviceToHost, g->stream), "readback");
   CK(cudaStreamSynchronize(g->stream), "create sync");
   if (bad) return set_error(COMO3R_ERR_INVALID_ARG, std::to_string(bad) + " match indices outside [-1, P_j)");
+  return autotune_k1(g);
+}
+
+// Chooses K1's (chunk, CTA residency) by timing every candidate on this graph's data
+// with CUDA events (identity poses: the arithmetic per match does not depend on them).
+int autotune_k1(como3r_graph* g) {
+  const HostPlan& p = g->plan;
+  std::vector<double> ident((size_t)p.N * 8, 0.0);
+  for (int k = 0; k < p.N; ++k) ident[8 * k + 6] = ident[8 * k + 7] = 1.0;
+  CK(cudaMemcpyAsync(g->d_poses, ident.data(), sizeof(double) * ident.size(), cudaMemcpyHostToDevice, g->stream),
+     "tune poses");
+  CK(launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, g->stream), "tune edge_prep");
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "event");
+  CK(cudaEventCreate(&e1), "event");
+  float best = 1e30f;
+  int best_chunk = kChunks[0], best_cfg = 0;
+  const int nchunks = p.mode == COMO3R_MIXED ? (int)(sizeof(kChunks) / sizeof(kChunks[0])) : 1;
+  std::vector<Item> items;
+  std::vector<int32_t> item_off;
+  int rc = COMO3R_OK;
+  for (int ci = 0; ci < nchunks && !rc; ++ci) {
+    const int chunk = p.mode == COMO3R_MIXED ? kChunks[ci] : kDefaultChunk;
+    build_items(p, chunk, items, item_off);
+    CK(cudaMemcpyAsync(g->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, g->stream),
+       "tune items");
+    for (int cfg = 0; cfg < residual_reduce_num_cfgs(p.mode); ++cfg) {
+      const int occ = residual_reduce_max_blocks_per_sm(p.mode, p.dtype, cfg);
+      const int warps_per_cta = residual_reduce_block() / 32;
+      const int grid = std::max(1, std::min(g->sms * std::max(occ, 1), ((int)items.size() + warps_per_cta - 1) / warps_per_cta));
+      float tot = 0.f;
+      for (int r = 0; r < 4; ++r) {
+        cudaError_t err = cudaEventRecord(e0, g->stream);
+        if (!err) err = launch_residual_reduce(p.mode, p.dtype, cfg, grid, g->points, g->midx, g->d_items,
+                                               (int)items.size(), g->d_es, g->d_T64, g->d_T32, g->rp, g->d_partials,
+                                               g->stream);
+        if (!err) err = cudaEventRecord(e1, g->stream);
+        if (!err) err = cudaEventSynchronize(e1);
+        if (err) {
+          rc = cuda_error(err, "autotune");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (r > 0) tot += ms;  // first run warms caches and clocks
+      }
+      if (rc) break;
+      if (tot / 3 < best) {
+        best = tot / 3;
+        best_chunk = chunk;
+        best_cfg = cfg;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  build_items(p, best_chunk, items, item_off);
+  CK(cudaMemcpyAsync(g->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, g->stream),
+     "items");
+  CK(cudaMemcpyAsync(g->d_item_off, item_off.data(), sizeof(int32_t) * item_off.size(), cudaMemcpyHostToDevice,
+                     g->stream),
+     "items");
+  g->num_items = (int)items.size();
+  g->k1_chunk = best_chunk;
+  g->k1_cfg = best_cfg;
+  g->k1_tuned_ms = best;
+  const int occ = residual_reduce_max_blocks_per_sm(p.mode, p.dtype, best_cfg);
+  const int warps_per_cta = residual_reduce_block() / 32;
+  g->k1_grid = std::max(1, std::min(g->sms * std::max(occ, 1), (g->num_items + warps_per_cta - 1) / warps_per_cta));
+  CK(cudaStreamSynchronize(g->stream), "tune sync");
   return COMO3R_OK;
 }
 
@@ -416,10 +489,10 @@ int como3r_time_stages(como3r_graph_t g, const double* poses, int32_t reps, floa
     cudaError_t err = cudaEventRecord(ev[0], s);
     if (!err) err = launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, s);
     if (!err) err = cudaEventRecord(ev[1], s);
-    if (!err) err = launch_residual_reduce(p.mode, p.dtype, g->k1_block, g->k1_grid, g->points, g->midx, g->d_items,
+    if (!err) err = launch_residual_reduce(p.mode, p.dtype, g->k1_cfg, g->k1_grid, g->points, g->midx, g->d_items,
                                            g->num_items, g->d_es, g->d_T64, g->d_T32, g->rp, g->d_partials, s);
     if (!err) err = cudaEventRecord(ev[2], s);
-    if (!err) err = launch_edge_reduce(g->d_partials, g->d_item_off, p.E, g->d_Ad, g->d_edge_M, g->d_edge_b,
+    if (!err) err = launch_edge_reduce(p.mode, g->d_partials, g->d_item_off, p.E, g->d_Ad, g->d_edge_M, g->d_edge_b,
                                        g->d_edge_cost, g->d_edge_skip, nullptr, g->d_edge_valid, s);
     if (!err) err = cudaEventRecord(ev[3], s);
     if (!err) err = launch_assemble(nslots, g->d_slot_contrib_off, g->d_slot_contrib, g->d_edge_M, g->d_A, p.N,
@@ -427,8 +500,8 @@ int como3r_time_stages(como3r_graph_t g, const double* poses, int32_t reps, floa
                                     g->d_edge_offset, g->d_edge_cost, g->d_edge_skip, g->d_ginfo, nullptr, nullptr,
                                     g->d_warn, s);
     if (!err) err = cudaEventRecord(ev[4], s);
-    if (!err) err = launch_factor_solve(p.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_Dinv,
-                                        g->d_gvec, g->d_y, g->d_tau, g->lambda, g->eps0, g->max_attempts, g->d_ginfo,
+    if (!err) err = launch_factor_solve(p.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_colscratch,
+                                        g->d_gvec, g->d_tau, g->lambda, g->eps0, g->max_attempts, g->d_ginfo,
                                         g->d_warn, s);
     if (!err) err = cudaEventRecord(ev[5], s);
     if (!err) err = launch_retract(g->d_tau, g->d_poses, g->d_frozen, p.N, nullptr, s);
@@ -464,7 +537,7 @@ int como3r_graph_stats(como3r_graph_t g, int64_t* stats) {
   for (long long x : g->edge_valid) v += x;
   stats[COMO3R_STAT_VALID] = v;
   stats[COMO3R_STAT_CHUNK] = g->k1_chunk;
-  stats[COMO3R_STAT_BLOCK] = g->k1_block;
+  stats[COMO3R_STAT_BLOCK] = residual_reduce_block() * 100 + g->k1_cfg;
   stats[COMO3R_STAT_GRID] = g->k1_grid;
   stats[COMO3R_STAT_SMEM_SOLVE] = g->smem_solve ? 1 : 0;
   return COMO3R_OK;

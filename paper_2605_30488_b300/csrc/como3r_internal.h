@@ -5,8 +5,9 @@
 
 namespace como3r {
 
-// Doubles per K1 work-item partial: [0..24] H_rel unique entries, [25..31] g_rel,
-// [32] cost, [33] skipped matches, [34..35] unused.
+// 8-byte slots per K1 work-item record: [0..24] H_rel unique entries, [25..31] g_rel,
+// [32] cost, [33] skipped matches, [34..35] zero.  MIXED: float2 (sum, compensation)
+// per slot; PLAIN: double.
 constexpr int kPartial = 36;
 // Unique nonzero H_rel entries kept by K1 (the (omega, zeta) block is identically zero):
 // vv (00 01 02 11 12 22), v-omega (3x3 row-major), omega-omega (00 01 02 11 12 22),
@@ -41,30 +42,39 @@ struct GraphInfoDev {          // per graph, written on the device
 
 // Solver plan of all graphs, flattened (device arrays).  Block columns are numbered
 // globally; the columns of graph g are [col_begin[g], col_begin[g+1]) in elimination
-// order.  Slot s is one stored 7x7 block (row-major) of the factor.
+// order.  Slot s is one stored 7x7 block (row-major) of the factor.  Each elimination-
+// tree level has three task lists, executed with a CTA barrier between them:
+//   U: one task per destination block of the level's columns, (dst, t0, t1, col):
+//      L[dst] -= sum_{t0 <= t < t1} L[tri[t].x] L[tri[t].y]^T; col >= 0 marks a diagonal
+//      destination, whose task also forms the forward right-hand side of column col;
+//   D: the level's columns (diagonal factorisation + forward substitution);
+//   T: (slot, col): the off-diagonal blocks of the level's columns, solved against L_cc.
 struct SolverPlan {
   const int32_t* col_begin;    // [G+1]
   const int32_t* col_kf;       // [C] keyframe of each column
   const int32_t* col_slot;     // [C+1] slots of column c: diagonal at col_slot[c], then its rows
   const int32_t* slot_row;     // [S] block row (global column id) of each slot
-  const int32_t* tri_off;      // [C+1] left-looking update triplets of column c
-  const int4* tri;             // [T] (src_r, src_k, dst, 0): L[dst] -= L[src_r] L[src_k]^T
-  const int32_t* rs_off;       // [C+1] row structure of column c
-  const int2* rs;              // [R] (slot of block (c, j), j) for the columns j < c with L_cj != 0
-  const int32_t* sched;        // [C] columns of each graph sorted by elimination-tree level
-  const int32_t* lvl_begin;    // [G+1] level range of graph g in lvl_off
+  const int4* tri;             // [T] (src_r, src_k, dst, j): L[dst] -= L[src_r] L[src_k]^T, j = source column
+  const int4* utask;           // [U] (dst, t0, t1, col or -1)
+  const int32_t* utask_off;    // [L+1]
+  const int32_t* sched;        // [C] columns of each graph sorted by level
   const int32_t* lvl_off;      // [L+1] offsets of the levels in sched
+  const int2* ttask;           // [X] (off-diagonal slot, column)
+  const int32_t* ttask_off;    // [L+1]
+  const int32_t* lvl_begin;    // [G+1] level range of graph g
 };
 
 // ---- kernel launchers (defined in the .cu files) ----
 cudaError_t launch_edge_prep(const double* poses, const EdgeStatic* es, int E, double* T64, float* T32,
                              double* Ad, cudaStream_t s);
-cudaError_t launch_residual_reduce(int mode, int dtype, int block, int grid, const void* points,
+cudaError_t launch_residual_reduce(int mode, int dtype, int cfg, int grid, const void* points,
                                    const int32_t* midx, const Item* items, int num_items,
                                    const EdgeStatic* es, const double* T64, const float* T32,
-                                   RobustParams rp, double* partials, cudaStream_t s);
-int residual_reduce_max_blocks_per_sm(int mode, int dtype, int block);
-cudaError_t launch_edge_reduce(const double* partials, const int32_t* item_off, int E, const double* Ad,
+                                   RobustParams rp, void* partials, cudaStream_t s);
+int residual_reduce_max_blocks_per_sm(int mode, int dtype, int cfg);
+int residual_reduce_num_cfgs(int mode);
+int residual_reduce_block();
+cudaError_t launch_edge_reduce(int mode, const void* partials, const int32_t* item_off, int E, const double* Ad,
                                double* edge_M, double* edge_b, double* edge_cost, double* edge_skip,
                                double* edge_rec, const long long* edge_valid, cudaStream_t s);
 cudaError_t launch_assemble(int num_slots, const int32_t* slot_contrib_off, const int32_t* slot_contrib,
@@ -76,10 +86,11 @@ cudaError_t launch_assemble(int num_slots, const int32_t* slot_contrib_off, cons
 cudaError_t launch_export_dense(int num_slots, const int32_t* slot_kf_r, const int32_t* slot_kf_c,
                                 const double* A, int N, const double* gvec, double* H_out, double* g_out,
                                 cudaStream_t s);
+// Workspace doubles per column (outside the slots): 7 Dinv + 7 rhs/solution + 49 L_cc^{-1}.
+constexpr int kColScratch = 63;
 cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t smem_bytes, const double* A,
-                                double* L, double* Dinv, const double* gvec, double* y, double* tau,
-                                double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
-                                cudaStream_t s);
+                                double* L, double* colscratch, const double* gvec, double* tau, double lambda,
+                                double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s);
 size_t factor_solve_max_smem();
 cudaError_t factor_solve_prepare(size_t smem_bytes);  // once, before any capture
 cudaError_t launch_retract(const double* tau, double* poses, const uint8_t* frozen, int N, int* iter_counter,

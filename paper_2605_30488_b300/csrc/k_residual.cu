@@ -1,13 +1,13 @@
 // K1: per-match residual, whitening, Huber IRLS weights, 4x7 Jacobian and reduction of
 // the relative-pose normal-equation blocks of every edge (Sec. III-A, III-D).
 //
-// Work is split into items (edge, [begin, end) of the streamed keyframe's pixels).  A
-// persistent grid walks the item list; for each item every thread accumulates its pixels
-// (pixel m = begin + tid + k * BLOCK: coalesced streams of match_idx and X_i, a gather of
-// X_j[n]) into 33 registers -- the 25 structurally nonzero entries of
-// H_rel = sum J^T W J, the 7 of g_rel = sum J^T W e, and the cost -- then the block
-// reduces them and writes one FP64 partial per item.  Nothing is accumulated with
-// atomics, so results are bitwise reproducible.
+// Work is split into items (edge, [begin, end) of the streamed keyframe's pixels), each
+// owned by one warp of a persistent grid.  Every lane accumulates its pixels (pixel
+// m = begin + lane + 32 k: coalesced streams of match_idx and X_i, a gather of X_j[n])
+// into 33 registers -- the 25 structurally nonzero entries of H_rel = sum J^T W J, the 7
+// of g_rel = sum J^T W e, and the cost -- then the warp reduces them with shuffles and
+// writes one partial record per item.  No CTA barrier, no shared memory, no atomics:
+// results are bitwise reproducible and warps never wait for each other.
 //
 // Per match (m, n) of edge (i, j), with T_ij = (sR, t) and x = sR X_j,n + t:
 //   d = ||x||, xh = x / d, e = [xh - psi(X_i,m); d - ||X_i,m||]          (Eq. residual)
@@ -18,11 +18,15 @@
 //   ray rows   [P, -[xh]x, 0],   range row [xh^T, 0, d].
 // So the (omega, zeta) block of H_rel vanishes and 25 of its 28 unique entries remain.
 //
-// MIXED mode: all of the above in FP32 (T_ij rounded from FP64 per edge), per-thread
-// sums over <= chunk/BLOCK matches, an error-free (TwoSum) compensated warp butterfly,
-// and FP64 from the warp level on.  PLAIN mode: FP64 throughout.
+// MIXED mode: all of the above in FP32 (T_ij rounded from FP64 per edge), per-lane sums
+// over <= chunk/32 matches, an error-free (TwoSum) compensated warp butterfly, and the
+// record written as (sum, compensation) FP32 pairs that the per-edge reduction adds in
+// FP64 (B300's FP64 pipe is slow, so no FP64 instruction runs in this kernel).
+// PLAIN mode: FP64 throughout, record of FP64 values.
 #include <cuda_fp16.h>
+
 #include <cstdint>
+#include <type_traits>
 
 #include "como3r_internal.h"
 
@@ -217,8 +221,9 @@ __device__ __forceinline__ void warp_transpose_reduce(double (&v)[kAcc], double 
   }
 }
 
-__device__ __forceinline__ double warp_sum_scalar(float x) {
-  float c = 0.f;
+// Compensated warp sum of one value: returns the sum, `c` receives the compensation.
+__device__ __forceinline__ float warp_sum_pair(float x, float& c) {
+  c = 0.f;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     const float rx = __shfl_xor_sync(0xffffffffu, x, off);
@@ -227,28 +232,36 @@ __device__ __forceinline__ double warp_sum_scalar(float x) {
     x = two_sum(x, rx, err);
     c = c + rc + err;
   }
-  return (double)x + (double)c;
+  return x;
 }
-__device__ __forceinline__ double warp_sum_scalar(double x) {
+__device__ __forceinline__ double warp_sum_pair(double x, double& c) {
+  c = 0.0;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
   return x;
 }
 
-template <typename R, int DT, int BLOCK, int UNROLL>
-__global__ void __launch_bounds__(BLOCK) residual_reduce_kernel(
+// Partial record of one item: kPartial slots of 8 bytes.  Slots 0..31 hold the 32
+// butterfly accumulators, 32 the cost, 33 the skipped-match count, 34..35 zero.  MIXED
+// writes each slot as float2 (sum, compensation), PLAIN as one double.
+__device__ __forceinline__ void store_slot(float2* rec, int k, float v, float c) { rec[k] = make_float2(v, c); }
+__device__ __forceinline__ void store_slot(double* rec, int k, double v, double c) { rec[k] = v + c; }
+
+template <typename R, int DT, int BLOCK, int MINB, int UNROLL>
+__global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
     const void* __restrict__ points, const int32_t* __restrict__ midx, const Item* __restrict__ items,
     int num_items, const EdgeStatic* __restrict__ es, const double* __restrict__ T64,
-    const float* __restrict__ T32, RobustParams rp, double* __restrict__ partials) {
-  constexpr int NW = BLOCK / 32;
-  __shared__ double red[NW][kAcc + 2];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float* __restrict__ T32, RobustParams rp, void* __restrict__ partials) {
+  using Slot = typename std::conditional<sizeof(R) == 4, float2, double>::type;
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * BLOCK + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * BLOCK) >> 5;
   Consts<R> k;
   k.isr = (R)rp.inv_sigma_ray; k.isd = (R)rp.inv_sigma_dist;
   k.ivr = (R)rp.inv_var_ray; k.ivd = (R)rp.inv_var_dist;
   k.kappa = (R)rp.kappa; k.half_kappa = (R)(0.5 * rp.kappa);
 
-  for (int it = blockIdx.x; it < num_items; it += gridDim.x) {
+  for (int it = gwarp; it < num_items; it += nwarps) {
     const Item item = items[it];
     const int64_t pix_i = es[item.edge].pix_i, pix_j = es[item.edge].pix_j;
     const int32_t* __restrict__ idx = midx + es[item.edge].idx_off;
@@ -260,18 +273,18 @@ __global__ void __launch_bounds__(BLOCK) residual_reduce_kernel(
     }
     Acc<R> acc;
     acc.zero();
-    for (int base = item.begin + tid; base < item.end; base += BLOCK * UNROLL) {
+    for (int base = item.begin + lane; base < item.end; base += 32 * UNROLL) {
       int n[UNROLL];
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) {
-        const int m = base + u * BLOCK;
+        const int m = base + 32 * u;
         n[u] = (m < item.end) ? __ldg(idx + m) : -1;
       }
       R xi[UNROLL], yi[UNROLL], zi[UNROLL], ci[UNROLL], xj[UNROLL], yj[UNROLL], zj[UNROLL], cj[UNROLL];
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) {
         if (n[u] >= 0) {
-          load_px<DT, R>(points, pix_i + base + u * BLOCK, xi[u], yi[u], zi[u], ci[u]);
+          load_px<DT, R>(points, pix_i + base + 32 * u, xi[u], yi[u], zi[u], ci[u]);
           load_px<DT, R>(points, pix_j + n[u], xj[u], yj[u], zj[u], cj[u]);
         }
       }
@@ -280,54 +293,50 @@ __global__ void __launch_bounds__(BLOCK) residual_reduce_kernel(
         if (n[u] >= 0) accumulate<R>(xi[u], yi[u], zi[u], ci[u], xj[u], yj[u], zj[u], cj[u], T, k, acc);
       }
     }
-    // ---- block reduction: warp butterfly, then FP64 across warps in fixed order
+    // ---- warp reduction: compensated butterfly, lane l ends with accumulator l
     R comp[kAcc];
     warp_transpose_reduce(acc.v, comp, lane);
-    const double Ew = warp_sum_scalar(acc.E);
+    R Ec = R(0);
+    const R Ev = warp_sum_pair(acc.E, Ec);
     const int sk = __reduce_add_sync(0xffffffffu, acc.skipped);
-    red[warp][lane] = (double)acc.v[0] + (double)comp[0];
+    Slot* rec = reinterpret_cast<Slot*>(partials) + (int64_t)it * kPartial;
+    store_slot(rec, lane, acc.v[0], comp[0]);
     if (lane == 0) {
-      red[warp][kAcc] = Ew;
-      red[warp][kAcc + 1] = (double)sk;
+      store_slot(rec, kAcc, Ev, Ec);
+      store_slot(rec, kAcc + 1, (R)sk, R(0));
+      store_slot(rec, kAcc + 2, R(0), R(0));
+      store_slot(rec, kAcc + 3, R(0), R(0));
     }
-    __syncthreads();
-    if (tid < kAcc + 2) {
-      double s = 0.0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) s += red[w][tid];
-      partials[(int64_t)it * kPartial + tid] = s;
-    }
-    __syncthreads();
   }
 }
 
-template <typename R, int DT, int BLOCK>
-const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, BLOCK, 4>);
-}
+// Launch configurations the autotuner chooses from: 256-thread CTAs with a register
+// budget for 2, 3 or 4 resident CTAs per SM (more warps to cover the gather latency
+// against a few spilled registers).  FP64 runs only the first.
+constexpr int kK1Block = 256;
 
 template <typename R, int DT>
-const void* pick_block(int block) {
-  switch (block) {
-    case 128: return kernel_ptr<R, DT, 128>();
-    case 256: return kernel_ptr<R, DT, 256>();
-    case 512: return kernel_ptr<R, DT, 512>();
+const void* pick_cfg(int cfg) {
+  switch (cfg) {
+    case 0: return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 2>);
+    case 1: return sizeof(R) == 4 ? reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 3, 2>) : nullptr;
+    case 2: return sizeof(R) == 4 ? reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 4, 2>) : nullptr;
     default: return nullptr;
   }
 }
 
-const void* pick_kernel(int mode, int dtype, int block) {
+const void* pick_kernel(int mode, int dtype, int cfg) {
   if (mode == 1) {
     switch (dtype) {
-      case 0: return pick_block<float, 0>(block);
-      case 1: return pick_block<float, 1>(block);
-      case 2: return pick_block<float, 2>(block);
+      case 0: return pick_cfg<float, 0>(cfg);
+      case 1: return pick_cfg<float, 1>(cfg);
+      case 2: return pick_cfg<float, 2>(cfg);
     }
   } else {
     switch (dtype) {
-      case 0: return pick_block<double, 0>(block);
-      case 1: return pick_block<double, 1>(block);
-      case 2: return pick_block<double, 2>(block);
+      case 0: return pick_cfg<double, 0>(cfg);
+      case 1: return pick_cfg<double, 1>(cfg);
+      case 2: return pick_cfg<double, 2>(cfg);
     }
   }
   return nullptr;
@@ -335,24 +344,28 @@ const void* pick_kernel(int mode, int dtype, int block) {
 
 }  // namespace
 
-int residual_reduce_max_blocks_per_sm(int mode, int dtype, int block) {
-  const void* f = pick_kernel(mode, dtype, block);
+int residual_reduce_num_cfgs(int mode) { return mode == 1 ? 3 : 1; }
+
+int residual_reduce_block() { return kK1Block; }
+
+int residual_reduce_max_blocks_per_sm(int mode, int dtype, int cfg) {
+  const void* f = pick_kernel(mode, dtype, cfg);
   if (!f) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, block, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kK1Block, 0) != cudaSuccess) return 0;
   return n;
 }
 
-cudaError_t launch_residual_reduce(int mode, int dtype, int block, int grid, const void* points,
+cudaError_t launch_residual_reduce(int mode, int dtype, int cfg, int grid, const void* points,
                                    const int32_t* midx, const Item* items, int num_items,
                                    const EdgeStatic* es, const double* T64, const float* T32,
-                                   RobustParams rp, double* partials, cudaStream_t s) {
-  const void* f = pick_kernel(mode, dtype, block);
+                                   RobustParams rp, void* partials, cudaStream_t s) {
+  const void* f = pick_kernel(mode, dtype, cfg);
   if (!f) return cudaErrorInvalidValue;
   if (num_items <= 0) return cudaSuccess;
   void* args[] = {(void*)&points, (void*)&midx, (void*)&items, (void*)&num_items, (void*)&es,
                   (void*)&T64, (void*)&T32, (void*)&rp, (void*)&partials};
-  return cudaLaunchKernel(f, dim3(grid), dim3(block), args, 0, s);
+  return cudaLaunchKernel(f, dim3(grid), dim3(kK1Block), args, 0, s);
 }
 
 }  // namespace como3r

@@ -53,30 +53,43 @@ __device__ __forceinline__ int hrel_index(int r, int c) {
   return -1;                                                            // (omega, zeta)
 }
 
-// ---- K2: per edge, fixed-order FP64 sum of its item partials, then
+// ---- K2: per edge, fixed-order FP64 sum of its item records, then
 // M_e = Ad^T H_rel Ad (= H_jj = H_ii = -H_ij) and b_e = Ad^T g_rel (= g_j = -g_i).
-__global__ void __launch_bounds__(64) edge_reduce_kernel(const double* __restrict__ partials,
-                                                         const int32_t* __restrict__ item_off,
-                                                         const double* __restrict__ Ad_all, double* __restrict__ edge_M,
-                                                         double* __restrict__ edge_b, double* __restrict__ edge_cost,
-                                                         double* __restrict__ edge_skip, double* __restrict__ edge_rec,
-                                                         const long long* __restrict__ edge_valid) {
+// Eight groups of 36 threads each sum every eighth record; the group sums are then added
+// in group order, so the result is independent of scheduling.
+constexpr int kReduceGroups = 8;
+constexpr int kReduceThreads = kReduceGroups * kPartial;  // 288
+
+__device__ __forceinline__ double slot_value(const float2* rec, int k) {
+  const float2 v = rec[k];
+  return (double)v.x + (double)v.y;
+}
+__device__ __forceinline__ double slot_value(const double* rec, int k) { return rec[k]; }
+
+template <typename Slot>
+__global__ void __launch_bounds__(kReduceThreads) edge_reduce_kernel(
+    const Slot* __restrict__ partials, const int32_t* __restrict__ item_off, const double* __restrict__ Ad_all,
+    double* __restrict__ edge_M, double* __restrict__ edge_b, double* __restrict__ edge_cost,
+    double* __restrict__ edge_skip, double* __restrict__ edge_rec, const long long* __restrict__ edge_valid) {
   const int e = blockIdx.x, t = threadIdx.x;
+  __shared__ double red[kReduceGroups][kPartial];
   __shared__ double acc[kPartial];
   __shared__ double H[49], Ad[49], T1[49], g[7];
   const int i0 = item_off[e], i1 = item_off[e + 1];
-  if (t < kPartial) {
-    // two interleaved chains halve the dependent-add latency; fixed order either way
-    double s0 = 0.0, s1 = 0.0;
-    int it = i0;
-    for (; it + 1 < i1; it += 2) {
-      s0 += partials[(int64_t)it * kPartial + t];
-      s1 += partials[(int64_t)(it + 1) * kPartial + t];
-    }
-    if (it < i1) s0 += partials[(int64_t)it * kPartial + t];
-    acc[t] = s0 + s1;
+  {
+    const int grp = t / kPartial, a = t % kPartial;
+    double s = 0.0;
+    for (int it = i0 + grp; it < i1; it += kReduceGroups) s += slot_value(partials + (int64_t)it * kPartial, a);
+    red[grp][a] = s;
   }
   if (t < 49) Ad[t] = Ad_all[49 * e + t];
+  __syncthreads();
+  if (t < kPartial) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kReduceGroups; ++q) s += red[q][t];
+    acc[t] = s;
+  }
   __syncthreads();
   if (t < 49) {
     const int k = hrel_index(t / 7, t % 7);
@@ -235,12 +248,18 @@ cudaError_t launch_edge_prep(const double* poses, const EdgeStatic* es, int E, d
   return cudaGetLastError();
 }
 
-cudaError_t launch_edge_reduce(const double* partials, const int32_t* item_off, int E, const double* Ad,
+cudaError_t launch_edge_reduce(int mode, const void* partials, const int32_t* item_off, int E, const double* Ad,
                                double* edge_M, double* edge_b, double* edge_cost, double* edge_skip,
                                double* edge_rec, const long long* edge_valid, cudaStream_t s) {
   if (E <= 0) return cudaSuccess;
-  edge_reduce_kernel<<<E, 64, 0, s>>>(partials, item_off, Ad, edge_M, edge_b, edge_cost, edge_skip, edge_rec,
-                                      edge_valid);
+  if (mode == 1)
+    edge_reduce_kernel<float2><<<E, kReduceThreads, 0, s>>>(static_cast<const float2*>(partials), item_off, Ad,
+                                                            edge_M, edge_b, edge_cost, edge_skip, edge_rec,
+                                                            edge_valid);
+  else
+    edge_reduce_kernel<double><<<E, kReduceThreads, 0, s>>>(static_cast<const double*>(partials), item_off, Ad,
+                                                            edge_M, edge_b, edge_cost, edge_skip, edge_rec,
+                                                            edge_valid);
   return cudaGetLastError();
 }
 

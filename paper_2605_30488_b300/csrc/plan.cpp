@@ -7,7 +7,10 @@
 // dissection by breadth-first level structures (a middle BFS level from a
 // pseudo-peripheral node is a vertex separator; both sides are ordered recursively,
 // the separator last) keeps the tree depth logarithmic at a small cost in fill, which
-// matters on a GPU where every tree level is a dependent FP64 step.
+// matters on a GPU where every tree level is a dependent FP64 step.  For graphs with
+// more cross-links a minimum-degree order can be both shallower in fill and not much
+// deeper; each graph takes whichever of the two a simple cost model rates cheaper
+// (levels x per-level latency + block updates x per-update FP64 time).
 #include "plan.h"
 
 #include <algorithm>
@@ -118,6 +121,78 @@ struct Dissector {
   }
 };
 
+// Exact minimum-degree elimination order on the (small) block graph; ties -> lowest id.
+std::vector<int> min_degree_order(const std::vector<std::vector<int>>& adj) {
+  const int n = (int)adj.size();
+  std::vector<std::set<int>> G(n);
+  for (int u = 0; u < n; ++u) G[u].insert(adj[u].begin(), adj[u].end());
+  std::vector<char> done(n, 0);
+  std::vector<int> order;
+  order.reserve(n);
+  for (int step = 0; step < n; ++step) {
+    int v = -1;
+    size_t best = SIZE_MAX;
+    for (int u = 0; u < n; ++u)
+      if (!done[u] && G[u].size() < best) {
+        best = G[u].size();
+        v = u;
+      }
+    done[v] = 1;
+    order.push_back(v);
+    std::vector<int> nb(G[v].begin(), G[v].end());
+    for (int a : nb) {
+      G[a].erase(v);
+      for (int b : nb)
+        if (b != a) G[a].insert(b);
+    }
+    G[v].clear();
+  }
+  return order;
+}
+
+struct Symbolic {
+  std::vector<int> pos;                 // node -> elimination position
+  std::vector<std::vector<int>> rows;   // per position: sorted rows > position
+  std::vector<int> level;               // per position: elimination-tree level
+  int nlev = 0;
+  int64_t updates = 0;
+};
+
+Symbolic symbolic(const std::vector<std::vector<int>>& adj, const std::vector<int>& order) {
+  const int n = (int)adj.size();
+  Symbolic S;
+  S.pos.assign(n, 0);
+  for (int q = 0; q < n; ++q) S.pos[order[q]] = q;
+  std::vector<std::set<int>> nb(n);
+  for (int u = 0; u < n; ++u)
+    for (int v : adj[u]) nb[S.pos[u]].insert(S.pos[v]);
+  S.rows.assign(n, {});
+  for (int k = 0; k < n; ++k) {
+    S.rows[k].assign(nb[k].begin(), nb[k].end());  // all > k: earlier columns were removed
+    for (int r : S.rows[k]) {
+      nb[r].erase(k);
+      for (int r2 : S.rows[k])
+        if (r2 != r) nb[r].insert(r2);
+    }
+    nb[k].clear();
+    const int64_t c = (int64_t)S.rows[k].size();
+    S.updates += c * (c + 1) / 2;
+  }
+  S.level.assign(n, 0);
+  S.nlev = n ? 1 : 0;
+  for (int k = 0; k < n; ++k)
+    if (!S.rows[k].empty()) {
+      S.level[S.rows[k][0]] = std::max(S.level[S.rows[k][0]], S.level[k] + 1);
+      S.nlev = std::max(S.nlev, S.level[S.rows[k][0]] + 1);
+    }
+  return S;
+}
+
+// Rough cost (microseconds) of one factorisation + solve on one SM: every level pays
+// the dependent-latency chain of a 7x7 factorisation and the substitutions, every
+// block update ~14 warp FP64 instructions at one per 20 cycles.
+double order_cost(const Symbolic& S) { return 3.0 * S.nlev + 0.15 * (double)S.updates; }
+
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 }  // namespace
@@ -202,10 +277,10 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
   // ---- per graph: ordering, symbolic factorisation, levels
   p.col_begin.assign(1, 0);
   p.col_slot.assign(1, 0);
-  p.tri_off.assign(1, 0);
-  p.rs_off.assign(1, 0);
   p.lvl_begin.assign(1, 0);
   p.lvl_off.assign(1, 0);
+  p.utask_off.assign(1, 0);
+  p.ttask_off.assign(1, 0);
   std::vector<std::vector<int32_t>> slot_lists;  // contributions per slot
   std::vector<std::vector<int32_t>> kf_lists(N);
   for (int g = 0; g < G; ++g) {
@@ -233,36 +308,22 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
     std::vector<int> all(n);
     std::iota(all.begin(), all.end(), 0);
     nd.run(all);
-    std::vector<int> pos(n);
-    for (int q = 0; q < n; ++q) pos[nd.order[q]] = q;
-    // symbolic elimination on positions
-    std::vector<std::set<int>> nb(n);
-    for (int u = 0; u < n; ++u)
-      for (int v : adj[u]) nb[pos[u]].insert(pos[v]);
-    std::vector<std::vector<int>> rows(n);
-    for (int k = 0; k < n; ++k) {
-      rows[k].assign(nb[k].begin(), nb[k].end());  // all > k: earlier columns were removed
-      for (int r : rows[k]) {
-        nb[r].erase(k);
-        for (int r2 : rows[k])
-          if (r2 != r) nb[r].insert(r2);
-      }
-      nb[k].clear();
-    }
-    // levels
-    std::vector<int> level(n, 0);
-    int nlev = n ? 1 : 0;
-    for (int k = 0; k < n; ++k)
-      if (!rows[k].empty()) {
-        level[rows[k][0]] = std::max(level[rows[k][0]], level[k] + 1);
-        nlev = std::max(nlev, level[rows[k][0]] + 1);
-      }
-    p.max_levels = std::max(p.max_levels, nlev);
+    Symbolic S_nd = symbolic(adj, nd.order);
+    const std::vector<int> md_order = min_degree_order(adj);
+    Symbolic S_md = symbolic(adj, md_order);
+    const bool use_md = order_cost(S_md) <= order_cost(S_nd);
+    const std::vector<int>& order = use_md ? md_order : nd.order;
+    Symbolic& S = use_md ? S_md : S_nd;
+    p.order_kind.push_back(use_md ? 0 : 1);
+    const std::vector<int>& pos = S.pos;
+    const std::vector<std::vector<int>>& rows = S.rows;
+    const std::vector<int>& level = S.level;
+    p.max_levels = std::max(p.max_levels, S.nlev);
     // columns and slots (global numbering)
     const int cbase = p.col_begin.back();
     std::vector<int> slot_base(n);
     for (int k = 0; k < n; ++k) {
-      p.col_kf.push_back(k0 + kf_of[nd.order[k]]);
+      p.col_kf.push_back(k0 + kf_of[order[k]]);
       slot_base[k] = p.col_slot.back();
       p.slot_row.push_back(cbase + k);  // diagonal
       for (int r : rows[k]) p.slot_row.push_back(cbase + r);
@@ -282,31 +343,49 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
         p.slot_kf_c.push_back(kc);
       }
     }
-    // row structure and left-looking update triplets
+    // left-looking update triplets, grouped by destination block
     std::vector<std::vector<int>> rowstruct(n);
     for (int j = 0; j < n; ++j)
       for (int r : rows[j]) rowstruct[r].push_back(j);
+    std::vector<std::vector<int4>> tasks_of_level(S.nlev);
     for (int k = 0; k < n; ++k) {
       std::vector<std::pair<int, int4>> ts;
-      for (int j : rowstruct[k]) {
-        p.rs.push_back(make_int2(slot_of(k, j), cbase + j));
+      for (int j : rowstruct[k])
         for (int r : rows[j])
-          if (r >= k) ts.push_back({j, make_int4(slot_of(r, j), slot_of(k, j), slot_of(r, k), 0)});
-      }
+          if (r >= k) ts.push_back({j, make_int4(slot_of(r, j), slot_of(k, j), slot_of(r, k), cbase + j)});
       std::stable_sort(ts.begin(), ts.end(), [](const auto& x, const auto& y) {
         return x.second.z != y.second.z ? x.second.z < y.second.z : x.first < y.first;
       });
-      for (auto& t : ts) p.tri.push_back(t.second);
-      p.tri_off.push_back((int)p.tri.size());
-      p.rs_off.push_back((int)p.rs.size());
+      size_t q = 0;
+      while (q < ts.size()) {
+        size_t e = q;
+        while (e < ts.size() && ts[e].second.z == ts[q].second.z) ++e;
+        const int dst = ts[q].second.z;
+        const int t0 = (int)p.tri.size();
+        for (size_t x = q; x < e; ++x) p.tri.push_back(ts[x].second);
+        tasks_of_level[level[k]].push_back(make_int4(dst, t0, (int)p.tri.size(), dst == slot_base[k] ? cbase + k : -1));
+        q = e;
+      }
     }
-    // level schedule
+    // level schedule: columns, update tasks (longest first), off-diagonal solve tasks
     std::vector<int> byl(n);
     std::iota(byl.begin(), byl.end(), 0);
     std::stable_sort(byl.begin(), byl.end(), [&](int x, int y) { return level[x] < level[y]; });
-    for (int q = 0; q < n; ++q) {
-      p.sched.push_back(cbase + byl[q]);
-      if (q + 1 == n || level[byl[q + 1]] != level[byl[q]]) p.lvl_off.push_back((int)p.sched.size());
+    if (p.utask_off.empty()) p.utask_off.push_back(0);
+    if (p.ttask_off.empty()) p.ttask_off.push_back(0);
+    int q = 0;
+    for (int lv = 0; lv < S.nlev; ++lv) {
+      for (; q < n && level[byl[q]] == lv; ++q) {
+        const int k = byl[q];
+        p.sched.push_back(cbase + k);
+        for (size_t b = 0; b < rows[k].size(); ++b) p.ttask.push_back(make_int2(slot_base[k] + 1 + (int)b, cbase + k));
+      }
+      p.lvl_off.push_back((int)p.sched.size());
+      auto& tl = tasks_of_level[lv];
+      std::stable_sort(tl.begin(), tl.end(), [](const int4& x, const int4& y) { return (x.z - x.y) > (y.z - y.y); });
+      p.utask.insert(p.utask.end(), tl.begin(), tl.end());
+      p.utask_off.push_back((int)p.utask.size());
+      p.ttask_off.push_back((int)p.ttask.size());
     }
     p.lvl_begin.push_back((int)p.lvl_off.size() - 1);
     p.col_begin.push_back(cbase + n);
@@ -329,7 +408,7 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
       }
     }
     const size_t nslot = (size_t)(p.col_slot.back() - p.col_slot[cbase]);
-    p.max_graph_smem = std::max(p.max_graph_smem, sizeof(double) * (nslot * 49 + (size_t)n * 14));
+    p.max_graph_smem = std::max(p.max_graph_smem, sizeof(double) * (nslot * 49 + (size_t)n * kColScratch));
   }
   p.slot_contrib_off.assign(1, 0);
   for (auto& l : slot_lists) {
@@ -365,6 +444,9 @@ void plan_stats(const HostPlan& p, int64_t* s) {
   s[COMO3R_STAT_FILL] = p.fill_blocks;
   s[COMO3R_STAT_UPDATES] = (int64_t)p.tri.size();
   s[COMO3R_STAT_LEVELS] = p.max_levels;
+  int64_t nd = 0;
+  for (int8_t k : p.order_kind) nd += k;
+  s[COMO3R_STAT_ND_GRAPHS] = nd;
 }
 
 }  // namespace como3r

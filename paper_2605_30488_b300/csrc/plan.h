@@ -20,9 +20,10 @@ struct HostPlan {
   std::vector<EdgeStatic> es;     // [E]
   std::vector<uint8_t> frozen;    // [N] anchors
   // solver plan (see SolverPlan)
-  std::vector<int32_t> col_begin, col_kf, col_slot, slot_row, tri_off, rs_off, sched, lvl_begin, lvl_off;
-  std::vector<int4> tri;
-  std::vector<int2> rs;
+  std::vector<int32_t> col_begin, col_kf, col_slot, slot_row, sched, lvl_begin, lvl_off, utask_off, ttask_off;
+  std::vector<int4> tri, utask;
+  std::vector<int2> ttask;
+  std::vector<int8_t> order_kind;  // per graph: 0 minimum degree, 1 nested dissection
   std::vector<int32_t> slot_kf_r, slot_kf_c;
   // assembly (entries edge * 2 + negate, in edge order)
   std::vector<int32_t> slot_contrib_off, slot_contrib, kf_contrib_off, kf_contrib;

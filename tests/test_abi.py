@@ -33,7 +33,7 @@ def test_plan_of_small_problem(C):
     s = C.plan_stats(p)
     assert s["keyframes"] == 12 and s["edges"] == 14 and s["columns"] == 11
     assert s["blocks"] >= 11 + 13  # diagonals + at least the non-anchor edges' pairs
-    assert s["items"] == 14        # one 8192-pixel item per 3072-pixel edge
+    assert s["items"] == 14 * -(-3072 // s["chunk"])  # ceil(3072 px / chunk) items per edge
 
 
 def test_plan_depth_is_logarithmic_on_a_long_chain(C):
