@@ -150,7 +150,6 @@ def oracle_sample(prob, n_edges: int):
     plus the dense damped Cholesky solve and retraction of a system of the full size 7N.
     One iteration = sampled edge time x E / n_edges + solve + retraction.
     """
-    import threadpoolctl
     from oracle import como3r_oracle as O
     arrs = O.problem_arrays(prob)
     T = [O.pose_to_matrix(p) for p in prob.poses_init]
@@ -170,7 +169,11 @@ def oracle_sample(prob, n_edges: int):
     O.retract(prob.poses_init, 1e-3 * tau)
     t_solve = time.perf_counter() - t1
     t_iter = t_edges * prob.num_edges / len(sel) + t_solve
-    threads = max([p.get("num_threads", 1) for p in threadpoolctl.threadpool_info()] + [1])
+    try:  # BLAS threads the oracle's library calls may use
+        import threadpoolctl
+        threads = max([p.get("num_threads", 1) for p in threadpoolctl.threadpool_info()] + [1])
+    except ImportError:
+        threads = os.cpu_count() or 1
     return {"value": 1.0 / t_iter, "unit": UNIT, "cores": int(threads), "kind": "oracle",
             "sample": (f"{len(sel)} of {prob.num_edges} edges linearised + full {n7}x{n7} dense solve and "
                        f"retraction ({t_edges + t_solve:.1f} s CPU), extrapolated to one GN iteration"),

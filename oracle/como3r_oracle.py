@@ -31,7 +31,11 @@ Readings where the paper is silent (each also listed in the design notes):
   not finite; attempts r = 0..5 use eps_r = 1e-6 * 100^r;
 * a match is skipped when ||X_i,m|| or ||T_ij X_j,n|| is not > 1e-12, when
   c_i,m * c_j,n is negative, or when any of them is not finite;
-* the anchor is removed from the unknowns (all seven of its degrees of freedom).
+* the anchor is removed from the unknowns (all seven of its degrees of freedom); a
+  connected component of the edge graph that does not contain it gets its own
+  deterministic reference, its lowest keyframe id (Sec. III-C: until a component is
+  joined to agent 0's, a deterministic reference is selected for it), so every
+  component's gauge is fixed and no update is decided by the eps regulariser alone.
 """
 from __future__ import annotations
 
@@ -290,16 +294,40 @@ def cholesky(A: np.ndarray) -> Optional[np.ndarray]:
     return L
 
 
-def damped_solve(H: np.ndarray, g: np.ndarray, anchor: int, lam: float, eps0: float,
+def component_anchors(prob, graph: int = 0) -> List[int]:
+    """Local ids of the fixed keyframes of one graph: the given anchor for its connected
+    component, the lowest keyframe id for every other component (edges define adjacency)."""
+    k0, k1 = int(prob.kf_offset[graph]), int(prob.kf_offset[graph + 1])
+    parent = list(range(k1 - k0))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for e in range(int(prob.edge_offset[graph]), int(prob.edge_offset[graph + 1])):
+        a, b = find(int(prob.edge_i[e]) - k0), find(int(prob.edge_j[e]) - k0)
+        if a != b:
+            parent[max(a, b)] = min(a, b)
+    anchor = int(prob.anchor[graph]) - k0
+    fixed = {find(anchor): anchor}
+    for k in range(k1 - k0):
+        fixed.setdefault(find(k), k)
+    return sorted(fixed.values())
+
+
+def damped_solve(H: np.ndarray, g: np.ndarray, anchor, lam: float, eps0: float,
                  max_attempts: int) -> Tuple[np.ndarray, int, bool]:
-    """Solve (H + lam diag(H) + eps_r I) tau = -g over all keyframes but the anchor.
+    """Solve (H + lam diag(H) + eps_r I) tau = -g over all keyframes but the anchor(s).
 
     eps_r = eps0 * 100^r for r = 0 .. max_attempts-1; the first successful
     factorisation is used; if none succeeds the update is zero.  Returns (tau [N, 7],
     attempts made, success).
     """
     N = H.shape[0] // 7
-    keep = np.array([k for k in range(7 * N) if k // 7 != anchor], dtype=np.int64)
+    fixed = {int(anchor)} if np.isscalar(anchor) else {int(a) for a in anchor}
+    keep = np.array([k for k in range(7 * N) if k // 7 not in fixed], dtype=np.int64)
     Hr = H[np.ix_(keep, keep)]
     gr = g[keep]
     tau = np.zeros(7 * N)
@@ -334,7 +362,8 @@ def gn_step(prob, poses: np.ndarray, arrs=None) -> Tuple[np.ndarray, List[dict]]
     for gidx in range(prob.num_graphs):
         k0 = int(prob.kf_offset[gidx])
         H, g, cost, recs = build_system(prob, poses, gidx, arrs)
-        tau, attempts, ok = damped_solve(H, g, int(prob.anchor[gidx]) - k0, prob.lam, prob.eps0, prob.max_attempts)
+        tau, attempts, ok = damped_solve(H, g, component_anchors(prob, gidx), prob.lam, prob.eps0,
+                                         prob.max_attempts)
         out = retract(out, tau, k0)
         infos.append(dict(cost=cost, attempts=attempts, ok=ok, H=H, g=g, tau=tau,
                           n_skipped=sum(r["n_skipped"] for r in recs)))

@@ -250,8 +250,7 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
     }
     p.anchor[g] = a;
   }
-  p.frozen.assign(N, 0);
-  for (int g = 0; g < G; ++g) p.frozen[p.anchor[g]] = 1;
+
   // edges
   p.es.resize(E);
   int64_t off = 0;
@@ -273,6 +272,34 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
       off += p.npix[i];
     }
   p.total_idx = off;
+  // Fixed keyframes: the anchor of each graph, plus the lowest keyframe of every other
+  // connected component (a component not joined to the anchor's keeps a deterministic
+  // reference of its own, so no gauge direction is left to the eps regulariser).
+  p.frozen.assign(N, 0);
+  {
+    std::vector<int> parent(N);
+    std::iota(parent.begin(), parent.end(), 0);
+    auto find = [&](int a) {
+      while (parent[a] != a) a = parent[a] = parent[parent[a]];
+      return a;
+    };
+    for (int e = 0; e < p.edge_offset[G]; ++e) {
+      const int a = find(d->edge_i[e]), b = find(d->edge_j[e]);
+      if (a != b) parent[std::max(a, b)] = std::min(a, b);
+    }
+    for (int g = 0; g < G; ++g) {
+      std::vector<char> has_fixed(N, 0);
+      has_fixed[find(p.anchor[g])] = 1;
+      p.frozen[p.anchor[g]] = 1;
+      for (int k = p.kf_offset[g]; k < p.kf_offset[g + 1]; ++k) {
+        const int r = find(k);
+        if (!has_fixed[r]) {
+          has_fixed[r] = 1;
+          p.frozen[k] = 1;
+        }
+      }
+    }
+  }
 
   // ---- per graph: ordering, symbolic factorisation, levels
   p.col_begin.assign(1, 0);
@@ -284,11 +311,11 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
   std::vector<std::vector<int32_t>> slot_lists;  // contributions per slot
   std::vector<std::vector<int32_t>> kf_lists(N);
   for (int g = 0; g < G; ++g) {
-    const int k0 = p.kf_offset[g], nk = p.kf_offset[g + 1] - k0, a = p.anchor[g] - k0;
-    // local node ids (anchor removed): node u <-> keyframe k0 + kf_of[u]
+    const int k0 = p.kf_offset[g], nk = p.kf_offset[g + 1] - k0;
+    // local node ids (fixed keyframes removed): node u <-> keyframe k0 + kf_of[u]
     std::vector<int> node_of(nk, -1), kf_of;
     for (int l = 0; l < nk; ++l)
-      if (l != a) {
+      if (!p.frozen[k0 + l]) {
         node_of[l] = (int)kf_of.size();
         kf_of.push_back(l);
       }

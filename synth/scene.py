@@ -10,7 +10,10 @@ Recipe (all draws from one ``numpy.random.Generator(PCG64(seed))``):
   0.5 m per step with a yaw change uniform in +-10 deg (+-25 deg when no such step is
   admissible), keeping >= 0.5 m clearance from every surface; when less than 4 m of
   free path lies ahead it turns (<= 25 deg per step) towards the most open heading.  Agent a > 0 starts within 1.5 m of a keyframe of an earlier agent with a
-  heading within +-45 deg of it, so that the agents' views overlap somewhere.
+  heading within +-45 deg of it, so that the agents' views overlap somewhere.  Inter-agent
+  edges: first, for every agent a > 0, the best-overlapping pair linking it to an earlier
+  agent (so the map is connected), then the highest-overlap pairs (overlap >= 0.1 on a
+  256-pixel sample), preferring keyframes not yet linked.
 * Pinhole camera (x right, y down, z forward), principal point at the image centre,
   pixel (u, v) looks along ((u + 0.5 - W/2)/f, (v + 0.5 - H/2)/f, 1).
 * Each agent a has a gauge scale s_a ~ U[0.5, 2]: keyframe pointmaps hold metric
@@ -350,10 +353,16 @@ def _build_graph(rng, geom, *, agents, n_kf, H, W, f, noise, conf, outlier, skip
                     cand.append((s, i, j))
         cand.sort(key=lambda t: -t[0])
         chosen, used = [], set()
+        for a in range(1, agents):     # first link every agent to an earlier one (connected map)
+            link = [(s, i, j) for s, i, j in cand if agent_of[j] == a and agent_of[i] < a]
+            if not link:
+                raise RuntimeError(f"agent {a} has no overlapping keyframe with an earlier agent")
+            s, i, j = link[0]
+            chosen.append((i, j)); used.update((i, j))
         for s, i, j in cand:           # prefer keyframes not yet linked across agents
             if len(chosen) >= n_inter:
                 break
-            if i in used or j in used:
+            if i in used or j in used or (i, j) in chosen:
                 continue
             chosen.append((i, j)); used.update((i, j))
         for s, i, j in cand:

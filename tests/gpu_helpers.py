@@ -5,13 +5,13 @@ from oracle import como3r_oracle as O
 
 
 def oracle_dense_without_anchor(prob, poses, graph=0):
-    """The oracle's H, g of one graph with the anchor's rows/columns zeroed (what the library exports)."""
+    """The oracle's H, g of one graph with the fixed keyframes' rows/columns zeroed (as exported)."""
     H, g, E, recs = O.build_system(prob, poses, graph)
-    a = int(prob.anchor[graph] - prob.kf_offset[graph])
     H = H.copy(); g = g.copy()
-    H[7 * a:7 * a + 7, :] = 0.0
-    H[:, 7 * a:7 * a + 7] = 0.0
-    g[7 * a:7 * a + 7] = 0.0
+    for a in O.component_anchors(prob, graph):
+        H[7 * a:7 * a + 7, :] = 0.0
+        H[:, 7 * a:7 * a + 7] = 0.0
+        g[7 * a:7 * a + 7] = 0.0
     return H, g, E, recs
 
 

@@ -368,3 +368,16 @@ def test_degenerate_matches_are_skipped():
     rec = O.linearize_edge(np.eye(4), np.eye(4), Pi, Pj, make_problem.__defaults__ and dict(
         sigma_ray=0.003, sigma_dist=10.0, huber_k=1.345, lam=0.0, eps0=1e-6, max_attempts=6))
     assert rec["n_skipped"] == 2 and rec["n_valid"] == 10 and rec["cost"] < 1e-20
+
+
+def test_unlinked_component_keeps_its_own_reference():
+    """Without inter-agent edges agent 1 forms its own component: its lowest keyframe is held
+    fixed (Sec. III-C reading) and its other poses are recovered exactly relative to it."""
+    p = make_problem(3, noise=0.0, outlier=0.0, exact=True, n_inter=0, name="split")
+    assert O.component_anchors(p, 0) == [0, 6]
+    poses, _ = O.gn_solve(p, p.poses_init, 10)
+    G = O.pose_to_matrix(p.poses_init[6]) @ np.linalg.inv(O.pose_to_matrix(p.poses_gt[6]))
+    want = np.array([O.matrix_to_pose(G @ O.pose_to_matrix(q)) for q in p.poses_gt[6:]])
+    err = O.pose_errors(poses[6:], want)
+    assert max(err.values()) < 1e-9, err
+    assert max(O.pose_errors(poses[:6], p.poses_gt[:6]).values()) < 1e-9
