@@ -194,6 +194,37 @@ int como3r_graph_stats(como3r_graph_t graph, int64_t* stats /* [COMO3R_STAT_COUN
  * as como3r_graph_stats (K1 launch fields 0).  For inspecting orderings without a GPU. */
 int como3r_plan_stats(const como3r_graph_desc* desc, int64_t* stats /* [COMO3R_STAT_COUNT] */);
 
+/* ---- Allocation-free linearisation ------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory when they need a linearisation: code running while a CUDA
+ * graph is being captured (cudaMalloc is not a capturable operation), real-time loops
+ * that must never wait on the allocator, and host frameworks that reserve the whole
+ * device memory budget for themselves.  It computes exactly what como3r_linearize
+ * writes to edge_out, without a graph handle and without allocating anything: every
+ * intermediate lives in one fixed device array of COMO3R_NOALLOC_SCRATCH_BYTES that the
+ * library declares statically, so every GPU that loads the library holds that memory
+ * until the process exits.
+ *   desc      as for como3r_graph_create, with copy_inputs = 0: points_conf and
+ *             match_idx must be device memory (16- / 4-byte aligned); host arrays as usual.
+ *   poses     device [N][8], read only.
+ *   edge_out  device [E][COMO3R_EDGE_RECORD], written as by como3r_linearize.
+ *   stream    stream to run on (NULL = legacy default stream).
+ * Limits: at most COMO3R_NOALLOC_MAX_EDGES edges and COMO3R_NOALLOC_MAX_GRAPHS graphs;
+ * larger descriptions are rejected with COMO3R_ERR_INVALID_ARG before any GPU work
+ * (the work-item size is raised as needed to stay within COMO3R_NOALLOC_MAX_ITEMS).
+ * The first call on a device looks up the array's device address (once per device);
+ * make that first call before any stream capture.  All calls share the one array and a
+ * call overwrites what the previous call left there, so calls whose GPU work may
+ * overlap (different streams or host threads) race and must be serialised by the
+ * caller; the entry point is also not reentrant on the host.  The call synchronises the
+ * stream once (to check the match indices) and returns with the rest enqueued. */
+#define COMO3R_NOALLOC_MAX_EDGES 2048
+#define COMO3R_NOALLOC_MAX_ITEMS 16384
+#define COMO3R_NOALLOC_MAX_GRAPHS 256
+#define COMO3R_NOALLOC_SCRATCH_BYTES (7u * 1024u * 1024u)
+int como3r_linearize_noalloc(const como3r_graph_desc* desc, const double* poses, double* edge_out,
+                             void* cuda_stream);
+
 /* Human-readable text of a status code. */
 const char* como3r_status_str(int code);
 

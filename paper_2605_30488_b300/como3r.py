@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.como3r_last_launch_count.restype = ctypes.c_int64
     lib.como3r_graph_stats.argtypes = [vp, _i64p]
     lib.como3r_plan_stats.argtypes = [ctypes.POINTER(GraphDesc), _i64p]
+    lib.como3r_linearize_noalloc.argtypes = [ctypes.POINTER(GraphDesc), vp, vp, vp]
     lib.como3r_status_str.argtypes = [ctypes.c_int]
     lib.como3r_status_str.restype = ctypes.c_char_p
     lib.como3r_last_error.argtypes = []
@@ -247,6 +248,15 @@ def sim3_retract(tau, poses, stream=None) -> None:
     """poses[k] <- Exp(tau[k]) poses[k] on the device (tau [n, 7], poses [n, 8], float64 CUDA tensors)."""
     n = int(poses.shape[0])
     _check(lib().como3r_sim3_retract(_ptr(tau), _ptr(poses), n, _torch_stream(stream)), "sim3_retract")
+
+
+def linearize_noalloc(prob, poses, edge_out, mode: int = MIXED, points=None, match_idx=None, stream=None) -> int:
+    """como3r_linearize_noalloc: per-edge records into `edge_out` without any allocation
+    by the library (inputs must already be device tensors; see include/como3r.h)."""
+    keep = []
+    d = _build_desc(prob, _ptr(points), _ptr(match_idx), mode, False, keep)
+    return _check(lib().como3r_linearize_noalloc(ctypes.byref(d), _ptr(poses), _ptr(edge_out), _torch_stream(stream)),
+                  "linearize_noalloc")
 
 
 def exported_symbols(header: str) -> Sequence[str]:
