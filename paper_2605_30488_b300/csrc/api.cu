@@ -135,7 +135,7 @@ int enqueue_linearize(como3r_graph* g, cudaStream_t s, double* cost_hist, const 
   CK(launch_edge_reduce(p.mode, g->d_partials, g->d_item_off, p.E, g->d_Ad, g->d_edge_M, g->d_edge_b, g->d_edge_cost,
                         g->d_edge_skip, edge_rec, g->d_edge_valid, s),
      "edge_reduce");
-  const int nslots = p.col_slot.back();
+  const int nslots = p.slot_begin.back();
   CK(launch_assemble(nslots, g->d_slot_contrib_off, g->d_slot_contrib, g->d_edge_M, g->d_A, p.N, g->d_kf_contrib_off,
                      g->d_kf_contrib, g->d_edge_b, g->d_gvec, p.G, g->d_edge_offset, g->d_edge_cost, g->d_edge_skip,
                      g->d_ginfo, cost_hist, iter, g->d_warn, s),
@@ -227,7 +227,7 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   build_items(p, kChunks[0], items, item_off);
   g->max_items = (int)items.size();
   const int E = p.E, N = p.N, G = p.G;
-  const int nslots = p.col_slot.back(), ncols = p.col_begin.back();
+  const int nslots = p.slot_begin.back(), ncols = p.col_begin.back();
   if ((rc = upload(g, &g->d_es, p.es)) || (rc = upload(g, &g->d_items, items)) ||
       (rc = upload(g, &g->d_item_off, item_off)) || (rc = dalloc(g, &g->d_T64, (size_t)E * 12)) ||
       (rc = dalloc(g, &g->d_T32, (size_t)E * 16)) || (rc = dalloc(g, &g->d_Ad, (size_t)E * 49)) ||
@@ -246,17 +246,15 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
       (rc = dalloc(g, &g->d_poses, (size_t)N * 8)) || (rc = dalloc(g, &g->d_bad, 1)))
     return rc;
   // solver plan
-  int32_t *col_begin, *col_kf, *col_slot, *slot_row, *utask_off, *sched, *lvl_off, *ttask_off, *lvl_begin;
-  int4 *tri, *utask;
-  int2* ttask;
-  if ((rc = upload(g, &col_begin, p.col_begin)) || (rc = upload(g, &col_kf, p.col_kf)) ||
-      (rc = upload(g, &col_slot, p.col_slot)) || (rc = upload(g, &slot_row, p.slot_row)) ||
-      (rc = upload(g, &tri, p.tri)) || (rc = upload(g, &utask, p.utask)) || (rc = upload(g, &utask_off, p.utask_off)) ||
-      (rc = upload(g, &sched, p.sched)) || (rc = upload(g, &lvl_off, p.lvl_off)) || (rc = upload(g, &ttask, p.ttask)) ||
-      (rc = upload(g, &ttask_off, p.ttask_off)) || (rc = upload(g, &lvl_begin, p.lvl_begin)))
+  int32_t *meta, *col_kf, *lcol_slot, *lslot_row, *lsched, *llvl;
+  int4 *ltri, *lutask;
+  int2* lttask;
+  if ((rc = upload(g, &meta, p.meta)) || (rc = upload(g, &col_kf, p.col_kf)) ||
+      (rc = upload(g, &lcol_slot, p.lcol_slot)) || (rc = upload(g, &lslot_row, p.lslot_row)) ||
+      (rc = upload(g, &lsched, p.lsched)) || (rc = upload(g, &ltri, p.ltri)) || (rc = upload(g, &lutask, p.lutask)) ||
+      (rc = upload(g, &lttask, p.lttask)) || (rc = upload(g, &llvl, p.llvl)))
     return rc;
-  g->sp = SolverPlan{col_begin, col_kf, col_slot, slot_row, tri, utask, utask_off, sched, lvl_off, ttask, ttask_off,
-                     lvl_begin};
+  g->sp = SolverPlan{meta, col_kf, lcol_slot, lslot_row, lsched, ltri, lutask, lttask, llvl};
   CK(cudaMallocHost(&g->h_ginfo, sizeof(GraphInfoDev) * G), "cudaMallocHost");
   CK(cudaMallocHost(&g->h_warn, sizeof(int)), "cudaMallocHost");
   CK(cudaMemsetAsync(g->d_tau, 0, sizeof(double) * 7 * (size_t)N, g->stream), "memset");
@@ -409,7 +407,7 @@ int como3r_gn_step(como3r_graph_t g, double* poses, double* H_out, double* g_out
   if (H_out || g_out) {
     if (H_out)
       CK(cudaMemsetAsync(H_out, 0, sizeof(double) * 49 * (size_t)p.N * p.N, g->stream), "memset H_out");
-    CK(launch_export_dense(p.col_slot.back(), g->d_slot_kf_r, g->d_slot_kf_c, g->d_A, p.N, g->d_gvec, H_out, g_out,
+    CK(launch_export_dense(p.slot_begin.back(), g->d_slot_kf_r, g->d_slot_kf_c, g->d_A, p.N, g->d_gvec, H_out, g_out,
                            g->stream),
        "export");
     ++launches;
@@ -484,7 +482,7 @@ int como3r_time_stages(como3r_graph_t g, const double* poses, int32_t reps, floa
   for (auto& e : ev) CK(cudaEventCreate(&e), "event create");
   double acc[COMO3R_STAGES] = {0};
   cudaStream_t s = g->stream;
-  const int nslots = p.col_slot.back();
+  const int nslots = p.slot_begin.back();
   for (int r = 0; r < reps && !rc; ++r) {
     cudaError_t err = cudaEventRecord(ev[0], s);
     if (!err) err = launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, s);

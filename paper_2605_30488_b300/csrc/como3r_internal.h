@@ -40,29 +40,41 @@ struct GraphInfoDev {          // per graph, written on the device
   long long skipped;
 };
 
-// Solver plan of all graphs, flattened (device arrays).  Block columns are numbered
-// globally; the columns of graph g are [col_begin[g], col_begin[g+1]) in elimination
-// order.  Slot s is one stored 7x7 block (row-major) of the factor.  Each elimination-
-// tree level has three task lists, executed with a CTA barrier between them:
+// Solver plan of all graphs (device arrays).  Every index inside a graph's plan is local
+// to that graph (slots 0..nslot-1, columns 0..ncol-1 in elimination order, triplets and
+// tasks from 0), so a CTA can stage its graph's plan in shared memory as is; meta[g]
+// locates the graph's part of each concatenated array.  Slot s is one stored 7x7 block
+// (row-major) of the factor.  Each elimination-tree level has three task lists, executed
+// with a CTA barrier between them:
 //   U: one task per destination block of the level's columns, (dst, t0, t1, col):
 //      L[dst] -= sum_{t0 <= t < t1} L[tri[t].x] L[tri[t].y]^T; col >= 0 marks a diagonal
 //      destination, whose task also forms the forward right-hand side of column col;
 //   D: the level's columns (diagonal factorisation + forward substitution);
 //   T: (slot, col): the off-diagonal blocks of the level's columns, solved against L_cc.
-struct SolverPlan {
-  const int32_t* col_begin;    // [G+1]
-  const int32_t* col_kf;       // [C] keyframe of each column
-  const int32_t* col_slot;     // [C+1] slots of column c: diagonal at col_slot[c], then its rows
-  const int32_t* slot_row;     // [S] block row (global column id) of each slot
-  const int4* tri;             // [T] (src_r, src_k, dst, j): L[dst] -= L[src_r] L[src_k]^T, j = source column
-  const int4* utask;           // [U] (dst, t0, t1, col or -1)
-  const int32_t* utask_off;    // [L+1]
-  const int32_t* sched;        // [C] columns of each graph sorted by level
-  const int32_t* lvl_off;      // [L+1] offsets of the levels in sched
-  const int2* ttask;           // [X] (off-diagonal slot, column)
-  const int32_t* ttask_off;    // [L+1]
-  const int32_t* lvl_begin;    // [G+1] level range of graph g
+enum GraphMeta {
+  kMetaColBase, kMetaNCol, kMetaSlotBase, kMetaNSlot, kMetaTriBase, kMetaNTri,
+  kMetaUBase, kMetaNU, kMetaTBase, kMetaNT, kMetaLvlBase, kMetaNLvl, kMetaCount
 };
+struct SolverPlan {
+  const int32_t* meta;      // [G][kMetaCount]
+  const int32_t* col_kf;    // [C] keyframe (global id) of each column, at col_base
+  const int32_t* col_slot;  // per graph ncol+1 local slot offsets (diagonal first), at col_base + g
+  const int32_t* slot_row;  // local block-row column of each slot, at slot_base
+  const int32_t* sched;     // local columns in level order, at col_base
+  const int4* tri;          // (src_r, src_k, dst, j) local slots / column, at tri_base
+  const int4* utask;        // (dst, t0, t1, col or -1), at u_base
+  const int2* ttask;        // (slot, col), at t_base
+  const int32_t* lvl;       // per graph (nlev+1) x 3: offsets of each level in sched, utask, ttask; at 3 * lvl_base
+};
+
+// Bytes of shared memory one graph's factor, per-column scratch and plan occupy.
+inline size_t solver_smem_bytes(int nslot, int ncol, int ntri, int nu, int nt, int nlev) {
+  auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+  size_t b = r16(sizeof(double) * ((size_t)nslot * 49 + (size_t)ncol * 63));
+  b += r16(16 * (size_t)ntri) + r16(16 * (size_t)nu) + r16(8 * (size_t)nt);
+  b += r16(4 * (size_t)(ncol + 1)) + r16(4 * (size_t)nslot) + r16(4 * (size_t)ncol) + r16(12 * (size_t)(nlev + 1));
+  return b;
+}
 
 // ---- kernel launchers (defined in the .cu files) ----
 cudaError_t launch_edge_prep(const double* poses, const EdgeStatic* es, int E, double* T64, float* T32,

@@ -7,9 +7,10 @@
 //   U  one warp per destination block: L[dst] -= sum L_rj L_cj^T over the descendants j
 //      (diagonal destinations also accumulate the forward right-hand side
 //      b_c - sum_j L_cj y_j);
-//   D  one warp per column: Cholesky of the 7x7 diagonal block in registers (lane r holds
-//      row r) with the right-hand side riding along as an eighth row, which yields
-//      y_c = L_cc^{-1}(...) for free; a pivot that is not > 0 or not finite fails the attempt;
+//   D  four columns per warp (8 lanes each): Cholesky of the 7x7 diagonal block in
+//      registers (lane r holds row r) with the right-hand side riding along as an eighth
+//      row, which yields y_c = L_cc^{-1}(...) for free; a pivot that is not > 0 or not
+//      finite fails the attempt;
 //   T  one thread per row of every off-diagonal block (B <- B L_cc^{-T}) and per column of
 //      L_cc^{-1}, all independent.
 // A failed attempt restarts with eps_r = eps0 * 100^r; after max_attempts failures the
@@ -29,15 +30,22 @@ constexpr int kSolveThreads = 512;
 constexpr int kSolveWarps = kSolveThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
+// Local view of one graph's solver state: blocks, per-column scratch and plan arrays,
+// all with graph-local indices (in shared memory, or the graph's part of global memory).
 struct SolveCtx {
-  const SolverPlan* P;
-  double* L;   // blocks of this graph: local slot (s - s0) * 49
-  double* S;   // per-column scratch: (col - c0) * kColScratch = [Dinv 7 | y 7 | Linv 49]
-  int s0, c0;
+  double* L;              // slot s at L + 49 s
+  double* S;              // column c at S + kColScratch c = [Dinv 7 | y 7 | Linv 49]
+  const int* col_slot;    // [ncol + 1]
+  const int* slot_row;    // [nslot]
+  const int* sched;       // [ncol]
+  const int4* tri;        // [ntri]
+  const int4* utask;      // [nu]
+  const int2* ttask;      // [nt]
+  const int* lvl;         // [(nlev + 1) * 3]
 };
 
-__device__ __forceinline__ double* blk(const SolveCtx& C, int s) { return C.L + (int64_t)(s - C.s0) * 49; }
-__device__ __forceinline__ double* dinv_of(const SolveCtx& C, int col) { return C.S + (int64_t)(col - C.c0) * kColScratch; }
+__device__ __forceinline__ double* blk(const SolveCtx& C, int s) { return C.L + (int64_t)s * 49; }
+__device__ __forceinline__ double* dinv_of(const SolveCtx& C, int col) { return C.S + (int64_t)col * kColScratch; }
 __device__ __forceinline__ double* y_of(const SolveCtx& C, int col) { return dinv_of(C, col) + 7; }
 __device__ __forceinline__ double* linv_of(const SolveCtx& C, int col) { return dinv_of(C, col) + 14; }
 
@@ -53,73 +61,83 @@ __device__ __forceinline__ double dot7(const double* a, const double* b, double 
   return p + q;
 }
 
-// U: one destination block (see file header)
+// U: one destination block (see file header).  Pass 1: lane l owns entry l of the 7x7
+// destination; pass 2: lanes 0..16 own entries 32..48, lanes 17..23 the seven rows of the
+// forward right-hand side (diagonal destinations only), lanes 24..31 idle.
 __device__ void update_task(const SolveCtx& C, int4 task, int lane) {
-  const SolverPlan& P = *C.P;
   const int e0 = lane, e1 = lane + 32;
   const bool has1 = e1 < 49;
-  const int r0 = e0 / 7, q0 = e0 % 7, r1 = has1 ? e1 / 7 : 0, q1 = has1 ? e1 % 7 : 0;
-  double a0 = 0.0, a1 = 0.0, rh = 0.0;
-  const bool rhs = task.w >= 0 && lane < 7;
+  const bool rhs = task.w >= 0 && lane >= 17 && lane < 24;
+  const int r0 = e0 / 7, q0 = e0 % 7, r1 = has1 ? e1 / 7 : lane - 17, q1 = has1 ? e1 % 7 : 0;
+  double a0 = 0.0, a1 = 0.0;
   for (int t = task.y; t < task.z; ++t) {
-    const int4 tr = P.tri[t];
+    const int4 tr = C.tri[t];
     const double* Lr = blk(C, tr.x);
     const double* Lk = blk(C, tr.y);
     a0 += dot7(Lr + 7 * r0, Lk + 7 * q0, 0.0);
     if (has1) a1 += dot7(Lr + 7 * r1, Lk + 7 * q1, 0.0);
-    if (rhs) rh += dot7(Lr + 7 * lane, y_of(C, tr.w), 0.0);
+    else if (rhs) a1 += dot7(Lr + 7 * r1, y_of(C, tr.w), 0.0);
   }
   double* D = blk(C, task.x);
   D[e0] -= a0;
   if (has1) D[e1] -= a1;
-  if (rhs) y_of(C, task.w)[lane] -= rh;
+  else if (rhs) y_of(C, task.w)[lane - 17] -= a1;
 }
 
-// D: Cholesky of the diagonal block with the forward right-hand side as row 7
-__device__ void diag_factor(const SolveCtx& C, int col, int lane, int* fail) {
-  const SolverPlan& P = *C.P;
-  double* D = blk(C, P.col_slot[col]);
+// D: Cholesky of diagonal blocks, four columns per warp (FP64 instructions occupy the
+// pipe for the whole warp, so idle lanes would waste it).  Segment s = lane / 8 handles
+// column cols[s]; within it lane r < 7 holds row r and lane 7 holds the forward
+// right-hand side as an eighth row, so the elimination also yields y_c = L_cc^{-1} t_c.
+// Segments without a column factor an identity block and write nothing.
+__device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int lane, int* fail) {
+  const int seg = lane >> 3, sl = lane & 7;
+  const bool active = seg < ncols;
+  const int col = cols[active ? seg : 0];
+  double* D = blk(C, C.col_slot[col]);
   double* y = y_of(C, col);
   double a[7];
 #pragma unroll
-  for (int c = 0; c < 7; ++c) a[c] = lane < 7 ? D[7 * lane + c] : (lane == 7 ? y[c] : 0.0);
+  for (int c = 0; c < 7; ++c) {
+    if (active) a[c] = sl < 7 ? D[7 * sl + c] : y[c];
+    else a[c] = (c == sl) ? 1.0 : 0.0;
+  }
   bool bad = false;
   double myinv = 0.0;
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
-    const double p = __shfl_sync(kFull, a[k], k);
+    const double p = __shfl_sync(kFull, a[k], k, 8);
     const bool okp = (p > 0.0) && (p < __longlong_as_double(0x7ff0000000000000LL));
     bad = bad || !okp;
     const double inv = rsqrt(okp ? p : 1.0);
-    const double lk = (lane == k) ? p * inv : a[k] * inv;
-    if (lane == k) myinv = inv;
-    if (lane >= k) a[k] = lk;
+    const double lk = (sl == k) ? p * inv : a[k] * inv;
+    if (sl == k) myinv = inv;
+    if (sl >= k) a[k] = lk;
 #pragma unroll
     for (int c = k + 1; c < 7; ++c) {
-      const double lc = __shfl_sync(kFull, lk, c);
-      if (lane >= c) a[c] = fma(-lk, lc, a[c]);
+      const double lc = __shfl_sync(kFull, lk, c, 8);
+      if (sl >= c) a[c] = fma(-lk, lc, a[c]);
     }
   }
-  if (lane < 7) {
+  if (active) {
+    if (sl < 7) {
 #pragma unroll
-    for (int c = 0; c < 7; ++c) D[7 * lane + c] = (c <= lane) ? a[c] : 0.0;
-    dinv_of(C, col)[lane] = myinv;
-  } else if (lane == 7) {
+      for (int c = 0; c < 7; ++c) D[7 * sl + c] = (c <= sl) ? a[c] : 0.0;
+      dinv_of(C, col)[sl] = myinv;
+    } else {
 #pragma unroll
-    for (int c = 0; c < 7; ++c) y[c] = a[c];
+      for (int c = 0; c < 7; ++c) y[c] = a[c];
+    }
+    if (bad && sl == 0) *fail = 1;
   }
-  if (bad && lane == 0) *fail = 1;
 }
 
-// T: item x < 7 * nt: row (x % 7) of off-diagonal block ttask[x / 7]; else column (x % 7)
-// of L_cc^{-1} for the level column (x - 7 nt) / 7.
-__device__ void trsm_or_inverse(const SolveCtx& C, int lv, int x) {
-  const SolverPlan& P = *C.P;
-  const int nt = P.ttask_off[lv + 1] - P.ttask_off[lv];
+// T: item x < 7 * nt: row (x % 7) of off-diagonal block ttask[t0 + x / 7]; else column
+// (x % 7) of L_cc^{-1} for the level column sched[s0 + (x - 7 nt) / 7].
+__device__ void trsm_or_inverse(const SolveCtx& C, int t0, int nt, int s0, int x) {
   if (x < 7 * nt) {
-    const int2 tt = P.ttask[P.ttask_off[lv] + x / 7];
+    const int2 tt = C.ttask[t0 + x / 7];
     const int i = x % 7;
-    const double* Lc = blk(C, P.col_slot[tt.y]);
+    const double* Lc = blk(C, C.col_slot[tt.y]);
     const double* dv = dinv_of(C, tt.y);
     double* B = blk(C, tt.x) + 7 * i;
     double xr[7];
@@ -134,8 +152,8 @@ __device__ void trsm_or_inverse(const SolveCtx& C, int lv, int x) {
     for (int c = 0; c < 7; ++c) B[c] = xr[c];
   } else {
     const int k = (x - 7 * nt) / 7, c = x % 7;
-    const int col = P.sched[P.lvl_off[lv] + k];
-    const double* Lc = blk(C, P.col_slot[col]);
+    const int col = C.sched[s0 + k];
+    const double* Lc = blk(C, C.col_slot[col]);
     const double* dv = dinv_of(C, col);
     double* X = linv_of(C, col);
     double xc[7];
@@ -160,14 +178,13 @@ __device__ void trsm_or_inverse(const SolveCtx& C, int lv, int x) {
 
 // back substitution of one column: x_c = L_cc^{-T} (y_c - sum_r L_rc^T x_r)
 __device__ void backward_column(const SolveCtx& C, int col, int lane) {
-  const SolverPlan& P = *C.P;
   const int grp = lane / 7, q = lane % 7;
-  const int s_begin = P.col_slot[col] + 1, nb = P.col_slot[col + 1] - s_begin;
+  const int s_begin = C.col_slot[col] + 1, nb = C.col_slot[col + 1] - s_begin;
   double part = 0.0;
   if (grp < 4) {
     for (int b = grp; b < nb; b += 4) {
       const double* B = blk(C, s_begin + b);
-      const double* xr = y_of(C, P.slot_row[s_begin + b]);
+      const double* xr = y_of(C, C.slot_row[s_begin + b]);
       double p0 = B[q] * xr[0];
       double p1 = B[7 + q] * xr[1];
       p0 = fma(B[14 + q], xr[2], p0);
@@ -194,14 +211,28 @@ __device__ void backward_column(const SolveCtx& C, int col, int lane) {
   if (lane < 7) y[q] = xq;
 }
 
+template <typename T>
+__device__ __forceinline__ T* carve(unsigned char*& p, size_t count) {
+  T* r = reinterpret_cast<T*>(p);
+  p += (sizeof(T) * count + 15) & ~size_t(15);
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void stage(T* dst, const T* src, int n, int tid) {
+  for (int x = tid; x < n; x += kSolveThreads) dst[x] = src[x];
+}
+
 template <bool SMEM>
 __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     SolverPlan P, const double* __restrict__ A, double* Lg, double* Sg, const double* __restrict__ gvec,
     double* __restrict__ tau, double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn) {
-  extern __shared__ __align__(16) double dyn[];
+  extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ int s_fail;
   const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int c0 = P.col_begin[g], c1 = P.col_begin[g + 1], ncol = c1 - c0;
+  const int* m = P.meta + kMetaCount * g;
+  const int cbase = m[kMetaColBase], ncol = m[kMetaNCol], sbase = m[kMetaSlotBase], nslot = m[kMetaNSlot];
+  const int nlev = m[kMetaNLvl];
   if (ncol == 0) {
     if (tid == 0) {
       ginfo[g].attempts = 1;
@@ -209,39 +240,68 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     }
     return;
   }
-  const int s0 = P.col_slot[c0], nslot = P.col_slot[c1] - s0;
+  const int* gcol_slot = P.col_slot + cbase + g;
+  const int* gslot_row = P.slot_row + sbase;
+  const int* gsched = P.sched + cbase;
+  const int4* gtri = P.tri + m[kMetaTriBase];
+  const int4* gutask = P.utask + m[kMetaUBase];
+  const int2* gttask = P.ttask + m[kMetaTBase];
+  const int* glvl = P.lvl + 3 * m[kMetaLvlBase];
   SolveCtx C;
-  C.P = &P;
-  C.L = SMEM ? dyn : Lg + (int64_t)s0 * 49;
-  C.S = SMEM ? dyn + (int64_t)nslot * 49 : Sg + (int64_t)c0 * kColScratch;
-  C.s0 = s0;
-  C.c0 = c0;
-  const int lv0 = P.lvl_begin[g], lv1 = P.lvl_begin[g + 1];
+  if (SMEM) {
+    unsigned char* q = dyn;
+    C.L = carve<double>(q, (size_t)nslot * 49 + (size_t)ncol * kColScratch);
+    C.S = C.L + (size_t)nslot * 49;
+    int4* tri = carve<int4>(q, m[kMetaNTri]);
+    int4* ut = carve<int4>(q, m[kMetaNU]);
+    int2* tt = carve<int2>(q, m[kMetaNT]);
+    int* cs = carve<int>(q, ncol + 1);
+    int* sr = carve<int>(q, nslot);
+    int* sc = carve<int>(q, ncol);
+    int* lv = carve<int>(q, 3 * (nlev + 1));
+    stage(tri, gtri, m[kMetaNTri], tid);
+    stage(ut, gutask, m[kMetaNU], tid);
+    stage(tt, gttask, m[kMetaNT], tid);
+    stage(cs, gcol_slot, ncol + 1, tid);
+    stage(sr, gslot_row, nslot, tid);
+    stage(sc, gsched, ncol, tid);
+    stage(lv, glvl, 3 * (nlev + 1), tid);
+    C.tri = tri; C.utask = ut; C.ttask = tt; C.col_slot = cs; C.slot_row = sr; C.sched = sc; C.lvl = lv;
+  } else {
+    C.L = Lg + (int64_t)sbase * 49;
+    C.S = Sg + (int64_t)cbase * kColScratch;
+    C.tri = gtri; C.utask = gutask; C.ttask = gttask; C.col_slot = gcol_slot; C.slot_row = gslot_row;
+    C.sched = gsched; C.lvl = glvl;
+  }
+  const double* Ag = A + (int64_t)sbase * 49;
+  const int* col_kf = P.col_kf + cbase;
 
   bool ok = false;
   int attempt = 0;
   double pow100 = 1.0;  // 100^attempt, exact in FP64
   for (; attempt < max_attempts; ++attempt, pow100 *= 100.0) {
     const double eps = eps0 * pow100;
-    for (int64_t x = tid; x < (int64_t)nslot * 49; x += kSolveThreads) C.L[x] = A[(int64_t)s0 * 49 + x];
+    for (int64_t x = tid; x < (int64_t)nslot * 49; x += kSolveThreads) C.L[x] = Ag[x];
     __syncthreads();
     for (int x = tid; x < 7 * ncol; x += kSolveThreads) {
-      const int col = c0 + x / 7, k = x % 7;
-      const int64_t ds = P.col_slot[col];
-      blk(C, (int)ds)[8 * k] += lambda * A[ds * 49 + 8 * k] + eps;
-      y_of(C, col)[k] = -gvec[7 * P.col_kf[col] + k];
+      const int col = x / 7, k = x % 7;
+      const int ds = C.col_slot[col];
+      blk(C, ds)[8 * k] += lambda * Ag[(int64_t)ds * 49 + 8 * k] + eps;
+      y_of(C, col)[k] = -gvec[7 * col_kf[col] + k];
     }
     if (tid == 0) s_fail = 0;
     __syncthreads();
-    for (int lv = lv0; lv < lv1; ++lv) {
-      for (int u = P.utask_off[lv] + warp; u < P.utask_off[lv + 1]; u += kSolveWarps) update_task(C, P.utask[u], lane);
+    for (int lv = 0; lv < nlev; ++lv) {
+      const int* L0 = C.lvl + 3 * lv;  // [sched, utask, ttask] offsets of this level and (at +3) the next
+      for (int u = L0[1] + warp; u < L0[4]; u += kSolveWarps) update_task(C, C.utask[u], lane);
       __syncthreads();
-      for (int q = P.lvl_off[lv] + warp; q < P.lvl_off[lv + 1]; q += kSolveWarps)
-        diag_factor(C, P.sched[q], lane, &s_fail);
+      for (int q = L0[0] + 4 * warp; q < L0[3]; q += 4 * kSolveWarps)
+        diag_factor4(C, C.sched + q, min(4, L0[3] - q), lane, &s_fail);
       __syncthreads();
       if (s_fail) break;
-      const int nx = 7 * (P.ttask_off[lv + 1] - P.ttask_off[lv] + P.lvl_off[lv + 1] - P.lvl_off[lv]);
-      for (int x = tid; x < nx; x += kSolveThreads) trsm_or_inverse(C, lv, x);
+      const int nt = L0[5] - L0[2];
+      const int nx = 7 * (nt + L0[3] - L0[0]);
+      for (int x = tid; x < nx; x += kSolveThreads) trsm_or_inverse(C, L0[2], nt, L0[0], x);
       __syncthreads();
     }
     ok = (s_fail == 0);
@@ -249,14 +309,14 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     if (ok) break;
   }
   if (ok) {
-    for (int lv = lv1 - 1; lv >= lv0; --lv) {
-      for (int q = P.lvl_off[lv] + warp; q < P.lvl_off[lv + 1]; q += kSolveWarps)
-        backward_column(C, P.sched[q], lane);
+    for (int lv = nlev - 1; lv >= 0; --lv) {
+      const int* L0 = C.lvl + 3 * lv;
+      for (int q = L0[0] + warp; q < L0[3]; q += kSolveWarps) backward_column(C, C.sched[q], lane);
       __syncthreads();
     }
-    for (int x = tid; x < 7 * ncol; x += kSolveThreads) tau[7 * P.col_kf[c0 + x / 7] + x % 7] = y_of(C, c0 + x / 7)[x % 7];
+    for (int x = tid; x < 7 * ncol; x += kSolveThreads) tau[7 * col_kf[x / 7] + x % 7] = y_of(C, x / 7)[x % 7];
   } else {
-    for (int x = tid; x < 7 * ncol; x += kSolveThreads) tau[7 * P.col_kf[c0 + x / 7] + x % 7] = 0.0;
+    for (int x = tid; x < 7 * ncol; x += kSolveThreads) tau[7 * col_kf[x / 7] + x % 7] = 0.0;
   }
   if (tid == 0) {
     ginfo[g].attempts = ok ? attempt + 1 : max_attempts;

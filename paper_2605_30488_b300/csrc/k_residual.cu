@@ -247,7 +247,42 @@ __device__ __forceinline__ double warp_sum_pair(double x, double& c) {
 __device__ __forceinline__ void store_slot(float2* rec, int k, float v, float c) { rec[k] = make_float2(v, c); }
 __device__ __forceinline__ void store_slot(double* rec, int k, double v, double c) { rec[k] = v + c; }
 
-template <typename R, int DT, int BLOCK, int MINB, int UNROLL>
+// One group of UNROLL pixels per lane: match indices, then the two packed pixels.
+template <typename R, int U>
+struct Group {
+  int n[U];
+  R xi[U], yi[U], zi[U], ci[U], xj[U], yj[U], zj[U], cj[U];
+};
+
+template <typename R, int U>
+__device__ __forceinline__ void load_indices(int (&n)[U], const int32_t* __restrict__ idx, int m0, int end) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int m = m0 + 32 * u;
+    n[u] = (m < end) ? __ldg(idx + m) : -1;
+  }
+}
+
+template <int DT, typename R, int U>
+__device__ __forceinline__ void load_pixels(Group<R, U>& G, const void* __restrict__ points, int64_t pix_i,
+                                            int64_t pix_j, int m0) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (G.n[u] >= 0) {
+      load_px<DT, R>(points, pix_i + m0 + 32 * u, G.xi[u], G.yi[u], G.zi[u], G.ci[u]);
+      load_px<DT, R>(points, pix_j + G.n[u], G.xj[u], G.yj[u], G.zj[u], G.cj[u]);
+    }
+  }
+}
+
+template <typename R, int U>
+__device__ __forceinline__ void accumulate_group(const Group<R, U>& G, const R* T, const Consts<R>& k, Acc<R>& acc) {
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    if (G.n[u] >= 0) accumulate<R>(G.xi[u], G.yi[u], G.zi[u], G.ci[u], G.xj[u], G.yj[u], G.zj[u], G.cj[u], T, k, acc);
+}
+
+template <typename R, int DT, int BLOCK, int MINB, int UNROLL, bool PIPE>
 __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
     const void* __restrict__ points, const int32_t* __restrict__ midx, const Item* __restrict__ items,
     int num_items, const EdgeStatic* __restrict__ es, const double* __restrict__ T64,
@@ -273,24 +308,39 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
     }
     Acc<R> acc;
     acc.zero();
-    for (int base = item.begin + lane; base < item.end; base += 32 * UNROLL) {
-      int n[UNROLL];
-#pragma unroll
-      for (int u = 0; u < UNROLL; ++u) {
-        const int m = base + 32 * u;
-        n[u] = (m < item.end) ? __ldg(idx + m) : -1;
+    constexpr int STEP = 32 * UNROLL;
+    if constexpr (!PIPE) {
+      // plain loop: indices, then both pixels, then the arithmetic of this group
+      for (int g0 = item.begin; g0 < item.end; g0 += STEP) {
+        Group<R, UNROLL> G;
+        load_indices<R, UNROLL>(G.n, idx, g0 + lane, item.end);
+        load_pixels<DT, R, UNROLL>(G, points, pix_i, pix_j, g0 + lane);
+        accumulate_group<R, UNROLL>(G, T, k, acc);
       }
-      R xi[UNROLL], yi[UNROLL], zi[UNROLL], ci[UNROLL], xj[UNROLL], yj[UNROLL], zj[UNROLL], cj[UNROLL];
+    } else {
+      // software pipeline over groups: while group g is computed, the pixels of g+1 and
+      // the match indices of g+2 are in flight (two register groups, ping-pong)
+      Group<R, UNROLL> A, B;
+      int g0 = item.begin;
+      load_indices<R, UNROLL>(A.n, idx, g0 + lane, item.end);
+      load_pixels<DT, R, UNROLL>(A, points, pix_i, pix_j, g0 + lane);
+      load_indices<R, UNROLL>(B.n, idx, g0 + STEP + lane, item.end);
+      while (g0 < item.end) {
+        load_pixels<DT, R, UNROLL>(B, points, pix_i, pix_j, g0 + STEP + lane);
+        int nA[UNROLL];
+        load_indices<R, UNROLL>(nA, idx, g0 + 2 * STEP + lane, item.end);
+        accumulate_group<R, UNROLL>(A, T, k, acc);
 #pragma unroll
-      for (int u = 0; u < UNROLL; ++u) {
-        if (n[u] >= 0) {
-          load_px<DT, R>(points, pix_i + base + 32 * u, xi[u], yi[u], zi[u], ci[u]);
-          load_px<DT, R>(points, pix_j + n[u], xj[u], yj[u], zj[u], cj[u]);
-        }
-      }
+        for (int u = 0; u < UNROLL; ++u) A.n[u] = nA[u];
+        g0 += STEP;
+        if (g0 >= item.end) break;
+        load_pixels<DT, R, UNROLL>(A, points, pix_i, pix_j, g0 + STEP + lane);
+        int nB[UNROLL];
+        load_indices<R, UNROLL>(nB, idx, g0 + 2 * STEP + lane, item.end);
+        accumulate_group<R, UNROLL>(B, T, k, acc);
 #pragma unroll
-      for (int u = 0; u < UNROLL; ++u) {
-        if (n[u] >= 0) accumulate<R>(xi[u], yi[u], zi[u], ci[u], xj[u], yj[u], zj[u], cj[u], T, k, acc);
+        for (int u = 0; u < UNROLL; ++u) B.n[u] = nB[u];
+        g0 += STEP;
       }
     }
     // ---- warp reduction: compensated butterfly, lane l ends with accumulator l
@@ -310,17 +360,22 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
   }
 }
 
-// Launch configurations the autotuner chooses from: 256-thread CTAs with a register
-// budget for 2, 3 or 4 resident CTAs per SM (more warps to cover the gather latency
-// against a few spilled registers).  FP64 runs only the first.
+// Launch configurations the autotuner chooses from (256-thread CTAs):
+//   0  plain loop, 2 pixels per lane per group, natural register budget
+//   1  software-pipelined loop, 1 pixel per lane per group
+//   2  software-pipelined loop, 2 pixels per lane per group
+//   3  software-pipelined loop, 1 pixel per lane, register budget for 3 CTAs per SM
+// FP64 runs configurations 0 and 1 only.
 constexpr int kK1Block = 256;
+constexpr int kK1Cfgs = 4;
 
 template <typename R, int DT>
 const void* pick_cfg(int cfg) {
   switch (cfg) {
-    case 0: return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 2>);
-    case 1: return sizeof(R) == 4 ? reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 3, 2>) : nullptr;
-    case 2: return sizeof(R) == 4 ? reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 4, 2>) : nullptr;
+    case 0: return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 2, false>);
+    case 1: return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 1, true>);
+    case 2: return sizeof(R) == 4 ? reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 2, true>) : nullptr;
+    case 3: return sizeof(R) == 4 ? reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 3, 1, true>) : nullptr;
     default: return nullptr;
   }
 }
@@ -344,7 +399,7 @@ const void* pick_kernel(int mode, int dtype, int cfg) {
 
 }  // namespace
 
-int residual_reduce_num_cfgs(int mode) { return mode == 1 ? 3 : 1; }
+int residual_reduce_num_cfgs(int mode) { return mode == 1 ? kK1Cfgs : 2; }
 
 int residual_reduce_block() { return kK1Block; }
 

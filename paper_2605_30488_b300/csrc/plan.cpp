@@ -303,11 +303,8 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
 
   // ---- per graph: ordering, symbolic factorisation, levels
   p.col_begin.assign(1, 0);
-  p.col_slot.assign(1, 0);
-  p.lvl_begin.assign(1, 0);
-  p.lvl_off.assign(1, 0);
-  p.utask_off.assign(1, 0);
-  p.ttask_off.assign(1, 0);
+  p.slot_begin.assign(1, 0);
+  int lvl_base = 0;
   std::vector<std::vector<int32_t>> slot_lists;  // contributions per slot
   std::vector<std::vector<int32_t>> kf_lists(N);
   for (int g = 0; g < G; ++g) {
@@ -346,17 +343,21 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
     const std::vector<std::vector<int>>& rows = S.rows;
     const std::vector<int>& level = S.level;
     p.max_levels = std::max(p.max_levels, S.nlev);
-    // columns and slots (global numbering)
-    const int cbase = p.col_begin.back();
-    std::vector<int> slot_base(n);
+    // columns and slots: local numbering inside the graph, global = base + local
+    const int cbase = p.col_begin.back(), sbase = p.slot_begin.back();
+    std::vector<int> slot_base(n);  // local slot of each column's diagonal block
+    int nslot = 0;
     for (int k = 0; k < n; ++k) {
       p.col_kf.push_back(k0 + kf_of[order[k]]);
-      slot_base[k] = p.col_slot.back();
-      p.slot_row.push_back(cbase + k);  // diagonal
-      for (int r : rows[k]) p.slot_row.push_back(cbase + r);
-      p.col_slot.push_back(slot_base[k] + 1 + (int)rows[k].size());
+      slot_base[k] = nslot;
+      p.col_slot.push_back(sbase + nslot);
+      p.lcol_slot.push_back(nslot);
+      p.lslot_row.push_back(k);  // diagonal
+      for (int r : rows[k]) p.lslot_row.push_back(r);
+      nslot += 1 + (int)rows[k].size();
     }
-    auto slot_of = [&](int r, int c) {  // block (r, c), r >= c, of this graph
+    p.lcol_slot.push_back(nslot);
+    auto slot_of = [&](int r, int c) {  // local slot of block (r, c), r >= c
       if (r == c) return slot_base[c];
       const auto it = std::lower_bound(rows[c].begin(), rows[c].end(), r);
       return slot_base[c] + 1 + (int)(it - rows[c].begin());
@@ -370,16 +371,17 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
         p.slot_kf_c.push_back(kc);
       }
     }
-    // left-looking update triplets, grouped by destination block
+    // left-looking update triplets, grouped by destination block (local indices)
     std::vector<std::vector<int>> rowstruct(n);
     for (int j = 0; j < n; ++j)
       for (int r : rows[j]) rowstruct[r].push_back(j);
     std::vector<std::vector<int4>> tasks_of_level(S.nlev);
+    const int tri0 = (int)p.ltri.size();
     for (int k = 0; k < n; ++k) {
       std::vector<std::pair<int, int4>> ts;
       for (int j : rowstruct[k])
         for (int r : rows[j])
-          if (r >= k) ts.push_back({j, make_int4(slot_of(r, j), slot_of(k, j), slot_of(r, k), cbase + j)});
+          if (r >= k) ts.push_back({j, make_int4(slot_of(r, j), slot_of(k, j), slot_of(r, k), j)});
       std::stable_sort(ts.begin(), ts.end(), [](const auto& x, const auto& y) {
         return x.second.z != y.second.z ? x.second.z < y.second.z : x.first < y.first;
       });
@@ -388,9 +390,9 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
         size_t e = q;
         while (e < ts.size() && ts[e].second.z == ts[q].second.z) ++e;
         const int dst = ts[q].second.z;
-        const int t0 = (int)p.tri.size();
-        for (size_t x = q; x < e; ++x) p.tri.push_back(ts[x].second);
-        tasks_of_level[level[k]].push_back(make_int4(dst, t0, (int)p.tri.size(), dst == slot_base[k] ? cbase + k : -1));
+        const int t0 = (int)p.ltri.size() - tri0;
+        for (size_t x = q; x < e; ++x) p.ltri.push_back(ts[x].second);
+        tasks_of_level[level[k]].push_back(make_int4(dst, t0, (int)p.ltri.size() - tri0, dst == slot_base[k] ? k : -1));
         q = e;
       }
     }
@@ -398,44 +400,44 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
     std::vector<int> byl(n);
     std::iota(byl.begin(), byl.end(), 0);
     std::stable_sort(byl.begin(), byl.end(), [&](int x, int y) { return level[x] < level[y]; });
-    if (p.utask_off.empty()) p.utask_off.push_back(0);
-    if (p.ttask_off.empty()) p.ttask_off.push_back(0);
+    const int u0 = (int)p.lutask.size(), t0 = (int)p.lttask.size();
     int q = 0;
+    p.llvl.insert(p.llvl.end(), {0, 0, 0});
     for (int lv = 0; lv < S.nlev; ++lv) {
       for (; q < n && level[byl[q]] == lv; ++q) {
         const int k = byl[q];
-        p.sched.push_back(cbase + k);
-        for (size_t b = 0; b < rows[k].size(); ++b) p.ttask.push_back(make_int2(slot_base[k] + 1 + (int)b, cbase + k));
+        p.lsched.push_back(k);
+        for (size_t b = 0; b < rows[k].size(); ++b) p.lttask.push_back(make_int2(slot_base[k] + 1 + (int)b, k));
       }
-      p.lvl_off.push_back((int)p.sched.size());
       auto& tl = tasks_of_level[lv];
       std::stable_sort(tl.begin(), tl.end(), [](const int4& x, const int4& y) { return (x.z - x.y) > (y.z - y.y); });
-      p.utask.insert(p.utask.end(), tl.begin(), tl.end());
-      p.utask_off.push_back((int)p.utask.size());
-      p.ttask_off.push_back((int)p.ttask.size());
+      p.lutask.insert(p.lutask.end(), tl.begin(), tl.end());
+      p.llvl.insert(p.llvl.end(), {q, (int)p.lutask.size() - u0, (int)p.lttask.size() - t0});
     }
-    p.lvl_begin.push_back((int)p.lvl_off.size() - 1);
+    const int ntri = (int)p.ltri.size() - tri0, nu = (int)p.lutask.size() - u0, nt = (int)p.lttask.size() - t0;
+    p.meta.insert(p.meta.end(), {cbase, n, sbase, nslot, tri0, ntri, u0, nu, t0, nt, lvl_base, S.nlev});
+    lvl_base += S.nlev + 1;
     p.col_begin.push_back(cbase + n);
-    // assembly contributions
-    slot_lists.resize(p.col_slot.back());
+    p.slot_begin.push_back(sbase + nslot);
+    p.max_graph_smem = std::max(p.max_graph_smem, solver_smem_bytes(nslot, n, ntri, nu, nt, S.nlev));
+    // assembly contributions (global slots)
+    slot_lists.resize(p.slot_begin.back());
     for (int e = p.edge_offset[g]; e < p.edge_offset[g + 1]; ++e) {
       const int i = d->edge_i[e], j = d->edge_j[e];
       const int ui = node_of[i - k0], uj = node_of[j - k0];
       if (ui >= 0) {
-        slot_lists[slot_of(pos[ui], pos[ui])].push_back(2 * e);
+        slot_lists[sbase + slot_of(pos[ui], pos[ui])].push_back(2 * e);
         kf_lists[i].push_back(2 * e + 1);
       }
       if (uj >= 0) {
-        slot_lists[slot_of(pos[uj], pos[uj])].push_back(2 * e);
+        slot_lists[sbase + slot_of(pos[uj], pos[uj])].push_back(2 * e);
         kf_lists[j].push_back(2 * e);
       }
       if (ui >= 0 && uj >= 0) {
         const int r = std::max(pos[ui], pos[uj]), c = std::min(pos[ui], pos[uj]);
-        slot_lists[slot_of(r, c)].push_back(2 * e + 1);
+        slot_lists[sbase + slot_of(r, c)].push_back(2 * e + 1);
       }
     }
-    const size_t nslot = (size_t)(p.col_slot.back() - p.col_slot[cbase]);
-    p.max_graph_smem = std::max(p.max_graph_smem, sizeof(double) * (nslot * 49 + (size_t)n * kColScratch));
   }
   p.slot_contrib_off.assign(1, 0);
   for (auto& l : slot_lists) {
@@ -467,9 +469,9 @@ void plan_stats(const HostPlan& p, int64_t* s) {
   s[COMO3R_STAT_KEYFRAMES] = p.N;
   s[COMO3R_STAT_EDGES] = p.E;
   s[COMO3R_STAT_COLUMNS] = p.col_begin.empty() ? 0 : p.col_begin.back();
-  s[COMO3R_STAT_BLOCKS] = p.col_slot.empty() ? 0 : p.col_slot.back();
+  s[COMO3R_STAT_BLOCKS] = p.slot_begin.empty() ? 0 : p.slot_begin.back();
   s[COMO3R_STAT_FILL] = p.fill_blocks;
-  s[COMO3R_STAT_UPDATES] = (int64_t)p.tri.size();
+  s[COMO3R_STAT_UPDATES] = (int64_t)p.ltri.size();
   s[COMO3R_STAT_LEVELS] = p.max_levels;
   int64_t nd = 0;
   for (int8_t k : p.order_kind) nd += k;

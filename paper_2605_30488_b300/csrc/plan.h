@@ -20,9 +20,13 @@ struct HostPlan {
   std::vector<EdgeStatic> es;     // [E]
   std::vector<uint8_t> frozen;    // [N] anchors
   // solver plan (see SolverPlan)
-  std::vector<int32_t> col_begin, col_kf, col_slot, slot_row, sched, lvl_begin, lvl_off, utask_off, ttask_off;
-  std::vector<int4> tri, utask;
-  std::vector<int2> ttask;
+  // global numbering (assembly, export): columns and slots of graph g start at
+  // col_begin[g] / slot_begin[g]; col_slot (global) gives each column's diagonal slot
+  std::vector<int32_t> col_begin, slot_begin, col_kf, col_slot;
+  // solver plan in per-graph local indices (see SolverPlan)
+  std::vector<int32_t> meta, lcol_slot, lslot_row, lsched, llvl;
+  std::vector<int4> ltri, lutask;
+  std::vector<int2> lttask;
   std::vector<int8_t> order_kind;  // per graph: 0 minimum degree, 1 nested dissection
   std::vector<int32_t> slot_kf_r, slot_kf_c;
   // assembly (entries edge * 2 + negate, in edge order)
