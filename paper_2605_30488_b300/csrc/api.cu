@@ -145,8 +145,7 @@ int enqueue_linearize(como3r_graph* g, cudaStream_t s, double* cost_hist, const 
 
 int enqueue_solve(como3r_graph* g, cudaStream_t s, int* iter) {
   const HostPlan& p = g->plan;
-  CK(launch_factor_solve(p.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_colscratch, g->d_gvec,
-                         g->d_tau, g->lambda, g->eps0, g->max_attempts, g->d_ginfo, g->d_warn, s),
+  CK(launch_factor_solve(p.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_colscratch, g->d_gvec, g->d_tau, g->lambda, g->eps0, g->max_attempts, g->d_ginfo, g->d_warn, s),
      "factor_solve");
   CK(launch_retract(g->d_tau, g->d_poses, g->d_frozen, p.N, iter, s), "retract");
   return COMO3R_OK;
@@ -240,7 +239,8 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
       (rc = upload(g, &g->d_kf_contrib_off, p.kf_contrib_off)) || (rc = upload(g, &g->d_kf_contrib, p.kf_contrib)) ||
       (rc = upload(g, &g->d_edge_offset, p.edge_offset)) || (rc = dalloc(g, &g->d_A, (size_t)nslots * 49)) ||
       (rc = dalloc(g, &g->d_L, (size_t)nslots * 49)) ||
-      (rc = dalloc(g, &g->d_colscratch, (size_t)ncols * kColScratch)) || (rc = dalloc(g, &g->d_gvec, (size_t)N * 7)) ||
+      (rc = dalloc(g, &g->d_colscratch, (size_t)ncols * kColScratch)) ||
+ (rc = dalloc(g, &g->d_gvec, (size_t)N * 7)) ||
       (rc = dalloc(g, &g->d_tau, (size_t)N * 7)) || (rc = upload(g, &g->d_frozen, p.frozen)) ||
       (rc = dalloc(g, &g->d_ginfo, G)) || (rc = dalloc(g, &g->d_iter, 1)) || (rc = dalloc(g, &g->d_warn, 1)) ||
       (rc = dalloc(g, &g->d_poses, (size_t)N * 8)) || (rc = dalloc(g, &g->d_bad, 1)))

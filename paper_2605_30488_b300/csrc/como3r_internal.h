@@ -45,12 +45,13 @@ struct GraphInfoDev {          // per graph, written on the device
 // tasks from 0), so a CTA can stage its graph's plan in shared memory as is; meta[g]
 // locates the graph's part of each concatenated array.  Slot s is one stored 7x7 block
 // (row-major) of the factor.  Each elimination-tree level has three task lists, executed
-// with a CTA barrier between them:
-//   U: one task per destination block of the level's columns, (dst, t0, t1, col):
-//      L[dst] -= sum_{t0 <= t < t1} L[tri[t].x] L[tri[t].y]^T; col >= 0 marks a diagonal
-//      destination, whose task also forms the forward right-hand side of column col;
+// in this order with a CTA barrier after each:
 //   D: the level's columns (diagonal factorisation + forward substitution);
-//   T: (slot, col): the off-diagonal blocks of the level's columns, solved against L_cc.
+//   T: (slot, col): the off-diagonal blocks of the level's columns, solved against L_cc;
+//   U: right-looking updates from the level's columns to all their ancestors, one task
+//      per destination block, (dst, t0, t1, col): L[dst] -= sum_{t0 <= t < t1}
+//      L[tri[t].x] L[tri[t].y]^T; col >= 0 marks a diagonal destination, whose task also
+//      updates the forward right-hand side of column col with L[tri[t].x] y_{tri[t].w}.
 enum GraphMeta {
   kMetaColBase, kMetaNCol, kMetaSlotBase, kMetaNSlot, kMetaTriBase, kMetaNTri,
   kMetaUBase, kMetaNU, kMetaTBase, kMetaNT, kMetaLvlBase, kMetaNLvl, kMetaCount

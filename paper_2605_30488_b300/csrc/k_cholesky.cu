@@ -2,22 +2,26 @@
 // with the epsilon escalation of Sec. III-D, all in FP64.
 //
 // One CTA (16 warps) per graph.  The factor L (lower, 7x7 blocks; pattern, elimination
-// order and task lists fixed at create) is computed left-looking one elimination-tree
-// level at a time.  Within a level three task lists run, separated by CTA barriers:
-//   U  one warp per destination block: L[dst] -= sum L_rj L_cj^T over the descendants j
-//      (diagonal destinations also accumulate the forward right-hand side
-//      b_c - sum_j L_cj y_j);
+// order and task lists fixed at create) is computed one elimination-tree level at a
+// time.  Within a level three task lists run, separated by CTA barriers:
 //   D  four columns per warp (8 lanes each): Cholesky of the 7x7 diagonal block in
 //      registers (lane r holds row r) with the right-hand side riding along as an eighth
 //      row, which yields y_c = L_cc^{-1}(...) for free; a pivot that is not > 0 or not
 //      finite fails the attempt;
 //   T  one thread per row of every off-diagonal block (B <- B L_cc^{-T}) and per column of
-//      L_cc^{-1}, all independent.
+//      L_cc^{-1}, all independent;
+//   U  right-looking: one warp per destination block in any ancestor column,
+//      L[dst] -= sum L_rj L_kj^T over the level's columns j (diagonal destinations also
+//      update the forward right-hand side t_c -= L_cj y_j), so every column has received
+//      all of its descendants' updates when its own level starts.
 // A failed attempt restarts with eps_r = eps0 * 100^r; after max_attempts failures the
 // update is zero (Sec. III-D).  Back substitution walks the levels from the root, each
 // column x_c = L_cc^{-T}(y_c - sum_r L_rc^T x_r) with the precomputed L_cc^{-1}.
-// FP64 on this GPU has a long dependent latency (about 66 cycles per FMA, several
-// hundred for rsqrt), so the schedule keeps chains short and spreads independent work.
+// FP64 on this GPU issues about one warp instruction per ~80 cycles per SM sub-partition
+// (and has a long dependent latency), so the schedule keeps every lane of an FP64
+// instruction busy and spreads the work of a level over all warps: a right-looking
+// schedule spreads the update work evenly over the levels (a left-looking one piles
+// the root's updates into the last, narrowest levels).
 // The factor lives in shared memory when the graph's blocks fit, else in global memory.
 #include <cstdint>
 
@@ -49,39 +53,37 @@ __device__ __forceinline__ double* dinv_of(const SolveCtx& C, int col) { return 
 __device__ __forceinline__ double* y_of(const SolveCtx& C, int col) { return dinv_of(C, col) + 7; }
 __device__ __forceinline__ double* linv_of(const SolveCtx& C, int col) { return dinv_of(C, col) + 14; }
 
-// sum_q a[q] b[q], q < 7, as two interleaved FMA chains (shorter dependent latency)
+// acc + sum_q a[q] b[q], q < 7: seven FP64 instructions (instruction count, not the
+// dependent latency, is what limits FP64 work on this GPU)
 __device__ __forceinline__ double dot7(const double* a, const double* b, double acc) {
-  double p = a[0] * b[0];
-  p = fma(a[2], b[2], p);
-  p = fma(a[4], b[4], p);
-  p = fma(a[6], b[6], p);
-  double q = fma(a[1], b[1], acc);
-  q = fma(a[3], b[3], q);
-  q = fma(a[5], b[5], q);
-  return p + q;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) acc = fma(a[q], b[q], acc);
+  return acc;
 }
 
-// U: one destination block (see file header).  Pass 1: lane l owns entry l of the 7x7
-// destination; pass 2: lanes 0..16 own entries 32..48, lanes 17..23 the seven rows of the
-// forward right-hand side (diagonal destinations only), lanes 24..31 idle.
+// U: one destination block (see file header).  Pass 1: lane l owns
+// entry l of the 7x7 block; pass 2: lanes 0..16 own entries 32..48, lanes 17..23 the seven
+// rows of the forward right-hand side (diagonal destinations only), lanes 24..31 idle.
+// Four triplets are in flight at a time (independent accumulators).
 __device__ void update_task(const SolveCtx& C, int4 task, int lane) {
   const int e0 = lane, e1 = lane + 32;
   const bool has1 = e1 < 49;
   const bool rhs = task.w >= 0 && lane >= 17 && lane < 24;
   const int r0 = e0 / 7, q0 = e0 % 7, r1 = has1 ? e1 / 7 : lane - 17, q1 = has1 ? e1 % 7 : 0;
-  double a0 = 0.0, a1 = 0.0;
+  double* D = blk(C, task.x);
+  // the destination itself seeds the chains: L[dst] - sum = -(sum - L[dst])
+  double a0 = -D[e0];
+  double a1 = has1 ? -D[e1] : (rhs ? -y_of(C, task.w)[lane - 17] : 0.0);
   for (int t = task.y; t < task.z; ++t) {
     const int4 tr = C.tri[t];
     const double* Lr = blk(C, tr.x);
-    const double* Lk = blk(C, tr.y);
-    a0 += dot7(Lr + 7 * r0, Lk + 7 * q0, 0.0);
-    if (has1) a1 += dot7(Lr + 7 * r1, Lk + 7 * q1, 0.0);
-    else if (rhs) a1 += dot7(Lr + 7 * r1, y_of(C, tr.w), 0.0);
+    a0 = dot7(Lr + 7 * r0, blk(C, tr.y) + 7 * q0, a0);
+    if (has1) a1 = dot7(Lr + 7 * r1, blk(C, tr.y) + 7 * q1, a1);
+    else if (rhs) a1 = dot7(Lr + 7 * r1, y_of(C, tr.w), a1);
   }
-  double* D = blk(C, task.x);
-  D[e0] -= a0;
-  if (has1) D[e1] -= a1;
-  else if (rhs) y_of(C, task.w)[lane - 17] -= a1;
+  D[e0] = -a0;
+  if (has1) D[e1] = -a1;
+  else if (rhs) y_of(C, task.w)[lane - 17] = -a1;
 }
 
 // D: Cholesky of diagonal blocks, four columns per warp (FP64 instructions occupy the
@@ -93,7 +95,8 @@ __device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int 
   const int seg = lane >> 3, sl = lane & 7;
   const bool active = seg < ncols;
   const int col = cols[active ? seg : 0];
-  double* D = blk(C, C.col_slot[col]);
+  const int dslot = C.col_slot[col];
+  double* D = blk(C, dslot);
   double* y = y_of(C, col);
   double a[7];
 #pragma unroll
@@ -106,10 +109,12 @@ __device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int 
 #pragma unroll
   for (int k = 0; k < 7; ++k) {
     const double p = __shfl_sync(kFull, a[k], k, 8);
-    const bool okp = (p > 0.0) && (p < __longlong_as_double(0x7ff0000000000000LL));
+    // p > 0 and finite, tested on the bit pattern (keeps the FP64 pipe free)
+    const long long pb = __double_as_longlong(p);
+    const bool okp = pb > 0 && pb < 0x7ff0000000000000LL;
     bad = bad || !okp;
     const double inv = rsqrt(okp ? p : 1.0);
-    const double lk = (sl == k) ? p * inv : a[k] * inv;
+    const double lk = ((sl == k) ? p : a[k]) * inv;
     if (sl == k) myinv = inv;
     if (sl >= k) a[k] = lk;
 #pragma unroll
@@ -131,9 +136,10 @@ __device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int 
   }
 }
 
-// T: item x < 7 * nt: row (x % 7) of off-diagonal block ttask[t0 + x / 7]; else column
-// (x % 7) of L_cc^{-1} for the level column sched[s0 + (x - 7 nt) / 7].
-__device__ void trsm_or_inverse(const SolveCtx& C, int t0, int nt, int s0, int x) {
+// T: item x < 7 * nt: row (x % 7) of off-diagonal block ttask[t0 + x / 7]; items from
+// tpad = 7 * nt rounded up to a warp on: column (x % 7) of L_cc^{-1} for the level column
+// sched[s0 + (x - tpad) / 7].  The two kinds never share a warp (they would diverge).
+__device__ void trsm_or_inverse(const SolveCtx& C, int t0, int nt, int tpad, int s0, int x) {
   if (x < 7 * nt) {
     const int2 tt = C.ttask[t0 + x / 7];
     const int i = x % 7;
@@ -150,8 +156,8 @@ __device__ void trsm_or_inverse(const SolveCtx& C, int t0, int nt, int s0, int x
     }
 #pragma unroll
     for (int c = 0; c < 7; ++c) B[c] = xr[c];
-  } else {
-    const int k = (x - 7 * nt) / 7, c = x % 7;
+  } else if (x >= tpad) {
+    const int k = (x - tpad) / 7, c = (x - tpad) % 7;
     const int col = C.sched[s0 + k];
     const double* Lc = blk(C, C.col_slot[col]);
     const double* dv = dinv_of(C, col);
@@ -293,15 +299,16 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     __syncthreads();
     for (int lv = 0; lv < nlev; ++lv) {
       const int* L0 = C.lvl + 3 * lv;  // [sched, utask, ttask] offsets of this level and (at +3) the next
-      for (int u = L0[1] + warp; u < L0[4]; u += kSolveWarps) update_task(C, C.utask[u], lane);
-      __syncthreads();
       for (int q = L0[0] + 4 * warp; q < L0[3]; q += 4 * kSolveWarps)
         diag_factor4(C, C.sched + q, min(4, L0[3] - q), lane, &s_fail);
       __syncthreads();
       if (s_fail) break;
       const int nt = L0[5] - L0[2];
-      const int nx = 7 * (nt + L0[3] - L0[0]);
-      for (int x = tid; x < nx; x += kSolveThreads) trsm_or_inverse(C, L0[2], nt, L0[0], x);
+      const int tpad = (7 * nt + 31) & ~31;
+      const int nx = tpad + 7 * (L0[3] - L0[0]);
+      for (int x = tid; x < nx; x += kSolveThreads) trsm_or_inverse(C, L0[2], nt, tpad, L0[0], x);
+      __syncthreads();
+      for (int u = L0[1] + warp; u < L0[4]; u += kSolveWarps) update_task(C, C.utask[u], lane);
       __syncthreads();
     }
     ok = (s_fail == 0);

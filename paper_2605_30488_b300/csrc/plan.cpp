@@ -371,17 +371,22 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
         p.slot_kf_c.push_back(kc);
       }
     }
-    // left-looking update triplets, grouped by destination block (local indices)
-    std::vector<std::vector<int>> rowstruct(n);
+    // right-looking update triplets: after the columns of a level are factored, their
+    // contributions L_rj L_kj^T go to every ancestor block (r, k); the triplets of one
+    // source level are grouped by destination block (local indices)
+    std::vector<std::vector<std::pair<int, int4>>> trip_of_level(S.nlev);
     for (int j = 0; j < n; ++j)
-      for (int r : rows[j]) rowstruct[r].push_back(j);
-    std::vector<std::vector<int4>> tasks_of_level(S.nlev);
+      for (size_t a = 0; a < rows[j].size(); ++a)
+        for (size_t b = 0; b <= a; ++b) {
+          const int r = rows[j][a], k = rows[j][b];
+          trip_of_level[level[j]].push_back({j, make_int4(slot_of(r, j), slot_of(k, j), slot_of(r, k), j)});
+        }
     const int tri0 = (int)p.ltri.size();
-    for (int k = 0; k < n; ++k) {
-      std::vector<std::pair<int, int4>> ts;
-      for (int j : rowstruct[k])
-        for (int r : rows[j])
-          if (r >= k) ts.push_back({j, make_int4(slot_of(r, j), slot_of(k, j), slot_of(r, k), j)});
+    std::vector<int> diag_col(nslot, -1);
+    for (int k = 0; k < n; ++k) diag_col[slot_base[k]] = k;
+    std::vector<std::vector<int4>> tasks_of_level(S.nlev);
+    for (int lv = 0; lv < S.nlev; ++lv) {
+      auto& ts = trip_of_level[lv];
       std::stable_sort(ts.begin(), ts.end(), [](const auto& x, const auto& y) {
         return x.second.z != y.second.z ? x.second.z < y.second.z : x.first < y.first;
       });
@@ -392,11 +397,12 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
         const int dst = ts[q].second.z;
         const int t0 = (int)p.ltri.size() - tri0;
         for (size_t x = q; x < e; ++x) p.ltri.push_back(ts[x].second);
-        tasks_of_level[level[k]].push_back(make_int4(dst, t0, (int)p.ltri.size() - tri0, dst == slot_base[k] ? k : -1));
+        // a diagonal destination also receives the forward right-hand side of its column
+        tasks_of_level[lv].push_back(make_int4(dst, t0, (int)p.ltri.size() - tri0, diag_col[dst]));
         q = e;
       }
     }
-    // level schedule: columns, update tasks (longest first), off-diagonal solve tasks
+    // level schedule: columns, off-diagonal solve tasks, update tasks (longest first)
     std::vector<int> byl(n);
     std::iota(byl.begin(), byl.end(), 0);
     std::stable_sort(byl.begin(), byl.end(), [&](int x, int y) { return level[x] < level[y]; });
