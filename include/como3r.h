@@ -112,7 +112,8 @@ typedef struct {
 /* Validate the description, plan the solve (fill-reducing ordering, symbolic block
  * factorisation, work lists), allocate workspaces, check every match index on the
  * device (-1 <= n < P_j) and autotune the residual kernel's work-item size and launch
- * configuration on this graph's data (a few milliseconds of timed trial launches).
+ * configuration on this graph's data (a few milliseconds of timed trial launches; the
+ * environment variable COMO3R_K1_CFG=<n> restricts the search to configuration n).
  * Synchronises the stream.  On error *out is NULL.
  * Errors: INVALID_ARG (bad sizes / ids / indices / parameters), OOM, CUDA. */
 int como3r_graph_create(const como3r_graph_desc* desc, void* cuda_stream, como3r_graph_t* out);

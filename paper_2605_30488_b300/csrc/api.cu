@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -53,6 +54,7 @@ struct como3r_graph {
   int max_attempts = 6;
   int k1_cfg = 0, k1_chunk = kDefaultChunk, k1_grid = 0, num_items = 0, max_items = 0;
   float k1_tuned_ms = 0.f;
+  bool idx_rows_aligned = false;
   std::vector<void*> allocs;
   const void* points = nullptr;
   const int32_t* midx = nullptr;
@@ -225,6 +227,10 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   std::vector<int32_t> item_off;
   build_items(p, kChunks[0], items, item_off);
   g->max_items = (int)items.size();
+  // the shared-memory-staged residual kernel copies match indices in 16-byte pieces
+  g->idx_rows_aligned = reinterpret_cast<uintptr_t>(g->midx) % 16 == 0;
+  for (int k = 0; k < p.N; ++k)
+    g->idx_rows_aligned = g->idx_rows_aligned && (p.npix[k] % 4 == 0) && p.npix[k] <= (1 << 22);
   const int E = p.E, N = p.N, G = p.G;
   const int nslots = p.slot_begin.back(), ncols = p.col_begin.back();
   if ((rc = upload(g, &g->d_es, p.es)) || (rc = upload(g, &g->d_items, items)) ||
@@ -259,6 +265,7 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   CK(cudaMallocHost(&g->h_warn, sizeof(int)), "cudaMallocHost");
   CK(cudaMemsetAsync(g->d_tau, 0, sizeof(double) * 7 * (size_t)N, g->stream), "memset");
   CK(cudaMemsetAsync(g->d_ginfo, 0, sizeof(GraphInfoDev) * G, g->stream), "memset");
+  CK(residual_reduce_prepare(), "residual kernel smem attribute");
   // shared-memory factor when every graph fits
   const size_t smax = factor_solve_max_smem();
   g->smem_solve = p.max_graph_smem <= smax;
@@ -293,17 +300,26 @@ int autotune_k1(como3r_graph* g) {
   CK(cudaEventCreate(&e1), "event");
   float best = 1e30f;
   int best_chunk = kChunks[0], best_cfg = 0;
-  const int nchunks = p.mode == COMO3R_MIXED ? (int)(sizeof(kChunks) / sizeof(kChunks[0])) : 1;
+  // COMO3R_K1_CFG=<n> restricts the search to one launch configuration (tests, studies)
+  const char* force = getenv("COMO3R_K1_CFG");
+  const int forced = force ? atoi(force) : -1;
+  // FP64 launches are long (the FP64 pipe bounds them): try two chunk sizes only
+  const int nchunks = p.mode == COMO3R_MIXED ? (int)(sizeof(kChunks) / sizeof(kChunks[0])) : 2;
   std::vector<Item> items;
   std::vector<int32_t> item_off;
   int rc = COMO3R_OK;
   for (int ci = 0; ci < nchunks && !rc; ++ci) {
-    const int chunk = p.mode == COMO3R_MIXED ? kChunks[ci] : kDefaultChunk;
+    const int chunk = kChunks[ci];
     build_items(p, chunk, items, item_off);
     CK(cudaMemcpyAsync(g->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, g->stream),
        "tune items");
     for (int cfg = 0; cfg < residual_reduce_num_cfgs(p.mode); ++cfg) {
+      const int need = residual_reduce_cfg_chunk(cfg);
+      if (need && (chunk != need || !g->idx_rows_aligned)) continue;
+      if (forced >= 0 && cfg != forced) continue;
+      if (p.mode == COMO3R_PLAIN_FP64 && forced < 0 && cfg != 1 && cfg != 4) continue;
       const int occ = residual_reduce_max_blocks_per_sm(p.mode, p.dtype, cfg);
+      if (occ <= 0) continue;
       const int warps_per_cta = residual_reduce_block() / 32;
       const int grid = std::max(1, std::min(g->sms * std::max(occ, 1), ((int)items.size() + warps_per_cta - 1) / warps_per_cta));
       float tot = 0.f;

@@ -86,6 +86,8 @@ cudaError_t launch_residual_reduce(int mode, int dtype, int cfg, int grid, const
                                    RobustParams rp, void* partials, cudaStream_t s);
 int residual_reduce_max_blocks_per_sm(int mode, int dtype, int cfg);
 int residual_reduce_num_cfgs(int mode);
+int residual_reduce_cfg_chunk(int cfg);      // required pixels per item, 0 = any
+cudaError_t residual_reduce_prepare();       // once, before any capture
 int residual_reduce_block();
 cudaError_t launch_edge_reduce(int mode, const void* partials, const int32_t* item_off, int E, const double* Ad,
                                double* edge_M, double* edge_b, double* edge_cost, double* edge_skip,

@@ -40,16 +40,26 @@ struct Consts {
   R isr, isd, ivr, ivd, kappa, half_kappa;
 };
 
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+// FP32: hardware approximations with denormals flushed (inputs here are far from the
+// denormal range; relative error ~2^-22, well inside the mixed form's 1e-5 tolerance)
+__device__ __forceinline__ float rsq(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 template <typename R> __device__ __forceinline__ R kInfinity();
 template <> __device__ __forceinline__ float kInfinity<float>() { return __int_as_float(0x7f800000); }
 template <> __device__ __forceinline__ double kInfinity<double>() { return __longlong_as_double(0x7ff0000000000000LL); }
 
 // Square root of a non-negative value (0 -> 0); FP32 through the reciprocal square root.
-__device__ __forceinline__ float nn_sqrt(float v) { return v > 0.f ? v * rsqrtf(v) : 0.f; }
+__device__ __forceinline__ float nn_sqrt(float v) { return v > 0.f ? v * rsq(v) : 0.f; }
 __device__ __forceinline__ double nn_sqrt(double v) { return sqrt(v); }
 
 // ---- pixel loads: (x, y, z, c) in the storage type, widened to R
@@ -73,14 +83,17 @@ __device__ __forceinline__ void load_px(const void* __restrict__ base, int64_t p
 template <typename R>
 struct Acc {
   R v[kAcc];  // [0..24] H_rel unique entries, [25..31] g_rel
-  R E;
+  R Ew;       // sum_c w_c r_c^2
+  R Em;       // sum_c min(|r_c|, kappa)^2; the cost is Ew - Em / 2
   int skipped;
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) v[k] = R(0);
-    E = R(0);
+    Ew = R(0);
+    Em = R(0);
     skipped = 0;
   }
+  __device__ __forceinline__ R cost() const { return fma(R(-0.5), Em, Ew); }
 };
 
 // One match: residual, robust weights, Jacobian rows, accumulation (see file header).
@@ -93,8 +106,10 @@ __device__ __forceinline__ void accumulate(R xi, R yi, R zi, R ci, R xj, R yj, R
   const R d2 = fma(x0, x0, fma(x1, x1, x2 * x2));
   const R di2 = fma(xi, xi, fma(yi, yi, zi * zi));
   const R cc = ci * cj;
+  // skip degenerate or non-finite matches: both squared ranges in (1e-24, inf), c_i c_j in
+  // [0, inf); NaN fails every comparison
   const R th2 = R(1e-24), inf = kInfinity<R>();
-  const bool ok = (d2 > th2) & (d2 < inf) & (di2 > th2) & (di2 < inf) & (cc >= R(0)) & (cc < inf);
+  const bool ok = (fmin(d2, di2) > th2) & (fmax(fmax(d2, di2), cc) < inf) & (cc >= R(0));
   if (!ok) {
     ++acc.skipped;
     return;
@@ -107,23 +122,23 @@ __device__ __forceinline__ void accumulate(R xi, R yi, R zi, R ci, R xj, R yj, R
   const R sq = nn_sqrt(q);
   const R sr = sq * k.isr, sd = sq * k.isd;
   const R r0 = sr * e0, r1 = sr * e1, r2 = sr * e2, r3 = sd * e3;
+  // Huber: w = min(1, kappa / |r|) (kappa / 0 = inf gives 1); with m = min(|r|, kappa),
+  // rho(r) = w r^2 - m^2 / 2 on both branches (r^2 / 2 inside, kappa |r| - kappa^2 / 2 outside)
   const R a0 = fabs(r0), a1 = fabs(r1), a2 = fabs(r2), a3 = fabs(r3);
-  const bool i0 = a0 <= k.kappa, i1 = a1 <= k.kappa, i2 = a2 <= k.kappa, i3 = a3 <= k.kappa;
-  const R w0 = i0 ? R(1) : qdiv(k.kappa, a0);
-  const R w1 = i1 ? R(1) : qdiv(k.kappa, a1);
-  const R w2 = i2 ? R(1) : qdiv(k.kappa, a2);
-  const R w3 = i3 ? R(1) : qdiv(k.kappa, a3);
-  const R rho0 = i0 ? R(0.5) * r0 * r0 : k.kappa * (a0 - k.half_kappa);
-  const R rho1 = i1 ? R(0.5) * r1 * r1 : k.kappa * (a1 - k.half_kappa);
-  const R rho2 = i2 ? R(0.5) * r2 * r2 : k.kappa * (a2 - k.half_kappa);
-  const R rho3 = i3 ? R(0.5) * r3 * r3 : k.kappa * (a3 - k.half_kappa);
-  acc.E += (rho0 + rho1) + (rho2 + rho3);
+  const R w0 = fmin(R(1), k.kappa * rcp(a0));
+  const R w1 = fmin(R(1), k.kappa * rcp(a1));
+  const R w2 = fmin(R(1), k.kappa * rcp(a2));
+  const R w3 = fmin(R(1), k.kappa * rcp(a3));
+  const R m0 = fmin(a0, k.kappa), m1 = fmin(a1, k.kappa), m2 = fmin(a2, k.kappa), m3 = fmin(a3, k.kappa);
+  acc.Ew = fma(w0 * r0, r0, fma(w1 * r1, r1, fma(w2 * r2, r2, fma(w3 * r3, r3, acc.Ew))));
+  acc.Em = fma(m0, m0, fma(m1, m1, fma(m2, m2, fma(m3, m3, acc.Em))));
   const R qr = q * k.ivr;
   const R u0 = w0 * qr, u1 = w1 * qr, u2 = w2 * qr, u3 = w3 * q * k.ivd;  // W_c
   const R f0 = u0 * e0, f1 = u1 * e1, f2 = u2 * e2, f3 = u3 * e3;        // W_c e_c
   // P = (I - xh xh^T) / d, symmetric
-  const R p00 = fma(-a, a, R(1)) * rd, p11 = fma(-b, b, R(1)) * rd, p22 = fma(-c, c, R(1)) * rd;
-  const R p01 = -a * b * rd, p02 = -a * c * rd, p12 = -b * c * rd;
+  const R ard = a * rd, brd = b * rd, crd = c * rd;
+  const R p00 = fma(-ard, a, rd), p11 = fma(-brd, b, rd), p22 = fma(-crd, c, rd);
+  const R p01 = -ard * b, p02 = -ard * c, p12 = -brd * c;
   // weighted ray rows  wk_l = u_k P_kl
   const R w00 = u0 * p00, w01 = u0 * p01, w02 = u0 * p02;
   const R w10 = u1 * p01, w11 = u1 * p11, w12 = u1 * p12;
@@ -282,12 +297,38 @@ __device__ __forceinline__ void accumulate_group(const Group<R, U>& G, const R* 
     if (G.n[u] >= 0) accumulate<R>(G.xi[u], G.yi[u], G.zi[u], G.ci[u], G.xj[u], G.yj[u], G.zj[u], G.cj[u], T, k, acc);
 }
 
+// Writes the warp's record for item `it`: the reduced accumulators when `flush` (last
+// item of a run of items of one edge owned by this warp), zeros otherwise (the per-edge
+// reduction adds all records of an edge, so folding items into one record is exact).
+template <typename R>
+__device__ __forceinline__ void write_record(Acc<R>& acc, void* partials, int it, bool flush, int lane) {
+  using Slot = typename std::conditional<sizeof(R) == 4, float2, double>::type;
+  Slot* rec = reinterpret_cast<Slot*>(partials) + (int64_t)it * kPartial;
+  if (!flush) {
+    store_slot(rec, lane, R(0), R(0));
+    if (lane < kPartial - kAcc) store_slot(rec, kAcc + lane, R(0), R(0));
+    return;
+  }
+  R comp[kAcc];
+  warp_transpose_reduce(acc.v, comp, lane);
+  R Ec = R(0);
+  const R Ev = warp_sum_pair(acc.cost(), Ec);
+  const int sk = __reduce_add_sync(0xffffffffu, acc.skipped);
+  store_slot(rec, lane, acc.v[0], comp[0]);
+  if (lane == 0) {
+    store_slot(rec, kAcc, Ev, Ec);
+    store_slot(rec, kAcc + 1, (R)sk, R(0));
+    store_slot(rec, kAcc + 2, R(0), R(0));
+    store_slot(rec, kAcc + 3, R(0), R(0));
+  }
+  acc.zero();
+}
+
 template <typename R, int DT, int BLOCK, int MINB, int UNROLL, bool PIPE>
 __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
     const void* __restrict__ points, const int32_t* __restrict__ midx, const Item* __restrict__ items,
     int num_items, const EdgeStatic* __restrict__ es, const double* __restrict__ T64,
     const float* __restrict__ T32, RobustParams rp, void* __restrict__ partials) {
-  using Slot = typename std::conditional<sizeof(R) == 4, float2, double>::type;
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * BLOCK + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * BLOCK) >> 5;
@@ -296,7 +337,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
   k.ivr = (R)rp.inv_var_ray; k.ivd = (R)rp.inv_var_dist;
   k.kappa = (R)rp.kappa; k.half_kappa = (R)(0.5 * rp.kappa);
 
-  for (int it = gwarp; it < num_items; it += nwarps) {
+  // each warp owns a contiguous run of items (mostly of one edge) and reduces once per edge
+  const int per = (num_items + nwarps - 1) / nwarps;
+  const int it0 = gwarp * per, it1 = min(it0 + per, num_items);
+  Acc<R> acc;
+  acc.zero();
+  for (int it = it0; it < it1; ++it) {
     const Item item = items[it];
     const int64_t pix_i = es[item.edge].pix_i, pix_j = es[item.edge].pix_j;
     const int32_t* __restrict__ idx = midx + es[item.edge].idx_off;
@@ -306,8 +352,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
       if constexpr (sizeof(R) == 4) T[q] = T32[16 * item.edge + q];
       else T[q] = T64[12 * item.edge + q];
     }
-    Acc<R> acc;
-    acc.zero();
     constexpr int STEP = 32 * UNROLL;
     if constexpr (!PIPE) {
       // plain loop: indices, then both pixels, then the arithmetic of this group
@@ -343,41 +387,200 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
         g0 += STEP;
       }
     }
-    // ---- warp reduction: compensated butterfly, lane l ends with accumulator l
-    R comp[kAcc];
-    warp_transpose_reduce(acc.v, comp, lane);
-    R Ec = R(0);
-    const R Ev = warp_sum_pair(acc.E, Ec);
-    const int sk = __reduce_add_sync(0xffffffffu, acc.skipped);
-    Slot* rec = reinterpret_cast<Slot*>(partials) + (int64_t)it * kPartial;
-    store_slot(rec, lane, acc.v[0], comp[0]);
-    if (lane == 0) {
-      store_slot(rec, kAcc, Ev, Ec);
-      store_slot(rec, kAcc + 1, (R)sk, R(0));
-      store_slot(rec, kAcc + 2, R(0), R(0));
-      store_slot(rec, kAcc + 3, R(0), R(0));
-    }
+    // ---- warp reduction (compensated butterfly) at the end of each edge run
+    write_record(acc, partials, it, it + 1 == it1 || items[it + 1].edge != item.edge, lane);
   }
 }
+
+// ---- shared-memory-staged variant (cp.async) -----------------------------------------
+// Each warp owns a slice of shared memory: two buffers of match indices (the current item
+// and the prefetched next one, kAsyncChunk entries each) and a ring of kRing pixel
+// groups (32 lanes x streamed + gathered pixel).  Once an item's indices have landed the
+// warp compacts its valid matches in place (ballot + prefix count; entry = n << 10 | m),
+// so every lane of the arithmetic works on a real match although a third of the
+// streamed pixels typically have none.  The pixels of the compacted matches then flow
+// through the ring: lane l only ever reads ring slots it filled itself, so the ring needs
+// no warp synchronisation, and kRing groups of both pixel loads stay in flight per warp
+// without costing registers.
+constexpr int kAsyncChunk = 1024;
+constexpr int kRing = 4;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int DT> struct PixBytes;
+template <> struct PixBytes<0> { static constexpr int v = 8; };
+template <> struct PixBytes<1> { static constexpr int v = 16; };
+template <> struct PixBytes<2> { static constexpr int v = 32; };
+
+template <int DT>
+__device__ __forceinline__ void copy_px(unsigned char* dst, const void* base, int64_t p) {
+  const unsigned char* src = static_cast<const unsigned char*>(base) + p * PixBytes<DT>::v;
+  if constexpr (DT == 0) cp_async8(dst, src);
+  else if constexpr (DT == 1) cp_async16(dst, src);
+  else {
+    cp_async16(dst, src);
+    cp_async16(dst + 16, src + 16);
+  }
+}
+
+template <int DT, typename R>
+__device__ __forceinline__ void read_px(const unsigned char* s, R& x, R& y, R& z, R& c) {
+  if constexpr (DT == 0) {
+    const uint2 v = *reinterpret_cast<const uint2*>(s);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+    x = (R)a.x; y = (R)a.y; z = (R)b.x; c = (R)b.y;
+  } else if constexpr (DT == 1) {
+    const float4 v = *reinterpret_cast<const float4*>(s);
+    x = (R)v.x; y = (R)v.y; z = (R)v.z; c = (R)v.w;
+  } else {
+    const double2 a = *reinterpret_cast<const double2*>(s), b = *reinterpret_cast<const double2*>(s + 16);
+    x = (R)a.x; y = (R)a.y; z = (R)b.x; c = (R)b.y;
+  }
+}
+
+// copies the match indices of `item` into buf (all lanes; 16-byte pieces, 4-byte tail)
+__device__ __forceinline__ void prefetch_indices(int32_t* buf, const int32_t* __restrict__ idx, const Item& item,
+                                                 int lane) {
+  const int n = item.end - item.begin;
+  const int n16 = n & ~3;
+  for (int q = 4 * lane; q < n16; q += 128) cp_async16(buf + q, idx + item.begin + q);
+  for (int q = n16 + lane; q < n; q += 32) cp_async4(buf + q, idx + item.begin + q);
+}
+
+template <typename R, int DT>
+__global__ void __launch_bounds__(256, 2) residual_reduce_async_kernel(
+    const void* __restrict__ points, const int32_t* __restrict__ midx, const Item* __restrict__ items,
+    int num_items, const EdgeStatic* __restrict__ es, const double* __restrict__ T64,
+    const float* __restrict__ T32, RobustParams rp, void* __restrict__ partials) {
+  constexpr int PX = PixBytes<DT>::v;
+  constexpr int kWarpBytes = 2 * kAsyncChunk * 4 + kRing * 32 * 2 * PX;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  unsigned char* mine = smem + (size_t)warp * kWarpBytes;
+  int32_t* ibuf[2] = {reinterpret_cast<int32_t*>(mine), reinterpret_cast<int32_t*>(mine) + kAsyncChunk};
+  unsigned char* ring = mine + 2 * kAsyncChunk * 4 + lane * 2 * PX;  // + slot * 32 * 2 * PX
+  const int gwarp = (blockIdx.x * 256 + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * 256) >> 5;
+  Consts<R> k;
+  k.isr = (R)rp.inv_sigma_ray; k.isd = (R)rp.inv_sigma_dist;
+  k.ivr = (R)rp.inv_var_ray; k.ivd = (R)rp.inv_var_dist;
+  k.kappa = (R)rp.kappa; k.half_kappa = (R)(0.5 * rp.kappa);
+
+  // each warp owns a contiguous run of items (mostly of one edge) and reduces once per edge
+  const int per = (num_items + nwarps - 1) / nwarps;
+  const int it0 = gwarp * per, it1 = min(it0 + per, num_items);
+  int b = 0;
+  if (it0 < it1) {
+    const Item first = items[it0];
+    prefetch_indices(ibuf[0], midx + es[first.edge].idx_off, first, lane);
+  }
+  cp_commit();
+  Acc<R> acc;
+  acc.zero();
+  for (int it = it0; it < it1; ++it, b ^= 1) {
+    const Item item = items[it];
+    const int next = it + 1;
+    if (next < it1) {
+      const Item itn = items[next];
+      prefetch_indices(ibuf[b ^ 1], midx + es[itn.edge].idx_off, itn, lane);
+    }
+    cp_commit();
+    cp_wait<1>();  // this item's indices (all but the group just committed)
+    __syncwarp();
+    const int64_t pix_i = es[item.edge].pix_i, pix_j = es[item.edge].pix_j;
+    const int32_t* cur = ibuf[b];
+    R T[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      if constexpr (sizeof(R) == 4) T[q] = T32[16 * item.edge + q];
+      else T[q] = T64[12 * item.edge + q];
+    }
+    const int n_pix = item.end - item.begin;
+    // compact the valid matches of the item in place (writes never reach unread entries)
+    int32_t* curw = ibuf[b];
+    int nvalid = 0;
+    const unsigned below = (1u << lane) - 1u;
+    for (int g0 = 0; g0 < n_pix; g0 += 32) {
+      const int m = g0 + lane;
+      const int n = m < n_pix ? cur[m] : -1;
+      const unsigned mask = __ballot_sync(0xffffffffu, n >= 0);
+      if (n >= 0) curw[nvalid + __popc(mask & below)] = (int32_t)(((uint32_t)n << 10) | (uint32_t)m);
+      nvalid += __popc(mask);
+    }
+    __syncwarp();
+    const int ngroups = (nvalid + 31) >> 5;
+    auto issue = [&](int gidx) {
+      const int e = 32 * gidx + lane;
+      if (gidx < ngroups && e < nvalid) {
+        const uint32_t v = (uint32_t)cur[e];
+        unsigned char* slot = ring + (size_t)(gidx % kRing) * 32 * 2 * PX;
+        copy_px<DT>(slot, points, pix_i + item.begin + (int)(v & 1023u));
+        copy_px<DT>(slot + PX, points, pix_j + (int)(v >> 10));
+      }
+      cp_commit();
+    };
+#pragma unroll
+    for (int s0 = 0; s0 < kRing; ++s0) issue(s0);
+    for (int gidx = 0; gidx < ngroups; ++gidx) {
+      cp_wait<kRing - 1>();
+      if (32 * gidx + lane < nvalid) {
+        const unsigned char* slot = ring + (size_t)(gidx % kRing) * 32 * 2 * PX;
+        R xi, yi, zi, ci, xj, yj, zj, cj;
+        read_px<DT, R>(slot, xi, yi, zi, ci);
+        read_px<DT, R>(slot + PX, xj, yj, zj, cj);
+        accumulate<R>(xi, yi, zi, ci, xj, yj, zj, cj, T, k, acc);
+      }
+      issue(gidx + kRing);
+    }
+    cp_wait<0>();
+    __syncwarp();  // the index buffer of this item is reused two items later
+    write_record(acc, partials, it, it + 1 == it1 || items[it + 1].edge != item.edge, lane);
+  }
+  cp_wait<0>();
+}
+
+template <int DT>
+constexpr int async_smem_bytes() { return 8 * (2 * kAsyncChunk * 4 + kRing * 32 * 2 * PixBytes<DT>::v); }
 
 // Launch configurations the autotuner chooses from (256-thread CTAs):
 //   0  plain loop, 2 pixels per lane per group, natural register budget
 //   1  software-pipelined loop, 1 pixel per lane per group
 //   2  software-pipelined loop, 2 pixels per lane per group
 //   3  software-pipelined loop, 1 pixel per lane, register budget for 3 CTAs per SM
+//   4  shared-memory-staged loop (cp.async ring) over warp-compacted valid matches; work
+//      items of exactly 1024 pixels, only when every match-index row starts 16-byte
+//      aligned and every keyframe has at most 2^22 pixels
 // FP64 runs configurations 0 and 1 only.
 constexpr int kK1Block = 256;
-constexpr int kK1Cfgs = 4;
+constexpr int kK1Cfgs = 5;
+constexpr int kAsyncCfg = 4;
 
 template <typename R, int DT>
 const void* pick_cfg(int cfg) {
-  switch (cfg) {
-    case 0: return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 2, false>);
-    case 1: return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 1, true>);
-    case 2: return sizeof(R) == 4 ? reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 2, true>) : nullptr;
-    case 3: return sizeof(R) == 4 ? reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 3, 1, true>) : nullptr;
-    default: return nullptr;
+  if (cfg == 0) return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 2, false>);
+  if (cfg == 1) return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 1, true>);
+  if constexpr (sizeof(R) == 4) {
+    if (cfg == 2) return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 2, true>);
+    if (cfg == 3) return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 3, 1, true>);
   }
+  if (cfg == kAsyncCfg) return reinterpret_cast<const void*>(&residual_reduce_async_kernel<R, DT>);
+  return nullptr;
 }
 
 const void* pick_kernel(int mode, int dtype, int cfg) {
@@ -399,7 +602,24 @@ const void* pick_kernel(int mode, int dtype, int cfg) {
 
 }  // namespace
 
-int residual_reduce_num_cfgs(int mode) { return mode == 1 ? kK1Cfgs : 2; }
+int residual_reduce_num_cfgs(int mode) { return kK1Cfgs; }
+
+int residual_reduce_cfg_chunk(int cfg) { return cfg == kAsyncCfg ? kAsyncChunk : 0; }
+
+static size_t cfg_smem(int dtype, int cfg) {
+  if (cfg != kAsyncCfg) return 0;
+  return dtype == 0 ? async_smem_bytes<0>() : (dtype == 1 ? async_smem_bytes<1>() : async_smem_bytes<2>());
+}
+
+cudaError_t residual_reduce_prepare() {
+  // opt the shared-memory-staged variants into more than 48 KB of dynamic shared memory
+  cudaError_t e = cudaSuccess;
+  for (int mode = 0; mode < 2; ++mode)
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d)
+      e = cudaFuncSetAttribute(pick_kernel(mode, d, kAsyncCfg), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)cfg_smem(d, kAsyncCfg));
+  return e;
+}
 
 int residual_reduce_block() { return kK1Block; }
 
@@ -407,7 +627,7 @@ int residual_reduce_max_blocks_per_sm(int mode, int dtype, int cfg) {
   const void* f = pick_kernel(mode, dtype, cfg);
   if (!f) return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kK1Block, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kK1Block, cfg_smem(dtype, cfg)) != cudaSuccess) return 0;
   return n;
 }
 
@@ -420,7 +640,7 @@ cudaError_t launch_residual_reduce(int mode, int dtype, int cfg, int grid, const
   if (num_items <= 0) return cudaSuccess;
   void* args[] = {(void*)&points, (void*)&midx, (void*)&items, (void*)&num_items, (void*)&es,
                   (void*)&T64, (void*)&T32, (void*)&rp, (void*)&partials};
-  return cudaLaunchKernel(f, dim3(grid), dim3(kK1Block), args, 0, s);
+  return cudaLaunchKernel(f, dim3(grid), dim3(kK1Block), args, cfg_smem(dtype, cfg), s);
 }
 
 }  // namespace como3r

@@ -210,3 +210,20 @@ def test_batched_graphs_match_individual(C):
     po, to = O.gn_solve(batch, batch.poses_init, 6)
     assert max(pose_err(poses.cpu().numpy(), po).values()) <= FP64_TOL
     np.testing.assert_allclose(trace, to, rtol=FP64_TOL)
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4])
+def test_every_residual_kernel_configuration(C, mid, tiny, cfg, monkeypatch):
+    """Each launch configuration the autotuner may choose gives the oracle's edge blocks
+    (mixed form; the FP64 form for the configurations that have one)."""
+    monkeypatch.setenv("COMO3R_K1_CFG", str(cfg))
+    cases = [(mid, C.MIXED, MIXED_TOL)] + ([(tiny, C.PLAIN_FP64, FP64_TOL)] if cfg in (0, 1, 4) else [])
+    for prob, mode, tol in cases:
+        with C.Graph(prob, mode=mode) as g:
+            st, cost, rec = edge_records(C, g, prob.poses_init)
+            assert g.stats()["block"] % 100 == cfg
+        _, _, E, recs = O.build_system(prob, prob.poses_init, 0)
+        for e, r in enumerate(recs):
+            assert rel_fro(rec[e, :49].reshape(7, 7), r["H_rel"]) <= tol, (cfg, mode, e)
+            assert abs(rec[e, 56] - r["cost"]) <= tol * r["cost"]
+            assert rec[e, 57] == r["n_valid"] and rec[e, 58] == r["n_skipped"]
