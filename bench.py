@@ -51,7 +51,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--cpu-sample-edges", type=int, default=16)
+    ap.add_argument("--cpu-sample-edges", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["all", "mixed"], default="all",
                     help="mixed: time only the resident mixed form (profiling runs)")
@@ -143,7 +143,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(inside)}
 
 
-def oracle_sample(prob, n_edges: int):
+def oracle_sample(prob, n_edges: int, offset: int = 0):
     """Time the FP64 oracle on a bounded sample of one iteration and extrapolate.
 
     Sample: `n_edges` edges (evenly spread) linearised with dense per-match Jacobians,
@@ -153,7 +153,8 @@ def oracle_sample(prob, n_edges: int):
     from oracle import como3r_oracle as O
     arrs = O.problem_arrays(prob)
     T = [O.pose_to_matrix(p) for p in prob.poses_init]
-    sel = np.unique(np.linspace(0, prob.num_edges - 1, n_edges).astype(int))
+    sel = np.unique(np.linspace(0, prob.num_edges - 1, n_edges).astype(int) + offset) % prob.num_edges
+    c0 = time.process_time()
     t0 = time.perf_counter()
     for e in sel:
         i, j, m, n, Pi, Pj = O.edge_matches(prob, arrs, int(e))
@@ -168,12 +169,10 @@ def oracle_sample(prob, n_edges: int):
     tau, _, _ = O.damped_solve(Hs, gs, int(prob.anchor[0]), prob.lam, prob.eps0, prob.max_attempts)
     O.retract(prob.poses_init, 1e-3 * tau)
     t_solve = time.perf_counter() - t1
+    cpu_s = time.process_time() - c0
     t_iter = t_edges * prob.num_edges / len(sel) + t_solve
-    try:  # BLAS threads the oracle's library calls may use
-        import threadpoolctl
-        threads = max([p.get("num_threads", 1) for p in threadpoolctl.threadpool_info()] + [1])
-    except ImportError:
-        threads = os.cpu_count() or 1
+    # threads actually used: CPU time over wall time of the sample (numpy / BLAS threads)
+    threads = max(1, round(cpu_s / max(t_edges + t_solve, 1e-9)))
     return {"value": 1.0 / t_iter, "unit": UNIT, "cores": int(threads), "kind": "oracle",
             "sample": (f"{len(sel)} of {prob.num_edges} edges linearised + full {n7}x{n7} dense solve and "
                        f"retraction ({t_edges + t_solve:.1f} s CPU), extrapolated to one GN iteration"),
@@ -187,17 +186,23 @@ def run_reference(args):
         return
     from synth import make_workload
     prob = make_workload(args.workload, seed=args.seed)
-    n_edges = max(2, min(8, args.cpu_sample_edges))
-    for _ in range(args.warmup):
-        oracle_sample(prob, n_edges)
+    # each step: a bounded sample of one GN iteration (a few edges, rotating over the edge
+    # list, plus the full dense solve), sized so that the whole run stays within minutes
+    n_edges = 1 if args.steps + args.warmup > 24 else 4
+    for w in range(args.warmup):
+        oracle_sample(prob, n_edges, offset=w)
     t0 = time.perf_counter()
-    its = []
-    for _ in range(args.steps):
-        its.append(oracle_sample(prob, n_edges)["seconds_per_iteration"])
+    its, cores = [], []
+    for k in range(args.steps):
+        r = oracle_sample(prob, n_edges, offset=args.warmup + k)
+        its.append(r["seconds_per_iteration"])
+        cores.append(r["cores"])
     wall = time.perf_counter() - t0
     value = 1.0 / float(np.mean(its))
-    cb = oracle_sample(prob, n_edges)
-    cb["value"] = value
+    cb = {"value": value, "unit": UNIT, "cores": int(max(cores)), "kind": "oracle",
+          "sample": (f"per step {n_edges} of {prob.num_edges} edges linearised (rotating) + the full "
+                     f"{7 * prob.num_kf}x{7 * prob.num_kf} dense solve and retraction, extrapolated to one "
+                     f"GN iteration; {args.steps} steps in {wall:.1f} s")}
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -258,6 +263,7 @@ def run_ours(args):
     barrier()
     launches = 0
     tw0 = time.time()
+    torch.cuda.nvtx.range_push("como3r_timed")  # lets ncu select the timed launches (--nvtx-include)
     ev0.record()
     for _ in range(args.steps):
         work.copy_(poses0)
@@ -265,6 +271,7 @@ def run_ours(args):
         launches += g.last_launch_count()
     ev1.record()
     barrier()
+    torch.cuda.nvtx.range_pop()
     tw1 = time.time()
     ms = max_over_ranks(ev0.elapsed_time(ev1))
     final_cost = info[0]["cost"]
