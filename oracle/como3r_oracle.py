@@ -48,6 +48,24 @@ import scipy.linalg
 DEGENERATE = 1e-12
 
 
+# Every routine below also runs on complex arrays: the derivative of the refined cost is
+# checked by the complex-step method (perturb an input by i h, read Im(L) / h), so norms
+# are sqrt(sum x^2) rather than absolute values and every branch (Huber region, pivot
+# test, degenerate-match test) is decided on the real part.  For real inputs the values
+# are unchanged.
+def _norm(X: np.ndarray, keepdims: bool = False) -> np.ndarray:
+    return np.sqrt(np.sum(X * X, axis=-1, keepdims=keepdims))
+
+
+def _abs_real_sign(r: np.ndarray) -> np.ndarray:
+    """|r| for real r; for complex r the analytic continuation r * sign(Re r)."""
+    return np.where(r.real >= 0, r, -r)
+
+
+def _dtype(*xs) -> type:
+    return np.result_type(*[np.asarray(x).dtype for x in xs], np.float64)
+
+
 # =============================================================== Sim(3) (Sec. III-A, III-D)
 def quat_to_rot(q: np.ndarray) -> np.ndarray:
     """Rotation matrix of a unit quaternion stored (x, y, z, w)."""
@@ -91,15 +109,16 @@ def skew(w: np.ndarray) -> np.ndarray:
 
 def hat(tau: np.ndarray) -> np.ndarray:
     """sim(3) generator of tau = (v, omega, zeta): [[omega^ + zeta I, v], [0, 0]] (Sec. III-D)."""
-    X = np.zeros((4, 4))
-    X[:3, :3] = skew(tau[3:6]) + tau[6] * np.eye(3)
+    X = np.zeros((4, 4), dtype=_dtype(tau))
+    X[:3, :3] = np.array(skew(tau[3:6])) + tau[6] * np.eye(3)
     X[:3, 3] = tau[:3]
     return X
 
 
 def exp_sim3(tau: np.ndarray) -> np.ndarray:
     """Exp(tau) as the matrix exponential of hat(tau) (library expm, scaling and squaring)."""
-    return scipy.linalg.expm(hat(np.asarray(tau, dtype=np.float64)))
+    tau = np.asarray(tau)
+    return scipy.linalg.expm(hat(tau if np.iscomplexobj(tau) else tau.astype(np.float64)))
 
 
 def log_sim3(T: np.ndarray) -> np.ndarray:
@@ -117,12 +136,13 @@ def adjoint(T: np.ndarray) -> np.ndarray:
     With T = (sR, t): v' = sR v + [t]x R omega - zeta t, omega' = R omega, zeta' = zeta.
     """
     sR = T[:3, :3]
-    s = np.cbrt(np.linalg.det(sR))
+    det = np.linalg.det(sR)
+    s = det ** (1.0 / 3.0) if np.iscomplexobj(det) else np.cbrt(det)
     R = sR / s
     t = T[:3, 3]
-    Ad = np.zeros((7, 7))
+    Ad = np.zeros((7, 7), dtype=_dtype(T))
     Ad[:3, :3] = sR
-    Ad[:3, 3:6] = skew(t) @ R
+    Ad[:3, 3:6] = np.array(skew(t)) @ R
     Ad[:3, 6] = -t
     Ad[3:6, 3:6] = R
     Ad[6, 6] = 1.0
@@ -132,7 +152,7 @@ def adjoint(T: np.ndarray) -> np.ndarray:
 # ============================================== residual, whitening, Huber (Sec. III-A)
 def psi(X: np.ndarray) -> np.ndarray:
     """Ray operator psi(X) = X / ||X|| (row-wise)."""
-    return X / np.linalg.norm(X, axis=-1, keepdims=True)
+    return X / _norm(X, keepdims=True)
 
 
 def transform(T: np.ndarray, X: np.ndarray) -> np.ndarray:
@@ -142,10 +162,10 @@ def transform(T: np.ndarray, X: np.ndarray) -> np.ndarray:
 def residual(Tij: np.ndarray, Xi: np.ndarray, Xj: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
     """e_mn = [psi(T_ij X_j,n) - psi(X_i,m); ||T_ij X_j,n|| - ||X_i,m||] (Eq. residual)."""
     x = transform(Tij, Xj)
-    e = np.empty((x.shape[0], 4))
+    e = np.empty((x.shape[0], 4), dtype=_dtype(x, Xi))
     with np.errstate(invalid="ignore", divide="ignore"):
         e[:, :3] = psi(x) - psi(Xi)
-    e[:, 3] = np.linalg.norm(x, axis=1) - np.linalg.norm(Xi, axis=1)
+    e[:, 3] = _norm(x) - _norm(Xi)
     return e, x
 
 
@@ -156,15 +176,15 @@ def whiten(e: np.ndarray, q: np.ndarray, sigma_ray: float, sigma_dist: float) ->
 
 
 def huber_rho(r: np.ndarray, kappa: float) -> np.ndarray:
-    a = np.abs(r)
-    return np.where(a <= kappa, 0.5 * r * r, kappa * a - 0.5 * kappa * kappa)
+    a = _abs_real_sign(r)
+    return np.where(a.real <= kappa, 0.5 * r * r, kappa * a - 0.5 * kappa * kappa)
 
 
 def huber_weight(r: np.ndarray, kappa: float) -> np.ndarray:
     """IRLS weight w(r) = min(1, kappa / |r|), equal to 1 at r = 0."""
-    a = np.abs(r)
+    a = _abs_real_sign(r)
     with np.errstate(divide="ignore"):
-        return np.where(a <= kappa, 1.0, kappa / np.where(a > 0, a, 1.0))
+        return np.where(a.real <= kappa, 1.0, kappa / np.where(a.real > 0, a, 1.0))
 
 
 # ========================================================== Jacobians (Eq. jacobian)
@@ -175,8 +195,8 @@ def jacobian_rel(x: np.ndarray) -> np.ndarray:
     Dd/Dx = x^T / d.
     """
     M = x.shape[0]
-    d = np.linalg.norm(x, axis=1)
-    Dx = np.zeros((M, 3, 7))
+    d = _norm(x)
+    Dx = np.zeros((M, 3, 7), dtype=_dtype(x))
     Dx[:, :, 0:3] = np.eye(3)
     Dx[:, 0, 4], Dx[:, 0, 5] = x[:, 2], -x[:, 1]   # -[x]x
     Dx[:, 1, 3], Dx[:, 1, 5] = -x[:, 2], x[:, 0]
@@ -185,7 +205,7 @@ def jacobian_rel(x: np.ndarray) -> np.ndarray:
     outer = x[:, :, None] * x[:, None, :]
     Dpsi = (np.eye(3)[None] - outer / (d * d)[:, None, None]) / d[:, None, None]
     Dd = (x / d[:, None])[:, None, :]
-    J = np.empty((M, 4, 7))
+    J = np.empty((M, 4, 7), dtype=_dtype(x))
     J[:, :3, :] = Dpsi @ Dx
     J[:, 3:, :] = Dd @ Dx
     return J
@@ -224,11 +244,12 @@ def linearize_edge(Ti: np.ndarray, Tj: np.ndarray, Pi: np.ndarray, Pj: np.ndarra
     Xi, ci = Pi[:, :3], Pi[:, 3]
     Xj, cj = Pj[:, :3], Pj[:, 3]
     e, x = residual(Tij, Xi, Xj)
-    di = np.linalg.norm(Xi, axis=1)
-    d = np.linalg.norm(x, axis=1)
+    di = _norm(Xi)
+    d = _norm(x)
     cc = ci * cj
     with np.errstate(invalid="ignore"):
-        ok = (di > DEGENERATE) & (d > DEGENERATE) & (cc >= 0) & np.isfinite(di) & np.isfinite(d) & np.isfinite(cc)
+        ok = ((di.real > DEGENERATE) & (d.real > DEGENERATE) & (cc.real >= 0) & np.isfinite(di) & np.isfinite(d)
+              & np.isfinite(cc))
     ok &= np.all(np.isfinite(e), axis=1)
     e, x, cc = e[ok], x[ok], cc[ok]
     q = np.sqrt(cc)
@@ -236,7 +257,8 @@ def linearize_edge(Ti: np.ndarray, Tj: np.ndarray, Pi: np.ndarray, Pj: np.ndarra
     w = huber_weight(r, params["huber_k"])
     sig = np.array([params["sigma_ray"]] * 3 + [params["sigma_dist"]])
     W = w * q[:, None] / (sig * sig)[None, :]
-    cost = float(huber_rho(r, params["huber_k"]).sum())
+    cost = huber_rho(r, params["huber_k"]).sum()
+    cost = complex(cost) if np.iscomplexobj(cost) else float(cost)
     J = jacobian_rel(x)
     Ad = adjoint(sim3_inverse(Ti))
     Ji = -J @ Ad
@@ -250,20 +272,23 @@ def linearize_edge(Ti: np.ndarray, Tj: np.ndarray, Pi: np.ndarray, Pj: np.ndarra
         cost=cost, n_valid=int(ok.size), n_skipped=int((~ok).sum()), Ad=Ad)
 
 
-def build_system(prob, poses: np.ndarray, graph: int = 0, arrs=None):
+def build_system(prob, poses: np.ndarray, graph: int = 0, arrs=None, T_global=None):
     """Dense normal equations of one graph: H (7N x 7N), g (7N), cost, per-edge records.
 
     Keyframes of the graph are numbered locally from 0; the anchor is still included.
+    The poses come from `poses` (stored form) or, when given, from the list of 4x4
+    matrices `T_global` indexed by global keyframe id.
     """
     arrs = arrs or problem_arrays(prob)
     params = prob.params()
     k0, k1 = int(prob.kf_offset[graph]), int(prob.kf_offset[graph + 1])
     N = k1 - k0
-    H = np.zeros((7 * N, 7 * N))
-    g = np.zeros(7 * N)
+    T = [pose_to_matrix(poses[k]) for k in range(k0, k1)] if T_global is None else T_global[k0:k1]
+    dt = _dtype(arrs["points"], *T)
+    H = np.zeros((7 * N, 7 * N), dtype=dt)
+    g = np.zeros(7 * N, dtype=dt)
     cost = 0.0
     records = []
-    T = [pose_to_matrix(poses[k]) for k in range(k0, k1)]
     for e in range(int(prob.edge_offset[graph]), int(prob.edge_offset[graph + 1])):
         i, j, m, n, Pi, Pj = edge_matches(prob, arrs, e)
         li, lj = i - k0, j - k0
@@ -287,9 +312,9 @@ def cholesky(A: np.ndarray) -> Optional[np.ndarray]:
     L = np.zeros_like(A)
     for j in range(n):
         piv = A[j, j] - L[j, :j] @ L[j, :j]
-        if not (np.isfinite(piv) and piv > 0.0):
+        if not (np.isfinite(piv) and piv.real > 0.0):
             return None
-        L[j, j] = math.sqrt(piv)
+        L[j, j] = np.sqrt(piv)
         L[j + 1:, j] = (A[j + 1:, j] - L[j + 1:, :j] @ L[j, :j]) / L[j, j]
     return L
 
@@ -330,7 +355,7 @@ def damped_solve(H: np.ndarray, g: np.ndarray, anchor, lam: float, eps0: float,
     keep = np.array([k for k in range(7 * N) if k // 7 not in fixed], dtype=np.int64)
     Hr = H[np.ix_(keep, keep)]
     gr = g[keep]
-    tau = np.zeros(7 * N)
+    tau = np.zeros(7 * N, dtype=_dtype(H, g))
     for r in range(max_attempts):
         eps = eps0 * 100.0 ** r
         A = Hr + lam * np.diag(np.diag(Hr)) + eps * np.eye(Hr.shape[0])
@@ -384,6 +409,68 @@ def gn_solve(prob, poses: np.ndarray, iters: int) -> Tuple[np.ndarray, np.ndarra
 def total_cost(prob, poses: np.ndarray) -> np.ndarray:
     arrs = problem_arrays(prob)
     return np.array([build_system(prob, poses, gidx, arrs)[2] for gidx in range(prob.num_graphs)])
+
+
+# ============== refined cost as a function of depth and confidence (Sec. III-E)
+# The pose-depth alternation of Sec. III-E feeds the refined back-end cost back into the
+# dense structure.  Here the structure is parameterised per pixel by its log-range l_p
+# (X_p = exp(l_p) psi(X_p): moving l_p slides the point along its fixed viewing ray, so a
+# log-depth and a log-range change have the same derivative) and its confidence c_p.  The
+# refined cost is L(theta) = sum over graphs of E_global(T^K(theta), theta): K Gauss-Newton
+# iterations from fixed initial poses, then the cost.  Its derivative is checked by the
+# complex-step method, which differentiates exactly the steps above (IRLS weights, the
+# damped factorisation, the retraction) without any hand-derived adjoint.
+def reparameterised_points(prob, dlog=None, dconf=None) -> np.ndarray:
+    """Stored pointmaps with every point scaled by exp(dlog_p) along its ray and every
+    confidence shifted by dconf_p ([sum P] each; real or complex)."""
+    pts = np.asarray(prob.points, dtype=np.float64)
+    dt = _dtype(pts, 0.0 if dlog is None else dlog, 0.0 if dconf is None else dconf)
+    out = pts.astype(dt)
+    if dlog is not None:
+        out[:, :3] = out[:, :3] * np.exp(dlog)[:, None]
+    if dconf is not None:
+        out[:, 3] = out[:, 3] + dconf
+    return out
+
+
+def gn_trajectory(prob, poses0: np.ndarray, iters: int, arrs) -> List[np.ndarray]:
+    """The iterations of gn_solve with every pose kept as a 4x4 similarity matrix and
+    updated by T <- Exp(tau) T (matrix exponential); runs in the dtype of the arrays.
+    Returns the matrices T^K, indexed by global keyframe id."""
+    T = [pose_to_matrix(p).astype(_dtype(arrs["points"])) for p in poses0]
+    for _ in range(iters):
+        steps = []
+        for gidx in range(prob.num_graphs):
+            H, g, _, _ = build_system(prob, None, gidx, arrs, T_global=T)
+            tau, _, _ = damped_solve(H, g, component_anchors(prob, gidx), prob.lam, prob.eps0, prob.max_attempts)
+            steps.append((int(prob.kf_offset[gidx]), tau))
+        for k0, tau in steps:
+            for l in range(tau.shape[0]):
+                if np.any(tau[l] != 0):
+                    T[k0 + l] = exp_sim3(tau[l]) @ T[k0 + l]
+    return T
+
+
+def refined_cost(prob, poses0: np.ndarray, iters: int, dlog=None, dconf=None, envelope: bool = False):
+    """L = sum_g E_g(T^K, theta) at theta shifted by (dlog, dconf).
+
+    Unrolled (default): T^K comes from `iters` iterations run at the shifted theta.
+    Envelope: T^K comes from the unshifted theta and only the explicit dependence of the
+    cost on theta remains (the partial derivative at fixed poses)."""
+    arrs = problem_arrays(prob)
+    arrs_theta = dict(arrs, points=reparameterised_points(prob, dlog, dconf))
+    T = gn_trajectory(prob, poses0, iters, arrs if envelope else arrs_theta)
+    return sum(build_system(prob, None, gidx, arrs_theta, T_global=T)[2] for gidx in range(prob.num_graphs))
+
+
+def refined_cost_derivative(prob, poses0: np.ndarray, iters: int, vlog=None, vconf=None, envelope: bool = False,
+                            h: float = 1e-30) -> float:
+    """Directional derivative of refined_cost along (vlog, vconf) by the complex step,
+    Im L(theta + i h v) / h (Squire and Trapp, 1998): no subtractive cancellation, so it is
+    exact to rounding for any small h; every branch is taken on the real part."""
+    dl = None if vlog is None else 1j * h * np.asarray(vlog, dtype=np.float64)
+    dc = None if vconf is None else 1j * h * np.asarray(vconf, dtype=np.float64)
+    return float(np.imag(refined_cost(prob, poses0, iters, dl, dc, envelope)) / h)
 
 
 # ================================================== Umeyama (Eq. align, Eq. umeyama)

@@ -381,3 +381,75 @@ def test_unlinked_component_keeps_its_own_reference():
     err = O.pose_errors(poses[6:], want)
     assert max(err.values()) < 1e-9, err
     assert max(O.pose_errors(poses[:6], p.poses_gt[:6]).values()) < 1e-9
+
+
+# --------------------------------------- refined cost vs depth and confidence (Sec. III-E)
+@pytest.fixture(scope="module")
+def small_adj():
+    """Two agents x 3 keyframes, 32x24 pointmaps, 5 edges, perturbed initial poses."""
+    return make_problem(3, agents=2, n_kf=3, H=24, W=32, f=25.0, n_inter=1, iters=3)
+
+
+@pytest.mark.parametrize("iters", [0, 2])
+def test_refined_cost_complex_step_matches_central_difference(small_adj, iters):
+    """The complex-step derivative of the unrolled refined cost equals a central finite
+    difference of the real-valued computation along a dense random direction."""
+    p = small_adj
+    rng = np.random.default_rng(11)
+    vl, vc = rng.normal(size=len(p.points)), rng.normal(size=len(p.points))
+    cs = O.refined_cost_derivative(p, p.poses_init, iters, vl, vc)
+    h = 1e-6
+    fd = (O.refined_cost(p, p.poses_init, iters, h * vl, h * vc)
+          - O.refined_cost(p, p.poses_init, iters, -h * vl, -h * vc)) / (2 * h)
+    assert abs(cs - fd) <= 1e-5 * abs(cs)
+
+
+def test_refined_cost_single_pixel_derivatives(small_adj):
+    """Per-pixel derivatives (one log-range, one confidence) match central differences."""
+    p = small_adj
+    P = len(p.points)
+    touched = np.unique(np.concatenate([p.pix_offset()[p.edge_i[e]] + np.nonzero(
+        p.match_idx[p.idx_offset()[e]:p.idx_offset()[e + 1]] >= 0)[0] for e in range(p.num_edges)]))
+    for pix in touched[[5, len(touched) // 2]]:
+        for which in ("log", "conf"):
+            v = np.zeros(P)
+            v[pix] = 1.0
+            args = (v, None) if which == "log" else (None, v)
+            cs = O.refined_cost_derivative(p, p.poses_init, 1, *args)
+            # the cost after an iteration carries ~1e-13 relative rounding noise, so the step
+            # balances it against truncation
+            h = 1e-4 if which == "log" else 1e-3
+            sh = lambda s: (s * v, None) if which == "log" else (None, s * v)
+            fd = (O.refined_cost(p, p.poses_init, 1, *sh(h)) - O.refined_cost(p, p.poses_init, 1, *sh(-h))) / (2 * h)
+            L = O.refined_cost(p, p.poses_init, 1)
+            assert abs(cs - fd) <= 1e-4 * abs(cs) + 2e-13 * abs(L) / h, (pix, which, cs, fd)
+
+
+def test_envelope_derivative_uniform_confidence_scaling(small_adj):
+    """Scaling every confidence by (1 + t) scales q by (1 + t) and every whitened residual
+    by sqrt(1 + t), so at fixed poses dE/dt = sum rho'(r) r / 2 = sum w r^2 / 2."""
+    p = small_adj
+    c = p.points[:, 3].astype(np.float64)
+    env = O.refined_cost_derivative(p, p.poses_init, 2, None, c, envelope=True)
+    arrs = O.problem_arrays(p)
+    T = O.gn_trajectory(p, p.poses_init, 2, arrs)
+    expect = 0.0
+    for e in range(p.num_edges):
+        i, j, m, n, Pi, Pj = O.edge_matches(p, arrs, e)
+        ee, _ = O.residual(np.linalg.inv(T[i]) @ T[j], Pi[:, :3], Pj[:, :3])
+        r = O.whiten(ee, np.sqrt(Pi[:, 3] * Pj[:, 3]), p.sigma_ray, p.sigma_dist)
+        expect += 0.5 * float((O.huber_weight(r, p.huber_k) * r * r).sum())
+    assert abs(env - expect) <= 1e-12 * abs(expect)
+
+
+def test_unrolled_derivative_approaches_envelope(small_adj):
+    """At convergence g(T^K) -> 0, so dL/dtheta -> the partial derivative at fixed poses;
+    after one iteration the two still differ."""
+    p = small_adj
+    rng = np.random.default_rng(5)
+    vl, vc = rng.normal(size=len(p.points)), rng.normal(size=len(p.points))
+    gap = lambda K: abs(O.refined_cost_derivative(p, p.poses_init, K, vl, vc)
+                        - O.refined_cost_derivative(p, p.poses_init, K, vl, vc, envelope=True))
+    env12 = abs(O.refined_cost_derivative(p, p.poses_init, 12, vl, vc, envelope=True))
+    assert gap(12) <= 1e-3 * env12
+    assert gap(1) >= 0.05 * env12
