@@ -150,6 +150,44 @@ int como3r_solve(como3r_graph_t graph, double* poses, int32_t iters, double* cos
  *   cost_out host [G] or NULL. */
 int como3r_linearize(como3r_graph_t graph, const double* poses, double* edge_out, double* cost_out);
 
+/* Gradient of the refined cost with respect to the dense structure (pose-depth
+ * alternation, Sec. III-E).  Each pixel p is parameterised by its log-range l_p, with
+ * X_p = exp(l_p) psi(X_p) (the point slides along its viewing ray, so this is also the
+ * derivative with respect to log-depth), and by its confidence c_p.  The refined cost is
+ *   L = sum over graphs of E_global(T^K, theta)                              (Eq. global)
+ * where T^K are the poses after `iters` Gauss-Newton iterations (Sec. III-D) from
+ * `poses_init`.
+ *   mode      COMO3R_VJP_UNROLLED: the total derivative through the K iterations (their
+ *             IRLS weights, damped factorisations and retractions); requires lambda = 0
+ *             (else UNSUPPORTED).  COMO3R_VJP_ENVELOPE: the partial derivative at fixed
+ *             T^K (equal to the total one at a stationary point).
+ *   upstream  factor applied to every output gradient (dLoss/dL of the caller).
+ *   grad_logdepth, grad_conf  device float [sum_k P_k], pixels in the packed order of
+ *             points_conf: upstream * dL/dl_p and upstream * dL/dc_p (overwritten).
+ *   poses_out [N][8] (host or device) or NULL: T^K.   loss_out host [G] or NULL: E_g(T^K).
+ * The forward iterations are recomputed inside the call; only the poses, steps and solve
+ * outcomes of each iteration are kept (checkpoints of 7N + 8N doubles per iteration), and
+ * each backward step re-linearises from its pose checkpoint and re-factorises with the
+ * recorded eps.  Pixel gradients are accumulated with atomics (FP32 in the MIXED form, so
+ * bitwise results can vary between runs; FP64 then rounded once in the PLAIN form).  A
+ * match with c_i c_j = 0 contributes no confidence gradient.  Synchronises the stream.
+ * Returns OK or the warning bitmask of the forward iterations, or an error. */
+typedef enum { COMO3R_VJP_UNROLLED = 0, COMO3R_VJP_ENVELOPE = 1 } como3r_vjp_mode;
+int como3r_vjp(como3r_graph_t graph, const double* poses_init, int32_t iters, int32_t mode, double upstream,
+               float* grad_logdepth, float* grad_conf, double* poses_out, double* loss_out);
+
+/* Packs pointmaps from the structure parameters: X_p = exp(logdepth_p) rays_p and c_p.
+ *   rays device float [n][3] (unit), logdepth / conf device float [n];
+ *   points_out device [n][4] in the storage type `dtype` (como3r_dtype); async on stream. */
+int como3r_points_from_logdepth(const float* rays, const float* logdepth, const float* conf, int64_t n,
+                                int32_t dtype, void* points_out, void* cuda_stream);
+
+/* The inverse split of packed points: unit ray, log-range (log ||X_p||) and confidence
+ * per point (device arrays; a point with zero or non-finite range gets ray 0 and log-range
+ * -inf); async on stream. */
+int como3r_rays_from_points(const void* points, int64_t n, int32_t dtype, float* rays, float* logdepth, float* conf,
+                            void* cuda_stream);
+
 /* Left retraction T_k <- Exp(tau_k) T_k (Sec. III-D) of n poses, tau_k = (v, omega, zeta).
  *   tau   device [n][7]; poses device [n][8] in/out; stream as at create (may be NULL).
  * Independent of any graph handle. */
@@ -169,7 +207,7 @@ int como3r_update_inputs(como3r_graph_t graph, const void* points_conf, const in
 #define COMO3R_STAGES 7
 int como3r_time_stages(como3r_graph_t graph, const double* poses, int32_t reps, float* ms /* [COMO3R_STAGES] */);
 
-/* Number of kernels the last gn_step / solve / linearize call enqueued (for accounting). */
+/* Number of kernels the last gn_step / solve / linearize / vjp call enqueued (for accounting). */
 int64_t como3r_last_launch_count(como3r_graph_t graph);
 
 /* Static description of the planned work (see COMO3R_STAT_* indices). */

@@ -24,6 +24,7 @@ ERR_OOM = -3
 ERR_UNSUPPORTED = -4
 F16, F32, F64 = 0, 1, 2
 PLAIN_FP64, MIXED = 0, 1
+VJP_UNROLLED, VJP_ENVELOPE = 0, 1
 EDGE_RECORD = 64
 STAT_NAMES = ["graphs", "keyframes", "edges", "items", "columns", "blocks", "fill", "updates", "levels",
               "valid", "chunk", "block", "grid", "smem_solve", "nd_graphs", "r15"]
@@ -72,6 +73,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.como3r_graph_stats.argtypes = [vp, _i64p]
     lib.como3r_plan_stats.argtypes = [ctypes.POINTER(GraphDesc), _i64p]
     lib.como3r_linearize_noalloc.argtypes = [ctypes.POINTER(GraphDesc), vp, vp, vp]
+    lib.como3r_vjp.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, vp, vp, vp, _f64p]
+    lib.como3r_points_from_logdepth.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
+    lib.como3r_rays_from_points.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, vp, vp, vp]
     lib.como3r_status_str.argtypes = [ctypes.c_int]
     lib.como3r_status_str.restype = ctypes.c_char_p
     lib.como3r_last_error.argtypes = []
@@ -230,6 +234,20 @@ class Graph:
         _check(lib().como3r_time_stages(self.handle, _ptr(poses), int(reps), ms), "time_stages")
         return dict(zip(STAGE_NAMES, [float(x) for x in ms]))
 
+    def vjp(self, poses_init, iters: int, mode: int = VJP_UNROLLED, upstream: float = 1.0, grad_logdepth=None,
+            grad_conf=None, poses_out=None):
+        """como3r_vjp: (status, grad_logdepth, grad_conf, loss per graph); the gradients are
+        float32 CUDA tensors over the packed pixels (allocated here unless given)."""
+        import torch
+        P = int(self.prob.points.shape[0])
+        dev = self.points.device if self.points.is_cuda else torch.device("cuda")
+        gl = grad_logdepth if grad_logdepth is not None else torch.empty(P, dtype=torch.float32, device=dev)
+        gc = grad_conf if grad_conf is not None else torch.empty(P, dtype=torch.float32, device=dev)
+        loss = np.zeros(self.G)
+        st = _check(lib().como3r_vjp(self.handle, _ptr(poses_init), int(iters), int(mode), float(upstream), _ptr(gl),
+                                     _ptr(gc), _ptr(poses_out), loss.ctypes.data_as(_f64p)), "vjp")
+        return st, gl, gc, loss
+
     def last_launch_count(self) -> int:
         return int(lib().como3r_last_launch_count(self.handle))
 
@@ -257,6 +275,69 @@ def linearize_noalloc(prob, poses, edge_out, mode: int = MIXED, points=None, mat
     d = _build_desc(prob, _ptr(points), _ptr(match_idx), mode, False, keep)
     return _check(lib().como3r_linearize_noalloc(ctypes.byref(d), _ptr(poses), _ptr(edge_out), _torch_stream(stream)),
                   "linearize_noalloc")
+
+
+def points_from_logdepth(rays, logdepth, conf, points_out, stream=None) -> None:
+    """points_out[p] = (exp(logdepth[p]) * rays[p], conf[p]) in points_out's storage type
+    (float16 / float32 / float64 CUDA tensor [n, 4]); rays [n, 3], logdepth / conf [n] float32."""
+    import torch
+    code = {torch.float16: F16, torch.float32: F32, torch.float64: F64}[points_out.dtype]
+    n = int(points_out.shape[0])
+    _check(lib().como3r_points_from_logdepth(_ptr(rays), _ptr(logdepth), _ptr(conf), n, code, _ptr(points_out),
+                                             _torch_stream(stream)), "points_from_logdepth")
+
+
+def rays_from_points(points, stream=None):
+    """(rays [n, 3], logdepth [n], conf [n]) float32 CUDA tensors split from packed points."""
+    import torch
+    code = {torch.float16: F16, torch.float32: F32, torch.float64: F64}[points.dtype]
+    n = int(points.shape[0])
+    rays = torch.empty((n, 3), dtype=torch.float32, device=points.device)
+    ld = torch.empty(n, dtype=torch.float32, device=points.device)
+    cf = torch.empty(n, dtype=torch.float32, device=points.device)
+    _check(lib().como3r_rays_from_points(_ptr(points), n, code, _ptr(rays), _ptr(ld), _ptr(cf), _torch_stream(stream)),
+           "rays_from_points")
+    return rays, ld, cf
+
+
+def _make_cost_function():
+    import torch
+
+    class Como3rCost(torch.autograd.Function):
+        """L(logdepth, conf) = refined cost after `iters` GN iterations from poses_init
+        (sum over graphs), with a backward pass through como3r_vjp.
+
+        forward(logdepth [P] f32, conf [P] f32, graph, rays [P, 3] f32, poses_init [N, 8]
+        f64 CUDA, iters, mode) packs the pointmaps into the buffer the graph borrows
+        (graph.points), runs the iterations and returns L as a float64 scalar tensor."""
+
+        @staticmethod
+        def forward(ctx, logdepth, conf, graph, rays, poses_init, iters, mode=VJP_UNROLLED):
+            points_from_logdepth(rays, logdepth.detach().contiguous(), conf.detach().contiguous(), graph.points)
+            work = poses_init.detach().clone()
+            _, trace, _ = graph.solve(work, int(iters), trace=True)
+            ctx.graph, ctx.iters, ctx.mode = graph, int(iters), int(mode)
+            ctx.save_for_backward(poses_init)
+            return torch.tensor(float(trace[-1].sum()), dtype=torch.float64, device=logdepth.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (poses_init,) = ctx.saved_tensors
+            _, gl, gc, _ = ctx.graph.vjp(poses_init, ctx.iters, ctx.mode, upstream=float(grad_out))
+            return gl, gc, None, None, None, None, None
+
+    return Como3rCost
+
+
+_cost_fn = None
+
+
+def refined_cost(logdepth, conf, graph: "Graph", rays, poses_init, iters: int, mode: int = VJP_UNROLLED):
+    """Differentiable refined cost (torch.autograd): see Como3rCost."""
+    global _cost_fn
+    if _cost_fn is None:
+        _cost_fn = _make_cost_function()
+    return _cost_fn.apply(logdepth, conf, graph, rays, poses_init, iters, mode)
 
 
 def exported_symbols(header: str) -> Sequence[str]:

@@ -86,6 +86,13 @@ struct como3r_graph {
   cudaGraphExec_t iter_exec = nullptr, eval_exec = nullptr;
   int64_t last_launches = 0;
   std::vector<long long> edge_valid;
+  // adjoint workspaces (allocated by the first como3r_vjp call, grown with iters)
+  int vjp_iters_cap = -1;
+  double *d_ckpt = nullptr, *d_tau_hist = nullptr;
+  GraphInfoDev *d_ginfo_hist = nullptr, *d_ginfo_bwd = nullptr, *d_ginfo_final = nullptr;
+  double *d_adj_a = nullptr, *d_adj_a2 = nullptr, *d_adj_rhs = nullptr, *d_adj_u = nullptr;
+  double *d_evec = nullptr, *d_adj_rec = nullptr, *d_edge_adj = nullptr, *d_gacc = nullptr;
+  int* d_warn_bwd = nullptr;
 };
 
 namespace {
@@ -471,6 +478,134 @@ int como3r_linearize(como3r_graph_t g, const double* poses, double* edge_out, do
   if (cost_out)
     for (int k = 0; k < g->plan.G; ++k) cost_out[k] = g->h_ginfo[k].cost;
   return *g->h_warn & COMO3R_WARN_SKIPPED;
+}
+
+int como3r_vjp(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t mode, double upstream,
+               float* grad_logdepth, float* grad_conf, double* poses_out, double* loss_out) {
+  if (!g) return set_error(COMO3R_ERR_INVALID_ARG, "graph handle is NULL");
+  if (iters < 0) return set_error(COMO3R_ERR_INVALID_ARG, "iters must be >= 0");
+  if (mode != COMO3R_VJP_UNROLLED && mode != COMO3R_VJP_ENVELOPE)
+    return set_error(COMO3R_ERR_INVALID_ARG, "mode must be COMO3R_VJP_UNROLLED or COMO3R_VJP_ENVELOPE");
+  if (!grad_logdepth || !grad_conf) return set_error(COMO3R_ERR_INVALID_ARG, "gradient outputs are NULL");
+  if (!is_device_pointer(grad_logdepth) || !is_device_pointer(grad_conf))
+    return set_error(COMO3R_ERR_INVALID_ARG, "gradient outputs must be device memory");
+  if (mode == COMO3R_VJP_UNROLLED && g->lambda != 0.0)
+    return set_error(COMO3R_ERR_UNSUPPORTED, "the unrolled adjoint requires lambda = 0");
+  const HostPlan& p = g->plan;
+  const int N = p.N, E = p.E, G = p.G;
+  const int64_t P = p.total_px;
+  int rc;
+  if (iters > g->vjp_iters_cap) {
+    const int cap = std::max<int>(iters, 8);
+    CK(cudaStreamSynchronize(g->stream), "sync");
+    if ((rc = dalloc(g, &g->d_ckpt, (size_t)(cap + 1) * 8 * N)) || (rc = dalloc(g, &g->d_tau_hist, (size_t)cap * 7 * N)) ||
+        (rc = dalloc(g, &g->d_ginfo_hist, (size_t)cap * G)))
+      return rc;
+    if (g->vjp_iters_cap < 0 &&
+        ((rc = dalloc(g, &g->d_ginfo_bwd, G)) || (rc = dalloc(g, &g->d_ginfo_final, G)) ||
+         (rc = dalloc(g, &g->d_adj_a, (size_t)7 * N)) ||
+         (rc = dalloc(g, &g->d_adj_a2, (size_t)7 * N)) || (rc = dalloc(g, &g->d_adj_rhs, (size_t)7 * N)) ||
+         (rc = dalloc(g, &g->d_adj_u, (size_t)7 * N)) || (rc = dalloc(g, &g->d_evec, (size_t)16 * E)) ||
+         (rc = dalloc(g, &g->d_adj_rec, (size_t)kAdjointRecord * std::max(g->max_items, 1))) ||
+         (rc = dalloc(g, &g->d_edge_adj, (size_t)14 * E)) || (rc = dalloc(g, &g->d_warn_bwd, 1)) ||
+         (p.mode == COMO3R_PLAIN_FP64 && (rc = dalloc(g, &g->d_gacc, (size_t)2 * P)))))
+      return rc;
+    g->vjp_iters_cap = cap;
+  }
+  if ((rc = begin_call(g, poses_init))) return rc;
+  cudaStream_t s = g->stream;
+  int64_t launches = 0;
+  // forward with checkpoints: T^k, tau_k and the solve outcome of every iteration
+  for (int k = 0; k < iters; ++k) {
+    CK(cudaMemcpyAsync(g->d_ckpt + (size_t)k * 8 * N, g->d_poses, sizeof(double) * 8 * N, cudaMemcpyDeviceToDevice, s),
+       "checkpoint");
+    if ((rc = enqueue_linearize(g, s, nullptr, nullptr, nullptr)) || (rc = enqueue_solve(g, s, nullptr))) return rc;
+    CK(cudaMemcpyAsync(g->d_tau_hist + (size_t)k * 7 * N, g->d_tau, sizeof(double) * 7 * N, cudaMemcpyDeviceToDevice,
+                       s),
+       "checkpoint");
+    CK(cudaMemcpyAsync(g->d_ginfo_hist + (size_t)k * G, g->d_ginfo, sizeof(GraphInfoDev) * G, cudaMemcpyDeviceToDevice,
+                       s),
+       "checkpoint");
+    launches += 6;
+  }
+  CK(cudaMemcpyAsync(g->d_ckpt + (size_t)iters * 8 * N, g->d_poses, sizeof(double) * 8 * N, cudaMemcpyDeviceToDevice, s),
+     "checkpoint");
+  // the refined cost at T^K, its pose gradient g(T^K) and the envelope pixel term
+  if ((rc = enqueue_linearize(g, s, nullptr, nullptr, nullptr))) return rc;
+  CK(cudaMemcpyAsync(g->d_ginfo_final, g->d_ginfo, sizeof(GraphInfoDev) * G, cudaMemcpyDeviceToDevice, s), "info");
+  launches += 4;
+  const bool plain = p.mode == COMO3R_PLAIN_FP64;
+  void* gl = plain ? (void*)g->d_gacc : (void*)grad_logdepth;
+  void* gc = plain ? (void*)(g->d_gacc + P) : (void*)grad_conf;
+  CK(cudaMemsetAsync(gl, 0, (plain ? sizeof(double) : sizeof(float)) * (size_t)P, s), "memset");
+  CK(cudaMemsetAsync(gc, 0, (plain ? sizeof(double) : sizeof(float)) * (size_t)P, s), "memset");
+  CK(launch_adjoint_match(p.mode, p.dtype, false, g->points, g->midx, g->d_items, g->num_items, g->d_es, g->d_T64,
+                          g->d_T32, nullptr, g->rp, upstream, gl, gc, nullptr, s),
+     "adjoint envelope");
+  ++launches;
+  if (mode == COMO3R_VJP_UNROLLED && iters > 0) {
+    CK(launch_adjoint_gather(nullptr, nullptr, nullptr, nullptr, g->d_frozen, N, g->d_gvec, upstream, g->d_adj_a, s),
+       "adjoint start");
+    ++launches;
+    for (int k = iters - 1; k >= 0; --k) {
+      const double* tau_k = g->d_tau_hist + (size_t)k * 7 * N;
+      CK(launch_adjoint_keyframe(g->d_adj_a, tau_k, g->d_frozen, N, g->d_adj_a2, g->d_adj_rhs, s), "adjoint keyframe");
+      CK(cudaMemcpyAsync(g->d_poses, g->d_ckpt + (size_t)k * 8 * N, sizeof(double) * 8 * N, cudaMemcpyDeviceToDevice,
+                         s),
+         "restore");
+      if ((rc = enqueue_linearize(g, s, nullptr, nullptr, nullptr))) return rc;
+      CK(cudaMemsetAsync(g->d_adj_u, 0, sizeof(double) * 7 * N, s), "memset");
+      CK(launch_factor_solve(G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_colscratch, g->d_adj_rhs,
+                             g->d_adj_u, g->lambda, g->eps0, g->max_attempts, g->d_ginfo_bwd, g->d_warn_bwd, s,
+                             g->d_ginfo_hist + (size_t)k * G),
+         "adjoint solve");
+      CK(launch_adjoint_edge_prep(p.mode, g->d_es, E, g->d_Ad, g->d_adj_u, tau_k, g->d_evec, s), "adjoint edge prep");
+      CK(launch_adjoint_match(p.mode, p.dtype, true, g->points, g->midx, g->d_items, g->num_items, g->d_es, g->d_T64,
+                              g->d_T32, g->d_evec, g->rp, -1.0, gl, gc, g->d_adj_rec, s),
+         "adjoint match");
+      CK(launch_adjoint_edge(g->d_adj_rec, g->d_item_off, E, g->d_es, g->d_Ad, g->d_adj_u, tau_k, g->d_edge_adj, s),
+         "adjoint edge");
+      CK(launch_adjoint_gather(g->d_adj_a2, g->d_edge_adj, g->d_kf_contrib_off, g->d_kf_contrib, g->d_frozen, N,
+                               nullptr, 1.0, g->d_adj_a, s),
+         "adjoint gather");
+      launches += 4 + 6;
+    }
+    CK(cudaMemcpyAsync(g->d_poses, g->d_ckpt + (size_t)iters * 8 * N, sizeof(double) * 8 * N,
+                       cudaMemcpyDeviceToDevice, s),
+       "restore");
+  }
+  if (plain) {
+    CK(launch_to_float(g->d_gacc, grad_logdepth, P, s), "to float");
+    CK(launch_to_float(g->d_gacc + P, grad_conf, P, s), "to float");
+    launches += 2;
+  }
+  g->last_launches = launches;
+  // the per-graph cost and status of the evaluation at T^K (not of the backward re-solves)
+  CK(cudaMemcpyAsync(g->d_ginfo, g->d_ginfo_final, sizeof(GraphInfoDev) * G, cudaMemcpyDeviceToDevice, s), "info");
+  if ((rc = end_call(g, poses_out))) return rc;
+  if (loss_out)
+    for (int k = 0; k < G; ++k) loss_out[k] = g->h_ginfo[k].cost;
+  return *g->h_warn;
+}
+
+int como3r_points_from_logdepth(const float* rays, const float* logdepth, const float* conf, int64_t n,
+                                int32_t dtype, void* points_out, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!rays || !logdepth || !conf || !points_out)))
+    return set_error(COMO3R_ERR_INVALID_ARG, "bad points_from_logdepth arguments");
+  if (dtype < COMO3R_F16 || dtype > COMO3R_F64) return set_error(COMO3R_ERR_INVALID_ARG, "bad dtype");
+  CK(launch_points_from_logdepth(dtype, rays, logdepth, conf, n, points_out, static_cast<cudaStream_t>(cuda_stream)),
+     "points_from_logdepth");
+  return COMO3R_OK;
+}
+
+int como3r_rays_from_points(const void* points, int64_t n, int32_t dtype, float* rays, float* logdepth, float* conf,
+                            void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!points || !rays || !logdepth || !conf)))
+    return set_error(COMO3R_ERR_INVALID_ARG, "bad rays_from_points arguments");
+  if (dtype < COMO3R_F16 || dtype > COMO3R_F64) return set_error(COMO3R_ERR_INVALID_ARG, "bad dtype");
+  CK(launch_rays_from_points(dtype, points, n, rays, logdepth, conf, static_cast<cudaStream_t>(cuda_stream)),
+     "rays_from_points");
+  return COMO3R_OK;
 }
 
 int como3r_sim3_retract(const double* tau, double* poses, int32_t n, void* cuda_stream) {

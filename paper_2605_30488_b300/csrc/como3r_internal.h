@@ -105,11 +105,32 @@ cudaError_t launch_export_dense(int num_slots, const int32_t* slot_kf_r, const i
 constexpr int kColScratch = 63;
 cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t smem_bytes, const double* A,
                                 double* L, double* colscratch, const double* gvec, double* tau, double lambda,
-                                double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s);
+                                double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s,
+                                const GraphInfoDev* fixed = nullptr);
 size_t factor_solve_max_smem();
 cudaError_t factor_solve_prepare(size_t smem_bytes);  // once, before any capture
 cudaError_t launch_retract(const double* tau, double* poses, const uint8_t* frozen, int N, int* iter_counter,
                            cudaStream_t s);
+// ---- adjoint of the refined cost (k_adjoint.cu)
+constexpr int kAdjointRecord = 21;  // doubles per K1 work item
+cudaError_t launch_adjoint_match(int mode, int dtype, bool phi, const void* points, const int32_t* midx,
+                                 const Item* items, int num_items, const EdgeStatic* es, const double* T64,
+                                 const float* T32, const void* evec, RobustParams rp, double out_scale, void* gl,
+                                 void* gc, double* rec, cudaStream_t s);
+cudaError_t launch_adjoint_edge_prep(int mode, const EdgeStatic* es, int E, const double* Ad, const double* u,
+                                     const double* tau, void* evec, cudaStream_t s);
+cudaError_t launch_adjoint_edge(const double* rec, const int32_t* item_off, int E, const EdgeStatic* es,
+                                const double* Ad, const double* u, const double* tau, double* out, cudaStream_t s);
+cudaError_t launch_adjoint_keyframe(const double* a, const double* tau, const uint8_t* frozen, int N, double* a_out,
+                                    double* rhs, cudaStream_t s);
+cudaError_t launch_adjoint_gather(const double* a_prime, const double* edge_out, const int32_t* kf_contrib_off,
+                                  const int32_t* kf_contrib, const uint8_t* frozen, int N, const double* gvec,
+                                  double scale, double* a, cudaStream_t s);
+cudaError_t launch_to_float(const double* src, float* dst, int64_t n, cudaStream_t s);
+cudaError_t launch_points_from_logdepth(int dtype, const float* rays, const float* logdepth, const float* conf,
+                                        int64_t n, void* out, cudaStream_t s);
+cudaError_t launch_rays_from_points(int dtype, const void* points, int64_t n, float* rays, float* logdepth,
+                                    float* conf, cudaStream_t s);
 cudaError_t launch_check_matches(const int32_t* midx, const EdgeStatic* es, int E, unsigned long long* bad,
                                  long long* edge_valid, cudaStream_t s);
 

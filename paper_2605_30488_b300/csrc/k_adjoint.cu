@@ -1,0 +1,553 @@
+// Adjoint of the refined cost: gradient of L(theta) = E_global(T^K(theta), theta) with
+// respect to per-pixel log-range l_p (X_p = exp(l_p) psi(X_p)) and confidence c_p, where
+// T^K are the poses after K Gauss-Newton iterations (Sec. III-D) and theta feeds the
+// pose-depth alternation of Sec. III-E.
+//
+// Reverse mode through the iterations.  Iteration k maps T^k to T^{k+1} = Exp(tau_k) T^k
+// with tau_k = -A_k^{-1} g_k, A_k = H_k + eps_k I (the attempt that succeeded forward).
+// With a_{k+1} the adjoint of T^{k+1} in left-perturbation coordinates:
+//   tau_bar = phi1(ad_tau)^T a_{k+1}            (left Jacobian of Exp, phi1(X) = sum X^n/(n+1)!)
+//   a' = exp(ad_tau)^T a_{k+1}                  (Exp(tau) Exp(d) = Exp(Ad_{Exp tau} d) Exp(tau))
+//   u = A_k^{-1} tau_bar                        (one more solve with the same factor)
+//   phi(T, theta) = -(u^T g(T, theta) + u^T H(T, theta) tau_k), u and tau_k held fixed
+//   a_k = a' + d phi / dT^k,   theta_bar += d phi / d theta,
+// starting from a_K = dE/dT^K = g(T^K) and theta_bar = dE/dtheta at fixed T^K (the
+// envelope term).  Per match, with W_c = w(r_c) q / sigma_c^2 and J_c the Jacobian row of
+// the relative pose (file k_residual.cu's simplified form), u^T g + u^T H tau is
+//   F = sum_matches sum_c W_c a_c (e_c + b_c),  a = J u~,  b = J tau~,
+// u~ = Ad_{T_i^{-1}} (u_j - u_i), tau~ = Ad_{T_i^{-1}} (tau_j - tau_i) per edge.  The match
+// kernel differentiates F by hand (reverse mode) with respect to the transformed point x,
+// the streamed range ||X_i||, q and (linearly) u~, tau~; it scatters the pixel derivatives
+// and reduces the edge's dF/dxi (relative pose), dF/du~, dF/dtau~.  The edge kernel chains
+// them to the keyframes: dF/dd_j = Ad^T F_xi; dF/dd_i = -Ad^T F_xi + ad_{du}^T Ad^T F_u~ +
+// ad_{dtau}^T Ad^T F_tau~ (Ad_{T_i^{-1}} itself moves with T_i: d(Ad w) = Ad ad_w d_i).
+#include <cuda_fp16.h>
+
+#include <cstdint>
+
+#include "como3r_internal.h"
+
+namespace como3r {
+namespace {
+
+template <int DT, typename R>
+__device__ __forceinline__ void load_point(const void* __restrict__ base, int64_t p, R& x, R& y, R& z, R& c) {
+  if constexpr (DT == 0) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(base) + p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+    x = (R)a.x; y = (R)a.y; z = (R)b.x; c = (R)b.y;
+  } else if constexpr (DT == 1) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(base) + p);
+    x = (R)v.x; y = (R)v.y; z = (R)v.z; c = (R)v.w;
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(base) + 2 * p;
+    const double2 a = __ldg(q), b = __ldg(q + 1);
+    x = (R)a.x; y = (R)a.y; z = (R)b.x; c = (R)b.y;
+  }
+}
+
+template <typename R> __device__ __forceinline__ R inf_of();
+template <> __device__ __forceinline__ float inf_of<float>() { return __int_as_float(0x7f800000); }
+template <> __device__ __forceinline__ double inf_of<double>() { return __longlong_as_double(0x7ff0000000000000LL); }
+
+template <typename R>
+struct V3 {
+  R x, y, z;
+};
+template <typename R> __device__ __forceinline__ V3<R> v3(R x, R y, R z) { return {x, y, z}; }
+template <typename R> __device__ __forceinline__ R dot(V3<R> a, V3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename R> __device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename R> __device__ __forceinline__ V3<R> axpy(R s, V3<R> a, V3<R> b) {
+  return {s * a.x + b.x, s * a.y + b.y, s * a.z + b.z};
+}
+template <typename R> __device__ __forceinline__ V3<R> scale(R s, V3<R> a) { return {s * a.x, s * a.y, s * a.z}; }
+
+constexpr int kAdjRec = kAdjointRecord;  // per item: dF/dxi (7), dF/du~ (7), dF/dtau~ (7)
+
+template <typename R>
+struct AdjConsts {
+  R isr, isd, ivr, ivd, kappa;
+};
+
+// Pixel-gradient accumulation: FP32 atomics into the caller's float arrays (MIXED), FP64
+// atomics into double accumulators (PLAIN).
+__device__ __forceinline__ void acc_add(float* p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void acc_add(double* p, double v) { atomicAdd(p, v); }
+
+// One warp per work item (edge, pixel range); lanes stride the streamed pixels.
+template <typename R, int DT, bool PHI>
+__global__ void __launch_bounds__(256) adjoint_match_kernel(
+    const void* __restrict__ points, const int32_t* __restrict__ midx, const Item* __restrict__ items, int num_items,
+    const EdgeStatic* __restrict__ es, const double* __restrict__ T64, const float* __restrict__ T32,
+    const R* __restrict__ evec, AdjConsts<R> k, R out_scale, R* __restrict__ gl, R* __restrict__ gc,
+    double* __restrict__ rec) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const R inf = inf_of<R>(), th2 = R(1e-24);
+  for (int it = warp; it < num_items; it += nwarps) {
+    const Item item = items[it];
+    const EdgeStatic e = es[item.edge];
+    R T[12];
+#pragma unroll
+    for (int t = 0; t < 12; ++t) {
+      if constexpr (sizeof(R) == 4) T[t] = T32[16 * item.edge + t];
+      else T[t] = T64[12 * item.edge + t];
+    }
+    V3<R> uv{}, uw{}, tv{}, tw{};
+    R uz = R(0), tz = R(0);
+    if (PHI) {
+      const R* ev = evec + 16 * item.edge;
+      uv = v3(ev[0], ev[1], ev[2]); uw = v3(ev[3], ev[4], ev[5]); uz = ev[6];
+      tv = v3(ev[7], ev[8], ev[9]); tw = v3(ev[10], ev[11], ev[12]); tz = ev[13];
+    }
+    R F[kAdjRec];
+#pragma unroll
+    for (int q = 0; q < kAdjRec; ++q) F[q] = R(0);
+    const int32_t* idx = midx + e.idx_off;
+    for (int m = item.begin + lane; m < item.end; m += 32) {
+      const int n = __ldg(idx + m);
+      if (n < 0) continue;
+      R xi, yi, zi, ci, xj, yj, zj, cj;
+      load_point<DT, R>(points, e.pix_i + m, xi, yi, zi, ci);
+      load_point<DT, R>(points, e.pix_j + n, xj, yj, zj, cj);
+      const V3<R> sx = v3(T[0] * xj + T[1] * yj + T[2] * zj, T[3] * xj + T[4] * yj + T[5] * zj,
+                          T[6] * xj + T[7] * yj + T[8] * zj);  // sR X_j = dx / dl_j
+      const V3<R> x = v3(sx.x + T[9], sx.y + T[10], sx.z + T[11]);
+      const R d2 = dot(x, x), di2 = xi * xi + yi * yi + zi * zi, cc = ci * cj;
+      const bool ok = (fmin(d2, di2) > th2) & (fmax(fmax(d2, di2), cc) < inf) & (cc >= R(0));
+      if (!ok) continue;  // skipped forward too
+      const R d = sqrt(d2), rd = R(1) / d, di = sqrt(di2), rdi = R(1) / di;
+      const V3<R> xh = scale(rd, x);
+      const R e0 = xh.x - xi * rdi, e1 = xh.y - yi * rdi, e2 = xh.z - zi * rdi, e3 = d - di;
+      const R q = sqrt(cc), sq = sqrt(q);
+      const R sr = sq * k.isr, sd = sq * k.isd;
+      const R r0 = sr * e0, r1 = sr * e1, r2 = sr * e2, r3 = sd * e3;
+      const R a0 = fabs(r0), a1 = fabs(r1), a2 = fabs(r2), a3 = fabs(r3);
+      const R w0 = a0 > k.kappa ? k.kappa / a0 : R(1);
+      const R w1 = a1 > k.kappa ? k.kappa / a1 : R(1);
+      const R w2 = a2 > k.kappa ? k.kappa / a2 : R(1);
+      const R w3 = a3 > k.kappa ? k.kappa / a3 : R(1);
+      V3<R> xhb;       // d/d xh
+      R db, eb3;       // d/d d, d/d e_d
+      R dci, dcj;      // d/d c_i, d/d c_j
+      if (!PHI) {
+        // f = sum_c rho(r_c): rho' = w r
+        const R rb0 = w0 * r0, rb1 = w1 * r1, rb2 = w2 * r2, rb3 = w3 * r3;
+        xhb = v3(rb0 * sr, rb1 * sr, rb2 * sr);
+        eb3 = rb3 * sd;
+        db = eb3;
+        // dq/dc_i = q / (2 c_i) and dr_c/dq = r_c / (2q): df/dc_i = sum_c w_c r_c^2 / (4 c_i)
+        const R s4 = R(0.25) * (rb0 * r0 + rb1 * r1 + rb2 * r2 + rb3 * r3);
+        dci = ci > R(0) ? s4 / ci : R(0);
+        dcj = cj > R(0) ? s4 / cj : R(0);
+      } else {
+        const R W0 = w0 * q * k.ivr, W1 = w1 * q * k.ivr, W2 = w2 * q * k.ivr, W3 = w3 * q * k.ivd;
+        // a = J u~ (ray rows P u_v + u_w x xh, range row xh.u_v + d u_z), b = J tau~
+        const R al = dot(xh, uv), be = dot(xh, tv);
+        const V3<R> av = scale(rd, axpy(-al, xh, uv)), bv = scale(rd, axpy(-be, xh, tv));
+        const V3<R> ar = axpy(R(1), av, cross(uw, xh)), br = axpy(R(1), bv, cross(tw, xh));
+        const R ad = al + d * uz, bd = be + d * tz;
+        const R s0 = e0 + br.x, s1 = e1 + br.y, s2 = e2 + br.z, s3 = e3 + bd;
+        const R h0 = ar.x * s0, h1 = ar.y * s1, h2 = ar.z * s2, h3 = ad * s3;
+        // W depends on q directly and through r (outer Huber region: w = kappa / |r|)
+        const bool o0 = a0 > k.kappa, o1 = a1 > k.kappa, o2 = a2 > k.kappa, o3 = a3 > k.kappa;
+        const R qb = (o0 ? R(0.5) : R(1)) * h0 * w0 * k.ivr + (o1 ? R(0.5) : R(1)) * h1 * w1 * k.ivr +
+                     (o2 ? R(0.5) : R(1)) * h2 * w2 * k.ivr + (o3 ? R(0.5) : R(1)) * h3 * w3 * k.ivd;
+        const R eb0 = W0 * ar.x - (o0 ? h0 * W0 / r0 * sr : R(0));
+        const R eb1 = W1 * ar.y - (o1 ? h1 * W1 / r1 * sr : R(0));
+        const R eb2 = W2 * ar.z - (o2 ? h2 * W2 / r2 * sr : R(0));
+        eb3 = W3 * ad - (o3 ? h3 * W3 / r3 * sd : R(0));
+        const V3<R> abr = v3(W0 * s0, W1 * s1, W2 * s2), bbr = v3(W0 * ar.x, W1 * ar.y, W2 * ar.z);
+        const R ab3 = W3 * s3, bb3 = W3 * ad;
+        xhb = v3(eb0, eb1, eb2);
+        db = eb3;
+        // through a_ray = (u_v - xh al) / d + u_w x xh and a_d = al + d u_z
+        db += -rd * dot(abr, av) + ab3 * uz;
+        xhb = axpy(-al * rd, abr, xhb);
+        xhb = axpy(-rd * dot(abr, xh) + ab3, uv, xhb);
+        xhb = axpy(R(1), cross(abr, uw), xhb);
+        // the same through b with tau~
+        db += -rd * dot(bbr, bv) + bb3 * tz;
+        xhb = axpy(-be * rd, bbr, xhb);
+        xhb = axpy(-rd * dot(bbr, xh) + bb3, tv, xhb);
+        xhb = axpy(R(1), cross(bbr, tw), xhb);
+        dci = ci > R(0) ? R(0.5) * qb * q / ci : R(0);
+        dcj = cj > R(0) ? R(0.5) * qb * q / cj : R(0);
+        // dF/du~ = sum_c abar_c J_c, dF/dtau~ = sum_c bbar_c J_c with
+        // sum_c beta_c J_c = [P beta_r + beta_d xh, xh x beta_r, beta_d d]
+        const V3<R> pa = axpy(ab3, xh, scale(rd, axpy(-dot(xh, abr), xh, abr)));
+        const V3<R> ca = cross(xh, abr);
+        const V3<R> pb = axpy(bb3, xh, scale(rd, axpy(-dot(xh, bbr), xh, bbr)));
+        const V3<R> cb = cross(xh, bbr);
+        F[7] += pa.x; F[8] += pa.y; F[9] += pa.z; F[10] += ca.x; F[11] += ca.y; F[12] += ca.z; F[13] += ab3 * d;
+        F[14] += pb.x; F[15] += pb.y; F[16] += pb.z; F[17] += cb.x; F[18] += cb.y; F[19] += cb.z; F[20] += bb3 * d;
+      }
+      // xh = x / d, d = ||x||: x_bar = (xh_bar - xh (xh . xh_bar)) / d + d_bar xh
+      const V3<R> xb = axpy(db, xh, scale(rd, axpy(-dot(xh, xhb), xh, xhb)));
+      if (PHI) {
+        const V3<R> xc = cross(x, xb);
+        F[0] += xb.x; F[1] += xb.y; F[2] += xb.z; F[3] += xc.x; F[4] += xc.y; F[5] += xc.z; F[6] += dot(xb, x);
+      }
+      // dl_j: dx/dl_j = sR X_j; dl_i: d||X_i||/dl_i = ||X_i|| and e_d = d - ||X_i||
+      acc_add(gl + e.pix_j + n, out_scale * dot(xb, sx));
+      acc_add(gl + e.pix_i + m, -out_scale * eb3 * di);
+      acc_add(gc + e.pix_i + m, out_scale * dci);
+      acc_add(gc + e.pix_j + n, out_scale * dcj);
+    }
+    if (PHI) {
+#pragma unroll
+      for (int q = 0; q < kAdjRec; ++q) {
+        R v = F[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        F[q] = v;
+      }
+      double mine = 0.0;
+#pragma unroll
+      for (int q = 0; q < kAdjRec; ++q)
+        if (lane == q) mine = (double)F[q];
+      if (lane < kAdjRec) rec[(int64_t)it * kAdjRec + lane] = mine;
+    }
+  }
+}
+
+// ad_xi^T y for xi = (v, w, z) with ad_xi = [[w^ + z I, v^, -v], [0, w^, 0], [0, 0, 0]].
+__device__ __forceinline__ void ad_transpose_apply(const double* xi, const double* y, double* out) {
+  const double v0 = xi[0], v1 = xi[1], v2 = xi[2], w0 = xi[3], w1 = xi[4], w2 = xi[5], z = xi[6];
+  const double y0 = y[0], y1 = y[1], y2 = y[2], q0 = y[3], q1 = y[4], q2 = y[5];
+  // (w^ + z I)^T y_v = y_v x w + z y_v
+  out[0] = (y1 * w2 - y2 * w1) + z * y0;
+  out[1] = (y2 * w0 - y0 * w2) + z * y1;
+  out[2] = (y0 * w1 - y1 * w0) + z * y2;
+  // (v^)^T y_v + (w^)^T y_w = y_v x v + y_w x w
+  out[3] = (y1 * v2 - y2 * v1) + (q1 * w2 - q2 * w1);
+  out[4] = (y2 * v0 - y0 * v2) + (q2 * w0 - q0 * w2);
+  out[5] = (y0 * v1 - y1 * v0) + (q0 * w1 - q1 * w0);
+  out[6] = -(v0 * y0 + v1 * y1 + v2 * y2);
+}
+
+// Per edge: Ad-rotated adjoint and step differences for the match kernel,
+// u~ = Ad (u_j - u_i), tau~ = Ad (tau_j - tau_i), stored in R (16 per edge).
+template <typename R>
+__global__ void adjoint_edge_prep_kernel(const EdgeStatic* __restrict__ es, int E, const double* __restrict__ Ad,
+                                         const double* __restrict__ u, const double* __restrict__ tau,
+                                         R* __restrict__ evec) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const int i = es[e].i, j = es[e].j;
+  double du[7], dt[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    du[k] = u[7 * j + k] - u[7 * i + k];
+    dt[k] = tau[7 * j + k] - tau[7 * i + k];
+  }
+  const double* A = Ad + 49 * (int64_t)e;
+  for (int r = 0; r < 7; ++r) {
+    double su = 0.0, st = 0.0;
+    for (int c = 0; c < 7; ++c) {
+      su += A[7 * r + c] * du[c];
+      st += A[7 * r + c] * dt[c];
+    }
+    evec[16 * e + r] = (R)su;
+    evec[16 * e + 7 + r] = (R)st;
+  }
+  evec[16 * e + 14] = R(0);
+  evec[16 * e + 15] = R(0);
+}
+
+// Per edge: fixed-order FP64 sum of the item records, then the keyframe terms
+// out[e][0..6] = dF/dd_i, out[e][7..13] = dF/dd_j.
+__global__ void adjoint_edge_kernel(const double* __restrict__ rec, const int32_t* __restrict__ item_off, int E,
+                                    const EdgeStatic* __restrict__ es, const double* __restrict__ Ad,
+                                    const double* __restrict__ u, const double* __restrict__ tau,
+                                    double* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double F[kAdjRec];
+  for (int q = 0; q < kAdjRec; ++q) F[q] = 0.0;
+  for (int it = item_off[e]; it < item_off[e + 1]; ++it)
+    for (int q = 0; q < kAdjRec; ++q) F[q] += rec[(int64_t)it * kAdjRec + q];
+  const double* A = Ad + 49 * (int64_t)e;
+  double yx[7], yu[7], yt[7];
+  for (int c = 0; c < 7; ++c) {
+    double a = 0.0, b = 0.0, d = 0.0;
+    for (int r = 0; r < 7; ++r) {
+      a += A[7 * r + c] * F[r];
+      b += A[7 * r + c] * F[7 + r];
+      d += A[7 * r + c] * F[14 + r];
+    }
+    yx[c] = a;
+    yu[c] = b;
+    yt[c] = d;
+  }
+  const int i = es[e].i, j = es[e].j;
+  double du[7], dt[7], pu[7], pt[7];
+  for (int k = 0; k < 7; ++k) {
+    du[k] = u[7 * j + k] - u[7 * i + k];
+    dt[k] = tau[7 * j + k] - tau[7 * i + k];
+  }
+  ad_transpose_apply(du, yu, pu);
+  ad_transpose_apply(dt, yt, pt);
+  for (int k = 0; k < 7; ++k) {
+    out[14 * e + k] = -yx[k] + pu[k] + pt[k];
+    out[14 * e + 7 + k] = yx[k];
+  }
+}
+
+// 7x7 helpers (row-major, one thread).
+__device__ void mat7_mul(const double* A, const double* B, double* C) {
+  for (int r = 0; r < 7; ++r)
+    for (int c = 0; c < 7; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < 7; ++k) s += A[7 * r + k] * B[7 * k + c];
+      C[7 * r + c] = s;
+    }
+}
+
+// Per keyframe: a' = exp(ad_tau)^T a and rhs = -phi1(ad_tau)^T a (so the solve returns
+// u = A^{-1} tau_bar); frozen keyframes get zeros.  exp and phi1 of X = ad_tau by scaling
+// and squaring (Higham, 2005): X / 2^s with ||X / 2^s|| <= 1/2, a 20-term Taylor series
+// of phi1 (Horner), exp = I + X phi1, then s doublings phi1(2X) = phi1(X)(exp(X) + I)/2,
+// exp(2X) = exp(X)^2.
+__global__ void adjoint_keyframe_kernel(const double* __restrict__ a, const double* __restrict__ tau,
+                                        const uint8_t* __restrict__ frozen, int N, double* __restrict__ a_out,
+                                        double* __restrict__ rhs) {
+  const int kf = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kf >= N) return;
+  if (frozen[kf]) {
+    for (int k = 0; k < 7; ++k) a_out[7 * kf + k] = rhs[7 * kf + k] = 0.0;
+    return;
+  }
+  const double* t = tau + 7 * kf;
+  double X[49] = {0};
+  // ad_tau = [[w^ + z I, v^, -v], [0, w^, 0], [0, 0, 0]]
+  const double v0 = t[0], v1 = t[1], v2 = t[2], w0 = t[3], w1 = t[4], w2 = t[5], z = t[6];
+  const double W[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+  const double V[9] = {0.0, -v2, v1, v2, 0.0, -v0, -v1, v0, 0.0};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      X[7 * r + c] = W[3 * r + c] + (r == c ? z : 0.0);
+      X[7 * r + 3 + c] = V[3 * r + c];
+      X[7 * (3 + r) + 3 + c] = W[3 * r + c];
+    }
+  X[6] = -v0;
+  X[13] = -v1;
+  X[20] = -v2;
+  double nrm = 0.0;
+  for (int r = 0; r < 7; ++r) {
+    double s = 0.0;
+    for (int c = 0; c < 7; ++c) s += fabs(X[7 * r + c]);
+    nrm = fmax(nrm, s);
+  }
+  int sq = 0;
+  while (nrm > 0.5 && sq < 64) {
+    nrm *= 0.5;
+    ++sq;
+  }
+  const double f = ldexp(1.0, -sq);
+  for (int q = 0; q < 49; ++q) X[q] *= f;
+  double P[49], E[49], Tm[49];
+  for (int q = 0; q < 49; ++q) P[q] = (q % 8 == 0) ? 1.0 : 0.0;
+  for (int n = 20; n >= 1; --n) {  // P <- I + X P / (n + 1)
+    mat7_mul(X, P, Tm);
+    const double inv = 1.0 / (double)(n + 1);
+    for (int q = 0; q < 49; ++q) P[q] = ((q % 8 == 0) ? 1.0 : 0.0) + Tm[q] * inv;
+  }
+  mat7_mul(X, P, E);
+  for (int q = 0; q < 49; q += 8) E[q] += 1.0;
+  for (int s = 0; s < sq; ++s) {
+    for (int q = 0; q < 49; q += 8) E[q] += 1.0;  // E + I
+    mat7_mul(P, E, Tm);
+    for (int q = 0; q < 49; q += 8) E[q] -= 1.0;
+    for (int q = 0; q < 49; ++q) P[q] = 0.5 * Tm[q];
+    mat7_mul(E, E, Tm);
+    for (int q = 0; q < 49; ++q) E[q] = Tm[q];
+  }
+  const double* ak = a + 7 * kf;
+  for (int c = 0; c < 7; ++c) {
+    double se = 0.0, sp = 0.0;
+    for (int r = 0; r < 7; ++r) {
+      se += E[7 * r + c] * ak[r];
+      sp += P[7 * r + c] * ak[r];
+    }
+    a_out[7 * kf + c] = se;
+    rhs[7 * kf + c] = -sp;
+  }
+}
+
+// Per keyframe: a = a' - sum over its edges of dF/dd (phi = -F), in the fixed list order
+// of the assembly (entries edge * 2 + [keyframe is the streamed side i]); or, when
+// `a_prime` is null, the start a = scale g(T^K).  Frozen keyframes get zeros.
+__global__ void adjoint_gather_kernel(const double* __restrict__ a_prime, const double* __restrict__ edge_out,
+                                      const int32_t* __restrict__ kf_contrib_off,
+                                      const int32_t* __restrict__ kf_contrib, const uint8_t* __restrict__ frozen,
+                                      int N, const double* __restrict__ gvec, double scale, double* __restrict__ a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= 7 * N) return;
+  const int kf = x / 7, k = x % 7;
+  if (frozen[kf]) {
+    a[x] = 0.0;
+    return;
+  }
+  if (!a_prime) {
+    a[x] = scale * gvec[x];
+    return;
+  }
+  double s = a_prime[x];
+  for (int q = kf_contrib_off[kf]; q < kf_contrib_off[kf + 1]; ++q) {
+    const int c = kf_contrib[q];
+    s -= edge_out[14 * (c >> 1) + ((c & 1) ? 0 : 7) + k];
+  }
+  a[x] = s;
+}
+
+__global__ void to_float_kernel(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+    dst[x] = (float)src[x];
+}
+
+// X_p = exp(l_p) r_p, confidence c_p, packed (x, y, z, c) in the storage type.
+template <int DT>
+__global__ void points_from_logdepth_kernel(const float* __restrict__ rays, const float* __restrict__ logdepth,
+                                            const float* __restrict__ conf, int64_t n, void* __restrict__ out) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const float s = expf(logdepth[p]);
+    const float x = s * rays[3 * p], y = s * rays[3 * p + 1], z = s * rays[3 * p + 2], c = conf[p];
+    if constexpr (DT == 0) {
+      __half2* o = reinterpret_cast<__half2*>(out) + 2 * p;
+      o[0] = __floats2half2_rn(x, y);
+      o[1] = __floats2half2_rn(z, c);
+    } else if constexpr (DT == 1) {
+      reinterpret_cast<float4*>(out)[p] = make_float4(x, y, z, c);
+    } else {
+      double* o = reinterpret_cast<double*>(out) + 4 * p;
+      o[0] = (double)x; o[1] = (double)y; o[2] = (double)z; o[3] = (double)c;
+    }
+  }
+}
+
+// Unit ray, log-range and confidence of every stored point (inverse of the above; a
+// point with zero or non-finite range gets ray 0 and log-range -inf).
+template <int DT>
+__global__ void rays_from_points_kernel(const void* __restrict__ points, int64_t n, float* __restrict__ rays,
+                                        float* __restrict__ logdepth, float* __restrict__ conf) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    double x, y, z, c;
+    load_point<DT, double>(points, p, x, y, z, c);
+    const double r = sqrt(x * x + y * y + z * z);
+    const bool ok = r > 0.0 && r < 1e300;
+    rays[3 * p] = ok ? (float)(x / r) : 0.f;
+    rays[3 * p + 1] = ok ? (float)(y / r) : 0.f;
+    rays[3 * p + 2] = ok ? (float)(z / r) : 0.f;
+    logdepth[p] = ok ? (float)log(r) : -__int_as_float(0x7f800000);
+    conf[p] = (float)c;
+  }
+}
+
+int grid_for(int64_t n, int block) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t need = (n + block - 1) / block;
+  return (int)(need < (int64_t)sms * 8 ? (need > 0 ? need : 1) : (int64_t)sms * 8);
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint_match(int mode, int dtype, bool phi, const void* points, const int32_t* midx,
+                                 const Item* items, int num_items, const EdgeStatic* es, const double* T64,
+                                 const float* T32, const void* evec, RobustParams rp, double out_scale, void* gl,
+                                 void* gc, double* rec, cudaStream_t s) {
+  if (num_items == 0) return cudaSuccess;
+  const int block = 256;
+  const int grid = grid_for((int64_t)num_items * 32, block);
+#define COMO3R_ADJ(R, DT)                                                                                       \
+  do {                                                                                                        \
+    AdjConsts<R> k{(R)rp.inv_sigma_ray, (R)rp.inv_sigma_dist, (R)rp.inv_var_ray, (R)rp.inv_var_dist,          \
+                   (R)rp.kappa};                                                                              \
+    if (phi)                                                                                                  \
+      adjoint_match_kernel<R, DT, true><<<grid, block, 0, s>>>(points, midx, items, num_items, es, T64, T32,  \
+                                                               (const R*)evec, k, (R)out_scale, (R*)gl,       \
+                                                               (R*)gc, rec);                                  \
+    else                                                                                                      \
+      adjoint_match_kernel<R, DT, false><<<grid, block, 0, s>>>(points, midx, items, num_items, es, T64, T32, \
+                                                                (const R*)evec, k, (R)out_scale, (R*)gl,      \
+                                                                (R*)gc, rec);                                 \
+  } while (0)
+  if (mode == 1) {
+    if (dtype == 0) COMO3R_ADJ(float, 0);
+    else if (dtype == 1) COMO3R_ADJ(float, 1);
+    else COMO3R_ADJ(float, 2);
+  } else {
+    if (dtype == 0) COMO3R_ADJ(double, 0);
+    else if (dtype == 1) COMO3R_ADJ(double, 1);
+    else COMO3R_ADJ(double, 2);
+  }
+#undef COMO3R_ADJ
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_edge_prep(int mode, const EdgeStatic* es, int E, const double* Ad, const double* u,
+                                     const double* tau, void* evec, cudaStream_t s) {
+  if (E == 0) return cudaSuccess;
+  const int grid = (E + 127) / 128;
+  if (mode == 1)
+    adjoint_edge_prep_kernel<float><<<grid, 128, 0, s>>>(es, E, Ad, u, tau, (float*)evec);
+  else
+    adjoint_edge_prep_kernel<double><<<grid, 128, 0, s>>>(es, E, Ad, u, tau, (double*)evec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_edge(const double* rec, const int32_t* item_off, int E, const EdgeStatic* es,
+                                const double* Ad, const double* u, const double* tau, double* out, cudaStream_t s) {
+  if (E == 0) return cudaSuccess;
+  adjoint_edge_kernel<<<(E + 63) / 64, 64, 0, s>>>(rec, item_off, E, es, Ad, u, tau, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_keyframe(const double* a, const double* tau, const uint8_t* frozen, int N, double* a_out,
+                                    double* rhs, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  adjoint_keyframe_kernel<<<(N + 31) / 32, 32, 0, s>>>(a, tau, frozen, N, a_out, rhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_gather(const double* a_prime, const double* edge_out, const int32_t* kf_contrib_off,
+                                  const int32_t* kf_contrib, const uint8_t* frozen, int N, const double* gvec,
+                                  double scale, double* a, cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  adjoint_gather_kernel<<<(7 * N + 127) / 128, 128, 0, s>>>(a_prime, edge_out, kf_contrib_off, kf_contrib, frozen,
+                                                            N, gvec, scale, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_float(const double* src, float* dst, int64_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  to_float_kernel<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_points_from_logdepth(int dtype, const float* rays, const float* logdepth, const float* conf,
+                                        int64_t n, void* out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int grid = grid_for(n, 256);
+  if (dtype == 0) points_from_logdepth_kernel<0><<<grid, 256, 0, s>>>(rays, logdepth, conf, n, out);
+  else if (dtype == 1) points_from_logdepth_kernel<1><<<grid, 256, 0, s>>>(rays, logdepth, conf, n, out);
+  else points_from_logdepth_kernel<2><<<grid, 256, 0, s>>>(rays, logdepth, conf, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rays_from_points(int dtype, const void* points, int64_t n, float* rays, float* logdepth,
+                                    float* conf, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int grid = grid_for(n, 256);
+  if (dtype == 0) rays_from_points_kernel<0><<<grid, 256, 0, s>>>(points, n, rays, logdepth, conf);
+  else if (dtype == 1) rays_from_points_kernel<1><<<grid, 256, 0, s>>>(points, n, rays, logdepth, conf);
+  else rays_from_points_kernel<2><<<grid, 256, 0, s>>>(points, n, rays, logdepth, conf);
+  return cudaGetLastError();
+}
+
+}  // namespace como3r

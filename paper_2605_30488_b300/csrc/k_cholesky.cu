@@ -232,7 +232,8 @@ __device__ __forceinline__ void stage(T* dst, const T* src, int n, int tid) {
 template <bool SMEM>
 __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     SolverPlan P, const double* __restrict__ A, double* Lg, double* Sg, const double* __restrict__ gvec,
-    double* __restrict__ tau, double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn) {
+    double* __restrict__ tau, double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
+    const GraphInfoDev* __restrict__ fixed) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ int s_fail;
   const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -282,10 +283,18 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
   const double* Ag = A + (int64_t)sbase * 49;
   const int* col_kf = P.col_kf + cbase;
 
+  // `fixed` (adjoint re-solves): exactly the attempt that succeeded in the recorded
+  // forward solve, or a zero result where that solve failed
+  int attempt = 0, last = max_attempts;
+  if (fixed) {
+    if (!fixed[g].solved) last = 0;
+    attempt = fixed[g].attempts - 1;
+    if (last) last = attempt + 1;
+  }
   bool ok = false;
-  int attempt = 0;
   double pow100 = 1.0;  // 100^attempt, exact in FP64
-  for (; attempt < max_attempts; ++attempt, pow100 *= 100.0) {
+  for (int r = 0; r < attempt; ++r) pow100 *= 100.0;
+  for (; attempt < last; ++attempt, pow100 *= 100.0) {
     const double eps = eps0 * pow100;
     for (int64_t x = tid; x < (int64_t)nslot * 49; x += kSolveThreads) C.L[x] = Ag[x];
     __syncthreads();
@@ -347,14 +356,15 @@ cudaError_t factor_solve_prepare(size_t smem_bytes) {
 
 cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t smem_bytes, const double* A,
                                 double* L, double* colscratch, const double* gvec, double* tau, double lambda,
-                                double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s) {
+                                double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s,
+                                const GraphInfoDev* fixed) {
   if (G <= 0) return cudaSuccess;
   if (smem) {
     factor_solve_kernel<true><<<G, kSolveThreads, smem_bytes, s>>>(plan, A, L, colscratch, gvec, tau, lambda, eps0,
-                                                                   max_attempts, ginfo, warn);
+                                                                   max_attempts, ginfo, warn, fixed);
   } else {
     factor_solve_kernel<false><<<G, kSolveThreads, 0, s>>>(plan, A, L, colscratch, gvec, tau, lambda, eps0,
-                                                           max_attempts, ginfo, warn);
+                                                           max_attempts, ginfo, warn, fixed);
   }
   return cudaGetLastError();
 }
