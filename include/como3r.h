@@ -226,6 +226,7 @@ int64_t como3r_last_launch_count(como3r_graph_t graph);
 #define COMO3R_STAT_GRID 12          /* K1 CTAs */
 #define COMO3R_STAT_SMEM_SOLVE 13    /* 1 if the factor of every graph fits in shared memory */
 #define COMO3R_STAT_ND_GRAPHS 14     /* graphs ordered by nested dissection (others: minimum degree) */
+#define COMO3R_STAT_K1_STALLS 15     /* bounded waits of the TMA-staged K1 that gave up (process-wide; 0 = healthy) */
 #define COMO3R_STAT_COUNT 16
 int como3r_graph_stats(como3r_graph_t graph, int64_t* stats /* [COMO3R_STAT_COUNT] */);
 

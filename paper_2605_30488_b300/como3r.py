@@ -27,7 +27,7 @@ PLAIN_FP64, MIXED = 0, 1
 VJP_UNROLLED, VJP_ENVELOPE = 0, 1
 EDGE_RECORD = 64
 STAT_NAMES = ["graphs", "keyframes", "edges", "items", "columns", "blocks", "fill", "updates", "levels",
-              "valid", "chunk", "block", "grid", "smem_solve", "nd_graphs", "r15"]
+              "valid", "chunk", "block", "grid", "smem_solve", "nd_graphs", "k1_stalls"]
 
 STAGE_NAMES = ["edge_prep", "residual_reduce", "edge_reduce", "assemble", "factor_solve", "retract", "iteration"]
 

@@ -9,10 +9,12 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/como3r.h"
@@ -64,6 +66,10 @@ struct como3r_graph {
   EdgeStatic* d_es = nullptr;
   Item* d_items = nullptr;
   int32_t* d_item_off = nullptr;
+  // balanced K1 schedule (rebuilt on the device when the match indices change)
+  int32_t *d_counts = nullptr, *d_wstart = nullptr, *d_wseg = nullptr, *d_seg_off = nullptr;
+  long long* d_cum = nullptr;
+  int max_warps = 0, k1_wv = 0, k1_wp = 1;
   double *d_T64 = nullptr, *d_Ad = nullptr, *d_partials = nullptr;
   float* d_T32 = nullptr;
   double *d_edge_M = nullptr, *d_edge_b = nullptr, *d_edge_cost = nullptr, *d_edge_skip = nullptr;
@@ -135,13 +141,40 @@ bool is_device_pointer(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+WarpSched sched(const como3r_graph* g) { return WarpSched{g->d_wstart, g->d_wseg}; }
+
+// Balanced K1 schedule for the current items and a grid of `grid` CTAs.
+int rebuild_schedule(como3r_graph* g, int cfg, int grid, int wv, int wp, cudaStream_t s) {
+  const int W = grid * residual_reduce_workers_per_cta(cfg);
+  if (W > g->max_warps) return set_error(COMO3R_ERR_UNSUPPORTED, "K1 grid larger than the schedule buffers");
+  CK(launch_schedule(g->midx, g->d_es, g->d_items, g->num_items, g->d_item_off, g->plan.E, W, wv, wp, g->d_counts,
+                     g->d_cum, g->d_wstart, g->d_wseg, g->d_seg_off, s),
+     "schedule");
+  return COMO3R_OK;
+}
+
+// Cost-weight candidates (valid match, pixel) of a launch configuration's schedule; the
+// environment variable COMO3R_K1_WEIGHTS=<wv>,<wp> replaces them (studies).
+std::vector<std::pair<int, int>> weight_candidates(int cfg) {
+  if (const char* w = getenv("COMO3R_K1_WEIGHTS")) {
+    int a = 0, b = 0;
+    if (sscanf(w, "%d,%d", &a, &b) == 2 && a >= 0 && b >= 0 && a + b > 0) return {{a, b}};
+  }
+  int wv = 0, wp = 1;
+  residual_reduce_cost_weights(cfg, wv, wp);
+  std::vector<std::pair<int, int>> c{{wv, wp}};
+  for (int a : {0, 1, 2, 3, 5})
+    if (a != wv || wp != 1) c.push_back({a, 1});
+  return c;
+}
+
 int enqueue_linearize(como3r_graph* g, cudaStream_t s, double* cost_hist, const int* iter, double* edge_rec) {
   const HostPlan& p = g->plan;
   CK(launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, s), "edge_prep");
   CK(launch_residual_reduce(p.mode, p.dtype, g->k1_cfg, g->k1_grid, g->points, g->midx, g->d_items, g->num_items,
-                            g->d_es, g->d_T64, g->d_T32, g->rp, g->d_partials, s),
+                            g->d_es, g->d_T64, g->d_T32, g->rp, g->d_partials, sched(g), s),
      "residual_reduce");
-  CK(launch_edge_reduce(p.mode, g->d_partials, g->d_item_off, p.E, g->d_Ad, g->d_edge_M, g->d_edge_b, g->d_edge_cost,
+  CK(launch_edge_reduce(p.mode, g->d_partials, g->d_seg_off, p.E, g->d_Ad, g->d_edge_M, g->d_edge_b, g->d_edge_cost,
                         g->d_edge_skip, edge_rec, g->d_edge_valid, s),
      "edge_reduce");
   const int nslots = p.slot_begin.back();
@@ -234,8 +267,9 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   std::vector<int32_t> item_off;
   build_items(p, kChunks[0], items, item_off);
   g->max_items = (int)items.size();
+  g->max_warps = g->sms * (2048 / 32);  // the most warps a persistent grid can hold
   // the shared-memory-staged residual kernel copies match indices in 16-byte pieces
-  g->idx_rows_aligned = reinterpret_cast<uintptr_t>(g->midx) % 16 == 0;
+  g->idx_rows_aligned = reinterpret_cast<uintptr_t>(g->midx) % 16 == 0 && reinterpret_cast<uintptr_t>(g->points) % 16 == 0;
   for (int k = 0; k < p.N; ++k)
     g->idx_rows_aligned = g->idx_rows_aligned && (p.npix[k] % 4 == 0) && p.npix[k] <= (1 << 22);
   const int E = p.E, N = p.N, G = p.G;
@@ -243,7 +277,10 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   if ((rc = upload(g, &g->d_es, p.es)) || (rc = upload(g, &g->d_items, items)) ||
       (rc = upload(g, &g->d_item_off, item_off)) || (rc = dalloc(g, &g->d_T64, (size_t)E * 12)) ||
       (rc = dalloc(g, &g->d_T32, (size_t)E * 16)) || (rc = dalloc(g, &g->d_Ad, (size_t)E * 49)) ||
-      (rc = dalloc(g, &g->d_partials, (size_t)g->max_items * kPartial)) ||
+      (rc = dalloc(g, &g->d_partials, (size_t)std::max(g->max_items, g->max_warps + E) * kPartial)) ||
+      (rc = dalloc(g, &g->d_counts, (size_t)g->max_items)) || (rc = dalloc(g, &g->d_cum, (size_t)g->max_items + 1)) ||
+      (rc = dalloc(g, &g->d_wstart, (size_t)g->max_warps + 1)) || (rc = dalloc(g, &g->d_wseg, (size_t)g->max_warps)) ||
+      (rc = dalloc(g, &g->d_seg_off, (size_t)E + 1)) ||
       (rc = dalloc(g, &g->d_edge_M, (size_t)E * 49)) || (rc = dalloc(g, &g->d_edge_b, (size_t)E * 7)) ||
       (rc = dalloc(g, &g->d_edge_cost, E)) || (rc = dalloc(g, &g->d_edge_skip, E)) ||
       (rc = dalloc(g, &g->d_edge_valid, E)) || (rc = upload(g, &g->d_slot_kf_r, p.slot_kf_r)) ||
@@ -320,6 +357,10 @@ int autotune_k1(como3r_graph* g) {
     build_items(p, chunk, items, item_off);
     CK(cudaMemcpyAsync(g->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, g->stream),
        "tune items");
+    CK(cudaMemcpyAsync(g->d_item_off, item_off.data(), sizeof(int32_t) * item_off.size(), cudaMemcpyHostToDevice,
+                       g->stream),
+       "tune items");
+    g->num_items = (int)items.size();
     for (int cfg = 0; cfg < residual_reduce_num_cfgs(p.mode); ++cfg) {
       const int need = residual_reduce_cfg_chunk(cfg);
       if (need && (chunk != need || !g->idx_rows_aligned)) continue;
@@ -329,28 +370,34 @@ int autotune_k1(como3r_graph* g) {
       if (occ <= 0) continue;
       const int warps_per_cta = residual_reduce_block() / 32;
       const int grid = std::max(1, std::min(g->sms * std::max(occ, 1), ((int)items.size() + warps_per_cta - 1) / warps_per_cta));
-      float tot = 0.f;
-      for (int r = 0; r < 4; ++r) {
-        cudaError_t err = cudaEventRecord(e0, g->stream);
-        if (!err) err = launch_residual_reduce(p.mode, p.dtype, cfg, grid, g->points, g->midx, g->d_items,
-                                               (int)items.size(), g->d_es, g->d_T64, g->d_T32, g->rp, g->d_partials,
-                                               g->stream);
-        if (!err) err = cudaEventRecord(e1, g->stream);
-        if (!err) err = cudaEventSynchronize(e1);
-        if (err) {
-          rc = cuda_error(err, "autotune");
-          break;
+      for (const auto& wt : weight_candidates(cfg)) {
+        if ((rc = rebuild_schedule(g, cfg, grid, wt.first, wt.second, g->stream))) break;
+        float tot = 0.f;
+        for (int r = 0; r < 4; ++r) {
+          cudaError_t err = cudaEventRecord(e0, g->stream);
+          if (!err) err = launch_residual_reduce(p.mode, p.dtype, cfg, grid, g->points, g->midx, g->d_items,
+                                                 (int)items.size(), g->d_es, g->d_T64, g->d_T32, g->rp, g->d_partials,
+                                                 sched(g), g->stream);
+          if (!err) err = cudaEventRecord(e1, g->stream);
+          if (!err) err = cudaEventSynchronize(e1);
+          if (err) {
+            rc = cuda_error(err, "autotune");
+            break;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (r > 0) tot += ms;  // first run warms caches and clocks
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (r > 0) tot += ms;  // first run warms caches and clocks
+        if (rc) break;
+        if (tot / 3 < best) {
+          best = tot / 3;
+          best_chunk = chunk;
+          best_cfg = cfg;
+          g->k1_wv = wt.first;
+          g->k1_wp = wt.second;
+        }
       }
       if (rc) break;
-      if (tot / 3 < best) {
-        best = tot / 3;
-        best_chunk = chunk;
-        best_cfg = cfg;
-      }
     }
   }
   cudaEventDestroy(e0);
@@ -369,6 +416,7 @@ int autotune_k1(como3r_graph* g) {
   const int occ = residual_reduce_max_blocks_per_sm(p.mode, p.dtype, best_cfg);
   const int warps_per_cta = residual_reduce_block() / 32;
   g->k1_grid = std::max(1, std::min(g->sms * std::max(occ, 1), (g->num_items + warps_per_cta - 1) / warps_per_cta));
+  if ((rc = rebuild_schedule(g, g->k1_cfg, g->k1_grid, g->k1_wv, g->k1_wp, g->stream))) return rc;
   CK(cudaStreamSynchronize(g->stream), "tune sync");
   return COMO3R_OK;
 }
@@ -619,8 +667,12 @@ int como3r_update_inputs(como3r_graph_t g, const void* points_conf, const int32_
   if (!g->own_points) return set_error(COMO3R_ERR_INVALID_ARG, "graph was created with copy_inputs = 0");
   if (points_conf)
     CK(cudaMemcpyAsync(g->own_points, points_conf, g->points_bytes, cudaMemcpyDefault, g->stream), "copy points");
-  if (match_idx && g->idx_bytes)
+  if (match_idx && g->idx_bytes) {
     CK(cudaMemcpyAsync(g->own_midx, match_idx, g->idx_bytes, cudaMemcpyDefault, g->stream), "copy matches");
+    // new valid counts: rebalance K1 (device only, no synchronisation)
+    const int rc = rebuild_schedule(g, g->k1_cfg, g->k1_grid, g->k1_wv, g->k1_wp, g->stream);
+    if (rc) return rc;
+  }
   return COMO3R_OK;
 }
 
@@ -639,9 +691,10 @@ int como3r_time_stages(como3r_graph_t g, const double* poses, int32_t reps, floa
     if (!err) err = launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, s);
     if (!err) err = cudaEventRecord(ev[1], s);
     if (!err) err = launch_residual_reduce(p.mode, p.dtype, g->k1_cfg, g->k1_grid, g->points, g->midx, g->d_items,
-                                           g->num_items, g->d_es, g->d_T64, g->d_T32, g->rp, g->d_partials, s);
+                                           g->num_items, g->d_es, g->d_T64, g->d_T32, g->rp, g->d_partials, sched(g),
+                                           s);
     if (!err) err = cudaEventRecord(ev[2], s);
-    if (!err) err = launch_edge_reduce(p.mode, g->d_partials, g->d_item_off, p.E, g->d_Ad, g->d_edge_M, g->d_edge_b,
+    if (!err) err = launch_edge_reduce(p.mode, g->d_partials, g->d_seg_off, p.E, g->d_Ad, g->d_edge_M, g->d_edge_b,
                                        g->d_edge_cost, g->d_edge_skip, nullptr, g->d_edge_valid, s);
     if (!err) err = cudaEventRecord(ev[3], s);
     if (!err) err = launch_assemble(nslots, g->d_slot_contrib_off, g->d_slot_contrib, g->d_edge_M, g->d_A, p.N,
@@ -689,6 +742,7 @@ int como3r_graph_stats(como3r_graph_t g, int64_t* stats) {
   stats[COMO3R_STAT_BLOCK] = residual_reduce_block() * 100 + g->k1_cfg;
   stats[COMO3R_STAT_GRID] = g->k1_grid;
   stats[COMO3R_STAT_SMEM_SOLVE] = g->smem_solve ? 1 : 0;
+  stats[COMO3R_STAT_K1_STALLS] = residual_reduce_stalls();
   return COMO3R_OK;
 }
 

@@ -27,6 +27,15 @@ struct EdgeStatic {            // per edge, fixed at create
   int32_t npix_i, npix_j;      // pixel counts of i and j
 };
 
+// K1 schedule (k_schedule.cu): warp w of the persistent grid processes items
+// [start[w], start[w+1]) and writes its records at seg[w], seg[w] + 1, ... (one per run of
+// items of one edge).  With start == nullptr the items are split evenly by count and every
+// item gets its own record (zeros unless it ends a run).
+struct WarpSched {
+  const int32_t* start;
+  const int32_t* seg;
+};
+
 struct RobustParams {          // whitening and Huber constants (Sec. III-A)
   double inv_sigma_ray, inv_sigma_dist;      // 1/sigma_r, 1/sigma_d
   double inv_var_ray, inv_var_dist;          // 1/sigma_r^2, 1/sigma_d^2
@@ -83,12 +92,23 @@ cudaError_t launch_edge_prep(const double* poses, const EdgeStatic* es, int E, d
 cudaError_t launch_residual_reduce(int mode, int dtype, int cfg, int grid, const void* points,
                                    const int32_t* midx, const Item* items, int num_items,
                                    const EdgeStatic* es, const double* T64, const float* T32,
-                                   RobustParams rp, void* partials, cudaStream_t s);
+                                   RobustParams rp, void* partials, WarpSched ws, cudaStream_t s);
 int residual_reduce_max_blocks_per_sm(int mode, int dtype, int cfg);
 int residual_reduce_num_cfgs(int mode);
 int residual_reduce_cfg_chunk(int cfg);      // required pixels per item, 0 = any
 cudaError_t residual_reduce_prepare();       // once, before any capture
 int residual_reduce_block();
+// Balanced schedule for W workers (warps or CTAs) with item cost wv x valid + wp x pixels:
+// per-item valid counts, cost prefix `cum` [num_items + 1], worker starts [W + 1], segment
+// bases [W], first segment per edge [E + 1].
+cudaError_t launch_schedule(const int32_t* midx, const EdgeStatic* es, const Item* items, int num_items,
+                            const int32_t* item_off, int E, int W, int wv, int wp, int32_t* counts, long long* cum,
+                            int32_t* start, int32_t* seg, int32_t* seg_off, cudaStream_t s);
+// Schedule workers of a launch configuration per CTA (1) or per warp (block / 32), and
+// the cost weights of its loop.
+int residual_reduce_workers_per_cta(int cfg);
+void residual_reduce_cost_weights(int cfg, int& wv, int& wp);
+unsigned int residual_reduce_stalls();  // bounded waits of the TMA variant that gave up
 cudaError_t launch_edge_reduce(int mode, const void* partials, const int32_t* item_off, int E, const double* Ad,
                                double* edge_M, double* edge_b, double* edge_cost, double* edge_skip,
                                double* edge_rec, const long long* edge_valid, cudaStream_t s);

@@ -324,11 +324,36 @@ __device__ __forceinline__ void write_record(Acc<R>& acc, void* partials, int it
   acc.zero();
 }
 
+// This warp's run of items and its first record index (-1: one record per item).
+__device__ __forceinline__ void warp_range(const WarpSched& ws, int gwarp, int nwarps, int num_items, int& it0,
+                                           int& it1, int& seg) {
+  if (ws.start) {
+    it0 = ws.start[gwarp];
+    it1 = ws.start[gwarp + 1];
+    seg = ws.seg[gwarp];
+  } else {
+    const int per = (num_items + nwarps - 1) / nwarps;
+    it0 = min(gwarp * per, num_items);
+    it1 = min(it0 + per, num_items);
+    seg = -1;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void finish_item(Acc<R>& acc, void* partials, int it, int& seg, bool flush, int lane) {
+  if (seg < 0) {
+    write_record(acc, partials, it, flush, lane);
+  } else if (flush) {
+    write_record(acc, partials, seg, true, lane);
+    ++seg;
+  }
+}
+
 template <typename R, int DT, int BLOCK, int MINB, int UNROLL, bool PIPE>
 __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
     const void* __restrict__ points, const int32_t* __restrict__ midx, const Item* __restrict__ items,
     int num_items, const EdgeStatic* __restrict__ es, const double* __restrict__ T64,
-    const float* __restrict__ T32, RobustParams rp, void* __restrict__ partials) {
+    const float* __restrict__ T32, RobustParams rp, void* __restrict__ partials, WarpSched ws) {
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * BLOCK + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * BLOCK) >> 5;
@@ -337,9 +362,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
   k.ivr = (R)rp.inv_var_ray; k.ivd = (R)rp.inv_var_dist;
   k.kappa = (R)rp.kappa; k.half_kappa = (R)(0.5 * rp.kappa);
 
-  // each warp owns a contiguous run of items (mostly of one edge) and reduces once per edge
-  const int per = (num_items + nwarps - 1) / nwarps;
-  const int it0 = gwarp * per, it1 = min(it0 + per, num_items);
+  // each warp owns a contiguous run of items and reduces once per edge
+  int it0, it1, seg;
+  warp_range(ws, gwarp, nwarps, num_items, it0, it1, seg);
   Acc<R> acc;
   acc.zero();
   for (int it = it0; it < it1; ++it) {
@@ -388,7 +413,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
       }
     }
     // ---- warp reduction (compensated butterfly) at the end of each edge run
-    write_record(acc, partials, it, it + 1 == it1 || items[it + 1].edge != item.edge, lane);
+    finish_item(acc, partials, it, seg, it + 1 == it1 || items[it + 1].edge != item.edge, lane);
   }
 }
 
@@ -404,6 +429,8 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
 // without costing registers.
 constexpr int kAsyncChunk = 1024;
 constexpr int kRing = 4;
+constexpr int kK1Block = 256;
+constexpr int kK1Warps = kK1Block / 32;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -466,7 +493,7 @@ template <typename R, int DT>
 __global__ void __launch_bounds__(256, 2) residual_reduce_async_kernel(
     const void* __restrict__ points, const int32_t* __restrict__ midx, const Item* __restrict__ items,
     int num_items, const EdgeStatic* __restrict__ es, const double* __restrict__ T64,
-    const float* __restrict__ T32, RobustParams rp, void* __restrict__ partials) {
+    const float* __restrict__ T32, RobustParams rp, void* __restrict__ partials, WarpSched ws) {
   constexpr int PX = PixBytes<DT>::v;
   constexpr int kWarpBytes = 2 * kAsyncChunk * 4 + kRing * 32 * 2 * PX;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -482,9 +509,9 @@ __global__ void __launch_bounds__(256, 2) residual_reduce_async_kernel(
   k.ivr = (R)rp.inv_var_ray; k.ivd = (R)rp.inv_var_dist;
   k.kappa = (R)rp.kappa; k.half_kappa = (R)(0.5 * rp.kappa);
 
-  // each warp owns a contiguous run of items (mostly of one edge) and reduces once per edge
-  const int per = (num_items + nwarps - 1) / nwarps;
-  const int it0 = gwarp * per, it1 = min(it0 + per, num_items);
+  // each warp owns a contiguous run of items and reduces once per edge
+  int it0, it1, seg;
+  warp_range(ws, gwarp, nwarps, num_items, it0, it1, seg);
   int b = 0;
   if (it0 < it1) {
     const Item first = items[it0];
@@ -550,13 +577,239 @@ __global__ void __launch_bounds__(256, 2) residual_reduce_async_kernel(
     }
     cp_wait<0>();
     __syncwarp();  // the index buffer of this item is reused two items later
-    write_record(acc, partials, it, it + 1 == it1 || items[it + 1].edge != item.edge, lane);
+    finish_item(acc, partials, it, seg, it + 1 == it1 || items[it + 1].edge != item.edge, lane);
   }
   cp_wait<0>();
 }
 
 template <int DT>
 constexpr int async_smem_bytes() { return 8 * (2 * kAsyncChunk * 4 + kRing * 32 * 2 * PixBytes<DT>::v); }
+
+// ---- TMA-staged variant (bulk asynchronous copies into a CTA ring) -------------------
+// CTA-level items of kAsyncChunk pixels.  Thread 0 streams each item's match indices and
+// streamed pixels (both contiguous) into a kTmaStages-deep shared-memory ring with bulk
+// copies (cp.async.bulk), whose completion an mbarrier counts in bytes: tens of KB per CTA
+// in flight at the cost of two instructions, none per lane.  The eight warps take four
+// interleaved 32-pixel groups of each item; while a warp computes item q from shared
+// memory, its gathers of item q + 1 (cp.async, one per valid match, into a per-warp double
+// buffer) are in flight, so the gather latency overlaps the arithmetic and holds no
+// registers.  A warp releases the stage on a second mbarrier after item q; thread 0
+// refills it with the item kTmaStages ahead.  The CTA reduces
+// (warp butterflies, then FP64 across warps in warp order) once per run of items of one
+// edge.  Every mbarrier wait is bounded: a wait that gives up is counted in
+// g_k1_stalls and the kernel finishes without that stage's data (the result is then
+// wrong and the count says so); it never hangs.
+constexpr int kTmaCfg = 5;
+constexpr int kTmaStages = 3;
+constexpr long long kSpinLimit = 1LL << 24;
+__device__ unsigned int g_k1_stalls = 0;
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Polls the phase of the given parity; false after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long spin = 0; spin < kSpinLimit; ++spin) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// This CTA's run of items and its first record index (-1: one record per item).
+__device__ __forceinline__ void cta_range(const WarpSched& ws, int num_items, int& it0, int& it1, int& seg) {
+  if (ws.start) {
+    it0 = ws.start[blockIdx.x];
+    it1 = ws.start[blockIdx.x + 1];
+    seg = ws.seg[blockIdx.x];
+  } else {
+    const int per = (num_items + gridDim.x - 1) / gridDim.x;
+    it0 = min((int)blockIdx.x * per, num_items);
+    it1 = min(it0 + per, num_items);
+    seg = -1;
+  }
+}
+
+// CTA-wide record of the accumulators (all threads call it; `flush` is CTA-uniform).
+template <typename R>
+__device__ __forceinline__ void cta_record(Acc<R>& acc, void* partials, int rec_idx, bool flush, double (*red)[kAcc + 2],
+                                           int tid, int lane, int warp) {
+  using Slot = typename std::conditional<sizeof(R) == 4, float2, double>::type;
+  Slot* rec = reinterpret_cast<Slot*>(partials) + (int64_t)rec_idx * kPartial;
+  if (!flush) {
+    if (tid < kPartial) store_slot(rec, tid, R(0), R(0));
+    return;
+  }
+  R comp[kAcc];
+  warp_transpose_reduce(acc.v, comp, lane);
+  R Ec = R(0);
+  const R Ev = warp_sum_pair(acc.cost(), Ec);
+  const int sk = __reduce_add_sync(0xffffffffu, acc.skipped);
+  red[warp][lane] = (double)acc.v[0] + (double)comp[0];
+  if (lane == 0) {
+    red[warp][kAcc] = (double)Ev + (double)Ec;
+    red[warp][kAcc + 1] = (double)sk;
+  }
+  acc.zero();
+  __syncthreads();
+  if (tid < kPartial) {
+    double sum = 0.0;
+    if (tid < kAcc + 2)
+#pragma unroll
+      for (int w = 0; w < kK1Warps; ++w) sum += red[w][tid];
+    if constexpr (sizeof(R) == 4) {
+      const float hi = (float)sum;
+      rec[tid] = make_float2(hi, (float)(sum - (double)hi));
+    } else {
+      rec[tid] = sum;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename R, int DT>
+__global__ void __launch_bounds__(256, 2) residual_reduce_tma_kernel(
+    const void* __restrict__ points, const int32_t* __restrict__ midx, const Item* __restrict__ items,
+    int num_items, const EdgeStatic* __restrict__ es, const double* __restrict__ T64,
+    const float* __restrict__ T32, RobustParams rp, void* __restrict__ partials, WarpSched ws) {
+  constexpr int PX = PixBytes<DT>::v;
+  constexpr int kIdxBytes = kAsyncChunk * 4;
+  constexpr int kStageBytes = kIdxBytes + kAsyncChunk * PX;
+  static_assert(kAsyncChunk == 4 * 32 * kK1Warps, "four 32-pixel groups per warp and item");
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full_bar[kTmaStages], empty_bar[kTmaStages];
+  __shared__ double red[kK1Warps][kAcc + 2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int it0, it1, seg;
+  cta_range(ws, num_items, it0, it1, seg);
+  const int n_local = it1 - it0;
+  if (tid == 0) {
+    for (int q = 0; q < kTmaStages; ++q) {
+      mbar_init(&full_bar[q], 1);
+      mbar_init(&empty_bar[q], kK1Warps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  Consts<R> k;
+  k.isr = (R)rp.inv_sigma_ray; k.isd = (R)rp.inv_sigma_dist;
+  k.ivr = (R)rp.inv_var_ray; k.ivd = (R)rp.inv_var_dist;
+  k.kappa = (R)rp.kappa; k.half_kappa = (R)(0.5 * rp.kappa);
+  // thread 0: bulk copies of local item q into stage q % kTmaStages
+  auto issue = [&](int q) {
+    const Item item = items[it0 + q];
+    const EdgeStatic& e = es[item.edge];
+    const uint32_t n = (uint32_t)(item.end - item.begin);
+    unsigned char* base = smem + (size_t)(q % kTmaStages) * kStageBytes;
+    uint64_t* bar = &full_bar[q % kTmaStages];
+    mbar_expect_tx(bar, n * (4u + (uint32_t)PX));
+    bulk_copy(base, midx + e.idx_off + item.begin, n * 4u, bar);
+    bulk_copy(base + kIdxBytes, static_cast<const unsigned char*>(points) + (e.pix_i + item.begin) * PX,
+              n * (uint32_t)PX, bar);
+  };
+  // gathered pixels of items q (buffer q & 1) and q + 1: per warp 4 groups x 32 lanes, each
+  // lane's own slots (written by its cp.async, read only by itself)
+  unsigned char* gbuf = smem + (size_t)kTmaStages * kStageBytes;
+  auto gslot = [&](int b, int u) -> unsigned char* {
+    return gbuf + ((size_t)((b * kK1Warps + warp) * 4 + u) * 32 + lane) * PX;
+  };
+  // groups interleaved across warps (warp w: groups w, w + 8, w + 16, w + 24), so a band of
+  // valid columns spreads over all warps of the CTA
+  auto gather = [&](int q) {
+    const Item item = items[it0 + q];
+    const int64_t pix_j = es[item.edge].pix_j;
+    const int32_t* sidx = reinterpret_cast<const int32_t*>(smem + (size_t)(q % kTmaStages) * kStageBytes);
+    const int n_pix = item.end - item.begin;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int m = 32 * (warp + kK1Warps * u) + lane;
+      const int n = m < n_pix ? sidx[m] : -1;
+      if (n >= 0) copy_px<DT>(gslot(q & 1, u), points, pix_j + n);
+    }
+  };
+  if (tid == 0)
+    for (int q = 0; q < kTmaStages && q < n_local; ++q) issue(q);
+  bool landed_cur = n_local > 0 && mbar_wait(&full_bar[0], 0u);
+  if (landed_cur) gather(0);
+  cp_commit();
+  Acc<R> acc;
+  acc.zero();
+  for (int q = 0; q < n_local; ++q) {
+    const int st = q % kTmaStages;
+    const uint32_t parity = (uint32_t)(q / kTmaStages) & 1u;
+    const int it = it0 + q;
+    const Item item = items[it];
+    if (!landed_cur && lane == 0) atomicAdd(&g_k1_stalls, 1u);
+    // the gathers of item q + 1 fly while item q is computed
+    bool landed_next = false;
+    if (q + 1 < n_local) {
+      landed_next = mbar_wait(&full_bar[(q + 1) % kTmaStages], (uint32_t)((q + 1) / kTmaStages) & 1u);
+      if (landed_next) gather(q + 1);
+    }
+    cp_commit();
+    cp_wait<1>();  // item q's gathers have landed (all groups but the newest)
+    R T[12];
+#pragma unroll
+    for (int t = 0; t < 12; ++t) {
+      if constexpr (sizeof(R) == 4) T[t] = T32[16 * item.edge + t];
+      else T[t] = T64[12 * item.edge + t];
+    }
+    if (landed_cur) {
+      const int32_t* sidx = reinterpret_cast<const int32_t*>(smem + (size_t)st * kStageBytes);
+      const unsigned char* sxi = smem + (size_t)st * kStageBytes + kIdxBytes;
+      const int n_pix = item.end - item.begin;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int m = 32 * (warp + kK1Warps * u) + lane;
+        if (m < n_pix && sidx[m] >= 0) {
+          R xi, yi, zi, ci, xj, yj, zj, cj;
+          read_px<DT, R>(sxi + (size_t)m * PX, xi, yi, zi, ci);
+          read_px<DT, R>(gslot(q & 1, u), xj, yj, zj, cj);
+          accumulate<R>(xi, yi, zi, ci, xj, yj, zj, cj, T, k, acc);
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty_bar[st]);  // this warp no longer reads the stage
+    if (tid == 0 && q + kTmaStages < n_local) {
+      if (mbar_wait(&empty_bar[st], parity)) issue(q + kTmaStages);
+      else atomicAdd(&g_k1_stalls, 1u);  // not refilled: the waits for it give up too
+    }
+    landed_cur = landed_next;
+    const bool flush = it + 1 == it1 || items[it + 1].edge != item.edge;
+    if (seg < 0) {
+      cta_record(acc, partials, it, flush, red, tid, lane, warp);
+    } else if (flush) {
+      cta_record(acc, partials, seg, true, red, tid, lane, warp);
+      ++seg;
+    }
+  }
+  cp_wait<0>();
+}
+
+template <int DT>
+constexpr int tma_smem_bytes() {
+  return kTmaStages * (kAsyncChunk * 4 + kAsyncChunk * PixBytes<DT>::v) + 2 * kAsyncChunk * PixBytes<DT>::v;
+}
 
 // Launch configurations the autotuner chooses from (256-thread CTAs):
 //   0  plain loop, 2 pixels per lane per group, natural register budget
@@ -566,9 +819,10 @@ constexpr int async_smem_bytes() { return 8 * (2 * kAsyncChunk * 4 + kRing * 32 
 //   4  shared-memory-staged loop (cp.async ring) over warp-compacted valid matches; work
 //      items of exactly 1024 pixels, only when every match-index row starts 16-byte
 //      aligned and every keyframe has at most 2^22 pixels
-// FP64 runs configurations 0 and 1 only.
-constexpr int kK1Block = 256;
-constexpr int kK1Cfgs = 5;
+//   5  TMA-staged CTA ring (bulk copies of index rows and streamed pixels), FP32 compute
+//      on FP16 / FP32 storage; the same item and alignment conditions as 4
+// FP64 has configurations 0, 1 and 4.
+constexpr int kK1Cfgs = 6;
 constexpr int kAsyncCfg = 4;
 
 template <typename R, int DT>
@@ -580,6 +834,9 @@ const void* pick_cfg(int cfg) {
     if (cfg == 3) return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 3, 1, true>);
   }
   if (cfg == kAsyncCfg) return reinterpret_cast<const void*>(&residual_reduce_async_kernel<R, DT>);
+  if constexpr (sizeof(R) == 4 && DT < 2) {
+    if (cfg == kTmaCfg) return reinterpret_cast<const void*>(&residual_reduce_tma_kernel<R, DT>);
+  }
   return nullptr;
 }
 
@@ -604,9 +861,10 @@ const void* pick_kernel(int mode, int dtype, int cfg) {
 
 int residual_reduce_num_cfgs(int mode) { return kK1Cfgs; }
 
-int residual_reduce_cfg_chunk(int cfg) { return cfg == kAsyncCfg ? kAsyncChunk : 0; }
+int residual_reduce_cfg_chunk(int cfg) { return (cfg == kAsyncCfg || cfg == kTmaCfg) ? kAsyncChunk : 0; }
 
 static size_t cfg_smem(int dtype, int cfg) {
+  if (cfg == kTmaCfg) return dtype == 0 ? tma_smem_bytes<0>() : tma_smem_bytes<1>();
   if (cfg != kAsyncCfg) return 0;
   return dtype == 0 ? async_smem_bytes<0>() : (dtype == 1 ? async_smem_bytes<1>() : async_smem_bytes<2>());
 }
@@ -618,10 +876,29 @@ cudaError_t residual_reduce_prepare() {
     for (int d = 0; d < 3 && e == cudaSuccess; ++d)
       e = cudaFuncSetAttribute(pick_kernel(mode, d, kAsyncCfg), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)cfg_smem(d, kAsyncCfg));
+  for (int d = 0; d < 2 && e == cudaSuccess; ++d)
+    e = cudaFuncSetAttribute(pick_kernel(1, d, kTmaCfg), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cfg_smem(d, kTmaCfg));
   return e;
 }
 
 int residual_reduce_block() { return kK1Block; }
+
+int residual_reduce_workers_per_cta(int cfg) { return cfg == kTmaCfg ? 1 : kK1Block / 32; }
+
+unsigned int residual_reduce_stalls() {
+  unsigned int v = 0;
+  cudaMemcpyFromSymbol(&v, g_k1_stalls, sizeof(v));
+  return v;
+}
+
+void residual_reduce_cost_weights(int cfg, int& wv, int& wp) {
+  // first candidates of the autotuner (measured on the 2x40 workload): cfg 0-3 pay one
+  // memory round trip per 32-pixel group whether it holds matches or not; cfg 4 and 5
+  // prefetch whole index rows, so valid matches weigh more
+  wp = 1;
+  wv = cfg == kAsyncCfg ? 3 : (cfg == kTmaCfg ? 1 : 0);
+}
 
 int residual_reduce_max_blocks_per_sm(int mode, int dtype, int cfg) {
   const void* f = pick_kernel(mode, dtype, cfg);
@@ -634,12 +911,12 @@ int residual_reduce_max_blocks_per_sm(int mode, int dtype, int cfg) {
 cudaError_t launch_residual_reduce(int mode, int dtype, int cfg, int grid, const void* points,
                                    const int32_t* midx, const Item* items, int num_items,
                                    const EdgeStatic* es, const double* T64, const float* T32,
-                                   RobustParams rp, void* partials, cudaStream_t s) {
+                                   RobustParams rp, void* partials, WarpSched ws, cudaStream_t s) {
   const void* f = pick_kernel(mode, dtype, cfg);
   if (!f) return cudaErrorInvalidValue;
   if (num_items <= 0) return cudaSuccess;
   void* args[] = {(void*)&points, (void*)&midx, (void*)&items, (void*)&num_items, (void*)&es,
-                  (void*)&T64, (void*)&T32, (void*)&rp, (void*)&partials};
+                  (void*)&T64, (void*)&T32, (void*)&rp, (void*)&partials, (void*)&ws};
   return cudaLaunchKernel(f, dim3(grid), dim3(kK1Block), args, cfg_smem(dtype, cfg), s);
 }
 

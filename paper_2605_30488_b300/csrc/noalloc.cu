@@ -200,7 +200,7 @@ extern "C" int como3r_linearize_noalloc(const como3r_graph_desc* d, const double
   const int grid = std::max(1, std::min(sms * occ, (n_items + warps_per_cta - 1) / warps_per_cta));
   err = launch_edge_prep(poses, es, E, T64, T32, Ad, s);
   if (!err) err = launch_residual_reduce(d->mode, d->dtype, 0, grid, d->points_conf, d->match_idx, items, n_items, es,
-                                         T64, T32, rp, records, s);
+                                         T64, T32, rp, records, WarpSched{nullptr, nullptr}, s);
   if (!err) err = launch_edge_reduce(d->mode, records, item_off, E, Ad, M, B, cost, skip, edge_out, valid, s);
   return err ? COMO3R_ERR_CUDA : COMO3R_OK;
 }

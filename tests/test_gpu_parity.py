@@ -6,6 +6,8 @@ angle / relative translation / relative scale); the mixed form matches to 1e-5 o
 Hessian and on converged poses.  Inputs are the same stored values on both sides
 (FP16 / FP32 storage upcast exactly by the oracle).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -212,16 +214,21 @@ def test_batched_graphs_match_individual(C):
     np.testing.assert_allclose(trace, to, rtol=FP64_TOL)
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5])
 def test_every_residual_kernel_configuration(C, mid, tiny, cfg, monkeypatch):
     """Each launch configuration the autotuner may choose gives the oracle's edge blocks
-    (mixed form; the FP64 form for the configurations that have one)."""
+    (mixed form on FP32 and FP16 storage; the FP64 form for the configurations that have
+    one)."""
     monkeypatch.setenv("COMO3R_K1_CFG", str(cfg))
-    cases = [(mid, C.MIXED, MIXED_TOL)] + ([(tiny, C.PLAIN_FP64, FP64_TOL)] if cfg in (0, 1, 4) else [])
+    mid16 = dataclasses.replace(mid, points=mid.points.astype(np.float16))
+    cases = [(mid, C.MIXED, MIXED_TOL), (mid16, C.MIXED, MIXED_TOL)]
+    cases += [(tiny, C.PLAIN_FP64, FP64_TOL)] if cfg in (0, 1, 4) else []
     for prob, mode, tol in cases:
         with C.Graph(prob, mode=mode) as g:
             st, cost, rec = edge_records(C, g, prob.poses_init)
-            assert g.stats()["block"] % 100 == cfg
+            stats = g.stats()
+            assert stats["block"] % 100 == cfg
+            assert stats["k1_stalls"] == 0
         _, _, E, recs = O.build_system(prob, prob.poses_init, 0)
         for e, r in enumerate(recs):
             assert rel_fro(rec[e, :49].reshape(7, 7), r["H_rel"]) <= tol, (cfg, mode, e)
