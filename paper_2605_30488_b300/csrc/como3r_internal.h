@@ -61,6 +61,8 @@ struct GraphInfoDev {          // per graph, written on the device
 //      per destination block, (dst, t0, t1, col): L[dst] -= sum_{t0 <= t < t1}
 //      L[tri[t].x] L[tri[t].y]^T; col >= 0 marks a diagonal destination, whose task also
 //      updates the forward right-hand side of column col with L[tri[t].x] y_{tri[t].w}.
+//      The tasks into the next level's columns ("near") come first; the others ("far")
+//      run together with the next level's D list.
 enum GraphMeta {
   kMetaColBase, kMetaNCol, kMetaSlotBase, kMetaNSlot, kMetaTriBase, kMetaNTri,
   kMetaUBase, kMetaNU, kMetaTBase, kMetaNT, kMetaLvlBase, kMetaNLvl, kMetaCount
@@ -74,7 +76,8 @@ struct SolverPlan {
   const int4* tri;          // (src_r, src_k, dst, j) local slots / column, at tri_base
   const int4* utask;        // (dst, t0, t1, col or -1), at u_base
   const int2* ttask;        // (slot, col), at t_base
-  const int32_t* lvl;       // per graph (nlev+1) x 3: offsets of each level in sched, utask, ttask; at 3 * lvl_base
+  const int32_t* lvl;       // per graph (nlev+1) x 4: level offsets in sched, utask (near), utask (far), ttask;
+                            // at 4 * lvl_base
 };
 
 // Bytes of shared memory one graph's factor, per-column scratch and plan occupy.
@@ -82,7 +85,7 @@ inline size_t solver_smem_bytes(int nslot, int ncol, int ntri, int nu, int nt, i
   auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
   size_t b = r16(sizeof(double) * ((size_t)nslot * 49 + (size_t)ncol * 63));
   b += r16(16 * (size_t)ntri) + r16(16 * (size_t)nu) + r16(8 * (size_t)nt);
-  b += r16(4 * (size_t)(ncol + 1)) + r16(4 * (size_t)nslot) + r16(4 * (size_t)ncol) + r16(12 * (size_t)(nlev + 1));
+  b += r16(4 * (size_t)(ncol + 1)) + r16(4 * (size_t)nslot) + r16(4 * (size_t)ncol) + r16(16 * (size_t)(nlev + 1));
   return b;
 }
 

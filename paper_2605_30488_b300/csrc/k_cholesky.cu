@@ -14,6 +14,8 @@
 //      L[dst] -= sum L_rj L_kj^T over the level's columns j (diagonal destinations also
 //      update the forward right-hand side t_c -= L_cj y_j), so every column has received
 //      all of its descendants' updates when its own level starts.
+// The update tasks into the next level's columns run in the U phase; the others run in
+// the next level's D phase, alongside its diagonal factorisations (lookahead).
 // A failed attempt restarts with eps_r = eps0 * 100^r; after max_attempts failures the
 // update is zero (Sec. III-D).  Back substitution walks the levels from the root, each
 // column x_c = L_cc^{-T}(y_c - sum_r L_rc^T x_r) with the precomputed L_cc^{-1}.
@@ -45,7 +47,7 @@ struct SolveCtx {
   const int4* tri;        // [ntri]
   const int4* utask;      // [nu]
   const int2* ttask;      // [nt]
-  const int* lvl;         // [(nlev + 1) * 3]
+  const int* lvl;         // [(nlev + 1) * 4]
 };
 
 __device__ __forceinline__ double* blk(const SolveCtx& C, int s) { return C.L + (int64_t)s * 49; }
@@ -224,10 +226,22 @@ __device__ __forceinline__ T* carve(unsigned char*& p, size_t count) {
   return r;
 }
 
+// Global -> shared copies issued as cp.async (all in flight at once; completed by
+// async_wait_all): element sizes 4, 8 and 16 bytes, each source element naturally aligned.
 template <typename T>
-__device__ __forceinline__ void stage(T* dst, const T* src, int n, int tid) {
-  for (int x = tid; x < n; x += kSolveThreads) dst[x] = src[x];
+__device__ __forceinline__ void stage(T* dst, const T* src, int64_t n, int tid) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "cp.async element size");
+  for (int64_t x = tid; x < n; x += kSolveThreads) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + x);
+    if constexpr (sizeof(T) == 16)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + x) : "memory");
+    else if constexpr (sizeof(T) == 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src + x) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + x) : "memory");
+  }
 }
+__device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <bool SMEM>
 __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
@@ -253,7 +267,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
   const int4* gtri = P.tri + m[kMetaTriBase];
   const int4* gutask = P.utask + m[kMetaUBase];
   const int2* gttask = P.ttask + m[kMetaTBase];
-  const int* glvl = P.lvl + 3 * m[kMetaLvlBase];
+  const int* glvl = P.lvl + 4 * m[kMetaLvlBase];
   SolveCtx C;
   if (SMEM) {
     unsigned char* q = dyn;
@@ -265,14 +279,14 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     int* cs = carve<int>(q, ncol + 1);
     int* sr = carve<int>(q, nslot);
     int* sc = carve<int>(q, ncol);
-    int* lv = carve<int>(q, 3 * (nlev + 1));
+    int* lv = carve<int>(q, 4 * (nlev + 1));
     stage(tri, gtri, m[kMetaNTri], tid);
     stage(ut, gutask, m[kMetaNU], tid);
     stage(tt, gttask, m[kMetaNT], tid);
     stage(cs, gcol_slot, ncol + 1, tid);
     stage(sr, gslot_row, nslot, tid);
     stage(sc, gsched, ncol, tid);
-    stage(lv, glvl, 3 * (nlev + 1), tid);
+    stage(lv, glvl, 4 * (nlev + 1), tid);
     C.tri = tri; C.utask = ut; C.ttask = tt; C.col_slot = cs; C.slot_row = sr; C.sched = sc; C.lvl = lv;
   } else {
     C.L = Lg + (int64_t)sbase * 49;
@@ -296,7 +310,12 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
   for (int r = 0; r < attempt; ++r) pow100 *= 100.0;
   for (; attempt < last; ++attempt, pow100 *= 100.0) {
     const double eps = eps0 * pow100;
-    for (int64_t x = tid; x < (int64_t)nslot * 49; x += kSolveThreads) C.L[x] = Ag[x];
+    if (SMEM) {
+      stage(C.L, Ag, (int64_t)nslot * 49, tid);
+      async_wait_all();  // also completes the plan staged above
+    } else {
+      for (int64_t x = tid; x < (int64_t)nslot * 49; x += kSolveThreads) C.L[x] = Ag[x];
+    }
     __syncthreads();
     for (int x = tid; x < 7 * ncol; x += kSolveThreads) {
       const int col = x / 7, k = x % 7;
@@ -307,27 +326,42 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     if (tid == 0) s_fail = 0;
     __syncthreads();
     for (int lv = 0; lv < nlev; ++lv) {
-      const int* L0 = C.lvl + 3 * lv;  // [sched, utask, ttask] offsets of this level and (at +3) the next
-      for (int q = L0[0] + 4 * warp; q < L0[3]; q += 4 * kSolveWarps)
-        diag_factor4(C, C.sched + q, min(4, L0[3] - q), lane, &s_fail);
+      // [sched, near updates, far updates, ttask] offsets of this level; the next level's at +4
+      const int* L0 = C.lvl + 4 * lv;
+      // D(lv) in groups of four columns, with the far updates of level lv - 1 (their
+      // destinations lie two or more levels up, so they do not touch this level's blocks):
+      // the latency-bound factorisations and the FP64-throughput-bound updates overlap
+      const int ncl = L0[4] - L0[0], nd = (ncl + 3) / 4;
+      const int f0 = lv > 0 ? C.lvl[4 * (lv - 1) + 2] : 0, nf = lv > 0 ? L0[1] - f0 : 0;
+      for (int i = warp; i < nd + nf; i += kSolveWarps) {
+        if (i < nd) diag_factor4(C, C.sched + L0[0] + 4 * i, min(4, ncl - 4 * i), lane, &s_fail);
+        else update_task(C, C.utask[f0 + i - nd], lane);
+      }
       __syncthreads();
       if (s_fail) break;
-      const int nt = L0[5] - L0[2];
+      const int nt = L0[7] - L0[3];
       const int tpad = (7 * nt + 31) & ~31;
-      const int nx = tpad + 7 * (L0[3] - L0[0]);
-      for (int x = tid; x < nx; x += kSolveThreads) trsm_or_inverse(C, L0[2], nt, tpad, L0[0], x);
+      const int nx = tpad + 7 * ncl;
+      for (int x = tid; x < nx; x += kSolveThreads) trsm_or_inverse(C, L0[3], nt, tpad, L0[0], x);
       __syncthreads();
-      for (int u = L0[1] + warp; u < L0[4]; u += kSolveWarps) update_task(C, C.utask[u], lane);
+      for (int u = L0[1] + warp; u < L0[2]; u += kSolveWarps) update_task(C, C.utask[u], lane);
+      __syncthreads();
+    }
+    if (s_fail == 0 && nlev > 0) {
+      // far updates of the last level (none in an elimination tree: its columns are roots)
+      const int* L0 = C.lvl + 4 * (nlev - 1);
+      for (int u = L0[2] + warp; u < L0[5]; u += kSolveWarps) update_task(C, C.utask[u], lane);
       __syncthreads();
     }
     ok = (s_fail == 0);
     __syncthreads();
     if (ok) break;
   }
+  async_wait_all();  // nothing left in flight when no attempt ran
   if (ok) {
     for (int lv = nlev - 1; lv >= 0; --lv) {
-      const int* L0 = C.lvl + 3 * lv;
-      for (int q = L0[0] + warp; q < L0[3]; q += kSolveWarps) backward_column(C, C.sched[q], lane);
+      const int* L0 = C.lvl + 4 * lv;
+      for (int q = L0[0] + warp; q < L0[4]; q += kSolveWarps) backward_column(C, C.sched[q], lane);
       __syncthreads();
     }
     for (int x = tid; x < 7 * ncol; x += kSolveThreads) tau[7 * col_kf[x / 7] + x % 7] = y_of(C, x / 7)[x % 7];

@@ -406,19 +406,37 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
     std::vector<int> byl(n);
     std::iota(byl.begin(), byl.end(), 0);
     std::stable_sort(byl.begin(), byl.end(), [&](int x, int y) { return level[x] < level[y]; });
+    // the level of the column that owns each local slot
+    std::vector<int> level_of_slot(nslot);
+    for (int k = 0; k < n; ++k)
+      for (int sl = slot_base[k]; sl < slot_base[k] + 1 + (int)rows[k].size(); ++sl) level_of_slot[sl] = level[k];
     const int u0 = (int)p.lutask.size(), t0 = (int)p.lttask.size();
     int q = 0;
-    p.llvl.insert(p.llvl.end(), {0, 0, 0});
     for (int lv = 0; lv < S.nlev; ++lv) {
+      const int sched0 = q, tt0 = (int)p.lttask.size() - t0;
       for (; q < n && level[byl[q]] == lv; ++q) {
         const int k = byl[q];
         p.lsched.push_back(k);
         for (size_t b = 0; b < rows[k].size(); ++b) p.lttask.push_back(make_int2(slot_base[k] + 1 + (int)b, k));
       }
+      // updates into the next level's columns ("near", needed by its factorisation) first,
+      // then the rest ("far", which the kernel overlaps with the next level's diagonal
+      // factorisations); longest first within each kind
       auto& tl = tasks_of_level[lv];
-      std::stable_sort(tl.begin(), tl.end(), [](const int4& x, const int4& y) { return (x.z - x.y) > (y.z - y.y); });
+      std::stable_sort(tl.begin(), tl.end(), [&](const int4& x, const int4& y) {
+        const bool nx = level_of_slot[x.x] == lv + 1, ny = level_of_slot[y.x] == lv + 1;
+        if (nx != ny) return nx;
+        return (x.z - x.y) > (y.z - y.y);
+      });
+      const int un0 = (int)p.lutask.size() - u0;
+      int n_near = 0;
+      for (const int4& t : tl) n_near += level_of_slot[t.x] == lv + 1;
       p.lutask.insert(p.lutask.end(), tl.begin(), tl.end());
-      p.llvl.insert(p.llvl.end(), {q, (int)p.lutask.size() - u0, (int)p.lttask.size() - t0});
+      p.llvl.insert(p.llvl.end(), {sched0, un0, un0 + n_near, tt0});
+    }
+    {
+      const int nu_all = (int)p.lutask.size() - u0;
+      p.llvl.insert(p.llvl.end(), {q, nu_all, nu_all, (int)p.lttask.size() - t0});
     }
     const int ntri = (int)p.ltri.size() - tri0, nu = (int)p.lutask.size() - u0, nt = (int)p.lttask.size() - t0;
     p.meta.insert(p.meta.end(), {cbase, n, sbase, nslot, tri0, ntri, u0, nu, t0, nt, lvl_base, S.nlev});
