@@ -7,8 +7,9 @@ none of the refinement's arithmetic (no residual, Jacobian, Huber, solve or Sim(
 exponential); poses are perturbed with a plain axis-angle rotation, a body-frame
 offset and a scale factor.
 """
+from .cloud import make_cloud_problem
 from .scene import (Problem, WORKLOADS, make_problem, make_workload, quat_from_matrix,
                     matrix_from_quat)
 
-__all__ = ["Problem", "WORKLOADS", "make_problem", "make_workload", "quat_from_matrix",
+__all__ = ["Problem", "WORKLOADS", "make_problem", "make_workload", "make_cloud_problem", "quat_from_matrix",
            "matrix_from_quat"]

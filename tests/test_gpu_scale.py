@@ -1,0 +1,167 @@
+"""Parity at the workloads' full sizes, on outputs the oracle can compute one at a time.
+
+* the 2 agents x 40 keyframes bench workload (512x384 FP32): sampled edges against the
+  oracle's per-edge blocks (both forms), one FP64 iteration against the oracle's dense
+  system and step, and 15 mixed iterations against 15 FP64 ones;
+* a 4 agents x 150 keyframes team at 512x384 with FP16 storage (about 1,000 edges):
+  sampled edges, and recovery of the ground truth from noise-free pointmaps;
+* a 2,000-keyframe chain with loop closures every 100 keyframes (the factor does not fit
+  in shared memory): ground-truth recovery in both forms;
+* a batch of 64 independent graphs of uneven sizes and resolutions: every graph recovers
+  its ground truth, and the FP64 system of a sampled graph equals the oracle's.
+The large graphs come from the shared-canvas generator (exact correspondences for any
+topology); the bench workload from the ray-cast scenes.
+"""
+import numpy as np
+import pytest
+
+from oracle import como3r_oracle as O
+from synth import make_cloud_problem, make_workload
+from tests.gpu_helpers import oracle_dense_without_anchor, pose_err, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-9
+MIXED_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def C():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_30488_b300 import build
+    build.build()
+    from paper_2605_30488_b300 import como3r
+    return como3r
+
+
+def dev(a, dtype=None):
+    import torch
+    return torch.tensor(np.asarray(a), dtype=dtype or torch.float64, device="cuda").contiguous()
+
+
+def edge_records(C, g, poses):
+    import torch
+    rec = torch.zeros((g.E, C.EDGE_RECORD), dtype=torch.float64, device="cuda")
+    g.linearize(dev(poses), rec)
+    return rec.cpu().numpy()
+
+
+def check_sampled_edges(prob, rec, edges, tol, poses):
+    arrs = O.problem_arrays(prob)
+    T = [O.pose_to_matrix(p) for p in poses]
+    for e in edges:
+        i, j, m, n, Pi, Pj = O.edge_matches(prob, arrs, int(e))
+        r = O.linearize_edge(T[i], T[j], Pi, Pj, prob.params())
+        assert rel_fro(rec[e, :49].reshape(7, 7), r["H_rel"]) <= tol, e
+        assert abs(rec[e, 56] - r["cost"]) <= tol * max(r["cost"], 1e-300), e
+        assert rec[e, 57] == r["n_valid"] and rec[e, 58] == r["n_skipped"], e
+
+
+@pytest.fixture(scope="module")
+def bench_workload():
+    return make_workload("two_agent_40kf_512x384", seed=0)
+
+
+def test_bench_workload_sampled_edges(C, bench_workload):
+    p = bench_workload
+    sample = np.linspace(0, p.num_edges - 1, 6).astype(int)
+    for mode, tol in ((C.MIXED, MIXED_TOL), (C.PLAIN_FP64, FP64_TOL)):
+        with C.Graph(p, mode=mode) as g:
+            rec = edge_records(C, g, p.poses_init)
+        check_sampled_edges(p, rec, sample, tol, p.poses_init)
+
+
+def test_bench_workload_fp64_step_matches_oracle(C, bench_workload):
+    import torch
+    p = bench_workload
+    N = p.num_kf
+    H = torch.zeros((7 * N, 7 * N), dtype=torch.float64, device="cuda")
+    gv = torch.zeros(7 * N, dtype=torch.float64, device="cuda")
+    poses = dev(p.poses_init)
+    with C.Graph(p, mode=C.PLAIN_FP64) as g:
+        st, info = g.gn_step(poses, H, gv)
+    Ho, go, Eo, _ = oracle_dense_without_anchor(p, p.poses_init)
+    assert rel_fro(H.cpu().numpy(), Ho) <= FP64_TOL
+    assert rel_fro(gv.cpu().numpy(), go) <= FP64_TOL
+    new_o, infos = O.gn_step(p, p.poses_init)
+    assert max(pose_err(poses.cpu().numpy(), new_o).values()) <= FP64_TOL
+
+
+def test_bench_workload_mixed_matches_fp64_after_15_iterations(C, bench_workload):
+    p = bench_workload
+    out = {}
+    for mode in (C.MIXED, C.PLAIN_FP64):
+        poses = dev(p.poses_init)
+        with C.Graph(p, mode=mode) as g:
+            st, trace, info = g.solve(poses, p.iters)
+        out[mode] = (poses.cpu().numpy(), trace)
+    err = pose_err(out[C.MIXED][0], out[C.PLAIN_FP64][0])
+    assert max(err.values()) <= MIXED_TOL, err
+    assert abs(out[C.MIXED][1][-1, 0] / out[C.PLAIN_FP64][1][-1, 0] - 1) <= MIXED_TOL
+
+
+def test_fp16_team_4x150(C):
+    spec = dict(agents=4, n_kf=150, H=384, W=512, period=100, shift=24, loop=0, n_inter=60)
+    p = make_cloud_problem(11, [dict(spec, outlier=0.15)], dtype=np.float16, name="team-f16")
+    assert p.num_edges >= 950
+    with C.Graph(p, mode=C.MIXED) as g:
+        rec = edge_records(C, g, p.poses_init)
+    check_sampled_edges(p, rec, np.linspace(0, p.num_edges - 1, 4).astype(int), MIXED_TOL, p.poses_init)
+    del p
+    # noise- and outlier-free: the mixed form recovers the ground truth
+    q = make_cloud_problem(12, [spec], dtype=np.float16, name="team-f16-exact")
+    poses = dev(q.poses_init)
+    with C.Graph(q, mode=C.MIXED) as g:
+        st, trace, info = g.solve(poses, 10)
+    # FP16 storage rounds the points (relative 2^-11), so the recovered poses carry that error
+    err = pose_err(poses.cpu().numpy(), q.poses_gt)
+    assert max(err.values()) <= 2e-3, err
+    assert trace[-1, 0] < 1e-3 * trace[0, 0]
+
+
+def test_chain_2000_with_loop_closures(C):
+    p = make_cloud_problem(13, [dict(agents=1, n_kf=2000, H=48, W=64, period=100, shift=8, loop=100)],
+                           dtype=np.float64, name="chain-2000")
+    assert p.num_edges == 1999 + 999 + 19
+    for mode, tol in ((C.PLAIN_FP64, 1e-9), (C.MIXED, 1e-5)):
+        poses = dev(p.poses_init)
+        with C.Graph(p, mode=mode) as g:
+            stats = g.stats()
+            st, trace, info = g.solve(poses, 8)
+        assert stats["smem_solve"] == 0  # the factor lives in global memory
+        assert info[0]["solved"]
+        err = pose_err(poses.cpu().numpy(), p.poses_gt)
+        assert max(err.values()) <= tol, (mode, err)
+
+
+def test_batch_of_64_uneven_graphs(C):
+    rng = np.random.default_rng(14)
+    res = [(48, 64), (72, 96), (96, 128)]
+    specs = []
+    for _ in range(64):
+        h, w = res[rng.integers(0, 3)]
+        specs.append(dict(agents=int(rng.integers(2, 5)), n_kf=int(rng.integers(5, 26)), H=h, W=w, period=40,
+                          shift=6, loop=0, n_inter=3))
+    p = make_cloud_problem(15, specs, dtype=np.float32, name="batch-64")
+    assert p.num_graphs == 64
+    poses = dev(p.poses_init)
+    with C.Graph(p, mode=C.MIXED) as g:
+        st, trace, info = g.solve(poses, 8)
+    assert all(x["solved"] for x in info)
+    err = pose_err(poses.cpu().numpy(), p.poses_gt)
+    assert max(err.values()) <= MIXED_TOL, err
+    # the FP64 system of one sampled graph equals the oracle's
+    gsel = 17
+    k0, k1 = int(p.kf_offset[gsel]), int(p.kf_offset[gsel + 1])
+    import torch
+    N = p.num_kf
+    H = torch.zeros((7 * N, 7 * N), dtype=torch.float64, device="cuda")
+    gv = torch.zeros(7 * N, dtype=torch.float64, device="cuda")
+    with C.Graph(p, mode=C.PLAIN_FP64) as g:
+        g.gn_step(dev(p.poses_init), H, gv)
+    Ho, go, _, _ = oracle_dense_without_anchor(p, p.poses_init, gsel)
+    sl = slice(7 * k0, 7 * k1)
+    assert rel_fro(H[sl, sl].cpu().numpy(), Ho) <= FP64_TOL
+    assert rel_fro(gv[sl].cpu().numpy(), go) <= FP64_TOL
