@@ -11,31 +11,73 @@ namespace como3r {
 namespace {
 
 // ---- K0: per edge T_ij (FP64 and its FP32 rounding) and Ad_{T_i^{-1}}
+// One warp per edge, SIMD across lanes: lanes 0 and 1 expand the two quaternions, lanes
+// 0..11 form the twelve entries of T_ij and all lanes the 49 entries of Ad.  (FP64 issues
+// ~20 cycles per warp instruction, so the instruction count of a warp is its duration.)
 __global__ void edge_prep_kernel(const double* __restrict__ poses, const EdgeStatic* __restrict__ es, int E,
                                  double* __restrict__ T64, float* __restrict__ T32, double* __restrict__ Ad) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double sh[2][13];  // R (row-major), t, s of keyframe i (row 0) and j (row 1)
+  const int e = blockIdx.x, lane = threadIdx.x;
   if (e >= E) return;
-  Sim3d Ti, Tj;
-  load_pose(poses + 8 * es[e].i, Ti);
-  load_pose(poses + 8 * es[e].j, Tj);
-  double sR[9], t[3];
-  relative_pose(Ti, Tj, sR, t);
+  if (lane < 2) {
+    const double* p = poses + 8 * (lane == 0 ? es[e].i : es[e].j);
+    double R[9];
+    quat_to_rot(p[3], p[4], p[5], p[6], R);
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    T64[12 * e + k] = sR[k];
-    T32[16 * e + k] = (float)sR[k];
+    for (int q = 0; q < 9; ++q) sh[lane][q] = R[q];
+    sh[lane][9] = p[0];
+    sh[lane][10] = p[1];
+    sh[lane][11] = p[2];
+    sh[lane][12] = p[7];
   }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    T64[12 * e + 9 + k] = t[k];
-    T32[16 * e + 9 + k] = (float)t[k];
+  __syncwarp();
+  const double* Ri = sh[0];
+  const double* Rj = sh[1];
+  const double si_inv = 1.0 / Ri[12];
+  // T_ij = T_i^{-1} T_j: sR_ij = (s_j / s_i) R_i^T R_j, t_ij = R_i^T (t_j - t_i) / s_i
+  if (lane < 12) {
+    const int r = lane < 9 ? lane / 3 : lane - 9;
+    double b0, b1, b2, f;
+    if (lane < 9) {
+      const int c = lane % 3;
+      b0 = Rj[c]; b1 = Rj[3 + c]; b2 = Rj[6 + c];
+      f = Rj[12] * si_inv;
+    } else {
+      b0 = Rj[9] - Ri[9]; b1 = Rj[10] - Ri[10]; b2 = Rj[11] - Ri[11];
+      f = si_inv;
+    }
+    const double v = f * fma(Ri[r], b0, fma(Ri[3 + r], b1, Ri[6 + r] * b2));
+    T64[12 * e + lane] = v;
+    T32[16 * e + lane] = (float)v;
+  } else if (lane < 16) {
+    T32[16 * e + lane] = 0.f;
   }
+  // Ad_{T_i^{-1}} with T_i^{-1} = (s' R', t'), s' = 1/s_i, R' = R_i^T, t' = -R_i^T t_i / s_i:
+  // [[s' R', [t']x R', -t'], [0, R', 0], [0, 0, 1]]
+  double tp[3];
 #pragma unroll
-  for (int k = 12; k < 16; ++k) T32[16 * e + k] = 0.f;
-  double A[49];
-  adjoint_of_inverse(Ti, A);
-#pragma unroll
-  for (int k = 0; k < 49; ++k) Ad[49 * e + k] = A[k];
+  for (int r = 0; r < 3; ++r) tp[r] = -si_inv * fma(Ri[r], Ri[9], fma(Ri[3 + r], Ri[10], Ri[6 + r] * Ri[11]));
+  for (int x = lane; x < 49; x += 32) {
+    const int r = x / 7, c = x % 7;
+    double v = 0.0;
+    if (r < 3 && c < 3) {
+      v = si_inv * Ri[3 * c + r];
+    } else if (r < 3 && c < 6) {
+      // ([t']x R')[r][c'] = sum_k [t']x[r][k] R_i[c'][k]
+      const int cc = c - 3;
+      const double t0 = r == 0 ? 0.0 : (r == 1 ? tp[2] : -tp[1]);
+      const double t1 = r == 0 ? -tp[2] : (r == 1 ? 0.0 : tp[0]);
+      const double t2 = r == 0 ? tp[1] : (r == 1 ? -tp[0] : 0.0);
+      v = fma(t0, Ri[3 * cc], fma(t1, Ri[3 * cc + 1], t2 * Ri[3 * cc + 2]));
+    } else if (r < 3) {
+      v = -tp[r];
+    } else if (r < 6 && c >= 3 && c < 6) {
+      v = Ri[3 * (c - 3) + (r - 3)];
+    } else if (r == 6 && c == 6) {
+      v = 1.0;
+    }
+    Ad[49 * e + x] = v;
+  }
 }
 
 // Index of entry (r, c) of the 7x7 H_rel among the 25 unique entries kept by K1, or -1
@@ -165,18 +207,32 @@ __global__ void __launch_bounds__(64) assemble_kernel(int num_slots, const int32
       s += (c & 1) ? -v : v;
     }
     gvec[7 * k + t] = s;
-  } else {
-    const int it = iter_counter ? *iter_counter : 0;
-    for (int g = t; g < G; g += blockDim.x) {
-      double c = 0.0, sk = 0.0;
-      for (int e = edge_offset[g]; e < edge_offset[g + 1]; ++e) {
-        c += edge_cost[e];
-        sk += edge_skip[e];
+  } else if (b < num_slots + N + G) {
+    // cost and skipped matches of graph g: strided partial sums, then a fixed-order tree
+    // (bitwise reproducible; a single thread's chain of FP64 adds is ~70 cycles per edge)
+    __shared__ double sc[64], ss[64];
+    const int g = b - num_slots - N;
+    double c = 0.0, sk = 0.0;
+    for (int e = edge_offset[g] + t; e < edge_offset[g + 1]; e += 64) {
+      c += edge_cost[e];
+      sk += edge_skip[e];
+    }
+    sc[t] = c;
+    ss[t] = sk;
+    __syncthreads();
+    for (int h = 32; h > 0; h >>= 1) {
+      if (t < h) {
+        sc[t] += sc[t + h];
+        ss[t] += ss[t + h];
       }
-      ginfo[g].cost = c;
-      ginfo[g].skipped = (long long)sk;
-      if (cost_hist) cost_hist[(int64_t)it * G + g] = c;
-      if (sk > 0.0) atomicOr(warn, 2);
+      __syncthreads();
+    }
+    if (t == 0) {
+      const int it = iter_counter ? *iter_counter : 0;
+      ginfo[g].cost = sc[0];
+      ginfo[g].skipped = (long long)ss[0];
+      if (cost_hist) cost_hist[(int64_t)it * G + g] = sc[0];
+      if (ss[0] > 0.0) atomicOr(warn, 2);
     }
   }
 }
@@ -199,19 +255,25 @@ __global__ void export_dense_kernel(int num_slots, const int32_t* __restrict__ s
   }
 }
 
+// One keyframe per warp: the warp evaluates the series coefficients together, lane 0
+// applies the update (see edge_prep_kernel on FP64 instruction counts).
 __global__ void retract_kernel(const double* __restrict__ tau, double* __restrict__ poses,
                                const uint8_t* __restrict__ frozen, int N, int* iter_counter) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k == 0 && iter_counter) *iter_counter += 1;
+  const int k = blockIdx.x, lane = threadIdx.x;
+  if (k == 0 && lane == 0 && iter_counter) *iter_counter += 1;
   if (k >= N) return;
   if (frozen && frozen[k]) return;
   const double* t = tau + 7 * k;
   // a zero update leaves the pose bitwise unchanged (no renormalisation)
   if (t[0] == 0.0 && t[1] == 0.0 && t[2] == 0.0 && t[3] == 0.0 && t[4] == 0.0 && t[5] == 0.0 && t[6] == 0.0) return;
+  const double th2 = t[3] * t[3] + t[4] * t[4] + t[5] * t[5];
+  double A, B, C, ez;
+  exp_coefficients_warp(th2, t[6], lane, A, B, C, ez);
+  if (lane != 0) return;
   double p[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) p[q] = poses[8 * k + q];
-  retract_left(tau + 7 * k, p);
+  retract_left_with(t, p, A, B, C, ez);
 #pragma unroll
   for (int q = 0; q < 8; ++q) poses[8 * k + q] = p[q];
 }
@@ -244,7 +306,7 @@ __global__ void check_matches_kernel(const int32_t* __restrict__ midx, const Edg
 cudaError_t launch_edge_prep(const double* poses, const EdgeStatic* es, int E, double* T64, float* T32,
                              double* Ad, cudaStream_t s) {
   if (E <= 0) return cudaSuccess;
-  edge_prep_kernel<<<(E + 63) / 64, 64, 0, s>>>(poses, es, E, T64, T32, Ad);
+  edge_prep_kernel<<<E, 32, 0, s>>>(poses, es, E, T64, T32, Ad);
   return cudaGetLastError();
 }
 
@@ -269,7 +331,7 @@ cudaError_t launch_assemble(int num_slots, const int32_t* slot_contrib_off, cons
                             const int32_t* edge_offset, const double* edge_cost, const double* edge_skip,
                             GraphInfoDev* ginfo, double* cost_hist, const int* iter_counter, int* warn,
                             cudaStream_t s) {
-  assemble_kernel<<<num_slots + N + 1, 64, 0, s>>>(num_slots, slot_contrib_off, slot_contrib, edge_M, A, N,
+  assemble_kernel<<<num_slots + N + G, 64, 0, s>>>(num_slots, slot_contrib_off, slot_contrib, edge_M, A, N,
                                                    kf_contrib_off, kf_contrib, edge_b, gvec, G, edge_offset,
                                                    edge_cost, edge_skip, ginfo, cost_hist, iter_counter, warn);
   return cudaGetLastError();
@@ -285,7 +347,7 @@ cudaError_t launch_export_dense(int num_slots, const int32_t* slot_kf_r, const i
 cudaError_t launch_retract(const double* tau, double* poses, const uint8_t* frozen, int N, int* iter_counter,
                            cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
-  retract_kernel<<<(N + 63) / 64, 64, 0, s>>>(tau, poses, frozen, N, iter_counter);
+  retract_kernel<<<N, 32, 0, s>>>(tau, poses, frozen, N, iter_counter);
   return cudaGetLastError();
 }
 

@@ -1,4 +1,5 @@
-// FP64 Sim(3) device math: pose loading, relative poses, Ad of an inverse, left Exp.
+// FP64 Sim(3) device math: quaternion to rotation, the coefficients of the left Exp and
+// the retraction.
 //
 // A pose is stored (tx, ty, tz, qx, qy, qz, qw, s) and means T = [s R(q) t; 0 1], which
 // maps camera coordinates into the world frame (Sec. III-A).  Tangent vectors are
@@ -7,12 +8,6 @@
 #include <cuda_runtime.h>
 
 namespace como3r {
-
-struct Sim3d {
-  double R[9];  // rotation, row-major
-  double s;     // scale
-  double t[3];  // translation
-};
 
 __device__ __forceinline__ void quat_to_rot(double x, double y, double z, double w, double* R) {
   const double n2 = x * x + y * y + z * z + w * w;
@@ -27,56 +22,6 @@ __device__ __forceinline__ void quat_to_rot(double x, double y, double z, double
   R[6] = 2.0 * (x * z - y * w);
   R[7] = 2.0 * (y * z + x * w);
   R[8] = 1.0 - 2.0 * (x * x + y * y);
-}
-
-__device__ __forceinline__ void load_pose(const double* p, Sim3d& T) {
-  T.t[0] = p[0]; T.t[1] = p[1]; T.t[2] = p[2];
-  quat_to_rot(p[3], p[4], p[5], p[6], T.R);
-  T.s = p[7];
-}
-
-// T_ij = T_i^{-1} T_j: sR_ij = (s_j / s_i) R_i^T R_j, t_ij = R_i^T (t_j - t_i) / s_i.
-__device__ __forceinline__ void relative_pose(const Sim3d& Ti, const Sim3d& Tj, double* sR, double* t) {
-  const double si_inv = 1.0 / Ti.s;
-  const double sij = Tj.s * si_inv;
-  const double dt[3] = {Tj.t[0] - Ti.t[0], Tj.t[1] - Ti.t[1], Tj.t[2] - Ti.t[2]};
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      // (R_i^T R_j)[r][c] = sum_k R_i[k][r] R_j[k][c]
-      sR[3 * r + c] = sij * (Ti.R[r] * Tj.R[c] + Ti.R[3 + r] * Tj.R[3 + c] + Ti.R[6 + r] * Tj.R[6 + c]);
-    }
-    t[r] = si_inv * (Ti.R[r] * dt[0] + Ti.R[3 + r] * dt[1] + Ti.R[6 + r] * dt[2]);
-  }
-}
-
-// Ad of T^{-1} for T = (s R, t): T^{-1} = (s' R', t') with s' = 1/s, R' = R^T,
-// t' = -R^T t / s, and Ad_(s'R', t') = [[s'R', [t']x R', -t'], [0, R', 0], [0, 0, 1]]
-// (tau = (v, omega, zeta); from T hat(tau) T^{-1} = hat(Ad tau)).  Row-major 7x7.
-__device__ __forceinline__ void adjoint_of_inverse(const Sim3d& T, double* Ad) {
-  const double sp = 1.0 / T.s;
-  double Rp[9], tp[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) Rp[3 * r + c] = T.R[3 * c + r];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) tp[r] = -sp * (Rp[3 * r] * T.t[0] + Rp[3 * r + 1] * T.t[1] + Rp[3 * r + 2] * T.t[2]);
-#pragma unroll
-  for (int k = 0; k < 49; ++k) Ad[k] = 0.0;
-  const double tx[9] = {0.0, -tp[2], tp[1], tp[2], 0.0, -tp[0], -tp[1], tp[0], 0.0};  // [t']x
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      Ad[7 * r + c] = sp * Rp[3 * r + c];
-      Ad[7 * r + 3 + c] = tx[3 * r] * Rp[c] + tx[3 * r + 1] * Rp[3 + c] + tx[3 * r + 2] * Rp[6 + c];
-      Ad[7 * (3 + r) + 3 + c] = Rp[3 * r + c];
-    }
-    Ad[7 * r + 6] = -tp[r];
-  }
-  Ad[48] = 1.0;
 }
 
 // Coefficients of W = A I + B [w]x + C [w]x^2 = int_0^1 e^{u zeta} R(u omega) du, the
@@ -108,27 +53,45 @@ __host__ __device__ constexpr ExpSeriesTables build_exp_series_tables() {
   return t;
 }
 static __constant__ ExpSeriesTables kExpSeries = build_exp_series_tables();
+// the same tables in global memory, for lane-dependent indexing (a constant-cache access
+// with different addresses across a warp is serialised)
+static __device__ const ExpSeriesTables kExpSeriesG = build_exp_series_tables();
 
-__device__ __forceinline__ void exp_coefficients(double theta2, double zeta, double& A, double& B, double& C) {
+// A, B, C and e^zeta.  Near the origin the series are evaluated in Horner form: for every
+// power a of zeta the polynomial in theta^2 is an independent chain, then one chain in
+// zeta combines them, and e^zeta = 1 + zeta A (exact to rounding there).  FP64 on this GPU
+// costs ~20 cycles per warp instruction per SM, so the instruction count matters.
+__device__ __forceinline__ void exp_coefficients(double theta2, double zeta, double& A, double& B, double& C,
+                                                 double& ez) {
   const double rho2 = theta2 + zeta * zeta;
   if (rho2 < 1e-2) {
-    A = 0.0; B = 0.0; C = 0.0;
-    double za = 1.0;  // zeta^a
+    const double x = -theta2;
+    double beta[13], gamma[14];
 #pragma unroll
     for (int a = 0; a <= 13; ++a) {
-      if (a <= 12) A += za * kExpSeries.A[a];
-      double tb = 1.0;  // (-theta^2)^b for B, (-theta^2)^(b'-1) with b' = b+1 for C
+      double pb = 0.0, pc = 0.0;
 #pragma unroll
-      for (int b = 0; b < 7; ++b) {
-        if (a <= 12 && a + 2 * b <= 12) B += za * tb * kExpSeries.B[a][b];
-        if (a + 2 * (b + 1) <= 13) C += za * tb * kExpSeries.C[a][b];
-        tb *= -theta2;
+      for (int b = 6; b >= 0; --b) {
+        if (a <= 12 && a + 2 * b <= 12) pb = fma(pb, x, kExpSeries.B[a][b]);
+        if (a + 2 * (b + 1) <= 13) pc = fma(pc, x, kExpSeries.C[a][b]);
       }
-      za *= zeta;
+      if (a <= 12) beta[a] = pb;
+      gamma[a] = pc;
     }
+    A = kExpSeries.A[12];
+    B = beta[12];
+    C = gamma[13];
+#pragma unroll
+    for (int a = 11; a >= 0; --a) {
+      A = fma(A, zeta, kExpSeries.A[a]);
+      B = fma(B, zeta, beta[a]);
+    }
+#pragma unroll
+    for (int a = 12; a >= 0; --a) C = fma(C, zeta, gamma[a]);
+    ez = fma(zeta, A, 1.0);
     return;
   }
-  const double ez = exp(zeta);
+  ez = exp(zeta);
   A = (fabs(zeta) > 1e-12) ? expm1(zeta) / zeta : 1.0 + 0.5 * zeta;
   if (theta2 > 1e-24) {
     const double th = sqrt(theta2);
@@ -143,30 +106,89 @@ __device__ __forceinline__ void exp_coefficients(double theta2, double zeta, dou
   }
 }
 
-// pose <- Exp(tau) pose.  s' = e^zeta s, q' = q_omega (x) q (renormalised),
-// t' = e^zeta R(omega) t + W v.
-__device__ __forceinline__ void retract_left(const double* tau, double* pose) {
+// exp_coefficients evaluated by a whole warp (all lanes call it with the same arguments
+// and receive the same results).  Near the origin lane a < 14 evaluates the polynomial in
+// theta^2 that multiplies zeta^a, scales it by zeta^a (binary powering) and a fixed-order
+// shuffle tree sums the terms: ~40 instructions per warp instead of ~150 on one lane.
+__device__ __forceinline__ void exp_coefficients_warp(double theta2, double zeta, int lane, double& A, double& B,
+                                                      double& C, double& ez) {
+  const double rho2 = theta2 + zeta * zeta;
+  if (rho2 < 1e-2) {
+    const double x = -theta2;
+    const int a = lane < 14 ? lane : 13;
+    double pb = 0.0, pc = 0.0;
+#pragma unroll
+    for (int b = 6; b >= 0; --b) {
+      const double cb = (a <= 12 && a + 2 * b <= 12) ? kExpSeriesG.B[a < 13 ? a : 12][b] : 0.0;
+      const double cc = (a + 2 * (b + 1) <= 13) ? kExpSeriesG.C[a][b] : 0.0;
+      pb = fma(pb, x, cb);
+      pc = fma(pc, x, cc);
+    }
+    double za = 1.0, base = zeta;
+#pragma unroll
+    for (int i = 0, e = a; i < 4; ++i, e >>= 1) {
+      if (e & 1) za *= base;
+      base *= base;
+    }
+    double tA = lane < 13 ? za * kExpSeriesG.A[a < 13 ? a : 12] : 0.0;
+    double tB = lane < 13 ? za * pb : 0.0;
+    double tC = lane < 14 ? za * pc : 0.0;
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) {
+      tA += __shfl_xor_sync(0xffffffffu, tA, off);
+      tB += __shfl_xor_sync(0xffffffffu, tB, off);
+      tC += __shfl_xor_sync(0xffffffffu, tC, off);
+    }
+    A = __shfl_sync(0xffffffffu, tA, 0);
+    B = __shfl_sync(0xffffffffu, tB, 0);
+    C = __shfl_sync(0xffffffffu, tC, 0);
+    ez = fma(zeta, A, 1.0);
+    return;
+  }
+  exp_coefficients(theta2, zeta, A, B, C, ez);
+}
+
+// Rotation of a quaternion that is unit by construction (no renormalisation).
+__device__ __forceinline__ void unit_quat_to_rot(double x, double y, double z, double w, double* R) {
+  R[0] = 1.0 - 2.0 * (y * y + z * z);
+  R[1] = 2.0 * (x * y - z * w);
+  R[2] = 2.0 * (x * z + y * w);
+  R[3] = 2.0 * (x * y + z * w);
+  R[4] = 1.0 - 2.0 * (x * x + z * z);
+  R[5] = 2.0 * (y * z - x * w);
+  R[6] = 2.0 * (x * z - y * w);
+  R[7] = 2.0 * (y * z + x * w);
+  R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+// pose <- Exp(tau) pose given the coefficients A, B, C, e^zeta of exp_coefficients.
+// s' = e^zeta s, q' = q_omega (x) q (renormalised), t' = e^zeta R(omega) t + W v.
+__device__ __forceinline__ void retract_left_with(const double* tau, double* pose, double A, double B, double C,
+                                                  double ez) {
   const double v0 = tau[0], v1 = tau[1], v2 = tau[2];
   const double w0 = tau[3], w1 = tau[4], w2 = tau[5];
-  const double zeta = tau[6];
   const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-  double A, B, C;
-  exp_coefficients(th2, zeta, A, B, C);
-  double k, qw;  // quaternion of the rotation by omega: (k omega, qw)
-  if (th2 > 1e-16) {
+  double k, qw;  // quaternion of the rotation by omega: (k omega, qw), k = sin(theta/2)/theta
+  if (th2 < 1e-2) {
+    // sin(h)/(2h) and cos(h) with h = theta/2 < 0.05: Taylor series in y = -h^2 to h^12
+    const double y = -0.25 * th2;
+    k = fma(fma(fma(fma(fma(y, 1.0 / 39916800.0, 1.0 / 362880.0), y, 1.0 / 5040.0), y, 1.0 / 120.0), y, 1.0 / 6.0), y,
+            1.0);
+    k *= 0.5;
+    qw = fma(fma(fma(fma(fma(fma(y, 1.0 / 479001600.0, 1.0 / 3628800.0), y, 1.0 / 40320.0), y, 1.0 / 720.0), y,
+                     1.0 / 24.0),
+                 y, 0.5),
+             y, 1.0);
+  } else {
     const double th = sqrt(th2);
     double sn, cs;
     sincos(0.5 * th, &sn, &cs);
     k = sn / th;
     qw = cs;
-  } else {
-    k = 0.5 - th2 / 48.0;
-    qw = 1.0 - th2 / 8.0;
   }
   const double ax = k * w0, ay = k * w1, az = k * w2;
   double Rw[9];
-  quat_to_rot(ax, ay, az, qw, Rw);
-  const double ez = exp(zeta);
+  unit_quat_to_rot(ax, ay, az, qw, Rw);
   // W v = A v + B (w x v) + C (w x (w x v))
   const double c1[3] = {w1 * v2 - w2 * v1, w2 * v0 - w0 * v2, w0 * v1 - w1 * v0};
   const double c2[3] = {w1 * c1[2] - w2 * c1[1], w2 * c1[0] - w0 * c1[2], w0 * c1[1] - w1 * c1[0]};
@@ -188,6 +210,14 @@ __device__ __forceinline__ void retract_left(const double* tau, double* pose) {
   pose[0] = tn[0]; pose[1] = tn[1]; pose[2] = tn[2];
   pose[3] = nx * inv; pose[4] = ny * inv; pose[5] = nz * inv; pose[6] = nw * inv;
   pose[7] = ez * pose[7];
+}
+
+// pose <- Exp(tau) pose (one thread).
+__device__ __forceinline__ void retract_left(const double* tau, double* pose) {
+  const double th2 = tau[3] * tau[3] + tau[4] * tau[4] + tau[5] * tau[5];
+  double A, B, C, ez;
+  exp_coefficients(th2, tau[6], A, B, C, ez);
+  retract_left_with(tau, pose, A, B, C, ez);
 }
 
 }  // namespace como3r
