@@ -329,6 +329,12 @@ def run_ours(args):
     h2d = pts_h.numel() * pts_h.element_size() + idx_h.numel() * idx_h.element_size() + poses_h.numel() * 8
     d2h = poses_h.numel() * 8 + (iters + 1) * prob.num_graphs * 8
 
+    # ---- adjoint (gradient of the refined cost w.r.t. per-pixel log-depth and confidence),
+    # unrolled through the same iterations, mixed form
+    ga = C.Graph(prob, mode=C.MIXED)
+    vjp_parts = ga.time_vjp(poses0, iters, reps=3)
+    ga.close()
+
     clocks.stop()
     if rank != 0:
         if dist:
@@ -371,6 +377,16 @@ def run_ours(args):
         "plan": {k: stats[k] for k in ("items", "chunk", "block", "grid", "blocks", "updates", "levels",
                                        "smem_solve")},
     }
+    # per-match adjoint kernel: K1's bytes plus four 4-byte atomic adds per valid match
+    adj_bytes = bytes_alg + 16 * valid
+    adj_ms = vjp_parts["adjoint_match"] / max(iters, 1)
+    adj_gbs = adj_bytes / (adj_ms / 1e3) / 1e9
+    out["adjoint"] = {"mode": "unrolled, mixed", "iters": iters,
+                      "vjp_ms": vjp_parts["forward"] + vjp_parts["envelope"] + vjp_parts["backward"],
+                      "parts_ms": vjp_parts, "forward_solve_ms": ms / args.steps,
+                      "match_kernel": {"bound": "hbm", "ms_per_launch": adj_ms, "achieved": adj_gbs, "peak": peak,
+                                       "unit": "GB/s", "frac": adj_gbs / peak,
+                                       "algorithmic_bytes_per_launch": int(adj_bytes)}}
     if cpu is not None:
         out["cpu_baseline"] = cpu
     print(json.dumps(out), flush=True)

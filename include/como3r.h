@@ -176,6 +176,14 @@ typedef enum { COMO3R_VJP_UNROLLED = 0, COMO3R_VJP_ENVELOPE = 1 } como3r_vjp_mod
 int como3r_vjp(como3r_graph_t graph, const double* poses_init, int32_t iters, int32_t mode, double upstream,
                float* grad_logdepth, float* grad_conf, double* poses_out, double* loss_out);
 
+/* Timing of `reps` unrolled como3r_vjp calls of `iters` iterations from poses_init (one
+ * more untimed call first), CUDA events on the graph's stream; ms[k] receives the mean
+ * duration of: 0 the forward pass with checkpoints, 1 the evaluation at T^K with the
+ * envelope pixel term, 2 the backward iterations, 3 the per-match adjoint kernels of the
+ * backward iterations (part of 2).  Allocates and frees its own gradient buffers. */
+int como3r_time_vjp(como3r_graph_t graph, const double* poses_init, int32_t iters, int32_t reps,
+                    float* ms /* [4] */);
+
 /* Packs pointmaps from the structure parameters: X_p = exp(logdepth_p) rays_p and c_p.
  *   rays device float [n][3] (unit), logdepth / conf device float [n];
  *   points_out device [n][4] in the storage type `dtype` (como3r_dtype); async on stream. */

@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.como3r_plan_stats.argtypes = [ctypes.POINTER(GraphDesc), _i64p]
     lib.como3r_linearize_noalloc.argtypes = [ctypes.POINTER(GraphDesc), vp, vp, vp]
     lib.como3r_vjp.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, vp, vp, vp, _f64p]
+    lib.como3r_time_vjp.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
     lib.como3r_points_from_logdepth.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
     lib.como3r_rays_from_points.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, vp, vp, vp]
     lib.como3r_status_str.argtypes = [ctypes.c_int]
@@ -247,6 +248,12 @@ class Graph:
         st = _check(lib().como3r_vjp(self.handle, _ptr(poses_init), int(iters), int(mode), float(upstream), _ptr(gl),
                                      _ptr(gc), _ptr(poses_out), loss.ctypes.data_as(_f64p)), "vjp")
         return st, gl, gc, loss
+
+    def time_vjp(self, poses_init, iters: int, reps: int = 3) -> dict:
+        """Mean durations (ms) of the parts of an unrolled como3r_vjp (CUDA events)."""
+        ms = (ctypes.c_float * 4)()
+        _check(lib().como3r_time_vjp(self.handle, _ptr(poses_init), int(iters), int(reps), ms), "time_vjp")
+        return dict(zip(["forward", "envelope", "backward", "adjoint_match"], [float(x) for x in ms]))
 
     def last_launch_count(self) -> int:
         return int(lib().como3r_last_launch_count(self.handle))

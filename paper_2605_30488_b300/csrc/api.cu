@@ -528,8 +528,19 @@ int como3r_linearize(como3r_graph_t g, const double* poses, double* edge_out, do
   return *g->h_warn & COMO3R_WARN_SKIPPED;
 }
 
-int como3r_vjp(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t mode, double upstream,
-               float* grad_logdepth, float* grad_conf, double* poses_out, double* loss_out) {
+}  // extern "C"
+
+namespace {
+// CUDA events of one timed adjoint call: ev[0] start, ev[1] after the forward pass,
+// ev[2] after the envelope pass, ev[3] end; ev[4 + 2k], ev[5 + 2k] around the per-match
+// adjoint kernel of backward step k.
+struct VjpEvents {
+  std::vector<cudaEvent_t> ev;
+};
+
+int vjp_impl(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t mode, double upstream,
+             float* grad_logdepth, float* grad_conf, double* poses_out, double* loss_out, VjpEvents* tm) {
+  auto mark = [&](int k) -> cudaError_t { return tm ? cudaEventRecord(tm->ev[k], g->stream) : cudaSuccess; };
   if (!g) return set_error(COMO3R_ERR_INVALID_ARG, "graph handle is NULL");
   if (iters < 0) return set_error(COMO3R_ERR_INVALID_ARG, "iters must be >= 0");
   if (mode != COMO3R_VJP_UNROLLED && mode != COMO3R_VJP_ENVELOPE)
@@ -563,6 +574,7 @@ int como3r_vjp(como3r_graph_t g, const double* poses_init, int32_t iters, int32_
   if ((rc = begin_call(g, poses_init))) return rc;
   cudaStream_t s = g->stream;
   int64_t launches = 0;
+  CK(mark(0), "event");
   // forward with checkpoints: T^k, tau_k and the solve outcome of every iteration
   for (int k = 0; k < iters; ++k) {
     CK(cudaMemcpyAsync(g->d_ckpt + (size_t)k * 8 * N, g->d_poses, sizeof(double) * 8 * N, cudaMemcpyDeviceToDevice, s),
@@ -578,6 +590,7 @@ int como3r_vjp(como3r_graph_t g, const double* poses_init, int32_t iters, int32_
   }
   CK(cudaMemcpyAsync(g->d_ckpt + (size_t)iters * 8 * N, g->d_poses, sizeof(double) * 8 * N, cudaMemcpyDeviceToDevice, s),
      "checkpoint");
+  CK(mark(1), "event");
   // the refined cost at T^K, its pose gradient g(T^K) and the envelope pixel term
   if ((rc = enqueue_linearize(g, s, nullptr, nullptr, nullptr))) return rc;
   CK(cudaMemcpyAsync(g->d_ginfo_final, g->d_ginfo, sizeof(GraphInfoDev) * G, cudaMemcpyDeviceToDevice, s), "info");
@@ -591,6 +604,7 @@ int como3r_vjp(como3r_graph_t g, const double* poses_init, int32_t iters, int32_
                           g->d_T32, nullptr, g->rp, upstream, gl, gc, nullptr, s),
      "adjoint envelope");
   ++launches;
+  CK(mark(2), "event");
   if (mode == COMO3R_VJP_UNROLLED && iters > 0) {
     CK(launch_adjoint_gather(nullptr, nullptr, nullptr, nullptr, g->d_frozen, N, g->d_gvec, upstream, g->d_adj_a, s),
        "adjoint start");
@@ -608,9 +622,11 @@ int como3r_vjp(como3r_graph_t g, const double* poses_init, int32_t iters, int32_
                              g->d_ginfo_hist + (size_t)k * G),
          "adjoint solve");
       CK(launch_adjoint_edge_prep(p.mode, g->d_es, E, g->d_Ad, g->d_adj_u, tau_k, g->d_evec, s), "adjoint edge prep");
+      CK(mark(4 + 2 * k), "event");
       CK(launch_adjoint_match(p.mode, p.dtype, true, g->points, g->midx, g->d_items, g->num_items, g->d_es, g->d_T64,
                               g->d_T32, g->d_evec, g->rp, -1.0, gl, gc, g->d_adj_rec, s),
          "adjoint match");
+      CK(mark(5 + 2 * k), "event");
       CK(launch_adjoint_edge(g->d_adj_rec, g->d_item_off, E, g->d_es, g->d_Ad, g->d_adj_u, tau_k, g->d_edge_adj, s),
          "adjoint edge");
       CK(launch_adjoint_gather(g->d_adj_a2, g->d_edge_adj, g->d_kf_contrib_off, g->d_kf_contrib, g->d_frozen, N,
@@ -622,6 +638,7 @@ int como3r_vjp(como3r_graph_t g, const double* poses_init, int32_t iters, int32_
                        cudaMemcpyDeviceToDevice, s),
        "restore");
   }
+  CK(mark(3), "event");
   if (plain) {
     CK(launch_to_float(g->d_gacc, grad_logdepth, P, s), "to float");
     CK(launch_to_float(g->d_gacc + P, grad_conf, P, s), "to float");
@@ -634,6 +651,50 @@ int como3r_vjp(como3r_graph_t g, const double* poses_init, int32_t iters, int32_
   if (loss_out)
     for (int k = 0; k < G; ++k) loss_out[k] = g->h_ginfo[k].cost;
   return *g->h_warn;
+}
+
+}  // namespace
+
+extern "C" {
+
+int como3r_vjp(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t mode, double upstream,
+               float* grad_logdepth, float* grad_conf, double* poses_out, double* loss_out) {
+  return vjp_impl(g, poses_init, iters, mode, upstream, grad_logdepth, grad_conf, poses_out, loss_out, nullptr);
+}
+
+int como3r_time_vjp(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t reps, float* ms) {
+  if (!g || !ms || reps < 1 || iters < 0) return set_error(COMO3R_ERR_INVALID_ARG, "bad time_vjp arguments");
+  const int64_t P = g->plan.total_px;
+  float* grads = nullptr;
+  CK(cudaMalloc(&grads, sizeof(float) * 2 * (size_t)std::max<int64_t>(P, 1)), "cudaMalloc");
+  VjpEvents tm;
+  tm.ev.resize(4 + 2 * (size_t)iters);
+  int rc = COMO3R_OK;
+  for (auto& e : tm.ev)
+    if (cudaEventCreate(&e) != cudaSuccess) rc = set_error(COMO3R_ERR_CUDA, "event create");
+  double acc[4] = {0, 0, 0, 0};
+  for (int r = 0; r <= reps && rc >= 0; ++r) {  // the first call warms up
+    rc = vjp_impl(g, poses_init, iters, COMO3R_VJP_UNROLLED, 1.0, grads, grads + P, nullptr, nullptr, &tm);
+    if (rc < 0 || r == 0) continue;
+    float a = 0.f, b = 0.f, c = 0.f;
+    cudaEventElapsedTime(&a, tm.ev[0], tm.ev[1]);
+    cudaEventElapsedTime(&b, tm.ev[1], tm.ev[2]);
+    cudaEventElapsedTime(&c, tm.ev[2], tm.ev[3]);
+    acc[0] += a;
+    acc[1] += b;
+    acc[2] += c;
+    for (int k = 0; k < iters; ++k) {
+      float d = 0.f;
+      cudaEventElapsedTime(&d, tm.ev[4 + 2 * k], tm.ev[5 + 2 * k]);
+      acc[3] += d;
+    }
+  }
+  for (auto& e : tm.ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(grads);
+  if (rc < 0) return rc;
+  for (int k = 0; k < 4; ++k) ms[k] = (float)(acc[k] / reps);
+  return COMO3R_OK;
 }
 
 int como3r_points_from_logdepth(const float* rays, const float* logdepth, const float* conf, int64_t n,

@@ -108,12 +108,29 @@ __global__ void __launch_bounds__(256) adjoint_match_kernel(
 #pragma unroll
     for (int q = 0; q < kAdjRec; ++q) F[q] = R(0);
     const int32_t* idx = midx + e.idx_off;
-    for (int m = item.begin + lane; m < item.end; m += 32) {
-      const int n = __ldg(idx + m);
+    // software pipeline: while group g (32 pixels) is differentiated, the pixels of group
+    // g + 1 and the match indices of group g + 2 are in flight
+    int nA = item.begin + lane < item.end ? __ldg(idx + item.begin + lane) : -1;
+    int nB = item.begin + 32 + lane < item.end ? __ldg(idx + item.begin + 32 + lane) : -1;
+    R ax = 0, ay = 0, az = 0, ac = 0, bx = 0, by = 0, bz = 0, bc = 0;
+    if (nA >= 0) {
+      load_point<DT, R>(points, e.pix_i + item.begin + lane, ax, ay, az, ac);
+      load_point<DT, R>(points, e.pix_j + nA, bx, by, bz, bc);
+    }
+    for (int g0 = item.begin; g0 < item.end; g0 += 32) {
+      const int m = g0 + lane;
+      R nax = 0, nay = 0, naz = 0, nac = 0, nbx = 0, nby = 0, nbz = 0, nbc = 0;
+      if (nB >= 0) {
+        load_point<DT, R>(points, e.pix_i + m + 32, nax, nay, naz, nac);
+        load_point<DT, R>(points, e.pix_j + nB, nbx, nby, nbz, nbc);
+      }
+      const int nC = m + 64 < item.end ? __ldg(idx + m + 64) : -1;
+      const int n = nA;
+      const R xi = ax, yi = ay, zi = az, ci = ac, xj = bx, yj = by, zj = bz, cj = bc;
+      nA = nB;
+      nB = nC;
+      ax = nax; ay = nay; az = naz; ac = nac; bx = nbx; by = nby; bz = nbz; bc = nbc;
       if (n < 0) continue;
-      R xi, yi, zi, ci, xj, yj, zj, cj;
-      load_point<DT, R>(points, e.pix_i + m, xi, yi, zi, ci);
-      load_point<DT, R>(points, e.pix_j + n, xj, yj, zj, cj);
       const V3<R> sx = v3(T[0] * xj + T[1] * yj + T[2] * zj, T[3] * xj + T[4] * yj + T[5] * zj,
                           T[6] * xj + T[7] * yj + T[8] * zj);  // sR X_j = dx / dl_j
       const V3<R> x = v3(sx.x + T[9], sx.y + T[10], sx.z + T[11]);
@@ -230,152 +247,174 @@ __device__ __forceinline__ void ad_transpose_apply(const double* xi, const doubl
   out[6] = -(v0 * y0 + v1 * y1 + v2 * y2);
 }
 
-// Per edge: Ad-rotated adjoint and step differences for the match kernel,
+// Per edge (one warp; FP64 costs ~20 cycles per warp instruction, so work is spread
+// over lanes): Ad-rotated adjoint and step differences for the match kernel,
 // u~ = Ad (u_j - u_i), tau~ = Ad (tau_j - tau_i), stored in R (16 per edge).
 template <typename R>
 __global__ void adjoint_edge_prep_kernel(const EdgeStatic* __restrict__ es, int E, const double* __restrict__ Ad,
                                          const double* __restrict__ u, const double* __restrict__ tau,
                                          R* __restrict__ evec) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double d[14];  // u_j - u_i, tau_j - tau_i
+  const int e = blockIdx.x, lane = threadIdx.x;
   if (e >= E) return;
   const int i = es[e].i, j = es[e].j;
-  double du[7], dt[7];
+  if (lane < 14) {
+    const double* src = lane < 7 ? u : tau;
+    const int k = lane % 7;
+    d[lane] = src[7 * j + k] - src[7 * i + k];
+  }
+  __syncwarp();
+  if (lane < 14) {
+    const int r = lane % 7, base = lane < 7 ? 0 : 7;
+    const double* A = Ad + 49 * (int64_t)e + 7 * r;
+    double acc = 0.0;
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    du[k] = u[7 * j + k] - u[7 * i + k];
-    dt[k] = tau[7 * j + k] - tau[7 * i + k];
+    for (int c = 0; c < 7; ++c) acc = fma(A[c], d[base + c], acc);
+    evec[16 * e + lane] = (R)acc;
+  } else if (lane < 16) {
+    evec[16 * e + lane] = R(0);
   }
-  const double* A = Ad + 49 * (int64_t)e;
-  for (int r = 0; r < 7; ++r) {
-    double su = 0.0, st = 0.0;
-    for (int c = 0; c < 7; ++c) {
-      su += A[7 * r + c] * du[c];
-      st += A[7 * r + c] * dt[c];
-    }
-    evec[16 * e + r] = (R)su;
-    evec[16 * e + 7 + r] = (R)st;
-  }
-  evec[16 * e + 14] = R(0);
-  evec[16 * e + 15] = R(0);
 }
 
-// Per edge: fixed-order FP64 sum of the item records, then the keyframe terms
-// out[e][0..6] = dF/dd_i, out[e][7..13] = dF/dd_j.
+// Per edge (one warp): fixed-order FP64 sum of the item records (lane q sums slot q), then
+// the keyframe terms out[e][0..6] = dF/dd_i, out[e][7..13] = dF/dd_j.
 __global__ void adjoint_edge_kernel(const double* __restrict__ rec, const int32_t* __restrict__ item_off, int E,
                                     const EdgeStatic* __restrict__ es, const double* __restrict__ Ad,
                                     const double* __restrict__ u, const double* __restrict__ tau,
                                     double* __restrict__ out) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double F[kAdjRec], y[kAdjRec], d[14];
+  const int e = blockIdx.x, lane = threadIdx.x;
   if (e >= E) return;
-  double F[kAdjRec];
-  for (int q = 0; q < kAdjRec; ++q) F[q] = 0.0;
-  for (int it = item_off[e]; it < item_off[e + 1]; ++it)
-    for (int q = 0; q < kAdjRec; ++q) F[q] += rec[(int64_t)it * kAdjRec + q];
-  const double* A = Ad + 49 * (int64_t)e;
-  double yx[7], yu[7], yt[7];
-  for (int c = 0; c < 7; ++c) {
-    double a = 0.0, b = 0.0, d = 0.0;
-    for (int r = 0; r < 7; ++r) {
-      a += A[7 * r + c] * F[r];
-      b += A[7 * r + c] * F[7 + r];
-      d += A[7 * r + c] * F[14 + r];
-    }
-    yx[c] = a;
-    yu[c] = b;
-    yt[c] = d;
-  }
   const int i = es[e].i, j = es[e].j;
-  double du[7], dt[7], pu[7], pt[7];
-  for (int k = 0; k < 7; ++k) {
-    du[k] = u[7 * j + k] - u[7 * i + k];
-    dt[k] = tau[7 * j + k] - tau[7 * i + k];
+  if (lane < kAdjRec) {
+    double f = 0.0;
+    for (int it = item_off[e]; it < item_off[e + 1]; ++it) f += rec[(int64_t)it * kAdjRec + lane];
+    F[lane] = f;
+  } else if (lane - kAdjRec < 7) {
+    const int k = lane - kAdjRec;
+    d[k] = u[7 * j + k] - u[7 * i + k];
   }
-  ad_transpose_apply(du, yu, pu);
-  ad_transpose_apply(dt, yt, pt);
-  for (int k = 0; k < 7; ++k) {
-    out[14 * e + k] = -yx[k] + pu[k] + pt[k];
-    out[14 * e + 7 + k] = yx[k];
+  if (lane < 7) d[7 + lane] = tau[7 * j + lane] - tau[7 * i + lane];
+  __syncwarp();
+  // y = [Ad^T F_xi, Ad^T F_u~, Ad^T F_tau~]
+  if (lane < kAdjRec) {
+    const int c = lane % 7, base = lane - c;
+    const double* A = Ad + 49 * (int64_t)e;
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < 7; ++r) acc = fma(A[7 * r + c], F[base + r], acc);
+    y[lane] = acc;
   }
-}
-
-// 7x7 helpers (row-major, one thread).
-__device__ void mat7_mul(const double* A, const double* B, double* C) {
-  for (int r = 0; r < 7; ++r)
-    for (int c = 0; c < 7; ++c) {
-      double s = 0.0;
-      for (int k = 0; k < 7; ++k) s += A[7 * r + k] * B[7 * k + c];
-      C[7 * r + c] = s;
+  __syncwarp();
+  if (lane == 0) {
+    double pu[7], pt[7];
+    ad_transpose_apply(d, y + 7, pu);
+    ad_transpose_apply(d + 7, y + 14, pt);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      out[14 * e + k] = -y[k] + pu[k] + pt[k];
+      out[14 * e + 7 + k] = y[k];
     }
+  }
 }
 
-// Per keyframe: a' = exp(ad_tau)^T a and rhs = -phi1(ad_tau)^T a (so the solve returns
-// u = A^{-1} tau_bar); frozen keyframes get zeros.  exp and phi1 of X = ad_tau by scaling
-// and squaring (Higham, 2005): X / 2^s with ||X / 2^s|| <= 1/2, a 20-term Taylor series
-// of phi1 (Horner), exp = I + X phi1, then s doublings phi1(2X) = phi1(X)(exp(X) + I)/2,
-// exp(2X) = exp(X)^2.
+// C = A B for 7x7 row-major matrices in shared memory, one warp: lane l computes entries
+// l and l + 32 (7 FMA each).  Reads A, B and writes C after a warp barrier.
+__device__ __forceinline__ void warp_mat7_mul(const double* A, const double* B, double* C, int lane) {
+  double c0 = 0.0, c1 = 0.0;
+  const int r0 = lane / 7, q0 = lane % 7, e1 = lane + 32, r1 = e1 / 7, q1 = e1 % 7;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    c0 = fma(A[7 * r0 + k], B[7 * k + q0], c0);
+    if (e1 < 49) c1 = fma(A[7 * r1 + k], B[7 * k + q1], c1);
+  }
+  __syncwarp();
+  C[lane] = c0;
+  if (e1 < 49) C[e1] = c1;
+  __syncwarp();
+}
+
+// Per keyframe (one warp): a' = exp(ad_tau)^T a and rhs = -phi1(ad_tau)^T a (so the solve
+// returns u = A^{-1} tau_bar); frozen keyframes get zeros.  exp and phi1 of X = ad_tau by
+// scaling and squaring (Higham, 2005): X / 2^s with ||X / 2^s||_inf <= 1/2, a 20-term
+// Taylor series of phi1 (Horner), exp = I + X phi1, then s doublings
+// phi1(2X) = phi1(X)(exp(X) + I)/2, exp(2X) = exp(X)^2.
 __global__ void adjoint_keyframe_kernel(const double* __restrict__ a, const double* __restrict__ tau,
                                         const uint8_t* __restrict__ frozen, int N, double* __restrict__ a_out,
                                         double* __restrict__ rhs) {
-  const int kf = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double X[49], P[49], E[49], T[49];
+  const int kf = blockIdx.x, lane = threadIdx.x;
   if (kf >= N) return;
   if (frozen[kf]) {
-    for (int k = 0; k < 7; ++k) a_out[7 * kf + k] = rhs[7 * kf + k] = 0.0;
+    if (lane < 7) a_out[7 * kf + lane] = rhs[7 * kf + lane] = 0.0;
     return;
   }
   const double* t = tau + 7 * kf;
-  double X[49] = {0};
   // ad_tau = [[w^ + z I, v^, -v], [0, w^, 0], [0, 0, 0]]
-  const double v0 = t[0], v1 = t[1], v2 = t[2], w0 = t[3], w1 = t[4], w2 = t[5], z = t[6];
-  const double W[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
-  const double V[9] = {0.0, -v2, v1, v2, 0.0, -v0, -v1, v0, 0.0};
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) {
-      X[7 * r + c] = W[3 * r + c] + (r == c ? z : 0.0);
-      X[7 * r + 3 + c] = V[3 * r + c];
-      X[7 * (3 + r) + 3 + c] = W[3 * r + c];
-    }
-  X[6] = -v0;
-  X[13] = -v1;
-  X[20] = -v2;
-  double nrm = 0.0;
-  for (int r = 0; r < 7; ++r) {
-    double s = 0.0;
-    for (int c = 0; c < 7; ++c) s += fabs(X[7 * r + c]);
-    nrm = fmax(nrm, s);
+  for (int x = lane; x < 49; x += 32) {
+    const int r = x / 7, c = x % 7;
+    auto skew = [&](const double* w, int i, int k) -> double {
+      if (i == k) return 0.0;
+      if (i == 0) return k == 1 ? -w[2] : w[1];
+      if (i == 1) return k == 0 ? w[2] : -w[0];
+      return k == 0 ? -w[1] : w[0];
+    };
+    double v = 0.0;
+    if (r < 3 && c < 3) v = skew(t + 3, r, c) + (r == c ? t[6] : 0.0);
+    else if (r < 3 && c < 6) v = skew(t, r, c - 3);
+    else if (r < 3) v = -t[r];
+    else if (r < 6 && c >= 3 && c < 6) v = skew(t + 3, r - 3, c - 3);
+    X[x] = v;
   }
+  __syncwarp();
+  // infinity norm (max row sum), the same value in every lane
+  double rs = 0.0;
+  if (lane < 7)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) rs += fabs(X[7 * lane + c]);
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1) rs = fmax(rs, __shfl_xor_sync(0xffffffffu, rs, off));
+  rs = __shfl_sync(0xffffffffu, rs, 0);
   int sq = 0;
-  while (nrm > 0.5 && sq < 64) {
-    nrm *= 0.5;
+  while (rs > 0.5 && sq < 64) {
+    rs *= 0.5;
     ++sq;
   }
   const double f = ldexp(1.0, -sq);
-  for (int q = 0; q < 49; ++q) X[q] *= f;
-  double P[49], E[49], Tm[49];
-  for (int q = 0; q < 49; ++q) P[q] = (q % 8 == 0) ? 1.0 : 0.0;
-  for (int n = 20; n >= 1; --n) {  // P <- I + X P / (n + 1)
-    mat7_mul(X, P, Tm);
-    const double inv = 1.0 / (double)(n + 1);
-    for (int q = 0; q < 49; ++q) P[q] = ((q % 8 == 0) ? 1.0 : 0.0) + Tm[q] * inv;
+  for (int x = lane; x < 49; x += 32) {
+    X[x] *= f;
+    P[x] = (x % 8 == 0) ? 1.0 : 0.0;
   }
-  mat7_mul(X, P, E);
-  for (int q = 0; q < 49; q += 8) E[q] += 1.0;
-  for (int s = 0; s < sq; ++s) {
-    for (int q = 0; q < 49; q += 8) E[q] += 1.0;  // E + I
-    mat7_mul(P, E, Tm);
-    for (int q = 0; q < 49; q += 8) E[q] -= 1.0;
-    for (int q = 0; q < 49; ++q) P[q] = 0.5 * Tm[q];
-    mat7_mul(E, E, Tm);
-    for (int q = 0; q < 49; ++q) E[q] = Tm[q];
+  __syncwarp();
+  for (int n = 20; n >= 1; --n) {  // P <- I + X P / (n + 1)
+    warp_mat7_mul(X, P, T, lane);
+    const double inv = 1.0 / (double)(n + 1);
+    for (int x = lane; x < 49; x += 32) P[x] = ((x % 8 == 0) ? 1.0 : 0.0) + T[x] * inv;
+    __syncwarp();
+  }
+  warp_mat7_mul(X, P, E, lane);
+  if (lane < 7) E[8 * lane] += 1.0;
+  __syncwarp();
+  for (int s2 = 0; s2 < sq; ++s2) {
+    if (lane < 7) E[8 * lane] += 1.0;  // E + I
+    __syncwarp();
+    warp_mat7_mul(P, E, T, lane);
+    if (lane < 7) E[8 * lane] -= 1.0;
+    for (int x = lane; x < 49; x += 32) P[x] = 0.5 * T[x];
+    __syncwarp();
+    warp_mat7_mul(E, E, T, lane);
+    for (int x = lane; x < 49; x += 32) E[x] = T[x];
+    __syncwarp();
   }
   const double* ak = a + 7 * kf;
-  for (int c = 0; c < 7; ++c) {
-    double se = 0.0, sp = 0.0;
-    for (int r = 0; r < 7; ++r) {
-      se += E[7 * r + c] * ak[r];
-      sp += P[7 * r + c] * ak[r];
-    }
-    a_out[7 * kf + c] = se;
-    rhs[7 * kf + c] = -sp;
+  if (lane < 14) {
+    const int c = lane % 7;
+    const double* M = lane < 7 ? E : P;
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < 7; ++r) acc = fma(M[7 * r + c], ak[r], acc);
+    if (lane < 7) a_out[7 * kf + c] = acc;
+    else rhs[7 * kf + c] = -acc;
   }
 }
 
@@ -493,25 +532,24 @@ cudaError_t launch_adjoint_match(int mode, int dtype, bool phi, const void* poin
 cudaError_t launch_adjoint_edge_prep(int mode, const EdgeStatic* es, int E, const double* Ad, const double* u,
                                      const double* tau, void* evec, cudaStream_t s) {
   if (E == 0) return cudaSuccess;
-  const int grid = (E + 127) / 128;
   if (mode == 1)
-    adjoint_edge_prep_kernel<float><<<grid, 128, 0, s>>>(es, E, Ad, u, tau, (float*)evec);
+    adjoint_edge_prep_kernel<float><<<E, 32, 0, s>>>(es, E, Ad, u, tau, (float*)evec);
   else
-    adjoint_edge_prep_kernel<double><<<grid, 128, 0, s>>>(es, E, Ad, u, tau, (double*)evec);
+    adjoint_edge_prep_kernel<double><<<E, 32, 0, s>>>(es, E, Ad, u, tau, (double*)evec);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_edge(const double* rec, const int32_t* item_off, int E, const EdgeStatic* es,
                                 const double* Ad, const double* u, const double* tau, double* out, cudaStream_t s) {
   if (E == 0) return cudaSuccess;
-  adjoint_edge_kernel<<<(E + 63) / 64, 64, 0, s>>>(rec, item_off, E, es, Ad, u, tau, out);
+  adjoint_edge_kernel<<<E, 32, 0, s>>>(rec, item_off, E, es, Ad, u, tau, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_keyframe(const double* a, const double* tau, const uint8_t* frozen, int N, double* a_out,
                                     double* rhs, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  adjoint_keyframe_kernel<<<(N + 31) / 32, 32, 0, s>>>(a, tau, frozen, N, a_out, rhs);
+  adjoint_keyframe_kernel<<<N, 32, 0, s>>>(a, tau, frozen, N, a_out, rhs);
   return cudaGetLastError();
 }
 
