@@ -187,6 +187,122 @@ __device__ __forceinline__ void accumulate(R xi, R yi, R zi, R ci, R xj, R yj, R
   h[31] = fma(f3, d, h[31]);
 }
 
+// ---- two matches per lane in packed FP32x2 arithmetic (sm_100+ FFMA2 / FMUL2 / FADD2)
+// Element .x is match A, .y is match B; every operation is the scalar one of accumulate()
+// applied to both elements, so each element's rounding is unchanged while the FP32
+// instruction count of the arithmetic roughly halves.  Accumulators stay separate per
+// element (AccPair) and are added when the record is written.
+struct AccPair {
+  float2 v[kAcc];
+  float2 Ew, Em;
+  int skipped;
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < kAcc; ++k) v[k] = make_float2(0.f, 0.f);
+    Ew = Em = make_float2(0.f, 0.f);
+    skipped = 0;
+  }
+};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// A pair of matches (either may be a padding or degenerate slot: its inputs are replaced
+// by a benign point with zero confidence, so it contributes exactly zero).
+__device__ __forceinline__ void accumulate_pair(float2 xi, float2 yi, float2 zi, float2 ci, float2 xj, float2 yj,
+                                                float2 zj, float2 cj, bool useA, bool useB, const float* T,
+                                                const Consts<float>& k, AccPair& acc) {
+  const float2 x0 = fma2(f2(T[0]), xj, fma2(f2(T[1]), yj, fma2(f2(T[2]), zj, f2(T[9]))));
+  const float2 x1 = fma2(f2(T[3]), xj, fma2(f2(T[4]), yj, fma2(f2(T[5]), zj, f2(T[10]))));
+  const float2 x2 = fma2(f2(T[6]), xj, fma2(f2(T[7]), yj, fma2(f2(T[8]), zj, f2(T[11]))));
+  float2 d2 = fma2(x0, x0, fma2(x1, x1, mul2(x2, x2)));
+  float2 di2 = fma2(xi, xi, fma2(yi, yi, mul2(zi, zi)));
+  float2 cc = mul2(ci, cj);
+  const float th2 = 1e-24f, inf = kInfinity<float>();
+  const bool okA = useA && (fminf(d2.x, di2.x) > th2) & (fmaxf(fmaxf(d2.x, di2.x), cc.x) < inf) & (cc.x >= 0.f);
+  const bool okB = useB && (fminf(d2.y, di2.y) > th2) & (fmaxf(fmaxf(d2.y, di2.y), cc.y) < inf) & (cc.y >= 0.f);
+  acc.skipped += (useA && !okA) + (useB && !okB);
+  if (!okA && !okB) return;
+  // a slot that does not contribute: unit ranges, zero confidence -> every term is 0
+  float2 XI = xi, YI = yi, ZI = zi;
+  if (!okA) { d2.x = 1.f; di2.x = 1.f; cc.x = 0.f; XI.x = 1.f; YI.x = 0.f; ZI.x = 0.f; }
+  if (!okB) { d2.y = 1.f; di2.y = 1.f; cc.y = 0.f; XI.y = 1.f; YI.y = 0.f; ZI.y = 0.f; }
+  const float2 X0 = f2(okA ? x0.x : 1.f, okB ? x0.y : 1.f);
+  const float2 X1 = f2(okA ? x1.x : 0.f, okB ? x1.y : 0.f);
+  const float2 X2 = f2(okA ? x2.x : 0.f, okB ? x2.y : 0.f);
+  const float2 rd = f2(rsq(d2.x), rsq(d2.y)), d = mul2(d2, rd);
+  const float2 rdi = f2(rsq(di2.x), rsq(di2.y)), di = mul2(di2, rdi);
+  const float2 a = mul2(X0, rd), b = mul2(X1, rd), c = mul2(X2, rd);
+  const float2 e0 = fma2(neg2(XI), rdi, a), e1 = fma2(neg2(YI), rdi, b), e2 = fma2(neg2(ZI), rdi, c);
+  const float2 e3 = add2(d, neg2(di));
+  const float2 q = f2(nn_sqrt(cc.x), nn_sqrt(cc.y));
+  const float2 sq = f2(nn_sqrt(q.x), nn_sqrt(q.y));
+  const float2 sr = mul2(sq, f2(k.isr)), sd = mul2(sq, f2(k.isd));
+  const float2 r0 = mul2(sr, e0), r1 = mul2(sr, e1), r2 = mul2(sr, e2), r3 = mul2(sd, e3);
+  const float2 a0 = f2(fabsf(r0.x), fabsf(r0.y)), a1 = f2(fabsf(r1.x), fabsf(r1.y));
+  const float2 a2 = f2(fabsf(r2.x), fabsf(r2.y)), a3 = f2(fabsf(r3.x), fabsf(r3.y));
+  const float2 kr0 = mul2(f2(k.kappa), f2(rcp(a0.x), rcp(a0.y)));
+  const float2 kr1 = mul2(f2(k.kappa), f2(rcp(a1.x), rcp(a1.y)));
+  const float2 kr2 = mul2(f2(k.kappa), f2(rcp(a2.x), rcp(a2.y)));
+  const float2 kr3 = mul2(f2(k.kappa), f2(rcp(a3.x), rcp(a3.y)));
+  const float2 w0 = f2(fminf(1.f, kr0.x), fminf(1.f, kr0.y)), w1 = f2(fminf(1.f, kr1.x), fminf(1.f, kr1.y));
+  const float2 w2 = f2(fminf(1.f, kr2.x), fminf(1.f, kr2.y)), w3 = f2(fminf(1.f, kr3.x), fminf(1.f, kr3.y));
+  const float2 m0 = f2(fminf(a0.x, k.kappa), fminf(a0.y, k.kappa)), m1 = f2(fminf(a1.x, k.kappa), fminf(a1.y, k.kappa));
+  const float2 m2 = f2(fminf(a2.x, k.kappa), fminf(a2.y, k.kappa)), m3 = f2(fminf(a3.x, k.kappa), fminf(a3.y, k.kappa));
+  acc.Ew = fma2(mul2(w0, r0), r0, fma2(mul2(w1, r1), r1, fma2(mul2(w2, r2), r2, fma2(mul2(w3, r3), r3, acc.Ew))));
+  acc.Em = fma2(m0, m0, fma2(m1, m1, fma2(m2, m2, fma2(m3, m3, acc.Em))));
+  const float2 qr = mul2(q, f2(k.ivr));
+  const float2 u0 = mul2(w0, qr), u1 = mul2(w1, qr), u2 = mul2(w2, qr), u3 = mul2(mul2(w3, q), f2(k.ivd));
+  const float2 g0 = mul2(u0, e0), g1 = mul2(u1, e1), g2 = mul2(u2, e2), g3 = mul2(u3, e3);
+  const float2 ard = mul2(a, rd), brd = mul2(b, rd), crd = mul2(c, rd);
+  const float2 p00 = fma2(neg2(ard), a, rd), p11 = fma2(neg2(brd), b, rd), p22 = fma2(neg2(crd), c, rd);
+  const float2 p01 = mul2(neg2(ard), b), p02 = mul2(neg2(ard), c), p12 = mul2(neg2(brd), c);
+  const float2 w00 = mul2(u0, p00), w01 = mul2(u0, p01), w02 = mul2(u0, p02);
+  const float2 w10 = mul2(u1, p01), w11 = mul2(u1, p11), w12 = mul2(u1, p12);
+  const float2 w20 = mul2(u2, p02), w21 = mul2(u2, p12), w22 = mul2(u2, p22);
+  const float2 ua = mul2(u3, a), ub = mul2(u3, b), uc = mul2(u3, c);
+  float2* h = acc.v;
+  h[0] = fma2(w00, p00, fma2(w10, p01, fma2(w20, p02, fma2(ua, a, h[0]))));
+  h[1] = fma2(w00, p01, fma2(w10, p11, fma2(w20, p12, fma2(ua, b, h[1]))));
+  h[2] = fma2(w00, p02, fma2(w10, p12, fma2(w20, p22, fma2(ua, c, h[2]))));
+  h[3] = fma2(w01, p01, fma2(w11, p11, fma2(w21, p12, fma2(ub, b, h[3]))));
+  h[4] = fma2(w01, p02, fma2(w11, p12, fma2(w21, p22, fma2(ub, c, h[4]))));
+  h[5] = fma2(w02, p02, fma2(w12, p12, fma2(w22, p22, fma2(uc, c, h[5]))));
+  const float2 na = neg2(a), nb = neg2(b), nc = neg2(c);
+  h[6] = fma2(nc, w10, fma2(b, w20, h[6]));
+  h[7] = fma2(c, w00, fma2(na, w20, h[7]));
+  h[8] = fma2(nb, w00, fma2(a, w10, h[8]));
+  h[9] = fma2(nc, w11, fma2(b, w21, h[9]));
+  h[10] = fma2(c, w01, fma2(na, w21, h[10]));
+  h[11] = fma2(nb, w01, fma2(a, w11, h[11]));
+  h[12] = fma2(nc, w12, fma2(b, w22, h[12]));
+  h[13] = fma2(c, w02, fma2(na, w22, h[13]));
+  h[14] = fma2(nb, w02, fma2(a, w12, h[14]));
+  const float2 cc2 = mul2(c, c), bb2 = mul2(b, b), aa2 = mul2(a, a);
+  h[15] = fma2(u1, cc2, fma2(u2, bb2, h[15]));
+  h[16] = fma2(neg2(mul2(u2, a)), b, h[16]);
+  h[17] = fma2(neg2(mul2(u1, a)), c, h[17]);
+  h[18] = fma2(u0, cc2, fma2(u2, aa2, h[18]));
+  h[19] = fma2(neg2(mul2(u0, b)), c, h[19]);
+  h[20] = fma2(u0, bb2, fma2(u1, aa2, h[20]));
+  const float2 ud = mul2(u3, d);
+  h[21] = fma2(ud, a, h[21]);
+  h[22] = fma2(ud, b, h[22]);
+  h[23] = fma2(ud, c, h[23]);
+  h[24] = fma2(ud, d, h[24]);
+  h[25] = fma2(g0, p00, fma2(g1, p01, fma2(g2, p02, fma2(g3, a, h[25]))));
+  h[26] = fma2(g0, p01, fma2(g1, p11, fma2(g2, p12, fma2(g3, b, h[26]))));
+  h[27] = fma2(g0, p02, fma2(g1, p12, fma2(g2, p22, fma2(g3, c, h[27]))));
+  h[28] = fma2(nc, g1, fma2(b, g2, h[28]));
+  h[29] = fma2(c, g0, fma2(na, g2, h[29]));
+  h[30] = fma2(nb, g0, fma2(a, g1, h[30]));
+  h[31] = fma2(g3, d, h[31]);
+}
+
 // Error-free transformation: s + err == a + b exactly (Knuth's TwoSum).
 __device__ __forceinline__ float two_sum(float a, float b, float& err) {
   const float s = __fadd_rn(a, b);
@@ -489,8 +605,8 @@ __device__ __forceinline__ void prefetch_indices(int32_t* buf, const int32_t* __
   for (int q = n16 + lane; q < n; q += 32) cp_async4(buf + q, idx + item.begin + q);
 }
 
-template <typename R, int DT>
-__global__ void __launch_bounds__(256, 2) residual_reduce_async_kernel(
+template <typename R, int DT, bool PAIR>
+__global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kernel(
     const void* __restrict__ points, const int32_t* __restrict__ midx, const Item* __restrict__ items,
     int num_items, const EdgeStatic* __restrict__ es, const double* __restrict__ T64,
     const float* __restrict__ T32, RobustParams rp, void* __restrict__ partials, WarpSched ws) {
@@ -520,6 +636,8 @@ __global__ void __launch_bounds__(256, 2) residual_reduce_async_kernel(
   cp_commit();
   Acc<R> acc;
   acc.zero();
+  AccPair pacc;  // PAIR only
+  if constexpr (PAIR) pacc.zero();
   for (int it = it0; it < it1; ++it, b ^= 1) {
     const Item item = items[it];
     const int next = it + 1;
@@ -564,20 +682,57 @@ __global__ void __launch_bounds__(256, 2) residual_reduce_async_kernel(
     };
 #pragma unroll
     for (int s0 = 0; s0 < kRing; ++s0) issue(s0);
-    for (int gidx = 0; gidx < ngroups; ++gidx) {
-      cp_wait<kRing - 1>();
-      if (32 * gidx + lane < nvalid) {
-        const unsigned char* slot = ring + (size_t)(gidx % kRing) * 32 * 2 * PX;
-        R xi, yi, zi, ci, xj, yj, zj, cj;
-        read_px<DT, R>(slot, xi, yi, zi, ci);
-        read_px<DT, R>(slot + PX, xj, yj, zj, cj);
-        accumulate<R>(xi, yi, zi, ci, xj, yj, zj, cj, T, k, acc);
+    if constexpr (!PAIR) {
+      for (int gidx = 0; gidx < ngroups; ++gidx) {
+        cp_wait<kRing - 1>();
+        if (32 * gidx + lane < nvalid) {
+          const unsigned char* slot = ring + (size_t)(gidx % kRing) * 32 * 2 * PX;
+          R xi, yi, zi, ci, xj, yj, zj, cj;
+          read_px<DT, R>(slot, xi, yi, zi, ci);
+          read_px<DT, R>(slot + PX, xj, yj, zj, cj);
+          accumulate<R>(xi, yi, zi, ci, xj, yj, zj, cj, T, k, acc);
+        }
+        issue(gidx + kRing);
       }
-      issue(gidx + kRing);
+    } else {
+      // two groups per step: the lane's matches of groups g and g + 1 as one packed pair
+      for (int gidx = 0; gidx < ngroups; gidx += 2) {
+        cp_wait<kRing - 2>();
+        const bool useA = 32 * gidx + lane < nvalid, useB = 32 * (gidx + 1) + lane < nvalid;
+        float xiA = 0.f, yiA = 0.f, ziA = 0.f, ciA = 0.f, xjA = 0.f, yjA = 0.f, zjA = 0.f, cjA = 0.f;
+        float xiB = 0.f, yiB = 0.f, ziB = 0.f, ciB = 0.f, xjB = 0.f, yjB = 0.f, zjB = 0.f, cjB = 0.f;
+        if (useA) {
+          const unsigned char* slot = ring + (size_t)(gidx % kRing) * 32 * 2 * PX;
+          read_px<DT, float>(slot, xiA, yiA, ziA, ciA);
+          read_px<DT, float>(slot + PX, xjA, yjA, zjA, cjA);
+        }
+        if (useB) {
+          const unsigned char* slot = ring + (size_t)((gidx + 1) % kRing) * 32 * 2 * PX;
+          read_px<DT, float>(slot, xiB, yiB, ziB, ciB);
+          read_px<DT, float>(slot + PX, xjB, yjB, zjB, cjB);
+        }
+        if (useA || useB)
+          accumulate_pair(f2(xiA, xiB), f2(yiA, yiB), f2(ziA, ziB), f2(ciA, ciB), f2(xjA, xjB), f2(yjA, yjB),
+                          f2(zjA, zjB), f2(cjA, cjB), useA, useB, T, k, pacc);
+        issue(gidx + kRing);
+        issue(gidx + kRing + 1);
+      }
     }
     cp_wait<0>();
     __syncwarp();  // the index buffer of this item is reused two items later
-    finish_item(acc, partials, it, seg, it + 1 == it1 || items[it + 1].edge != item.edge, lane);
+    const bool flush = it + 1 == it1 || items[it + 1].edge != item.edge;
+    if constexpr (PAIR) {
+      // fold the two elements of the packed accumulators (only read when flushing)
+      if (flush) {
+#pragma unroll
+        for (int q = 0; q < kAcc; ++q) acc.v[q] = pacc.v[q].x + pacc.v[q].y;
+        acc.Ew = pacc.Ew.x + pacc.Ew.y;
+        acc.Em = pacc.Em.x + pacc.Em.y;
+        acc.skipped = pacc.skipped;
+        pacc.zero();
+      }
+    }
+    finish_item(acc, partials, it, seg, flush, lane);
   }
   cp_wait<0>();
 }
@@ -821,8 +976,10 @@ constexpr int tma_smem_bytes() {
 //      aligned and every keyframe has at most 2^22 pixels
 //   5  TMA-staged CTA ring (bulk copies of index rows and streamed pixels), FP32 compute
 //      on FP16 / FP32 storage; the same item and alignment conditions as 4
+//   6  as 4 with two matches per lane in packed FP32x2 arithmetic (FP32 compute only)
 // FP64 has configurations 0, 1 and 4.
-constexpr int kK1Cfgs = 6;
+constexpr int kK1Cfgs = 7;
+constexpr int kPairCfg = 6;
 constexpr int kAsyncCfg = 4;
 
 template <typename R, int DT>
@@ -833,7 +990,10 @@ const void* pick_cfg(int cfg) {
     if (cfg == 2) return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 1, 2, true>);
     if (cfg == 3) return reinterpret_cast<const void*>(&residual_reduce_kernel<R, DT, kK1Block, 3, 1, true>);
   }
-  if (cfg == kAsyncCfg) return reinterpret_cast<const void*>(&residual_reduce_async_kernel<R, DT>);
+  if (cfg == kAsyncCfg) return reinterpret_cast<const void*>(&residual_reduce_async_kernel<R, DT, false>);
+  if constexpr (sizeof(R) == 4) {
+    if (cfg == kPairCfg) return reinterpret_cast<const void*>(&residual_reduce_async_kernel<R, DT, true>);
+  }
   if constexpr (sizeof(R) == 4 && DT < 2) {
     if (cfg == kTmaCfg) return reinterpret_cast<const void*>(&residual_reduce_tma_kernel<R, DT>);
   }
@@ -861,11 +1021,13 @@ const void* pick_kernel(int mode, int dtype, int cfg) {
 
 int residual_reduce_num_cfgs(int mode) { return kK1Cfgs; }
 
-int residual_reduce_cfg_chunk(int cfg) { return (cfg == kAsyncCfg || cfg == kTmaCfg) ? kAsyncChunk : 0; }
+int residual_reduce_cfg_chunk(int cfg) {
+  return (cfg == kAsyncCfg || cfg == kTmaCfg || cfg == kPairCfg) ? kAsyncChunk : 0;
+}
 
 static size_t cfg_smem(int dtype, int cfg) {
   if (cfg == kTmaCfg) return dtype == 0 ? tma_smem_bytes<0>() : tma_smem_bytes<1>();
-  if (cfg != kAsyncCfg) return 0;
+  if (cfg != kAsyncCfg && cfg != kPairCfg) return 0;
   return dtype == 0 ? async_smem_bytes<0>() : (dtype == 1 ? async_smem_bytes<1>() : async_smem_bytes<2>());
 }
 
@@ -879,6 +1041,9 @@ cudaError_t residual_reduce_prepare() {
   for (int d = 0; d < 2 && e == cudaSuccess; ++d)
     e = cudaFuncSetAttribute(pick_kernel(1, d, kTmaCfg), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)cfg_smem(d, kTmaCfg));
+  for (int d = 0; d < 3 && e == cudaSuccess; ++d)
+    e = cudaFuncSetAttribute(pick_kernel(1, d, kPairCfg), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cfg_smem(d, kPairCfg));
   return e;
 }
 
@@ -897,7 +1062,7 @@ void residual_reduce_cost_weights(int cfg, int& wv, int& wp) {
   // memory round trip per 32-pixel group whether it holds matches or not; cfg 4 and 5
   // prefetch whole index rows, so valid matches weigh more
   wp = 1;
-  wv = cfg == kAsyncCfg ? 3 : (cfg == kTmaCfg ? 1 : 0);
+  wv = (cfg == kAsyncCfg || cfg == kPairCfg) ? 3 : (cfg == kTmaCfg ? 1 : 0);
 }
 
 int residual_reduce_max_blocks_per_sm(int mode, int dtype, int cfg) {

@@ -214,7 +214,7 @@ def test_batched_graphs_match_individual(C):
     np.testing.assert_allclose(trace, to, rtol=FP64_TOL)
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5, 6])
 def test_every_residual_kernel_configuration(C, mid, tiny, cfg, monkeypatch):
     """Each launch configuration the autotuner may choose gives the oracle's edge blocks
     (mixed form on FP32 and FP16 storage; the FP64 form for the configurations that have
