@@ -234,3 +234,36 @@ def test_every_residual_kernel_configuration(C, mid, tiny, cfg, monkeypatch):
             assert rel_fro(rec[e, :49].reshape(7, 7), r["H_rel"]) <= tol, (cfg, mode, e)
             assert abs(rec[e, 56] - r["cost"]) <= tol * r["cost"]
             assert rec[e, 57] == r["n_valid"] and rec[e, 58] == r["n_skipped"]
+
+
+def test_lm_damping_matches_oracle(C, tiny):
+    """lambda > 0 (the LM damping H + lambda diag(H) of the local and tracking solves):
+    one FP64 step and a 5-iteration solve against the oracle."""
+    p = dataclasses.replace(tiny, lam=0.05)
+    poses = torch_poses(p.poses_init)
+    with C.Graph(p, mode=C.PLAIN_FP64) as g:
+        st, info = g.gn_step(poses)
+    new_o, _ = O.gn_step(p, p.poses_init)
+    assert max(pose_err(poses.cpu().numpy(), new_o).values()) <= FP64_TOL
+    poses = torch_poses(p.poses_init)
+    with C.Graph(p, mode=C.PLAIN_FP64) as g:
+        st, trace, info = g.solve(poses, 5)
+    po, to = O.gn_solve(p, p.poses_init, 5)
+    assert max(pose_err(poses.cpu().numpy(), po).values()) <= FP64_TOL
+    np.testing.assert_allclose(trace, to, rtol=FP64_TOL)
+
+
+def test_batched_tracking(C):
+    """Ray-range tracking of 12 frames (one per agent) against their keyframes in one
+    launch: 12 one-edge graphs (the keyframe fixed, the frame's Sim(3) free), LM damped."""
+    prob = make_problem(21, agents=1, n_kf=2, H=48, W=64, f=50.0, noise=0.005, outlier=0.1, exact=False,
+                        num_graphs=12, name="tracking")
+    prob = dataclasses.replace(prob, lam=0.01)
+    assert prob.num_edges == 12 and prob.num_kf == 24
+    for mode, tol in ((C.PLAIN_FP64, FP64_TOL), (C.MIXED, MIXED_TOL)):
+        poses = torch_poses(prob.poses_init)
+        with C.Graph(prob, mode=mode) as g:
+            st, trace, info = g.solve(poses, 8)
+        po, to = O.gn_solve(prob, prob.poses_init, 8)
+        assert max(pose_err(poses.cpu().numpy(), po).values()) <= tol, mode
+        assert all(x["solved"] for x in info)
