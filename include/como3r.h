@@ -110,7 +110,8 @@ typedef struct {
 } como3r_graph_info;
 
 /* Validate the description, plan the solve (fill-reducing ordering, symbolic block
- * factorisation, work lists), allocate workspaces, check every match index on the
+ * factorisation, work lists; for a few large graphs a multi-SM solve with one cluster of 8
+ * CTAs per graph, COMO3R_SOLVE_CLUSTER=<C> forcing C CTAs or 0 none), allocate workspaces, check every match index on the
  * device (-1 <= n < P_j) and autotune the residual kernel's work-item size and launch
  * configuration on this graph's data (a few milliseconds of timed trial launches; the
  * environment variable COMO3R_K1_CFG=<n> restricts the search to configuration n).
@@ -235,7 +236,8 @@ int64_t como3r_last_launch_count(como3r_graph_t graph);
 #define COMO3R_STAT_SMEM_SOLVE 13    /* 1 if the factor of every graph fits in shared memory */
 #define COMO3R_STAT_ND_GRAPHS 14     /* graphs ordered by nested dissection (others: minimum degree) */
 #define COMO3R_STAT_K1_STALLS 15     /* bounded waits of the TMA-staged K1 that gave up (process-wide; 0 = healthy) */
-#define COMO3R_STAT_COUNT 16
+#define COMO3R_STAT_SOLVE_CTAS 16    /* CTAs per graph of the factorisation (1, or the cluster of the multi-SM solve) */
+#define COMO3R_STAT_COUNT 17
 int como3r_graph_stats(como3r_graph_t graph, int64_t* stats /* [COMO3R_STAT_COUNT] */);
 
 /* Plan a description on the host only (no device memory touched): fills the same stats

@@ -27,7 +27,7 @@ PLAIN_FP64, MIXED = 0, 1
 VJP_UNROLLED, VJP_ENVELOPE = 0, 1
 EDGE_RECORD = 64
 STAT_NAMES = ["graphs", "keyframes", "edges", "items", "columns", "blocks", "fill", "updates", "levels",
-              "valid", "chunk", "block", "grid", "smem_solve", "nd_graphs", "k1_stalls"]
+              "valid", "chunk", "block", "grid", "smem_solve", "nd_graphs", "k1_stalls", "solve_ctas"]
 
 STAGE_NAMES = ["edge_prep", "residual_reduce", "edge_reduce", "assemble", "factor_solve", "retract", "iteration"]
 
@@ -155,7 +155,7 @@ def plan_stats(prob) -> dict:
     keep = []
     pts = np.zeros(4, dtype=prob.points.dtype)  # non-NULL placeholder; never dereferenced
     d = _build_desc(prob, _ptr(pts), _ptr(np.zeros(1, np.int32)), MIXED, False, keep)
-    out = (ctypes.c_int64 * 16)()
+    out = (ctypes.c_int64 * len(STAT_NAMES))()
     _check(lib().como3r_plan_stats(ctypes.byref(d), out), "plan_stats")
     return dict(zip(STAT_NAMES, list(out)))
 
@@ -259,7 +259,7 @@ class Graph:
         return int(lib().como3r_last_launch_count(self.handle))
 
     def stats(self) -> dict:
-        out = (ctypes.c_int64 * 16)()
+        out = (ctypes.c_int64 * len(STAT_NAMES))()
         _check(lib().como3r_graph_stats(self.handle, out), "graph_stats")
         return dict(zip(STAT_NAMES, list(out)))
 

@@ -89,6 +89,10 @@ struct como3r_graph {
   bool smem_solve = false;
   size_t solve_smem = 0;
   SolverPlan sp{};
+  // multi-SM solve (one cluster of cluster_ctas CTAs per graph), when chosen at create
+  int cluster_ctas = 0;
+  size_t cluster_smem = 0;
+  ClusterPlan cp{};
   cudaGraphExec_t iter_exec = nullptr, eval_exec = nullptr;
   int64_t last_launches = 0;
   std::vector<long long> edge_valid;
@@ -185,10 +189,20 @@ int enqueue_linearize(como3r_graph* g, cudaStream_t s, double* cost_hist, const 
   return COMO3R_OK;
 }
 
+// The damped factorisation and solve of every graph: the multi-SM variant when it was
+// chosen at create, else one CTA per graph.
+cudaError_t launch_solver(como3r_graph* g, const double* gvec, double* tau, GraphInfoDev* ginfo, int* warn,
+                          cudaStream_t s, const GraphInfoDev* fixed = nullptr) {
+  if (g->cluster_ctas > 0)
+    return launch_factor_solve_cluster(g->plan.G, g->sp, g->cp, g->cluster_smem, g->d_A, gvec, tau, g->lambda,
+                                       g->eps0, g->max_attempts, ginfo, warn, s, fixed);
+  return launch_factor_solve(g->plan.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_colscratch, gvec,
+                             tau, g->lambda, g->eps0, g->max_attempts, ginfo, warn, s, fixed);
+}
+
 int enqueue_solve(como3r_graph* g, cudaStream_t s, int* iter) {
   const HostPlan& p = g->plan;
-  CK(launch_factor_solve(p.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_colscratch, g->d_gvec, g->d_tau, g->lambda, g->eps0, g->max_attempts, g->d_ginfo, g->d_warn, s),
-     "factor_solve");
+  CK(launch_solver(g, g->d_gvec, g->d_tau, g->d_ginfo, g->d_warn, s), "factor_solve");
   CK(launch_retract(g->d_tau, g->d_poses, g->d_frozen, p.N, iter, s), "retract");
   return COMO3R_OK;
 }
@@ -313,6 +327,32 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   // shared-memory factor when every graph fits
   const size_t smax = factor_solve_max_smem();
   g->smem_solve = p.max_graph_smem <= smax;
+  // multi-SM solve for a few large graphs (it needs the graphs' clusters to fit on the GPU);
+  // COMO3R_SOLVE_CLUSTER=<C> forces C CTAs per graph, 0 disables it
+  {
+    int C = 0, max_col = 0;
+    for (int k = 0; k < p.G; ++k) max_col = std::max(max_col, p.col_begin[k + 1] - p.col_begin[k]);
+    if (max_col >= 32 && 8 * p.G <= g->sms) C = 8;
+    if (const char* e = getenv("COMO3R_SOLVE_CLUSTER")) C = std::max(0, std::min(16, atoi(e)));
+    if (C > 1) {
+      HostClusterPlan hc;
+      build_cluster_plan(p, C, hc);
+      if (hc.max_cta_smem <= smax) {
+        int32_t *cmeta, *csched, *clvl, *own, *shome, *chome;
+        int4* cut;
+        int2* ctt;
+        if ((rc = upload(g, &cmeta, hc.cmeta)) || (rc = upload(g, &csched, hc.csched)) ||
+            (rc = upload(g, &clvl, hc.clvl)) || (rc = upload(g, &own, hc.own_slot)) ||
+            (rc = upload(g, &shome, hc.slot_home)) || (rc = upload(g, &chome, hc.col_home)) ||
+            (rc = upload(g, &cut, hc.cutask)) || (rc = upload(g, &ctt, hc.cttask)))
+          return rc;
+        g->cp = ClusterPlan{C, cmeta, csched, cut, ctt, clvl, own, shome, chome};
+        g->cluster_smem = hc.max_cta_smem;
+        CK(factor_solve_cluster_prepare(g->cluster_smem, C), "cluster solver attributes");
+        g->cluster_ctas = C;
+      }
+    }
+  }
   if (g->smem_solve) {
     g->solve_smem = p.max_graph_smem;
     CK(factor_solve_prepare(g->solve_smem), "solver smem attribute");
@@ -617,9 +657,7 @@ int vjp_impl(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t 
          "restore");
       if ((rc = enqueue_linearize(g, s, nullptr, nullptr, nullptr))) return rc;
       CK(cudaMemsetAsync(g->d_adj_u, 0, sizeof(double) * 7 * N, s), "memset");
-      CK(launch_factor_solve(G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_colscratch, g->d_adj_rhs,
-                             g->d_adj_u, g->lambda, g->eps0, g->max_attempts, g->d_ginfo_bwd, g->d_warn_bwd, s,
-                             g->d_ginfo_hist + (size_t)k * G),
+      CK(launch_solver(g, g->d_adj_rhs, g->d_adj_u, g->d_ginfo_bwd, g->d_warn_bwd, s, g->d_ginfo_hist + (size_t)k * G),
          "adjoint solve");
       CK(launch_adjoint_edge_prep(p.mode, g->d_es, E, g->d_Ad, g->d_adj_u, tau_k, g->d_evec, s), "adjoint edge prep");
       CK(mark(4 + 2 * k), "event");
@@ -763,9 +801,7 @@ int como3r_time_stages(como3r_graph_t g, const double* poses, int32_t reps, floa
                                     g->d_edge_offset, g->d_edge_cost, g->d_edge_skip, g->d_ginfo, nullptr, nullptr,
                                     g->d_warn, s);
     if (!err) err = cudaEventRecord(ev[4], s);
-    if (!err) err = launch_factor_solve(p.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_colscratch,
-                                        g->d_gvec, g->d_tau, g->lambda, g->eps0, g->max_attempts, g->d_ginfo,
-                                        g->d_warn, s);
+    if (!err) err = launch_solver(g, g->d_gvec, g->d_tau, g->d_ginfo, g->d_warn, s);
     if (!err) err = cudaEventRecord(ev[5], s);
     if (!err) err = launch_retract(g->d_tau, g->d_poses, g->d_frozen, p.N, nullptr, s);
     if (!err) err = cudaEventRecord(ev[6], s);
@@ -803,6 +839,7 @@ int como3r_graph_stats(como3r_graph_t g, int64_t* stats) {
   stats[COMO3R_STAT_BLOCK] = residual_reduce_block() * 100 + g->k1_cfg;
   stats[COMO3R_STAT_GRID] = g->k1_grid;
   stats[COMO3R_STAT_SMEM_SOLVE] = g->smem_solve ? 1 : 0;
+  stats[COMO3R_STAT_SOLVE_CTAS] = g->cluster_ctas > 0 ? g->cluster_ctas : 1;
   stats[COMO3R_STAT_K1_STALLS] = residual_reduce_stalls();
   return COMO3R_OK;
 }

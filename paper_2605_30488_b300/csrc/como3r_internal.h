@@ -80,12 +80,47 @@ struct SolverPlan {
                             // at 4 * lvl_base
 };
 
+// Multi-SM solve: one thread-block cluster of `C` CTAs per graph.  Every column has an
+// owner CTA (round robin within its elimination level) that keeps the column's blocks and
+// scratch in its shared memory and runs its diagonal factorisation, off-diagonal solves,
+// backward step, and every update whose destination lies in one of its columns (sources
+// are read from the owners' shared memory through the cluster window).  Per (graph, rank):
+// the owned columns, update tasks and off-diagonal tasks in level order, with offsets
+// (nlev + 1) x 4 like SolverPlan::lvl.  Homes are encoded rank << 24 | local index.
+// Every CTA of a graph lays out its shared memory identically up to the blocks (column
+// scratch for kCNColMax columns first, then the blocks), so a remote column or block is
+// found at the same offset as a local one.
+enum ClusterMeta { kCSched, kCNSched, kCU, kCNU, kCT, kCNT, kCLvl, kCNSlot, kCNCol, kCOwn, kCNColMax, kCMetaCount };
+struct ClusterPlan {
+  int C;                    // CTAs per graph
+  const int32_t* cmeta;     // [G * C][kCMetaCount]
+  const int32_t* csched;    // owned columns (graph-local), level order
+  const int4* cutask;       // owned update tasks (graph-local slots), per level near then far
+  const int2* cttask;       // owned off-diagonal tasks
+  const int32_t* clvl;      // [(nlev + 1) * 4] per (graph, rank)
+  const int32_t* own_slot;  // graph-local slot of each local slot, per (graph, rank)
+  const int32_t* slot_home; // per slot (at slot_base)
+  const int32_t* col_home;  // per column (at col_base)
+};
+
 // Bytes of shared memory one graph's factor, per-column scratch and plan occupy.
 inline size_t solver_smem_bytes(int nslot, int ncol, int ntri, int nu, int nt, int nlev) {
   auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
   size_t b = r16(sizeof(double) * ((size_t)nslot * 49 + (size_t)ncol * 63));
   b += r16(16 * (size_t)ntri) + r16(16 * (size_t)nu) + r16(8 * (size_t)nt);
   b += r16(4 * (size_t)(ncol + 1)) + r16(4 * (size_t)nslot) + r16(4 * (size_t)ncol) + r16(16 * (size_t)(nlev + 1));
+  return b;
+}
+
+// Bytes of shared memory of one CTA of the multi-SM solve: its blocks and column scratch,
+// the graph's triplets, its task lists and the graph's home / column-slot / row maps.
+inline size_t cluster_smem_bytes(int nslot_loc, int ncol_loc, int ncol_max, int ntri, int nu, int nt, int nlev,
+                                 int nslot, int ncol) {
+  auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+  size_t b = r16(sizeof(double) * (size_t)ncol_max * 63) + r16(sizeof(double) * (size_t)nslot_loc * 49);
+  b += r16(16 * (size_t)ntri) + r16(16 * (size_t)nu) + r16(8 * (size_t)nt);
+  b += r16(4 * (size_t)ncol_loc) + r16(16 * (size_t)(nlev + 1)) + r16(4 * (size_t)nslot_loc);
+  b += r16(4 * (size_t)nslot) + r16(4 * (size_t)ncol) + r16(4 * (size_t)(ncol + 1)) + r16(4 * (size_t)nslot);
   return b;
 }
 
@@ -126,6 +161,12 @@ cudaError_t launch_export_dense(int num_slots, const int32_t* slot_kf_r, const i
                                 cudaStream_t s);
 // Workspace doubles per column (outside the slots): 7 Dinv + 7 rhs/solution + 49 L_cc^{-1}.
 constexpr int kColScratch = 63;
+// The multi-SM solve (same arguments; `cp` adds the cluster plan; smem_bytes per CTA).
+cudaError_t launch_factor_solve_cluster(int G, const SolverPlan& plan, const ClusterPlan& cp, size_t smem_bytes,
+                                        const double* A, const double* gvec, double* tau, double lambda, double eps0,
+                                        int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s,
+                                        const GraphInfoDev* fixed = nullptr);
+cudaError_t factor_solve_cluster_prepare(size_t smem_bytes, int C);
 cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t smem_bytes, const double* A,
                                 double* L, double* colscratch, const double* gvec, double* tau, double lambda,
                                 double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s,

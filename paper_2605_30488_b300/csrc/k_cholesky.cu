@@ -25,6 +25,8 @@
 // schedule spreads the update work evenly over the levels (a left-looking one piles
 // the root's updates into the last, narrowest levels).
 // The factor lives in shared memory when the graph's blocks fit, else in global memory.
+#include <cooperative_groups.h>
+
 #include <cstdint>
 
 #include "como3r_internal.h"
@@ -48,12 +50,39 @@ struct SolveCtx {
   const int4* utask;      // [nu]
   const int2* ttask;      // [nt]
   const int* lvl;         // [(nlev + 1) * 4]
+  // multi-SM solve only: homes (rank << 24 | local index) of the graph's slots and columns
+  const int* slot_home;
+  const int* col_home;
+  int rank;
 };
 
-__device__ __forceinline__ double* blk(const SolveCtx& C, int s) { return C.L + (int64_t)s * 49; }
-__device__ __forceinline__ double* dinv_of(const SolveCtx& C, int col) { return C.S + (int64_t)col * kColScratch; }
-__device__ __forceinline__ double* y_of(const SolveCtx& C, int col) { return dinv_of(C, col) + 7; }
-__device__ __forceinline__ double* linv_of(const SolveCtx& C, int col) { return dinv_of(C, col) + 14; }
+// A location in the shared memory of CTA `rank` of this cluster (direct when it is ours).
+__device__ __forceinline__ double* at_rank(double* p, int rank, int mine) {
+  if (rank == mine) return p;
+  return cooperative_groups::this_cluster().map_shared_rank(p, (unsigned)rank);
+}
+template <bool CL>
+__device__ __forceinline__ double* blk(const SolveCtx& C, int s) {
+  if constexpr (!CL) {
+    return C.L + (int64_t)s * 49;
+  } else {
+    const int h = C.slot_home[s];
+    return at_rank(C.L + (int64_t)(h & 0xffffff) * 49, h >> 24, C.rank);
+  }
+}
+template <bool CL>
+__device__ __forceinline__ double* dinv_of(const SolveCtx& C, int col) {
+  if constexpr (!CL) {
+    return C.S + (int64_t)col * kColScratch;
+  } else {
+    const int h = C.col_home[col];
+    return at_rank(C.S + (int64_t)(h & 0xffffff) * kColScratch, h >> 24, C.rank);
+  }
+}
+template <bool CL>
+__device__ __forceinline__ double* y_of(const SolveCtx& C, int col) { return dinv_of<CL>(C, col) + 7; }
+template <bool CL>
+__device__ __forceinline__ double* linv_of(const SolveCtx& C, int col) { return dinv_of<CL>(C, col) + 14; }
 
 // acc + sum_q a[q] b[q], q < 7: seven FP64 instructions (instruction count, not the
 // dependent latency, is what limits FP64 work on this GPU)
@@ -67,25 +96,26 @@ __device__ __forceinline__ double dot7(const double* a, const double* b, double 
 // entry l of the 7x7 block; pass 2: lanes 0..16 own entries 32..48, lanes 17..23 the seven
 // rows of the forward right-hand side (diagonal destinations only), lanes 24..31 idle.
 // Four triplets are in flight at a time (independent accumulators).
+template <bool CL>
 __device__ void update_task(const SolveCtx& C, int4 task, int lane) {
   const int e0 = lane, e1 = lane + 32;
   const bool has1 = e1 < 49;
   const bool rhs = task.w >= 0 && lane >= 17 && lane < 24;
   const int r0 = e0 / 7, q0 = e0 % 7, r1 = has1 ? e1 / 7 : lane - 17, q1 = has1 ? e1 % 7 : 0;
-  double* D = blk(C, task.x);
+  double* D = blk<CL>(C, task.x);
   // the destination itself seeds the chains: L[dst] - sum = -(sum - L[dst])
   double a0 = -D[e0];
-  double a1 = has1 ? -D[e1] : (rhs ? -y_of(C, task.w)[lane - 17] : 0.0);
+  double a1 = has1 ? -D[e1] : (rhs ? -y_of<CL>(C, task.w)[lane - 17] : 0.0);
   for (int t = task.y; t < task.z; ++t) {
     const int4 tr = C.tri[t];
-    const double* Lr = blk(C, tr.x);
-    a0 = dot7(Lr + 7 * r0, blk(C, tr.y) + 7 * q0, a0);
-    if (has1) a1 = dot7(Lr + 7 * r1, blk(C, tr.y) + 7 * q1, a1);
-    else if (rhs) a1 = dot7(Lr + 7 * r1, y_of(C, tr.w), a1);
+    const double* Lr = blk<CL>(C, tr.x);
+    a0 = dot7(Lr + 7 * r0, blk<CL>(C, tr.y) + 7 * q0, a0);
+    if (has1) a1 = dot7(Lr + 7 * r1, blk<CL>(C, tr.y) + 7 * q1, a1);
+    else if (rhs) a1 = dot7(Lr + 7 * r1, y_of<CL>(C, tr.w), a1);
   }
   D[e0] = -a0;
   if (has1) D[e1] = -a1;
-  else if (rhs) y_of(C, task.w)[lane - 17] = -a1;
+  else if (rhs) y_of<CL>(C, task.w)[lane - 17] = -a1;
 }
 
 // D: Cholesky of diagonal blocks, four columns per warp (FP64 instructions occupy the
@@ -93,13 +123,14 @@ __device__ void update_task(const SolveCtx& C, int4 task, int lane) {
 // column cols[s]; within it lane r < 7 holds row r and lane 7 holds the forward
 // right-hand side as an eighth row, so the elimination also yields y_c = L_cc^{-1} t_c.
 // Segments without a column factor an identity block and write nothing.
+template <bool CL>
 __device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int lane, int* fail) {
   const int seg = lane >> 3, sl = lane & 7;
   const bool active = seg < ncols;
   const int col = cols[active ? seg : 0];
   const int dslot = C.col_slot[col];
-  double* D = blk(C, dslot);
-  double* y = y_of(C, col);
+  double* D = blk<CL>(C, dslot);
+  double* y = y_of<CL>(C, col);
   double a[7];
 #pragma unroll
   for (int c = 0; c < 7; ++c) {
@@ -129,7 +160,7 @@ __device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int 
     if (sl < 7) {
 #pragma unroll
       for (int c = 0; c < 7; ++c) D[7 * sl + c] = (c <= sl) ? a[c] : 0.0;
-      dinv_of(C, col)[sl] = myinv;
+      dinv_of<CL>(C, col)[sl] = myinv;
     } else {
 #pragma unroll
       for (int c = 0; c < 7; ++c) y[c] = a[c];
@@ -141,13 +172,14 @@ __device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int 
 // T: item x < 7 * nt: row (x % 7) of off-diagonal block ttask[t0 + x / 7]; items from
 // tpad = 7 * nt rounded up to a warp on: column (x % 7) of L_cc^{-1} for the level column
 // sched[s0 + (x - tpad) / 7].  The two kinds never share a warp (they would diverge).
+template <bool CL>
 __device__ void trsm_or_inverse(const SolveCtx& C, int t0, int nt, int tpad, int s0, int x) {
   if (x < 7 * nt) {
     const int2 tt = C.ttask[t0 + x / 7];
     const int i = x % 7;
-    const double* Lc = blk(C, C.col_slot[tt.y]);
-    const double* dv = dinv_of(C, tt.y);
-    double* B = blk(C, tt.x) + 7 * i;
+    const double* Lc = blk<CL>(C, C.col_slot[tt.y]);
+    const double* dv = dinv_of<CL>(C, tt.y);
+    double* B = blk<CL>(C, tt.x) + 7 * i;
     double xr[7];
 #pragma unroll
     for (int c = 0; c < 7; ++c) {
@@ -161,9 +193,9 @@ __device__ void trsm_or_inverse(const SolveCtx& C, int t0, int nt, int tpad, int
   } else if (x >= tpad) {
     const int k = (x - tpad) / 7, c = (x - tpad) % 7;
     const int col = C.sched[s0 + k];
-    const double* Lc = blk(C, C.col_slot[col]);
-    const double* dv = dinv_of(C, col);
-    double* X = linv_of(C, col);
+    const double* Lc = blk<CL>(C, C.col_slot[col]);
+    const double* dv = dinv_of<CL>(C, col);
+    double* X = linv_of<CL>(C, col);
     double xc[7];
 #pragma unroll
     for (int r = 0; r < 7; ++r) {
@@ -185,14 +217,15 @@ __device__ void trsm_or_inverse(const SolveCtx& C, int t0, int nt, int tpad, int
 }
 
 // back substitution of one column: x_c = L_cc^{-T} (y_c - sum_r L_rc^T x_r)
+template <bool CL>
 __device__ void backward_column(const SolveCtx& C, int col, int lane) {
   const int grp = lane / 7, q = lane % 7;
   const int s_begin = C.col_slot[col] + 1, nb = C.col_slot[col + 1] - s_begin;
   double part = 0.0;
   if (grp < 4) {
     for (int b = grp; b < nb; b += 4) {
-      const double* B = blk(C, s_begin + b);
-      const double* xr = y_of(C, C.slot_row[s_begin + b]);
+      const double* B = blk<CL>(C, s_begin + b);
+      const double* xr = y_of<CL>(C, C.slot_row[s_begin + b]);
       double p0 = B[q] * xr[0];
       double p1 = B[7 + q] * xr[1];
       p0 = fma(B[14 + q], xr[2], p0);
@@ -206,9 +239,9 @@ __device__ void backward_column(const SolveCtx& C, int col, int lane) {
   const double o1 = __shfl_sync(kFull, part, (q + 7) & 31);
   const double o2 = __shfl_sync(kFull, part, (q + 14) & 31);
   const double o3 = __shfl_sync(kFull, part, (q + 21) & 31);
-  double* y = y_of(C, col);
+  double* y = y_of<CL>(C, col);
   const double t = (lane < 7) ? y[q] - ((part + o1) + (o2 + o3)) : 0.0;
-  const double* X = linv_of(C, col);
+  const double* X = linv_of<CL>(C, col);
   double xq = 0.0;
 #pragma unroll
   for (int r = 0; r < 7; ++r) {
@@ -229,9 +262,9 @@ __device__ __forceinline__ T* carve(unsigned char*& p, size_t count) {
 // Global -> shared copies issued as cp.async (all in flight at once; completed by
 // async_wait_all): element sizes 4, 8 and 16 bytes, each source element naturally aligned.
 template <typename T>
-__device__ __forceinline__ void stage(T* dst, const T* src, int64_t n, int tid) {
+__device__ __forceinline__ void stage(T* dst, const T* src, int64_t n, int tid, int nthreads = kSolveThreads) {
   static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "cp.async element size");
-  for (int64_t x = tid; x < n; x += kSolveThreads) {
+  for (int64_t x = tid; x < n; x += nthreads) {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst + x);
     if constexpr (sizeof(T) == 16)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + x) : "memory");
@@ -320,8 +353,8 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     for (int x = tid; x < 7 * ncol; x += kSolveThreads) {
       const int col = x / 7, k = x % 7;
       const int ds = C.col_slot[col];
-      blk(C, ds)[8 * k] += lambda * Ag[(int64_t)ds * 49 + 8 * k] + eps;
-      y_of(C, col)[k] = -gvec[7 * col_kf[col] + k];
+      blk<false>(C, ds)[8 * k] += lambda * Ag[(int64_t)ds * 49 + 8 * k] + eps;
+      y_of<false>(C, col)[k] = -gvec[7 * col_kf[col] + k];
     }
     if (tid == 0) s_fail = 0;
     __syncthreads();
@@ -334,23 +367,23 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
       const int ncl = L0[4] - L0[0], nd = (ncl + 3) / 4;
       const int f0 = lv > 0 ? C.lvl[4 * (lv - 1) + 2] : 0, nf = lv > 0 ? L0[1] - f0 : 0;
       for (int i = warp; i < nd + nf; i += kSolveWarps) {
-        if (i < nd) diag_factor4(C, C.sched + L0[0] + 4 * i, min(4, ncl - 4 * i), lane, &s_fail);
-        else update_task(C, C.utask[f0 + i - nd], lane);
+        if (i < nd) diag_factor4<false>(C, C.sched + L0[0] + 4 * i, min(4, ncl - 4 * i), lane, &s_fail);
+        else update_task<false>(C, C.utask[f0 + i - nd], lane);
       }
       __syncthreads();
       if (s_fail) break;
       const int nt = L0[7] - L0[3];
       const int tpad = (7 * nt + 31) & ~31;
       const int nx = tpad + 7 * ncl;
-      for (int x = tid; x < nx; x += kSolveThreads) trsm_or_inverse(C, L0[3], nt, tpad, L0[0], x);
+      for (int x = tid; x < nx; x += kSolveThreads) trsm_or_inverse<false>(C, L0[3], nt, tpad, L0[0], x);
       __syncthreads();
-      for (int u = L0[1] + warp; u < L0[2]; u += kSolveWarps) update_task(C, C.utask[u], lane);
+      for (int u = L0[1] + warp; u < L0[2]; u += kSolveWarps) update_task<false>(C, C.utask[u], lane);
       __syncthreads();
     }
     if (s_fail == 0 && nlev > 0) {
       // far updates of the last level (none in an elimination tree: its columns are roots)
       const int* L0 = C.lvl + 4 * (nlev - 1);
-      for (int u = L0[2] + warp; u < L0[5]; u += kSolveWarps) update_task(C, C.utask[u], lane);
+      for (int u = L0[2] + warp; u < L0[5]; u += kSolveWarps) update_task<false>(C, C.utask[u], lane);
       __syncthreads();
     }
     ok = (s_fail == 0);
@@ -361,10 +394,10 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
   if (ok) {
     for (int lv = nlev - 1; lv >= 0; --lv) {
       const int* L0 = C.lvl + 4 * lv;
-      for (int q = L0[0] + warp; q < L0[4]; q += kSolveWarps) backward_column(C, C.sched[q], lane);
+      for (int q = L0[0] + warp; q < L0[4]; q += kSolveWarps) backward_column<false>(C, C.sched[q], lane);
       __syncthreads();
     }
-    for (int x = tid; x < 7 * ncol; x += kSolveThreads) tau[7 * col_kf[x / 7] + x % 7] = y_of(C, x / 7)[x % 7];
+    for (int x = tid; x < 7 * ncol; x += kSolveThreads) tau[7 * col_kf[x / 7] + x % 7] = y_of<false>(C, x / 7)[x % 7];
   } else {
     for (int x = tid; x < 7 * ncol; x += kSolveThreads) tau[7 * col_kf[x / 7] + x % 7] = 0.0;
   }
@@ -373,6 +406,157 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     ginfo[g].solved = ok ? 1 : 0;
     if (!ok) atomicOr(warn, 1);
   }
+}
+
+// ---- multi-SM solve: one cluster of C CTAs per graph (see ClusterPlan) ----------------
+// Each CTA keeps its columns' blocks and scratch in its shared memory.  Per level: D of the
+// CTA's columns with its far updates of the previous level, then its off-diagonal solves
+// (both read only its own blocks), one cluster barrier (their results become visible to the
+// other CTAs), the failure flags of the level, then the CTA's near updates (sources read
+// through the cluster window, destinations its own).  Backward substitution: one cluster
+// barrier per level.  A failed attempt is decided from the level's flags of all CTAs, read
+// after the barrier; flags are double-buffered by level parity and a failing level takes a
+// second barrier before the flags are reset, so every CTA sees the same decision.
+constexpr int kClusterThreads = 256;
+constexpr int kClusterWarps = kClusterThreads / 32;
+
+__global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kernel(
+    SolverPlan P, ClusterPlan CP, const double* __restrict__ A, const double* __restrict__ gvec,
+    double* __restrict__ tau, double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
+    const GraphInfoDev* __restrict__ fixed) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ int s_fail[2];
+  __shared__ int s_any;
+  const int rank = (int)cl.block_rank();
+  const int g = blockIdx.x / CP.C;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int* m = P.meta + kMetaCount * g;
+  const int* cm = CP.cmeta + kCMetaCount * (g * CP.C + rank);
+  const int cbase = m[kMetaColBase], ncol = m[kMetaNCol], sbase = m[kMetaSlotBase], nslot = m[kMetaNSlot];
+  const int nlev = m[kMetaNLvl], ntri = m[kMetaNTri];
+  if (ncol == 0) {  // the whole cluster returns here (same graph)
+    if (tid == 0 && rank == 0) {
+      ginfo[g].attempts = 1;
+      ginfo[g].solved = 1;
+    }
+    return;
+  }
+  const int nsl = cm[kCNSlot], ncl = cm[kCNCol], nu = cm[kCNU], nt = cm[kCNT];
+  unsigned char* q = dyn;
+  SolveCtx C;
+  // column scratch, then blocks: the same offsets in every CTA of the cluster
+  C.S = carve<double>(q, (size_t)cm[kCNColMax] * kColScratch);
+  C.L = carve<double>(q, (size_t)nsl * 49);
+  int4* tri = carve<int4>(q, ntri);
+  int4* ut = carve<int4>(q, nu);
+  int2* tt = carve<int2>(q, nt);
+  int* cs = carve<int>(q, ncl);
+  int* lv = carve<int>(q, 4 * (nlev + 1));
+  int* own = carve<int>(q, nsl);
+  int* sh = carve<int>(q, nslot);
+  int* ch = carve<int>(q, ncol);
+  int* colslot = carve<int>(q, ncol + 1);
+  int* srow = carve<int>(q, nslot);
+  stage(tri, P.tri + m[kMetaTriBase], ntri, tid, kClusterThreads);
+  stage(ut, CP.cutask + cm[kCU], nu, tid, kClusterThreads);
+  stage(tt, CP.cttask + cm[kCT], nt, tid, kClusterThreads);
+  stage(cs, CP.csched + cm[kCSched], ncl, tid, kClusterThreads);
+  stage(lv, CP.clvl + cm[kCLvl], 4 * (nlev + 1), tid, kClusterThreads);
+  stage(own, CP.own_slot + cm[kCOwn], nsl, tid, kClusterThreads);
+  stage(sh, CP.slot_home + sbase, nslot, tid, kClusterThreads);
+  stage(ch, CP.col_home + cbase, ncol, tid, kClusterThreads);
+  stage(colslot, P.col_slot + cbase + g, ncol + 1, tid, kClusterThreads);
+  stage(srow, P.slot_row + sbase, nslot, tid, kClusterThreads);
+  C.tri = tri; C.utask = ut; C.ttask = tt; C.col_slot = colslot; C.slot_row = srow; C.sched = cs; C.lvl = lv;
+  C.slot_home = sh; C.col_home = ch; C.rank = rank;
+  // the block gather below takes its source addresses from `own`: the plan must have
+  // landed (and be visible to every thread) before any address is formed from it
+  async_wait_all();
+  __syncthreads();
+  const double* Ag = A + (int64_t)sbase * 49;
+  const int* col_kf = P.col_kf + cbase;
+
+  int attempt = 0, last = max_attempts;
+  if (fixed) {
+    if (!fixed[g].solved) last = 0;
+    attempt = fixed[g].attempts - 1;
+    if (last) last = attempt + 1;
+  }
+  bool ok = false;
+  double pow100 = 1.0;
+  for (int r = 0; r < attempt; ++r) pow100 *= 100.0;
+  for (; attempt < last; ++attempt, pow100 *= 100.0) {
+    const double eps = eps0 * pow100;
+    // this CTA's blocks of A (gathered by slot), damping and the forward right-hand side
+    for (int64_t x = tid; x < (int64_t)nsl * 49; x += kClusterThreads) {
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(C.L + x);
+      const double* src = Ag + (int64_t)own[x / 49] * 49 + x % 49;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    }
+    async_wait_all();
+    if (tid < 2) s_fail[tid] = 0;
+    __syncthreads();
+    for (int x = tid; x < 7 * ncl; x += kClusterThreads) {
+      const int col = cs[x / 7], k = x % 7;
+      const int ds = colslot[col];
+      blk<true>(C, ds)[8 * k] += lambda * Ag[(int64_t)ds * 49 + 8 * k] + eps;
+      y_of<true>(C, col)[k] = -gvec[7 * col_kf[col] + k];
+    }
+    cl.sync();  // every CTA's blocks are in place
+    bool failed = false;
+    for (int l = 0; l < nlev; ++l) {
+      const int* L0 = lv + 4 * l;  // [own columns, near updates, far updates, off-diagonal tasks]
+      const int ncl_l = L0[4] - L0[0], nd = (ncl_l + 3) / 4;
+      const int f0 = l > 0 ? lv[4 * (l - 1) + 2] : 0, nf = l > 0 ? L0[1] - f0 : 0;
+      for (int i = warp; i < nd + nf; i += kClusterWarps) {
+        if (i < nd) diag_factor4<true>(C, cs + L0[0] + 4 * i, min(4, ncl_l - 4 * i), lane, &s_fail[l & 1]);
+        else update_task<true>(C, ut[f0 + i - nd], lane);
+      }
+      __syncthreads();
+      const int ntl = L0[7] - L0[3];
+      const int tpad = (7 * ntl + 31) & ~31;
+      const int nx = tpad + 7 * ncl_l;
+      for (int x = tid; x < nx; x += kClusterThreads) trsm_or_inverse<true>(C, L0[3], ntl, tpad, L0[0], x);
+      cl.sync();
+      if (tid == 0) {
+        int any = 0;
+        for (int r = 0; r < CP.C; ++r) any |= *cl.map_shared_rank(&s_fail[l & 1], (unsigned)r);
+        s_any = any;
+      }
+      __syncthreads();
+      if (s_any) {
+        cl.sync();  // every CTA has read the flags before any resets them
+        failed = true;
+        break;
+      }
+      if (tid == 0) s_fail[(l + 1) & 1] = 0;  // nobody reads it before the next barrier
+      for (int u = L0[1] + warp; u < L0[2]; u += kClusterWarps) update_task<true>(C, ut[u], lane);
+      __syncthreads();
+    }
+    if (!failed) {
+      ok = true;
+      break;
+    }
+  }
+  if (ok) {
+    for (int l = nlev - 1; l >= 0; --l) {
+      const int* L0 = lv + 4 * l;
+      for (int x = L0[0] + warp; x < L0[4]; x += kClusterWarps) backward_column<true>(C, cs[x], lane);
+      cl.sync();  // this level's solutions are read by the columns below it
+    }
+    for (int x = tid; x < 7 * ncl; x += kClusterThreads)
+      tau[7 * col_kf[cs[x / 7]] + x % 7] = y_of<true>(C, cs[x / 7])[x % 7];
+  } else {
+    for (int x = tid; x < 7 * ncl; x += kClusterThreads) tau[7 * col_kf[cs[x / 7]] + x % 7] = 0.0;
+  }
+  if (tid == 0 && rank == 0) {
+    ginfo[g].attempts = ok ? attempt + 1 : max_attempts;
+    ginfo[g].solved = ok ? 1 : 0;
+    if (!ok) atomicOr(warn, 1);
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 }  // namespace
@@ -401,6 +585,38 @@ cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t
                                                            max_attempts, ginfo, warn, fixed);
   }
   return cudaGetLastError();
+}
+
+}  // namespace como3r
+
+namespace como3r {
+
+cudaError_t factor_solve_cluster_prepare(size_t smem_bytes, int C) {
+  cudaError_t e = cudaFuncSetAttribute(factor_solve_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e == cudaSuccess && C > 8)
+    e = cudaFuncSetAttribute(factor_solve_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+cudaError_t launch_factor_solve_cluster(int G, const SolverPlan& plan, const ClusterPlan& cp, size_t smem_bytes,
+                                        const double* A, const double* gvec, double* tau, double lambda, double eps0,
+                                        int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s,
+                                        const GraphInfoDev* fixed) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(G * cp.C));
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cp.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, factor_solve_cluster_kernel, plan, cp, A, gvec, tau, lambda, eps0, max_attempts,
+                            ginfo, warn, fixed);
 }
 
 }  // namespace como3r

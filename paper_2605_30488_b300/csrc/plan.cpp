@@ -502,4 +502,75 @@ void plan_stats(const HostPlan& p, int64_t* s) {
   s[COMO3R_STAT_ND_GRAPHS] = nd;
 }
 
+
+void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
+  cp = HostClusterPlan{};
+  cp.C = C;
+  cp.slot_home.assign(p.slot_begin.back(), 0);
+  cp.col_home.assign(p.col_begin.back(), 0);
+  for (int g = 0; g < p.G; ++g) {
+    const int* m = p.meta.data() + kMetaCount * g;
+    const int cbase = m[kMetaColBase], ncol = m[kMetaNCol], sbase = m[kMetaSlotBase], nslot = m[kMetaNSlot];
+    const int ubase = m[kMetaUBase], tbase = m[kMetaTBase], nlev = m[kMetaNLvl], ntri = m[kMetaNTri];
+    const int* lvl = p.llvl.data() + 4 * m[kMetaLvlBase];
+    const int* colslot = p.lcol_slot.data() + cbase + g;
+    const int* sched = p.lsched.data() + cbase;
+    // owners: round robin over the columns of each level
+    std::vector<int> owner(ncol, 0), clocal(ncol, 0), slocal(nslot, 0), shome(nslot, 0);
+    std::vector<std::vector<int>> own_cols(C), own_slots(C);
+    for (int l = 0; l < nlev; ++l)
+      for (int q = lvl[4 * l]; q < lvl[4 * (l + 1)]; ++q) owner[sched[q]] = (q - lvl[4 * l]) % C;
+    for (int q = 0; q < ncol; ++q) {  // level order
+      const int c = sched[q], r = owner[c];
+      clocal[c] = (int)own_cols[r].size();
+      own_cols[r].push_back(c);
+      for (int sl = colslot[c]; sl < colslot[c + 1]; ++sl) {
+        shome[sl] = r;
+        slocal[sl] = (int)own_slots[r].size();
+        own_slots[r].push_back(sl);
+      }
+    }
+    for (int c = 0; c < ncol; ++c) cp.col_home[cbase + c] = (owner[c] << 24) | clocal[c];
+    int ncol_max = 0;
+    for (int r = 0; r < C; ++r) ncol_max = std::max(ncol_max, (int)own_cols[r].size());
+    for (int sl = 0; sl < nslot; ++sl) cp.slot_home[sbase + sl] = (shome[sl] << 24) | slocal[sl];
+    for (int r = 0; r < C; ++r) {
+      const int s0 = (int)cp.csched.size(), u0 = (int)cp.cutask.size(), t0 = (int)cp.cttask.size();
+      const int l0 = (int)cp.clvl.size(), o0 = (int)cp.own_slot.size();
+      for (int l = 0; l < nlev; ++l) {
+        const int sc = (int)cp.csched.size() - s0, un = (int)cp.cutask.size() - u0;
+        for (int q = lvl[4 * l]; q < lvl[4 * (l + 1)]; ++q)
+          if (owner[sched[q]] == r) cp.csched.push_back(sched[q]);
+        int nn = 0;
+        for (int u = lvl[4 * l + 1]; u < lvl[4 * l + 2]; ++u) {
+          const int4 t = p.lutask[ubase + u];
+          if (shome[t.x] == r) {
+            cp.cutask.push_back(t);
+            ++nn;
+          }
+        }
+        for (int u = lvl[4 * l + 2]; u < lvl[4 * (l + 1) + 1]; ++u) {
+          const int4 t = p.lutask[ubase + u];
+          if (shome[t.x] == r) cp.cutask.push_back(t);
+        }
+        const int tt = (int)cp.cttask.size() - t0;
+        for (int x = lvl[4 * l + 3]; x < lvl[4 * (l + 1) + 3]; ++x) {
+          const int2 t = p.lttask[tbase + x];
+          if (shome[t.x] == r) cp.cttask.push_back(t);
+        }
+        cp.clvl.insert(cp.clvl.end(), {sc, un, un + nn, tt});
+      }
+      cp.clvl.insert(cp.clvl.end(), {(int)cp.csched.size() - s0, (int)cp.cutask.size() - u0,
+                                     (int)cp.cutask.size() - u0, (int)cp.cttask.size() - t0});
+      for (int sl : own_slots[r]) cp.own_slot.push_back(sl);
+      const int nsl = (int)own_slots[r].size(), ncl = (int)own_cols[r].size();
+      cp.cmeta.insert(cp.cmeta.end(), {s0, (int)cp.csched.size() - s0, u0, (int)cp.cutask.size() - u0, t0,
+                                       (int)cp.cttask.size() - t0, l0, nsl, ncl, o0, ncol_max});
+      cp.max_cta_smem = std::max(cp.max_cta_smem,
+                                 cluster_smem_bytes(nsl, ncl, ncol_max, ntri, (int)cp.cutask.size() - u0,
+                                                    (int)cp.cttask.size() - t0, nlev, nslot, ncol));
+    }
+  }
+}
+
 }  // namespace como3r

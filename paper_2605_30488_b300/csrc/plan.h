@@ -37,6 +37,18 @@ struct HostPlan {
   std::string error;
 };
 
+// Host side of ClusterPlan (concatenated arrays; see como3r_internal.h).
+struct HostClusterPlan {
+  int C = 0;
+  std::vector<int32_t> cmeta, csched, clvl, own_slot, slot_home, col_home;
+  std::vector<int4> cutask;
+  std::vector<int2> cttask;
+  size_t max_cta_smem = 0;  // shared memory of the largest (graph, rank) CTA
+};
+
+// Splits every graph's columns over C CTAs (see ClusterPlan).
+void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp);
+
 // Validates `d` and fills `p`; returns COMO3R_OK or COMO3R_ERR_INVALID_ARG (message in p.error).
 int build_plan(const como3r_graph_desc* d, HostPlan& p);
 

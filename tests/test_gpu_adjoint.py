@@ -229,3 +229,14 @@ def test_vjp_full_size_mixed_matches_fp64(C, adjoint_workload):
         for k in (0, 1):
             mag = float(np.abs(b[k] * v).sum())
             assert abs(float(a[k] @ v - b[k] @ v)) <= tol * mag, (vjp_mode, iters, k)
+
+
+def test_vjp_with_multi_sm_solve(C, mid, monkeypatch):
+    """The adjoint's recorded-eps re-solves through the multi-SM factorisation."""
+    monkeypatch.setenv("COMO3R_SOLVE_CLUSTER", "4")
+    gl, gc, _, _, _ = gpu_grads(C, mid, 0, 2, C.VJP_UNROLLED)
+    rng = np.random.default_rng(7)
+    vl, vc = rng.normal(size=gl.size), rng.normal(size=gl.size)
+    ref = O.refined_cost_derivative(mid, mid.poses_init, 2, vl, vc)
+    mag = float(np.abs(gl * vl).sum() + np.abs(gc * vc).sum())
+    assert abs(float(gl @ vl + gc @ vc) - ref) <= TOL[0] * mag

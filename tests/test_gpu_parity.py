@@ -267,3 +267,47 @@ def test_batched_tracking(C):
         po, to = O.gn_solve(prob, prob.poses_init, 8)
         assert max(pose_err(poses.cpu().numpy(), po).values()) <= tol, mode
         assert all(x["solved"] for x in info)
+
+
+@pytest.mark.parametrize("ctas", [2, 4, 8])
+def test_multi_sm_solve_matches_oracle(C, tiny, mid, ctas, monkeypatch):
+    """The multi-SM factorisation (one cluster of `ctas` CTAs per graph, columns spread over
+    them) gives the oracle's FP64 steps and solves, alone and for a batch of graphs."""
+    for prob in (tiny, mid):
+        out = {}
+        for c in (0, ctas):
+            monkeypatch.setenv("COMO3R_SOLVE_CLUSTER", str(c))
+            poses = torch_poses(prob.poses_init)
+            with C.Graph(prob, mode=C.PLAIN_FP64) as g:
+                assert g.stats()["solve_ctas"] == max(c, 1)
+                st, trace, info = g.solve(poses, 6)
+            out[c] = (poses.cpu().numpy(), trace)
+        # the same task order: bitwise the single-CTA result
+        np.testing.assert_array_equal(out[ctas][0], out[0][0])
+        np.testing.assert_array_equal(out[ctas][1], out[0][1])
+    po, to = O.gn_solve(tiny, tiny.poses_init, 6)
+    monkeypatch.setenv("COMO3R_SOLVE_CLUSTER", str(ctas))
+    poses = torch_poses(tiny.poses_init)
+    with C.Graph(tiny, mode=C.PLAIN_FP64) as g:
+        st, trace, info = g.solve(poses, 6)
+    assert max(pose_err(poses.cpu().numpy(), po).values()) <= FP64_TOL
+    np.testing.assert_allclose(trace, to, rtol=FP64_TOL)
+    batch = make_problem(22, agents=2, n_kf=4, H=24, W=32, f=25.0, n_inter=1, num_graphs=3, name="batch3")
+    poses = torch_poses(batch.poses_init)
+    with C.Graph(batch, mode=C.MIXED) as g:
+        st, trace, info = g.solve(poses, 6)
+    po, _ = O.gn_solve(batch, batch.poses_init, 6)
+    assert max(pose_err(poses.cpu().numpy(), po).values()) <= MIXED_TOL
+
+
+def test_multi_sm_solve_failure_gives_zero_update(C, tiny, monkeypatch):
+    """Every attempt fails in the multi-SM solve too (all CTAs agree), and the update is zero."""
+    monkeypatch.setenv("COMO3R_SOLVE_CLUSTER", "4")
+    p = tiny.poses_init.copy()
+    p[3, 7] = 0.0
+    poses = torch_poses(p)
+    with C.Graph(tiny, mode=C.PLAIN_FP64) as g:
+        st, info = g.gn_step(poses)
+    assert st & C.WARN_SOLVE_FAILED
+    assert info[0]["attempts"] == tiny.max_attempts and not info[0]["solved"]
+    np.testing.assert_array_equal(poses.cpu().numpy(), p)
