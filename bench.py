@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["all", "mixed"], default="all",
                     help="mixed: time only the resident mixed form (profiling runs)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 64-graph batch and the 2,000-keyframe chain (per-graph latency)")
+    ap.add_argument("--batch-reps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -141,6 +144,62 @@ class ClockSampler:
         reasons = sorted({n for s in inside for n, v in zip(names, s[4:8]) if v.lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": reasons, "samples": len(inside)}
+
+
+def measure_batched(C, torch, prob, points, midx, iters: int, reps: int) -> dict:
+    """Mixed-form solves of a (device-generated) batch: per-graph latency from the
+    library's device-clock stamps (start of the call -> end of the graph's last
+    factorisation), pooled over `reps` calls, and aggregate residuals/s from CUDA events."""
+    g = C.Graph(prob, mode=C.MIXED, points=points, match_idx=midx)
+    stats = g.stats()
+    poses0 = torch.tensor(prob.poses_init, dtype=torch.float64, device=points.device)
+    work = poses0.clone()
+    g.solve(work, iters, trace=False)  # warm-up (also captures the iteration graph)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat, total_ms, solved = [], 0.0, True
+    for _ in range(reps):
+        work.copy_(poses0)
+        torch.cuda.synchronize()
+        ev0.record()
+        st, _, info = g.solve(work, iters, trace=False)
+        ev1.record()
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        t0, done = g.timestamps()
+        lat.extend(((done - t0) / 1e6).tolist())
+        solved = solved and all(x["solved"] for x in info)
+    stages = g.time_stages(poses0, reps=3)
+    g.close()
+    lat = np.sort(np.asarray(lat))
+    valid = int(stats["valid"])
+    return {"graphs": prob.num_graphs, "keyframes": prob.num_kf, "edges": prob.num_edges,
+            "pixels": int(prob.pixels_of().sum()), "valid_matches_per_iter": valid, "iters_per_call": iters,
+            "calls": reps, "all_solved": bool(solved),
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "min": float(lat[0]), "max": float(lat[-1])},
+            "ms_per_call": total_ms / reps, "gn_iters_per_s": reps * iters / (total_ms / 1e3),
+            "mresiduals_per_s": valid * reps * iters / (total_ms / 1e3) / 1e6, "stages_ms": stages,
+            "plan": {k: stats[k] for k in ("items", "chunk", "block", "grid", "levels", "smem_solve", "solve_ctas")}}
+
+
+def measure_cfg5(C, torch, dev, reps: int) -> dict:
+    """The 64-graph batch (2-4 agents, 10-200 keyframes per agent, 256x192..512x384, FP32,
+    1 % depth noise, 15 % outliers) and the 2,000-keyframe chain (512x384, 2 % outliers,
+    loop closures every 100 keyframes), both generated in device memory from seed 5."""
+    from synth.cloud_gpu import batch64_specs, chain2000_spec, make_cloud_batch_gpu
+    out = {}
+    for key, specs, iters in (("batch64", batch64_specs(), 10), ("chain2000", chain2000_spec(), 10)):
+        t = time.time()
+        prob, pts, midx = make_cloud_batch_gpu(5, specs, device=str(dev), name=key)
+        torch.cuda.synchronize()
+        gen_s = time.time() - t
+        r = measure_batched(C, torch, prob, pts, midx, iters, reps)
+        r["generate_s"] = gen_s
+        r["inputs_gb"] = (pts.numel() * pts.element_size() + midx.numel() * 4) / 1e9
+        out[key] = r
+        del pts, midx
+        torch.cuda.empty_cache()
+    return out
 
 
 def oracle_sample(prob, n_edges: int, offset: int = 0):
@@ -335,6 +394,9 @@ def run_ours(args):
     vjp_parts = ga.time_vjp(poses0, iters, reps=3)
     ga.close()
 
+    # ---- cfg5: a 64-graph batch in one launch per step, per-graph latency; the long chain
+    cfg5 = None if args.no_batch else measure_cfg5(C, torch, dev, args.batch_reps)
+
     clocks.stop()
     if rank != 0:
         if dist:
@@ -387,6 +449,15 @@ def run_ours(args):
                       "match_kernel": {"bound": "hbm", "ms_per_launch": adj_ms, "achieved": adj_gbs, "peak": peak,
                                        "unit": "GB/s", "frac": adj_gbs / peak,
                                        "algorithmic_bytes_per_launch": int(adj_bytes)}}
+    # K3: FP64 operations of one factorisation + solve (from the plan) over its measured time
+    flops = float(stats["solve_flops"])
+    out["factor_solve"] = {"bound": "latency (dependent FP64 chains along the elimination tree)",
+                           "flops_per_solve": flops, "ms": stages["factor_solve"],
+                           "gflops": flops / (stages["factor_solve"] / 1e3) / 1e9,
+                           "levels": stats["levels"], "ctas_per_graph": stats["solve_ctas"],
+                           "fp64_nominal_tflops": 1.25}
+    if cfg5 is not None:
+        out["cfg5"] = cfg5
     if cpu is not None:
         out["cpu_baseline"] = cpu
     print(json.dumps(out), flush=True)

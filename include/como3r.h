@@ -142,6 +142,15 @@ int como3r_gn_step(como3r_graph_t graph, double* poses, double* H_out, double* g
 int como3r_solve(como3r_graph_t graph, double* poses, int32_t iters, double* cost_trace,
                  como3r_graph_info* info);
 
+/* Device-clock stamps (ns, the GPU's %globaltimer) of the last como3r_gn_step or
+ * como3r_solve: the moment its first kernel ran (after the pose upload), and for every
+ * graph the moment its last damped factorisation and solve (Eq. 7) finished.  In a batch
+ * all graphs share each residual launch and each graph's solve ends on its own CTA(s),
+ * so done_ns[g] - start_ns is graph g's latency within the call.
+ *   start_ns host [1] or NULL;  done_ns host [G] or NULL.
+ * Synchronises the graph's stream.  Errors: INVALID_ARG (NULL graph), CUDA. */
+int como3r_solve_timestamps(como3r_graph_t graph, int64_t* start_ns, int64_t* done_ns);
+
 /* Linearise every edge at `poses` without solving.
  *   edge_out device [E][COMO3R_EDGE_RECORD] or NULL: per edge e = (i, j) the blocks with
  *            respect to a left perturbation of T_ij: [0..48] H_rel = sum J^T W J row-major,
@@ -237,7 +246,8 @@ int64_t como3r_last_launch_count(como3r_graph_t graph);
 #define COMO3R_STAT_ND_GRAPHS 14     /* graphs ordered by nested dissection (others: minimum degree) */
 #define COMO3R_STAT_K1_STALLS 15     /* bounded waits of the TMA-staged K1 that gave up (process-wide; 0 = healthy) */
 #define COMO3R_STAT_SOLVE_CTAS 16    /* CTAs per graph of the factorisation (1, or the cluster of the multi-SM solve) */
-#define COMO3R_STAT_COUNT 17
+#define COMO3R_STAT_SOLVE_FLOPS 17   /* FP64 operations of one factorisation + solve, all graphs (FMA = 2) */
+#define COMO3R_STAT_COUNT 18
 int como3r_graph_stats(como3r_graph_t graph, int64_t* stats /* [COMO3R_STAT_COUNT] */);
 
 /* Plan a description on the host only (no device memory touched): fills the same stats

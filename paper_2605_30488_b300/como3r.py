@@ -27,7 +27,7 @@ PLAIN_FP64, MIXED = 0, 1
 VJP_UNROLLED, VJP_ENVELOPE = 0, 1
 EDGE_RECORD = 64
 STAT_NAMES = ["graphs", "keyframes", "edges", "items", "columns", "blocks", "fill", "updates", "levels",
-              "valid", "chunk", "block", "grid", "smem_solve", "nd_graphs", "k1_stalls", "solve_ctas"]
+              "valid", "chunk", "block", "grid", "smem_solve", "nd_graphs", "k1_stalls", "solve_ctas", "solve_flops"]
 
 STAGE_NAMES = ["edge_prep", "residual_reduce", "edge_reduce", "assemble", "factor_solve", "retract", "iteration"]
 
@@ -65,6 +65,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.como3r_gn_step.argtypes = [vp, vp, vp, vp, ctypes.POINTER(GraphInfo)]
     lib.como3r_solve.argtypes = [vp, vp, ctypes.c_int32, _f64p, ctypes.POINTER(GraphInfo)]
     lib.como3r_linearize.argtypes = [vp, vp, vp, _f64p]
+    lib.como3r_solve_timestamps.argtypes = [vp, _i64p, _i64p]
     lib.como3r_sim3_retract.argtypes = [vp, vp, ctypes.c_int32, vp]
     lib.como3r_update_inputs.argtypes = [vp, vp, vp]
     lib.como3r_time_stages.argtypes = [vp, vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
@@ -219,6 +220,14 @@ class Graph:
         st = _check(lib().como3r_solve(self.handle, _ptr(poses), int(iters),
                                        tr.ctypes.data_as(_f64p) if trace else None, info), "solve")
         return st, (tr.reshape(iters + 1, self.G) if trace else None), [_info_dict(x) for x in info]
+
+    def timestamps(self):
+        """como3r_solve_timestamps: (start_ns, done_ns[G]) of the last gn_step / solve."""
+        t0 = np.zeros(1, dtype=np.int64)
+        done = np.zeros(self.G, dtype=np.int64)
+        _check(lib().como3r_solve_timestamps(self.handle, t0.ctypes.data_as(_i64p), done.ctypes.data_as(_i64p)),
+               "solve_timestamps")
+        return int(t0[0]), done
 
     def linearize(self, poses, edge_out=None):
         cost = np.zeros(self.G)

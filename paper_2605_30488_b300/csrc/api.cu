@@ -79,6 +79,7 @@ struct como3r_graph {
   double *d_A = nullptr, *d_L = nullptr, *d_colscratch = nullptr, *d_gvec = nullptr, *d_tau = nullptr;
   uint8_t* d_frozen = nullptr;
   GraphInfoDev* d_ginfo = nullptr;
+  long long* d_start_ns = nullptr;  // device clock at the start of the last gn_step / solve
   int *d_iter = nullptr, *d_warn = nullptr;
   double* d_cost_hist = nullptr;
   int64_t cost_hist_cap = 0;
@@ -306,7 +307,7 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
       (rc = dalloc(g, &g->d_colscratch, (size_t)ncols * kColScratch)) ||
  (rc = dalloc(g, &g->d_gvec, (size_t)N * 7)) ||
       (rc = dalloc(g, &g->d_tau, (size_t)N * 7)) || (rc = upload(g, &g->d_frozen, p.frozen)) ||
-      (rc = dalloc(g, &g->d_ginfo, G)) || (rc = dalloc(g, &g->d_iter, 1)) || (rc = dalloc(g, &g->d_warn, 1)) ||
+      (rc = dalloc(g, &g->d_ginfo, G)) || (rc = dalloc(g, &g->d_start_ns, 1)) || (rc = dalloc(g, &g->d_iter, 1)) || (rc = dalloc(g, &g->d_warn, 1)) ||
       (rc = dalloc(g, &g->d_poses, (size_t)N * 8)) || (rc = dalloc(g, &g->d_bad, 1)))
     return rc;
   // solver plan
@@ -513,8 +514,9 @@ int como3r_gn_step(como3r_graph_t g, double* poses, double* H_out, double* g_out
   int rc = begin_call(g, poses);
   if (rc) return rc;
   const HostPlan& p = g->plan;
+  CK(launch_stamp(g->d_start_ns, g->stream), "stamp");
   if ((rc = enqueue_linearize(g, g->stream, nullptr, nullptr, nullptr))) return rc;
-  int64_t launches = 4;
+  int64_t launches = 5;
   if (H_out || g_out) {
     if (H_out)
       CK(cudaMemsetAsync(H_out, 0, sizeof(double) * 49 * (size_t)p.N * p.N, g->stream), "memset H_out");
@@ -547,14 +549,29 @@ int como3r_solve(como3r_graph_t g, double* poses, int32_t iters, double* cost_tr
   if (!g->iter_exec && (rc = capture(g, true, &g->iter_exec))) return rc;
   if (!g->eval_exec && (rc = capture(g, false, &g->eval_exec))) return rc;
   CK(cudaMemsetAsync(g->d_iter, 0, sizeof(int), g->stream), "memset");
+  CK(launch_stamp(g->d_start_ns, g->stream), "stamp");
   for (int k = 0; k < iters; ++k) CK(cudaGraphLaunch(g->iter_exec, g->stream), "graph launch");
   CK(cudaGraphLaunch(g->eval_exec, g->stream), "graph launch");
-  g->last_launches = 6 * (int64_t)iters + 4;
+  g->last_launches = 6 * (int64_t)iters + 5;
   if (cost_trace)
     CK(cudaMemcpyAsync(cost_trace, g->d_cost_hist, sizeof(double) * need, cudaMemcpyDeviceToHost, g->stream),
        "trace");
   if ((rc = end_call(g, poses))) return rc;
   return finish_info(g, info);
+}
+
+int como3r_solve_timestamps(como3r_graph_t g, int64_t* start_ns, int64_t* done_ns) {
+  if (!g) return set_error(COMO3R_ERR_INVALID_ARG, "graph handle is NULL");
+  const int G = g->plan.G;
+  long long t0 = 0;
+  CK(cudaMemcpyAsync(&t0, g->d_start_ns, sizeof(t0), cudaMemcpyDeviceToHost, g->stream), "readback");
+  CK(cudaMemcpyAsync(g->h_ginfo, g->d_ginfo, sizeof(GraphInfoDev) * G, cudaMemcpyDeviceToHost, g->stream),
+     "readback");
+  CK(cudaStreamSynchronize(g->stream), "sync");
+  if (start_ns) *start_ns = t0;
+  if (done_ns)
+    for (int k = 0; k < G; ++k) done_ns[k] = g->h_ginfo[k].done_ns;
+  return COMO3R_OK;
 }
 
 int como3r_linearize(como3r_graph_t g, const double* poses, double* edge_out, double* cost_out) {

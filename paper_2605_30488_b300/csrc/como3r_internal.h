@@ -47,7 +47,17 @@ struct GraphInfoDev {          // per graph, written on the device
   int32_t attempts;
   int32_t solved;
   long long skipped;
+  long long done_ns;           // %globaltimer when this graph's last factorisation ended
 };
+
+#ifdef __CUDACC__
+// Device clock (ns): %globaltimer, the same time base on every SM.
+__device__ __forceinline__ long long globaltimer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+#endif
 
 // Solver plan of all graphs (device arrays).  Every index inside a graph's plan is local
 // to that graph (slots 0..nslot-1, columns 0..ncol-1 in elimination order, triplets and
@@ -195,6 +205,7 @@ cudaError_t launch_points_from_logdepth(int dtype, const float* rays, const floa
                                         int64_t n, void* out, cudaStream_t s);
 cudaError_t launch_rays_from_points(int dtype, const void* points, int64_t n, float* rays, float* logdepth,
                                     float* conf, cudaStream_t s);
+cudaError_t launch_stamp(long long* out, cudaStream_t s);
 cudaError_t launch_check_matches(const int32_t* midx, const EdgeStatic* es, int E, unsigned long long* bad,
                                  long long* edge_valid, cudaStream_t s);
 

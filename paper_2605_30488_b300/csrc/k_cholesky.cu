@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     if (tid == 0) {
       ginfo[g].attempts = 1;
       ginfo[g].solved = 1;
+      ginfo[g].done_ns = globaltimer_ns();
     }
     return;
   }
@@ -401,9 +402,11 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
   } else {
     for (int x = tid; x < 7 * ncol; x += kSolveThreads) tau[7 * col_kf[x / 7] + x % 7] = 0.0;
   }
+  __syncthreads();  // every thread's tau is written before the stamp
   if (tid == 0) {
     ginfo[g].attempts = ok ? attempt + 1 : max_attempts;
     ginfo[g].solved = ok ? 1 : 0;
+    ginfo[g].done_ns = globaltimer_ns();
     if (!ok) atomicOr(warn, 1);
   }
 }
@@ -440,6 +443,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
     if (tid == 0 && rank == 0) {
       ginfo[g].attempts = 1;
       ginfo[g].solved = 1;
+      ginfo[g].done_ns = globaltimer_ns();
     }
     return;
   }
@@ -557,6 +561,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
     if (!ok) atomicOr(warn, 1);
   }
   cl.sync();  // no CTA leaves while another may still read its shared memory
+  if (tid == 0 && rank == 0) ginfo[g].done_ns = globaltimer_ns();  // every CTA's tau is written
 }
 
 }  // namespace

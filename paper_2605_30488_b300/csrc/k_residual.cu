@@ -4,8 +4,10 @@
 // Work is split into items (edge, [begin, end) of the streamed keyframe's pixels), each
 // owned by one warp of a persistent grid.  Every lane accumulates its pixels (pixel
 // m = begin + lane + 32 k: coalesced streams of match_idx and X_i, a gather of X_j[n])
-// into 33 registers -- the 25 structurally nonzero entries of H_rel = sum J^T W J, the 7
-// of g_rel = sum J^T W e, and the cost -- then the warp reduces them with shuffles and
+// into 34 registers -- the 25 structurally nonzero entries of H_rel = sum J^T W J, the 7
+// of g_rel = sum J^T W e, and the cost with the error of its FP32 sum (the cost terms are
+// all non-negative, so a lane's long sum would otherwise drift by ~1e-5 relative over a
+// few thousand matches) -- then the warp reduces them with shuffles and
 // writes one partial record per item.  No CTA barrier, no shared memory, no atomics:
 // results are bitwise reproducible and warps never wait for each other.
 //
@@ -83,18 +85,27 @@ __device__ __forceinline__ void load_px(const void* __restrict__ base, int64_t p
 template <typename R>
 struct Acc {
   R v[kAcc];  // [0..24] H_rel unique entries, [25..31] g_rel
-  R Ew;       // sum_c w_c r_c^2
-  R Em;       // sum_c min(|r_c|, kappa)^2; the cost is Ew - Em / 2
+  R E;        // sum of the Huber costs rho(r_c) of the lane's matches
+  R Ec;       // its compensation (FP32: error-free Fast2Sum terms; FP64: unused, 0)
   int skipped;
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) v[k] = R(0);
-    Ew = R(0);
-    Em = R(0);
+    E = R(0);
+    Ec = R(0);
     skipped = 0;
   }
-  __device__ __forceinline__ R cost() const { return fma(R(-0.5), Em, Ew); }
 };
+
+// E + x with its rounding error kept in Ec (both non-negative: Fast2Sum on the larger
+// and the smaller operand is error-free); FP64 adds plainly.
+__device__ __forceinline__ void add_cost(float& E, float& Ec, float x) {
+  const float hi = fmaxf(E, x), lo = fminf(E, x);
+  const float s = __fadd_rn(hi, lo);
+  Ec = __fadd_rn(Ec, __fsub_rn(lo, __fsub_rn(s, hi)));
+  E = s;
+}
+__device__ __forceinline__ void add_cost(double& E, double&, double x) { E += x; }
 
 // One match: residual, robust weights, Jacobian rows, accumulation (see file header).
 template <typename R>
@@ -123,15 +134,17 @@ __device__ __forceinline__ void accumulate(R xi, R yi, R zi, R ci, R xj, R yj, R
   const R sr = sq * k.isr, sd = sq * k.isd;
   const R r0 = sr * e0, r1 = sr * e1, r2 = sr * e2, r3 = sd * e3;
   // Huber: w = min(1, kappa / |r|) (kappa / 0 = inf gives 1); with m = min(|r|, kappa),
-  // rho(r) = w r^2 - m^2 / 2 on both branches (r^2 / 2 inside, kappa |r| - kappa^2 / 2 outside)
+  // rho(r) = m (|r| - m / 2) on both branches (r^2 / 2 inside, kappa |r| - kappa^2 / 2 outside)
   const R a0 = fabs(r0), a1 = fabs(r1), a2 = fabs(r2), a3 = fabs(r3);
   const R w0 = fmin(R(1), k.kappa * rcp(a0));
   const R w1 = fmin(R(1), k.kappa * rcp(a1));
   const R w2 = fmin(R(1), k.kappa * rcp(a2));
   const R w3 = fmin(R(1), k.kappa * rcp(a3));
   const R m0 = fmin(a0, k.kappa), m1 = fmin(a1, k.kappa), m2 = fmin(a2, k.kappa), m3 = fmin(a3, k.kappa);
-  acc.Ew = fma(w0 * r0, r0, fma(w1 * r1, r1, fma(w2 * r2, r2, fma(w3 * r3, r3, acc.Ew))));
-  acc.Em = fma(m0, m0, fma(m1, m1, fma(m2, m2, fma(m3, m3, acc.Em))));
+  // rho(r_c) = m_c (|r_c| - m_c / 2) on both branches
+  const R mh = R(-0.5);
+  add_cost(acc.E, acc.Ec,
+           fma(m0, fma(mh, m0, a0), fma(m1, fma(mh, m1, a1), fma(m2, fma(mh, m2, a2), m3 * fma(mh, m3, a3)))));
   const R qr = q * k.ivr;
   const R u0 = w0 * qr, u1 = w1 * qr, u2 = w2 * qr, u3 = w3 * q * k.ivd;  // W_c
   const R f0 = u0 * e0, f1 = u1 * e1, f2 = u2 * e2, f3 = u3 * e3;        // W_c e_c
@@ -194,12 +207,12 @@ __device__ __forceinline__ void accumulate(R xi, R yi, R zi, R ci, R xj, R yj, R
 // element (AccPair) and are added when the record is written.
 struct AccPair {
   float2 v[kAcc];
-  float2 Ew, Em;
+  float2 E, Ec;  // Huber cost sums and their compensations, per element
   int skipped;
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int k = 0; k < kAcc; ++k) v[k] = make_float2(0.f, 0.f);
-    Ew = Em = make_float2(0.f, 0.f);
+    E = Ec = make_float2(0.f, 0.f);
     skipped = 0;
   }
 };
@@ -253,8 +266,13 @@ __device__ __forceinline__ void accumulate_pair(float2 xi, float2 yi, float2 zi,
   const float2 w2 = f2(fminf(1.f, kr2.x), fminf(1.f, kr2.y)), w3 = f2(fminf(1.f, kr3.x), fminf(1.f, kr3.y));
   const float2 m0 = f2(fminf(a0.x, k.kappa), fminf(a0.y, k.kappa)), m1 = f2(fminf(a1.x, k.kappa), fminf(a1.y, k.kappa));
   const float2 m2 = f2(fminf(a2.x, k.kappa), fminf(a2.y, k.kappa)), m3 = f2(fminf(a3.x, k.kappa), fminf(a3.y, k.kappa));
-  acc.Ew = fma2(mul2(w0, r0), r0, fma2(mul2(w1, r1), r1, fma2(mul2(w2, r2), r2, fma2(mul2(w3, r3), r3, acc.Ew))));
-  acc.Em = fma2(m0, m0, fma2(m1, m1, fma2(m2, m2, fma2(m3, m3, acc.Em))));
+  {
+    const float2 h = f2(-0.5f);
+    const float2 rho = fma2(m0, fma2(h, m0, a0), fma2(m1, fma2(h, m1, a1), fma2(m2, fma2(h, m2, a2),
+                                                                            mul2(m3, fma2(h, m3, a3)))));
+    add_cost(acc.E.x, acc.Ec.x, rho.x);
+    add_cost(acc.E.y, acc.Ec.y, rho.y);
+  }
   const float2 qr = mul2(q, f2(k.ivr));
   const float2 u0 = mul2(w0, qr), u1 = mul2(w1, qr), u2 = mul2(w2, qr), u3 = mul2(mul2(w3, q), f2(k.ivd));
   const float2 g0 = mul2(u0, e0), g1 = mul2(u1, e1), g2 = mul2(u2, e2), g3 = mul2(u3, e3);
@@ -372,6 +390,14 @@ __device__ __forceinline__ double warp_sum_pair(double x, double& c) {
   return x;
 }
 
+// Plain warp sum (the lanes' cost compensations: tiny, so their own rounding is moot).
+__device__ __forceinline__ float warp_sum_plain(float x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  return x;
+}
+__device__ __forceinline__ double warp_sum_plain(double) { return 0.0; }
+
 // Partial record of one item: kPartial slots of 8 bytes.  Slots 0..31 hold the 32
 // butterfly accumulators, 32 the cost, 33 the skipped-match count, 34..35 zero.  MIXED
 // writes each slot as float2 (sum, compensation), PLAIN as one double.
@@ -428,7 +454,8 @@ __device__ __forceinline__ void write_record(Acc<R>& acc, void* partials, int it
   R comp[kAcc];
   warp_transpose_reduce(acc.v, comp, lane);
   R Ec = R(0);
-  const R Ev = warp_sum_pair(acc.cost(), Ec);
+  const R Ev = warp_sum_pair(acc.E, Ec);
+  Ec += warp_sum_plain(acc.Ec);
   const int sk = __reduce_add_sync(0xffffffffu, acc.skipped);
   store_slot(rec, lane, acc.v[0], comp[0]);
   if (lane == 0) {
@@ -726,8 +753,9 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
       if (flush) {
 #pragma unroll
         for (int q = 0; q < kAcc; ++q) acc.v[q] = pacc.v[q].x + pacc.v[q].y;
-        acc.Ew = pacc.Ew.x + pacc.Ew.y;
-        acc.Em = pacc.Em.x + pacc.Em.y;
+        float err;
+        acc.E = two_sum(pacc.E.x, pacc.E.y, err);
+        acc.Ec = pacc.Ec.x + pacc.Ec.y + err;
         acc.skipped = pacc.skipped;
         pacc.zero();
       }
@@ -816,7 +844,8 @@ __device__ __forceinline__ void cta_record(Acc<R>& acc, void* partials, int rec_
   R comp[kAcc];
   warp_transpose_reduce(acc.v, comp, lane);
   R Ec = R(0);
-  const R Ev = warp_sum_pair(acc.cost(), Ec);
+  const R Ev = warp_sum_pair(acc.E, Ec);
+  Ec += warp_sum_plain(acc.Ec);
   const int sk = __reduce_add_sync(0xffffffffu, acc.skipped);
   red[warp][lane] = (double)acc.v[0] + (double)comp[0];
   if (lane == 0) {

@@ -351,6 +351,14 @@ cudaError_t launch_retract(const double* tau, double* poses, const uint8_t* froz
   return cudaGetLastError();
 }
 
+// One device-clock stamp into *out (marks the start of a timed call on its stream).
+__global__ void stamp_kernel(long long* out) { *out = globaltimer_ns(); }
+
+cudaError_t launch_stamp(long long* out, cudaStream_t s) {
+  stamp_kernel<<<1, 1, 0, s>>>(out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_matches(const int32_t* midx, const EdgeStatic* es, int E, unsigned long long* bad,
                                  long long* edge_valid, cudaStream_t s) {
   if (E <= 0) return cudaSuccess;

@@ -500,6 +500,17 @@ void plan_stats(const HostPlan& p, int64_t* s) {
   int64_t nd = 0;
   for (int8_t k : p.order_kind) nd += k;
   s[COMO3R_STAT_ND_GRAPHS] = nd;
+  // FP64 operations of one factorisation and solve (an FMA counts 2): per column the 7x7
+  // Cholesky (140) with its right-hand side (49), L_cc^{-1} (114) and the back-substitution
+  // product with it (56); per off-diagonal block the triangular solve (343) and its
+  // back-substitution product (98); per update triplet a 7x7x7 product (686), and 98 more
+  // when the destination is diagonal (the right-hand side rides along).
+  const int64_t cols = s[COMO3R_STAT_COLUMNS], offdiag = s[COMO3R_STAT_BLOCKS] - cols;
+  int64_t rhs_tri = 0;
+  for (const int4& t : p.lutask)
+    if (t.w >= 0) rhs_tri += t.z - t.y;
+  s[COMO3R_STAT_SOLVE_FLOPS] = cols * (140 + 49 + 114 + 56) + offdiag * (343 + 98) +
+                               (int64_t)p.ltri.size() * 686 + rhs_tri * 98;
 }
 
 

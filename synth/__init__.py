@@ -8,8 +8,9 @@ exponential); poses are perturbed with a plain axis-angle rotation, a body-frame
 offset and a scale factor.
 """
 from .cloud import make_cloud_problem
+from .cloud_gpu import graph_subproblem, make_cloud_batch_gpu
 from .scene import (Problem, WORKLOADS, make_problem, make_workload, quat_from_matrix,
                     matrix_from_quat)
 
-__all__ = ["Problem", "WORKLOADS", "make_problem", "make_workload", "make_cloud_problem", "quat_from_matrix",
-           "matrix_from_quat"]
+__all__ = ["Problem", "WORKLOADS", "make_problem", "make_workload", "make_cloud_problem", "make_cloud_batch_gpu",
+           "graph_subproblem", "quat_from_matrix", "matrix_from_quat"]

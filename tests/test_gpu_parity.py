@@ -311,3 +311,27 @@ def test_multi_sm_solve_failure_gives_zero_update(C, tiny, monkeypatch):
     assert st & C.WARN_SOLVE_FAILED
     assert info[0]["attempts"] == tiny.max_attempts and not info[0]["solved"]
     np.testing.assert_array_equal(poses.cpu().numpy(), p)
+
+
+@pytest.mark.parametrize("ctas", [0, 4])
+def test_solve_timestamps(C, ctas, monkeypatch):
+    """Device-clock stamps of a call: start after the pose upload, each graph's end after
+    it and inside the call's wall time; the last gn_step's stamps replace the solve's."""
+    import time
+    import torch
+    monkeypatch.setenv("COMO3R_SOLVE_CLUSTER", str(ctas))
+    batch = make_problem(22, agents=2, n_kf=4, H=24, W=32, f=25.0, n_inter=1, num_graphs=3, name="batch3")
+    poses = torch_poses(batch.poses_init)
+    with C.Graph(batch, mode=C.MIXED) as g:
+        assert g.stats()["solve_ctas"] == max(ctas, 1)
+        torch.cuda.synchronize()
+        w0 = time.time_ns()
+        g.solve(poses, 5)
+        torch.cuda.synchronize()
+        wall = time.time_ns() - w0
+        t0, done = g.timestamps()
+        assert t0 > 0 and done.shape == (3,)
+        assert np.all(done > t0) and np.all(done - t0 <= wall)
+        g.gn_step(poses)
+        t1, done1 = g.timestamps()
+        assert t1 > done.max() and np.all(done1 > t1)

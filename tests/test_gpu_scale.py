@@ -165,3 +165,44 @@ def test_batch_of_64_uneven_graphs(C):
     sl = slice(7 * k0, 7 * k1)
     assert rel_fro(H[sl, sl].cpu().numpy(), Ho) <= FP64_TOL
     assert rel_fro(gv[sl].cpu().numpy(), go) <= FP64_TOL
+
+
+def _cfg5_check(C, specs, sample_graphs, iters):
+    """Noise-free cfg5-sized batch generated in device memory: every graph recovers its
+    ground truth in the mixed form; sampled edges of sampled graphs equal the oracle's
+    blocks at the initial poses; the per-graph device stamps lie inside the call."""
+    import time
+    import torch
+    from synth import graph_subproblem, make_cloud_batch_gpu
+    prob, pts, midx = make_cloud_batch_gpu(5, specs, device="cuda", noise=0.0, outlier=0.0)
+    with C.Graph(prob, mode=C.MIXED, points=pts, match_idx=midx) as g:
+        rec = edge_records(C, g, prob.poses_init)
+        poses = dev(prob.poses_init)
+        torch.cuda.synchronize()
+        w0 = time.time_ns()
+        st, trace, info = g.solve(poses, iters)
+        torch.cuda.synchronize()
+        wall_ns = time.time_ns() - w0
+        t0, done = g.timestamps()
+    assert all(x["solved"] for x in info)
+    assert np.all(done >= t0) and np.all(done - t0 <= wall_ns)
+    err = pose_err(poses.cpu().numpy(), prob.poses_gt)
+    assert max(err.values()) <= MIXED_TOL, err
+    rng = np.random.default_rng(0)
+    for gsel in sample_graphs:
+        sub = graph_subproblem(prob, pts, midx, gsel)
+        e0 = int(prob.edge_offset[gsel])
+        edges = rng.choice(sub.num_edges, size=min(2, sub.num_edges), replace=False)
+        check_sampled_edges(sub, rec[e0:e0 + sub.num_edges], edges, MIXED_TOL, sub.poses_init)
+    return prob
+
+
+def test_cfg5_batch_of_64_full_size(C):
+    from synth.cloud_gpu import batch64_specs
+    prob = _cfg5_check(C, batch64_specs(noise=0.0, outlier=0.0), sample_graphs=(0, 31, 63), iters=10)
+    assert prob.num_graphs == 64 and prob.pixels_of().sum() > 2 ** 31  # 64-bit pixel offsets exercised
+
+
+def test_cfg5_chain_2000_full_resolution(C):
+    from synth.cloud_gpu import chain2000_spec
+    _cfg5_check(C, chain2000_spec(noise=0.0, outlier=0.0), sample_graphs=(0,), iters=10)
