@@ -18,7 +18,9 @@ matrices and no blocking or fusion:
   (Eq. jacobian) chained to both endpoints by -/+ Ad_{T_i^{-1}} (Sec. III-D);
 * the regularised normal equations (Eq. normal) with the epsilon escalation
   eps_r = eps_0 * 100^r, at most six attempts, zero update if all fail (Sec. III-D);
-* closed-form Umeyama alignment (Eq. align, Eq. umeyama).
+* closed-form Umeyama alignment (Eq. align, Eq. umeyama), the bidirectional support gate
+  of cross-agent candidates (Sec. III-B) and the gauge transport with its endpoint
+  fallback (Sec. III-C).
 
 Readings where the paper is silent (each also listed in the design notes):
 
@@ -485,6 +487,67 @@ def umeyama(x: np.ndarray, y: np.ndarray) -> Tuple[float, np.ndarray, np.ndarray
     s = float(np.trace(S @ np.diag(lam)) / ((yc * yc).sum() / x.shape[0]))
     t = mx - s * R @ my
     return s, R, t
+
+
+# ============================ cross-agent verification and gauge synchronisation
+# Sec. III-B (bidirectional support gate) and Sec. III-C (Eq. align, Eq. umeyama, and the
+# endpoint transform below N_c^min correspondences).
+#
+# Readings: a match of pixel m (of the view whose pixels are listed) is "valid" when its
+# index is >= 0, and "high-confidence" when moreover c_m * c_n >= q_min^2, i.e.
+# q_mn = sqrt(c_m c_n) >= q_min, tested on the exact product of the stored confidences
+# (exact in FP64 for FP16 / FP32 storage) against q_min^2 rounded once to FP64; nu of a
+# view = its high-confidence matches / its pixel count; the alignment uses the
+# high-confidence matches of the forward direction (pixels of i matched into j), lifted
+# with the current poses; a match whose points are not finite is neither counted nor used.
+def support_mask(Pa: np.ndarray, Pb: np.ndarray, idx: np.ndarray, q_min: float) -> np.ndarray:
+    """High-confidence valid matches of the pixels of view a into view b (boolean [P_a])."""
+    idx = np.asarray(idx, dtype=np.int64)
+    ok = idx >= 0
+    n = np.where(ok, idx, 0)
+    ca = Pa[:, 3].astype(np.float64)
+    cb = Pb[n, 3].astype(np.float64)
+    fin = np.isfinite(Pa.astype(np.float64)).all(axis=1) & np.isfinite(Pb[n].astype(np.float64)).all(axis=1)
+    return ok & fin & (ca * cb >= float(q_min) * float(q_min))
+
+
+def gauge_candidate(Ti: np.ndarray, Tj: np.ndarray, Pi: np.ndarray, Pj: np.ndarray, idx_ij: np.ndarray,
+                    idx_ji: np.ndarray, q_min: float = 1.5, nu_min: float = 0.1, nc_min: int = 64) -> dict:
+    """One inter-agent candidate (i, j): the support fractions nu_i, nu_j, the admission
+    decision min(nu_i, nu_j) >= nu_min (Sec. III-B), and the similarity T* that maps j's
+    component onto i's (Sec. III-C): Umeyama on the lifted correspondences
+    x = T_i X_i,m, y = T_j X_j,n when there are at least nc_min of them, else the
+    endpoint transform T_i T_j^{-1}.  T* is to be left-multiplied onto the moving poses."""
+    mf = support_mask(Pi, Pj, idx_ij, q_min)
+    mb = support_mask(Pj, Pi, idx_ji, q_min)
+    nu_i = float(mf.sum()) / Pi.shape[0]
+    nu_j = float(mb.sum()) / Pj.shape[0]
+    m = np.nonzero(mf)[0]
+    n = np.asarray(idx_ij, dtype=np.int64)[m]
+    x = transform(Ti, Pi[m, :3].astype(np.float64))
+    y = transform(Tj, Pj[n, :3].astype(np.float64))
+    Nc = int(m.size)
+    if Nc >= nc_min:
+        s, R, t = umeyama(x, y)
+        Ts = np.eye(4)
+        Ts[:3, :3] = s * R
+        Ts[:3, 3] = t
+        fallback = False
+    else:
+        Ts = Ti @ sim3_inverse(Tj)
+        fallback = True
+    res = x - transform(Ts, y) if Nc else np.zeros((0, 3))
+    rms = float(np.sqrt((res * res).sum(axis=1).mean())) if Nc else 0.0
+    return dict(nu_i=nu_i, nu_j=nu_j, n_i=int(mf.sum()), n_j=int(mb.sum()), n_c=Nc,
+                admitted=bool(min(nu_i, nu_j) >= nu_min), fallback=fallback, T=Ts, rms=rms)
+
+
+def gauge_transport(poses: np.ndarray, Ts: np.ndarray, members: Sequence[int]) -> np.ndarray:
+    """Left-multiplies T* onto the poses of the moving component's keyframes (Sec. III-C)."""
+    out = np.array(poses, dtype=np.float64, copy=True)
+    for k in members:
+        out[k] = matrix_to_pose(Ts @ pose_to_matrix(out[k]))
+    return out
 
 
 # =================================================================== error reports

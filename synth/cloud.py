@@ -20,7 +20,9 @@ loop closures, 4 x 150 keyframe teams, batches of dozens of graphs).  Recipe (on
   ground truth) and the matches form a shifted, coherent gather with a non-overlap band.
 * Edges: sequential (k, k+1), covisibility (k, k+2) for even k, loop closures
   (k, k - loop) for k = loop, 2 loop, ..., and for teams ``n_inter`` inter-agent pairs
-  with the most shared canvas cells (each agent linked to an earlier one first).
+  with the most shared canvas cells (each agent linked to an earlier one first); with
+  ``reverse_inter`` the inter-agent pairs are listed again in the other direction (the
+  two decoded directions of a cross-agent candidate).
 * Noise, outliers and confidences as in the ray-cast scenes: points scaled along their
   ray by (1 + noise N(0,1)), a fraction ``outlier`` of each edge's matches redirected to
   a uniformly drawn pixel of j, confidences lognormal(1, 0.5).
@@ -60,7 +62,7 @@ def _canvas(rng, Hc: int, Wc: int) -> np.ndarray:
 
 def _graph(rng, *, agents: int, n_kf: int, H: int, W: int, period: int, shift: int, loop: int, n_inter: int,
            noise: float, outlier: float, pert_rot: float, pert_trans: float, pert_scale: float, kf_base: int,
-           dtype=np.float32):
+           dtype=np.float32, reverse_inter: bool = False):
     Hc, Wc = H + 2 * shift + 2, W + 2 * shift + 2
     world = _canvas(rng, Hc, Wc).reshape(-1, 3)
     N = agents * n_kf
@@ -120,6 +122,8 @@ def _graph(rng, *, agents: int, n_kf: int, H: int, W: int, period: int, shift: i
             if (j, i) not in inter and sc > 0:
                 inter.append((j, i))
         edges += inter
+        if reverse_inter:  # the same pairs in the other direction (pixels of the later agent listed)
+            edges += [(j, i) for (i, j) in inter]
     idx = []
     for (i, j) in edges:
         dv = orig[i, 0] - orig[j, 0]
@@ -163,7 +167,7 @@ def make_cloud_problem(seed: int = 0, graph_specs: Optional[Sequence[dict]] = No
     pert_scale)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     base = dict(agents=1, n_kf=20, H=48, W=64, period=100, shift=8, loop=0, n_inter=4, noise=0.0, outlier=0.0,
-                pert_rot=0.05, pert_trans=0.1, pert_scale=1.05)
+                pert_rot=0.05, pert_trans=0.1, pert_scale=1.05, reverse_inter=False)
     base.update(defaults)
     specs = list(graph_specs) if graph_specs is not None else [base]
     parts: List[dict] = []

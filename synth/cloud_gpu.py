@@ -33,11 +33,12 @@ import numpy as np
 from .scene import Problem, _axis_angle, quat_from_matrix
 
 _DEFAULTS = dict(agents=1, n_kf=20, H=48, W=64, period=100, shift=8, loop=0, n_inter=4, noise=0.0, outlier=0.0,
-                 pert_rot=0.05, pert_trans=0.1, pert_scale=1.05)
+                 pert_rot=0.05, pert_trans=0.1, pert_scale=1.05, reverse_inter=False)
 
 
 def _graph_meta(rng, *, agents: int, n_kf: int, H: int, W: int, period: int, shift: int, loop: int, n_inter: int,
-                noise: float, outlier: float, pert_rot: float, pert_trans: float, pert_scale: float) -> dict:
+                noise: float, outlier: float, pert_rot: float, pert_trans: float, pert_scale: float,
+                reverse_inter: bool = False) -> dict:
     """Host part of one graph: canvas field, window origins, cameras, edges and poses."""
     Hc, Wc = H + 2 * shift + 2, W + 2 * shift + 2
     field = [tuple(rng.uniform(0.5, 3.0, size=2)) + tuple(rng.uniform(0, 2 * math.pi, size=2)) for _ in range(4)]
@@ -85,6 +86,8 @@ def _graph_meta(rng, *, agents: int, n_kf: int, H: int, W: int, period: int, shi
             if (j, i) not in inter and sc > 0:
                 inter.append((j, i))
         edges += inter
+        if reverse_inter:  # the same pairs in the other direction (pixels of the later agent listed)
+            edges += [(j, i) for (i, j) in inter]
     gt = np.zeros((N, 8))
     init = np.zeros((N, 8))
     for k in range(N):

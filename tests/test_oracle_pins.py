@@ -3,7 +3,9 @@
 Each test checks the oracle against something other than itself: hand-derived values
 of Eq. (jacobian) / Eq. (residual), central finite differences, Lie-group identities,
 the Sim(3) gauge symmetry of Eq. (global), noise-free recovery, closed-form Umeyama
-(Eq. umeyama) against brute force, and the escalation schedule of Sec. III-D.
+(Eq. umeyama) against brute force, the escalation schedule of Sec. III-D, and the
+cross-agent gate and gauge synchronisation of Sec. III-B/III-C against constructed cases
+(a known extra similarity, the endpoint fallback, counted supports, equivariance).
 """
 import math
 import os
@@ -453,3 +455,103 @@ def test_unrolled_derivative_approaches_envelope(small_adj):
     env12 = abs(O.refined_cost_derivative(p, p.poses_init, 12, vl, vc, envelope=True))
     assert gap(12) <= 1e-3 * env12
     assert gap(1) >= 0.05 * env12
+
+
+# -------------------------------------- cross-agent gate and gauge synchronisation
+def _candidate(prob, e_fwd, e_bwd):
+    """Keyframes, pointmaps and the two match directions of one cross-agent candidate."""
+    px = prob.pixels_of().astype(np.int64)
+    off = np.concatenate([[0], np.cumsum(px)])
+    slots = np.concatenate([[0], np.cumsum(px[prob.edge_i.astype(np.int64)])])
+    i, j = int(prob.edge_i[e_fwd]), int(prob.edge_j[e_fwd])
+    assert (int(prob.edge_i[e_bwd]), int(prob.edge_j[e_bwd])) == (j, i)
+    Pi = prob.points[off[i]:off[i + 1]].astype(np.float64)
+    Pj = prob.points[off[j]:off[j + 1]].astype(np.float64)
+    return i, j, Pi, Pj, prob.match_idx[slots[e_fwd]:slots[e_fwd + 1]], prob.match_idx[slots[e_bwd]:slots[e_bwd + 1]]
+
+
+def _team(seed=31, **kw):
+    from synth import make_cloud_problem
+    spec = dict(agents=2, n_kf=6, H=24, W=32, period=30, shift=4, n_inter=2, reverse_inter=True)
+    spec.update(kw)
+    return make_cloud_problem(seed, [spec], dtype=np.float64)
+
+
+def test_gauge_sync_recovers_the_moving_components_gauge():
+    """Sec. III-C: if agent 1's poses carry an extra similarity G, the aligned T* is G^{-1}
+    (exact correspondences), and transporting agent 1 by T* restores the ground truth."""
+    p = _team()
+    rng = np.random.default_rng(4)
+    G = rand_sim3(rng, rot=0.7, trans=3.0, logs=0.4)
+    moving = [k for k in range(p.num_kf) if p.agent_of[k] == 1]
+    poses = p.poses_gt.copy()
+    for k in moving:
+        poses[k] = O.matrix_to_pose(G @ O.pose_to_matrix(poses[k]))
+    E = p.num_edges
+    i, j, Pi, Pj, fwd, bwd = _candidate(p, E - 4, E - 2)
+    r = O.gauge_candidate(O.pose_to_matrix(poses[i]), O.pose_to_matrix(poses[j]), Pi, Pj, fwd, bwd, q_min=0.0)
+    assert not r["fallback"] and r["n_c"] >= 64 and r["admitted"]
+    np.testing.assert_allclose(r["T"], O.sim3_inverse(G), atol=1e-12)
+    assert r["rms"] < 1e-12
+    back = O.gauge_transport(poses, r["T"], moving)
+    assert max(O.pose_errors(back, p.poses_gt).values()) < 1e-12
+
+
+def test_gauge_sync_endpoint_fallback_below_nc_min():
+    """Fewer than N_c^min high-confidence matches: T* = T_i T_j^{-1}, which puts j's pose
+    exactly onto i's (the moving endpoint snaps onto the anchor)."""
+    p = _team()
+    E = p.num_edges
+    i, j, Pi, Pj, fwd, bwd = _candidate(p, E - 4, E - 2)
+    keep = np.nonzero(fwd >= 0)[0][:10]
+    Pi = Pi.copy()
+    Pi[:, 3] = 0.5
+    Pi[keep, 3] = 10.0  # with c_j in (e^-1, ...) only these pass q_min = 1.5 (c_i c_j >= 2.25)
+    Pj = Pj.copy()
+    Pj[:, 3] = 1.0
+    Ti, Tj = O.pose_to_matrix(p.poses_init[i]), O.pose_to_matrix(p.poses_init[j])
+    r = O.gauge_candidate(Ti, Tj, Pi, Pj, fwd, bwd, q_min=1.5, nc_min=64)
+    assert r["n_c"] == 10 and r["fallback"]
+    np.testing.assert_allclose(r["T"] @ Tj, Ti, atol=1e-12)
+
+
+def test_support_gate_counts_and_threshold():
+    """Sec. III-B: nu = fraction of a view's pixels with a valid match whose
+    q = sqrt(c_m c_n) reaches q_min (equality counts); the edge is admitted only when
+    both directions reach nu_min; non-finite points are not counted."""
+    p = _team()
+    E = p.num_edges
+    i, j, Pi, Pj, fwd, bwd = _candidate(p, E - 4, E - 2)
+    Pi, Pj = Pi.copy(), Pj.copy()
+    Pi[:, 3] = 1.0
+    Pj[:, 3] = 1.0
+    vf = np.nonzero(fwd >= 0)[0]
+    pick = vf[:100]
+    Pi[pick, 3] = 2.25  # with c_j = 1: q = 1.5 exactly, in both directions of a partner pair
+    partners = fwd[pick]
+    assert np.array_equal(bwd[partners], pick)  # the canvas matches are mutual on the overlap
+    bwd = bwd.copy()
+    bwd[partners[:63]] = -1  # 63 of the partners lose their backward match
+    Pi[vf[100], 3] = 2.25
+    Pi[vf[100], 0] = np.nan  # not finite: counted in neither direction
+    r = O.gauge_candidate(np.eye(4), np.eye(4), Pi, Pj, fwd, bwd, q_min=1.5, nu_min=0.1)
+    assert r["n_i"] == 100 and r["nu_i"] == 100 / Pi.shape[0]
+    assert r["n_j"] == 37 and r["nu_j"] == 37 / Pj.shape[0]
+    assert not r["admitted"]
+    r2 = O.gauge_candidate(np.eye(4), np.eye(4), Pi, Pj, fwd, bwd, q_min=1.0, nu_min=0.1)
+    nb = int((bwd >= 0).sum())
+    assert r2["n_i"] == len(vf) - 1 and r2["n_j"] == nb - 1
+    assert r2["admitted"] == (min((len(vf) - 1) / Pi.shape[0], (nb - 1) / Pj.shape[0]) >= 0.1)
+
+
+def test_gauge_sync_is_equivariant_under_a_common_similarity():
+    """A common similarity H applied to all poses conjugates T*: T*' = H T* H^{-1}."""
+    p = _team(seed=32, noise=0.01, outlier=0.1)
+    E = p.num_edges
+    i, j, Pi, Pj, fwd, bwd = _candidate(p, E - 3, E - 1)
+    H = rand_sim3(np.random.default_rng(5))
+    Ti, Tj = O.pose_to_matrix(p.poses_init[i]), O.pose_to_matrix(p.poses_init[j])
+    r = O.gauge_candidate(Ti, Tj, Pi, Pj, fwd, bwd, q_min=1.0)
+    r2 = O.gauge_candidate(H @ Ti, H @ Tj, Pi, Pj, fwd, bwd, q_min=1.0)
+    assert not r["fallback"]
+    np.testing.assert_allclose(r2["T"], H @ r["T"] @ O.sim3_inverse(H), rtol=1e-9, atol=1e-9)
