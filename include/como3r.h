@@ -285,6 +285,68 @@ int como3r_plan_stats(const como3r_graph_desc* desc, int64_t* stats /* [COMO3R_S
 int como3r_linearize_noalloc(const como3r_graph_desc* desc, const double* poses, double* edge_out,
                              void* cuda_stream);
 
+/* ---- Cross-agent candidate verification and gauge synchronisation (Sec. III-B, III-C).
+ *
+ * Candidate c = (kf_i[c], kf_j[c]) is a pair of keyframes of different agents with the two
+ * decoded match directions of the two-view prior.  Keyframe i belongs to the reference
+ * component, j to the moving one.  A match of pixel m (of the view whose pixels are listed)
+ * to pixel n is valid when its index is >= 0, and high-confidence when moreover both points
+ * are finite and c_m c_n >= q_min^2, i.e. q_mn = sqrt(c_m c_n) >= q_min (the exact product of
+ * the stored confidences, decided as in FP64 by both arithmetic modes).
+ *   nu_i = high-confidence matches of i's pixels into j / P_i, nu_j likewise from j into i;
+ *   admitted = min(nu_i, nu_j) >= nu_min (Sec. III-B);
+ *   T* (Sec. III-C) maps j's component onto i's and is to be left-multiplied onto every pose
+ *   of the moving component: with x = T_i X_i,m and y = T_j X_j,n over the forward
+ *   high-confidence matches (N_c = n_i of them), the Umeyama similarity of Eq. (umeyama)
+ *   minimising sum |x - (s R y + t)|^2 when N_c >= nc_min; otherwise (and when the
+ *   cross-covariance has rank < 2, so R is undetermined) the endpoint transform
+ *   T_i T_j^{-1}, which puts j's pose onto i's.
+ * The pass over the matches is HBM-bound: match rows and the streamed pixels are read once,
+ * the gathered pixels once per valid match.  MIXED accumulates the camera-frame moments in
+ * FP32 with Kahan-compensated lane sums and TwoSum warp merges (FP64 above the warp);
+ * PLAIN_FP64 in FP64.  The 3x3 SVD and everything after it are FP64. */
+typedef struct {
+  int32_t num_candidates;       /* C >= 0 */
+  int32_t num_kf;               /* keyframes described by pix_off and poses */
+  const int64_t* pix_off;       /* host [num_kf + 1]: first pixel of keyframe k in points_conf (non-decreasing) */
+  const void* points_conf;      /* device, packed (x, y, z, confidence) pixels of every keyframe (see above) */
+  int32_t dtype;                /* como3r_dtype of points_conf */
+  const int32_t* kf_i;          /* host [C] reference-side keyframe of each candidate */
+  const int32_t* kf_j;          /* host [C] moving-side keyframe (!= kf_i) */
+  const int32_t* match_ij;      /* device: per candidate P_{kf_i[c]} entries (pixel of j or -1), candidates concatenated */
+  const int32_t* match_ji;      /* device: per candidate P_{kf_j[c]} entries (pixel of i or -1), candidates concatenated */
+  const double* poses;          /* [num_kf][8] current poses, host or device */
+  double q_min;                 /* high-confidence threshold on q = sqrt(c_m c_n) (>= 0) */
+  double nu_min;                /* admission threshold of min(nu_i, nu_j), 0.1 in the paper */
+  int32_t nc_min;               /* fewest correspondences for the point-based alignment, 64 in the paper */
+  int32_t mode;                 /* COMO3R_MIXED or COMO3R_PLAIN_FP64 */
+} como3r_gauge_desc;
+
+typedef struct {
+  double T[8];                  /* T* as (tx, ty, tz, qx, qy, qz, qw, s) */
+  double nu_i, nu_j;            /* support fractions of the two views */
+  int64_t n_i, n_j;             /* high-confidence matches of each direction (n_i = N_c) */
+  int64_t valid_i, valid_j;     /* matches with index >= 0 of each direction */
+  int32_t admitted;             /* 1 if min(nu_i, nu_j) >= nu_min */
+  int32_t fallback;             /* 0 Umeyama; 1 endpoint transform (N_c < nc_min); 2 endpoint transform (rank < 2) */
+} como3r_gauge_result;
+
+/* Verifies and aligns C candidates on `cuda_stream` (device temporaries allocated and freed
+ * inside the call; synchronises the stream).  out host [C].  kernel_ms (host, nullable)
+ * receives the duration of the pass over the matches (CUDA events).
+ * Errors: INVALID_ARG (NULL pointers, bad ids or sizes, a match index outside [-1, P)),
+ * OOM, CUDA. */
+int como3r_gauge_sync(const como3r_gauge_desc* desc, void* cuda_stream, como3r_gauge_result* out,
+                      float* kernel_ms);
+
+/* Gauge transport (Sec. III-C): poses[k] <- T[which[k]] * poses[k] (Sim(3) left
+ * multiplication) for every keyframe k with 0 <= which[k] < num_candidates; others are
+ * left unchanged.  poses device [num_kf][8] in/out, which device [num_kf], T device
+ * [num_candidates][8] (e.g. the T fields of como3r_gauge_sync's results, uploaded).
+ * Asynchronous on `cuda_stream`.  Errors: INVALID_ARG, CUDA. */
+int como3r_gauge_transport(double* poses, int32_t num_kf, const int32_t* which, const double* T,
+                           int32_t num_candidates, void* cuda_stream);
+
 /* Human-readable text of a status code. */
 const char* como3r_status_str(int code);
 

@@ -54,6 +54,22 @@ class GraphInfo(ctypes.Structure):
                 ("valid_matches", ctypes.c_int64), ("skipped_matches", ctypes.c_int64)]
 
 
+class GaugeDesc(ctypes.Structure):
+    _fields_ = [
+        ("num_candidates", ctypes.c_int32), ("num_kf", ctypes.c_int32), ("pix_off", ctypes.POINTER(ctypes.c_int64)),
+        ("points_conf", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("kf_i", ctypes.POINTER(ctypes.c_int32)),
+        ("kf_j", ctypes.POINTER(ctypes.c_int32)), ("match_ij", ctypes.c_void_p), ("match_ji", ctypes.c_void_p),
+        ("poses", ctypes.c_void_p), ("q_min", ctypes.c_double), ("nu_min", ctypes.c_double),
+        ("nc_min", ctypes.c_int32), ("mode", ctypes.c_int32),
+    ]
+
+
+class GaugeResult(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_double * 8), ("nu_i", ctypes.c_double), ("nu_j", ctypes.c_double),
+                ("n_i", ctypes.c_int64), ("n_j", ctypes.c_int64), ("valid_i", ctypes.c_int64),
+                ("valid_j", ctypes.c_int64), ("admitted", ctypes.c_int32), ("fallback", ctypes.c_int32)]
+
+
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     if not os.path.exists(path):
         raise RuntimeError(f"libcomo3r.so not built ({path}); run `python -m paper_2605_30488_b300.build`")
@@ -78,6 +94,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.como3r_time_vjp.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
     lib.como3r_points_from_logdepth.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_int32, vp, vp]
     lib.como3r_rays_from_points.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, vp, vp, vp, vp]
+    lib.como3r_gauge_sync.argtypes = [ctypes.POINTER(GaugeDesc), vp, ctypes.POINTER(GaugeResult),
+                                      ctypes.POINTER(ctypes.c_float)]
+    lib.como3r_gauge_transport.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_int32, vp]
     lib.como3r_status_str.argtypes = [ctypes.c_int]
     lib.como3r_status_str.restype = ctypes.c_char_p
     lib.como3r_last_error.argtypes = []
@@ -361,3 +380,37 @@ def exported_symbols(header: str) -> Sequence[str]:
     import re
     txt = open(header).read()
     return re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(como3r_[a-z_0-9]+)\s*\(", txt, flags=re.M)
+
+
+def gauge_sync(points, dtype: int, pix_off, kf_i, kf_j, match_ij, match_ji, poses, q_min: float = 1.5,
+               nu_min: float = 0.1, nc_min: int = 64, mode: int = MIXED, stream=None, timing: bool = False):
+    """como3r_gauge_sync over candidates (kf_i[c], kf_j[c]) (Sec. III-B/III-C).
+
+    points, match_ij, match_ji: CUDA tensors (packed pixels; per-candidate match rows
+    concatenated); pix_off: int64 [num_kf + 1]; poses: [num_kf][8] (host or device).
+    Returns a list of dicts (T as a (t, q, s) array, nu_i, nu_j, n_i, n_j, valid_i, valid_j,
+    admitted, fallback), plus the kernel time in ms when `timing`."""
+    pix_off = np.ascontiguousarray(np.asarray(pix_off, dtype=np.int64))
+    kf_i = np.ascontiguousarray(np.asarray(kf_i, dtype=np.int32))
+    kf_j = np.ascontiguousarray(np.asarray(kf_j, dtype=np.int32))
+    C = int(kf_i.size)
+    d = GaugeDesc(num_candidates=C, num_kf=int(pix_off.size - 1),
+                  pix_off=pix_off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), points_conf=_ptr(points),
+                  dtype=int(dtype), kf_i=kf_i.ctypes.data_as(_i32p), kf_j=kf_j.ctypes.data_as(_i32p),
+                  match_ij=_ptr(match_ij), match_ji=_ptr(match_ji), poses=_ptr(poses), q_min=float(q_min),
+                  nu_min=float(nu_min), nc_min=int(nc_min), mode=int(mode))
+    out = (GaugeResult * max(C, 1))()
+    ms = ctypes.c_float(0.0)
+    _check(lib().como3r_gauge_sync(ctypes.byref(d), _torch_stream(stream), out,
+                                   ctypes.byref(ms) if timing else None), "gauge_sync")
+    res = [dict(T=np.array(list(r.T)), nu_i=r.nu_i, nu_j=r.nu_j, n_i=int(r.n_i), n_j=int(r.n_j),
+                valid_i=int(r.valid_i), valid_j=int(r.valid_j), admitted=bool(r.admitted), fallback=int(r.fallback))
+           for r in out[:C]]
+    return (res, float(ms.value)) if timing else res
+
+
+def gauge_transport(poses, which, T, stream=None):
+    """como3r_gauge_transport: poses[k] <- T[which[k]] poses[k] for which[k] >= 0 (CUDA tensors)."""
+    _check(lib().como3r_gauge_transport(_ptr(poses), int(poses.shape[0]), _ptr(which), _ptr(T), int(T.shape[0]),
+                                        _torch_stream(stream)), "gauge_transport")
+

@@ -36,6 +36,13 @@ int cuda_error(cudaError_t e, const char* where) {
   return set_error(COMO3R_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+}  // namespace
+
+// Error reporting for the entry points defined in other files (como3r_last_error).
+int como3r::report_error(int code, const char* msg) { return set_error(code, msg); }
+int como3r::report_cuda_error(cudaError_t e, const char* where) { return cuda_error(e, where); }
+
+namespace {
 #define CK(expr, where)                      \
   do {                                       \
     cudaError_t e_ = (expr);                 \

@@ -206,6 +206,9 @@ cudaError_t launch_points_from_logdepth(int dtype, const float* rays, const floa
 cudaError_t launch_rays_from_points(int dtype, const void* points, int64_t n, float* rays, float* logdepth,
                                     float* conf, cudaStream_t s);
 cudaError_t launch_stamp(long long* out, cudaStream_t s);
+// Sets the calling thread's como3r_last_error message and returns `code` (defined in api.cu).
+int report_error(int code, const char* msg);
+int report_cuda_error(cudaError_t e, const char* where);
 cudaError_t launch_check_matches(const int32_t* midx, const EdgeStatic* es, int E, unsigned long long* bad,
                                  long long* edge_valid, cudaStream_t s);
 
