@@ -550,6 +550,156 @@ def gauge_transport(poses: np.ndarray, Ts: np.ndarray, members: Sequence[int]) -
     return out
 
 
+# ======================= terminal segment-level structure refinement (Sec. III-E)
+# Eq. depth_parameter, Eq. depth_data, Eq. depth_total and the Jacobi-style damped Newton
+# update described after them.
+#
+# Readings: segment labels are given per pixel (the SLIC clustering is not part of the
+# method's hot path); a pixel takes part when its label is >= 0, its confidence >= c_min
+# (1.5), its point is finite with range > 1e-12, and its segment has >= min_pixels (16)
+# such pixels -- otherwise its point stays at the snapshot (eta = 0 for it).  Global
+# segment ids are k's base + label (base = sum of (max label + 1) of earlier keyframes).
+# Delta_gh (g < h) is the mean, over the unordered 4-adjacent pixel pairs (p in g,
+# p' in h) of a keyframe, of log d_p - log d_p' of the snapshot.  The normal equations are
+# those of the stacked weighted least-squares problem, which the printed H_prior =
+# lambda_prior I fixes: the boundary and prior terms enter as lambda * (.)^2 / 2 blocks
+# beside the data term's Huber costs (rho = r^2 / 2 inside the breakpoint):
+#   E' = E_data + lambda_smooth / 2 * E_bnd + lambda_prior / 2 * E_prior,  g = dE'/d eta.
+# The Huber breakpoint is the graph's kappa.  The 1x1 step is the LM step of the
+# back-end's damping form, delta = -g / ((1 + lambda_lm) H), clipped to |delta| <= eta_max;
+# segments of the fixed keyframes (the anchor and every other component's reference)
+# and inactive segments do not move.  A match touches the segments of its two pixels
+# (either may be none); the per-match degenerate rule is the pose path's.
+DEPTH_DEFAULTS = dict(c_min=1.5, min_pixels=16, sigma_point=0.05, lambda_smooth=1.0, lambda_prior=1.0,
+                      lambda_lm=0.05, eta_max=0.5)
+
+
+def depth_segments(prob, labels: np.ndarray, c_min: float = 1.5, min_pixels: int = 16, **_) -> dict:
+    """Effective global segment of every pixel (-1: none), segment count M, the boundary
+    pairs (g, h, Delta_gh), fixed segments, and the snapshot rays / log-ranges."""
+    arrs = problem_arrays(prob)
+    P = arrs["points"]
+    X = P[:, :3]
+    with np.errstate(invalid="ignore", over="ignore"):
+        d = np.sqrt((X * X).sum(axis=1))
+        fin = np.isfinite(P).all(axis=1) & (d > DEGENERATE)
+    logd = np.where(fin, np.log(np.where(fin, d, 1.0)), 0.0)
+    psi_ = np.where(fin[:, None], X / np.where(fin, d, 1.0)[:, None], 0.0)
+    labels = np.asarray(labels, dtype=np.int64)
+    eff = np.full(labels.shape, -1, dtype=np.int64)
+    fixed_kf = set()
+    for g in range(prob.num_graphs):
+        k0 = int(prob.kf_offset[g])
+        fixed_kf.update(k0 + a for a in component_anchors(prob, g))
+    base, M = [], 0
+    pairs: Dict[Tuple[int, int], List[float]] = {}
+    fixed = []
+    for g in range(prob.num_graphs):
+        H, W = int(prob.height[g]), int(prob.width[g])
+        for k in range(int(prob.kf_offset[g]), int(prob.kf_offset[g + 1])):
+            a0, a1 = arrs["pix_off"][k], arrs["pix_off"][k + 1]
+            L = labels[a0:a1]
+            Mk = int(L.max()) + 1 if (L >= 0).any() else 0
+            ok = (L >= 0) & fin[a0:a1] & (P[a0:a1, 3] >= c_min)
+            cnt = np.bincount(L[ok], minlength=Mk) if Mk else np.zeros(0, dtype=np.int64)
+            act = cnt >= min_pixels
+            e = np.where(ok & (L >= 0) & act[np.maximum(L, 0)] if Mk else ok & False, M + L, -1)
+            eff[a0:a1] = e
+            if k in fixed_kf:
+                fixed += list(range(M, M + Mk))
+            E2 = e.reshape(H, W)
+            LD = logd[a0:a1].reshape(H, W)
+            for (ea, eb, la, lb) in ((E2[:, :-1], E2[:, 1:], LD[:, :-1], LD[:, 1:]),
+                                     (E2[:-1, :], E2[1:, :], LD[:-1, :], LD[1:, :])):
+                sel = (ea >= 0) & (eb >= 0) & (ea != eb)
+                for u, v, lu, lv in zip(ea[sel], eb[sel], la[sel], lb[sel]):
+                    key, diff = ((int(u), int(v)), lu - lv) if u < v else ((int(v), int(u)), lv - lu)
+                    acc = pairs.setdefault(key, [0.0, 0])
+                    acc[0] += diff
+                    acc[1] += 1
+            base.append(M)
+            M += Mk
+    bnd = [(g_, h_, sm / n) for (g_, h_), (sm, n) in sorted(pairs.items())]
+    active = np.zeros(M, dtype=bool)
+    active[eff[eff >= 0]] = True
+    return dict(eff=eff, M=M, base=np.array(base, dtype=np.int64), pairs=bnd, fixed=np.array(sorted(set(fixed)),
+                dtype=np.int64), active=active, logd=logd, psi=psi_, conf=P[:, 3].copy(), arrs=arrs)
+
+
+def depth_terms(prob, poses: np.ndarray, eta: np.ndarray, seg: dict, sigma_point: float = 0.05,
+                lambda_smooth: float = 1.0, lambda_prior: float = 1.0, **_) -> Tuple[float, np.ndarray, np.ndarray]:
+    """(E', g, H) at eta: the objective, its full gradient and the Jacobi diagonal (the
+    cross-segment data term J_g^T W J_h and the off-diagonal boundary pair dropped)."""
+    M = seg["M"]
+    eta = np.asarray(eta)
+    g = np.zeros(M, dtype=eta.dtype)
+    Hd = np.zeros(M)
+    E = 0.0 * eta.sum()
+    arrs, eff, logd, psi_, conf = seg["arrs"], seg["eff"], seg["logd"], seg["psi"], seg["conf"]
+    kappa = prob.huber_k
+    T = [pose_to_matrix(p) for p in poses]
+    for e in range(prob.num_edges):
+        i, j = int(prob.edge_i[e]), int(prob.edge_j[e])
+        idx = prob.match_idx[arrs["idx_off"][e]:arrs["idx_off"][e + 1]]
+        m = np.nonzero(idx >= 0)[0]
+        n = idx[m].astype(np.int64)
+        pm, pn = arrs["pix_off"][i] + m, arrs["pix_off"][j] + n
+        si, sj = eff[pm], eff[pn]
+        eti = np.where(si >= 0, eta[np.maximum(si, 0)], 0.0)
+        etj = np.where(sj >= 0, eta[np.maximum(sj, 0)], 0.0)
+        Xi = (np.exp(logd[pm] + eti))[:, None] * psi_[pm]
+        Xj = (np.exp(logd[pn] + etj))[:, None] * psi_[pn]
+        Tij = sim3_inverse(T[i]) @ T[j]
+        Y = transform(Tij, Xj)
+        cc = conf[pm] * conf[pn]
+        ok = (np.isfinite(arrs["points"][pm]).all(1) & np.isfinite(arrs["points"][pn]).all(1)
+              & (_norm(Xi).real > DEGENERATE) & (_norm(Y).real > DEGENERATE) & (cc >= 0))
+        if not ok.any():
+            continue
+        Xi, Y, cc, si, sj = Xi[ok], Y[ok], cc[ok], si[ok], sj[ok]
+        k = np.sqrt(np.sqrt(cc)) / sigma_point
+        r = k[:, None] * (Y - Xi)
+        w = huber_weight(r, kappa)
+        E = E + huber_rho(r, kappa).sum()
+        Jg = -k[:, None] * Xi
+        Jh = k[:, None] * (Y - Tij[:3, 3])
+        for sg, J in ((si, Jg), (sj, Jh)):
+            a = sg >= 0
+            np.add.at(g, sg[a], (w * r * J).sum(axis=1)[a])
+            np.add.at(Hd, sg[a], (w * J * J).real.sum(axis=1)[a])
+    for (a, b, delta) in seg["pairs"]:
+        res = eta[a] - eta[b] + delta
+        E = E + 0.5 * lambda_smooth * res * res
+        g[a] += lambda_smooth * res
+        g[b] -= lambda_smooth * res
+        Hd[a] += lambda_smooth
+        Hd[b] += lambda_smooth
+    act = seg["active"]
+    E = E + 0.5 * lambda_prior * (eta[act] * eta[act]).sum()
+    g[act] += lambda_prior * eta[act]
+    Hd[act] += lambda_prior
+    return E, g, Hd
+
+
+def depth_refine(prob, poses: np.ndarray, eta0: np.ndarray, iters: int, seg: dict, **params):
+    """Up to `iters` Jacobi 1x1 damped Newton steps (poses fixed); returns (eta, trace of E')."""
+    p = dict(DEPTH_DEFAULTS)
+    p.update(params)
+    eta = np.array(eta0, dtype=np.float64, copy=True)
+    movable = seg["active"].copy()
+    movable[seg["fixed"]] = False
+    trace = []
+    for _ in range(iters):
+        E, g, Hd = depth_terms(prob, poses, eta, seg, **p)
+        trace.append(float(E))
+        step = np.zeros_like(eta)
+        mv = movable & (Hd > 0)
+        step[mv] = np.clip(-g[mv] / ((1.0 + p["lambda_lm"]) * Hd[mv]), -p["eta_max"], p["eta_max"])
+        eta = eta + step
+    trace.append(float(depth_terms(prob, poses, eta, seg, **p)[0]))
+    return eta, np.array(trace)
+
+
 # =================================================================== error reports
 def pose_errors(pa: np.ndarray, pb: np.ndarray, ref_scale: Optional[float] = None) -> Dict[str, float]:
     """Max over keyframes of rotation angle (rad), relative translation and relative scale error.

@@ -555,3 +555,113 @@ def test_gauge_sync_is_equivariant_under_a_common_similarity():
     r2 = O.gauge_candidate(H @ Ti, H @ Tj, Pi, Pj, fwd, bwd, q_min=1.0)
     assert not r["fallback"]
     np.testing.assert_allclose(r2["T"], H @ r["T"] @ O.sim3_inverse(H), rtol=1e-9, atol=1e-9)
+
+
+# ------------------------------------ segment-level structure refinement (Sec. III-E)
+def _depth_case(seed=51, sigma=0.05, outlier=0.0, noise=0.0):
+    from synth import make_cloud_problem
+    from synth.segments import perturb_segment_ranges, problem_labels
+    p = make_cloud_problem(seed, [dict(agents=2, n_kf=4, H=24, W=32, period=30, shift=4, n_inter=2,
+                                       noise=noise, outlier=outlier)], dtype=np.float64)
+    lab = problem_labels(p, n_seg=12, seed=seed)
+    pix_off = np.concatenate([[0], np.cumsum(p.pixels_of())])
+    anchors = set(O.component_anchors(p, 0))
+    pts = perturb_segment_ranges(p.points, lab, pix_off, sigma, seed=seed)
+    for k in anchors:  # the fixed keyframes keep their true ranges
+        pts[pix_off[k]:pix_off[k + 1]] = p.points[pix_off[k]:pix_off[k + 1]]
+    pts[:, 3] = np.maximum(pts[:, 3], 1.6)  # every pixel passes c_min
+    import dataclasses
+    return dataclasses.replace(p, points=pts), lab, p
+
+
+def test_depth_gradient_is_the_full_gradient():
+    """The Jacobi solver keeps the full gradient: g = dE'/d eta (complex step, exact to
+    rounding), with Huber-downweighted outliers present."""
+    p, lab, _ = _depth_case(outlier=0.1, noise=0.01)
+    seg = O.depth_segments(p, lab)
+    rng = np.random.default_rng(0)
+    eta = rng.normal(size=seg["M"]) * 0.05
+    _, g, _ = O.depth_terms(p, p.poses_gt, eta, seg)
+    h = 1e-30
+    for s in rng.choice(np.nonzero(seg["active"])[0], size=8, replace=False):
+        e = eta.astype(complex)
+        e[s] += 1j * h
+        Ec, _, _ = O.depth_terms(p, p.poses_gt, e, seg)
+        assert abs(np.imag(Ec) / h - g[s]) <= 1e-9 * max(1.0, abs(g[s])), s
+
+
+def test_depth_jacobi_diagonal_is_the_exact_hessian_diagonal_at_zero_residual():
+    """At consistent geometry (true ranges and poses) every data residual is 0, so the
+    Gauss-Newton diagonal equals d^2 E'/d eta_s^2 (central difference of the gradient)."""
+    _, lab, p = _depth_case()
+    seg = O.depth_segments(p, lab)
+    eta = np.zeros(seg["M"])
+    _, g0, H = O.depth_terms(p, p.poses_gt, eta, seg)
+    h = 1e-5
+    for s in np.nonzero(seg["active"])[0][::7]:
+        e1, e2 = eta.copy(), eta.copy()
+        e1[s] += h
+        e2[s] -= h
+        d2 = (O.depth_terms(p, p.poses_gt, e1, seg)[1][s] - O.depth_terms(p, p.poses_gt, e2, seg)[1][s]) / (2 * h)
+        assert abs(d2 - H[s]) <= 1e-6 * H[s], s
+
+
+def test_depth_boundary_delta_of_a_constructed_step():
+    """Two segments side by side whose log-ranges differ by a constant: Delta = -step."""
+    _, lab, p = _depth_case()
+    pts = p.points.copy()
+    H, W = int(p.height[0]), int(p.width[0])
+    lab2 = np.full(lab.shape, -1, dtype=np.int32)
+    P = H * W
+    cols = np.arange(P) % W
+    lab2[:P] = np.where(cols < W // 2, 0, 1)
+    d = np.where(cols < W // 2, np.exp(0.2), np.exp(0.2 + 0.37))
+    ray = pts[:P, :3] / np.linalg.norm(pts[:P, :3], axis=1, keepdims=True)
+    pts[:P, :3] = ray * d[:, None]
+    pts[:, 3] = 2.0
+    import dataclasses
+    seg = O.depth_segments(dataclasses.replace(p, points=pts), lab2)
+    assert len(seg["pairs"]) == 1
+    a, b, delta = seg["pairs"][0]
+    assert (a, b) == (0, 1) and abs(delta + 0.37) < 1e-12
+
+
+def test_depth_refinement_recovers_injected_segment_scales():
+    """Per-segment range errors exp(delta_g) on consistent data: iterated to convergence
+    the Jacobi steps reach a stationary point of E' (g = 0) that undoes the errors
+    (eta_g ~ -delta_g, up to the prior's pull), and E' falls."""
+    from synth.segments import problem_labels
+    p, lab, p0 = _depth_case(sigma=0.05)
+    seg = O.depth_segments(p, lab)
+    eta, trace = O.depth_refine(p, p.poses_gt, np.zeros(seg["M"]), 200, seg)
+    _, g, H = O.depth_terms(p, p.poses_gt, eta, seg)
+    assert np.abs(g[seg["active"]]).max() <= 1e-8 * np.abs(H).max()
+    assert trace[-1] < 1e-3 * trace[0]
+    # compare with the injected scales: log(|X_perturbed| / |X_true|) per segment
+    d_pert = np.linalg.norm(p.points[:, :3], axis=1)
+    d_true = np.linalg.norm(p0.points[:, :3], axis=1)
+    inj = np.log(d_pert / d_true)
+    e = seg["eff"]
+    err = [abs(eta[s] + inj[e == s].mean()) for s in np.nonzero(seg["active"])[0]]
+    assert np.median(err) < 2e-3 and max(err) < 2e-2
+
+
+def test_depth_step_clip_and_fixed_segments():
+    """A large range error moves its segment by exactly eta_max per step; segments of the
+    fixed keyframes and inactive segments stay at 0."""
+    p, lab, _ = _depth_case(sigma=0.0)
+    seg = O.depth_segments(p, lab)
+    pix_off = np.concatenate([[0], np.cumsum(p.pixels_of())])
+    k = 5
+    s0 = int(seg["base"][k]) + 3
+    pts = p.points.copy()
+    a = pix_off[k]
+    sel = seg["eff"][a:pix_off[k + 1]] == s0
+    pts[a:pix_off[k + 1]][sel, :3] *= np.exp(2.0)
+    import dataclasses
+    pb = dataclasses.replace(p, points=pts)
+    seg = O.depth_segments(pb, lab)
+    eta, _ = O.depth_refine(pb, pb.poses_gt, np.zeros(seg["M"]), 1, seg)
+    assert abs(eta[s0] + 0.5) < 1e-15
+    assert np.all(eta[seg["fixed"]] == 0) and np.all(eta[~seg["active"]] == 0)
+    assert len(seg["fixed"]) > 0
