@@ -239,6 +239,41 @@ def measure_gauge(C, torch, dev, reps: int = 10) -> dict:
                          "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes_per_launch": int(bytes_alg)}}
 
 
+def measure_depth(C, torch, prob, iters: int = 10) -> dict:
+    """Segment-level structure refinement (Sec. III-E) on the bench workload: 200 Voronoi
+    segments per keyframe, per-segment range errors exp(N(0, 0.05)), `iters` Jacobi steps
+    at the initial poses, mixed form.  The per-match pass is HBM-bound: 4 B per streamed
+    pixel plus, per valid match, the two pixels' 24-B records (ray and log-range, segment,
+    confidence)."""
+    import dataclasses
+    from synth.segments import perturb_segment_ranges, problem_labels
+    lab = problem_labels(prob, n_seg=200, seed=1)
+    pix_off = np.concatenate([[0], np.cumsum(prob.pixels_of())])
+    p = dataclasses.replace(prob, points=perturb_segment_ranges(prob.points, lab, pix_off, 0.05, seed=1))
+    g = C.Graph(p, mode=C.MIXED)
+    M = g.depth_setup(lab)
+    poses = torch.tensor(p.poses_init, dtype=torch.float64, device="cuda")
+    eta = torch.zeros(M, dtype=torch.float64, device="cuda")
+    g.depth_refine(poses, eta, 2)  # warm-up
+    eta.zero_()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    _, tr, match_ms = g.depth_refine(poses, eta, iters, timing=True)
+    ev1.record()
+    ev1.synchronize()
+    call_ms = ev0.elapsed_time(ev1)
+    g.close()
+    valid = p.valid_matches()
+    bytes_alg = 4 * int(p.pixels_of()[p.edge_i].sum()) + 48 * valid
+    peak, _ = measured_hbm_peak()
+    ach = bytes_alg / (match_ms / 1e3) / 1e9
+    return {"segments": M, "iters": iters, "cost_first": float(tr[0]), "cost_last": float(tr[-1]),
+            "call_ms": call_ms, "ms_per_iter": call_ms / (iters + 1), "match_ms": match_ms,
+            "roofline": {"kernel": "depth_match (mixed)", "bound": "hbm", "achieved": ach, "peak": peak,
+                         "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes_per_launch": int(bytes_alg)}}
+
+
 def oracle_sample(prob, n_edges: int, offset: int = 0):
     """Time the FP64 oracle on a bounded sample of one iteration and extrapolate.
 
@@ -439,6 +474,7 @@ def run_ours(args):
     # ---- cfg5: a 64-graph batch in one launch per step, per-graph latency; the long chain
     cfg5 = None if args.no_batch else measure_cfg5(C, torch, dev, args.batch_reps)
     gauge = None if args.no_batch else measure_gauge(C, torch, dev)
+    depth = measure_depth(C, torch, prob)
 
     clocks.stop()
     if rank != 0:
@@ -503,6 +539,7 @@ def run_ours(args):
         out["cfg5"] = cfg5
     if gauge is not None:
         out["gauge_sync"] = gauge
+    out["depth_refine"] = depth
     if cpu is not None:
         out["cpu_baseline"] = cpu
     print(json.dumps(out), flush=True)

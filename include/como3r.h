@@ -347,6 +347,52 @@ int como3r_gauge_sync(const como3r_gauge_desc* desc, void* cuda_stream, como3r_g
 int como3r_gauge_transport(double* poses, int32_t num_kf, const int32_t* which, const double* T,
                            int32_t num_candidates, void* cuda_stream);
 
+/* ---- Terminal segment-level structure refinement (Sec. III-E).
+ *
+ * One log-scale eta_g per segment: a pixel p of segment g moves along the ray of its
+ * snapshot point, X_p(eta_g) = |X_p,init| exp(eta_g) psi(X_p,init) (Eq. depth_parameter);
+ * with the poses fixed, E' = E_data + lambda_smooth E_bnd / 2 + lambda_prior E_prior / 2
+ * where E_data = sum over the graph's matches and c = 1..3 of
+ * rho(sqrt(q_mn) [T_ij X_j,n(eta) - X_i,m(eta)]_c / sigma_point) (Eq. depth_data, Huber of
+ * the graph's kappa), E_bnd = sum over 4-adjacent segment pairs of ((eta_g - eta_h) +
+ * Delta_gh)^2 and E_prior = sum eta_g^2 (Eq. depth_total; the halves follow from the
+ * printed H_prior = lambda_prior I).  Each iteration takes the Jacobi 1x1 damped Newton
+ * step delta_g = -g_g / ((1 + lambda_lm) H_gg), |delta_g| <= eta_max, with the full gradient
+ * and the diagonal of the normal matrix (cross terms dropped); segments of the graph's
+ * fixed keyframes do not move.
+ * Segments: a pixel belongs to segment (its keyframe's base + label) when its label is
+ * >= 0, its confidence >= c_min, its point finite with range > 1e-12, and the segment has
+ * >= min_pixels such pixels; otherwise it keeps its snapshot point.  Keyframe k's base =
+ * sum over earlier keyframes of (max label + 1); M = the total.  Delta_gh (g < h) is the
+ * mean over the 4-adjacent pixel pairs (p in g, p' in h) of log|X_p| - log|X_p'| of the
+ * snapshot. */
+typedef struct {
+  const int32_t* labels;        /* [sum P_k] host or device: segment of each pixel within its keyframe, or -1 */
+  double c_min;                 /* 1.5 */
+  int32_t min_pixels;           /* 16 */
+  double sigma_point;           /* 0.05 */
+  double lambda_smooth;         /* 1 */
+  double lambda_prior;          /* 1 */
+  double lambda_lm;             /* 0.05 */
+  double eta_max;               /* 0.5 */
+} como3r_depth_desc;
+
+/* Snapshots the graph's current pointmaps (the pristine reference rays and ranges),
+ * builds the segments and boundary pairs on the host and uploads them; replaces an earlier
+ * setup.  *num_segments (nullable) receives M.  Synchronises.  Errors: INVALID_ARG, OOM,
+ * CUDA. */
+int como3r_depth_setup(como3r_graph_t graph, const como3r_depth_desc* desc, int64_t* num_segments);
+
+/* Up to `iters` (>= 0) Jacobi steps at fixed poses.  poses [N][8] host or device;
+ * eta [M] host or device, in/out (start and result); cost_trace host [iters + 1] or NULL
+ * (E' before each step and at the result); points_out device or NULL: the refined
+ * pointmaps in the graph's storage type and layout (pixels without a segment keep the
+ * snapshot point; confidences copied) -- e.g. for the next pose pass via
+ * como3r_update_inputs.  match_ms host or NULL: mean duration of the per-match pass
+ * (CUDA events).  Synchronises.  Errors: INVALID_ARG (no setup), CUDA. */
+int como3r_depth_refine(como3r_graph_t graph, const double* poses, double* eta, int32_t iters,
+                        double* cost_trace, void* points_out, float* match_ms);
+
 /* Human-readable text of a status code. */
 const char* como3r_status_str(int code);
 

@@ -54,6 +54,16 @@ class GraphInfo(ctypes.Structure):
                 ("valid_matches", ctypes.c_int64), ("skipped_matches", ctypes.c_int64)]
 
 
+class DepthDesc(ctypes.Structure):
+    _fields_ = [("labels", ctypes.c_void_p), ("c_min", ctypes.c_double), ("min_pixels", ctypes.c_int32),
+                ("sigma_point", ctypes.c_double), ("lambda_smooth", ctypes.c_double),
+                ("lambda_prior", ctypes.c_double), ("lambda_lm", ctypes.c_double), ("eta_max", ctypes.c_double)]
+
+
+DEPTH_DEFAULTS = dict(c_min=1.5, min_pixels=16, sigma_point=0.05, lambda_smooth=1.0, lambda_prior=1.0,
+                      lambda_lm=0.05, eta_max=0.5)
+
+
 class GaugeDesc(ctypes.Structure):
     _fields_ = [
         ("num_candidates", ctypes.c_int32), ("num_kf", ctypes.c_int32), ("pix_off", ctypes.POINTER(ctypes.c_int64)),
@@ -97,6 +107,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.como3r_gauge_sync.argtypes = [ctypes.POINTER(GaugeDesc), vp, ctypes.POINTER(GaugeResult),
                                       ctypes.POINTER(ctypes.c_float)]
     lib.como3r_gauge_transport.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_int32, vp]
+    lib.como3r_depth_setup.argtypes = [vp, ctypes.POINTER(DepthDesc), _i64p]
+    lib.como3r_depth_refine.argtypes = [vp, vp, vp, ctypes.c_int32, _f64p, vp, ctypes.POINTER(ctypes.c_float)]
     lib.como3r_status_str.argtypes = [ctypes.c_int]
     lib.como3r_status_str.restype = ctypes.c_char_p
     lib.como3r_last_error.argtypes = []
@@ -203,6 +215,7 @@ class Graph:
             match_idx = torch.from_numpy(np.ascontiguousarray(prob.match_idx.astype(np.int32)))
             match_idx = match_idx.pin_memory() if copy_inputs else match_idx.to(device)
         self.points, self.match_idx = points, match_idx
+        self.copy_inputs = bool(copy_inputs)
         self._stream = _torch_stream(stream)
         d = _build_desc(prob, _ptr(points), _ptr(match_idx), mode, copy_inputs, self._keep)
         h = ctypes.c_void_p()
@@ -239,6 +252,33 @@ class Graph:
         st = _check(lib().como3r_solve(self.handle, _ptr(poses), int(iters),
                                        tr.ctypes.data_as(_f64p) if trace else None, info), "solve")
         return st, (tr.reshape(iters + 1, self.G) if trace else None), [_info_dict(x) for x in info]
+
+    def depth_setup(self, labels, **params) -> int:
+        """como3r_depth_setup: snapshot the current pointmaps, build the segments from the
+        per-pixel labels (host or device int32, concatenated like the pixels); returns M."""
+        pr = dict(DEPTH_DEFAULTS)
+        pr.update(params)
+        if not hasattr(labels, "data_ptr"):
+            labels = np.ascontiguousarray(np.asarray(labels, dtype=np.int32))
+        self._depth_labels = labels
+        d = DepthDesc(labels=_ptr(labels), c_min=float(pr["c_min"]), min_pixels=int(pr["min_pixels"]),
+                      sigma_point=float(pr["sigma_point"]), lambda_smooth=float(pr["lambda_smooth"]),
+                      lambda_prior=float(pr["lambda_prior"]), lambda_lm=float(pr["lambda_lm"]),
+                      eta_max=float(pr["eta_max"]))
+        M = np.zeros(1, dtype=np.int64)
+        _check(lib().como3r_depth_setup(self.handle, ctypes.byref(d), M.ctypes.data_as(_i64p)), "depth_setup")
+        return int(M[0])
+
+    def depth_refine(self, poses, eta, iters: int, points_out=None, timing: bool = False):
+        """como3r_depth_refine: `iters` Jacobi steps from eta (host float64 array or CUDA
+        tensor, updated in place); returns (eta, cost trace [iters + 1]) and the mean
+        per-match pass time in ms when `timing`."""
+        tr = np.zeros(iters + 1)
+        ms = ctypes.c_float(0.0)
+        _check(lib().como3r_depth_refine(self.handle, _ptr(poses), _ptr(eta), int(iters),
+                                         tr.ctypes.data_as(_f64p), _ptr(points_out),
+                                         ctypes.byref(ms) if timing else None), "depth_refine")
+        return (eta, tr, float(ms.value)) if timing else (eta, tr)
 
     def timestamps(self):
         """como3r_solve_timestamps: (start_ns, done_ns[G]) of the last gn_step / solve."""
@@ -413,4 +453,26 @@ def gauge_transport(poses, which, T, stream=None):
     """como3r_gauge_transport: poses[k] <- T[which[k]] poses[k] for which[k] >= 0 (CUDA tensors)."""
     _check(lib().como3r_gauge_transport(_ptr(poses), int(poses.shape[0]), _ptr(which), _ptr(T), int(T.shape[0]),
                                         _torch_stream(stream)), "gauge_transport")
+
+
+def terminal_refine(graph: "Graph", poses, labels, rounds: int = 3, depth_iters: int = 10, pose_iters: int = 50,
+                    **params):
+    """Terminal schedule (Sec. III-E): `rounds` times, up to `depth_iters` Jacobi structure
+    steps at fixed poses (como3r_depth_refine, eta carried over), then a pose pass of
+    `pose_iters` Gauss-Newton iterations (como3r_solve) on the refined pointmaps.  The
+    segments are built from the graph's pointmaps at the call (the pristine snapshot).
+    Returns (poses [N][8] as a numpy array, eta [M])."""
+    import torch
+    M = graph.depth_setup(labels, **params)
+    eta = np.zeros(M)
+    work = torch.tensor(np.asarray(poses, dtype=np.float64), device="cuda")
+    buf = torch.empty(graph.points.shape, dtype=graph.points.dtype, device="cuda")
+    for _ in range(rounds):
+        eta, _ = graph.depth_refine(work, eta, depth_iters, points_out=buf)
+        if graph.copy_inputs:
+            graph.update_inputs(points=buf)
+        else:
+            graph.points.copy_(buf)
+        graph.solve(work, pose_iters, trace=False)
+    return work.cpu().numpy(), eta
 

@@ -87,6 +87,7 @@ struct como3r_graph {
   uint8_t* d_frozen = nullptr;
   GraphInfoDev* d_ginfo = nullptr;
   long long* d_start_ns = nullptr;  // device clock at the start of the last gn_step / solve
+  DepthState* depth = nullptr;      // segment-level structure refinement (como3r_depth_setup)
   int *d_iter = nullptr, *d_warn = nullptr;
   double* d_cost_hist = nullptr;
   int64_t cost_hist_cap = 0;
@@ -135,6 +136,8 @@ int upload(como3r_graph* g, T** p, const std::vector<T>& v) {
 }
 
 void free_all(como3r_graph* g) {
+  depth_free(g->depth);
+  g->depth = nullptr;
   if (g->iter_exec) cudaGraphExecDestroy(g->iter_exec);
   if (g->eval_exec) cudaGraphExecDestroy(g->eval_exec);
   for (void* p : g->allocs) cudaFree(p);
@@ -579,6 +582,31 @@ int como3r_solve_timestamps(como3r_graph_t g, int64_t* start_ns, int64_t* done_n
   if (done_ns)
     for (int k = 0; k < G; ++k) done_ns[k] = g->h_ginfo[k].done_ns;
   return COMO3R_OK;
+}
+
+int como3r_depth_setup(como3r_graph_t g, const como3r_depth_desc* d, int64_t* num_segments) {
+  if (!g || !d || !d->labels) return set_error(COMO3R_ERR_INVALID_ARG, "graph, desc and desc->labels must be non-NULL");
+  if (!(d->sigma_point > 0) || !(d->lambda_smooth >= 0) || !(d->lambda_prior >= 0) || !(d->lambda_lm >= 0) ||
+      !(d->eta_max > 0) || d->min_pixels < 1 || !(d->c_min == d->c_min))
+    return set_error(COMO3R_ERR_INVALID_ARG, "depth parameters out of range");
+  depth_free(g->depth);
+  g->depth = nullptr;
+  return depth_setup(g->plan, g->points, g->plan.dtype, g->plan.mode, d->labels, d, g->stream, &g->depth,
+                     num_segments);
+}
+
+int como3r_depth_refine(como3r_graph_t g, const double* poses, double* eta, int32_t iters, double* cost_trace,
+                        void* points_out, float* match_ms) {
+  if (!g) return set_error(COMO3R_ERR_INVALID_ARG, "graph handle is NULL");
+  if (!g->depth) return set_error(COMO3R_ERR_INVALID_ARG, "como3r_depth_setup was not called");
+  if (iters < 0 || !eta) return set_error(COMO3R_ERR_INVALID_ARG, "iters must be >= 0 and eta non-NULL");
+  int rc = begin_call(g, poses);
+  if (rc) return rc;
+  const HostPlan& p = g->plan;
+  CK(launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, g->stream), "edge_prep");
+  g->last_launches = 1 + 2 * ((int64_t)iters + 1) + (points_out ? 1 : 0);
+  return depth_run(g->depth, p, g->d_items, g->num_items, g->d_es, g->midx, g->d_T64, g->d_T32, g->rp.kappa, g->sms,
+                   eta, iters, cost_trace, points_out, g->points, match_ms, g->stream);
 }
 
 int como3r_linearize(como3r_graph_t g, const double* poses, double* edge_out, double* cost_out) {

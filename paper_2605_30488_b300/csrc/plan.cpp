@@ -231,6 +231,7 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
   if (!d->points_conf) return fail("points_conf is NULL");
   if (E > 0 && !d->match_idx) return fail("match_idx is NULL");
   if (E >= (1 << 29)) return fail("too many edges");
+  p.width.assign(d->width, d->width + G);
   p.npix.resize(N);
   p.pix_off.assign(N + 1, 0);
   for (int g = 0; g < G; ++g)

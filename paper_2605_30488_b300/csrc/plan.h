@@ -15,6 +15,7 @@ struct HostPlan {
   int mode = 1, dtype = 1;
   int64_t total_px = 0, total_idx = 0, valid_hint = 0;
   std::vector<int32_t> kf_offset, edge_offset, anchor;
+  std::vector<int32_t> width;     // [G] pointmap width of each graph
   std::vector<int64_t> pix_off;   // [N+1]
   std::vector<int32_t> npix;      // [N]
   std::vector<EdgeStatic> es;     // [E]
@@ -57,5 +58,16 @@ void build_items(const HostPlan& p, int chunk, std::vector<Item>& items, std::ve
 
 // Fills the COMO3R_STAT_* entries that depend on the plan only.
 void plan_stats(const HostPlan& p, int64_t* stats);
+
+// Segment-level structure refinement state (k_depth.cu): built by depth_setup from the
+// graph's current pointmaps, run by depth_run, released by depth_free.
+struct DepthState;
+int depth_setup(const HostPlan& p, const void* points, int dtype, int mode, const int32_t* labels,
+                const como3r_depth_desc* d, cudaStream_t s, DepthState** out, int64_t* num_segments);
+int depth_run(DepthState* st, const HostPlan& p, const Item* items, int num_items, const EdgeStatic* es,
+              const int32_t* midx, const double* T64, const float* T32, double kappa, int sms, double* eta,
+              int iters, double* cost_trace, void* points_out, const void* points_src, float* match_ms,
+              cudaStream_t s);
+void depth_free(DepthState* st);
 
 }  // namespace como3r

@@ -15,22 +15,30 @@ import numpy as np
 
 
 def voronoi_labels(H: int, W: int, n_seg: int, rng) -> np.ndarray:
-    """int32 [H*W] labels of ~n_seg compact cells (nearest jittered grid seed)."""
+    """int32 [H*W] labels of ~n_seg compact cells: the nearest of a grid of seeds, each
+    jittered by up to 0.3 of its cell (so the nearest seed of a pixel is always one of
+    the 3 x 3 cells around the pixel's own cell, the only ones compared)."""
     gy = max(1, int(round(math.sqrt(n_seg * H / W))))
     gx = max(1, int(round(n_seg / gy)))
-    cy = (np.arange(gy) + 0.5) * H / gy
-    cx = (np.arange(gx) + 0.5) * W / gx
-    sy = (cy[:, None] + rng.uniform(-0.3, 0.3, size=(gy, gx)) * H / gy).ravel()
-    sx = (cx[None, :] + rng.uniform(-0.3, 0.3, size=(gy, gx)) * W / gx).ravel()
+    ch, cw = H / gy, W / gx
+    sy = (np.arange(gy)[:, None] + 0.5 + rng.uniform(-0.3, 0.3, size=(gy, gx))) * ch
+    sx = (np.arange(gx)[None, :] + 0.5 + rng.uniform(-0.3, 0.3, size=(gy, gx))) * cw
     yy, xx = np.mgrid[0:H, 0:W]
-    lab = np.zeros((H, W), dtype=np.int32)
+    cy = np.minimum((yy / ch).astype(np.int64), gy - 1)
+    cx = np.minimum((xx / cw).astype(np.int64), gx - 1)
     best = np.full((H, W), np.inf)
-    for s in range(sy.size):
-        d = (yy - sy[s]) ** 2 + (xx - sx[s]) ** 2
-        upd = d < best
-        best[upd] = d[upd]
-        lab[upd] = s
-    return lab.ravel()
+    lab = np.zeros((H, W), dtype=np.int64)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            ny, nx = cy + dy, cx + dx
+            ok = (ny >= 0) & (ny < gy) & (nx >= 0) & (nx < gx)
+            nyc, nxc = np.clip(ny, 0, gy - 1), np.clip(nx, 0, gx - 1)
+            d = (yy + 0.5 - sy[nyc, nxc]) ** 2 + (xx + 0.5 - sx[nyc, nxc]) ** 2
+            d = np.where(ok, d, np.inf)
+            upd = d < best
+            best[upd] = d[upd]
+            lab[upd] = (nyc * gx + nxc)[upd]
+    return lab.ravel().astype(np.int32)
 
 
 def problem_labels(prob, n_seg: int = 200, seed: int = 0) -> np.ndarray:
