@@ -53,9 +53,9 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-sample-edges", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["all", "mixed", "gauge"], default="all",
-                    help="mixed: time only the resident mixed form; gauge: only the gauge synchronisation "
-                         "(profiling runs)")
+    ap.add_argument("--only", choices=["all", "mixed", "gauge", "depth"], default="all",
+                    help="mixed: time only the resident mixed form; gauge / depth: only the gauge "
+                         "synchronisation / the structure refinement (profiling runs)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-graph batch and the 2,000-keyframe chain (per-graph latency)")
     ap.add_argument("--batch-reps", type=int, default=3)
@@ -366,6 +366,11 @@ def run_ours(args):
             print(json.dumps({"gauge_sync": gauge, "note": "profiling run (--only gauge)"}), flush=True)
         return
     prob = make_workload(args.workload, seed=args.seed)
+    if args.only == "depth":
+        if rank == 0:
+            print(json.dumps({"depth_refine": measure_depth(C, torch, prob), "note": "profiling run (--only depth)"}),
+                  flush=True)
+        return
     iters = prob.iters
     dev = torch.device("cuda", local_rank)
     props = torch.cuda.get_device_properties(dev)

@@ -51,6 +51,21 @@ struct GraphInfoDev {          // per graph, written on the device
 };
 
 #ifdef __CUDACC__
+// FP32 -> FP64 on the integer ALU (exact for normal numbers and zero; FP32 denormals flush
+// to signed zero; inf / NaN keep their class).  On this GPU a warp's FP64-pipe
+// instruction -- a conversion included -- takes the pipe for a whole warp's time however
+// few lanes are active, so widening in a hot FP32 loop goes through the ALU instead.
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+  const unsigned ex = (u >> 23) & 0xffu, man = u & 0x7fffffu;
+  unsigned long long bits;
+  if (ex == 0u) bits = sgn;
+  else if (ex == 0xffu) bits = sgn | (0x7ffull << 52) | ((unsigned long long)man << 29);
+  else bits = sgn | ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)man << 29);
+  return __longlong_as_double((long long)bits);
+}
+
 // Device clock (ns): %globaltimer, the same time base on every SM.
 __device__ __forceinline__ long long globaltimer_ns() {
   long long t;

@@ -57,8 +57,8 @@ struct AlignCand {
 struct AlignItem {
   int32_t cand, dir, begin, end;
 };
-struct AlignRecord {   // per item
-  double v[kSums];
+struct AlignRecord {   // per item: sums as (value, compensation) pairs, added in FP64 by the finish
+  double v[kSums], c[kSums];
   long long n_valid, n_conf;
 };
 
@@ -82,11 +82,14 @@ __device__ __forceinline__ void load_point(const void* __restrict__ base, int64_
 // c_a c_b >= q2 decided exactly.  FP32 operands (FP16 / FP32 storage): the rounded FP32
 // product is within a relative 2^-24 of the exact one, so outside a +-2^-21 band around
 // q2 its comparison is the exact one; inside, the exact FP64 product decides.
+// The exact check stays out of line: if-converted into every lane, its FP64 multiply and
+// conversions would occupy B300's narrow FP64 pipe on every match.
+__device__ __noinline__ bool high_conf_exact(float ca, float cb, double q2) { return (double)ca * (double)cb >= q2; }
 __device__ __forceinline__ bool high_conf(float ca, float cb, double q2, float q2f) {
   const float p = ca * cb;
   if (p > q2f * (1.f + 0x1p-21f)) return true;
   if (p < q2f * (1.f - 0x1p-21f)) return false;
-  return (double)ca * (double)cb >= q2;
+  return high_conf_exact(ca, cb, q2);
 }
 __device__ __forceinline__ bool high_conf(double ca, double cb, double q2, float) { return ca * cb >= q2; }
 
@@ -111,8 +114,9 @@ __device__ __forceinline__ float two_sum_f(float a, float b, float& err) {
   return s;
 }
 
-// Warp total of (s + c) over the lanes, as a double (TwoSum butterfly in FP32).
-__device__ __forceinline__ double warp_total(float s, float c) {
+// Warp total of (s + c) over the lanes as a (value, compensation) pair (TwoSum butterfly
+// in FP32, both widened on the ALU: no FP64-pipe instruction in the pass).
+__device__ __forceinline__ void warp_total(float s, float c, double& hi, double& lo) {
   float comp = c;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -122,12 +126,14 @@ __device__ __forceinline__ double warp_total(float s, float c) {
     s = two_sum_f(s, rs, err);
     comp = comp + rc + err;
   }
-  return (double)s + (double)comp;
+  hi = widen_f32(s);
+  lo = widen_f32(comp);
 }
-__device__ __forceinline__ double warp_total(double s, double) {
+__device__ __forceinline__ void warp_total(double s, double, double& hi, double& lo) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  return s;
+  hi = s;
+  lo = 0.0;
 }
 
 // U pixels per lane in flight: index loads, then every pixel load, then the sums.
@@ -195,11 +201,16 @@ __global__ void __launch_bounds__(kAlignThreads, 2) align_reduce_kernel(
     if (item.dir == 0) {
 #pragma unroll
       for (int k = 0; k < kSums; ++k) {
-        const double tot = warp_total(s[k], -c[k]);  // a lane's Kahan total is s - c
-        if (lane == k) r->v[k] = tot;
+        double hi, lo;
+        warp_total(s[k], -c[k], hi, lo);  // a lane's Kahan total is s - c
+        if (lane == k) {
+          r->v[k] = hi;
+          r->c[k] = lo;
+        }
       }
     } else if (lane < kSums) {
       r->v[lane] = 0.0;
+      r->c[lane] = 0.0;
     }
     const int tv = __reduce_add_sync(0xffffffffu, n_valid);
     const int tc = __reduce_add_sync(0xffffffffu, n_conf);
@@ -314,7 +325,7 @@ __global__ void align_finish_kernel(const AlignCand* __restrict__ cands, int C, 
     const AlignRecord& r = rec[it];
     const int dir = it < cd.item0 + (cd.dir[0].na + kAlignItem - 1) / kAlignItem ? 0 : 1;
     if (dir == 0)
-      for (int k = 0; k < kSums; ++k) S[k] += r.v[k];
+      for (int k = 0; k < kSums; ++k) S[k] += r.v[k] + r.c[k];
     nv[dir] += r.n_valid;
     nc[dir] += r.n_conf;
   }

@@ -18,7 +18,8 @@
 //     long) and the run's head adds them with one FP64 atomic each;
 //   depth_update_kernel (one thread per segment, FP64): boundary and prior terms, the
 //     damped clipped step into the other eta buffer (Jacobi: every step reads the same eta).
-// MIXED does the per-match arithmetic in FP32, PLAIN_FP64 in FP64; accumulators are FP64.
+// MIXED does the per-match arithmetic in FP32 (hardware exp / reciprocal square root /
+// reciprocal approximations), PLAIN_FP64 in FP64; accumulators are FP64.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -62,10 +63,44 @@ __device__ __forceinline__ void run_sums(int key, R& a, R& b, int lane, bool& he
   }
 }
 
-template <typename R>
-__device__ __forceinline__ R huber_w(R r, R kappa) {
-  const R a = fabs(r);
-  return a <= kappa ? R(1) : kappa / a;
+// A run head's FP64 atomics (executed in L2); FP32 values are widened on the ALU, so the
+// SM's FP64 pipe stays free.
+__device__ __forceinline__ void seg_add(double* __restrict__ gsum, double* __restrict__ hsum, int k, float a,
+                                        float b) {
+  atomicAdd(gsum + k, widen_f32(a));
+  atomicAdd(hsum + k, widen_f32(b));
+}
+__device__ __forceinline__ void seg_add(double* __restrict__ gsum, double* __restrict__ hsum, int k, double a,
+                                        double b) {
+  atomicAdd(gsum + k, a);
+  atomicAdd(hsum + k, b);
+}
+
+// FP32: hardware approximations (relative error ~2^-22, far inside the mixed form's 1e-5);
+// FP64: the exact functions.
+__device__ __forceinline__ float rsq_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float exp_m(float x) { return __expf(x); }
+__device__ __forceinline__ double exp_m(double x) { return exp(x); }
+// c^(1/4) of c >= 0 (0 -> 0)
+__device__ __forceinline__ float qroot(float c) {
+  if (!(c > 0.f)) return 0.f;
+  const float s = c * rsq_approx(c);
+  return s * rsq_approx(s);
+}
+__device__ __forceinline__ double qroot(double c) { return sqrt(sqrt(c)); }
+__device__ __forceinline__ float huber_w(float r, float kappa) { return fminf(1.f, kappa * rcp_approx(fabsf(r))); }
+__device__ __forceinline__ double huber_w(double r, double kappa) {
+  const double a = fabs(r);
+  return a <= kappa ? 1.0 : kappa / a;
 }
 template <typename R>
 __device__ __forceinline__ R huber_rho(R r, R kappa) {
@@ -78,7 +113,7 @@ __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
     const typename Rec<R>::T* __restrict__ rec, const int32_t* __restrict__ seg, const R* __restrict__ conf,
     const int32_t* __restrict__ midx, const Item* __restrict__ items, int num_items,
     const EdgeStatic* __restrict__ es, const double* __restrict__ T64, const float* __restrict__ T32,
-    const double* __restrict__ eta, double kscale, double kappa_d, double* __restrict__ gsum,
+    const R* __restrict__ eta, double kscale, double kappa_d, double* __restrict__ gsum,
     double* __restrict__ hsum, double* __restrict__ cost) {
   const int lane = threadIdx.x & 31;
   const int w0 = (blockIdx.x * kDepthThreads + threadIdx.x) >> 5;
@@ -125,9 +160,9 @@ __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
         R gi = R(0), hi = R(0), gj = R(0), hj = R(0);
         int ki = -1, kj = -1;
         if (nn[u] >= 0) {  // every valid match adds to the objective; sides with a segment to (g, H)
-          const R ei = si[u] >= 0 ? (R)__ldg(eta + si[u]) : R(0);
-          const R ej = sj[u] >= 0 ? (R)__ldg(eta + sj[u]) : R(0);
-          const R di = exp(ri[u].w + ei), dj = exp(rj[u].w + ej);
+          const R ei = si[u] >= 0 ? __ldg(eta + si[u]) : R(0);  // FP32 copy in the mixed form
+          const R ej = sj[u] >= 0 ? __ldg(eta + sj[u]) : R(0);
+          const R di = exp_m(ri[u].w + ei), dj = exp_m(rj[u].w + ej);
           const R xi0 = di * ri[u].x, xi1 = di * ri[u].y, xi2 = di * ri[u].z;
           const R xj0 = dj * rj[u].x, xj1 = dj * rj[u].y, xj2 = dj * rj[u].z;
           const R a0 = fma(T[0], xj0, fma(T[1], xj1, T[2] * xj2));  // s R X_j
@@ -139,7 +174,7 @@ __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
           const bool ok = isfinite(nx2) && isfinite(ny2) && isfinite(cc) && nx2 > R(1e-24) && ny2 > R(1e-24) &&
                           cc >= R(0);
           if (ok) {
-            const R k = sqrt(sqrt(cc)) * ks;
+            const R k = qroot(cc) * ks;
             const R r0 = k * (y0 - xi0), r1 = k * (y1 - xi1), r2 = k * (y2 - xi2);
             const R w0 = huber_w(r0, kappa), w1 = huber_w(r1, kappa), w2 = huber_w(r2, kappa);
             item_cost += huber_rho(r0, kappa) + huber_rho(r1, kappa) + huber_rho(r2, kappa);
@@ -160,18 +195,13 @@ __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
         }
         bool head;
         run_sums(ki, gi, hi, lane, head);
-        if (head && ki >= 0) {
-          atomicAdd(gsum + ki, (double)gi);
-          atomicAdd(hsum + ki, (double)hi);
-        }
+        if (head && ki >= 0) seg_add(gsum, hsum, ki, gi, hi);
         run_sums(kj, gj, hj, lane, head);
-        if (head && kj >= 0) {
-          atomicAdd(gsum + kj, (double)gj);
-          atomicAdd(hsum + kj, (double)hj);
-        }
+        if (head && kj >= 0) seg_add(gsum, hsum, kj, gj, hj);
       }
     }
-    lane_cost += (double)item_cost;
+    if constexpr (sizeof(R) == 4) lane_cost += widen_f32(item_cost);
+    else lane_cost += item_cost;
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) lane_cost += __shfl_xor_sync(0xffffffffu, lane_cost, off);
@@ -184,7 +214,8 @@ __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
 __global__ void depth_update_kernel(int M, const uint8_t* __restrict__ movable, const uint8_t* __restrict__ active,
                                     const int32_t* __restrict__ poff, const int32_t* __restrict__ pother,
                                     const double* __restrict__ pdelta, const double* __restrict__ eta_in,
-                                    double* __restrict__ eta_out, double* __restrict__ gsum,
+                                    double* __restrict__ eta_out, float* __restrict__ eta32_out,
+                                    double* __restrict__ gsum,
                                     double* __restrict__ hsum, double lambda_smooth, double lambda_prior,
                                     double lambda_lm, double eta_max, int apply, double* __restrict__ cost) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -206,9 +237,15 @@ __global__ void depth_update_kernel(int M, const uint8_t* __restrict__ movable, 
   double step = 0.0;
   if (apply && movable[s] && h > 0.0) step = fmin(eta_max, fmax(-eta_max, -g / ((1.0 + lambda_lm) * h)));
   eta_out[s] = es + step;
+  if (eta32_out) eta32_out[s] = (float)(es + step);
   gsum[s] = 0.0;
   hsum[s] = 0.0;
   if (e != 0.0) atomicAdd(cost, e);
+}
+
+__global__ void eta_to_float_kernel(const double* __restrict__ a, float* __restrict__ b, int M) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < M) b[s] = (float)a[s];
 }
 
 // Refined pointmap in the graph's storage type: X = exp(logd + eta) psi for pixels of a
@@ -278,6 +315,7 @@ struct DepthState {
   int32_t* pother = nullptr;  // [2 n_pairs]
   double* pdelta = nullptr;   // [2 n_pairs] Delta oriented from the list's segment
   double *eta[2] = {nullptr, nullptr}, *gsum = nullptr, *hsum = nullptr, *cost = nullptr;
+  float* eta32[2] = {nullptr, nullptr};  // FP32 copies read by the mixed-form match pass
   double sigma_point = 0.05, lambda_smooth = 1.0, lambda_prior = 1.0, lambda_lm = 0.05, eta_max = 0.5;
   std::vector<void*> allocs;
 };
@@ -426,6 +464,7 @@ int depth_setup(const HostPlan& p, const void* points, int dtype, int mode, cons
       (e = dmalloc(st, &st->active, (size_t)M)) || (e = dmalloc(st, &st->poff, (size_t)M + 1)) ||
       (e = dmalloc(st, &st->pother, pother.size())) || (e = dmalloc(st, &st->pdelta, pdelta.size())) ||
       (e = dmalloc(st, &st->eta[0], (size_t)M)) || (e = dmalloc(st, &st->eta[1], (size_t)M)) ||
+      (e = dmalloc(st, &st->eta32[0], (size_t)M)) || (e = dmalloc(st, &st->eta32[1], (size_t)M)) ||
       (e = dmalloc(st, &st->gsum, (size_t)M)) || (e = dmalloc(st, &st->hsum, (size_t)M)) ||
       (e = dmalloc(st, &st->cost, 1))) {
     depth_free(st);
@@ -462,6 +501,10 @@ int depth_run(DepthState* st, const HostPlan& p, const Item* items, int num_item
   const int M = st->M;
   cudaError_t e = cudaSuccess;
   if (M) e = cudaMemcpyAsync(st->eta[0], eta_io, sizeof(double) * M, cudaMemcpyDefault, s);
+  if (!e && M) {
+    eta_to_float_kernel<<<(M + 255) / 256, 256, 0, s>>>(st->eta[0], st->eta32[0], M);
+    e = cudaGetLastError();
+  }
   const int grid = std::max(1, std::min(sms * 2, (num_items + 7) / 8));
   const double kscale = 1.0 / st->sigma_point;
   std::vector<double> trace((size_t)iters + 1, 0.0);
@@ -477,7 +520,7 @@ int depth_run(DepthState* st, const HostPlan& p, const Item* items, int num_item
       if (st->mode == COMO3R_MIXED)
         depth_match_kernel<float><<<grid, kDepthThreads, 0, s>>>(
             static_cast<const float4*>(st->rec), st->seg, static_cast<const float*>(st->conf), midx, items,
-            num_items, es, T64, T32, st->eta[cur], kscale, kappa, st->gsum, st->hsum, st->cost);
+            num_items, es, T64, T32, st->eta32[cur], kscale, kappa, st->gsum, st->hsum, st->cost);
       else
         depth_match_kernel<double><<<grid, kDepthThreads, 0, s>>>(
             static_cast<const double4*>(st->rec), st->seg, static_cast<const double*>(st->conf), midx, items,
@@ -488,7 +531,9 @@ int depth_run(DepthState* st, const HostPlan& p, const Item* items, int num_item
     // the last pass only evaluates the objective at the final eta
     if (!e && M)
       depth_update_kernel<<<(M + 127) / 128, 128, 0, s>>>(M, st->movable, st->active, st->poff, st->pother,
-                                                           st->pdelta, st->eta[cur], st->eta[cur ^ 1], st->gsum,
+                                                           st->pdelta, st->eta[cur], st->eta[cur ^ 1],
+                                                           st->mode == COMO3R_MIXED ? st->eta32[cur ^ 1] : nullptr,
+                                                           st->gsum,
                                                            st->hsum, st->lambda_smooth, st->lambda_prior,
                                                            st->lambda_lm, st->eta_max, k < iters ? 1 : 0, st->cost);
     if (!e) e = cudaGetLastError();
