@@ -86,9 +86,18 @@ def algorithmic_bytes(prob) -> int:
 def k1_traffic_from_profile():
     """DRAM bytes per K1 launch from the committed ncu summary, if it was taken on the
     current K1 source (sha256 recorded in the summary); else None."""
+    return traffic_from_profile(PROFILE, K1_SOURCE)
+
+
+def traffic_from_profile(summary: str, source: str):
+    """DRAM bytes per launch from a committed ncu summary (path under profiles/ or
+    absolute), if it was taken on the kernel's current source file (sha256 recorded in the
+    summary; path under the package's csrc/ or absolute); else None."""
+    summary = summary if os.path.isabs(summary) else os.path.join(ROOT, "profiles", summary)
+    source = source if os.path.isabs(source) else os.path.join(ROOT, "paper_2605_30488_b300", "csrc", source)
     try:
-        txt = open(PROFILE).read()
-        src = hashlib.sha256(open(K1_SOURCE, "rb").read()).hexdigest()
+        txt = open(summary).read()
+        src = hashlib.sha256(open(source, "rb").read()).hexdigest()
         fields = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l)
         if fields.get("source_sha256", "").strip() != src:
             return None
@@ -236,7 +245,8 @@ def measure_gauge(C, torch, dev, reps: int = 10) -> dict:
             "admitted": int(sum(r["admitted"] for r in res)), "fallbacks": int(sum(r["fallback"] > 0 for r in res)),
             "call_ms": statistics.median(calls), "kernel_ms": k_ms,
             "roofline": {"kernel": "align_reduce (mixed)", "bound": "hbm", "achieved": ach, "peak": peak,
-                         "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes_per_launch": int(bytes_alg)}}
+                         "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes_per_launch": int(bytes_alg),
+                         "traffic": traffic_from_profile("align_reduce_gauge60_512x384.txt", "k_align.cu")}}
 
 
 def measure_depth(C, torch, prob, iters: int = 10) -> dict:
@@ -271,7 +281,8 @@ def measure_depth(C, torch, prob, iters: int = 10) -> dict:
     return {"segments": M, "iters": iters, "cost_first": float(tr[0]), "cost_last": float(tr[-1]),
             "call_ms": call_ms, "ms_per_iter": call_ms / (iters + 1), "match_ms": match_ms,
             "roofline": {"kernel": "depth_match (mixed)", "bound": "hbm", "achieved": ach, "peak": peak,
-                         "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes_per_launch": int(bytes_alg)}}
+                         "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes_per_launch": int(bytes_alg),
+                         "traffic": traffic_from_profile("depth_match_two_agent_40kf_512x384.txt", "k_depth.cu")}}
 
 
 def oracle_sample(prob, n_edges: int, offset: int = 0):
