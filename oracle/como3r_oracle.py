@@ -700,6 +700,85 @@ def depth_refine(prob, poses: np.ndarray, eta0: np.ndarray, iters: int, seg: dic
     return eta, np.array(trace)
 
 
+# ================== front-end: projective ray matching and fusion (Sec. III-A)
+# Matching minimises the angular discrepancy on the frame's predicted ray image,
+# p* = argmin_p |psi([X^f_f]_p) - psi(x)|^2, for every queried point x.  Reading (the paper
+# cites its iterative solver without printing it): a deterministic descent over pixels --
+# from a start pixel, move to the best of the 8 neighbours (fixed order, strictly smaller
+# distance, first in order on ties) while it improves, at most max_steps moves -- with
+# every distance in FP32, each operation correctly rounded in this order:
+#   n = sqrt((x0*x0 + x1*x1) + x2*x2), psi = (x0/n, x1/n, x2/n),
+#   d = ((a0-b0)*(a0-b0) + (a1-b1)*(a1-b1)) + (a2-b2)*(a2-b2),
+# so that the integer result is the same on any IEEE implementation.  A query whose
+# point is not finite or has zero norm, or whose final distance exceeds d_max (the
+# squared chord of max_angle: 2 - 2 cos(max_angle), rounded to FP32), gets -1.  Frame
+# pixels whose ray is not finite are never entered.
+_NB8 = ((-1, -1), (-1, 0), (-1, 1), (0, -1), (0, 1), (1, -1), (1, 0), (1, 1))
+
+
+def ray_image_f32(P: np.ndarray) -> np.ndarray:
+    """psi of every point in FP32 with the fixed operation order (NaN for a zero or
+    non-finite point)."""
+    x = np.asarray(P[:, :3], dtype=np.float32)
+    with np.errstate(invalid="ignore", divide="ignore", over="ignore"):
+        n = np.sqrt((x[:, 0] * x[:, 0] + x[:, 1] * x[:, 1]) + x[:, 2] * x[:, 2])
+        r = x / n[:, None]
+    bad = ~(np.isfinite(r).all(axis=1) & (n > 0))
+    r[bad] = np.float32(np.nan)
+    return r
+
+
+def ray_dist_f32(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    d0, d1, d2 = a[..., 0] - b[..., 0], a[..., 1] - b[..., 1], a[..., 2] - b[..., 2]
+    return (d0 * d0 + d1 * d1) + d2 * d2
+
+
+def project_match(frame_points: np.ndarray, H: int, W: int, query_points: np.ndarray, init: np.ndarray,
+                  max_steps: int = 64, max_angle: float = 0.01) -> Tuple[np.ndarray, np.ndarray]:
+    """(pixel of f or -1, final FP32 distance) for every query (see the reading above)."""
+    rays = ray_image_f32(frame_points)
+    q = ray_image_f32(query_points)
+    Q = q.shape[0]
+    cur = np.clip(np.asarray(init, dtype=np.int64), 0, H * W - 1)
+    with np.errstate(invalid="ignore"):
+        dcur = ray_dist_f32(rays[cur], q)
+    dcur = np.where(np.isnan(dcur), np.float32(np.inf), dcur).astype(np.float32)
+    active = np.isfinite(q).all(axis=1)
+    for _ in range(max_steps):
+        if not active.any():
+            break
+        y, x = cur // W, cur % W
+        best = dcur.copy()
+        bidx = cur.copy()
+        for dy, dx in _NB8:
+            ny, nx = y + dy, x + dx
+            inside = (ny >= 0) & (ny < H) & (nx >= 0) & (nx < W)
+            cand = np.where(inside, ny * W + nx, 0)
+            with np.errstate(invalid="ignore"):
+                d = ray_dist_f32(rays[cand], q)
+            better = active & inside & (d < best)  # NaN compares false
+            best = np.where(better, d, best)
+            bidx = np.where(better, cand, bidx)
+        moved = bidx != cur
+        active = active & moved
+        cur, dcur = bidx, best
+    dmax = np.float32(2.0 - 2.0 * math.cos(max_angle))
+    ok = np.isfinite(q).all(axis=1) & (dcur <= dmax)
+    return np.where(ok, cur, -1).astype(np.int64), dcur
+
+
+def fuse(canon: np.ndarray, pred: np.ndarray, T_kf: np.ndarray) -> np.ndarray:
+    """Eq. (fusion): X_k <- (C_k X_k + C_f (T_kf X_f)) / (C_k + C_f), C_k <- C_k + C_f for
+    every pixel, with canon = (X_k, C_k) and pred = (X^k_f in f's frame, C^k_f)."""
+    ck = canon[:, 3:4].astype(np.float64)
+    cf = pred[:, 3:4].astype(np.float64)
+    Y = transform(T_kf, pred[:, :3].astype(np.float64))
+    out = np.empty_like(canon, dtype=np.float64)
+    out[:, :3] = (ck * canon[:, :3] + cf * Y) / (ck + cf)
+    out[:, 3:4] = ck + cf
+    return out
+
+
 # =================================================================== error reports
 def pose_errors(pa: np.ndarray, pb: np.ndarray, ref_scale: Optional[float] = None) -> Dict[str, float]:
     """Max over keyframes of rotation angle (rad), relative translation and relative scale error.

@@ -665,3 +665,67 @@ def test_depth_step_clip_and_fixed_segments():
     assert abs(eta[s0] + 0.5) < 1e-15
     assert np.all(eta[seg["fixed"]] == 0) and np.all(eta[~seg["active"]] == 0)
     assert len(seg["fixed"]) > 0
+
+
+# ----------------------------------- front-end: projective matching and fusion (Sec. III-A)
+def _pair(seed=71, H=32, W=40, shift=5, noise=0.0):
+    from synth import make_cloud_problem
+    p = make_cloud_problem(seed, [dict(agents=1, n_kf=4, H=H, W=W, period=30, shift=shift, n_inter=0,
+                                       noise=noise)], dtype=np.float32)
+    arrs = O.problem_arrays(p)
+    e = 0
+    i, j = int(p.edge_i[e]), int(p.edge_j[e])
+    idx = p.match_idx[arrs["idx_off"][e]:arrs["idx_off"][e + 1]]
+    Pi = p.points[arrs["pix_off"][i]:arrs["pix_off"][i + 1]]
+    Pj = p.points[arrs["pix_off"][j]:arrs["pix_off"][j + 1]]
+    Tji = O.sim3_inverse(O.pose_to_matrix(p.poses_gt[j])) @ O.pose_to_matrix(p.poses_gt[i])
+    q = np.concatenate([O.transform(Tji, Pi[:, :3].astype(np.float64)), Pi[:, 3:4]], axis=1).astype(np.float32)
+    return p, Pj, q, idx, H, W
+
+
+def test_projective_match_recovers_exact_correspondences():
+    """Keyframe i's points expressed in frame j's camera are matched to exactly the pixels of
+    j that see the same surface point (the generator's correspondences), from the same
+    pixel index as start; pixels outside the overlap end beyond the angle threshold."""
+    p, Pj, q, idx, H, W = _pair()
+    got, d = O.project_match(Pj, H, W, q, np.arange(H * W), max_steps=64, max_angle=0.002)
+    valid = idx >= 0
+    assert valid.mean() > 0.5
+    np.testing.assert_array_equal(got[valid], idx[valid])
+    # outside the overlap the best ray is on j's border and farther than the threshold
+    assert (got[~valid] == -1).mean() > 0.9
+
+
+def test_projective_match_equals_brute_force_argmin():
+    """On a smooth central-camera ray image the descent reaches the global argmin of the
+    FP32 ray distance over all pixels (ties: lowest distance found first), from a far start."""
+    rng = np.random.default_rng(5)
+    H, W, f = 24, 32, 30.0
+    v, u = np.mgrid[0:H, 0:W]
+    rays = np.stack([(u - W / 2 + 0.5) / f, (v - H / 2 + 0.5) / f, np.ones_like(u, dtype=float)], -1).reshape(-1, 3)
+    depth = 2.0 + rng.uniform(size=H * W)
+    frame = np.concatenate([rays * depth[:, None], np.ones((H * W, 1))], 1).astype(np.float32)
+    qd = np.stack([rng.uniform(-0.5, 0.5, 200), rng.uniform(-0.35, 0.35, 200), np.ones(200)], -1) * 3.0
+    query = np.concatenate([qd, np.ones((200, 1))], 1).astype(np.float32)
+    got, d = O.project_match(frame, H, W, query, np.zeros(200, dtype=np.int64), max_steps=200, max_angle=1.0)
+    R = O.ray_image_f32(frame)
+    Qr = O.ray_image_f32(query)
+    allD = O.ray_dist_f32(R[None, :, :], Qr[:, None, :])
+    np.testing.assert_array_equal(d, allD.min(axis=1))
+    assert np.all(got >= 0)
+
+
+def test_fusion_closed_forms():
+    """Eq. (fusion): equal confidences average, the confidence accumulates, and a prediction
+    that already equals the map (through T_kf) leaves the map's points unchanged."""
+    rng = np.random.default_rng(6)
+    X = rng.normal(size=(50, 3)) + np.array([0, 0, 5.0])
+    canon = np.concatenate([X, np.full((50, 1), 2.0)], 1)
+    T = rand_sim3(rng)
+    pred_same = np.concatenate([O.transform(O.sim3_inverse(T), X), np.full((50, 1), 3.0)], 1)
+    out = O.fuse(canon, pred_same, T)
+    np.testing.assert_allclose(out[:, :3], X, atol=1e-12)
+    np.testing.assert_array_equal(out[:, 3], 5.0)
+    Y = rng.normal(size=(50, 3))
+    out2 = O.fuse(canon, np.concatenate([Y, np.full((50, 1), 2.0)], 1), np.eye(4))
+    np.testing.assert_allclose(out2[:, :3], 0.5 * (X + Y), atol=1e-15)
