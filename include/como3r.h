@@ -393,6 +393,45 @@ int como3r_depth_setup(como3r_graph_t graph, const como3r_depth_desc* desc, int6
 int como3r_depth_refine(como3r_graph_t graph, const double* poses, double* eta, int32_t iters,
                         double* cost_trace, void* points_out, float* match_ms);
 
+/* ---- Front-end kernels (Sec. III-A).
+ *
+ * Projective ray matching: for every queried point x (keyframe k's pointmap predicted in
+ * frame f's camera, X^k_f), the pixel p* of f minimising |psi([X^f_f]_p) - psi(x)|^2 on f's
+ * ray image, by a deterministic descent: from init[q] (or pixel q mod H*W when init is
+ * NULL), move to the best of the 8 neighbours (order (-1,-1) (-1,0) (-1,1) (0,-1) (0,1)
+ * (1,-1) (1,0) (1,1); strictly smaller distance; the first on ties) while it improves, at
+ * most max_steps moves.  Distances are FP32 with every operation correctly rounded in
+ * the fixed order n = sqrt((x0 x0 + x1 x1) + x2 x2), psi = x / n,
+ * d = ((a0-b0)^2 + (a1-b1)^2) + (a2-b2)^2 (no fused multiply-adds), so the result is
+ * reproducible on any IEEE implementation.  match[q] = -1 when x is not finite or has zero
+ * norm, or when the final distance exceeds 2 - 2 cos(max_angle) (rounded to FP32).  Pixels
+ * of f whose ray is not finite are never entered.  The descriptor-window refinement of the
+ * paper needs the prior's descriptors and is not part of this call. */
+typedef struct {
+  int32_t H, W;                 /* frame f's pointmap size */
+  const void* frame_points;     /* device [H*W] packed (x, y, z, c) pixels of X^f_f */
+  const void* query_points;     /* device [num_queries] packed (x, y, z, c) points x */
+  int32_t num_queries;
+  int32_t dtype;                /* como3r_dtype of both point arrays (converted to FP32, round to nearest) */
+  const int32_t* init;          /* device [num_queries] start pixels, or NULL */
+  int32_t max_steps;            /* >= 0 */
+  double max_angle;             /* radians, >= 0 */
+} como3r_match_desc;
+
+/* match device int32 [num_queries] (pixel of f or -1); dist device float [num_queries] or
+ * NULL (final FP32 distance).  Asynchronous on `cuda_stream` (a scratch ray image is
+ * allocated stream-ordered).  Errors: INVALID_ARG, CUDA. */
+int como3r_project_match(const como3r_match_desc* desc, int32_t* match, float* dist, void* cuda_stream);
+
+/* Confidence-weighted fusion, Eq. (fusion), per pixel:
+ *   X_k <- (C_k X_k + C_f (T_kf X_f)) / (C_k + C_f),  C_k <- C_k + C_f,
+ * canon device [num_pixels] packed (X_k, C_k), in/out; pred device [num_pixels] packed
+ * (X^k_f in f's frame, C^k_f); T_kf host [8] pose (t, q, s) mapping f's camera to k's.
+ * dtype COMO3R_F32 or COMO3R_F64 (a running average is not kept in FP16: UNSUPPORTED).
+ * Asynchronous on `cuda_stream`.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+int como3r_fuse(void* canon, const void* pred, int64_t num_pixels, int32_t dtype, const double* T_kf,
+                void* cuda_stream);
+
 /* Human-readable text of a status code. */
 const char* como3r_status_str(int code);
 

@@ -64,6 +64,12 @@ DEPTH_DEFAULTS = dict(c_min=1.5, min_pixels=16, sigma_point=0.05, lambda_smooth=
                       lambda_lm=0.05, eta_max=0.5)
 
 
+class MatchDesc(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("frame_points", ctypes.c_void_p),
+                ("query_points", ctypes.c_void_p), ("num_queries", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("init", ctypes.c_void_p), ("max_steps", ctypes.c_int32), ("max_angle", ctypes.c_double)]
+
+
 class GaugeDesc(ctypes.Structure):
     _fields_ = [
         ("num_candidates", ctypes.c_int32), ("num_kf", ctypes.c_int32), ("pix_off", ctypes.POINTER(ctypes.c_int64)),
@@ -109,6 +115,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.como3r_gauge_transport.argtypes = [vp, ctypes.c_int32, vp, vp, ctypes.c_int32, vp]
     lib.como3r_depth_setup.argtypes = [vp, ctypes.POINTER(DepthDesc), _i64p]
     lib.como3r_depth_refine.argtypes = [vp, vp, vp, ctypes.c_int32, _f64p, vp, ctypes.POINTER(ctypes.c_float)]
+    lib.como3r_project_match.argtypes = [ctypes.POINTER(MatchDesc), vp, vp, vp]
+    lib.como3r_fuse.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, _f64p, vp]
     lib.como3r_status_str.argtypes = [ctypes.c_int]
     lib.como3r_status_str.restype = ctypes.c_char_p
     lib.como3r_last_error.argtypes = []
@@ -475,4 +483,27 @@ def terminal_refine(graph: "Graph", poses, labels, rounds: int = 3, depth_iters:
             graph.points.copy_(buf)
         graph.solve(work, pose_iters, trace=False)
     return work.cpu().numpy(), eta
+
+
+def project_match(frame_points, H: int, W: int, query_points, dtype: int = F32, init=None, max_steps: int = 64,
+                  max_angle: float = 0.01, stream=None, with_dist: bool = False):
+    """como3r_project_match on CUDA tensors; returns int32 matches (and FP32 distances)."""
+    import torch
+    Q = int(query_points.shape[0])
+    match = torch.empty(Q, dtype=torch.int32, device=query_points.device)
+    dist = torch.empty(Q, dtype=torch.float32, device=query_points.device) if with_dist else None
+    d = MatchDesc(H=int(H), W=int(W), frame_points=_ptr(frame_points), query_points=_ptr(query_points),
+                  num_queries=Q, dtype=int(dtype), init=_ptr(init), max_steps=int(max_steps),
+                  max_angle=float(max_angle))
+    _check(lib().como3r_project_match(ctypes.byref(d), _ptr(match), _ptr(dist), _torch_stream(stream)),
+           "project_match")
+    return (match, dist) if with_dist else match
+
+
+def fuse(canon, pred, T_kf, dtype: int = F32, stream=None):
+    """como3r_fuse: canon <- confidence-weighted running average with T_kf pred (in place)."""
+    T = np.ascontiguousarray(np.asarray(T_kf, dtype=np.float64))
+    _check(lib().como3r_fuse(_ptr(canon), _ptr(pred), int(canon.shape[0]), int(dtype), T.ctypes.data_as(_f64p),
+                             _torch_stream(stream)), "fuse")
+    return canon
 
