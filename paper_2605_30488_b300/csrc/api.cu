@@ -75,6 +75,8 @@ struct como3r_graph {
   int32_t* d_item_off = nullptr;
   // balanced K1 schedule (rebuilt on the device when the match indices change)
   int32_t *d_counts = nullptr, *d_wstart = nullptr, *d_wseg = nullptr, *d_seg_off = nullptr;
+  uint32_t* d_compact = nullptr;  // valid-match lists per 1024-pixel item (kCompactSlot entries per item)
+  bool k1_compact = false;        // d_compact is allocated (index rows aligned, P <= 2^22)
   long long* d_cum = nullptr;
   int max_warps = 0, k1_wv = 0, k1_wp = 1;
   double *d_T64 = nullptr, *d_Ad = nullptr, *d_partials = nullptr;
@@ -156,14 +158,14 @@ bool is_device_pointer(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-WarpSched sched(const como3r_graph* g) { return WarpSched{g->d_wstart, g->d_wseg}; }
+WarpSched sched(const como3r_graph* g) { return WarpSched{g->d_wstart, g->d_wseg, g->d_counts, g->d_compact}; }
 
 // Balanced K1 schedule for the current items and a grid of `grid` CTAs.
 int rebuild_schedule(como3r_graph* g, int cfg, int grid, int wv, int wp, cudaStream_t s) {
   const int W = grid * residual_reduce_workers_per_cta(cfg);
   if (W > g->max_warps) return set_error(COMO3R_ERR_UNSUPPORTED, "K1 grid larger than the schedule buffers");
   CK(launch_schedule(g->midx, g->d_es, g->d_items, g->num_items, g->d_item_off, g->plan.E, W, wv, wp, g->d_counts,
-                     g->d_cum, g->d_wstart, g->d_wseg, g->d_seg_off, s),
+                     g->d_cum, g->d_wstart, g->d_wseg, g->d_seg_off, g->k1_compact ? g->d_compact : nullptr, s),
      "schedule");
   return COMO3R_OK;
 }
@@ -178,8 +180,9 @@ std::vector<std::pair<int, int>> weight_candidates(int cfg) {
   int wv = 0, wp = 1;
   residual_reduce_cost_weights(cfg, wv, wp);
   std::vector<std::pair<int, int>> c{{wv, wp}};
-  for (int a : {0, 1, 2, 3, 5})
+  for (int a : {0, 1, 2, 3, 5, 8})
     if (a != wv || wp != 1) c.push_back({a, 1});
+  c.push_back({1, 0});  // valid matches only (the precompacted lists skip the index rows)
   return c;
 }
 
@@ -297,12 +300,14 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   g->idx_rows_aligned = reinterpret_cast<uintptr_t>(g->midx) % 16 == 0 && reinterpret_cast<uintptr_t>(g->points) % 16 == 0;
   for (int k = 0; k < p.N; ++k)
     g->idx_rows_aligned = g->idx_rows_aligned && (p.npix[k] % 4 == 0) && p.npix[k] <= (1 << 22);
+  g->k1_compact = g->idx_rows_aligned;
   const int E = p.E, N = p.N, G = p.G;
   const int nslots = p.slot_begin.back(), ncols = p.col_begin.back();
   if ((rc = upload(g, &g->d_es, p.es)) || (rc = upload(g, &g->d_items, items)) ||
       (rc = upload(g, &g->d_item_off, item_off)) || (rc = dalloc(g, &g->d_T64, (size_t)E * 12)) ||
       (rc = dalloc(g, &g->d_T32, (size_t)E * 16)) || (rc = dalloc(g, &g->d_Ad, (size_t)E * 49)) ||
       (rc = dalloc(g, &g->d_partials, (size_t)std::max(g->max_items, g->max_warps + E) * kPartial)) ||
+      (g->idx_rows_aligned && (rc = dalloc(g, &g->d_compact, (size_t)g->max_items * kCompactSlot))) ||
       (rc = dalloc(g, &g->d_counts, (size_t)g->max_items)) || (rc = dalloc(g, &g->d_cum, (size_t)g->max_items + 1)) ||
       (rc = dalloc(g, &g->d_wstart, (size_t)g->max_warps + 1)) || (rc = dalloc(g, &g->d_wseg, (size_t)g->max_warps)) ||
       (rc = dalloc(g, &g->d_seg_off, (size_t)E + 1)) ||

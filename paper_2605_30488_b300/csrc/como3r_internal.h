@@ -34,7 +34,12 @@ struct EdgeStatic {            // per edge, fixed at create
 struct WarpSched {
   const int32_t* start;
   const int32_t* seg;
+  // valid-match lists (or nullptr): item it's counts[it] valid matches, packed
+  // (n << 10) | (pixel offset in the item), at compact + it * kCompactSlot
+  const int32_t* counts = nullptr;
+  const uint32_t* compact = nullptr;
 };
+constexpr int kCompactSlot = 1024;  // entries per item slot of the valid-match lists
 
 struct RobustParams {          // whitening and Huber constants (Sec. III-A)
   double inv_sigma_ray, inv_sigma_dist;      // 1/sigma_r, 1/sigma_d
@@ -166,7 +171,7 @@ int residual_reduce_block();
 // bases [W], first segment per edge [E + 1].
 cudaError_t launch_schedule(const int32_t* midx, const EdgeStatic* es, const Item* items, int num_items,
                             const int32_t* item_off, int E, int W, int wv, int wp, int32_t* counts, long long* cum,
-                            int32_t* start, int32_t* seg, int32_t* seg_off, cudaStream_t s);
+                            int32_t* start, int32_t* seg, int32_t* seg_off, uint32_t* compact, cudaStream_t s);
 // Schedule workers of a launch configuration per CTA (1) or per warp (block / 32), and
 // the cost weights of its loop.
 int residual_reduce_workers_per_cta(int cfg);

@@ -54,6 +54,7 @@ struct SolveCtx {
   const int* slot_home;
   const int* col_home;
   int rank;
+  int nranks;             // CTAs of the cluster
 };
 
 // A location in the shared memory of CTA `rank` of this cluster (direct when it is ours).
@@ -165,7 +166,13 @@ __device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int 
 #pragma unroll
       for (int c = 0; c < 7; ++c) y[c] = a[c];
     }
-    if (bad && sl == 0) *fail = 1;
+    if (bad && sl == 0) {
+      if constexpr (CL) {  // every CTA's copy of the level's flag: each reads its own after the barrier
+        for (int r = 0; r < C.nranks; ++r) *cooperative_groups::this_cluster().map_shared_rank(fail, (unsigned)r) = 1;
+      } else {
+        *fail = 1;
+      }
+    }
   }
 }
 
@@ -415,11 +422,12 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
 // Each CTA keeps its columns' blocks and scratch in its shared memory.  Per level: D of the
 // CTA's columns with its far updates of the previous level, then its off-diagonal solves
 // (both read only its own blocks), one cluster barrier (their results become visible to the
-// other CTAs), the failure flags of the level, then the CTA's near updates (sources read
+// other CTAs), the level's failure flag, then the CTA's near updates (sources read
 // through the cluster window, destinations its own).  Backward substitution: one cluster
-// barrier per level.  A failed attempt is decided from the level's flags of all CTAs, read
-// after the barrier; flags are double-buffered by level parity and a failing level takes a
-// second barrier before the flags are reset, so every CTA sees the same decision.
+// barrier per level.  A CTA whose pivot fails writes the level's flag into every CTA's
+// shared memory before the barrier, so after it each CTA reads only its own copy (no
+// remote read on the common path) and all take the same decision; flags are
+// double-buffered by level parity.
 constexpr int kClusterThreads = 256;
 constexpr int kClusterWarps = kClusterThreads / 32;
 
@@ -431,7 +439,6 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ int s_fail[2];
-  __shared__ int s_any;
   const int rank = (int)cl.block_rank();
   const int g = blockIdx.x / CP.C;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -474,7 +481,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
   stage(colslot, P.col_slot + cbase + g, ncol + 1, tid, kClusterThreads);
   stage(srow, P.slot_row + sbase, nslot, tid, kClusterThreads);
   C.tri = tri; C.utask = ut; C.ttask = tt; C.col_slot = colslot; C.slot_row = srow; C.sched = cs; C.lvl = lv;
-  C.slot_home = sh; C.col_home = ch; C.rank = rank;
+  C.slot_home = sh; C.col_home = ch; C.rank = rank; C.nranks = CP.C;
   // the block gather below takes its source addresses from `own`: the plan must have
   // landed (and be visible to every thread) before any address is formed from it
   async_wait_all();
@@ -523,19 +530,17 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
       const int tpad = (7 * ntl + 31) & ~31;
       const int nx = tpad + 7 * ncl_l;
       for (int x = tid; x < nx; x += kClusterThreads) trsm_or_inverse<true>(C, L0[3], ntl, tpad, L0[0], x);
+      // the next level's flag: its last writers (level l - 1) finished before the previous
+      // barrier, its next ones (level l + 1) start after this one
+      if (tid == 0) s_fail[(l + 1) & 1] = 0;
       cl.sync();
-      if (tid == 0) {
-        int any = 0;
-        for (int r = 0; r < CP.C; ++r) any |= *cl.map_shared_rank(&s_fail[l & 1], (unsigned)r);
-        s_any = any;
-      }
-      __syncthreads();
-      if (s_any) {
-        cl.sync();  // every CTA has read the flags before any resets them
+      // a failing CTA wrote this level's flag into every CTA before the barrier, so the
+      // local copy is the OR over the cluster and every CTA takes the same decision
+      if (s_fail[l & 1]) {
+        cl.sync();
         failed = true;
         break;
       }
-      if (tid == 0) s_fail[(l + 1) & 1] = 0;  // nobody reads it before the next barrier
       for (int u = L0[1] + warp; u < L0[2]; u += kClusterWarps) update_task<true>(C, ut[u], lane);
       __syncthreads();
     }

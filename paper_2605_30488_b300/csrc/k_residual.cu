@@ -623,6 +623,16 @@ __device__ __forceinline__ void read_px(const unsigned char* s, R& x, R& y, R& z
   }
 }
 
+static_assert(kAsyncChunk == kCompactSlot, "valid-match list slots hold one 1024-pixel item");
+
+// copies an item's precompacted valid-match list (cnt packed entries, slot 16-byte aligned)
+// into buf (all lanes; 16-byte pieces, 4-byte tail)
+__device__ __forceinline__ void prefetch_packed(int32_t* buf, const uint32_t* __restrict__ src, int cnt, int lane) {
+  const int n16 = cnt & ~3;
+  for (int q = 4 * lane; q < n16; q += 128) cp_async16(buf + q, src + q);
+  for (int q = n16 + lane; q < cnt; q += 32) cp_async4(buf + q, src + q);
+}
+
 // copies the match indices of `item` into buf (all lanes; 16-byte pieces, 4-byte tail)
 __device__ __forceinline__ void prefetch_indices(int32_t* buf, const int32_t* __restrict__ idx, const Item& item,
                                                  int lane) {
@@ -656,9 +666,17 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
   int it0, it1, seg;
   warp_range(ws, gwarp, nwarps, num_items, it0, it1, seg);
   int b = 0;
+  // with precompacted valid-match lists the index rows are not read at all
+  const bool pre = ws.compact != nullptr;
+  int cnt_cur = 0, cnt_next = 0;
   if (it0 < it1) {
     const Item first = items[it0];
-    prefetch_indices(ibuf[0], midx + es[first.edge].idx_off, first, lane);
+    if (pre) {
+      cnt_cur = ws.counts[it0];
+      prefetch_packed(ibuf[0], ws.compact + (int64_t)it0 * kCompactSlot, cnt_cur, lane);
+    } else {
+      prefetch_indices(ibuf[0], midx + es[first.edge].idx_off, first, lane);
+    }
   }
   cp_commit();
   Acc<R> acc;
@@ -669,8 +687,13 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
     const Item item = items[it];
     const int next = it + 1;
     if (next < it1) {
-      const Item itn = items[next];
-      prefetch_indices(ibuf[b ^ 1], midx + es[itn.edge].idx_off, itn, lane);
+      if (pre) {
+        cnt_next = ws.counts[next];
+        prefetch_packed(ibuf[b ^ 1], ws.compact + (int64_t)next * kCompactSlot, cnt_next, lane);
+      } else {
+        const Item itn = items[next];
+        prefetch_indices(ibuf[b ^ 1], midx + es[itn.edge].idx_off, itn, lane);
+      }
     }
     cp_commit();
     cp_wait<1>();  // this item's indices (all but the group just committed)
@@ -684,18 +707,23 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
       else T[q] = T64[12 * item.edge + q];
     }
     const int n_pix = item.end - item.begin;
-    // compact the valid matches of the item in place (writes never reach unread entries)
-    int32_t* curw = ibuf[b];
     int nvalid = 0;
-    const unsigned below = (1u << lane) - 1u;
-    for (int g0 = 0; g0 < n_pix; g0 += 32) {
-      const int m = g0 + lane;
-      const int n = m < n_pix ? cur[m] : -1;
-      const unsigned mask = __ballot_sync(0xffffffffu, n >= 0);
-      if (n >= 0) curw[nvalid + __popc(mask & below)] = (int32_t)(((uint32_t)n << 10) | (uint32_t)m);
-      nvalid += __popc(mask);
+    if (pre) {
+      nvalid = cnt_cur;  // the list is in the buffer already
+      cnt_cur = cnt_next;
+    } else {
+      // compact the valid matches of the item in place (writes never reach unread entries)
+      int32_t* curw = ibuf[b];
+      const unsigned below = (1u << lane) - 1u;
+      for (int g0 = 0; g0 < n_pix; g0 += 32) {
+        const int m = g0 + lane;
+        const int n = m < n_pix ? cur[m] : -1;
+        const unsigned mask = __ballot_sync(0xffffffffu, n >= 0);
+        if (n >= 0) curw[nvalid + __popc(mask & below)] = (int32_t)(((uint32_t)n << 10) | (uint32_t)m);
+        nvalid += __popc(mask);
+      }
+      __syncwarp();
     }
-    __syncwarp();
     const int ngroups = (nvalid + 31) >> 5;
     auto issue = [&](int gidx) {
       const int e = 32 * gidx + lane;

@@ -19,18 +19,28 @@ namespace {
 
 constexpr int kBalanceThreads = 1024;
 
-// Valid matches of every item (one warp per item).
+// Valid matches of every item (one warp per item); with `compact`, also the item's list of
+// valid matches in pixel order, packed (n << 10) | (pixel offset in the item), at
+// compact + it * kCompactSlot (items of at most kCompactSlot pixels, n < 2^22).
 __global__ void count_item_valid_kernel(const int32_t* __restrict__ midx, const EdgeStatic* __restrict__ es,
-                                        const Item* __restrict__ items, int num_items, int32_t* __restrict__ counts) {
+                                        const Item* __restrict__ items, int num_items, int32_t* __restrict__ counts,
+                                        uint32_t* __restrict__ compact) {
   const int lane = threadIdx.x & 31;
   const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned below = (1u << lane) - 1u;
   for (int it = w0; it < num_items; it += nw) {
     const Item item = items[it];
     const int32_t* idx = midx + es[item.edge].idx_off;
+    uint32_t* out = (compact && item.end - item.begin <= kCompactSlot) ? compact + (int64_t)it * kCompactSlot : nullptr;
     int c = 0;
-    for (int m = item.begin + lane; m < item.end; m += 32) c += __ldg(idx + m) >= 0;
-    c = __reduce_add_sync(0xffffffffu, c);
+    for (int g0 = item.begin; g0 < item.end; g0 += 32) {
+      const int m = g0 + lane;
+      const int n = m < item.end ? __ldg(idx + m) : -1;
+      const unsigned mask = __ballot_sync(0xffffffffu, n >= 0);
+      if (out && n >= 0) out[c + __popc(mask & below)] = ((uint32_t)n << 10) | (uint32_t)(m - item.begin);
+      c += __popc(mask);
+    }
     if (lane == 0) counts[it] = c;
   }
 }
@@ -134,11 +144,11 @@ __global__ void __launch_bounds__(kBalanceThreads) balance_kernel(const int32_t*
 
 cudaError_t launch_schedule(const int32_t* midx, const EdgeStatic* es, const Item* items, int num_items,
                             const int32_t* item_off, int E, int W, int wv, int wp, int32_t* counts, long long* cum,
-                            int32_t* start, int32_t* seg, int32_t* seg_off, cudaStream_t s) {
+                            int32_t* start, int32_t* seg, int32_t* seg_off, uint32_t* compact, cudaStream_t s) {
   if (num_items <= 0 || W <= 0) return cudaErrorInvalidValue;
   int blocks = (num_items + 7) / 8;
   if (blocks > 1184) blocks = 1184;
-  count_item_valid_kernel<<<blocks, 256, 0, s>>>(midx, es, items, num_items, counts);
+  count_item_valid_kernel<<<blocks, 256, 0, s>>>(midx, es, items, num_items, counts, compact);
   balance_kernel<<<1, kBalanceThreads, 0, s>>>(counts, items, num_items, item_off, E, W, wv, wp, cum, start, seg,
                                                 seg_off);
   return cudaGetLastError();
