@@ -60,8 +60,12 @@ template <typename R> __device__ __forceinline__ R kInfinity();
 template <> __device__ __forceinline__ float kInfinity<float>() { return __int_as_float(0x7f800000); }
 template <> __device__ __forceinline__ double kInfinity<double>() { return __longlong_as_double(0x7ff0000000000000LL); }
 
-// Square root of a non-negative value (0 -> 0); FP32 through the reciprocal square root.
-__device__ __forceinline__ float nn_sqrt(float v) { return v > 0.f ? v * rsq(v) : 0.f; }
+// Square root of a non-negative value (0 -> 0).
+__device__ __forceinline__ float nn_sqrt(float v) {  // hardware approximation (sqrt(0) = 0)
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(v));
+  return y;
+}
 __device__ __forceinline__ double nn_sqrt(double v) { return sqrt(v); }
 
 // ---- pixel loads: (x, y, z, c) in the storage type, widened to R
@@ -563,8 +567,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
 // ---- shared-memory-staged variant (cp.async) -----------------------------------------
 // Each warp owns a slice of shared memory: two buffers of match indices (the current item
 // and the prefetched next one, kAsyncChunk entries each) and a ring of kRing pixel
-// groups (32 lanes x streamed + gathered pixel).  Once an item's indices have landed the
-// warp compacts its valid matches in place (ballot + prefix count; entry = n << 10 | m),
+// groups (32 lanes x streamed + gathered pixel).  The item's list of valid matches
+// (entry = n << 10 | m) is precompacted when the schedule is built, or, without a list,
+// compacted by the warp in place once its index row has landed (ballot + prefix count),
 // so every lane of the arithmetic works on a real match although a third of the
 // streamed pixels typically have none.  The pixels of the compacted matches then flow
 // through the ring: lane l only ever reads ring slots it filled itself, so the ring needs
