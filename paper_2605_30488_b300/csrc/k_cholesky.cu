@@ -181,41 +181,44 @@ __device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int 
 // sched[s0 + (x - tpad) / 7].  The two kinds never share a warp (they would diverge).
 template <bool CL>
 __device__ void trsm_or_inverse(const SolveCtx& C, int t0, int nt, int tpad, int s0, int x) {
+  // Both solves are right-looking: once x_q is known its term leaves every later row at
+  // once (independent FMAs), so the dependent chain is one multiply and one FMA per
+  // unknown (14 deep) instead of a dot product per unknown (28 deep).
   if (x < 7 * nt) {
     const int2 tt = C.ttask[t0 + x / 7];
     const int i = x % 7;
     const double* Lc = blk<CL>(C, C.col_slot[tt.y]);
     const double* dv = dinv_of<CL>(C, tt.y);
     double* B = blk<CL>(C, tt.x) + 7 * i;
-    double xr[7];
+    double sr[7];
 #pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      double s = B[c];
+    for (int c = 0; c < 7; ++c) sr[c] = B[c];
 #pragma unroll
-      for (int q = 0; q < c; ++q) s = fma(-Lc[7 * c + q], xr[q], s);
-      xr[c] = s * dv[c];
+    for (int q = 0; q < 7; ++q) {
+      sr[q] *= dv[q];  // x_q
+#pragma unroll
+      for (int c = q + 1; c < 7; ++c) sr[c] = fma(-Lc[7 * c + q], sr[q], sr[c]);
     }
 #pragma unroll
-    for (int c = 0; c < 7; ++c) B[c] = xr[c];
+    for (int c = 0; c < 7; ++c) B[c] = sr[c];
   } else if (x >= tpad) {
     const int k = (x - tpad) / 7, c = (x - tpad) % 7;
     const int col = C.sched[s0 + k];
     const double* Lc = blk<CL>(C, C.col_slot[col]);
     const double* dv = dinv_of<CL>(C, col);
     double* X = linv_of<CL>(C, col);
-    double xc[7];
+    // column c of L_cc^{-1}: xc[r] = 0 (r < c), dv[c] (r = c), -dv[r] sum_{c<=q<r} L[r][q] xc[q]
+    double xc[7], acc[7];
 #pragma unroll
-    for (int r = 0; r < 7; ++r) {
-      if (r < c) {
-        xc[r] = 0.0;
-      } else if (r == c) {
-        xc[r] = dv[r];
+    for (int r = 0; r < 7; ++r) acc[r] = 0.0;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      if (q < c) {
+        xc[q] = 0.0;
       } else {
-        double s = 0.0;
+        xc[q] = (q == c) ? dv[q] : -acc[q] * dv[q];
 #pragma unroll
-        for (int q = 0; q < r; ++q)
-          if (q >= c) s = fma(Lc[7 * r + q], xc[q], s);
-        xc[r] = -s * dv[r];
+        for (int r = q + 1; r < 7; ++r) acc[r] = fma(Lc[7 * r + q], xc[q], acc[r]);
       }
     }
 #pragma unroll
