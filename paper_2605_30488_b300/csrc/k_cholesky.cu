@@ -8,8 +8,9 @@
 //      registers (lane r holds row r) with the right-hand side riding along as an eighth
 //      row, which yields y_c = L_cc^{-1}(...) for free; a pivot that is not > 0 or not
 //      finite fails the attempt;
-//   T  one thread per row of every off-diagonal block (B <- B L_cc^{-T}) and per column of
-//      L_cc^{-1}, all independent;
+//   T  one thread per row of every off-diagonal block (B <- B L_cc^{-T}), all independent
+//      (the columns of L_cc^{-1}, needed only by the back substitution, are computed in
+//      the U phase by threads the update tasks leave idle);
 //   U  right-looking: one warp per destination block in any ancestor column,
 //      L[dst] -= sum L_rj L_kj^T over the level's columns j (diagonal destinations also
 //      update the forward right-hand side t_c -= L_cj y_j), so every column has received
@@ -119,6 +120,25 @@ __device__ void update_task(const SolveCtx& C, int4 task, int lane) {
   else if (rhs) y_of<CL>(C, task.w)[lane - 17] = -a1;
 }
 
+// 1/sqrt(p) of a pivot p > 0: an FP32 seed (exponent and leading mantissa bits moved on
+// the ALU, the hardware reciprocal-square-root approximation, widened on the ALU) and one
+// Newton step in FP64, y1 = y0 (3/2 - (p/2) y0^2): relative error ~1e-13 (the seed's
+// ~2^-22, squared), in about half the dependent latency of the FP64 rsqrt, which sits on
+// the factorisation's critical chain seven times per column.  Pivots outside 2^+-100
+// take the FP64 rsqrt, out of line (if-converted it would run for every pivot).
+__device__ __noinline__ double rsqrt_wide_range(double p) { return rsqrt(p); }
+__device__ __forceinline__ double rsqrt_pivot(double p) {
+  const long long b = __double_as_longlong(p);
+  const int ex = (int)((b >> 52) & 0x7ff) - 1023;
+  if (ex < -100 || ex > 100) return rsqrt_wide_range(p);
+  const float pf = __uint_as_float(((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
+  float yf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(pf));
+  const double y0 = widen_f32(yf);
+  const double t = (0.5 * p) * y0;
+  return y0 * fma(-t, y0, 1.5);
+}
+
 // D: Cholesky of diagonal blocks, four columns per warp (FP64 instructions occupy the
 // pipe for the whole warp, so idle lanes would waste it).  Segment s = lane / 8 handles
 // column cols[s]; within it lane r < 7 holds row r and lane 7 holds the forward
@@ -147,7 +167,7 @@ __device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int 
     const long long pb = __double_as_longlong(p);
     const bool okp = pb > 0 && pb < 0x7ff0000000000000LL;
     bad = bad || !okp;
-    const double inv = rsqrt(okp ? p : 1.0);
+    const double inv = rsqrt_pivot(okp ? p : 1.0);
     const double lk = ((sl == k) ? p : a[k]) * inv;
     if (sl == k) myinv = inv;
     if (sl >= k) a[k] = lk;
@@ -384,11 +404,13 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
       __syncthreads();
       if (s_fail) break;
       const int nt = L0[7] - L0[3];
-      const int tpad = (7 * nt + 31) & ~31;
-      const int nx = tpad + 7 * ncl;
-      for (int x = tid; x < nx; x += kSolveThreads) trsm_or_inverse<false>(C, L0[3], nt, tpad, L0[0], x);
+      for (int x = tid; x < 7 * nt; x += kSolveThreads) trsm_or_inverse<false>(C, L0[3], nt, 7 * nt, L0[0], x);
       __syncthreads();
       for (int u = L0[1] + warp; u < L0[2]; u += kSolveWarps) update_task<false>(C, C.utask[u], lane);
+      // the level's L_cc^{-1} (read only by the back substitution), off the critical path:
+      // threads of the last warps, which the update tasks leave idle first
+      for (int x = kSolveThreads - 1 - tid; x < 7 * ncl; x += kSolveThreads)
+        trsm_or_inverse<false>(C, 0, 0, 0, L0[0], x);
       __syncthreads();
     }
     if (s_fail == 0 && nlev > 0) {
@@ -530,9 +552,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
       }
       __syncthreads();
       const int ntl = L0[7] - L0[3];
-      const int tpad = (7 * ntl + 31) & ~31;
-      const int nx = tpad + 7 * ncl_l;
-      for (int x = tid; x < nx; x += kClusterThreads) trsm_or_inverse<true>(C, L0[3], ntl, tpad, L0[0], x);
+      for (int x = tid; x < 7 * ntl; x += kClusterThreads) trsm_or_inverse<true>(C, L0[3], ntl, 7 * ntl, L0[0], x);
       // the next level's flag: its last writers (level l - 1) finished before the previous
       // barrier, its next ones (level l + 1) start after this one
       if (tid == 0) s_fail[(l + 1) & 1] = 0;
@@ -545,6 +565,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
         break;
       }
       for (int u = L0[1] + warp; u < L0[2]; u += kClusterWarps) update_task<true>(C, ut[u], lane);
+      // the level's L_cc^{-1} (read only by the back substitution), off the critical path:
+      // threads of the last warps, which the update tasks leave idle first
+      for (int x = kClusterThreads - 1 - tid; x < 7 * ncl_l; x += kClusterThreads)
+        trsm_or_inverse<true>(C, 0, 0, 0, L0[0], x);
       __syncthreads();
     }
     if (!failed) {

@@ -527,11 +527,14 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
     const int* lvl = p.llvl.data() + 4 * m[kMetaLvlBase];
     const int* colslot = p.lcol_slot.data() + cbase + g;
     const int* sched = p.lsched.data() + cbase;
-    // owners: round robin over the columns of each level
+    // owners: round robin over the columns of each level, starting one rank further at
+    // every level, so that the narrow top of the elimination tree (one column per level)
+    // and the update tasks into it, run by the destination's owner, spread over all CTAs
+    // (one SM's FP64 pipe would otherwise do all of them)
     std::vector<int> owner(ncol, 0), clocal(ncol, 0), slocal(nslot, 0), shome(nslot, 0);
     std::vector<std::vector<int>> own_cols(C), own_slots(C);
     for (int l = 0; l < nlev; ++l)
-      for (int q = lvl[4 * l]; q < lvl[4 * (l + 1)]; ++q) owner[sched[q]] = (q - lvl[4 * l]) % C;
+      for (int q = lvl[4 * l]; q < lvl[4 * (l + 1)]; ++q) owner[sched[q]] = (q - lvl[4 * l] + l) % C;
     for (int q = 0; q < ncol; ++q) {  // level order
       const int c = sched[q], r = owner[c];
       clocal[c] = (int)own_cols[r].size();
