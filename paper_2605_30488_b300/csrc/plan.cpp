@@ -527,14 +527,13 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
     const int* lvl = p.llvl.data() + 4 * m[kMetaLvlBase];
     const int* colslot = p.lcol_slot.data() + cbase + g;
     const int* sched = p.lsched.data() + cbase;
-    // owners: round robin over the columns of each level, starting one rank further at
-    // every level, so that the narrow top of the elimination tree (one column per level)
-    // and the update tasks into it, run by the destination's owner, spread over all CTAs
-    // (one SM's FP64 pipe would otherwise do all of them)
+    // owners: round robin over the columns of each level from rank 0, so that the narrow
+    // top of the elimination tree (one column per level) stays on one CTA and its near
+    // updates read local shared memory; the far updates are spread below
     std::vector<int> owner(ncol, 0), clocal(ncol, 0), slocal(nslot, 0), shome(nslot, 0);
     std::vector<std::vector<int>> own_cols(C), own_slots(C);
     for (int l = 0; l < nlev; ++l)
-      for (int q = lvl[4 * l]; q < lvl[4 * (l + 1)]; ++q) owner[sched[q]] = (q - lvl[4 * l] + l) % C;
+      for (int q = lvl[4 * l]; q < lvl[4 * (l + 1)]; ++q) owner[sched[q]] = (q - lvl[4 * l]) % C;
     for (int q = 0; q < ncol; ++q) {  // level order
       const int c = sched[q], r = owner[c];
       clocal[c] = (int)own_cols[r].size();
@@ -549,6 +548,30 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
     int ncol_max = 0;
     for (int r = 0; r < C; ++r) ncol_max = std::max(ncol_max, (int)own_cols[r].size());
     for (int sl = 0; sl < nslot; ++sl) cp.slot_home[sbase + sl] = (shome[sl] << 24) | slocal[sl];
+    // Executors of the far update tasks of level l (they run during level l + 1's diagonal
+    // factorisations): when level l + 1 has fewer columns than CTAs, the CTAs that own none
+    // of them, round robin (writing the destinations through the cluster window) -- on
+    // this GPU an SM's FP64 pipe is narrow, and updates run beside a critical
+    // factorisation delay it; otherwise the destination's owner.
+    std::vector<int> far_exec(std::max(lvl[4 * nlev + 1], 0), -1);
+    for (int l = 0; l < nlev; ++l) {
+      std::vector<char> busy(C, 0);
+      int nbusy = 0;
+      if (l + 1 < nlev)
+        for (int q = lvl[4 * (l + 1)]; q < lvl[4 * (l + 2)]; ++q)
+          if (!busy[owner[sched[q]]]) {
+            busy[owner[sched[q]]] = 1;
+            ++nbusy;
+          }
+      std::vector<int> idle;
+      for (int r = 0; r < C; ++r)
+        if (!busy[r]) idle.push_back(r);
+      int k = 0;
+      for (int u = lvl[4 * l + 2]; u < lvl[4 * (l + 1) + 1]; ++u) {
+        const int4 t = p.lutask[ubase + u];
+        far_exec[u] = (nbusy < C && !idle.empty()) ? idle[k++ % (int)idle.size()] : shome[t.x];
+      }
+    }
     for (int r = 0; r < C; ++r) {
       const int s0 = (int)cp.csched.size(), u0 = (int)cp.cutask.size(), t0 = (int)cp.cttask.size();
       const int l0 = (int)cp.clvl.size(), o0 = (int)cp.own_slot.size();
@@ -564,10 +587,8 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
             ++nn;
           }
         }
-        for (int u = lvl[4 * l + 2]; u < lvl[4 * (l + 1) + 1]; ++u) {
-          const int4 t = p.lutask[ubase + u];
-          if (shome[t.x] == r) cp.cutask.push_back(t);
-        }
+        for (int u = lvl[4 * l + 2]; u < lvl[4 * (l + 1) + 1]; ++u)
+          if (far_exec[u] == r) cp.cutask.push_back(p.lutask[ubase + u]);
         const int tt = (int)cp.cttask.size() - t0;
         for (int x = lvl[4 * l + 3]; x < lvl[4 * (l + 1) + 3]; ++x) {
           const int2 t = p.lttask[tbase + x];
