@@ -253,8 +253,8 @@ def measure_depth(C, torch, prob, iters: int = 10) -> dict:
     """Segment-level structure refinement (Sec. III-E) on the bench workload: 200 Voronoi
     segments per keyframe, per-segment range errors exp(N(0, 0.05)), `iters` Jacobi steps
     at the initial poses, mixed form.  The per-match pass is HBM-bound: 4 B per streamed
-    pixel plus, per valid match, the two pixels' 24-B records (ray and log-range, segment,
-    confidence)."""
+    pixel plus, per valid match, the two pixels' 20-B records (snapshot point and
+    confidence, segment)."""
     import dataclasses
     from synth.segments import perturb_segment_ranges, problem_labels
     lab = problem_labels(prob, n_seg=200, seed=1)
@@ -275,7 +275,7 @@ def measure_depth(C, torch, prob, iters: int = 10) -> dict:
     call_ms = ev0.elapsed_time(ev1)
     g.close()
     valid = p.valid_matches()
-    bytes_alg = 4 * int(p.pixels_of()[p.edge_i].sum()) + 48 * valid
+    bytes_alg = 4 * int(p.pixels_of()[p.edge_i].sum()) + 40 * valid
     peak, _ = measured_hbm_peak()
     ach = bytes_alg / (match_ms / 1e3) / 1e9
     return {"segments": M, "iters": iters, "cost_first": float(tr[0]), "cost_last": float(tr[-1]),

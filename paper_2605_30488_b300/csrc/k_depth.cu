@@ -9,13 +9,16 @@
 // clipped to |delta| <= eta_max; segments of fixed keyframes stay.
 //
 // Setup (host, once): the pristine snapshot of the graph's pointmaps becomes per-pixel
-// records (ray, log-range; the effective segment and the confidence), the boundary pairs
+// records (the snapshot point and its confidence: X(eta) = e^eta X_init, with e^eta per
+// segment; the effective segment), the boundary pairs
 // (g, h, Delta_gh) and their per-segment lists.  Per iteration:
-//   depth_match_kernel (HBM-bound): persistent warps over the graph's work items, four
-//     pixels per lane in flight (two in FP64); per match the two endpoints' (g, H) contributions are
-//     reduced over runs of lanes with the same segment (segmented warp reduction: the
-//     streamed pixels of a warp are contiguous, the gathered ones shifted, so runs are
-//     long) and the run's head adds them with one FP64 atomic each;
+//   depth_match_kernel (HBM-bound): persistent warps over the graph's work items, each
+//     lane taking four consecutive pixels (two in FP64) with all their loads in flight;
+//     a lane first adds its pixels' (g, H) contributions per side in two (segment, g, H)
+//     slots (consecutive pixels mostly share a segment), then runs of lanes with the same
+//     segment are reduced (segmented warp reduction: the streamed pixels of a warp are
+//     contiguous, the gathered ones shifted, so runs are long) and the run's head adds
+//     them with one FP64 atomic each -- one warp-level reduction per side per 128 pixels;
 //   depth_update_kernel (one thread per segment, FP64): boundary and prior terms, the
 //     damped clipped step into the other eta buffer (Jacobi: every step reads the same eta).
 // MIXED does the per-match arithmetic in FP32 (hardware exp / reciprocal square root /
@@ -77,7 +80,7 @@ __device__ __forceinline__ void seg_add(double* __restrict__ gsum, double* __res
 }
 
 // FP32: hardware approximations (relative error ~2^-22, far inside the mixed form's 1e-5);
-// FP64: the exact functions.
+// FP64: the exact functions.  (e^eta is computed once per segment by the update kernel.)
 __device__ __forceinline__ float rsq_approx(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -88,14 +91,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float exp_m(float x) { return __expf(x); }
-__device__ __forceinline__ double exp_m(double x) { return exp(x); }
 // c^(1/4) of c >= 0 (0 -> 0)
-__device__ __forceinline__ float qroot(float c) {
-  if (!(c > 0.f)) return 0.f;
-  const float s = c * rsq_approx(c);
-  return s * rsq_approx(s);
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
+__device__ __forceinline__ float qroot(float c) { return sqrt_approx(sqrt_approx(c)); }
 __device__ __forceinline__ double qroot(double c) { return sqrt(sqrt(c)); }
 __device__ __forceinline__ float huber_w(float r, float kappa) { return fminf(1.f, kappa * rcp_approx(fabsf(r))); }
 __device__ __forceinline__ double huber_w(double r, double kappa) {
@@ -108,12 +110,46 @@ __device__ __forceinline__ R huber_rho(R r, R kappa) {
   return a <= kappa ? R(0.5) * r * r : kappa * a - R(0.5) * kappa * kappa;
 }
 
+// A lane's two (segment, g, H) accumulation slots of one side: a value goes to the slot
+// holding its segment, else to a free slot, else straight to the atomics (a third
+// segment among a lane's few consecutive pixels is rare).
+template <typename R>
+struct Slots {
+  int ka = -1, kb = -1;
+  R ga = R(0), ha = R(0), gb = R(0), hb = R(0);
+  __device__ __forceinline__ void add(int k, R g, R h, double* gsum, double* hsum) {
+    if (k < 0) return;
+    if (k == ka || ka < 0) {
+      ka = k;
+      ga += g;
+      ha += h;
+    } else if (k == kb || kb < 0) {
+      kb = k;
+      gb += g;
+      hb += h;
+    } else {
+      seg_add(gsum, hsum, k, g, h);
+    }
+  }
+  // warp-level: runs of lanes with the same segment add once per run (the second slot
+  // only when some lane uses it)
+  __device__ __forceinline__ void flush(int lane, double* gsum, double* hsum) {
+    bool head;
+    run_sums(ka, ga, ha, lane, head);
+    if (head && ka >= 0) seg_add(gsum, hsum, ka, ga, ha);
+    if (__any_sync(0xffffffffu, kb >= 0)) {
+      run_sums(kb, gb, hb, lane, head);
+      if (head && kb >= 0) seg_add(gsum, hsum, kb, gb, hb);
+    }
+  }
+};
+
 template <typename R>
 __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
-    const typename Rec<R>::T* __restrict__ rec, const int32_t* __restrict__ seg, const R* __restrict__ conf,
+    const typename Rec<R>::T* __restrict__ rec, const int32_t* __restrict__ seg,
     const int32_t* __restrict__ midx, const Item* __restrict__ items, int num_items,
     const EdgeStatic* __restrict__ es, const double* __restrict__ T64, const float* __restrict__ T32,
-    const R* __restrict__ eta, double kscale, double kappa_d, double* __restrict__ gsum,
+    const R* __restrict__ scale, double kscale, double kappa_d, double* __restrict__ gsum,
     double* __restrict__ hsum, double* __restrict__ cost) {
   const int lane = threadIdx.x & 31;
   const int w0 = (blockIdx.x * kDepthThreads + threadIdx.x) >> 5;
@@ -132,73 +168,58 @@ __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
       else T[q] = T64[12 * item.edge + q];
     }
     const int32_t* idx = midx + e.idx_off;
+    // each lane takes kDepthUnroll consecutive pixels of the item (streamed loads of a lane
+    // are contiguous; its pixels mostly share one segment, so they add up in the lane)
     for (int m0 = item.begin; m0 < item.end; m0 += 32 * kDepthUnroll) {
+      const int mb = m0 + kDepthUnroll * lane;
       int nn[kDepthUnroll];
 #pragma unroll
-      for (int u = 0; u < kDepthUnroll; ++u) {
-        const int m = m0 + 32 * u + lane;
-        nn[u] = m < item.end ? __ldg(idx + m) : -1;
-      }
+      for (int u = 0; u < kDepthUnroll; ++u) nn[u] = mb + u < item.end ? __ldg(idx + mb + u) : -1;
       typename Rec<R>::T ri[kDepthUnroll], rj[kDepthUnroll];
       int si[kDepthUnroll], sj[kDepthUnroll];
-      R ci[kDepthUnroll], cj[kDepthUnroll];
 #pragma unroll
       for (int u = 0; u < kDepthUnroll; ++u) {
         si[u] = sj[u] = -1;
         if (nn[u] >= 0) {
-          const int64_t pi = e.pix_i + m0 + 32 * u + lane, pj = e.pix_j + nn[u];
+          const int64_t pi = e.pix_i + mb + u, pj = e.pix_j + nn[u];
           ri[u] = rec[pi];
           rj[u] = rec[pj];
           si[u] = __ldg(seg + pi);
           sj[u] = __ldg(seg + pj);
-          ci[u] = conf[pi];
-          cj[u] = conf[pj];
         }
       }
+      Slots<R> side_i, side_j;
 #pragma unroll
       for (int u = 0; u < kDepthUnroll; ++u) {
-        R gi = R(0), hi = R(0), gj = R(0), hj = R(0);
-        int ki = -1, kj = -1;
-        if (nn[u] >= 0) {  // every valid match adds to the objective; sides with a segment to (g, H)
-          const R ei = si[u] >= 0 ? __ldg(eta + si[u]) : R(0);  // FP32 copy in the mixed form
-          const R ej = sj[u] >= 0 ? __ldg(eta + sj[u]) : R(0);
-          const R di = exp_m(ri[u].w + ei), dj = exp_m(rj[u].w + ej);
-          const R xi0 = di * ri[u].x, xi1 = di * ri[u].y, xi2 = di * ri[u].z;
-          const R xj0 = dj * rj[u].x, xj1 = dj * rj[u].y, xj2 = dj * rj[u].z;
-          const R a0 = fma(T[0], xj0, fma(T[1], xj1, T[2] * xj2));  // s R X_j
-          const R a1 = fma(T[3], xj0, fma(T[4], xj1, T[5] * xj2));
-          const R a2 = fma(T[6], xj0, fma(T[7], xj1, T[8] * xj2));
-          const R y0 = a0 + T[9], y1 = a1 + T[10], y2 = a2 + T[11];
-          const R cc = ci[u] * cj[u];
-          const R nx2 = fma(xi0, xi0, fma(xi1, xi1, xi2 * xi2)), ny2 = fma(y0, y0, fma(y1, y1, y2 * y2));
-          const bool ok = isfinite(nx2) && isfinite(ny2) && isfinite(cc) && nx2 > R(1e-24) && ny2 > R(1e-24) &&
-                          cc >= R(0);
-          if (ok) {
-            const R k = qroot(cc) * ks;
-            const R r0 = k * (y0 - xi0), r1 = k * (y1 - xi1), r2 = k * (y2 - xi2);
-            const R w0 = huber_w(r0, kappa), w1 = huber_w(r1, kappa), w2 = huber_w(r2, kappa);
-            item_cost += huber_rho(r0, kappa) + huber_rho(r1, kappa) + huber_rho(r2, kappa);
-            // J_g = -k X_i, J_h = k s R X_j
-            const R g0 = -k * xi0, g1 = -k * xi1, g2 = -k * xi2;
-            const R h0 = k * a0, h1 = k * a1, h2 = k * a2;
-            if (si[u] >= 0) {
-              ki = si[u];
-              gi = w0 * r0 * g0 + w1 * r1 * g1 + w2 * r2 * g2;
-              hi = w0 * g0 * g0 + w1 * g1 * g1 + w2 * g2 * g2;
-            }
-            if (sj[u] >= 0) {
-              kj = sj[u];
-              gj = w0 * r0 * h0 + w1 * r1 * h1 + w2 * r2 * h2;
-              hj = w0 * h0 * h0 + w1 * h1 * h1 + w2 * h2 * h2;
-            }
-          }
-        }
-        bool head;
-        run_sums(ki, gi, hi, lane, head);
-        if (head && ki >= 0) seg_add(gsum, hsum, ki, gi, hi);
-        run_sums(kj, gj, hj, lane, head);
-        if (head && kj >= 0) seg_add(gsum, hsum, kj, gj, hj);
+        if (nn[u] < 0) continue;  // every valid match adds to the objective; sides with a segment to (g, H)
+        // X(eta) = |X_init| e^eta psi(X_init) = e^eta X_init; e^eta per segment
+        const R di = si[u] >= 0 ? __ldg(scale + si[u]) : R(1);
+        const R dj = sj[u] >= 0 ? __ldg(scale + sj[u]) : R(1);
+        const R xi0 = di * ri[u].x, xi1 = di * ri[u].y, xi2 = di * ri[u].z;
+        const R xj0 = dj * rj[u].x, xj1 = dj * rj[u].y, xj2 = dj * rj[u].z;
+        const R a0 = fma(T[0], xj0, fma(T[1], xj1, T[2] * xj2));  // s R X_j
+        const R a1 = fma(T[3], xj0, fma(T[4], xj1, T[5] * xj2));
+        const R a2 = fma(T[6], xj0, fma(T[7], xj1, T[8] * xj2));
+        const R y0 = a0 + T[9], y1 = a1 + T[10], y2 = a2 + T[11];
+        const R cc = ri[u].w * rj[u].w;
+        const R nx2 = fma(xi0, xi0, fma(xi1, xi1, xi2 * xi2)), ny2 = fma(y0, y0, fma(y1, y1, y2 * y2));
+        const bool ok = isfinite(nx2) && isfinite(ny2) && isfinite(cc) && nx2 > R(1e-24) && ny2 > R(1e-24) &&
+                        cc >= R(0);
+        if (!ok) continue;
+        const R k = qroot(cc) * ks;
+        const R r0 = k * (y0 - xi0), r1 = k * (y1 - xi1), r2 = k * (y2 - xi2);
+        const R w0 = huber_w(r0, kappa), w1 = huber_w(r1, kappa), w2 = huber_w(r2, kappa);
+        item_cost += huber_rho(r0, kappa) + huber_rho(r1, kappa) + huber_rho(r2, kappa);
+        // J_g = -k X_i, J_h = k s R X_j
+        const R g0 = -k * xi0, g1 = -k * xi1, g2 = -k * xi2;
+        const R h0 = k * a0, h1 = k * a1, h2 = k * a2;
+        side_i.add(si[u], w0 * r0 * g0 + w1 * r1 * g1 + w2 * r2 * g2, w0 * g0 * g0 + w1 * g1 * g1 + w2 * g2 * g2,
+                   gsum, hsum);
+        side_j.add(sj[u], w0 * r0 * h0 + w1 * r1 * h1 + w2 * r2 * h2, w0 * h0 * h0 + w1 * h1 * h1 + w2 * h2 * h2,
+                   gsum, hsum);
       }
+      side_i.flush(lane, gsum, hsum);
+      side_j.flush(lane, gsum, hsum);
     }
     if constexpr (sizeof(R) == 4) lane_cost += widen_f32(item_cost);
     else lane_cost += item_cost;
@@ -214,7 +235,8 @@ __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
 __global__ void depth_update_kernel(int M, const uint8_t* __restrict__ movable, const uint8_t* __restrict__ active,
                                     const int32_t* __restrict__ poff, const int32_t* __restrict__ pother,
                                     const double* __restrict__ pdelta, const double* __restrict__ eta_in,
-                                    double* __restrict__ eta_out, float* __restrict__ eta32_out,
+                                    double* __restrict__ eta_out, float* __restrict__ scale32_out,
+                                    double* __restrict__ scale64_out,
                                     double* __restrict__ gsum,
                                     double* __restrict__ hsum, double lambda_smooth, double lambda_prior,
                                     double lambda_lm, double eta_max, int apply, double* __restrict__ cost) {
@@ -237,15 +259,19 @@ __global__ void depth_update_kernel(int M, const uint8_t* __restrict__ movable, 
   double step = 0.0;
   if (apply && movable[s] && h > 0.0) step = fmin(eta_max, fmax(-eta_max, -g / ((1.0 + lambda_lm) * h)));
   eta_out[s] = es + step;
-  if (eta32_out) eta32_out[s] = (float)(es + step);
+  if (scale32_out) scale32_out[s] = expf((float)(es + step));
+  if (scale64_out) scale64_out[s] = exp(es + step);
   gsum[s] = 0.0;
   hsum[s] = 0.0;
   if (e != 0.0) atomicAdd(cost, e);
 }
 
-__global__ void eta_to_float_kernel(const double* __restrict__ a, float* __restrict__ b, int M) {
+__global__ void eta_to_scale_kernel(const double* __restrict__ a, float* __restrict__ b32, double* __restrict__ b64,
+                                    int M) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < M) b[s] = (float)a[s];
+  if (s >= M) return;
+  if (b32) b32[s] = expf((float)a[s]);
+  if (b64) b64[s] = exp(a[s]);
 }
 
 // Refined pointmap in the graph's storage type: X = exp(logd + eta) psi for pixels of a
@@ -260,7 +286,7 @@ __global__ void depth_points_kernel(const typename Rec<R>::T* __restrict__ rec, 
       uint2 v = reinterpret_cast<const uint2*>(src)[p];
       if (s >= 0) {
         const typename Rec<R>::T r = rec[p];
-        const double d = exp((double)r.w + eta[s]);
+        const double d = exp(eta[s]);
         const __half2 a = __floats2half2_rn((float)(d * r.x), (float)(d * r.y));
         const float cz = __half2float(reinterpret_cast<const __half2*>(&v.y)->y);
         const __half2 b = __floats2half2_rn((float)(d * r.z), cz);
@@ -272,7 +298,7 @@ __global__ void depth_points_kernel(const typename Rec<R>::T* __restrict__ rec, 
       float4 v = reinterpret_cast<const float4*>(src)[p];
       if (s >= 0) {
         const typename Rec<R>::T r = rec[p];
-        const double d = exp((double)r.w + eta[s]);
+        const double d = exp(eta[s]);
         v.x = (float)(d * r.x); v.y = (float)(d * r.y); v.z = (float)(d * r.z);
       }
       reinterpret_cast<float4*>(dst)[p] = v;
@@ -281,7 +307,7 @@ __global__ void depth_points_kernel(const typename Rec<R>::T* __restrict__ rec, 
       double2 a = q[0], b = q[1];
       if (s >= 0) {
         const typename Rec<R>::T r = rec[p];
-        const double d = exp((double)r.w + eta[s]);
+        const double d = exp(eta[s]);
         a.x = d * r.x; a.y = d * r.y; b.x = d * r.z;
       }
       double2* o = reinterpret_cast<double2*>(dst) + 2 * p;
@@ -306,16 +332,16 @@ struct DepthState {
   int mode = COMO3R_MIXED, dtype = COMO3R_F32;
   int64_t npix = 0;
   int M = 0, n_active = 0, n_pairs = 0;
-  void* rec = nullptr;        // float4 / double4 [npix]: psi (x, y, z), log range
+  void* rec = nullptr;        // float4 / double4 [npix]: snapshot point (x, y, z), confidence
   int32_t* seg = nullptr;     // [npix] effective global segment or -1
-  void* conf = nullptr;       // float / double [npix]
   uint8_t* movable = nullptr; // [M]
   uint8_t* active = nullptr;  // [M]
   int32_t* poff = nullptr;    // [M + 1] pair lists per segment
   int32_t* pother = nullptr;  // [2 n_pairs]
   double* pdelta = nullptr;   // [2 n_pairs] Delta oriented from the list's segment
   double *eta[2] = {nullptr, nullptr}, *gsum = nullptr, *hsum = nullptr, *cost = nullptr;
-  float* eta32[2] = {nullptr, nullptr};  // FP32 copies read by the mixed-form match pass
+  float* sc32[2] = {nullptr, nullptr};   // e^eta, FP32, read by the mixed-form match pass
+  double* sc64[2] = {nullptr, nullptr};  // e^eta, FP64, read by the plain-form match pass
   double sigma_point = 0.05, lambda_smooth = 1.0, lambda_prior = 1.0, lambda_lm = 0.05, eta_max = 0.5;
   std::vector<void*> allocs;
 };
@@ -358,17 +384,17 @@ int depth_setup(const HostPlan& p, const void* points, int dtype, int mode, cons
       for (int c = 0; c < 4; ++c) v[c] = f[c];
     }
   };
-  std::vector<double> logd((size_t)npix), psi((size_t)npix * 3), cf((size_t)npix);
+  std::vector<double> logd((size_t)npix), cf((size_t)npix), xyz((size_t)npix * 3);
   std::vector<uint8_t> fin((size_t)npix);
   for (int64_t q = 0; q < npix; ++q) {
     double v[4];
     px(q, v);
+    for (int c = 0; c < 3; ++c) xyz[3 * q + c] = v[c];
     const double dd = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     const bool ok = std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]) && std::isfinite(v[3]) &&
                     dd > 1e-12;
     fin[q] = ok;
     logd[q] = ok ? std::log(dd) : NAN;
-    for (int c = 0; c < 3; ++c) psi[3 * q + c] = ok ? v[c] / dd : NAN;
     cf[q] = v[3];
   }
   std::vector<int32_t> eff((size_t)npix, -1);
@@ -445,35 +471,35 @@ int depth_setup(const HostPlan& p, const void* points, int dtype, int mode, cons
   st->eta_max = d->eta_max;
   for (uint8_t a : active) st->n_active += a;
   const bool f32 = mode == COMO3R_MIXED;
-  std::vector<unsigned char> recb((size_t)npix * (f32 ? 16 : 32)), confb((size_t)npix * (f32 ? 4 : 8));
+  // per pixel the snapshot point and its confidence (a degenerate point becomes NaN, so
+  // every match touching it fails the per-match test)
+  std::vector<unsigned char> recb((size_t)npix * (f32 ? 16 : 32));
   for (int64_t q = 0; q < npix; ++q) {
-    const double r[4] = {psi[3 * q], psi[3 * q + 1], psi[3 * q + 2], logd[q]};
+    const double r[4] = {fin[q] ? xyz[3 * q] : NAN, fin[q] ? xyz[3 * q + 1] : NAN, fin[q] ? xyz[3 * q + 2] : NAN,
+                         cf[q]};
     if (f32) {
       float* o = reinterpret_cast<float*>(recb.data()) + 4 * q;
       for (int c = 0; c < 4; ++c) o[c] = (float)r[c];
-      reinterpret_cast<float*>(confb.data())[q] = (float)cf[q];
     } else {
       double* o = reinterpret_cast<double*>(recb.data()) + 4 * q;
       for (int c = 0; c < 4; ++c) o[c] = r[c];
-      reinterpret_cast<double*>(confb.data())[q] = cf[q];
     }
   }
-  unsigned char *rec_d = nullptr, *conf_d = nullptr;
-  if ((e = dmalloc(st, &rec_d, recb.size())) || (e = dmalloc(st, &conf_d, confb.size())) ||
+  unsigned char* rec_d = nullptr;
+  if ((e = dmalloc(st, &rec_d, recb.size())) ||
       (e = dmalloc(st, &st->seg, (size_t)npix)) || (e = dmalloc(st, &st->movable, (size_t)M)) ||
       (e = dmalloc(st, &st->active, (size_t)M)) || (e = dmalloc(st, &st->poff, (size_t)M + 1)) ||
       (e = dmalloc(st, &st->pother, pother.size())) || (e = dmalloc(st, &st->pdelta, pdelta.size())) ||
       (e = dmalloc(st, &st->eta[0], (size_t)M)) || (e = dmalloc(st, &st->eta[1], (size_t)M)) ||
-      (e = dmalloc(st, &st->eta32[0], (size_t)M)) || (e = dmalloc(st, &st->eta32[1], (size_t)M)) ||
+      (e = dmalloc(st, &st->sc32[0], (size_t)M)) || (e = dmalloc(st, &st->sc32[1], (size_t)M)) ||
+      (e = dmalloc(st, &st->sc64[0], (size_t)M)) || (e = dmalloc(st, &st->sc64[1], (size_t)M)) ||
       (e = dmalloc(st, &st->gsum, (size_t)M)) || (e = dmalloc(st, &st->hsum, (size_t)M)) ||
       (e = dmalloc(st, &st->cost, 1))) {
     depth_free(st);
     return report_cuda_error(e, "depth setup allocation");
   }
   st->rec = rec_d;
-  st->conf = conf_d;
   e = cudaMemcpyAsync(rec_d, recb.data(), recb.size(), cudaMemcpyHostToDevice, s);
-  if (!e) e = cudaMemcpyAsync(conf_d, confb.data(), confb.size(), cudaMemcpyHostToDevice, s);
   if (!e) e = cudaMemcpyAsync(st->seg, eff.data(), sizeof(int32_t) * npix, cudaMemcpyHostToDevice, s);
   if (!e && M) e = cudaMemcpyAsync(st->movable, movable.data(), M, cudaMemcpyHostToDevice, s);
   if (!e && M) e = cudaMemcpyAsync(st->active, active.data(), M, cudaMemcpyHostToDevice, s);
@@ -502,7 +528,9 @@ int depth_run(DepthState* st, const HostPlan& p, const Item* items, int num_item
   cudaError_t e = cudaSuccess;
   if (M) e = cudaMemcpyAsync(st->eta[0], eta_io, sizeof(double) * M, cudaMemcpyDefault, s);
   if (!e && M) {
-    eta_to_float_kernel<<<(M + 255) / 256, 256, 0, s>>>(st->eta[0], st->eta32[0], M);
+    const bool f32 = st->mode == COMO3R_MIXED;
+    eta_to_scale_kernel<<<(M + 255) / 256, 256, 0, s>>>(st->eta[0], f32 ? st->sc32[0] : nullptr,
+                                                        f32 ? nullptr : st->sc64[0], M);
     e = cudaGetLastError();
   }
   const int grid = std::max(1, std::min(sms * 2, (num_items + 7) / 8));
@@ -519,12 +547,12 @@ int depth_run(DepthState* st, const HostPlan& p, const Item* items, int num_item
     if (!e) {
       if (st->mode == COMO3R_MIXED)
         depth_match_kernel<float><<<grid, kDepthThreads, 0, s>>>(
-            static_cast<const float4*>(st->rec), st->seg, static_cast<const float*>(st->conf), midx, items,
-            num_items, es, T64, T32, st->eta32[cur], kscale, kappa, st->gsum, st->hsum, st->cost);
+            static_cast<const float4*>(st->rec), st->seg, midx, items, num_items, es, T64, T32, st->sc32[cur],
+            kscale, kappa, st->gsum, st->hsum, st->cost);
       else
         depth_match_kernel<double><<<grid, kDepthThreads, 0, s>>>(
-            static_cast<const double4*>(st->rec), st->seg, static_cast<const double*>(st->conf), midx, items,
-            num_items, es, T64, T32, st->eta[cur], kscale, kappa, st->gsum, st->hsum, st->cost);
+            static_cast<const double4*>(st->rec), st->seg, midx, items, num_items, es, T64, T32, st->sc64[cur],
+            kscale, kappa, st->gsum, st->hsum, st->cost);
       e = cudaGetLastError();
     }
     if (!e && match_ms) e = cudaEventRecord(e1, s);
@@ -532,7 +560,8 @@ int depth_run(DepthState* st, const HostPlan& p, const Item* items, int num_item
     if (!e && M)
       depth_update_kernel<<<(M + 127) / 128, 128, 0, s>>>(M, st->movable, st->active, st->poff, st->pother,
                                                            st->pdelta, st->eta[cur], st->eta[cur ^ 1],
-                                                           st->mode == COMO3R_MIXED ? st->eta32[cur ^ 1] : nullptr,
+                                                           st->mode == COMO3R_MIXED ? st->sc32[cur ^ 1] : nullptr,
+                                                           st->mode == COMO3R_MIXED ? nullptr : st->sc64[cur ^ 1],
                                                            st->gsum,
                                                            st->hsum, st->lambda_smooth, st->lambda_prior,
                                                            st->lambda_lm, st->eta_max, k < iters ? 1 : 0, st->cost);
