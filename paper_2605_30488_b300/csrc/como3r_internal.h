@@ -191,6 +191,11 @@ cudaError_t launch_export_dense(int num_slots, const int32_t* slot_kf_r, const i
                                 cudaStream_t s);
 // Workspace doubles per column (outside the slots): 7 Dinv + 7 rhs/solution + 49 L_cc^{-1}.
 constexpr int kColScratch = 63;
+// Panel levels of the factorisation: at most this many columns, each with at most this
+// many off-diagonal blocks (7 diagonal rows + the right-hand side + 7 rows per block fit a
+// warp's 32 lanes).
+constexpr int kPanelCols = 4;
+constexpr int kPanelBlocks = 3;
 // The multi-SM solve (same arguments; `cp` adds the cluster plan; smem_bytes per CTA).
 cudaError_t launch_factor_solve_cluster(int G, const SolverPlan& plan, const ClusterPlan& cp, size_t smem_bytes,
                                         const double* A, const double* gvec, double* tau, double lambda, double eps0,

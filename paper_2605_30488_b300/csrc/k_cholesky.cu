@@ -11,10 +11,13 @@
 //   T  one thread per row of every off-diagonal block (B <- B L_cc^{-T}), all independent
 //      (the columns of L_cc^{-1}, needed only by the back substitution, are computed in
 //      the U phase by threads the update tasks leave idle);
-//   U  right-looking: one warp per destination block in any ancestor column,
-//      L[dst] -= sum L_rj L_kj^T over the level's columns j (diagonal destinations also
-//      update the forward right-hand side t_c -= L_cj y_j), so every column has received
-//      all of its descendants' updates when its own level starts.
+//   U  right-looking: two warps per destination block in any ancestor column (half the
+//      entries each), L[dst] -= sum L_rj L_kj^T over the level's columns j (diagonal
+//      destinations also update the forward right-hand side t_c -= L_cj y_j), so every
+//      column has received all of its descendants' updates when its own level starts.
+// Narrow levels (at most 4 columns of at most 3 off-diagonal blocks: the top of the tree)
+// have no T list: one warp per column eliminates the whole column panel, its off-diagonal
+// rows riding along with the diagonal block's, bitwise as D then T would.
 // The update tasks into the next level's columns run in the U phase; the others run in
 // the next level's D phase, alongside its diagonal factorisations (lookahead).
 // A failed attempt restarts with eps_r = eps0 * 100^r; after max_attempts failures the
@@ -94,35 +97,32 @@ __device__ __forceinline__ double dot7(const double* a, const double* b, double 
   return acc;
 }
 
-// U: one destination block (see file header).  Pass 1: lane l owns
-// entry l of the 7x7 block; pass 2: lanes 0..16 own entries 32..48, lanes 17..23 the seven
-// rows of the forward right-hand side (diagonal destinations only), lanes 24..31 idle.
-// Four triplets are in flight at a time (independent accumulators).
+// U: half h of one destination block (see file header), so that a block's two halves run
+// on two warps (two SM sub-partitions: an FP64 warp instruction holds its sub-partition's
+// pipe for ~80 cycles however few lanes are active).  Half 0: lane l < 28 owns entry l of
+// the 7x7 block, lanes 28..31 rows 0..3 of the forward right-hand side; half 1: lane
+// l < 21 owns entry 28 + l, lanes 21..23 rows 4..6 (right-hand side rows: diagonal
+// destinations only).  Each entry is one chain of FMAs over the level's triplets.
 template <bool CL>
-__device__ void update_task(const SolveCtx& C, int4 task, int lane) {
-  const int e0 = lane, e1 = lane + 32;
-  const bool has1 = e1 < 49;
-  const bool rhs = task.w >= 0 && lane >= 17 && lane < 24;
-  const int r0 = e0 / 7, q0 = e0 % 7, r1 = has1 ? e1 / 7 : lane - 17, q1 = has1 ? e1 % 7 : 0;
-  double* D = blk<CL>(C, task.x);
-  // the destination itself seeds the chains: L[dst] - sum = -(sum - L[dst])
-  double a0 = -D[e0];
-  double a1 = has1 ? -D[e1] : (rhs ? -y_of<CL>(C, task.w)[lane - 17] : 0.0);
+__device__ void update_half(const SolveCtx& C, int4 task, int h, int lane) {
+  const int ne = h ? 21 : 28;
+  const bool ent = lane < ne;
+  if (!ent && (task.w < 0 || lane >= ne + (h ? 3 : 4))) return;
+  const int e = (h ? 28 : 0) + lane;
+  const int r = ent ? e / 7 : (h ? 4 : 0) + lane - ne, q = e % 7;
+  double* dst = ent ? blk<CL>(C, task.x) + e : y_of<CL>(C, task.w) + r;
+  // the destination itself seeds the chain: L[dst] - sum = -(sum - L[dst])
+  double a = -*dst;
   for (int t = task.y; t < task.z; ++t) {
     const int4 tr = C.tri[t];
-    const double* Lr = blk<CL>(C, tr.x);
-    a0 = dot7(Lr + 7 * r0, blk<CL>(C, tr.y) + 7 * q0, a0);
-    if (has1) a1 = dot7(Lr + 7 * r1, blk<CL>(C, tr.y) + 7 * q1, a1);
-    else if (rhs) a1 = dot7(Lr + 7 * r1, y_of<CL>(C, tr.w), a1);
+    a = dot7(blk<CL>(C, tr.x) + 7 * r, ent ? blk<CL>(C, tr.y) + 7 * q : y_of<CL>(C, tr.w), a);
   }
-  D[e0] = -a0;
-  if (has1) D[e1] = -a1;
-  else if (rhs) y_of<CL>(C, task.w)[lane - 17] = -a1;
+  *dst = -a;
 }
 
 // 1/sqrt(p) of a pivot p > 0: an FP32 seed (exponent and leading mantissa bits moved on
 // the ALU, the hardware reciprocal-square-root approximation, widened on the ALU) and one
-// Newton step in FP64, y1 = y0 (3/2 - (p/2) y0^2): relative error ~1e-13 (the seed's
+// Newton step in FP64, y1 = y0 (3/2 - p (y0/2) y0): relative error ~1e-13 (the seed's
 // ~2^-22, squared), in about half the dependent latency of the FP64 rsqrt, which sits on
 // the factorisation's critical chain seven times per column.  Pivots outside 2^+-100
 // take the FP64 rsqrt, out of line (if-converted it would run for every pivot).
@@ -134,9 +134,47 @@ __device__ __forceinline__ double rsqrt_pivot(double p) {
   const float pf = __uint_as_float(((unsigned)(ex + 127) << 23) | (unsigned)((b >> 29) & 0x7fffff));
   float yf;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(pf));
-  const double y0 = widen_f32(yf);
-  const double t = (0.5 * p) * y0;
+  // p (y0 / 2) is bitwise (p / 2) y0: halving is exact on both sides, and it saves an
+  // FP64 instruction on the pivot's chain
+  const double y0 = widen_f32(yf), hy0 = widen_f32(0.5f * yf);
+  const double t = p * hy0;
   return y0 * fma(-t, y0, 1.5);
+}
+
+// Right-looking elimination of a column's seven pivots, one row per lane in groups of W
+// lanes: lane sl < 7 of a group holds row sl of the diagonal block, lanes sl >= 7 rows
+// below it (the forward right-hand side, off-diagonal rows), which end as L_rk = B_rk
+// L_cc^{-T} (and y_c = L_cc^{-1} t_c) by the same operations, in the same order, as the
+// off-diagonal solve below.  A pivot that is not > 0 or not finite sets `bad`; myinv is
+// the pivot's 1 / sqrt for lane sl < 7.
+template <int W>
+__device__ __forceinline__ void eliminate7(double (&a)[7], int sl, bool& bad, double& myinv) {
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const double p = __shfl_sync(kFull, a[k], k, W);
+    // p > 0 and finite, tested on the bit pattern (keeps the FP64 pipe free)
+    const long long pb = __double_as_longlong(p);
+    const bool okp = pb > 0 && pb < 0x7ff0000000000000LL;
+    bad = bad || !okp;
+    const double inv = rsqrt_pivot(okp ? p : 1.0);
+    const double lk = ((sl == k) ? p : a[k]) * inv;
+    if (sl == k) myinv = inv;
+    if (sl >= k) a[k] = lk;
+#pragma unroll
+    for (int c = k + 1; c < 7; ++c) {
+      const double lc = __shfl_sync(kFull, lk, c, W);
+      if (sl >= c) a[c] = fma(-lk, lc, a[c]);
+    }
+  }
+}
+
+template <bool CL>
+__device__ __forceinline__ void raise_fail(const SolveCtx& C, int* fail) {
+  if constexpr (CL) {  // every CTA's copy of the level's flag: each reads its own after the barrier
+    for (int r = 0; r < C.nranks; ++r) *cooperative_groups::this_cluster().map_shared_rank(fail, (unsigned)r) = 1;
+  } else {
+    *fail = 1;
+  }
 }
 
 // D: Cholesky of diagonal blocks, four columns per warp (FP64 instructions occupy the
@@ -160,23 +198,7 @@ __device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int 
   }
   bool bad = false;
   double myinv = 0.0;
-#pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    const double p = __shfl_sync(kFull, a[k], k, 8);
-    // p > 0 and finite, tested on the bit pattern (keeps the FP64 pipe free)
-    const long long pb = __double_as_longlong(p);
-    const bool okp = pb > 0 && pb < 0x7ff0000000000000LL;
-    bad = bad || !okp;
-    const double inv = rsqrt_pivot(okp ? p : 1.0);
-    const double lk = ((sl == k) ? p : a[k]) * inv;
-    if (sl == k) myinv = inv;
-    if (sl >= k) a[k] = lk;
-#pragma unroll
-    for (int c = k + 1; c < 7; ++c) {
-      const double lc = __shfl_sync(kFull, lk, c, 8);
-      if (sl >= c) a[c] = fma(-lk, lc, a[c]);
-    }
-  }
+  eliminate7<8>(a, sl, bad, myinv);
   if (active) {
     if (sl < 7) {
 #pragma unroll
@@ -186,14 +208,44 @@ __device__ void diag_factor4(const SolveCtx& C, const int* cols, int ncols, int 
 #pragma unroll
       for (int c = 0; c < 7; ++c) y[c] = a[c];
     }
-    if (bad && sl == 0) {
-      if constexpr (CL) {  // every CTA's copy of the level's flag: each reads its own after the barrier
-        for (int r = 0; r < C.nranks; ++r) *cooperative_groups::this_cluster().map_shared_rank(fail, (unsigned)r) = 1;
-      } else {
-        *fail = 1;
-      }
-    }
+    if (bad && sl == 0) raise_fail<CL>(C, fail);
   }
+}
+
+// D of a panel level (no off-diagonal solve tasks): one column per warp, the whole column
+// at once.  Lane r < 7 holds row r of the diagonal block, lane 7 the forward right-hand
+// side, lane 8 + 7 b + i row i of the column's off-diagonal block b (at most kPanelBlocks
+// blocks), so the elimination also yields the off-diagonal blocks of L, bitwise as the
+// separate off-diagonal solve would.  A column with more blocks (never planned) fails the
+// attempt rather than leave blocks unsolved.
+template <bool CL>
+__device__ void panel_factor(const SolveCtx& C, int col, int lane, int* fail) {
+  const int dslot = C.col_slot[col], nb = C.col_slot[col + 1] - dslot - 1;
+  if (nb > kPanelBlocks) {
+    if (lane == 0) raise_fail<CL>(C, fail);
+    return;
+  }
+  double* D = blk<CL>(C, dslot);
+  double* y = y_of<CL>(C, col);
+  double* row = nullptr;
+  if (lane < 7) row = D + 7 * lane;
+  else if (lane == 7) row = y;
+  else if (lane < 8 + 7 * nb) row = blk<CL>(C, dslot + 1 + (lane - 8) / 7) + 7 * ((lane - 8) % 7);
+  double a[7];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) a[c] = row ? row[c] : 0.0;
+  bool bad = false;
+  double myinv = 0.0;
+  eliminate7<32>(a, lane, bad, myinv);
+  if (lane < 7) {
+#pragma unroll
+    for (int c = 0; c < 7; ++c) row[c] = (c <= lane) ? a[c] : 0.0;
+    dinv_of<CL>(C, col)[lane] = myinv;
+  } else if (row) {
+#pragma unroll
+    for (int c = 0; c < 7; ++c) row[c] = a[c];
+  }
+  if (bad && lane == 0) raise_fail<CL>(C, fail);
 }
 
 // T: item x < 7 * nt: row (x % 7) of off-diagonal block ttask[t0 + x / 7]; items from
@@ -395,18 +447,24 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
       // D(lv) in groups of four columns, with the far updates of level lv - 1 (their
       // destinations lie two or more levels up, so they do not touch this level's blocks):
       // the latency-bound factorisations and the FP64-throughput-bound updates overlap
-      const int ncl = L0[4] - L0[0], nd = (ncl + 3) / 4;
+      // a level without off-diagonal solve tasks is a panel level: one column per warp
+      const int ncl = L0[4] - L0[0], nt = L0[7] - L0[3];
+      const bool panel = nt == 0;
+      const int nd = panel ? ncl : (ncl + 3) / 4;
       const int f0 = lv > 0 ? C.lvl[4 * (lv - 1) + 2] : 0, nf = lv > 0 ? L0[1] - f0 : 0;
-      for (int i = warp; i < nd + nf; i += kSolveWarps) {
-        if (i < nd) diag_factor4<false>(C, C.sched + L0[0] + 4 * i, min(4, ncl - 4 * i), lane, &s_fail);
-        else update_task<false>(C, C.utask[f0 + i - nd], lane);
+      for (int i = warp; i < nd + 2 * nf; i += kSolveWarps) {
+        if (i >= nd) update_half<false>(C, C.utask[f0 + (i - nd) / 2], (i - nd) & 1, lane);
+        else if (panel) panel_factor<false>(C, C.sched[L0[0] + i], lane, &s_fail);
+        else diag_factor4<false>(C, C.sched + L0[0] + 4 * i, min(4, ncl - 4 * i), lane, &s_fail);
       }
       __syncthreads();
       if (s_fail) break;
-      const int nt = L0[7] - L0[3];
-      for (int x = tid; x < 7 * nt; x += kSolveThreads) trsm_or_inverse<false>(C, L0[3], nt, 7 * nt, L0[0], x);
-      __syncthreads();
-      for (int u = L0[1] + warp; u < L0[2]; u += kSolveWarps) update_task<false>(C, C.utask[u], lane);
+      if (!panel) {
+        for (int x = tid; x < 7 * nt; x += kSolveThreads) trsm_or_inverse<false>(C, L0[3], nt, 7 * nt, L0[0], x);
+        __syncthreads();
+      }
+      for (int x = warp; x < 2 * (L0[2] - L0[1]); x += kSolveWarps)
+        update_half<false>(C, C.utask[L0[1] + x / 2], x & 1, lane);
       // the level's L_cc^{-1} (read only by the back substitution), off the critical path:
       // threads of the last warps, which the update tasks leave idle first
       for (int x = kSolveThreads - 1 - tid; x < 7 * ncl; x += kSolveThreads)
@@ -416,7 +474,8 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     if (s_fail == 0 && nlev > 0) {
       // far updates of the last level (none in an elimination tree: its columns are roots)
       const int* L0 = C.lvl + 4 * (nlev - 1);
-      for (int u = L0[2] + warp; u < L0[5]; u += kSolveWarps) update_task<false>(C, C.utask[u], lane);
+      for (int x = warp; x < 2 * (L0[5] - L0[2]); x += kSolveWarps)
+        update_half<false>(C, C.utask[L0[2] + x / 2], x & 1, lane);
       __syncthreads();
     }
     ok = (s_fail == 0);
@@ -544,15 +603,22 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
     bool failed = false;
     for (int l = 0; l < nlev; ++l) {
       const int* L0 = lv + 4 * l;  // [own columns, near updates, far updates, off-diagonal tasks]
-      const int ncl_l = L0[4] - L0[0], nd = (ncl_l + 3) / 4;
+      // no off-diagonal solve tasks of this CTA at this level: its columns are factored as
+      // whole panels (a panel level, or columns without off-diagonal blocks)
+      const int ncl_l = L0[4] - L0[0], ntl = L0[7] - L0[3];
+      const bool panel = ntl == 0;
+      const int nd = panel ? ncl_l : (ncl_l + 3) / 4;
       const int f0 = l > 0 ? lv[4 * (l - 1) + 2] : 0, nf = l > 0 ? L0[1] - f0 : 0;
-      for (int i = warp; i < nd + nf; i += kClusterWarps) {
-        if (i < nd) diag_factor4<true>(C, cs + L0[0] + 4 * i, min(4, ncl_l - 4 * i), lane, &s_fail[l & 1]);
-        else update_task<true>(C, ut[f0 + i - nd], lane);
+      for (int i = warp; i < nd + 2 * nf; i += kClusterWarps) {
+        if (i >= nd) update_half<true>(C, ut[f0 + (i - nd) / 2], (i - nd) & 1, lane);
+        else if (panel) panel_factor<true>(C, cs[L0[0] + i], lane, &s_fail[l & 1]);
+        else diag_factor4<true>(C, cs + L0[0] + 4 * i, min(4, ncl_l - 4 * i), lane, &s_fail[l & 1]);
       }
-      __syncthreads();
-      const int ntl = L0[7] - L0[3];
-      for (int x = tid; x < 7 * ntl; x += kClusterThreads) trsm_or_inverse<true>(C, L0[3], ntl, 7 * ntl, L0[0], x);
+      if (!panel) {  // (a panel level's next barrier is the cluster barrier below)
+        __syncthreads();
+        for (int x = tid; x < 7 * ntl; x += kClusterThreads)
+          trsm_or_inverse<true>(C, L0[3], ntl, 7 * ntl, L0[0], x);
+      }
       // the next level's flag: its last writers (level l - 1) finished before the previous
       // barrier, its next ones (level l + 1) start after this one
       if (tid == 0) s_fail[(l + 1) & 1] = 0;
@@ -564,7 +630,8 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
         failed = true;
         break;
       }
-      for (int u = L0[1] + warp; u < L0[2]; u += kClusterWarps) update_task<true>(C, ut[u], lane);
+      for (int x = warp; x < 2 * (L0[2] - L0[1]); x += kClusterWarps)
+        update_half<true>(C, ut[L0[1] + x / 2], x & 1, lane);
       // the level's L_cc^{-1} (read only by the back substitution), off the critical path:
       // threads of the last warps, which the update tasks leave idle first
       for (int x = kClusterThreads - 1 - tid; x < 7 * ncl_l; x += kClusterThreads)

@@ -415,10 +415,17 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
     int q = 0;
     for (int lv = 0; lv < S.nlev; ++lv) {
       const int sched0 = q, tt0 = (int)p.lttask.size() - t0;
-      for (; q < n && level[byl[q]] == lv; ++q) {
+      int qe = q, max_nb = 0;
+      for (; qe < n && level[byl[qe]] == lv; ++qe) max_nb = std::max(max_nb, (int)rows[byl[qe]].size());
+      // a narrow level (at most kPanelCols columns, each with at most kPanelBlocks
+      // off-diagonal blocks) is factored as whole column panels: its off-diagonal rows ride
+      // along in the diagonal elimination, so it gets no off-diagonal solve tasks
+      const bool panel = qe - q <= kPanelCols && max_nb <= kPanelBlocks;
+      for (; q < qe; ++q) {
         const int k = byl[q];
         p.lsched.push_back(k);
-        for (size_t b = 0; b < rows[k].size(); ++b) p.lttask.push_back(make_int2(slot_base[k] + 1 + (int)b, k));
+        if (!panel)
+          for (size_t b = 0; b < rows[k].size(); ++b) p.lttask.push_back(make_int2(slot_base[k] + 1 + (int)b, k));
       }
       // updates into the next level's columns ("near", needed by its factorisation) first,
       // then the rest ("far", which the kernel overlaps with the next level's diagonal
@@ -590,10 +597,20 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
         for (int u = lvl[4 * l + 2]; u < lvl[4 * (l + 1) + 1]; ++u)
           if (far_exec[u] == r) cp.cutask.push_back(p.lutask[ubase + u]);
         const int tt = (int)cp.cttask.size() - t0;
-        for (int x = lvl[4 * l + 3]; x < lvl[4 * (l + 1) + 3]; ++x) {
-          const int2 t = p.lttask[tbase + x];
-          if (shome[t.x] == r) cp.cttask.push_back(t);
-        }
+        // this CTA factors its columns of the level as whole panels (no off-diagonal solve
+        // tasks) when it owns at most kPanelCols of them, each with at most kPanelBlocks
+        // off-diagonal blocks: one warp per column on separate SM sub-partitions
+        int n_own = 0, max_nb = 0;
+        for (int q = lvl[4 * l]; q < lvl[4 * (l + 1)]; ++q)
+          if (owner[sched[q]] == r) {
+            ++n_own;
+            max_nb = std::max(max_nb, colslot[sched[q] + 1] - colslot[sched[q]] - 1);
+          }
+        if (n_own > kPanelCols || max_nb > kPanelBlocks)
+          for (int x = lvl[4 * l + 3]; x < lvl[4 * (l + 1) + 3]; ++x) {
+            const int2 t = p.lttask[tbase + x];
+            if (shome[t.x] == r) cp.cttask.push_back(t);
+          }
         cp.clvl.insert(cp.clvl.end(), {sc, un, un + nn, tt});
       }
       cp.clvl.insert(cp.clvl.end(), {(int)cp.csched.size() - s0, (int)cp.cutask.size() - u0,
