@@ -39,6 +39,8 @@ namespace como3r {
 namespace {
 
 constexpr int kSolveThreads = 512;
+// Pivot hand-over buffer of the four-warp panel (doubles: one 32-row column per pivot).
+constexpr int kPanelXchg = 7 * 32;
 constexpr int kSolveWarps = kSolveThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -248,6 +250,78 @@ __device__ void panel_factor(const SolveCtx& C, int col, int lane, int* fail) {
   if (bad && lane == 0) raise_fail<CL>(C, fail);
 }
 
+// The same panel on warps 0..3 of the CTA, for a CTA whose only column of the level it
+// is: every FP64 instruction holds its SM sub-partition's FP64 unit for ~80 cycles
+// whether or not it depends on the previous one, so one warp's ~50 instructions per
+// column are the level's critical path.  Here warp w keeps columns w and w + 4 of every
+// row (lane r = row r as in panel_factor) and only the pivot's owner forms 1 / sqrt(p)
+// and the scaled column l_.k, which it hands to the others through `xbuf` (slot k per
+// pivot, so it is never rewritten within a column) across one named barrier of the four
+// warps (barrier 1; all four warps call this together and pass every barrier).  Every
+// entry sees the operations of panel_factor in the same order: bitwise the same factor.
+__device__ __forceinline__ void panel_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+template <bool CL>
+__device__ void panel_factor4(const SolveCtx& C, int col, int warp, int lane, double* xbuf, int* fail) {
+  const int dslot = C.col_slot[col], nb = C.col_slot[col + 1] - dslot - 1;
+  if (nb > kPanelBlocks) {  // never planned; the same decision in all four warps
+    if (warp == 0 && lane == 0) raise_fail<CL>(C, fail);
+    return;
+  }
+  const int rows = 8 + 7 * nb;  // <= 29
+  const bool has = lane < rows;
+  double* D = blk<CL>(C, dslot);
+  double* row = nullptr;
+  if (has)
+    row = lane < 7 ? D + 7 * lane
+                   : (lane == 7 ? y_of<CL>(C, col) : blk<CL>(C, dslot + 1 + (lane - 8) / 7) + 7 * ((lane - 8) % 7));
+  const int c0 = warp, c1 = warp + 4;
+  const bool two = c1 < 7;
+  double a0 = has ? row[c0] : 0.0, a1 = (has && two) ? row[c1] : 0.0;
+  bool bad = false;
+  double myinv = 0.0;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    if (warp == (k & 3)) {
+      const double ak = k < 4 ? a0 : a1;
+      const double p = __shfl_sync(kFull, ak, k);
+      // p > 0 and finite, tested on the bit pattern (keeps the FP64 pipe free)
+      const long long pb = __double_as_longlong(p);
+      const bool okp = pb > 0 && pb < 0x7ff0000000000000LL;
+      bad = bad || !okp;
+      const double inv = rsqrt_pivot(okp ? p : 1.0);
+      const double lk = ((lane == k) ? p : ak) * inv;
+      if (lane == k) myinv = inv;
+      if (lane >= k) {
+        if (k < 4) a0 = lk;
+        else a1 = lk;
+      }
+      xbuf[32 * k + lane] = lk;
+    }
+    panel_barrier();
+    const double lr = xbuf[32 * k + lane];
+    if (c0 > k) {
+      const double lc = xbuf[32 * k + c0];
+      if (lane >= c0) a0 = fma(-lr, lc, a0);
+    }
+    if (two && c1 > k) {
+      const double lc = xbuf[32 * k + c1];
+      if (lane >= c1) a1 = fma(-lr, lc, a1);
+    }
+  }
+  if (has) {
+    if (lane < 7) {
+      row[c0] = (c0 <= lane) ? a0 : 0.0;
+      if (two) row[c1] = (c1 <= lane) ? a1 : 0.0;
+    } else {
+      row[c0] = a0;
+      if (two) row[c1] = a1;
+    }
+  }
+  if (lane < 7 && (lane & 3) == warp) dinv_of<CL>(C, col)[lane] = myinv;
+  if (__any_sync(kFull, bad) && lane == 0) raise_fail<CL>(C, fail);
+}
+
 // T: item x < 7 * nt: row (x % 7) of off-diagonal block ttask[t0 + x / 7]; items from
 // tpad = 7 * nt rounded up to a warp on: column (x % 7) of L_cc^{-1} for the level column
 // sched[s0 + (x - tpad) / 7].  The two kinds never share a warp (they would diverge).
@@ -365,6 +439,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     const GraphInfoDev* __restrict__ fixed) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ int s_fail;
+  __shared__ double s_xbuf[kPanelXchg];
   const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int* m = P.meta + kMetaCount * g;
   const int cbase = m[kMetaColBase], ncol = m[kMetaNCol], sbase = m[kMetaSlotBase], nslot = m[kMetaNSlot];
@@ -452,10 +527,17 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
       const bool panel = nt == 0;
       const int nd = panel ? ncl : (ncl + 3) / 4;
       const int f0 = lv > 0 ? C.lvl[4 * (lv - 1) + 2] : 0, nf = lv > 0 ? L0[1] - f0 : 0;
-      for (int i = warp; i < nd + 2 * nf; i += kSolveWarps) {
-        if (i >= nd) update_half<false>(C, C.utask[f0 + (i - nd) / 2], (i - nd) & 1, lane);
-        else if (panel) panel_factor<false>(C, C.sched[L0[0] + i], lane, &s_fail);
-        else diag_factor4<false>(C, C.sched + L0[0] + 4 * i, min(4, ncl - 4 * i), lane, &s_fail);
+      if (panel && ncl == 1) {  // one column: spread over four warps, far updates on the rest
+        if (warp < 4) panel_factor4<false>(C, C.sched[L0[0]], warp, lane, s_xbuf, &s_fail);
+        else
+          for (int i = warp - 4; i < 2 * nf; i += kSolveWarps - 4)
+            update_half<false>(C, C.utask[f0 + i / 2], i & 1, lane);
+      } else {
+        for (int i = warp; i < nd + 2 * nf; i += kSolveWarps) {
+          if (i >= nd) update_half<false>(C, C.utask[f0 + (i - nd) / 2], (i - nd) & 1, lane);
+          else if (panel) panel_factor<false>(C, C.sched[L0[0] + i], lane, &s_fail);
+          else diag_factor4<false>(C, C.sched + L0[0] + 4 * i, min(4, ncl - 4 * i), lane, &s_fail);
+        }
       }
       __syncthreads();
       if (s_fail) break;
@@ -523,6 +605,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ int s_fail[2];
+  __shared__ double s_xbuf[kPanelXchg];
   const int rank = (int)cl.block_rank();
   const int g = blockIdx.x / CP.C;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -609,10 +692,17 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
       const bool panel = ntl == 0;
       const int nd = panel ? ncl_l : (ncl_l + 3) / 4;
       const int f0 = l > 0 ? lv[4 * (l - 1) + 2] : 0, nf = l > 0 ? L0[1] - f0 : 0;
-      for (int i = warp; i < nd + 2 * nf; i += kClusterWarps) {
-        if (i >= nd) update_half<true>(C, ut[f0 + (i - nd) / 2], (i - nd) & 1, lane);
-        else if (panel) panel_factor<true>(C, cs[L0[0] + i], lane, &s_fail[l & 1]);
-        else diag_factor4<true>(C, cs + L0[0] + 4 * i, min(4, ncl_l - 4 * i), lane, &s_fail[l & 1]);
+      if (panel && ncl_l == 1) {  // one column: spread over four warps, far updates on the rest
+        if (warp < 4) panel_factor4<true>(C, cs[L0[0]], warp, lane, s_xbuf, &s_fail[l & 1]);
+        else
+          for (int i = warp - 4; i < 2 * nf; i += kClusterWarps - 4)
+            update_half<true>(C, ut[f0 + i / 2], i & 1, lane);
+      } else {
+        for (int i = warp; i < nd + 2 * nf; i += kClusterWarps) {
+          if (i >= nd) update_half<true>(C, ut[f0 + (i - nd) / 2], (i - nd) & 1, lane);
+          else if (panel) panel_factor<true>(C, cs[L0[0] + i], lane, &s_fail[l & 1]);
+          else diag_factor4<true>(C, cs + L0[0] + 4 * i, min(4, ncl_l - 4 * i), lane, &s_fail[l & 1]);
+        }
       }
       if (!panel) {  // (a panel level's next barrier is the cluster barrier below)
         __syncthreads();
@@ -669,7 +759,9 @@ size_t factor_solve_max_smem() {
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
-  return optin > 64 ? (size_t)optin - 64 : 0;
+  // static shared memory of the kernels: flags and the panel hand-over buffer
+  const int reserve = 64 + (int)sizeof(double) * kPanelXchg;
+  return optin > reserve ? (size_t)optin - reserve : 0;
 }
 
 cudaError_t factor_solve_prepare(size_t smem_bytes) {
