@@ -53,9 +53,10 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-sample-edges", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["all", "mixed", "gauge", "depth"], default="all",
-                    help="mixed: time only the resident mixed form; gauge / depth: only the gauge "
-                         "synchronisation / the structure refinement (profiling runs)")
+    ap.add_argument("--only", choices=["all", "mixed", "gauge", "depth", "cfg5"], default="all",
+                    help="mixed: time only the resident mixed form; gauge / depth / cfg5: only the gauge "
+                         "synchronisation / the structure refinement / the 64-graph batch and the "
+                         "2,000-keyframe chain (profiling runs)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-graph batch and the 2,000-keyframe chain (per-graph latency)")
     ap.add_argument("--batch-reps", type=int, default=3)
@@ -418,6 +419,11 @@ def run_ours(args):
     from paper_2605_30488_b300 import como3r as C
     from synth import make_workload
 
+    if args.only == "cfg5":
+        if rank == 0:
+            cfg5 = measure_cfg5(C, torch, torch.device("cuda", local_rank), args.batch_reps)
+            print(json.dumps({"cfg5": cfg5, "note": "profiling run (--only cfg5)"}), flush=True)
+        return
     if args.only == "gauge":
         if rank == 0:
             gauge = measure_gauge(C, torch, torch.device("cuda", local_rank))

@@ -111,7 +111,10 @@ typedef struct {
 
 /* Validate the description, plan the solve (fill-reducing ordering, symbolic block
  * factorisation, work lists; for a few large graphs a multi-SM solve with one cluster of 8
- * CTAs per graph, COMO3R_SOLVE_CLUSTER=<C> forcing C CTAs or 0 none), allocate workspaces, check every match index on the
+ * CTAs per graph, COMO3R_SOLVE_CLUSTER=<C> forcing C CTAs or 0 none; for one graph whose
+ * factor fits neither one SM nor a cluster, a grid-wide solve over one CTA per SM (a
+ * cooperative launch), COMO3R_SOLVE_GRID=1 forcing it for any one-graph plan, 0 disabling
+ * it), allocate workspaces, check every match index on the
  * device (-1 <= n < P_j) and autotune the residual kernel's work-item size and launch
  * configuration on this graph's data (a few milliseconds of timed trial launches; the
  * environment variable COMO3R_K1_CFG=<n> restricts the search to configuration n).
@@ -245,7 +248,7 @@ int64_t como3r_last_launch_count(como3r_graph_t graph);
 #define COMO3R_STAT_SMEM_SOLVE 13    /* 1 if the factor of every graph fits in shared memory */
 #define COMO3R_STAT_ND_GRAPHS 14     /* graphs ordered by nested dissection (others: minimum degree) */
 #define COMO3R_STAT_K1_STALLS 15     /* bounded waits of the TMA-staged K1 that gave up (process-wide; 0 = healthy) */
-#define COMO3R_STAT_SOLVE_CTAS 16    /* CTAs per graph of the factorisation (1, or the cluster of the multi-SM solve) */
+#define COMO3R_STAT_SOLVE_CTAS 16    /* CTAs per graph of the factorisation: 1, the cluster of the multi-SM solve, or the grid of the grid-wide solve of one large graph */
 #define COMO3R_STAT_SOLVE_FLOPS 17   /* FP64 operations of one factorisation + solve, all graphs (FMA = 2) */
 #define COMO3R_STAT_COUNT 18
 int como3r_graph_stats(como3r_graph_t graph, int64_t* stats /* [COMO3R_STAT_COUNT] */);

@@ -102,6 +102,9 @@ struct como3r_graph {
   SolverPlan sp{};
   // multi-SM solve (one cluster of cluster_ctas CTAs per graph), when chosen at create
   int cluster_ctas = 0;
+  // grid-wide solve of a single large graph (grid_ctas co-resident CTAs), when chosen
+  int grid_ctas = 0;
+  GridSync* d_gsync = nullptr;
   size_t cluster_smem = 0;
   ClusterPlan cp{};
   cudaGraphExec_t iter_exec = nullptr, eval_exec = nullptr;
@@ -203,10 +206,13 @@ int enqueue_linearize(como3r_graph* g, cudaStream_t s, double* cost_hist, const 
   return COMO3R_OK;
 }
 
-// The damped factorisation and solve of every graph: the multi-SM variant when it was
-// chosen at create, else one CTA per graph.
+// The damped factorisation and solve of every graph: the grid-wide or the multi-SM
+// variant when one was chosen at create, else one CTA per graph.
 cudaError_t launch_solver(como3r_graph* g, const double* gvec, double* tau, GraphInfoDev* ginfo, int* warn,
                           cudaStream_t s, const GraphInfoDev* fixed = nullptr) {
+  if (g->grid_ctas > 0)
+    return launch_factor_solve_grid(g->grid_ctas, g->sp, g->d_A, g->d_L, g->d_colscratch, gvec, tau, g->lambda,
+                                    g->eps0, g->max_attempts, ginfo, warn, g->d_gsync, s, fixed);
   if (g->cluster_ctas > 0)
     return launch_factor_solve_cluster(g->plan.G, g->sp, g->cp, g->cluster_smem, g->d_A, gvec, tau, g->lambda,
                                        g->eps0, g->max_attempts, ginfo, warn, s, fixed);
@@ -367,6 +373,19 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
         CK(factor_solve_cluster_prepare(g->cluster_smem, C), "cluster solver attributes");
         g->cluster_ctas = C;
       }
+    }
+  }
+  // grid-wide solve for one graph whose factor fits neither one SM nor a cluster
+  // (COMO3R_SOLVE_GRID=0 disables it, =1 forces it for any one-graph plan)
+  if (p.G == 1 && g->cluster_ctas == 0) {
+    const int ncol = p.col_begin[1] - p.col_begin[0];
+    bool want = !g->smem_solve && ncol >= 64;
+    if (const char* e = getenv("COMO3R_SOLVE_GRID")) want = atoi(e) != 0;
+    const int ctas = want ? factor_solve_grid_ctas() : 0;
+    if (ctas > 0) {
+      if ((rc = dalloc(g, &g->d_gsync, 1))) return rc;
+      CK(cudaMemsetAsync(g->d_gsync, 0, sizeof(GridSync), g->stream), "memset");
+      g->grid_ctas = ctas;
     }
   }
   if (g->smem_solve) {
@@ -896,7 +915,7 @@ int como3r_graph_stats(como3r_graph_t g, int64_t* stats) {
   stats[COMO3R_STAT_BLOCK] = residual_reduce_block() * 100 + g->k1_cfg;
   stats[COMO3R_STAT_GRID] = g->k1_grid;
   stats[COMO3R_STAT_SMEM_SOLVE] = g->smem_solve ? 1 : 0;
-  stats[COMO3R_STAT_SOLVE_CTAS] = g->cluster_ctas > 0 ? g->cluster_ctas : 1;
+  stats[COMO3R_STAT_SOLVE_CTAS] = g->grid_ctas > 0 ? g->grid_ctas : (g->cluster_ctas > 0 ? g->cluster_ctas : 1);
   stats[COMO3R_STAT_K1_STALLS] = residual_reduce_stalls();
   return COMO3R_OK;
 }

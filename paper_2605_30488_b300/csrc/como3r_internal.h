@@ -208,6 +208,23 @@ cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t
                                 const GraphInfoDev* fixed = nullptr);
 size_t factor_solve_max_smem();
 cudaError_t factor_solve_prepare(size_t smem_bytes);  // once, before any capture
+// Grid-wide solve of graph 0 of a one-graph plan with the factor in global memory: the
+// per-level task lists over every warp of `ctas` co-resident CTAs (a cooperative launch),
+// phases separated by a grid barrier on `sync` (zeroed once; it resets itself).  A barrier
+// wait has an iteration limit; when it runs out the kernel sets sync->err, every CTA
+// leaves, and the graph gets the zero update of a failed factorisation.
+struct GridSync {
+  unsigned count;  // arrivals at the current barrier
+  unsigned gen;    // barrier generation
+  int fail[2];     // pivot failure flags of the factorisation levels, by level parity
+  int err;         // a barrier wait ran out
+  int pad[3];
+};
+int factor_solve_grid_ctas();  // CTAs of the grid solve on this GPU (one per SM), 0 if unavailable
+cudaError_t launch_factor_solve_grid(int ctas, const SolverPlan& plan, const double* A, double* L, double* colscratch,
+                                     const double* gvec, double* tau, double lambda, double eps0, int max_attempts,
+                                     GraphInfoDev* ginfo, int* warn, GridSync* sync, cudaStream_t s,
+                                     const GraphInfoDev* fixed = nullptr);
 cudaError_t launch_retract(const double* tau, double* poses, const uint8_t* frozen, int N, int* iter_counter,
                            cudaStream_t s);
 // ---- adjoint of the refined cost (k_adjoint.cu)

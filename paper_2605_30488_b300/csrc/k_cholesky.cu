@@ -584,6 +584,179 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
   }
 }
 
+// ---- grid-wide solve of one large graph (factor in global memory) -------------------
+// For a graph whose factor fits neither one SM's nor a cluster's shared memory: the task
+// lists of factor_solve_kernel (graph 0), spread over every warp of a co-resident grid,
+// with a grid barrier where that kernel has a CTA barrier, so the factor is bitwise the
+// same.  The barrier: CTA barrier, then thread 0 arrives on a global counter (the last
+// arrival resets it and advances the generation) and waits for the generation to change,
+// fenced on both sides so that every write before the barrier is seen after it on every
+// SM; the wait has an iteration limit (sync->err, and the solve gives up).
+constexpr unsigned long long kGridSpinLimit = 1ull << 24;  // ~1 s of 64-ns sleeps
+
+__device__ bool grid_barrier(GridSync* gs, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &gs->gen;
+    const unsigned g0 = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&gs->count, 1u) == gridDim.x - 1) {
+      gs->count = 0;
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    } else {
+      unsigned long long it = 0;
+      while (*vgen == g0) {
+        if (++it > kGridSpinLimit) {
+          atomicExch(&gs->err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)&gs->err) ok = 0;
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
+    SolverPlan P, const double* __restrict__ A, double* Lg, double* Sg, const double* __restrict__ gvec,
+    double* __restrict__ tau, double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
+    const GraphInfoDev* __restrict__ fixed, GridSync* gs) {
+  __shared__ double s_xbuf[kPanelXchg];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gw = blockIdx.x * kSolveWarps + warp, GW = gridDim.x * kSolveWarps;
+  const int gt = blockIdx.x * kSolveThreads + tid, GT = gridDim.x * kSolveThreads;
+  const int* m = P.meta;  // graph 0
+  const int cbase = m[kMetaColBase], ncol = m[kMetaNCol], sbase = m[kMetaSlotBase], nslot = m[kMetaNSlot];
+  const int nlev = m[kMetaNLvl];
+  if (ncol == 0) {  // the same in every CTA
+    if (gt == 0) {
+      ginfo[0].attempts = 1;
+      ginfo[0].solved = 1;
+      ginfo[0].done_ns = globaltimer_ns();
+    }
+    return;
+  }
+  SolveCtx C;
+  C.L = Lg + (int64_t)sbase * 49;
+  C.S = Sg + (int64_t)cbase * kColScratch;
+  C.col_slot = P.col_slot + cbase;
+  C.slot_row = P.slot_row + sbase;
+  C.sched = P.sched + cbase;
+  C.tri = P.tri + m[kMetaTriBase];
+  C.utask = P.utask + m[kMetaUBase];
+  C.ttask = P.ttask + m[kMetaTBase];
+  C.lvl = P.lvl + 4 * m[kMetaLvlBase];
+  C.slot_home = nullptr;
+  C.col_home = nullptr;
+  C.rank = 0;
+  C.nranks = 1;
+  const double* Ag = A + (int64_t)sbase * 49;
+  const int* col_kf = P.col_kf + cbase;
+  volatile int* vfail = gs->fail;
+
+  int attempt = 0, last = max_attempts;
+  if (fixed) {
+    if (!fixed[0].solved) last = 0;
+    attempt = fixed[0].attempts - 1;
+    if (last) last = attempt + 1;
+  }
+  bool ok = false, alive = true;
+  double pow100 = 1.0;
+  for (int r = 0; r < attempt; ++r) pow100 *= 100.0;
+  for (; attempt < last && alive; ++attempt, pow100 *= 100.0) {
+    const double eps = eps0 * pow100;
+    for (int64_t x = gt; x < (int64_t)nslot * 49; x += GT) C.L[x] = Ag[x];
+    if (gt == 0) vfail[0] = 0;
+    if (!(alive = grid_barrier(gs, &s_ok))) break;
+    for (int x = gt; x < 7 * ncol; x += GT) {
+      const int col = x / 7, k = x % 7;
+      const int ds = C.col_slot[col];
+      blk<false>(C, ds)[8 * k] += lambda * Ag[(int64_t)ds * 49 + 8 * k] + eps;
+      y_of<false>(C, col)[k] = -gvec[7 * col_kf[col] + k];
+    }
+    if (!(alive = grid_barrier(gs, &s_ok))) break;
+    bool failed = false;
+    for (int lv = 0; lv < nlev; ++lv) {
+      const int* L0 = C.lvl + 4 * lv;
+      const int ncl = L0[4] - L0[0], nt = L0[7] - L0[3];
+      const bool panel = nt == 0;
+      const int nd = panel ? ncl : (ncl + 3) / 4;
+      const int f0 = lv > 0 ? C.lvl[4 * (lv - 1) + 2] : 0, nf = lv > 0 ? L0[1] - f0 : 0;
+      int* fail = gs->fail + (lv & 1);
+      if (panel && ncl == 1) {
+        if (blockIdx.x == 0 && warp < 4) {
+          panel_factor4<false>(C, C.sched[L0[0]], warp, lane, s_xbuf, fail);
+        } else {
+          for (int i = gw - 4; i < 2 * nf; i += GW - 4) update_half<false>(C, C.utask[f0 + i / 2], i & 1, lane);
+        }
+      } else {
+        for (int i = gw; i < nd + 2 * nf; i += GW) {
+          if (i >= nd) update_half<false>(C, C.utask[f0 + (i - nd) / 2], (i - nd) & 1, lane);
+          else if (panel) panel_factor<false>(C, C.sched[L0[0] + i], lane, fail);
+          else diag_factor4<false>(C, C.sched + L0[0] + 4 * i, min(4, ncl - 4 * i), lane, fail);
+        }
+      }
+      // the next level's flag: its last readers passed the previous barrier, its writers
+      // start after this one
+      if (gt == 0) vfail[(lv + 1) & 1] = 0;
+      if (!(alive = grid_barrier(gs, &s_ok))) break;
+      if (vfail[lv & 1]) {
+        // every CTA has read the flag before any can reset it for the next attempt
+        failed = true;
+        alive = grid_barrier(gs, &s_ok);
+        break;
+      }
+      if (!panel) {
+        for (int x = gt; x < 7 * nt; x += GT) trsm_or_inverse<false>(C, L0[3], nt, 7 * nt, L0[0], x);
+        if (!(alive = grid_barrier(gs, &s_ok))) break;
+      }
+      for (int x = gw; x < 2 * (L0[2] - L0[1]); x += GW) update_half<false>(C, C.utask[L0[1] + x / 2], x & 1, lane);
+      // L_cc^{-1} of the level's columns (read only by the back substitution): the last
+      // threads of the grid, which the update tasks leave idle first
+      for (int x = GT - 1 - gt; x < 7 * ncl; x += GT) trsm_or_inverse<false>(C, 0, 0, 0, L0[0], x);
+      if (!(alive = grid_barrier(gs, &s_ok))) break;
+    }
+    if (!alive) break;
+    if (!failed) {
+      const int* L0 = C.lvl + 4 * (nlev - 1);  // far updates of the last level (none in an elimination tree)
+      for (int x = gw; x < 2 * (L0[5] - L0[2]); x += GW) update_half<false>(C, C.utask[L0[2] + x / 2], x & 1, lane);
+      if (!(alive = grid_barrier(gs, &s_ok))) break;
+      ok = true;
+      break;
+    }
+  }
+  if (ok && alive) {
+    for (int lv = nlev - 1; lv >= 0 && alive; --lv) {
+      const int* L0 = C.lvl + 4 * lv;
+      for (int q = L0[0] + gw; q < L0[4]; q += GW) backward_column<false>(C, C.sched[q], lane);
+      alive = grid_barrier(gs, &s_ok);
+    }
+  }
+  bool solved = ok && alive;
+  for (int x = gt; x < 7 * ncol; x += GT) tau[7 * col_kf[x / 7] + x % 7] = solved ? y_of<false>(C, x / 7)[x % 7] : 0.0;
+  // every CTA's tau is written before the stamp; a CTA whose last wait ran out zeroes its
+  // part again (the others then run out too, or had already given up and written zeros)
+  if (alive) alive = grid_barrier(gs, &s_ok);
+  if (solved && !alive) {
+    solved = false;
+    for (int x = gt; x < 7 * ncol; x += GT) tau[7 * col_kf[x / 7] + x % 7] = 0.0;
+  }
+  if (gt == 0) {
+    ginfo[0].attempts = solved ? attempt + 1 : max_attempts;
+    ginfo[0].solved = solved ? 1 : 0;
+    ginfo[0].done_ns = globaltimer_ns();
+    if (!solved) atomicOr(warn, 1);
+  }
+}
+
 // ---- multi-SM solve: one cluster of C CTAs per graph (see ClusterPlan) ----------------
 // Each CTA keeps its columns' blocks and scratch in its shared memory.  Per level: D of the
 // CTA's columns with its far updates of the previous level, then its off-diagonal solves
@@ -762,6 +935,35 @@ size_t factor_solve_max_smem() {
   // static shared memory of the kernels: flags and the panel hand-over buffer
   const int reserve = 64 + (int)sizeof(double) * kPanelXchg;
   return optin > reserve ? (size_t)optin - reserve : 0;
+}
+
+int factor_solve_grid_ctas() {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_solve_grid_kernel, kSolveThreads, 0) != cudaSuccess)
+    return 0;
+  return per_sm >= 1 ? sms : 0;  // one CTA per SM: co-resident by construction
+}
+
+cudaError_t launch_factor_solve_grid(int ctas, const SolverPlan& plan, const double* A, double* L, double* colscratch,
+                                     const double* gvec, double* tau, double lambda, double eps0, int max_attempts,
+                                     GraphInfoDev* ginfo, int* warn, GridSync* sync, cudaStream_t s,
+                                     const GraphInfoDev* fixed) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3(kSolveThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, factor_solve_grid_kernel, plan, A, L, colscratch, gvec, tau, lambda, eps0,
+                            max_attempts, ginfo, warn, fixed, sync);
 }
 
 cudaError_t factor_solve_prepare(size_t smem_bytes) {

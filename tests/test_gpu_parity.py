@@ -317,6 +317,51 @@ def test_multi_sm_solve_failure_gives_zero_update(C, tiny, monkeypatch):
     np.testing.assert_array_equal(poses.cpu().numpy(), p)
 
 
+def test_grid_solve_matches_single_cta(C, tiny, mid, monkeypatch):
+    """The grid-wide factorisation (the level task lists over every warp of one CTA per SM,
+    a grid barrier between phases, the factor in global memory) is bitwise the single-CTA
+    solve, and within FP64 tolerance of the oracle's."""
+    monkeypatch.setenv("COMO3R_K1_CFG", "1")  # the same residual kernel in both graphs
+    monkeypatch.setenv("COMO3R_SOLVE_CLUSTER", "0")
+    res = {}
+    for name, prob in (("tiny", tiny), ("mid", mid)):
+        out = {}
+        for grid in ("0", "1"):
+            monkeypatch.setenv("COMO3R_SOLVE_GRID", grid)
+            poses = torch_poses(prob.poses_init)
+            with C.Graph(prob, mode=C.PLAIN_FP64) as g:
+                assert (g.stats()["solve_ctas"] > 1) == (grid == "1")
+                st, trace, info = g.solve(poses, 6)
+            assert info[0]["solved"]
+            out[grid] = (poses.cpu().numpy(), trace)
+        np.testing.assert_array_equal(out["1"][0], out["0"][0])
+        np.testing.assert_array_equal(out["1"][1], out["0"][1])
+        res[name] = out["1"]
+    po, to = O.gn_solve(tiny, tiny.poses_init, 6)
+    assert max(pose_err(res["tiny"][0], po).values()) <= FP64_TOL
+    np.testing.assert_allclose(res["tiny"][1], to, rtol=FP64_TOL)
+
+
+def test_grid_solve_failure_gives_zero_update(C, tiny, monkeypatch):
+    """Every attempt fails in the grid-wide solve too (all CTAs take the decision from the
+    same flag after a grid barrier): the update is zero and the warning is set; the next
+    call on the same graph starts from clean flags."""
+    monkeypatch.setenv("COMO3R_SOLVE_CLUSTER", "0")
+    monkeypatch.setenv("COMO3R_SOLVE_GRID", "1")
+    p = tiny.poses_init.copy()
+    p[3, 7] = 0.0
+    poses = torch_poses(p)
+    with C.Graph(tiny, mode=C.PLAIN_FP64) as g:
+        assert g.stats()["solve_ctas"] > 1
+        st, info = g.gn_step(poses)
+        poses2 = torch_poses(tiny.poses_init)
+        st2, info2 = g.gn_step(poses2)
+    assert st & C.WARN_SOLVE_FAILED
+    assert info[0]["attempts"] == tiny.max_attempts and not info[0]["solved"]
+    np.testing.assert_array_equal(poses.cpu().numpy(), p)
+    assert info2[0]["solved"] and not (st2 & C.WARN_SOLVE_FAILED)
+
+
 @pytest.mark.parametrize("ctas", [0, 4])
 def test_solve_timestamps(C, ctas, monkeypatch):
     """Device-clock stamps of a call: start after the pose upload, each graph's end after

@@ -121,7 +121,9 @@ def test_fp16_team_4x150(C):
     assert trace[-1, 0] < 1e-3 * trace[0, 0]
 
 
-def test_chain_2000_with_loop_closures(C):
+def test_chain_2000_with_loop_closures(C, monkeypatch):
+    """Noise-free recovery of the 2,000-keyframe chain (its factor fits neither one SM nor a
+    cluster: the grid-wide solve), and the grid solve bitwise against the single-CTA one."""
     p = make_cloud_problem(13, [dict(agents=1, n_kf=2000, H=48, W=64, period=100, shift=8, loop=100)],
                            dtype=np.float64, name="chain-2000")
     assert p.num_edges == 1999 + 999 + 19
@@ -131,9 +133,20 @@ def test_chain_2000_with_loop_closures(C):
             stats = g.stats()
             st, trace, info = g.solve(poses, 8)
         assert stats["smem_solve"] == 0  # the factor lives in global memory
+        assert stats["solve_ctas"] > 8   # the grid-wide solve
         assert info[0]["solved"]
         err = pose_err(poses.cpu().numpy(), p.poses_gt)
         assert max(err.values()) <= tol, (mode, err)
+    monkeypatch.setenv("COMO3R_K1_CFG", "1")
+    out = {}
+    for grid in ("0", "1"):
+        monkeypatch.setenv("COMO3R_SOLVE_GRID", grid)
+        poses = dev(p.poses_init)
+        with C.Graph(p, mode=C.PLAIN_FP64) as g:
+            st, trace, info = g.solve(poses, 3)
+        out[grid] = (poses.cpu().numpy(), trace)
+    np.testing.assert_array_equal(out["1"][0], out["0"][0])
+    np.testing.assert_array_equal(out["1"][1], out["0"][1])
 
 
 def test_batch_of_64_uneven_graphs(C):
