@@ -10,7 +10,9 @@ reduction, per-edge reduction, assembly, damped block Cholesky solve with eps
 escalation, retraction) from the perturbed initial poses.  `value` is GN iterations/s of
 the mixed form with inputs resident in HBM; the plain FP64 form is timed beside it.
 `e2e` repeats the mixed measurement through the C ABI with host (pinned) buffers: every
-step uploads the pointmaps and matches and reads the poses back.
+step uploads the pointmaps and matches and reads the poses and cost trace back; two graphs
+are used in turn on two streams (one host thread each), so that one step's upload overlaps
+another step's solve (`e2e.serial`: one graph, one step after the other).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -191,6 +193,63 @@ def measure_batched(C, torch, prob, points, midx, iters: int, reps: int) -> dict
             "ms_per_call": total_ms / reps, "gn_iters_per_s": reps * iters / (total_ms / 1e3),
             "mresiduals_per_s": valid * reps * iters / (total_ms / 1e3) / 1e6, "stages_ms": stages,
             "plan": {k: stats[k] for k in ("items", "chunk", "block", "grid", "levels", "smem_solve", "solve_ctas")}}
+
+
+def pipelined_e2e(C, torch, prob, pts_h, idx_h, iters: int, esteps: int, warmup: int, barrier, max_over_ranks):
+    """End-to-end throughput of two graphs used in turn on two streams, one host thread
+    each: every step uploads its pointmaps and matches from pinned host memory, solves and
+    reads its poses and cost trace back (como3r_solve returns after the readback); one
+    upload at a time holds the host-to-device link, so one graph's upload overlaps the
+    other's solve.  Timed on the device: both streams wait on a
+    start event of the current stream, which waits on both before the end event."""
+    cur = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    graphs = [C.Graph(prob, mode=C.MIXED, points=pts_h, match_idx=idx_h, copy_inputs=True, stream=st)
+              for st in streams]
+    poses = [torch.tensor(prob.poses_init, dtype=torch.float64).pin_memory() for _ in graphs]
+    init = torch.from_numpy(prob.poses_init)
+    per = max(2, (esteps + 1) // 2)
+    errors = []
+    upload = threading.Lock()  # one upload on the link at a time: the two graphs alternate
+
+    def run(k: int, n: int):
+        try:
+            with torch.cuda.stream(streams[k]):
+                for _ in range(n):
+                    poses[k].copy_(init)
+                    with upload:
+                        graphs[k].update_inputs(pts_h, idx_h)
+                        streams[k].synchronize()
+                    graphs[k].solve(poses[k], iters, trace=True)
+        except Exception as e:  # surfaced after the join
+            errors.append(e)
+
+    def both(n: int):
+        ts = [threading.Thread(target=run, args=(k, n)) for k in range(2)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        if errors:
+            raise errors[0]
+
+    both(max(1, min(warmup, 2)))
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cur)
+    for st in streams:
+        st.wait_event(e0)
+    both(per)
+    for st in streams:
+        cur.wait_stream(st)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    for g in graphs:
+        g.close()
+    return 2 * per * iters / (ms / 1e3), 2 * per
 
 
 def measure_cfg5(C, torch, dev, reps: int) -> dict:
@@ -530,9 +589,14 @@ def run_ours(args):
     barrier()
     ems = max_over_ranks(ev0.elapsed_time(ev1))
     ge.close()
-    e2e_value = world * esteps * iters / (ems / 1e3)
+    e2e_serial = world * esteps * iters / (ems / 1e3)
     h2d = pts_h.numel() * pts_h.element_size() + idx_h.numel() * idx_h.element_size() + poses_h.numel() * 8
     d2h = poses_h.numel() * 8 + (iters + 1) * prob.num_graphs * 8
+    # pipelined: two graphs on two streams, each step still uploading its inputs and reading
+    # its poses and cost trace back, so that one step's upload overlaps the other's solve
+    e2e_value, e2e_pipe_steps = pipelined_e2e(C, torch, prob, pts_h, idx_h, iters, esteps, args.warmup, barrier,
+                                              max_over_ranks)
+    e2e_value *= world
 
     # ---- adjoint (gradient of the refined cost w.r.t. per-pixel log-depth and confidence),
     # unrolled through the same iterations, mixed form
@@ -582,6 +646,8 @@ def run_ours(args):
                      "traffic": traffic, "algorithmic_bytes_per_launch": bytes_alg,
                      "k1_ms_per_launch": k1_ms},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "pipeline": "2 graphs on 2 streams (one host thread each), %d steps" % e2e_pipe_steps,
+                "serial": e2e_serial,
                 "steps": esteps},
         "gpu_launches": int(launches),
         "clocks": clocks.summary(tw0, tw1),

@@ -165,8 +165,8 @@ def _dtype_code(np_dtype) -> int:
 
 
 def _torch_stream(stream):
-    if stream is not None:
-        return ctypes.c_void_p(stream)
+    if stream is not None:  # a raw cudaStream_t handle or a torch.cuda.Stream
+        return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
     import torch
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
