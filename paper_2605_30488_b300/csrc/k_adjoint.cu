@@ -247,8 +247,8 @@ __device__ __forceinline__ void ad_transpose_apply(const double* xi, const doubl
   out[6] = -(v0 * y0 + v1 * y1 + v2 * y2);
 }
 
-// Per edge (one warp; FP64 costs ~20 cycles per warp instruction, so work is spread
-// over lanes): Ad-rotated adjoint and step differences for the match kernel,
+// Per edge (one warp; an FP64 warp instruction holds its SM sub-partition's FP64 unit
+// ~80 cycles however many lanes it uses, so work is spread over lanes): Ad-rotated adjoint and step differences for the match kernel,
 // u~ = Ad (u_j - u_i), tau~ = Ad (tau_j - tau_i), stored in R (16 per edge).
 template <typename R>
 __global__ void adjoint_edge_prep_kernel(const EdgeStatic* __restrict__ es, int E, const double* __restrict__ Ad,

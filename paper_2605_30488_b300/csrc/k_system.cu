@@ -12,8 +12,9 @@ namespace {
 
 // ---- K0: per edge T_ij (FP64 and its FP32 rounding) and Ad_{T_i^{-1}}
 // One warp per edge, SIMD across lanes: lanes 0 and 1 expand the two quaternions, lanes
-// 0..11 form the twelve entries of T_ij and all lanes the 49 entries of Ad.  (FP64 issues
-// ~20 cycles per warp instruction, so the instruction count of a warp is its duration.)
+// 0..11 form the twelve entries of T_ij and all lanes the 49 entries of Ad.  (An FP64 warp
+// instruction holds its SM sub-partition's FP64 unit ~80 cycles whatever its lane count,
+// so the instruction count of a warp is its duration.)
 __global__ void edge_prep_kernel(const double* __restrict__ poses, const EdgeStatic* __restrict__ es, int E,
                                  double* __restrict__ T64, float* __restrict__ T32, double* __restrict__ Ad) {
   __shared__ double sh[2][13];  // R (row-major), t, s of keyframe i (row 0) and j (row 1)

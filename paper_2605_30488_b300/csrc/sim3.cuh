@@ -59,8 +59,9 @@ static __device__ const ExpSeriesTables kExpSeriesG = build_exp_series_tables();
 
 // A, B, C and e^zeta.  Near the origin the series are evaluated in Horner form: for every
 // power a of zeta the polynomial in theta^2 is an independent chain, then one chain in
-// zeta combines them, and e^zeta = 1 + zeta A (exact to rounding there).  FP64 on this GPU
-// costs ~20 cycles per warp instruction per SM, so the instruction count matters.
+// zeta combines them, and e^zeta = 1 + zeta A (exact to rounding there).  An FP64 warp
+// instruction on this GPU holds its SM sub-partition's FP64 unit ~80 cycles, so the
+// instruction count matters.
 __device__ __forceinline__ void exp_coefficients(double theta2, double zeta, double& A, double& B, double& C,
                                                  double& ez) {
   const double rho2 = theta2 + zeta * zeta;
