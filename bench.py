@@ -55,10 +55,10 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-sample-edges", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["all", "mixed", "gauge", "depth", "cfg5"], default="all",
-                    help="mixed: time only the resident mixed form; gauge / depth / cfg5: only the gauge "
-                         "synchronisation / the structure refinement / the 64-graph batch and the "
-                         "2,000-keyframe chain (profiling runs)")
+    ap.add_argument("--only", choices=["all", "mixed", "gauge", "depth", "cfg5", "front"], default="all",
+                    help="mixed: time only the resident mixed form; gauge / depth / cfg5 / front: only the "
+                         "gauge synchronisation / the structure refinement / the 64-graph batch and the "
+                         "2,000-keyframe chain / the front-end kernels (profiling runs)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-graph batch and the 2,000-keyframe chain (per-graph latency)")
     ap.add_argument("--batch-reps", type=int, default=3)
@@ -350,8 +350,8 @@ def measure_front(C, torch, reps: int = 20) -> dict:
     (shared-canvas generator, seed 82, 1 % noise): projective ray matching of all 196,608
     pixels of a keyframe into the frame (start = same pixel), and confidence-weighted
     fusion of one prediction into the keyframe's map (FP32: read 2 x 16 B, write 16 B per
-    pixel)."""
-    from oracle import como3r_oracle as O  # only to express the queries in the frame's camera
+    pixel), one keyframe per call and 80 keyframes in one packed call."""
+    from oracle import como3r_oracle as O  # only to express the queries and poses
     from synth import make_cloud_problem
     p = make_cloud_problem(82, [dict(agents=1, n_kf=3, H=384, W=512, period=40, shift=51, n_inter=0, noise=0.01,
                                      outlier=0.0)], dtype=np.float32)
@@ -384,12 +384,35 @@ def measure_front(C, torch, reps: int = 20) -> dict:
     fuse_ms = ev0.elapsed_time(ev1) / reps
     peak, _ = measured_hbm_peak()
     fuse_gbs = 48 * P / (fuse_ms / 1e3) / 1e9
+    # many keyframes per call: the 80 maps of a 2 x 40 team at 512 x 384 (FP32, 755 MB of
+    # reads and writes per call, far beyond L2), each fused with its own pose
+    nk = 80
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    bc = torch.rand((nk * P, 4), device="cuda", generator=gen) + torch.tensor([0.0, 0.0, 5.0, 1.0], device="cuda")
+    bp = torch.rand((nk * P, 4), device="cuda", generator=gen) + torch.tensor([0.0, 0.0, 5.0, 0.5], device="cuda")
+    rng = np.random.default_rng(8)
+    bT = np.stack([O.matrix_to_pose(O.exp_sim3(np.concatenate([rng.normal(size=3), 0.3 * rng.normal(size=3),
+                                                                [0.05 * rng.normal()]]))) for _ in range(nk)])
+    boff = np.arange(nk + 1, dtype=np.int64) * P
+    C.fuse_packed(bc, bp, boff, bT)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        C.fuse_packed(bc, bp, boff, bT)
+    ev1.record()
+    ev1.synchronize()
+    packed_ms = ev0.elapsed_time(ev1) / reps
+    packed_gbs = 48 * nk * P / (packed_ms / 1e3) / 1e9
+    del bc, bp
     return {"pixels": P, "match_ms": match_ms, "mqueries_per_s": P / (match_ms / 1e3) / 1e6,
             "valid_fraction": float((m >= 0).float().mean().item()),
             "match_bound": "latency (a dependent walk on the ray image; the image stays in L2)",
             "fuse_ms": fuse_ms, "fuse_roofline": {"bound": "hbm", "achieved": fuse_gbs, "peak": peak,
                                                   "unit": "GB/s", "frac": fuse_gbs / peak,
-                                                  "algorithmic_bytes_per_launch": 48 * P}}
+                                                  "algorithmic_bytes_per_launch": 48 * P},
+            "fuse_packed": {"keyframes": nk, "ms": packed_ms,
+                            "roofline": {"bound": "hbm", "achieved": packed_gbs, "peak": peak, "unit": "GB/s",
+                                         "frac": packed_gbs / peak, "algorithmic_bytes_per_launch": 48 * nk * P}}}
 
 
 def oracle_sample(prob, n_edges: int, offset: int = 0):
@@ -478,6 +501,11 @@ def run_ours(args):
     from paper_2605_30488_b300 import como3r as C
     from synth import make_workload
 
+    if args.only == "front":
+        if rank == 0:
+            print(json.dumps({"front_end": measure_front(C, torch), "note": "profiling run (--only front)"}),
+                  flush=True)
+        return
     if args.only == "cfg5":
         if rank == 0:
             cfg5 = measure_cfg5(C, torch, torch.device("cuda", local_rank), args.batch_reps)

@@ -435,6 +435,17 @@ int como3r_project_match(const como3r_match_desc* desc, int32_t* match, float* d
 int como3r_fuse(void* canon, const void* pred, int64_t num_pixels, int32_t dtype, const double* T_kf,
                 void* cuda_stream);
 
+/* Fusion of many keyframes in one launch (Eq. (fusion) as in como3r_fuse, pixel for pixel
+ * the same results): keyframe q owns rows pix_off[q] .. pix_off[q+1]-1 of the packed canon
+ * (in/out) and pred device arrays and is fused with its own pose T_kf[8q .. 8q+7].
+ * pix_off host int64 [n+1], non-decreasing from 0; T_kf host [n][8]; n >= 0.  The
+ * transforms travel as kernel parameters (128 keyframes per launch), so nothing is
+ * allocated.  dtype COMO3R_F32 or COMO3R_F64.  Asynchronous on `cuda_stream`.
+ * Errors: INVALID_ARG (bad offsets, NULL pointers, a zero quaternion), UNSUPPORTED (FP16),
+ * CUDA. */
+int como3r_fuse_packed(void* canon, const void* pred, const int64_t* pix_off, const double* T_kf, int32_t n,
+                       int32_t dtype, void* cuda_stream);
+
 /* Human-readable text of a status code. */
 const char* como3r_status_str(int code);
 

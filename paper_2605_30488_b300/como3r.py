@@ -117,6 +117,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.como3r_depth_refine.argtypes = [vp, vp, vp, ctypes.c_int32, _f64p, vp, ctypes.POINTER(ctypes.c_float)]
     lib.como3r_project_match.argtypes = [ctypes.POINTER(MatchDesc), vp, vp, vp]
     lib.como3r_fuse.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int32, _f64p, vp]
+    lib.como3r_fuse_packed.argtypes = [vp, vp, _i64p, _f64p, ctypes.c_int32, ctypes.c_int32, vp]
     lib.como3r_status_str.argtypes = [ctypes.c_int]
     lib.como3r_status_str.restype = ctypes.c_char_p
     lib.como3r_last_error.argtypes = []
@@ -498,6 +499,18 @@ def project_match(frame_points, H: int, W: int, query_points, dtype: int = F32, 
     _check(lib().como3r_project_match(ctypes.byref(d), _ptr(match), _ptr(dist), _torch_stream(stream)),
            "project_match")
     return (match, dist) if with_dist else match
+
+
+def fuse_packed(canon, pred, pix_off, T_kf, dtype: int = F32, stream=None):
+    """como3r_fuse_packed: every keyframe q (rows pix_off[q] .. pix_off[q+1]-1 of the packed
+    canon / pred CUDA tensors) fused in place with its own pose T_kf[q] (one launch per 128)."""
+    off = np.ascontiguousarray(np.asarray(pix_off, dtype=np.int64))
+    T = np.ascontiguousarray(np.asarray(T_kf, dtype=np.float64).reshape(-1, 8))
+    if T.shape[0] != off.shape[0] - 1:
+        raise ValueError("T_kf needs one pose per keyframe of pix_off")
+    _check(lib().como3r_fuse_packed(_ptr(canon), _ptr(pred), off.ctypes.data_as(_i64p), T.ctypes.data_as(_f64p),
+                                    int(T.shape[0]), int(dtype), _torch_stream(stream)), "fuse_packed")
+    return canon
 
 
 def fuse(canon, pred, T_kf, dtype: int = F32, stream=None):

@@ -14,7 +14,8 @@
 // in L2 while the queries walk); match_kernel is one thread per query.
 //
 // Fusion (Eq. fusion): X_k <- (C_k X_k + C_f (T_kf X_f)) / (C_k + C_f), C_k <- C_k + C_f,
-// one thread per pixel, in the storage type's precision (FP32 or FP64).
+// one thread per pixel, in the storage type's precision (FP32 or FP64); como3r_fuse_packed
+// fuses many keyframes (each with its own T_kf) in one launch, pixel for pixel the same.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -103,22 +104,53 @@ __global__ void match_kernel(const float4* __restrict__ rays, int H, int W, cons
   if (dist) dist[t] = dcur;
 }
 
+// One pixel of the fusion; m = (s R row-major, t) of T_kf in the storage precision.
 template <typename T, typename V4>
-__global__ void fuse_kernel(V4* __restrict__ canon, const V4* __restrict__ pred, int64_t n, T r00, T r01, T r02, T r10,
-                            T r11, T r12, T r20, T r21, T r22, T t0, T t1, T t2) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    V4 a = canon[p];
-    const V4 b = pred[p];
-    const T y0 = r00 * b.x + r01 * b.y + r02 * b.z + t0;
-    const T y1 = r10 * b.x + r11 * b.y + r12 * b.z + t1;
-    const T y2 = r20 * b.x + r21 * b.y + r22 * b.z + t2;
-    const T c = a.w + b.w;
-    a.x = (a.w * a.x + b.w * y0) / c;
-    a.y = (a.w * a.y + b.w * y1) / c;
-    a.z = (a.w * a.z + b.w * y2) / c;
-    a.w = c;
-    canon[p] = a;
-  }
+__device__ __forceinline__ void fuse_pixel(V4* __restrict__ canon, const V4* __restrict__ pred, int64_t p,
+                                           const T (&m)[12]) {
+  V4 a = canon[p];
+  const V4 b = pred[p];
+  const T y0 = m[0] * b.x + m[1] * b.y + m[2] * b.z + m[9];
+  const T y1 = m[3] * b.x + m[4] * b.y + m[5] * b.z + m[10];
+  const T y2 = m[6] * b.x + m[7] * b.y + m[8] * b.z + m[11];
+  const T c = a.w + b.w;
+  a.x = (a.w * a.x + b.w * y0) / c;
+  a.y = (a.w * a.y + b.w * y1) / c;
+  a.z = (a.w * a.z + b.w * y2) / c;
+  a.w = c;
+  canon[p] = a;
+}
+
+template <typename T>
+struct FuseOne {
+  T m[12];
+};
+
+template <typename T, typename V4>
+__global__ void fuse_kernel(V4* __restrict__ canon, const V4* __restrict__ pred, int64_t n, FuseOne<T> f) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x)
+    fuse_pixel<T, V4>(canon, pred, p, f.m);
+}
+
+// Many keyframes per launch: blockIdx.y is the keyframe within the batch, blockIdx.x strides
+// over its pixels; the transforms and offsets travel as kernel parameters.
+constexpr int kFuseBatch = 128;
+template <typename T>
+struct FuseBatch {
+  int64_t off[kFuseBatch + 1];
+  T m[kFuseBatch][12];
+};
+
+template <typename T, typename V4>
+__global__ void fuse_packed_kernel(V4* __restrict__ canon, const V4* __restrict__ pred, FuseBatch<T> b) {
+  const int q = blockIdx.y;
+  const int64_t p1 = b.off[q + 1];
+  T m[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) m[k] = b.m[q][k];
+  for (int64_t p = b.off[q] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1;
+       p += (int64_t)gridDim.x * blockDim.x)
+    fuse_pixel<T, V4>(canon, pred, p, m);
 }
 
 int grid_for_n(int64_t n) {
@@ -159,6 +191,54 @@ extern "C" int como3r_project_match(const como3r_match_desc* d, int32_t* match, 
   return COMO3R_OK;
 }
 
+namespace {
+
+// T_kf = (t, q, s) -> (s R row-major, t) in FP64 on the host, then rounded to the storage
+// precision; false for a zero (or non-finite) quaternion.
+template <typename T>
+bool fuse_transform(const double* T_kf, T (&m)[12]) {
+  const double qx = T_kf[3], qy = T_kf[4], qz = T_kf[5], qw = T_kf[6];
+  const double nq = std::sqrt(qx * qx + qy * qy + qz * qz + qw * qw);
+  if (!(nq > 0.0)) return false;
+  const double x = qx / nq, y = qy / nq, z = qz / nq, w = qw / nq, sc = T_kf[7];
+  const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w),
+                       2 * (x * y + z * w),     1 - 2 * (x * x + z * z), 2 * (y * z - x * w),
+                       2 * (x * z - y * w),     2 * (y * z + x * w),     1 - 2 * (x * x + y * y)};
+  for (int k = 0; k < 9; ++k) m[k] = (T)(sc * R[k]);
+  for (int k = 0; k < 3; ++k) m[9 + k] = (T)T_kf[k];
+  return true;
+}
+
+template <typename T, typename V4>
+int fuse_packed_typed(void* canon, const void* pred, const int64_t* pix_off, const double* T_kf, int n,
+                      cudaStream_t s) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int q0 = 0; q0 < n; q0 += kFuseBatch) {
+    const int nb = std::min(kFuseBatch, n - q0);
+    FuseBatch<T> b{};
+    int64_t longest = 0;
+    for (int q = 0; q <= nb; ++q) b.off[q] = pix_off[q0 + q];
+    for (int q = 0; q < nb; ++q) {
+      if (!fuse_transform<T>(T_kf + 8 * (int64_t)(q0 + q), b.m[q]))
+        return report_error(COMO3R_ERR_INVALID_ARG, "a T_kf has a zero quaternion");
+      longest = std::max(longest, b.off[q + 1] - b.off[q]);
+    }
+    if (longest == 0) continue;
+    // about four resident waves of 256-thread blocks over the batch, at most one block per
+    // 256 pixels of the longest keyframe
+    const int64_t want = std::max<int64_t>(1, (int64_t)sms * 16 / nb);
+    const int gx = (int)std::min<int64_t>(want, (longest + 255) / 256);
+    fuse_packed_kernel<T, V4><<<dim3(gx, nb), 256, 0, s>>>(static_cast<V4*>(canon), static_cast<const V4*>(pred), b);
+    const cudaError_t e = cudaGetLastError();
+    if (e) return report_cuda_error(e, "fuse_packed");
+  }
+  return COMO3R_OK;
+}
+
+}  // namespace
+
 extern "C" int como3r_fuse(void* canon, const void* pred, int64_t num_pixels, int32_t dtype, const double* T_kf,
                            void* cuda_stream) {
   if (num_pixels < 0) return report_error(COMO3R_ERR_INVALID_ARG, "num_pixels must be >= 0");
@@ -166,26 +246,35 @@ extern "C" int como3r_fuse(void* canon, const void* pred, int64_t num_pixels, in
   if (!canon || !pred || !T_kf) return report_error(COMO3R_ERR_INVALID_ARG, "canon, pred and T_kf must be non-NULL");
   if (dtype != COMO3R_F32 && dtype != COMO3R_F64)
     return report_error(COMO3R_ERR_UNSUPPORTED, "fusion keeps a running average: FP32 or FP64 storage");
-  // T_kf = (t, q, s) -> s R and t on the host (FP64)
-  const double qx = T_kf[3], qy = T_kf[4], qz = T_kf[5], qw = T_kf[6];
-  const double nq = std::sqrt(qx * qx + qy * qy + qz * qz + qw * qw);
-  if (!(nq > 0.0)) return report_error(COMO3R_ERR_INVALID_ARG, "T_kf has a zero quaternion");
-  const double x = qx / nq, y = qy / nq, z = qz / nq, w = qw / nq, sc = T_kf[7];
-  const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w),
-                       2 * (x * y + z * w),     1 - 2 * (x * x + z * z), 2 * (y * z - x * w),
-                       2 * (x * z - y * w),     2 * (y * z + x * w),     1 - 2 * (x * x + y * y)};
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   const int g = grid_for_n(num_pixels);
-  if (dtype == COMO3R_F32)
-    fuse_kernel<float, float4><<<g, 256, 0, s>>>(
-        static_cast<float4*>(canon), static_cast<const float4*>(pred), num_pixels, (float)(sc * R[0]),
-        (float)(sc * R[1]), (float)(sc * R[2]), (float)(sc * R[3]), (float)(sc * R[4]), (float)(sc * R[5]),
-        (float)(sc * R[6]), (float)(sc * R[7]), (float)(sc * R[8]), (float)T_kf[0], (float)T_kf[1], (float)T_kf[2]);
-  else
-    fuse_kernel<double, double4><<<g, 256, 0, s>>>(
-        static_cast<double4*>(canon), static_cast<const double4*>(pred), num_pixels, sc * R[0], sc * R[1], sc * R[2],
-        sc * R[3], sc * R[4], sc * R[5], sc * R[6], sc * R[7], sc * R[8], T_kf[0], T_kf[1], T_kf[2]);
+  if (dtype == COMO3R_F32) {
+    FuseOne<float> f;
+    if (!fuse_transform<float>(T_kf, f.m)) return report_error(COMO3R_ERR_INVALID_ARG, "T_kf has a zero quaternion");
+    fuse_kernel<float, float4><<<g, 256, 0, s>>>(static_cast<float4*>(canon), static_cast<const float4*>(pred),
+                                                  num_pixels, f);
+  } else {
+    FuseOne<double> f;
+    if (!fuse_transform<double>(T_kf, f.m)) return report_error(COMO3R_ERR_INVALID_ARG, "T_kf has a zero quaternion");
+    fuse_kernel<double, double4><<<g, 256, 0, s>>>(static_cast<double4*>(canon), static_cast<const double4*>(pred),
+                                                    num_pixels, f);
+  }
   const cudaError_t e = cudaGetLastError();
   if (e) return report_cuda_error(e, "fuse");
   return COMO3R_OK;
+}
+
+extern "C" int como3r_fuse_packed(void* canon, const void* pred, const int64_t* pix_off, const double* T_kf,
+                                  int32_t n, int32_t dtype, void* cuda_stream) {
+  if (n < 0 || !pix_off) return report_error(COMO3R_ERR_INVALID_ARG, "n must be >= 0 and pix_off non-NULL");
+  if (pix_off[0] != 0) return report_error(COMO3R_ERR_INVALID_ARG, "pix_off[0] must be 0");
+  for (int q = 0; q < n; ++q)
+    if (pix_off[q + 1] < pix_off[q]) return report_error(COMO3R_ERR_INVALID_ARG, "pix_off must be non-decreasing");
+  if (n == 0 || pix_off[n] == 0) return COMO3R_OK;
+  if (!canon || !pred || !T_kf) return report_error(COMO3R_ERR_INVALID_ARG, "canon, pred and T_kf must be non-NULL");
+  if (dtype != COMO3R_F32 && dtype != COMO3R_F64)
+    return report_error(COMO3R_ERR_UNSUPPORTED, "fusion keeps a running average: FP32 or FP64 storage");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (dtype == COMO3R_F32) return fuse_packed_typed<float, float4>(canon, pred, pix_off, T_kf, n, s);
+  return fuse_packed_typed<double, double4>(canon, pred, pix_off, T_kf, n, s);
 }

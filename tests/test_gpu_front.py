@@ -91,3 +91,53 @@ def test_fuse_matches_oracle(C):
     with pytest.raises(C.Como3rError):
         C.fuse(torch.zeros((4, 4), dtype=torch.float16, device="cuda"),
                torch.zeros((4, 4), dtype=torch.float16, device="cuda"), O.matrix_to_pose(T), dtype=C.F16)
+
+
+def test_fuse_packed_matches_single_calls(C):
+    """Many keyframes in one call (each with its own T_kf, uneven sizes, an empty one, more
+    keyframes than one launch takes): bit for bit the per-keyframe como3r_fuse, and the
+    oracle's fusion within FP32 / FP64 rounding."""
+    import torch
+    rng = np.random.default_rng(3)
+    for n in (5, 130):
+        sizes = rng.integers(0, 3000, size=n)
+        sizes[1] = 0
+        off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        P = int(off[-1])
+        X = rng.normal(size=(P, 3)) + np.array([0, 0, 5.0])
+        canon = np.concatenate([X, rng.uniform(1, 5, (P, 1))], 1)
+        pred = np.concatenate([rng.normal(size=(P, 3)), rng.uniform(0.5, 3, (P, 1))], 1)
+        Ts = [O.exp_sim3(np.concatenate([rng.normal(size=3), rng.normal(size=3) * 0.4, [0.1 * rng.normal()]]))
+              for _ in range(n)]
+        poses = np.stack([O.matrix_to_pose(T) for T in Ts])
+        for dt, code, tol in ((np.float32, C.F32, 2e-6), (np.float64, C.F64, 1e-13)):
+            c0 = torch.from_numpy(canon.astype(dt)).cuda()
+            pr = torch.from_numpy(pred.astype(dt)).cuda()
+            packed = c0.clone()
+            C.fuse_packed(packed, pr, off, poses, dtype=code)
+            single = c0.clone()
+            for q in range(n):
+                a, b = int(off[q]), int(off[q + 1])
+                if b > a:
+                    C.fuse(single[a:b], pr[a:b], poses[q], dtype=code)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(packed.cpu().numpy(), single.cpu().numpy())
+            got = packed.cpu().numpy().astype(np.float64)
+            for q in (0, 2, n - 1):
+                a, b = int(off[q]), int(off[q + 1])
+                if b == a:
+                    continue
+                ref = O.fuse(canon[a:b].astype(dt).astype(np.float64), pred[a:b].astype(dt).astype(np.float64),
+                             Ts[q])
+                assert np.abs(got[a:b] - ref).max() / np.abs(ref).max() <= tol
+    z = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(C.Como3rError):
+        C.fuse_packed(z, z, [0, 2, 1], np.tile(O.matrix_to_pose(np.eye(4)), (2, 1)))  # decreasing offsets
+    bad = np.tile(O.matrix_to_pose(np.eye(4)), (1, 1))
+    bad[0, 3:7] = 0.0
+    with pytest.raises(C.Como3rError):
+        C.fuse_packed(z, z, [0, 4], bad)  # zero quaternion
+    with pytest.raises(C.Como3rError):
+        C.fuse_packed(torch.zeros((4, 4), dtype=torch.float16, device="cuda"),
+                      torch.zeros((4, 4), dtype=torch.float16, device="cuda"), [0, 4],
+                      np.tile(O.matrix_to_pose(np.eye(4)), (1, 1)), dtype=C.F16)
