@@ -168,13 +168,30 @@ __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
       else T[q] = T64[12 * item.edge + q];
     }
     const int32_t* idx = midx + e.idx_off;
+    // a lane's match indices of one chunk: one 16-byte load when the four are in range and
+    // aligned, else one by one (-1 past the item)
+    auto load_idx = [&](int mb, int (&nn)[kDepthUnroll]) {
+      if constexpr (kDepthUnroll == 4) {
+        if (mb + 3 < item.end && (reinterpret_cast<uintptr_t>(idx + mb) & 15u) == 0) {
+          const int4 v = __ldg(reinterpret_cast<const int4*>(idx + mb));
+          nn[0] = v.x; nn[1] = v.y; nn[2] = v.z; nn[3] = v.w;
+          return;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kDepthUnroll; ++u) nn[u] = mb + u < item.end ? __ldg(idx + mb + u) : -1;
+    };
     // each lane takes kDepthUnroll consecutive pixels of the item (streamed loads of a lane
-    // are contiguous; its pixels mostly share one segment, so they add up in the lane)
+    // are contiguous; its pixels mostly share one segment, so they add up in the lane); the
+    // next chunk's indices are in flight while this chunk's records are gathered and used
+    int nxt[kDepthUnroll];
+    load_idx(item.begin + kDepthUnroll * lane, nxt);
     for (int m0 = item.begin; m0 < item.end; m0 += 32 * kDepthUnroll) {
       const int mb = m0 + kDepthUnroll * lane;
       int nn[kDepthUnroll];
 #pragma unroll
-      for (int u = 0; u < kDepthUnroll; ++u) nn[u] = mb + u < item.end ? __ldg(idx + mb + u) : -1;
+      for (int u = 0; u < kDepthUnroll; ++u) nn[u] = nxt[u];
+      if (m0 + 32 * kDepthUnroll < item.end) load_idx(mb + 32 * kDepthUnroll, nxt);
       typename Rec<R>::T ri[kDepthUnroll], rj[kDepthUnroll];
       int si[kDepthUnroll], sj[kDepthUnroll];
 #pragma unroll
