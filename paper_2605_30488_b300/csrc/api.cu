@@ -105,6 +105,7 @@ struct como3r_graph {
   // grid-wide solve of a single large graph (grid_ctas co-resident CTAs), when chosen
   int grid_ctas = 0;
   GridSync* d_gsync = nullptr;
+  unsigned grid_extra = 0;  // COMO3R_GRID_BARRIER_EXTRA: test of the barrier's wait limit
   size_t cluster_smem = 0;
   ClusterPlan cp{};
   cudaGraphExec_t iter_exec = nullptr, eval_exec = nullptr;
@@ -212,7 +213,7 @@ cudaError_t launch_solver(como3r_graph* g, const double* gvec, double* tau, Grap
                           cudaStream_t s, const GraphInfoDev* fixed = nullptr) {
   if (g->grid_ctas > 0)
     return launch_factor_solve_grid(g->grid_ctas, g->sp, g->d_A, g->d_L, g->d_colscratch, gvec, tau, g->lambda,
-                                    g->eps0, g->max_attempts, ginfo, warn, g->d_gsync, s, fixed);
+                                    g->eps0, g->max_attempts, ginfo, warn, g->d_gsync, s, fixed, g->grid_extra);
   if (g->cluster_ctas > 0)
     return launch_factor_solve_cluster(g->plan.G, g->sp, g->cp, g->cluster_smem, g->d_A, gvec, tau, g->lambda,
                                        g->eps0, g->max_attempts, ginfo, warn, s, fixed);
@@ -386,6 +387,8 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
       if ((rc = dalloc(g, &g->d_gsync, 1))) return rc;
       CK(cudaMemsetAsync(g->d_gsync, 0, sizeof(GridSync), g->stream), "memset");
       g->grid_ctas = ctas;
+      // test setting: arrivals that never come, so every barrier wait runs out its limit
+      if (const char* e = getenv("COMO3R_GRID_BARRIER_EXTRA")) g->grid_extra = (unsigned)std::max(0, atoi(e));
     }
   }
   if (g->smem_solve) {

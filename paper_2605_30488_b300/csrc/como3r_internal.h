@@ -212,7 +212,8 @@ cudaError_t factor_solve_prepare(size_t smem_bytes);  // once, before any captur
 // per-level task lists over every warp of `ctas` co-resident CTAs (a cooperative launch),
 // phases separated by a grid barrier on `sync` (zeroed once; it resets itself).  A barrier
 // wait has an iteration limit; when it runs out the kernel sets sync->err, every CTA
-// leaves, and the graph gets the zero update of a failed factorisation.
+// leaves, and the graph gets the zero update of a failed factorisation (extra_arrivals > 0,
+// a test setting only, makes every wait run out that way).
 struct GridSync {
   unsigned count;  // arrivals at the current barrier
   unsigned gen;    // barrier generation
@@ -224,7 +225,7 @@ int factor_solve_grid_ctas();  // CTAs of the grid solve on this GPU (one per SM
 cudaError_t launch_factor_solve_grid(int ctas, const SolverPlan& plan, const double* A, double* L, double* colscratch,
                                      const double* gvec, double* tau, double lambda, double eps0, int max_attempts,
                                      GraphInfoDev* ginfo, int* warn, GridSync* sync, cudaStream_t s,
-                                     const GraphInfoDev* fixed = nullptr);
+                                     const GraphInfoDev* fixed = nullptr, unsigned extra_arrivals = 0);
 cudaError_t launch_retract(const double* tau, double* poses, const uint8_t* frozen, int N, int* iter_counter,
                            cudaStream_t s);
 // ---- adjoint of the refined cost (k_adjoint.cu)

@@ -594,14 +594,16 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
 // SM; the wait has an iteration limit (sync->err, and the solve gives up).
 constexpr unsigned long long kGridSpinLimit = 1ull << 24;  // ~1 s of 64-ns sleeps
 
-__device__ bool grid_barrier(GridSync* gs, int* s_ok) {
+// `extra` arrivals are expected beyond the grid's CTAs: 0 always, except in the test that
+// makes every wait run out (no arrival completes the count).
+__device__ bool grid_barrier(GridSync* gs, int* s_ok, unsigned extra) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vgen = &gs->gen;
     const unsigned g0 = *vgen;
     __threadfence();
     int ok = 1;
-    if (atomicAdd(&gs->count, 1u) == gridDim.x - 1) {
+    if (atomicAdd(&gs->count, 1u) == gridDim.x - 1 + extra) {
       gs->count = 0;
       __threadfence();
       atomicAdd(&gs->gen, 1u);
@@ -627,7 +629,7 @@ __device__ bool grid_barrier(GridSync* gs, int* s_ok) {
 __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
     SolverPlan P, const double* __restrict__ A, double* Lg, double* Sg, const double* __restrict__ gvec,
     double* __restrict__ tau, double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
-    const GraphInfoDev* __restrict__ fixed, GridSync* gs) {
+    const GraphInfoDev* __restrict__ fixed, GridSync* gs, unsigned extra) {
   __shared__ double s_xbuf[kPanelXchg];
   __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -675,14 +677,14 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
     const double eps = eps0 * pow100;
     for (int64_t x = gt; x < (int64_t)nslot * 49; x += GT) C.L[x] = Ag[x];
     if (gt == 0) vfail[0] = 0;
-    if (!(alive = grid_barrier(gs, &s_ok))) break;
+    if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
     for (int x = gt; x < 7 * ncol; x += GT) {
       const int col = x / 7, k = x % 7;
       const int ds = C.col_slot[col];
       blk<false>(C, ds)[8 * k] += lambda * Ag[(int64_t)ds * 49 + 8 * k] + eps;
       y_of<false>(C, col)[k] = -gvec[7 * col_kf[col] + k];
     }
-    if (!(alive = grid_barrier(gs, &s_ok))) break;
+    if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
     bool failed = false;
     for (int lv = 0; lv < nlev; ++lv) {
       const int* L0 = C.lvl + 4 * lv;
@@ -707,28 +709,28 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
       // the next level's flag: its last readers passed the previous barrier, its writers
       // start after this one
       if (gt == 0) vfail[(lv + 1) & 1] = 0;
-      if (!(alive = grid_barrier(gs, &s_ok))) break;
+      if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
       if (vfail[lv & 1]) {
         // every CTA has read the flag before any can reset it for the next attempt
         failed = true;
-        alive = grid_barrier(gs, &s_ok);
+        alive = grid_barrier(gs, &s_ok, extra);
         break;
       }
       if (!panel) {
         for (int x = gt; x < 7 * nt; x += GT) trsm_or_inverse<false>(C, L0[3], nt, 7 * nt, L0[0], x);
-        if (!(alive = grid_barrier(gs, &s_ok))) break;
+        if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
       }
       for (int x = gw; x < 2 * (L0[2] - L0[1]); x += GW) update_half<false>(C, C.utask[L0[1] + x / 2], x & 1, lane);
       // L_cc^{-1} of the level's columns (read only by the back substitution): the last
       // threads of the grid, which the update tasks leave idle first
       for (int x = GT - 1 - gt; x < 7 * ncl; x += GT) trsm_or_inverse<false>(C, 0, 0, 0, L0[0], x);
-      if (!(alive = grid_barrier(gs, &s_ok))) break;
+      if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
     }
     if (!alive) break;
     if (!failed) {
       const int* L0 = C.lvl + 4 * (nlev - 1);  // far updates of the last level (none in an elimination tree)
       for (int x = gw; x < 2 * (L0[5] - L0[2]); x += GW) update_half<false>(C, C.utask[L0[2] + x / 2], x & 1, lane);
-      if (!(alive = grid_barrier(gs, &s_ok))) break;
+      if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
       ok = true;
       break;
     }
@@ -737,14 +739,14 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
     for (int lv = nlev - 1; lv >= 0 && alive; --lv) {
       const int* L0 = C.lvl + 4 * lv;
       for (int q = L0[0] + gw; q < L0[4]; q += GW) backward_column<false>(C, C.sched[q], lane);
-      alive = grid_barrier(gs, &s_ok);
+      alive = grid_barrier(gs, &s_ok, extra);
     }
   }
   bool solved = ok && alive;
   for (int x = gt; x < 7 * ncol; x += GT) tau[7 * col_kf[x / 7] + x % 7] = solved ? y_of<false>(C, x / 7)[x % 7] : 0.0;
   // every CTA's tau is written before the stamp; a CTA whose last wait ran out zeroes its
   // part again (the others then run out too, or had already given up and written zeros)
-  if (alive) alive = grid_barrier(gs, &s_ok);
+  if (alive) alive = grid_barrier(gs, &s_ok, extra);
   if (solved && !alive) {
     solved = false;
     for (int x = gt; x < 7 * ncol; x += GT) tau[7 * col_kf[x / 7] + x % 7] = 0.0;
@@ -951,7 +953,7 @@ int factor_solve_grid_ctas() {
 cudaError_t launch_factor_solve_grid(int ctas, const SolverPlan& plan, const double* A, double* L, double* colscratch,
                                      const double* gvec, double* tau, double lambda, double eps0, int max_attempts,
                                      GraphInfoDev* ginfo, int* warn, GridSync* sync, cudaStream_t s,
-                                     const GraphInfoDev* fixed) {
+                                     const GraphInfoDev* fixed, unsigned extra_arrivals) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)ctas);
   cfg.blockDim = dim3(kSolveThreads);
@@ -963,7 +965,7 @@ cudaError_t launch_factor_solve_grid(int ctas, const SolverPlan& plan, const dou
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, factor_solve_grid_kernel, plan, A, L, colscratch, gvec, tau, lambda, eps0,
-                            max_attempts, ginfo, warn, fixed, sync);
+                            max_attempts, ginfo, warn, fixed, sync, extra_arrivals);
 }
 
 cudaError_t factor_solve_prepare(size_t smem_bytes) {

@@ -362,6 +362,25 @@ def test_grid_solve_failure_gives_zero_update(C, tiny, monkeypatch):
     assert info2[0]["solved"] and not (st2 & C.WARN_SOLVE_FAILED)
 
 
+def test_grid_barrier_wait_limit(C, tiny, monkeypatch):
+    """A grid barrier whose count nothing completes (a test setting expects one arrival that
+    never comes) runs out its wait limit instead of hanging: every CTA leaves, the solve
+    reports the zero update and its warning, and the poses are unchanged."""
+    import time
+    monkeypatch.setenv("COMO3R_SOLVE_CLUSTER", "0")
+    monkeypatch.setenv("COMO3R_SOLVE_GRID", "1")
+    monkeypatch.setenv("COMO3R_GRID_BARRIER_EXTRA", "1")
+    poses = torch_poses(tiny.poses_init)
+    with C.Graph(tiny, mode=C.PLAIN_FP64) as g:
+        assert g.stats()["solve_ctas"] > 1
+        t0 = time.time()
+        st, info = g.gn_step(poses)
+        dt = time.time() - t0
+    assert st & C.WARN_SOLVE_FAILED and not info[0]["solved"]
+    np.testing.assert_array_equal(poses.cpu().numpy(), tiny.poses_init)
+    assert dt < 60, dt
+
+
 @pytest.mark.parametrize("ctas", [0, 4])
 def test_solve_timestamps(C, ctas, monkeypatch):
     """Device-clock stamps of a call: start after the pose upload, each graph's end after
