@@ -117,7 +117,9 @@ typedef struct {
  * it), allocate workspaces, check every match index on the
  * device (-1 <= n < P_j) and autotune the residual kernel's work-item size and launch
  * configuration on this graph's data (a few milliseconds of timed trial launches; the
- * environment variable COMO3R_K1_CFG=<n> restricts the search to configuration n).
+ * environment variables COMO3R_K1_CFG=<n>, COMO3R_K1_CHUNK=<pixels> and
+ * COMO3R_K1_WEIGHTS=<wv>,<wp> restrict the search, and together fix the residual kernel's
+ * schedule, so that two graphs of the same problem round alike).
  * Synchronises the stream.  On error *out is NULL.
  * Errors: INVALID_ARG (bad sizes / ids / indices / parameters), OOM, CUDA. */
 int como3r_graph_create(const como3r_graph_desc* desc, void* cuda_stream, como3r_graph_t* out);

@@ -425,6 +425,10 @@ int autotune_k1(como3r_graph* g) {
   // COMO3R_K1_CFG=<n> restricts the search to one launch configuration (tests, studies)
   const char* force = getenv("COMO3R_K1_CFG");
   const int forced = force ? atoi(force) : -1;
+  // COMO3R_K1_CHUNK=<n> restricts it to work items of n pixels (with COMO3R_K1_CFG and
+  // COMO3R_K1_WEIGHTS the residual kernel's schedule, and so its rounding, is then fixed)
+  const char* force_chunk = getenv("COMO3R_K1_CHUNK");
+  const int forced_chunk = force_chunk ? atoi(force_chunk) : 0;
   // FP64 launches are long (the FP64 pipe bounds them): try two chunk sizes only
   const int nchunks = p.mode == COMO3R_MIXED ? (int)(sizeof(kChunks) / sizeof(kChunks[0])) : 2;
   std::vector<Item> items;
@@ -432,6 +436,7 @@ int autotune_k1(como3r_graph* g) {
   int rc = COMO3R_OK;
   for (int ci = 0; ci < nchunks && !rc; ++ci) {
     const int chunk = kChunks[ci];
+    if (forced_chunk > 0 && chunk != forced_chunk) continue;
     build_items(p, chunk, items, item_off);
     CK(cudaMemcpyAsync(g->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice, g->stream),
        "tune items");

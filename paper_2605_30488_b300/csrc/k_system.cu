@@ -256,8 +256,9 @@ __global__ void export_dense_kernel(int num_slots, const int32_t* __restrict__ s
   }
 }
 
-// One keyframe per warp: the warp evaluates the series coefficients together, lane 0
-// applies the update (see edge_prep_kernel on FP64 instruction counts).
+// One keyframe per warp: the warp evaluates the series coefficients together, and lanes
+// 0..7 apply the update, one pose entry each (see edge_prep_kernel on FP64 instruction
+// counts).
 __global__ void retract_kernel(const double* __restrict__ tau, double* __restrict__ poses,
                                const uint8_t* __restrict__ frozen, int N, int* iter_counter) {
   const int k = blockIdx.x, lane = threadIdx.x;
@@ -270,13 +271,7 @@ __global__ void retract_kernel(const double* __restrict__ tau, double* __restric
   const double th2 = t[3] * t[3] + t[4] * t[4] + t[5] * t[5];
   double A, B, C, ez;
   exp_coefficients_warp(th2, t[6], lane, A, B, C, ez);
-  if (lane != 0) return;
-  double p[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) p[q] = poses[8 * k + q];
-  retract_left_with(t, p, A, B, C, ez);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) poses[8 * k + q] = p[q];
+  retract_left_warp(t, poses + 8 * k, A, B, C, ez, lane);
 }
 
 // Counts entries outside [-1, P_j) (any edge) and valid entries per edge.

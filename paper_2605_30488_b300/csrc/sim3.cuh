@@ -213,6 +213,69 @@ __device__ __forceinline__ void retract_left_with(const double* tau, double* pos
   pose[7] = ez * pose[7];
 }
 
+// pose <- Exp(tau) pose as retract_left_with, eight lanes at once: lanes 0..2 the
+// translation rows, lane 3 the scale, lanes 4..7 the quaternion (x, y, z, w).  Every lane
+// runs the same straight-line code on lane-selected operands (an FP64 warp instruction costs
+// the same whatever the lane count, so the update takes ~1/2 of the one-lane version's
+// instructions).  R(omega) t = t + 2 (qw u + a x u), u = a x t, for the unit quaternion
+// (a, qw) of omega.  All 32 lanes must call it (shuffles); lanes >= 8 write nothing.
+__device__ __forceinline__ void retract_left_warp(const double* tau, double* pose, double A, double B, double C,
+                                                  double ez, int lane) {
+  const double v[3] = {tau[0], tau[1], tau[2]};
+  const double w[3] = {tau[3], tau[4], tau[5]};
+  const double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  double k, qw;  // quaternion of the rotation by omega: (k omega, qw), k = sin(theta/2)/theta
+  if (th2 < 1e-2) {
+    // the two series of retract_left_with in y = -theta^2/4, term for term: 2k on even
+    // lanes, qw on odd lanes
+    const double y = -0.25 * th2;
+    const bool odd = lane & 1;
+    double sr = odd ? 1.0 / 479001600.0 : 0.0;
+    sr = fma(sr, y, odd ? 1.0 / 3628800.0 : 1.0 / 39916800.0);
+    sr = fma(sr, y, odd ? 1.0 / 40320.0 : 1.0 / 362880.0);
+    sr = fma(sr, y, odd ? 1.0 / 720.0 : 1.0 / 5040.0);
+    sr = fma(sr, y, odd ? 1.0 / 24.0 : 1.0 / 120.0);
+    sr = fma(sr, y, odd ? 0.5 : 1.0 / 6.0);
+    sr = fma(sr, y, 1.0);
+    k = 0.5 * __shfl_sync(0xffffffffu, sr, 0);
+    qw = __shfl_sync(0xffffffffu, sr, 1);
+  } else {
+    const double th = sqrt(th2);
+    double sn, cs;
+    sincos(0.5 * th, &sn, &cs);
+    k = sn / th;
+    qw = cs;
+  }
+  const double a[3] = {k * w[0], k * w[1], k * w[2]};
+  const double t[3] = {pose[0], pose[1], pose[2]};
+  const double b[4] = {pose[3], pose[4], pose[5], pose[6]};
+  // translation row r (lanes 0..2; other lanes compute row lane % 3 and drop it)
+  const int r = lane % 3, r1 = r == 2 ? 0 : r + 1, r2 = r == 0 ? 2 : r - 1;
+  const double u[3] = {a[1] * t[2] - a[2] * t[1], a[2] * t[0] - a[0] * t[2], a[0] * t[1] - a[1] * t[0]};
+  const double axu = a[r1] * u[r2] - a[r2] * u[r1];
+  const double rt = fma(2.0, fma(qw, u[r], axu), t[r]);
+  const double c1[3] = {w[1] * v[2] - w[2] * v[1], w[2] * v[0] - w[0] * v[2], w[0] * v[1] - w[1] * v[0]};
+  const double c2 = w[r1] * c1[r2] - w[r2] * c1[r1];
+  const double tn = fma(C, c2, fma(B, c1[r], fma(A, v[r], ez * rt)));
+  // Hamilton product q_omega (x) q, component c = lane - 4 (lanes 4..7), as one chain of
+  // lane-selected products: qw b_c + b_w a_c + a_{c+1} b_{c+2} - a_{c+2} b_{c+1} for x, y, z
+  // and qw b_w - a . b for w
+  const int c = (lane - 4) & 3, cc = c < 3 ? c : 0, c1i = cc == 2 ? 0 : cc + 1, c2i = cc == 0 ? 2 : cc - 1;
+  const bool isw = c == 3;
+  double n = qw * (isw ? b[3] : b[cc]);
+  n = fma(isw ? -a[0] : b[3], isw ? b[0] : a[cc], n);
+  n = fma(isw ? -a[1] : a[c1i], isw ? b[1] : b[c2i], n);
+  n = fma(isw ? -a[2] : -a[c2i], isw ? b[2] : b[c1i], n);
+  double n2 = n * n;  // |q'|^2 over lanes 4..7
+  n2 += __shfl_xor_sync(0xffffffffu, n2, 1);
+  n2 += __shfl_xor_sync(0xffffffffu, n2, 2);
+  const double qn = n * rsqrt(n2);
+  __syncwarp();  // every lane has read the pose before lanes 0..7 overwrite it
+  if (lane < 3) pose[lane] = tn;
+  else if (lane == 3) pose[7] = ez * pose[7];
+  else if (lane < 8) pose[lane - 1] = qn;
+}
+
 // pose <- Exp(tau) pose (one thread).
 __device__ __forceinline__ void retract_left(const double* tau, double* pose) {
   const double th2 = tau[3] * tau[3] + tau[4] * tau[4] + tau[5] * tau[5];

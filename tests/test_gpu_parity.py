@@ -49,6 +49,15 @@ def mid():
                         outlier=0.15, skip_max=4, n_inter=4, exact=False, dtype=np.float32, name="mid")
 
 
+def pin_residual_kernel(monkeypatch):
+    """Fix the residual kernel's autotuned launch configuration, work-item size and schedule
+    weights, so that two graphs of one problem sum the per-match terms in the same grouping
+    (bitwise comparisons of two solver variants)."""
+    monkeypatch.setenv("COMO3R_K1_CFG", "1")
+    monkeypatch.setenv("COMO3R_K1_CHUNK", "1024")
+    monkeypatch.setenv("COMO3R_K1_WEIGHTS", "1,1")
+
+
 def torch_poses(p):
     import torch
     return torch.tensor(p, dtype=torch.float64, device="cuda").contiguous()
@@ -275,7 +284,7 @@ def test_multi_sm_solve_matches_oracle(C, tiny, mid, ctas, monkeypatch):
     them) gives the oracle's FP64 steps and solves, alone and for a batch of graphs."""
     # the residual kernel's configuration is autotuned per graph by timing; pin it so that
     # the two graphs differ only in the solver
-    monkeypatch.setenv("COMO3R_K1_CFG", "1")
+    pin_residual_kernel(monkeypatch)
     for prob in (tiny, mid):
         out = {}
         for c in (0, ctas):
@@ -295,7 +304,8 @@ def test_multi_sm_solve_matches_oracle(C, tiny, mid, ctas, monkeypatch):
         st, trace, info = g.solve(poses, 6)
     assert max(pose_err(poses.cpu().numpy(), po).values()) <= FP64_TOL
     np.testing.assert_allclose(trace, to, rtol=FP64_TOL)
-    monkeypatch.delenv("COMO3R_K1_CFG")  # the mixed batch runs with the autotuned residual kernel
+    for v in ("COMO3R_K1_CFG", "COMO3R_K1_CHUNK", "COMO3R_K1_WEIGHTS"):  # the mixed batch: autotuned
+        monkeypatch.delenv(v)
     batch = make_problem(22, agents=2, n_kf=4, H=24, W=32, f=25.0, n_inter=1, num_graphs=3, name="batch3")
     poses = torch_poses(batch.poses_init)
     with C.Graph(batch, mode=C.MIXED) as g:
@@ -321,7 +331,7 @@ def test_grid_solve_matches_single_cta(C, tiny, mid, monkeypatch):
     """The grid-wide factorisation (the level task lists over every warp of one CTA per SM,
     a grid barrier between phases, the factor in global memory) is bitwise the single-CTA
     solve, and within FP64 tolerance of the oracle's."""
-    monkeypatch.setenv("COMO3R_K1_CFG", "1")  # the same residual kernel in both graphs
+    pin_residual_kernel(monkeypatch)  # the same residual kernel schedule in both graphs
     monkeypatch.setenv("COMO3R_SOLVE_CLUSTER", "0")
     res = {}
     for name, prob in (("tiny", tiny), ("mid", mid)):

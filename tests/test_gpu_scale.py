@@ -137,7 +137,10 @@ def test_chain_2000_with_loop_closures(C, monkeypatch):
         assert info[0]["solved"]
         err = pose_err(poses.cpu().numpy(), p.poses_gt)
         assert max(err.values()) <= tol, (mode, err)
+    # the residual kernel's autotuned schedule pinned: the two graphs differ only in the solver
     monkeypatch.setenv("COMO3R_K1_CFG", "1")
+    monkeypatch.setenv("COMO3R_K1_CHUNK", "1024")
+    monkeypatch.setenv("COMO3R_K1_WEIGHTS", "1,1")
     out = {}
     for grid in ("0", "1"):
         monkeypatch.setenv("COMO3R_SOLVE_GRID", grid)
