@@ -68,3 +68,30 @@ def test_invalid_descriptions_rejected(C, mutate, msg):
         C.plan_stats(p)
     assert ei.value.code == C.ERR_INVALID_ARG
     assert msg in str(ei.value)
+
+
+def test_fuse_packed_arguments_checked_on_the_host(C):
+    """como3r_fuse_packed rejects bad offsets, NULL buffers and FP16 storage before touching
+    the GPU, and an empty batch is a no-op (every case here returns before any CUDA call)."""
+    lib = ctypes.CDLL(C.LIB_PATH)
+    f = lib.como3r_fuse_packed
+    vp, i64p, f64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+    f.argtypes = [vp, vp, i64p, f64p, ctypes.c_int32, ctypes.c_int32, vp]
+    f.restype = ctypes.c_int
+    pose = np.zeros((2, 8))
+    pose[:, 6] = pose[:, 7] = 1.0
+    buf = np.zeros(64, dtype=np.float32)  # stands in for device buffers; never dereferenced here
+
+    def call(off, n, dtype=C.F32, data=True):
+        o = np.ascontiguousarray(np.asarray(off, dtype=np.int64))
+        p = buf.ctypes.data if data else None
+        return f(p, p, o.ctypes.data_as(i64p), pose.ctypes.data_as(f64p), n, dtype, None)
+
+    assert call([0, 0, 0], 2) == C.OK              # nothing to fuse
+    assert call([0], 0) == C.OK                    # no keyframes
+    assert call([0, 4], -1) == C.ERR_INVALID_ARG   # negative count
+    assert call([1, 4], 1) == C.ERR_INVALID_ARG    # offsets must start at 0
+    assert call([0, 4, 2], 2) == C.ERR_INVALID_ARG  # and not decrease
+    assert call([0, 4], 1, data=False) == C.ERR_INVALID_ARG
+    assert call([0, 4], 1, dtype=C.F16) == C.ERR_UNSUPPORTED
+    assert f(buf.ctypes.data, buf.ctypes.data, None, pose.ctypes.data_as(f64p), 1, C.F32, None) == C.ERR_INVALID_ARG
