@@ -99,7 +99,11 @@ def test_vjp_untouched_pixels_have_zero_gradient(C, small):
     assert np.all(gl[untouched] == 0.0) and np.all(gc[untouched] == 0.0)
 
 
-def test_vjp_is_linear_in_upstream_and_returns_final_poses(C, small):
+def test_vjp_is_linear_in_upstream_and_returns_final_poses(C, small, monkeypatch):
+    # two graphs: the residual kernel's autotuned schedule pinned, so that they round alike
+    monkeypatch.setenv("COMO3R_K1_CFG", "1")
+    monkeypatch.setenv("COMO3R_K1_CHUNK", "1024")
+    monkeypatch.setenv("COMO3R_K1_WEIGHTS", "1,1")
     gl1, gc1, loss1, poses1, launches = gpu_grads(C, small, 0, 2, C.VJP_UNROLLED, upstream=1.0)
     gl3, gc3, loss3, poses3, _ = gpu_grads(C, small, 0, 2, C.VJP_UNROLLED, upstream=-3.0)
     np.testing.assert_allclose(gl3, -3.0 * gl1, rtol=1e-6, atol=1e-12 * np.abs(gl1).max())
