@@ -783,19 +783,20 @@ def fuse(canon: np.ndarray, pred: np.ndarray, T_kf: np.ndarray) -> np.ndarray:
 def pose_errors(pa: np.ndarray, pb: np.ndarray, ref_scale: Optional[float] = None) -> Dict[str, float]:
     """Max over keyframes of rotation angle (rad), relative translation and relative scale error.
 
-    Translation error is ||t_a - t_b|| / max(||t_b||, ref), ref = RMS distance of the
-    reference camera centres from their mean unless given.
+    Rotation error is the angle of R_a R_b^T, i.e. ||Log(R_a R_b^T)||, taken as
+    atan2(sin, cos) of the relative rotation (sin from its skew part, cos from its trace),
+    which keeps full relative accuracy at small and near-pi angles alike.  Translation
+    error is ||t_a - t_b|| / max(||t_b||, ref), ref = RMS distance of the reference camera
+    centres from their mean unless given.  Scale error is |s_a / s_b - 1|.
     """
     tb = pb[:, :3]
     ref = ref_scale if ref_scale is not None else float(np.sqrt(((tb - tb.mean(0)) ** 2).sum(1).mean()))
     rot, tra, sca = 0.0, 0.0, 0.0
     for a, b in zip(pa, pb):
-        Ra, Rb = quat_to_rot(a[3:7]), quat_to_rot(b[3:7])
-        c = (np.trace(Ra @ Rb.T) - 1.0) / 2.0
-        rot = max(rot, math.acos(max(-1.0, min(1.0, c))) if c < 0.999999 else
-                  np.linalg.norm(0.5 * np.array([(Ra @ Rb.T)[2, 1] - (Ra @ Rb.T)[1, 2],
-                                                 (Ra @ Rb.T)[0, 2] - (Ra @ Rb.T)[2, 0],
-                                                 (Ra @ Rb.T)[1, 0] - (Ra @ Rb.T)[0, 1]])))
+        M = quat_to_rot(a[3:7]) @ quat_to_rot(b[3:7]).T
+        sin_t = 0.5 * float(np.linalg.norm([M[2, 1] - M[1, 2], M[0, 2] - M[2, 0], M[1, 0] - M[0, 1]]))
+        cos_t = 0.5 * (float(np.trace(M)) - 1.0)
+        rot = max(rot, math.atan2(sin_t, cos_t))
         tra = max(tra, float(np.linalg.norm(a[:3] - b[:3]) / max(np.linalg.norm(b[:3]), ref, 1e-300)))
         sca = max(sca, abs(a[7] / b[7] - 1.0))
     return dict(rot=rot, trans=tra, scale=sca)

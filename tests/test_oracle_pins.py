@@ -729,3 +729,87 @@ def test_fusion_closed_forms():
     Y = rng.normal(size=(50, 3))
     out2 = O.fuse(canon, np.concatenate([Y, np.full((50, 1), 2.0)], 1), np.eye(4))
     np.testing.assert_allclose(out2[:, :3], 0.5 * (X + Y), atol=1e-15)
+
+
+# -------------------------------------------------- pose error reports (parity measure)
+# Every pose comparison of the GPU parity tests goes through O.pose_errors, so its three
+# figures are pinned to constructed pose pairs whose errors are known by construction:
+# a rotation composed from a known rotation vector (library rotation algebra, not the
+# oracle's), a translation moved by a known length, a scale multiplied by a known ratio.
+def _random_poses(rng, n):
+    from scipy.spatial.transform import Rotation
+    p = np.zeros((n, 8))
+    p[:, :3] = rng.normal(size=(n, 3)) * 4.0
+    p[:, 3:7] = Rotation.random(n, random_state=rng.integers(1 << 31)).as_quat()
+    p[:, 7] = rng.uniform(0.5, 2.0, size=n)
+    return p
+
+
+def _unit(rng):
+    u = rng.normal(size=3)
+    return u / np.linalg.norm(u)
+
+
+@pytest.mark.parametrize("theta", [3.1, 2.0, 0.1, 1.5e-3, 1.0e-3, 1e-4, 1e-6, 1e-8])
+def test_pose_errors_known_rotation_angle(theta):
+    """The rotation error is the angle of R_a R_b^T (the reading ||Log(R_a R_b^T)||), to 1e-12
+    relative at any angle, the largest over keyframes; translation and scale are untouched."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(int(theta * 1e9) % 1000 + 7)
+    b = _random_poses(rng, 6)
+    a = b.copy()
+    for l in range(6):
+        ang = theta if l == 4 else theta * 0.25 * (l + 1) / 6
+        a[l, 3:7] = (Rotation.from_rotvec(ang * _unit(rng)) * Rotation.from_quat(b[l, 3:7])).as_quat()
+    err = O.pose_errors(a, b)
+    assert abs(err["rot"] - theta) <= 1e-12 * theta + 1e-15, (err["rot"], theta)
+    assert err["trans"] == 0.0 and err["scale"] == 0.0
+
+
+def test_pose_errors_quaternion_sign_and_identity():
+    """q and -q are one rotation (error 0); equal poses give exactly zero errors."""
+    rng = np.random.default_rng(11)
+    b = _random_poses(rng, 5)
+    assert O.pose_errors(b, b) == dict(rot=0.0, trans=0.0, scale=0.0)
+    a = b.copy()
+    a[:, 3:7] = -a[:, 3:7]
+    assert O.pose_errors(a, b)["rot"] <= 1e-15
+
+
+@pytest.mark.parametrize("delta", [2.5, 1e-3, 1e-9])
+def test_pose_errors_known_translation_offset(delta):
+    """Camera centres at c +/- r e_x, c +/- r e_y have RMS radius r about their mean; a centre
+    moved by delta reports delta / max(||t_b||, r) (relative to the larger of its own norm and
+    the trajectory radius), or delta / max(||t_b||, ref) for a given reference length."""
+    rng = np.random.default_rng(3)
+    r = 3.0
+    for c in (np.zeros(3), np.array([0.0, 0.0, 12.0])):
+        b = _random_poses(rng, 4)
+        b[:, :3] = c + r * np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0]], dtype=float)
+        a = b.copy()
+        a[2, :3] += delta * _unit(rng)
+        a[1, :3] += 0.5 * delta * _unit(rng)
+        want = delta / max(np.hypot(r, c[2]), r)
+        err = O.pose_errors(a, b)
+        # the offset itself is stored to the rounding of coordinates of size ||c|| + r
+        ulp = 8 * np.finfo(float).eps * (np.linalg.norm(c) + r)
+        assert abs(err["trans"] - want) <= 1e-12 * want + ulp / max(np.hypot(r, c[2]), r), (c, err, want)
+        assert err["rot"] == 0.0 and err["scale"] == 0.0
+        err = O.pose_errors(a, b, ref_scale=100.0)
+        assert abs(err["trans"] - delta / 100.0) <= 1e-12 * delta / 100.0 + ulp / 100.0
+    # the translation of an unmoved keyframe does not count, however far the others moved
+    b = _random_poses(rng, 3)
+    assert O.pose_errors(b, b, ref_scale=1.0)["trans"] == 0.0
+
+
+@pytest.mark.parametrize("ratio", [0.3, -0.3, 1e-6, -1e-9])
+def test_pose_errors_known_scale_ratio(ratio):
+    """s_a = s_b (1 + rho) reports |rho|, the largest over keyframes."""
+    rng = np.random.default_rng(5)
+    b = _random_poses(rng, 5)
+    a = b.copy()
+    a[3, 7] = b[3, 7] * (1.0 + ratio)
+    a[0, 7] = b[0, 7] * (1.0 + 0.5 * ratio)
+    err = O.pose_errors(a, b)
+    assert abs(err["scale"] - abs(ratio)) <= 1e-12 * abs(ratio) + 4e-16, (err, ratio)
+    assert err["rot"] == 0.0 and err["trans"] == 0.0
