@@ -147,6 +147,15 @@ int como3r_gn_step(como3r_graph_t graph, double* poses, double* H_out, double* g
 int como3r_solve(como3r_graph_t graph, double* poses, int32_t iters, double* cost_trace,
                  como3r_graph_info* info);
 
+/* The step tau of the last Gauss-Newton iteration of como3r_gn_step or como3r_solve, the
+ * solution of Eq. (normal), (H + lambda diag(H) + eps_r I) tau = -g (Sec. III-D), before
+ * its retraction T_i <- Exp(tau_i) T_i.
+ *   tau_out  [N][7] (host or device), tau = (v, omega, zeta) per keyframe on the flat
+ *            keyframe index; rows of fixed keyframes, and every row of a graph whose six
+ *            attempts all failed, are zero.  Undefined before the first iteration.
+ * Synchronises the graph's stream.  Errors: INVALID_ARG (NULL argument), CUDA. */
+int como3r_last_step(como3r_graph_t graph, double* tau_out);
+
 /* Device-clock stamps (ns, the GPU's %globaltimer) of the last como3r_gn_step or
  * como3r_solve: the moment its first kernel ran (after the pose upload), and for every
  * graph the moment its last damped factorisation and solve (Eq. 7) finished.  In a batch
@@ -261,11 +270,10 @@ int como3r_plan_stats(const como3r_graph_desc* desc, int64_t* stats /* [COMO3R_S
 
 /* ---- Allocation-free linearisation ------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot
- * allocate device memory when they need a linearisation: code running while a CUDA
- * graph is being captured (cudaMalloc is not a capturable operation), real-time loops
- * that must never wait on the allocator, and host frameworks that reserve the whole
- * device memory budget for themselves.  It computes exactly what como3r_linearize
- * writes to edge_out, without a graph handle and without allocating anything: every
+ * allocate device memory when they need a linearisation: real-time loops that must never
+ * wait on the allocator, and host frameworks that reserve the whole device memory budget
+ * for themselves and forbid side allocations.  It computes what como3r_linearize writes
+ * to edge_out, without a graph handle and without allocating anything: every
  * intermediate lives in one fixed device array of COMO3R_NOALLOC_SCRATCH_BYTES that the
  * library declares statically, so every GPU that loads the library holds that memory
  * until the process exits.
@@ -282,7 +290,10 @@ int como3r_plan_stats(const como3r_graph_desc* desc, int64_t* stats /* [COMO3R_S
  * call overwrites what the previous call left there, so calls whose GPU work may
  * overlap (different streams or host threads) race and must be serialised by the
  * caller; the entry point is also not reentrant on the host.  The call synchronises the
- * stream once (to check the match indices) and returns with the rest enqueued. */
+ * stream once (to check the match indices) and returns with the rest enqueued.
+ * Returns OK or an error (como3r_last_error says which).  Unlike como3r_linearize it
+ * does not return COMO3R_WARN_SKIPPED: matches skipped as degenerate or non-finite are
+ * counted only in each edge record's skip slot (entry 58), which the caller reads. */
 #define COMO3R_NOALLOC_MAX_EDGES 2048
 #define COMO3R_NOALLOC_MAX_ITEMS 16384
 #define COMO3R_NOALLOC_MAX_GRAPHS 256

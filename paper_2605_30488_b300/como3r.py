@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.como3r_solve.argtypes = [vp, vp, ctypes.c_int32, _f64p, ctypes.POINTER(GraphInfo)]
     lib.como3r_linearize.argtypes = [vp, vp, vp, _f64p]
     lib.como3r_solve_timestamps.argtypes = [vp, _i64p, _i64p]
+    lib.como3r_last_step.argtypes = [vp, vp]
     lib.como3r_sim3_retract.argtypes = [vp, vp, ctypes.c_int32, vp]
     lib.como3r_update_inputs.argtypes = [vp, vp, vp]
     lib.como3r_time_stages.argtypes = [vp, vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]
@@ -296,6 +297,12 @@ class Graph:
         _check(lib().como3r_solve_timestamps(self.handle, t0.ctypes.data_as(_i64p), done.ctypes.data_as(_i64p)),
                "solve_timestamps")
         return int(t0[0]), done
+
+    def last_step(self, tau_out=None):
+        """como3r_last_step: the step tau [N, 7] of the last iteration (host float64)."""
+        tau = tau_out if tau_out is not None else np.zeros((self.prob.num_kf, 7))
+        _check(lib().como3r_last_step(self.handle, _ptr(tau)), "last_step")
+        return tau
 
     def linearize(self, poses, edge_out=None):
         cost = np.zeros(self.G)

@@ -106,6 +106,7 @@ struct como3r_graph {
   int grid_ctas = 0;
   GridSync* d_gsync = nullptr;
   unsigned grid_extra = 0;  // COMO3R_GRID_BARRIER_EXTRA: test of the barrier's wait limit
+  double* d_diag_shift = nullptr;  // COMO3R_TEST_DIAG_SHIFT: per-graph diagonal shift (tests only)
   size_t cluster_smem = 0;
   ClusterPlan cp{};
   cudaGraphExec_t iter_exec = nullptr, eval_exec = nullptr;
@@ -204,6 +205,7 @@ int enqueue_linearize(como3r_graph* g, cudaStream_t s, double* cost_hist, const 
                      g->d_kf_contrib, g->d_edge_b, g->d_gvec, p.G, g->d_edge_offset, g->d_edge_cost, g->d_edge_skip,
                      g->d_ginfo, cost_hist, iter, g->d_warn, s),
      "assemble");
+  if (g->d_diag_shift) CK(launch_diag_shift(p.G, g->sp, g->d_A, g->d_diag_shift, s), "diag_shift");
   return COMO3R_OK;
 }
 
@@ -342,6 +344,20 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
       (rc = upload(g, &lttask, p.lttask)) || (rc = upload(g, &llvl, p.llvl)))
     return rc;
   g->sp = SolverPlan{meta, col_kf, lcol_slot, lslot_row, lsched, ltri, lutask, lttask, llvl};
+  // test setting COMO3R_TEST_DIAG_SHIFT=<s0>,<s1>,...: graph g's assembled diagonal is
+  // lowered by s_g before every solve (missing entries 0), which makes the first epsilon
+  // attempts fail by construction; off unless the variable is set
+  if (const char* e = getenv("COMO3R_TEST_DIAG_SHIFT")) {
+    std::vector<double> sh(p.G, 0.0);
+    const char* c = e;
+    for (int k = 0; k < p.G && *c; ++k) {
+      char* end = nullptr;
+      sh[k] = strtod(c, &end);
+      if (end == c) return set_error(COMO3R_ERR_INVALID_ARG, "COMO3R_TEST_DIAG_SHIFT: expected numbers separated by commas");
+      c = *end == ',' ? end + 1 : end;
+    }
+    if ((rc = upload(g, &g->d_diag_shift, sh))) return rc;
+  }
   CK(cudaMallocHost(&g->h_ginfo, sizeof(GraphInfoDev) * G), "cudaMallocHost");
   CK(cudaMallocHost(&g->h_warn, sizeof(int)), "cudaMallocHost");
   CK(cudaMemsetAsync(g->d_tau, 0, sizeof(double) * 7 * (size_t)N, g->stream), "memset");
@@ -600,6 +616,15 @@ int como3r_solve(como3r_graph_t g, double* poses, int32_t iters, double* cost_tr
        "trace");
   if ((rc = end_call(g, poses))) return rc;
   return finish_info(g, info);
+}
+
+int como3r_last_step(como3r_graph_t g, double* tau_out) {
+  if (!g) return set_error(COMO3R_ERR_INVALID_ARG, "graph handle is NULL");
+  if (!tau_out) return set_error(COMO3R_ERR_INVALID_ARG, "tau_out is NULL");
+  CK(cudaMemcpyAsync(tau_out, g->d_tau, sizeof(double) * 7 * (size_t)g->plan.N, cudaMemcpyDefault, g->stream),
+     "step out");
+  CK(cudaStreamSynchronize(g->stream), "sync");
+  return COMO3R_OK;
 }
 
 int como3r_solve_timestamps(como3r_graph_t g, int64_t* start_ns, int64_t* done_ns) {

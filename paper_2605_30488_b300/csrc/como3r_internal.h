@@ -207,6 +207,10 @@ cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t
                                 double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s,
                                 const GraphInfoDev* fixed = nullptr);
 size_t factor_solve_max_smem();
+// Test setting only (COMO3R_TEST_DIAG_SHIFT): A_gg -= shift[g] I on every graph's
+// assembled diagonal, launched after the assembly when the setting is given at create.
+cudaError_t launch_diag_shift(int G, const SolverPlan& plan, double* A, const double* shift, cudaStream_t s);
+
 cudaError_t factor_solve_prepare(size_t smem_bytes);  // once, before any capture
 // Grid-wide solve of graph 0 of a one-graph plan with the factor in global memory: the
 // per-level task lists over every warp of `ctas` co-resident CTAs (a cooperative launch),

@@ -968,6 +968,27 @@ cudaError_t launch_factor_solve_grid(int ctas, const SolverPlan& plan, const dou
                             max_attempts, ginfo, warn, fixed, sync, extra_arrivals);
 }
 
+// Test setting only: subtracts shift[g] from every diagonal entry of graph g's assembled
+// system (one CTA per graph), so that a test can make the first attempts of the epsilon
+// escalation fail by construction (an indefinite H - shift I) and check the retried
+// factorisation against the oracle's on the same shifted system.
+__global__ void diag_shift_kernel(SolverPlan P, double* __restrict__ A, const double* __restrict__ shift) {
+  const int g = blockIdx.x;
+  const double sh = shift[g];
+  if (sh == 0.0) return;
+  const int* m = P.meta + kMetaCount * g;
+  const int cbase = m[kMetaColBase], ncol = m[kMetaNCol], sbase = m[kMetaSlotBase];
+  const int* col_slot = P.col_slot + cbase + g;
+  for (int x = threadIdx.x; x < 7 * ncol; x += blockDim.x)
+    A[(int64_t)(sbase + col_slot[x / 7]) * 49 + 8 * (x % 7)] -= sh;
+}
+
+cudaError_t launch_diag_shift(int G, const SolverPlan& plan, double* A, const double* shift, cudaStream_t s) {
+  if (G <= 0) return cudaSuccess;
+  diag_shift_kernel<<<G, 256, 0, s>>>(plan, A, shift);
+  return cudaGetLastError();
+}
+
 cudaError_t factor_solve_prepare(size_t smem_bytes) {
   return cudaFuncSetAttribute(factor_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
