@@ -274,6 +274,12 @@ extern "C" int como3r_fuse_packed(void* canon, const void* pred, const int64_t* 
   if (!canon || !pred || !T_kf) return report_error(COMO3R_ERR_INVALID_ARG, "canon, pred and T_kf must be non-NULL");
   if (dtype != COMO3R_F32 && dtype != COMO3R_F64)
     return report_error(COMO3R_ERR_UNSUPPORTED, "fusion keeps a running average: FP32 or FP64 storage");
+  // every transform is checked before the first launch, so a rejected call leaves canon untouched
+  for (int q = 0; q < n; ++q) {
+    double m[12];
+    if (!fuse_transform<double>(T_kf + 8 * (int64_t)q, m))
+      return report_error(COMO3R_ERR_INVALID_ARG, "a T_kf has a zero quaternion");
+  }
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   if (dtype == COMO3R_F32) return fuse_packed_typed<float, float4>(canon, pred, pix_off, T_kf, n, s);
   return fuse_packed_typed<double, double4>(canon, pred, pix_off, T_kf, n, s);

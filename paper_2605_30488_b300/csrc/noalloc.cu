@@ -1,13 +1,12 @@
 // como3r_linearize_noalloc: per-edge linearisation that allocates no memory.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// linearisation: code that runs inside a region being captured into a CUDA graph (where
-// cudaMalloc is not a legal capture operation), real-time loops that must not stall on
-// the allocator, and host frameworks that own the whole device memory budget and forbid
-// side allocations.  For them this file keeps every intermediate buffer of the
-// linearisation -- per-edge relative poses and adjoints, the residual kernel's work list
-// and per-item records, the per-edge reduction outputs -- in one file-scope device array
-// of fixed size, so the call needs only the caller's inputs and output.
+// linearisation: real-time loops that must not stall on the allocator, and host
+// frameworks that own the whole device memory budget and forbid side allocations.  For
+// them this file keeps every intermediate buffer of the linearisation -- per-edge
+// relative poses and adjoints, the residual kernel's work list and per-item records, the
+// per-edge reduction outputs -- in one file-scope device array of fixed size, so the
+// call needs only the caller's inputs and output.
 //
 // The array lives as long as the library is loaded, on every device that loads it.  Its
 // device address is looked up once per device with cudaGetSymbolAddress (host code may
@@ -89,6 +88,8 @@ bool device_pointer(const void* p) {
 
 bool positive(double x) { return x > 0.0 && x < 1e300; }
 
+int invalid(const char* why) { return report_error(COMO3R_ERR_INVALID_ARG, why); }
+
 }  // namespace
 }  // namespace como3r
 
@@ -96,25 +97,26 @@ using namespace como3r;
 
 extern "C" int como3r_linearize_noalloc(const como3r_graph_desc* d, const double* poses, double* edge_out,
                                         void* cuda_stream) {
-  if (!d || !poses || !edge_out) return COMO3R_ERR_INVALID_ARG;
+  if (!d || !poses || !edge_out) return invalid("desc, poses and edge_out must not be NULL");
   const int G = d->num_graphs;
-  if (G < 1 || G > kMaxGraphs) return COMO3R_ERR_INVALID_ARG;
+  if (G < 1 || G > kMaxGraphs) return invalid("num_graphs must be in [1, COMO3R_NOALLOC_MAX_GRAPHS]");
   if (!d->kf_offset || !d->height || !d->width || !d->edge_offset || !d->edge_i || !d->edge_j || !d->points_conf)
-    return COMO3R_ERR_INVALID_ARG;
+    return invalid("a required array of the description is NULL");
   if (d->copy_inputs || (d->mode != COMO3R_PLAIN_FP64 && d->mode != COMO3R_MIXED) || d->dtype < COMO3R_F16 ||
       d->dtype > COMO3R_F64 || !positive(d->sigma_ray) || !positive(d->sigma_dist) || !positive(d->huber_k))
-    return COMO3R_ERR_INVALID_ARG;
-  if (d->kf_offset[0] != 0 || d->edge_offset[0] != 0) return COMO3R_ERR_INVALID_ARG;
+    return invalid("copy_inputs must be 0; mode, dtype, sigma_ray, sigma_dist and huber_k must be valid");
+  if (d->kf_offset[0] != 0 || d->edge_offset[0] != 0) return invalid("kf_offset[0] and edge_offset[0] must be 0");
   const int E = d->edge_offset[G];
-  if (E < 0 || E > kMaxEdges) return COMO3R_ERR_INVALID_ARG;  // beyond the fixed scratch
+  if (E < 0 || E > kMaxEdges) return invalid("more edges than COMO3R_NOALLOC_MAX_EDGES");  // beyond the scratch
   if (E == 0) return COMO3R_OK;
-  if (!d->match_idx) return COMO3R_ERR_INVALID_ARG;
+  if (!d->match_idx) return invalid("match_idx is NULL");
   // pixel layout: graph g's keyframes each hold height[g] * width[g] pixels
   h_graph_px[0] = 0;
   for (int g = 0; g < G; ++g) {
-    if (d->kf_offset[g + 1] <= d->kf_offset[g] || d->edge_offset[g + 1] < d->edge_offset[g]) return COMO3R_ERR_INVALID_ARG;
+    if (d->kf_offset[g + 1] <= d->kf_offset[g] || d->edge_offset[g + 1] < d->edge_offset[g])
+      return invalid("kf_offset must increase and edge_offset must not decrease");
     if (d->height[g] <= 0 || d->width[g] <= 0 || (int64_t)d->height[g] * d->width[g] >= (int64_t(1) << 30))
-      return COMO3R_ERR_INVALID_ARG;
+      return invalid("height and width must be positive with fewer than 2^30 pixels");
     h_graph_px[g + 1] = h_graph_px[g] + (int64_t)(d->kf_offset[g + 1] - d->kf_offset[g]) * d->height[g] * d->width[g];
   }
   int64_t streamed = 0, idx_off = 0;
@@ -123,7 +125,8 @@ extern "C" int como3r_linearize_noalloc(const como3r_graph_desc* d, const double
     const int32_t P = d->height[g] * d->width[g];
     for (int e = d->edge_offset[g]; e < d->edge_offset[g + 1]; ++e) {
       const int i = d->edge_i[e], j = d->edge_j[e];
-      if (i < k0 || i >= k1 || j < k0 || j >= k1 || i == j) return COMO3R_ERR_INVALID_ARG;
+      if (i < k0 || i >= k1 || j < k0 || j >= k1 || i == j)
+        return invalid("edge endpoints must be two different keyframes of the edge's graph");
       EdgeStatic s{};
       s.pix_i = h_graph_px[g] + (int64_t)(i - k0) * P;
       s.pix_j = h_graph_px[g] + (int64_t)(j - k0) * P;
@@ -140,25 +143,25 @@ extern "C" int como3r_linearize_noalloc(const como3r_graph_desc* d, const double
   // smallest chunk (a multiple of kMinChunk) whose items fit the scratch
   int64_t chunk = kMinChunk;
   const int64_t room = kMaxItems - E;
-  if (room <= 0) return COMO3R_ERR_INVALID_ARG;
+  if (room <= 0) return invalid("more edges than the work-item table holds");
   while ((streamed + chunk - 1) / chunk > room) chunk += kMinChunk;
   int n_items = 0;
   h_item_off[0] = 0;
   for (int e = 0; e < E; ++e) {
     for (int64_t b = 0; b < h_es[e].npix_i; b += chunk) {
-      if (n_items >= kMaxItems) return COMO3R_ERR_INVALID_ARG;
+      if (n_items >= kMaxItems) return invalid("more work items than COMO3R_NOALLOC_MAX_ITEMS");
       h_items[n_items++] = Item{e, (int32_t)b, (int32_t)std::min<int64_t>(b + chunk, h_es[e].npix_i), 0};
     }
     h_item_off[e + 1] = n_items;
   }
   if (!device_pointer(d->points_conf) || !device_pointer(d->match_idx) || !device_pointer(poses) ||
       !device_pointer(edge_out))
-    return COMO3R_ERR_INVALID_ARG;
+    return invalid("points_conf, match_idx, poses and edge_out must be device memory");
   if (reinterpret_cast<uintptr_t>(d->points_conf) % 16 || reinterpret_cast<uintptr_t>(d->match_idx) % 4)
-    return COMO3R_ERR_INVALID_ARG;
+    return invalid("points_conf must be 16-byte and match_idx 4-byte aligned");
 
   unsigned char* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) return COMO3R_ERR_CUDA;
+  if (cudaError_t e = scratch_address(&base)) return report_cuda_error(e, "scratch address");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   auto* es = reinterpret_cast<EdgeStatic*>(base + kOffEs);
   auto* items = reinterpret_cast<Item*>(base + kOffItems);
@@ -183,8 +186,8 @@ extern "C" int como3r_linearize_noalloc(const como3r_graph_desc* d, const double
   if (!err) err = launch_check_matches(d->match_idx, es, E, bad, valid, s);
   if (!err) err = cudaMemcpyAsync(&h_bad, bad, sizeof(h_bad), cudaMemcpyDeviceToHost, s);
   if (!err) err = cudaStreamSynchronize(s);
-  if (err) return COMO3R_ERR_CUDA;
-  if (h_bad) return COMO3R_ERR_INVALID_ARG;  // a match index outside [-1, P_j)
+  if (err) return report_cuda_error(err, "linearize_noalloc match check");
+  if (h_bad) return invalid("a match index lies outside [-1, P_j)");
 
   RobustParams rp{};
   rp.inv_sigma_ray = 1.0 / d->sigma_ray;
@@ -193,8 +196,9 @@ extern "C" int como3r_linearize_noalloc(const como3r_graph_desc* d, const double
   rp.inv_var_dist = 1.0 / (d->sigma_dist * d->sigma_dist);
   rp.kappa = d->huber_k;
   int dev = 0, sms = 1;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return COMO3R_ERR_CUDA;
+  if (cudaError_t e = cudaGetDevice(&dev)) return report_cuda_error(e, "cudaGetDevice");
+  if (cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
+    return report_cuda_error(e, "attribute");
   const int occ = std::max(1, residual_reduce_max_blocks_per_sm(d->mode, d->dtype, 0));
   const int warps_per_cta = residual_reduce_block() / 32;
   const int grid = std::max(1, std::min(sms * occ, (n_items + warps_per_cta - 1) / warps_per_cta));
@@ -202,5 +206,5 @@ extern "C" int como3r_linearize_noalloc(const como3r_graph_desc* d, const double
   if (!err) err = launch_residual_reduce(d->mode, d->dtype, 0, grid, d->points_conf, d->match_idx, items, n_items, es,
                                          T64, T32, rp, records, WarpSched{nullptr, nullptr}, s);
   if (!err) err = launch_edge_reduce(d->mode, records, item_off, E, Ad, M, B, cost, skip, edge_out, valid, s);
-  return err ? COMO3R_ERR_CUDA : COMO3R_OK;
+  return err ? report_cuda_error(err, "linearize_noalloc") : COMO3R_OK;
 }

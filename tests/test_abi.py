@@ -95,3 +95,28 @@ def test_fuse_packed_arguments_checked_on_the_host(C):
     assert call([0, 4], 1, data=False) == C.ERR_INVALID_ARG
     assert call([0, 4], 1, dtype=C.F16) == C.ERR_UNSUPPORTED
     assert f(buf.ctypes.data, buf.ctypes.data, None, pose.ctypes.data_as(f64p), 1, C.F32, None) == C.ERR_INVALID_ARG
+
+
+def test_fuse_packed_checks_every_quaternion_before_any_launch(C):
+    """A zero quaternion in a later batch of 128 keyframes is rejected before the first batch
+    is launched, so a rejected call leaves canon untouched (the buffers below are host
+    memory that no CUDA call may touch: the call must return before any)."""
+    lib = ctypes.CDLL(C.LIB_PATH)
+    f = lib.como3r_fuse_packed
+    vp, i64p, f64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+    f.argtypes = [vp, vp, i64p, f64p, ctypes.c_int32, ctypes.c_int32, vp]
+    f.restype = ctypes.c_int
+    n = 300
+    pose = np.zeros((n, 8))
+    pose[:, 6] = pose[:, 7] = 1.0
+    pose[200, 3:7] = 0.0  # keyframe 200 lies in the second launch batch
+    off = np.arange(n + 1, dtype=np.int64) * 4
+    buf = np.zeros(4 * 4 * n, dtype=np.float32)
+    assert f(buf.ctypes.data, buf.ctypes.data, off.ctypes.data_as(i64p), pose.ctypes.data_as(f64p), n, C.F32,
+             None) == C.ERR_INVALID_ARG
+    assert "quaternion" in lib_last_error(C)
+    assert not buf.any()
+
+
+def lib_last_error(C):
+    return C.lib().como3r_last_error().decode()
