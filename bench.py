@@ -351,13 +351,12 @@ def measure_front(C, torch, reps: int = 20) -> dict:
     pixels of a keyframe into the frame (start = same pixel), and confidence-weighted
     fusion of one prediction into the keyframe's map (FP32: read 2 x 16 B, write 16 B per
     pixel), one keyframe per call and 80 keyframes in one packed call."""
-    from oracle import como3r_oracle as O  # only to express the queries and poses
-    from synth import make_cloud_problem
+    from synth import make_cloud_problem, pose_from_matrix, pose_matrix, random_pose
     p = make_cloud_problem(82, [dict(agents=1, n_kf=3, H=384, W=512, period=40, shift=51, n_inter=0, noise=0.01,
                                      outlier=0.0)], dtype=np.float32)
     P = 384 * 512
     i, j = int(p.edge_i[0]), int(p.edge_j[0])
-    Tji = np.linalg.inv(O.pose_to_matrix(p.poses_init[j])) @ O.pose_to_matrix(p.poses_init[i])
+    Tji = np.linalg.inv(pose_matrix(p.poses_init[j])) @ pose_matrix(p.poses_init[i])
     Xi = p.points[i * P:(i + 1) * P].astype(np.float64)
     q = np.concatenate([Xi[:, :3] @ Tji[:3, :3].T + Tji[:3, 3], Xi[:, 3:4]], 1).astype(np.float32)
     frame = torch.from_numpy(np.ascontiguousarray(p.points[j * P:(j + 1) * P])).cuda()
@@ -373,7 +372,7 @@ def measure_front(C, torch, reps: int = 20) -> dict:
     ev1.synchronize()
     match_ms = ev0.elapsed_time(ev1) / reps
     canon = frame.clone()
-    T = O.matrix_to_pose(np.linalg.inv(Tji))
+    T = pose_from_matrix(np.linalg.inv(Tji))
     C.fuse(canon, qd, T)
     torch.cuda.synchronize()
     ev0.record()
@@ -391,8 +390,7 @@ def measure_front(C, torch, reps: int = 20) -> dict:
     bc = torch.rand((nk * P, 4), device="cuda", generator=gen) + torch.tensor([0.0, 0.0, 5.0, 1.0], device="cuda")
     bp = torch.rand((nk * P, 4), device="cuda", generator=gen) + torch.tensor([0.0, 0.0, 5.0, 0.5], device="cuda")
     rng = np.random.default_rng(8)
-    bT = np.stack([O.matrix_to_pose(O.exp_sim3(np.concatenate([rng.normal(size=3), 0.3 * rng.normal(size=3),
-                                                                [0.05 * rng.normal()]]))) for _ in range(nk)])
+    bT = np.stack([random_pose(rng) for _ in range(nk)])
     boff = np.arange(nk + 1, dtype=np.int64) * P
     C.fuse_packed(bc, bp, boff, bT)
     torch.cuda.synchronize()

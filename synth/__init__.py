@@ -10,7 +10,7 @@ offset and a scale factor.
 from .cloud import make_cloud_problem
 from .cloud_gpu import graph_subproblem, make_cloud_batch_gpu
 from .scene import (Problem, WORKLOADS, make_problem, make_workload, quat_from_matrix,
-                    matrix_from_quat)
+                    matrix_from_quat, pose_matrix, pose_from_matrix, random_pose)
 
 __all__ = ["Problem", "WORKLOADS", "make_problem", "make_workload", "make_cloud_problem", "make_cloud_batch_gpu",
-           "graph_subproblem", "quat_from_matrix", "matrix_from_quat"]
+           "graph_subproblem", "quat_from_matrix", "matrix_from_quat", "pose_matrix", "pose_from_matrix", "random_pose"]

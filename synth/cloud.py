@@ -25,7 +25,9 @@ loop closures, 4 x 150 keyframe teams, batches of dozens of graphs).  Recipe (on
   two decoded directions of a cross-agent candidate).
 * Noise, outliers and confidences as in the ray-cast scenes: points scaled along their
   ray by (1 + noise N(0,1)), a fraction ``outlier`` of each edge's matches redirected to
-  a uniformly drawn pixel of j, confidences lognormal(1, 0.5).
+  a uniformly drawn pixel of j, confidences lognormal(1, 0.5).  With ``band = (lo, hi)``
+  each edge keeps only the matches of a column band of i covering a fraction U[lo, hi]
+  of the image width at a uniformly drawn position (uneven per-edge valid counts).
 * Initial poses: ground truth with a body-frame perturbation (rotation ``pert_rot``,
   offset ``pert_trans``, scale ``pert_scale`` or its inverse); anchors unperturbed.
 """
@@ -62,7 +64,7 @@ def _canvas(rng, Hc: int, Wc: int) -> np.ndarray:
 
 def _graph(rng, *, agents: int, n_kf: int, H: int, W: int, period: int, shift: int, loop: int, n_inter: int,
            noise: float, outlier: float, pert_rot: float, pert_trans: float, pert_scale: float, kf_base: int,
-           dtype=np.float32, reverse_inter: bool = False):
+           dtype=np.float32, reverse_inter: bool = False, band: Optional[Sequence[float]] = None):
     Hc, Wc = H + 2 * shift + 2, W + 2 * shift + 2
     world = _canvas(rng, Hc, Wc).reshape(-1, 3)
     N = agents * n_kf
@@ -135,6 +137,10 @@ def _graph(rng, *, agents: int, n_kf: int, H: int, W: int, period: int, shift: i
             vm = np.nonzero(ok)[0]
             pick = vm[rng.random(vm.size) < outlier]
             out[pick] = rng.integers(0, P, size=pick.size)
+        if band is not None:  # valid-pixel mask: a column band covering U[band] of the image
+            width = max(1, int(round(rng.uniform(band[0], band[1]) * W)))
+            u0 = int(rng.integers(0, W - width + 1))
+            out[(cols < u0) | (cols >= u0 + width)] = -1
         idx.append(out)
     # poses
     gt = np.zeros((N, 8))
@@ -164,10 +170,10 @@ def make_cloud_problem(seed: int = 0, graph_specs: Optional[Sequence[dict]] = No
                        iters: int = 10, name: str = "cloud", **defaults) -> Problem:
     """A batch of shared-canvas graphs (one per entry of ``graph_specs``; keys: agents,
     n_kf, H, W, period, shift, loop, n_inter, noise, outlier, pert_rot, pert_trans,
-    pert_scale)."""
+    pert_scale, reverse_inter, band)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     base = dict(agents=1, n_kf=20, H=48, W=64, period=100, shift=8, loop=0, n_inter=4, noise=0.0, outlier=0.0,
-                pert_rot=0.05, pert_trans=0.1, pert_scale=1.05, reverse_inter=False)
+                pert_rot=0.05, pert_trans=0.1, pert_scale=1.05, reverse_inter=False, band=None)
     base.update(defaults)
     specs = list(graph_specs) if graph_specs is not None else [base]
     parts: List[dict] = []

@@ -97,6 +97,30 @@ def _axis_angle(axis: np.ndarray, angle: float) -> np.ndarray:
     return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * (K @ K)
 
 
+def pose_matrix(p: np.ndarray) -> np.ndarray:
+    """4x4 similarity [sR t; 0 1] of a stored pose (tx, ty, tz, qx, qy, qz, qw, s): the input
+    format, for building queries and fusion transforms on the host."""
+    p = np.asarray(p, dtype=np.float64)
+    T = np.eye(4)
+    T[:3, :3] = p[7] * matrix_from_quat(p[3:7] / np.linalg.norm(p[3:7]))
+    T[:3, 3] = p[:3]
+    return T
+
+
+def pose_from_matrix(T: np.ndarray) -> np.ndarray:
+    """Stored pose (t, q, s) of a 4x4 similarity (s = cube root of det(sR))."""
+    s = float(np.cbrt(np.linalg.det(T[:3, :3])))
+    return np.concatenate([T[:3, 3], quat_from_matrix(T[:3, :3] / s), [s]])
+
+
+def random_pose(rng: np.random.Generator, trans: float = 1.0, rot: float = 0.3, log_scale: float = 0.05) -> np.ndarray:
+    """A stored pose with N(0, trans^2) translation, a rotation of angle |N(0, rot^2)| about a
+    uniform axis and scale exp(N(0, log_scale^2))."""
+    t = rng.normal(size=3) * trans
+    R = _axis_angle(rng.normal(size=3), abs(rng.normal()) * rot)
+    return np.concatenate([t, quat_from_matrix(R), [math.exp(rng.normal() * log_scale)]])
+
+
 def _camera_rotation(yaw: float) -> np.ndarray:
     """Camera-to-world rotation: forward (z) horizontal at `yaw`, down (y) = -world z."""
     fwd = np.array([math.cos(yaw), math.sin(yaw), 0.0])

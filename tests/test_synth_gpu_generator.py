@@ -58,3 +58,25 @@ def test_cfg5_specs():
     assert all(2 <= s["agents"] <= 4 and 10 <= s["n_kf"] <= 200 for s in specs)
     (chain,) = chain2000_spec()
     assert chain["n_kf"] == 2000 and chain["loop"] == 100 and (chain["H"], chain["W"]) == (384, 512)
+
+
+def test_cloud_band_masks_keep_one_column_band_per_edge():
+    """band=(lo, hi): every edge keeps matches only inside one column band of i (valid columns
+    span at most the band, at least lo of the width is kept wherever the unmasked edge had
+    matches everywhere), the pointmaps are unchanged, and the per-edge counts become uneven."""
+    from synth import make_cloud_problem
+    spec = dict(agents=2, n_kf=6, H=24, W=40, period=10, shift=4, n_inter=2, noise=0.01, outlier=0.0)
+    a = make_cloud_problem(3, [spec])
+    b = make_cloud_problem(3, [dict(spec, band=(0.2, 1.0))])
+    np.testing.assert_array_equal(a.points, b.points)
+    P, W = 24 * 40, 40
+    ratios = []
+    for e in range(b.num_edges):
+        ib = b.match_idx[e * P:(e + 1) * P].reshape(24, W)
+        ia = a.match_idx[e * P:(e + 1) * P].reshape(24, W)
+        assert np.all((ib == ia) | (ib == -1))  # without outliers the kept matches are the exact ones
+        cols = np.nonzero((ib >= 0).any(axis=0))[0]
+        if cols.size:
+            assert np.all(np.diff(cols) == 1)  # one contiguous band of columns
+        ratios.append((ib >= 0).sum() / max((ia >= 0).sum(), 1))
+    assert min(ratios) < 0.6 and max(ratios) > 0.6
