@@ -272,11 +272,7 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   CK(cudaGetDevice(&g->device), "cudaGetDevice");
   CK(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device), "attribute");
   CK(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking), "stream create");
-  g->rp.inv_sigma_ray = 1.0 / d->sigma_ray;
-  g->rp.inv_sigma_dist = 1.0 / d->sigma_dist;
-  g->rp.inv_var_ray = 1.0 / (d->sigma_ray * d->sigma_ray);
-  g->rp.inv_var_dist = 1.0 / (d->sigma_dist * d->sigma_dist);
-  g->rp.kappa = d->huber_k;
+  g->rp = make_robust_params(d->sigma_ray, d->sigma_dist, d->huber_k);
   g->lambda = d->lambda;
   g->eps0 = d->eps0;
   g->max_attempts = d->max_attempts;
@@ -749,8 +745,12 @@ int vjp_impl(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t 
   void* gc = plain ? (void*)(g->d_gacc + P) : (void*)grad_conf;
   CK(cudaMemsetAsync(gl, 0, (plain ? sizeof(double) : sizeof(float)) * (size_t)P, s), "memset");
   CK(cudaMemsetAsync(gc, 0, (plain ? sizeof(double) : sizeof(float)) * (size_t)P, s), "memset");
+  // K1's valid-match lists, when its items are small enough to have them
+  const bool lists = g->k1_compact && g->k1_chunk <= kCompactSlot;
+  const int32_t* lcounts = lists ? g->d_counts : nullptr;
+  const uint32_t* lcompact = lists ? g->d_compact : nullptr;
   CK(launch_adjoint_match(p.mode, p.dtype, false, g->points, g->midx, g->d_items, g->num_items, g->d_es, g->d_T64,
-                          g->d_T32, nullptr, g->rp, upstream, gl, gc, nullptr, s),
+                          g->d_T32, nullptr, g->rp, upstream, gl, gc, nullptr, lcounts, lcompact, s),
      "adjoint envelope");
   ++launches;
   CK(mark(2), "event");
@@ -771,7 +771,7 @@ int vjp_impl(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t 
       CK(launch_adjoint_edge_prep(p.mode, g->d_es, E, g->d_Ad, g->d_adj_u, tau_k, g->d_evec, s), "adjoint edge prep");
       CK(mark(4 + 2 * k), "event");
       CK(launch_adjoint_match(p.mode, p.dtype, true, g->points, g->midx, g->d_items, g->num_items, g->d_es, g->d_T64,
-                              g->d_T32, g->d_evec, g->rp, -1.0, gl, gc, g->d_adj_rec, s),
+                              g->d_T32, g->d_evec, g->rp, -1.0, gl, gc, g->d_adj_rec, lcounts, lcompact, s),
          "adjoint match");
       CK(mark(5 + 2 * k), "event");
       CK(launch_adjoint_edge(g->d_adj_rec, g->d_item_off, E, g->d_es, g->d_Ad, g->d_adj_u, tau_k, g->d_edge_adj, s),

@@ -45,7 +45,29 @@ struct RobustParams {          // whitening and Huber constants (Sec. III-A)
   double inv_sigma_ray, inv_sigma_dist;      // 1/sigma_r, 1/sigma_d
   double inv_var_ray, inv_var_dist;          // 1/sigma_r^2, 1/sigma_d^2
   double kappa;
+  // FP32 copies for the mixed form, rounded once on the host: a kernel that converted the
+  // FP64 values itself could have the conversion rematerialised inside its hot loop, where
+  // every FP64-pipe instruction holds the pipe for a whole warp's time
+  float f_inv_sigma_ray, f_inv_sigma_dist, f_inv_var_ray, f_inv_var_dist, f_kappa;
+  float f_kappa_inv_var_ray, f_kappa_inv_var_dist;  // kappa / sigma_r^2, kappa / sigma_d^2
 };
+
+inline RobustParams make_robust_params(double sigma_ray, double sigma_dist, double kappa) {
+  RobustParams rp{};
+  rp.inv_sigma_ray = 1.0 / sigma_ray;
+  rp.inv_sigma_dist = 1.0 / sigma_dist;
+  rp.inv_var_ray = 1.0 / (sigma_ray * sigma_ray);
+  rp.inv_var_dist = 1.0 / (sigma_dist * sigma_dist);
+  rp.kappa = kappa;
+  rp.f_inv_sigma_ray = (float)rp.inv_sigma_ray;
+  rp.f_inv_sigma_dist = (float)rp.inv_sigma_dist;
+  rp.f_inv_var_ray = (float)rp.inv_var_ray;
+  rp.f_inv_var_dist = (float)rp.inv_var_dist;
+  rp.f_kappa = (float)kappa;
+  rp.f_kappa_inv_var_ray = (float)(kappa * rp.inv_var_ray);
+  rp.f_kappa_inv_var_dist = (float)(kappa * rp.inv_var_dist);
+  return rp;
+}
 
 struct GraphInfoDev {          // per graph, written on the device
   double cost;
@@ -237,7 +259,7 @@ constexpr int kAdjointRecord = 21;  // doubles per K1 work item
 cudaError_t launch_adjoint_match(int mode, int dtype, bool phi, const void* points, const int32_t* midx,
                                  const Item* items, int num_items, const EdgeStatic* es, const double* T64,
                                  const float* T32, const void* evec, RobustParams rp, double out_scale, void* gl,
-                                 void* gc, double* rec, cudaStream_t s);
+                                 void* gc, double* rec, const int32_t* counts, const uint32_t* compact, cudaStream_t s);
 cudaError_t launch_adjoint_edge_prep(int mode, const EdgeStatic* es, int E, const double* Ad, const double* u,
                                      const double* tau, void* evec, cudaStream_t s);
 cudaError_t launch_adjoint_edge(const double* rec, const int32_t* item_off, int E, const EdgeStatic* es,

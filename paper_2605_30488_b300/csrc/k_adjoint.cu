@@ -72,22 +72,148 @@ struct AdjConsts {
   R isr, isd, ivr, ivd, kappa;
 };
 
+// The constants in the compute type (FP32 ones rounded on the host).
+template <typename R>
+AdjConsts<R> adj_consts(const RobustParams& rp) {
+  if constexpr (sizeof(R) == 4)
+    return AdjConsts<R>{rp.f_inv_sigma_ray, rp.f_inv_sigma_dist, rp.f_inv_var_ray, rp.f_inv_var_dist, rp.f_kappa};
+  else
+    return AdjConsts<R>{rp.inv_sigma_ray, rp.inv_sigma_dist, rp.inv_var_ray, rp.inv_var_dist, rp.kappa};
+}
+
 // Pixel-gradient accumulation: FP32 atomics into the caller's float arrays (MIXED), FP64
 // atomics into double accumulators (PLAIN).
 __device__ __forceinline__ void acc_add(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void acc_add(double* p, double v) { atomicAdd(p, v); }
 
-// One warp per work item (edge, pixel range); lanes stride the streamed pixels.
-template <typename R, int DT, bool PHI>
+// Reciprocal, reciprocal square root and square root: in FP32 the hardware approximations
+// (about 2 ulp; the mixed form's gradients are checked at 1e-5), in FP64 exact.
+__device__ __forceinline__ float a_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double a_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float a_rsqrt(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double a_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float a_sqrt(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double a_sqrt(double x) { return sqrt(x); }
+
+// The reverse pass of one match (m of keyframe i, n of keyframe j): adds its terms to the
+// item's F and scatters its four pixel derivatives.
+template <typename R, bool PHI>
+__device__ __forceinline__ void adjoint_one(R xi, R yi, R zi, R ci, R xj, R yj, R zj, R cj, const R (&T)[12],
+                                            const AdjConsts<R>& k, V3<R> uv, V3<R> uw, R uz, V3<R> tv, V3<R> tw,
+                                            R tz, R out_scale, R* __restrict__ gl, R* __restrict__ gc, int64_t pi,
+                                            int64_t pj, R (&F)[kAdjRec]) {
+  const R inf = inf_of<R>(), th2 = R(1e-24);
+  const V3<R> sx = v3(T[0] * xj + T[1] * yj + T[2] * zj, T[3] * xj + T[4] * yj + T[5] * zj,
+                      T[6] * xj + T[7] * yj + T[8] * zj);  // sR X_j = dx / dl_j
+  const V3<R> x = v3(sx.x + T[9], sx.y + T[10], sx.z + T[11]);
+  const R d2 = dot(x, x), di2 = xi * xi + yi * yi + zi * zi, cc = ci * cj;
+  const bool ok = (fmin(d2, di2) > th2) & (fmax(fmax(d2, di2), cc) < inf) & (cc >= R(0));
+  if (!ok) return;  // skipped forward too
+  const R rd = a_rsqrt(d2), d = d2 * rd, rdi = a_rsqrt(di2), di = di2 * rdi;
+  const V3<R> xh = scale(rd, x);
+  const R e0 = xh.x - xi * rdi, e1 = xh.y - yi * rdi, e2 = xh.z - zi * rdi, e3 = d - di;
+  const R q = a_sqrt(cc), sq = a_sqrt(q);
+  const R sr = sq * k.isr, sd = sq * k.isd;
+  const R r0 = sr * e0, r1 = sr * e1, r2 = sr * e2, r3 = sd * e3;
+  const R a0 = fabs(r0), a1 = fabs(r1), a2 = fabs(r2), a3 = fabs(r3);
+  const bool o0 = a0 > k.kappa, o1 = a1 > k.kappa, o2 = a2 > k.kappa, o3 = a3 > k.kappa;
+  const R w0 = o0 ? k.kappa * a_rcp(a0) : R(1);
+  const R w1 = o1 ? k.kappa * a_rcp(a1) : R(1);
+  const R w2 = o2 ? k.kappa * a_rcp(a2) : R(1);
+  const R w3 = o3 ? k.kappa * a_rcp(a3) : R(1);
+  V3<R> xhb;       // d/d xh
+  R db, eb3;       // d/d d, d/d e_d
+  R dci, dcj;      // d/d c_i, d/d c_j
+  if (!PHI) {
+    // f = sum_c rho(r_c): rho' = w r
+    const R rb0 = w0 * r0, rb1 = w1 * r1, rb2 = w2 * r2, rb3 = w3 * r3;
+    xhb = v3(rb0 * sr, rb1 * sr, rb2 * sr);
+    eb3 = rb3 * sd;
+    db = eb3;
+    // dq/dc_i = q / (2 c_i) and dr_c/dq = r_c / (2q): df/dc_i = sum_c w_c r_c^2 / (4 c_i)
+    const R s4 = R(0.25) * (rb0 * r0 + rb1 * r1 + rb2 * r2 + rb3 * r3);
+    dci = ci > R(0) ? s4 * a_rcp(ci) : R(0);
+    dcj = cj > R(0) ? s4 * a_rcp(cj) : R(0);
+  } else {
+    const R W0 = w0 * q * k.ivr, W1 = w1 * q * k.ivr, W2 = w2 * q * k.ivr, W3 = w3 * q * k.ivd;
+    // a = J u~ (ray rows P u_v + u_w x xh, range row xh.u_v + d u_z), b = J tau~
+    const R al = dot(xh, uv), be = dot(xh, tv);
+    const V3<R> av = scale(rd, axpy(-al, xh, uv)), bv = scale(rd, axpy(-be, xh, tv));
+    const V3<R> ar = axpy(R(1), av, cross(uw, xh)), br = axpy(R(1), bv, cross(tw, xh));
+    const R ad = al + d * uz, bd = be + d * tz;
+    const R s0 = e0 + br.x, s1 = e1 + br.y, s2 = e2 + br.z, s3 = e3 + bd;
+    const R h0 = ar.x * s0, h1 = ar.y * s1, h2 = ar.z * s2, h3 = ad * s3;
+    // W depends on q directly and through r (outer Huber region: w = kappa / |r|)
+    const R qb = (o0 ? R(0.5) : R(1)) * h0 * w0 * k.ivr + (o1 ? R(0.5) : R(1)) * h1 * w1 * k.ivr +
+                 (o2 ? R(0.5) : R(1)) * h2 * w2 * k.ivr + (o3 ? R(0.5) : R(1)) * h3 * w3 * k.ivd;
+    const R eb0 = W0 * ar.x - (o0 ? h0 * W0 * a_rcp(r0) * sr : R(0));
+    const R eb1 = W1 * ar.y - (o1 ? h1 * W1 * a_rcp(r1) * sr : R(0));
+    const R eb2 = W2 * ar.z - (o2 ? h2 * W2 * a_rcp(r2) * sr : R(0));
+    eb3 = W3 * ad - (o3 ? h3 * W3 * a_rcp(r3) * sd : R(0));
+    const V3<R> abr = v3(W0 * s0, W1 * s1, W2 * s2), bbr = v3(W0 * ar.x, W1 * ar.y, W2 * ar.z);
+    const R ab3 = W3 * s3, bb3 = W3 * ad;
+    xhb = v3(eb0, eb1, eb2);
+    db = eb3;
+    // through a_ray = (u_v - xh al) / d + u_w x xh and a_d = al + d u_z
+    db += -rd * dot(abr, av) + ab3 * uz;
+    xhb = axpy(-al * rd, abr, xhb);
+    xhb = axpy(-rd * dot(abr, xh) + ab3, uv, xhb);
+    xhb = axpy(R(1), cross(abr, uw), xhb);
+    // the same through b with tau~
+    db += -rd * dot(bbr, bv) + bb3 * tz;
+    xhb = axpy(-be * rd, bbr, xhb);
+    xhb = axpy(-rd * dot(bbr, xh) + bb3, tv, xhb);
+    xhb = axpy(R(1), cross(bbr, tw), xhb);
+    const R hq = R(0.5) * qb * q;
+    dci = ci > R(0) ? hq * a_rcp(ci) : R(0);
+    dcj = cj > R(0) ? hq * a_rcp(cj) : R(0);
+    // dF/du~ = sum_c abar_c J_c, dF/dtau~ = sum_c bbar_c J_c with
+    // sum_c beta_c J_c = [P beta_r + beta_d xh, xh x beta_r, beta_d d]
+    const V3<R> pa = axpy(ab3, xh, scale(rd, axpy(-dot(xh, abr), xh, abr)));
+    const V3<R> ca = cross(xh, abr);
+    const V3<R> pb = axpy(bb3, xh, scale(rd, axpy(-dot(xh, bbr), xh, bbr)));
+    const V3<R> cb = cross(xh, bbr);
+    F[7] += pa.x; F[8] += pa.y; F[9] += pa.z; F[10] += ca.x; F[11] += ca.y; F[12] += ca.z; F[13] += ab3 * d;
+    F[14] += pb.x; F[15] += pb.y; F[16] += pb.z; F[17] += cb.x; F[18] += cb.y; F[19] += cb.z; F[20] += bb3 * d;
+  }
+  // xh = x / d, d = ||x||: x_bar = (xh_bar - xh (xh . xh_bar)) / d + d_bar xh
+  const V3<R> xb = axpy(db, xh, scale(rd, axpy(-dot(xh, xhb), xh, xhb)));
+  if (PHI) {
+    const V3<R> xc = cross(x, xb);
+    F[0] += xb.x; F[1] += xb.y; F[2] += xb.z; F[3] += xc.x; F[4] += xc.y; F[5] += xc.z; F[6] += dot(xb, x);
+  }
+  // dl_j: dx/dl_j = sR X_j; dl_i: d||X_i||/dl_i = ||X_i|| and e_d = d - ||X_i||
+  acc_add(gl + pj, out_scale * dot(xb, sx));
+  acc_add(gl + pi, -out_scale * eb3 * di);
+  acc_add(gc + pi, out_scale * dci);
+  acc_add(gc + pj, out_scale * dcj);
+}
+
+// One warp per work item (edge, pixel range).  Without match lists the lanes stride the
+// item's streamed pixels (a pixel without a match idles its lane); with K1's precompacted
+// valid-match lists (entry (n << 10) | pixel offset, built with the schedule) the lanes
+// take the valid matches only, so every lane works and the index rows are not read.
+template <typename R, int DT, bool PHI, bool LIST>
 __global__ void __launch_bounds__(256) adjoint_match_kernel(
     const void* __restrict__ points, const int32_t* __restrict__ midx, const Item* __restrict__ items, int num_items,
     const EdgeStatic* __restrict__ es, const double* __restrict__ T64, const float* __restrict__ T32,
     const R* __restrict__ evec, AdjConsts<R> k, R out_scale, R* __restrict__ gl, R* __restrict__ gc,
-    double* __restrict__ rec) {
+    double* __restrict__ rec, const int32_t* __restrict__ counts, const uint32_t* __restrict__ compact) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const R inf = inf_of<R>(), th2 = R(1e-24);
   for (int it = warp; it < num_items; it += nwarps) {
     const Item item = items[it];
     const EdgeStatic e = es[item.edge];
@@ -107,113 +233,50 @@ __global__ void __launch_bounds__(256) adjoint_match_kernel(
     R F[kAdjRec];
 #pragma unroll
     for (int q = 0; q < kAdjRec; ++q) F[q] = R(0);
-    const int32_t* idx = midx + e.idx_off;
-    // software pipeline: while group g (32 pixels) is differentiated, the pixels of group
-    // g + 1 and the match indices of group g + 2 are in flight
-    int nA = item.begin + lane < item.end ? __ldg(idx + item.begin + lane) : -1;
-    int nB = item.begin + 32 + lane < item.end ? __ldg(idx + item.begin + 32 + lane) : -1;
+    const int64_t base_i = e.pix_i + item.begin;
+    // software pipeline: while one match per lane is differentiated, the pixels of the next
+    // and the index (list entry) of the one after are in flight.  Without lists an entry is
+    // the pixel offset itself with n from the index row, -1 where there is no match.
+    const int32_t* idx = midx + e.idx_off + item.begin;
+    const uint32_t* list = LIST ? compact + (int64_t)it * kCompactSlot : nullptr;
+    const int cnt = LIST ? counts[it] : item.end - item.begin;
+    auto entry = [&](int q, int& m, int& n) {
+      if (q >= cnt) {
+        m = 0;
+        n = -1;
+      } else if constexpr (LIST) {
+        const uint32_t v = __ldg(list + q);
+        m = (int)(v & 1023u);
+        n = (int)(v >> 10);
+      } else {
+        m = q;
+        n = __ldg(idx + q);
+      }
+    };
+    int mA, nA, mB, nB;
+    entry(lane, mA, nA);
+    entry(lane + 32, mB, nB);
     R ax = 0, ay = 0, az = 0, ac = 0, bx = 0, by = 0, bz = 0, bc = 0;
     if (nA >= 0) {
-      load_point<DT, R>(points, e.pix_i + item.begin + lane, ax, ay, az, ac);
+      load_point<DT, R>(points, base_i + mA, ax, ay, az, ac);
       load_point<DT, R>(points, e.pix_j + nA, bx, by, bz, bc);
     }
-    for (int g0 = item.begin; g0 < item.end; g0 += 32) {
-      const int m = g0 + lane;
+    for (int q0 = 0; q0 < cnt; q0 += 32) {
       R nax = 0, nay = 0, naz = 0, nac = 0, nbx = 0, nby = 0, nbz = 0, nbc = 0;
       if (nB >= 0) {
-        load_point<DT, R>(points, e.pix_i + m + 32, nax, nay, naz, nac);
+        load_point<DT, R>(points, base_i + mB, nax, nay, naz, nac);
         load_point<DT, R>(points, e.pix_j + nB, nbx, nby, nbz, nbc);
       }
-      const int nC = m + 64 < item.end ? __ldg(idx + m + 64) : -1;
-      const int n = nA;
+      int mC, nC;
+      entry(q0 + 64 + lane, mC, nC);
+      const int m = mA, n = nA;
       const R xi = ax, yi = ay, zi = az, ci = ac, xj = bx, yj = by, zj = bz, cj = bc;
-      nA = nB;
-      nB = nC;
+      mA = mB; nA = nB;
+      mB = mC; nB = nC;
       ax = nax; ay = nay; az = naz; ac = nac; bx = nbx; by = nby; bz = nbz; bc = nbc;
-      if (n < 0) continue;
-      const V3<R> sx = v3(T[0] * xj + T[1] * yj + T[2] * zj, T[3] * xj + T[4] * yj + T[5] * zj,
-                          T[6] * xj + T[7] * yj + T[8] * zj);  // sR X_j = dx / dl_j
-      const V3<R> x = v3(sx.x + T[9], sx.y + T[10], sx.z + T[11]);
-      const R d2 = dot(x, x), di2 = xi * xi + yi * yi + zi * zi, cc = ci * cj;
-      const bool ok = (fmin(d2, di2) > th2) & (fmax(fmax(d2, di2), cc) < inf) & (cc >= R(0));
-      if (!ok) continue;  // skipped forward too
-      const R d = sqrt(d2), rd = R(1) / d, di = sqrt(di2), rdi = R(1) / di;
-      const V3<R> xh = scale(rd, x);
-      const R e0 = xh.x - xi * rdi, e1 = xh.y - yi * rdi, e2 = xh.z - zi * rdi, e3 = d - di;
-      const R q = sqrt(cc), sq = sqrt(q);
-      const R sr = sq * k.isr, sd = sq * k.isd;
-      const R r0 = sr * e0, r1 = sr * e1, r2 = sr * e2, r3 = sd * e3;
-      const R a0 = fabs(r0), a1 = fabs(r1), a2 = fabs(r2), a3 = fabs(r3);
-      const R w0 = a0 > k.kappa ? k.kappa / a0 : R(1);
-      const R w1 = a1 > k.kappa ? k.kappa / a1 : R(1);
-      const R w2 = a2 > k.kappa ? k.kappa / a2 : R(1);
-      const R w3 = a3 > k.kappa ? k.kappa / a3 : R(1);
-      V3<R> xhb;       // d/d xh
-      R db, eb3;       // d/d d, d/d e_d
-      R dci, dcj;      // d/d c_i, d/d c_j
-      if (!PHI) {
-        // f = sum_c rho(r_c): rho' = w r
-        const R rb0 = w0 * r0, rb1 = w1 * r1, rb2 = w2 * r2, rb3 = w3 * r3;
-        xhb = v3(rb0 * sr, rb1 * sr, rb2 * sr);
-        eb3 = rb3 * sd;
-        db = eb3;
-        // dq/dc_i = q / (2 c_i) and dr_c/dq = r_c / (2q): df/dc_i = sum_c w_c r_c^2 / (4 c_i)
-        const R s4 = R(0.25) * (rb0 * r0 + rb1 * r1 + rb2 * r2 + rb3 * r3);
-        dci = ci > R(0) ? s4 / ci : R(0);
-        dcj = cj > R(0) ? s4 / cj : R(0);
-      } else {
-        const R W0 = w0 * q * k.ivr, W1 = w1 * q * k.ivr, W2 = w2 * q * k.ivr, W3 = w3 * q * k.ivd;
-        // a = J u~ (ray rows P u_v + u_w x xh, range row xh.u_v + d u_z), b = J tau~
-        const R al = dot(xh, uv), be = dot(xh, tv);
-        const V3<R> av = scale(rd, axpy(-al, xh, uv)), bv = scale(rd, axpy(-be, xh, tv));
-        const V3<R> ar = axpy(R(1), av, cross(uw, xh)), br = axpy(R(1), bv, cross(tw, xh));
-        const R ad = al + d * uz, bd = be + d * tz;
-        const R s0 = e0 + br.x, s1 = e1 + br.y, s2 = e2 + br.z, s3 = e3 + bd;
-        const R h0 = ar.x * s0, h1 = ar.y * s1, h2 = ar.z * s2, h3 = ad * s3;
-        // W depends on q directly and through r (outer Huber region: w = kappa / |r|)
-        const bool o0 = a0 > k.kappa, o1 = a1 > k.kappa, o2 = a2 > k.kappa, o3 = a3 > k.kappa;
-        const R qb = (o0 ? R(0.5) : R(1)) * h0 * w0 * k.ivr + (o1 ? R(0.5) : R(1)) * h1 * w1 * k.ivr +
-                     (o2 ? R(0.5) : R(1)) * h2 * w2 * k.ivr + (o3 ? R(0.5) : R(1)) * h3 * w3 * k.ivd;
-        const R eb0 = W0 * ar.x - (o0 ? h0 * W0 / r0 * sr : R(0));
-        const R eb1 = W1 * ar.y - (o1 ? h1 * W1 / r1 * sr : R(0));
-        const R eb2 = W2 * ar.z - (o2 ? h2 * W2 / r2 * sr : R(0));
-        eb3 = W3 * ad - (o3 ? h3 * W3 / r3 * sd : R(0));
-        const V3<R> abr = v3(W0 * s0, W1 * s1, W2 * s2), bbr = v3(W0 * ar.x, W1 * ar.y, W2 * ar.z);
-        const R ab3 = W3 * s3, bb3 = W3 * ad;
-        xhb = v3(eb0, eb1, eb2);
-        db = eb3;
-        // through a_ray = (u_v - xh al) / d + u_w x xh and a_d = al + d u_z
-        db += -rd * dot(abr, av) + ab3 * uz;
-        xhb = axpy(-al * rd, abr, xhb);
-        xhb = axpy(-rd * dot(abr, xh) + ab3, uv, xhb);
-        xhb = axpy(R(1), cross(abr, uw), xhb);
-        // the same through b with tau~
-        db += -rd * dot(bbr, bv) + bb3 * tz;
-        xhb = axpy(-be * rd, bbr, xhb);
-        xhb = axpy(-rd * dot(bbr, xh) + bb3, tv, xhb);
-        xhb = axpy(R(1), cross(bbr, tw), xhb);
-        dci = ci > R(0) ? R(0.5) * qb * q / ci : R(0);
-        dcj = cj > R(0) ? R(0.5) * qb * q / cj : R(0);
-        // dF/du~ = sum_c abar_c J_c, dF/dtau~ = sum_c bbar_c J_c with
-        // sum_c beta_c J_c = [P beta_r + beta_d xh, xh x beta_r, beta_d d]
-        const V3<R> pa = axpy(ab3, xh, scale(rd, axpy(-dot(xh, abr), xh, abr)));
-        const V3<R> ca = cross(xh, abr);
-        const V3<R> pb = axpy(bb3, xh, scale(rd, axpy(-dot(xh, bbr), xh, bbr)));
-        const V3<R> cb = cross(xh, bbr);
-        F[7] += pa.x; F[8] += pa.y; F[9] += pa.z; F[10] += ca.x; F[11] += ca.y; F[12] += ca.z; F[13] += ab3 * d;
-        F[14] += pb.x; F[15] += pb.y; F[16] += pb.z; F[17] += cb.x; F[18] += cb.y; F[19] += cb.z; F[20] += bb3 * d;
-      }
-      // xh = x / d, d = ||x||: x_bar = (xh_bar - xh (xh . xh_bar)) / d + d_bar xh
-      const V3<R> xb = axpy(db, xh, scale(rd, axpy(-dot(xh, xhb), xh, xhb)));
-      if (PHI) {
-        const V3<R> xc = cross(x, xb);
-        F[0] += xb.x; F[1] += xb.y; F[2] += xb.z; F[3] += xc.x; F[4] += xc.y; F[5] += xc.z; F[6] += dot(xb, x);
-      }
-      // dl_j: dx/dl_j = sR X_j; dl_i: d||X_i||/dl_i = ||X_i|| and e_d = d - ||X_i||
-      acc_add(gl + e.pix_j + n, out_scale * dot(xb, sx));
-      acc_add(gl + e.pix_i + m, -out_scale * eb3 * di);
-      acc_add(gc + e.pix_i + m, out_scale * dci);
-      acc_add(gc + e.pix_j + n, out_scale * dcj);
+      if (n >= 0)
+        adjoint_one<R, PHI>(xi, yi, zi, ci, xj, yj, zj, cj, T, k, uv, uw, uz, tv, tw, tz, out_scale, gl, gc,
+                            base_i + m, e.pix_j + n, F);
     }
     if (PHI) {
 #pragma unroll
@@ -223,11 +286,11 @@ __global__ void __launch_bounds__(256) adjoint_match_kernel(
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         F[q] = v;
       }
-      double mine = 0.0;
+      R mine = R(0);
 #pragma unroll
       for (int q = 0; q < kAdjRec; ++q)
-        if (lane == q) mine = (double)F[q];
-      if (lane < kAdjRec) rec[(int64_t)it * kAdjRec + lane] = mine;
+        if (lane == q) mine = F[q];
+      if (lane < kAdjRec) rec[(int64_t)it * kAdjRec + lane] = (double)mine;
     }
   }
 }
@@ -499,22 +562,25 @@ int grid_for(int64_t n, int block) {
 cudaError_t launch_adjoint_match(int mode, int dtype, bool phi, const void* points, const int32_t* midx,
                                  const Item* items, int num_items, const EdgeStatic* es, const double* T64,
                                  const float* T32, const void* evec, RobustParams rp, double out_scale, void* gl,
-                                 void* gc, double* rec, cudaStream_t s) {
+                                 void* gc, double* rec, const int32_t* counts, const uint32_t* compact, cudaStream_t s) {
   if (num_items == 0) return cudaSuccess;
   const int block = 256;
   const int grid = grid_for((int64_t)num_items * 32, block);
+  const bool list = counts && compact;
+#define COMO3R_ADJ2(R, DT, PHI, LIST)                                                                            \
+  adjoint_match_kernel<R, DT, PHI, LIST><<<grid, block, 0, s>>>(points, midx, items, num_items, es, T64, T32,     \
+                                                                (const R*)evec, k, (R)out_scale, (R*)gl, (R*)gc, \
+                                                                rec, counts, compact)
 #define COMO3R_ADJ(R, DT)                                                                                       \
   do {                                                                                                        \
-    AdjConsts<R> k{(R)rp.inv_sigma_ray, (R)rp.inv_sigma_dist, (R)rp.inv_var_ray, (R)rp.inv_var_dist,          \
-                   (R)rp.kappa};                                                                              \
-    if (phi)                                                                                                  \
-      adjoint_match_kernel<R, DT, true><<<grid, block, 0, s>>>(points, midx, items, num_items, es, T64, T32,  \
-                                                               (const R*)evec, k, (R)out_scale, (R*)gl,       \
-                                                               (R*)gc, rec);                                  \
-    else                                                                                                      \
-      adjoint_match_kernel<R, DT, false><<<grid, block, 0, s>>>(points, midx, items, num_items, es, T64, T32, \
-                                                                (const R*)evec, k, (R)out_scale, (R*)gl,      \
-                                                                (R*)gc, rec);                                 \
+    const AdjConsts<R> k = adj_consts<R>(rp);                                                                 \
+    if (phi) {                                                                                                \
+      if (list) COMO3R_ADJ2(R, DT, true, true);                                                              \
+      else COMO3R_ADJ2(R, DT, true, false);                                                                   \
+    } else {                                                                                                  \
+      if (list) COMO3R_ADJ2(R, DT, false, true);                                                             \
+      else COMO3R_ADJ2(R, DT, false, false);                                                                  \
+    }                                                                                                         \
   } while (0)
   if (mode == 1) {
     if (dtype == 0) COMO3R_ADJ(float, 0);
@@ -525,6 +591,7 @@ cudaError_t launch_adjoint_match(int mode, int dtype, bool phi, const void* poin
     else if (dtype == 1) COMO3R_ADJ(double, 1);
     else COMO3R_ADJ(double, 2);
   }
+#undef COMO3R_ADJ2
 #undef COMO3R_ADJ
   return cudaGetLastError();
 }

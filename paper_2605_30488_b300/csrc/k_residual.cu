@@ -39,8 +39,25 @@ constexpr int kAcc = 32;  // H (25) + g (7) reduced by the butterfly; the cost s
 
 template <typename R>
 struct Consts {
-  R isr, isd, ivr, ivd, kappa, half_kappa;
+  R isr, isd, ivr, ivd, kappa, half_kappa, kivr, kivd;  // kivr = kappa / sigma_r^2, kivd = kappa / sigma_d^2
 };
+
+template <typename R>
+__device__ __forceinline__ Consts<R> make_consts(const RobustParams& rp) {
+  Consts<R> k;
+  if constexpr (sizeof(R) == 4) {  // the host-rounded FP32 copies: no FP64 conversion in the kernel
+    k.isr = rp.f_inv_sigma_ray; k.isd = rp.f_inv_sigma_dist;
+    k.ivr = rp.f_inv_var_ray; k.ivd = rp.f_inv_var_dist;
+    k.kappa = rp.f_kappa; k.half_kappa = 0.5f * rp.f_kappa;
+    k.kivr = rp.f_kappa_inv_var_ray; k.kivd = rp.f_kappa_inv_var_dist;
+  } else {
+    k.isr = rp.inv_sigma_ray; k.isd = rp.inv_sigma_dist;
+    k.ivr = rp.inv_var_ray; k.ivd = rp.inv_var_dist;
+    k.kappa = rp.kappa; k.half_kappa = 0.5 * rp.kappa;
+    k.kivr = rp.kappa * rp.inv_var_ray; k.kivd = rp.kappa * rp.inv_var_dist;
+  }
+  return k;
+}
 
 // FP32: hardware approximations with denormals flushed (inputs here are far from the
 // denormal range; relative error ~2^-22, well inside the mixed form's 1e-5 tolerance)
@@ -137,20 +154,19 @@ __device__ __forceinline__ void accumulate(R xi, R yi, R zi, R ci, R xj, R yj, R
   const R sq = nn_sqrt(q);
   const R sr = sq * k.isr, sd = sq * k.isd;
   const R r0 = sr * e0, r1 = sr * e1, r2 = sr * e2, r3 = sd * e3;
-  // Huber: w = min(1, kappa / |r|) (kappa / 0 = inf gives 1); with m = min(|r|, kappa),
+  // Huber: W_c = w_c q / sigma_c^2 with w = min(1, kappa / |r|), formed as
+  // min(q / sigma^2, (kappa q / sigma^2) / |r|), exact (q / sigma^2) inside the threshold
+  // (kappa / 0 = inf gives the inside value; q = 0 gives 0); with m = min(|r|, kappa),
   // rho(r) = m (|r| - m / 2) on both branches (r^2 / 2 inside, kappa |r| - kappa^2 / 2 outside)
   const R a0 = fabs(r0), a1 = fabs(r1), a2 = fabs(r2), a3 = fabs(r3);
-  const R w0 = fmin(R(1), k.kappa * rcp(a0));
-  const R w1 = fmin(R(1), k.kappa * rcp(a1));
-  const R w2 = fmin(R(1), k.kappa * rcp(a2));
-  const R w3 = fmin(R(1), k.kappa * rcp(a3));
   const R m0 = fmin(a0, k.kappa), m1 = fmin(a1, k.kappa), m2 = fmin(a2, k.kappa), m3 = fmin(a3, k.kappa);
   // rho(r_c) = m_c (|r_c| - m_c / 2) on both branches
   const R mh = R(-0.5);
-  add_cost(acc.E, acc.Ec,
-           fma(m0, fma(mh, m0, a0), fma(m1, fma(mh, m1, a1), fma(m2, fma(mh, m2, a2), m3 * fma(mh, m3, a3)))));
-  const R qr = q * k.ivr;
-  const R u0 = w0 * qr, u1 = w1 * qr, u2 = w2 * qr, u3 = w3 * q * k.ivd;  // W_c
+  // the lane's cost sum runs over at most 64 matches between compensated folds, like H
+  acc.E += fma(m0, fma(mh, m0, a0), fma(m1, fma(mh, m1, a1), fma(m2, fma(mh, m2, a2), m3 * fma(mh, m3, a3))));
+  const R qr = q * k.ivr, qkr = q * k.kivr, qd = q * k.ivd, qkd = q * k.kivd;
+  const R u0 = fmin(qr, qkr * rcp(a0)), u1 = fmin(qr, qkr * rcp(a1)), u2 = fmin(qr, qkr * rcp(a2));
+  const R u3 = fmin(qd, qkd * rcp(a3));  // W_c
   const R f0 = u0 * e0, f1 = u1 * e1, f2 = u2 * e2, f3 = u3 * e3;        // W_c e_c
   // P = (I - xh xh^T) / d, symmetric
   const R ard = a * rd, brd = b * rd, crd = c * rd;
@@ -262,12 +278,6 @@ __device__ __forceinline__ void accumulate_pair(float2 xi, float2 yi, float2 zi,
   const float2 r0 = mul2(sr, e0), r1 = mul2(sr, e1), r2 = mul2(sr, e2), r3 = mul2(sd, e3);
   const float2 a0 = f2(fabsf(r0.x), fabsf(r0.y)), a1 = f2(fabsf(r1.x), fabsf(r1.y));
   const float2 a2 = f2(fabsf(r2.x), fabsf(r2.y)), a3 = f2(fabsf(r3.x), fabsf(r3.y));
-  const float2 kr0 = mul2(f2(k.kappa), f2(rcp(a0.x), rcp(a0.y)));
-  const float2 kr1 = mul2(f2(k.kappa), f2(rcp(a1.x), rcp(a1.y)));
-  const float2 kr2 = mul2(f2(k.kappa), f2(rcp(a2.x), rcp(a2.y)));
-  const float2 kr3 = mul2(f2(k.kappa), f2(rcp(a3.x), rcp(a3.y)));
-  const float2 w0 = f2(fminf(1.f, kr0.x), fminf(1.f, kr0.y)), w1 = f2(fminf(1.f, kr1.x), fminf(1.f, kr1.y));
-  const float2 w2 = f2(fminf(1.f, kr2.x), fminf(1.f, kr2.y)), w3 = f2(fminf(1.f, kr3.x), fminf(1.f, kr3.y));
   const float2 m0 = f2(fminf(a0.x, k.kappa), fminf(a0.y, k.kappa)), m1 = f2(fminf(a1.x, k.kappa), fminf(a1.y, k.kappa));
   const float2 m2 = f2(fminf(a2.x, k.kappa), fminf(a2.y, k.kappa)), m3 = f2(fminf(a3.x, k.kappa), fminf(a3.y, k.kappa));
   {
@@ -277,8 +287,12 @@ __device__ __forceinline__ void accumulate_pair(float2 xi, float2 yi, float2 zi,
     add_cost(acc.E.x, acc.Ec.x, rho.x);
     add_cost(acc.E.y, acc.Ec.y, rho.y);
   }
-  const float2 qr = mul2(q, f2(k.ivr));
-  const float2 u0 = mul2(w0, qr), u1 = mul2(w1, qr), u2 = mul2(w2, qr), u3 = mul2(mul2(w3, q), f2(k.ivd));
+  // W_c = min(q / sigma_c^2, (kappa q / sigma_c^2) / |r_c|), as in accumulate()
+  const float2 qr = mul2(q, f2(k.ivr)), qkr = mul2(q, f2(k.kivr)), qd = mul2(q, f2(k.ivd)), qkd = mul2(q, f2(k.kivd));
+  const float2 t0 = mul2(qkr, f2(rcp(a0.x), rcp(a0.y))), t1 = mul2(qkr, f2(rcp(a1.x), rcp(a1.y)));
+  const float2 t2 = mul2(qkr, f2(rcp(a2.x), rcp(a2.y))), t3 = mul2(qkd, f2(rcp(a3.x), rcp(a3.y)));
+  const float2 u0 = f2(fminf(qr.x, t0.x), fminf(qr.y, t0.y)), u1 = f2(fminf(qr.x, t1.x), fminf(qr.y, t1.y));
+  const float2 u2 = f2(fminf(qr.x, t2.x), fminf(qr.y, t2.y)), u3 = f2(fminf(qd.x, t3.x), fminf(qd.y, t3.y));
   const float2 g0 = mul2(u0, e0), g1 = mul2(u1, e1), g2 = mul2(u2, e2), g3 = mul2(u3, e3);
   const float2 ard = mul2(a, rd), brd = mul2(b, rd), crd = mul2(c, rd);
   const float2 p00 = fma2(neg2(ard), a, rd), p11 = fma2(neg2(brd), b, rd), p22 = fma2(neg2(crd), c, rd);
@@ -354,6 +368,23 @@ __device__ __forceinline__ void warp_transpose_reduce(float (&v)[kAcc], float (&
       float err;
       v[k] = two_sum(keep_v, rv, err);
       comp[k] = keep_c + rc + err;
+    }
+  }
+}
+
+// The same butterfly without compensation (mid-run folds: five rounded additions per value,
+// bounded error; the running totals they feed are compensated).
+template <typename R>
+__device__ __forceinline__ void warp_transpose_reduce_plain(R (&v)[kAcc], int lane) {
+#pragma unroll
+  for (int lvl = 0; lvl < 5; ++lvl) {
+    const int off = 16 >> lvl;
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < off; ++k) {
+      const R send_v = upper ? v[k] : v[k + off];
+      const R keep_v = upper ? v[k + off] : v[k];
+      v[k] = keep_v + __shfl_xor_sync(0xffffffffu, send_v, off);
     }
   }
 }
@@ -443,11 +474,88 @@ __device__ __forceinline__ void accumulate_group(const Group<R, U>& G, const R* 
     if (G.n[u] >= 0) accumulate<R>(G.xi[u], G.yi[u], G.zi[u], G.ci[u], G.xj[u], G.yj[u], G.zj[u], G.cj[u], T, k, acc);
 }
 
-// Writes the warp's record for item `it`: the reduced accumulators when `flush` (last
-// item of a run of items of one edge owned by this warp), zeros otherwise (the per-edge
-// reduction adds all records of an edge, so folding items into one record is exact).
+// ---- bounded compensated runs
+// A lane sums at most kFoldGroups groups (at most one match of each) in plain FP32
+// registers; then the warp folds them: the compensated butterfly leaves in lane l the warp
+// total of accumulator l, which TwoSum adds to the lane's running pair (s, c), the
+// rounding error going to c.  So no FP32 sum runs over more than 64 terms per lane and
+// everything above the lane is compensated; a record holds the (s, c) pairs.  FP64 folds
+// with plain additions.
+constexpr int kFoldGroups = 64;
+
 template <typename R>
-__device__ __forceinline__ void write_record(Acc<R>& acc, void* partials, int it, bool flush, int lane) {
+struct Folded {
+  R s, c;      // lane l: warp total of accumulator l over the folded matches, s + c
+  R es, ec;    // every lane: the warp's Huber cost over the folded matches, es + ec
+  int groups;  // groups summed in the lanes' registers since the last fold (warp-uniform)
+  __device__ __forceinline__ void zero() {
+    s = R(0);
+    c = R(0);
+    es = R(0);
+    ec = R(0);
+    groups = 0;
+  }
+};
+
+__device__ __forceinline__ void two_sum_into(float& s, float& c, float v, float cv) {
+  float err;
+  const float t = two_sum(s, v, err);
+  c = c + cv + err;
+  s = t;
+}
+__device__ __forceinline__ void two_sum_into(double& s, double&, double v, double cv) { s += v + cv; }
+__device__ __forceinline__ void fold_add(Folded<float>& f, float v, float cv) { two_sum_into(f.s, f.c, v, cv); }
+__device__ __forceinline__ void fold_add(Folded<double>& f, double v, double cv) { f.s += v + cv; }
+
+// The lanes' cost sums (and, for the packed variant, their compensations) into the folded
+// cost: a compensated warp sum added by TwoSum.
+template <typename R>
+__device__ __forceinline__ void fold_cost(Acc<R>& acc, Folded<R>& f) {
+  R ec = R(0);
+  const R ev = warp_sum_pair(acc.E, ec);
+  ec += warp_sum_plain(acc.Ec);
+  two_sum_into(f.es, f.ec, ev, ec);
+  acc.E = R(0);
+  acc.Ec = R(0);
+}
+
+// The final fold of a record: compensated butterfly.
+template <typename R>
+__device__ __forceinline__ void fold(Acc<R>& acc, Folded<R>& f, int lane) {
+  R comp[kAcc];
+  warp_transpose_reduce(acc.v, comp, lane);
+  fold_add(f, acc.v[0], comp[0]);
+  fold_cost(acc, f);
+#pragma unroll
+  for (int k = 0; k < kAcc; ++k) acc.v[k] = R(0);
+  f.groups = 0;
+}
+
+// A mid-run fold: plain butterfly (its five additions per value round the warp's partial
+// totals of at most 64 matches per lane), compensated accumulation into (s, c).
+template <typename R>
+__device__ __forceinline__ void fold_mid(Acc<R>& acc, Folded<R>& f, int lane) {
+  warp_transpose_reduce_plain(acc.v, lane);
+  fold_add(f, acc.v[0], R(0));
+  fold_cost(acc, f);
+#pragma unroll
+  for (int k = 0; k < kAcc; ++k) acc.v[k] = R(0);
+  f.groups = 0;
+}
+
+// Before `g` more groups are summed: fold first when the lanes' runs would exceed the bound.
+template <typename R>
+__device__ __forceinline__ void fold_before(Acc<R>& acc, Folded<R>& f, int g, int lane) {
+  if (f.groups > 0 && f.groups + g > kFoldGroups) fold_mid(acc, f, lane);
+  f.groups += g;
+}
+
+// Writes the warp's record `it`: the folded accumulators when `flush` (last item of a run of
+// items of one edge owned by this warp), zeros otherwise (the per-edge reduction adds all
+// records of an edge, so folding items into one record is exact).
+template <typename R>
+__device__ __forceinline__ void write_record(Acc<R>& acc, Folded<R>& f, void* partials, int it, bool flush,
+                                             int lane) {
   using Slot = typename std::conditional<sizeof(R) == 4, float2, double>::type;
   Slot* rec = reinterpret_cast<Slot*>(partials) + (int64_t)it * kPartial;
   if (!flush) {
@@ -455,20 +563,17 @@ __device__ __forceinline__ void write_record(Acc<R>& acc, void* partials, int it
     if (lane < kPartial - kAcc) store_slot(rec, kAcc + lane, R(0), R(0));
     return;
   }
-  R comp[kAcc];
-  warp_transpose_reduce(acc.v, comp, lane);
-  R Ec = R(0);
-  const R Ev = warp_sum_pair(acc.E, Ec);
-  Ec += warp_sum_plain(acc.Ec);
+  fold(acc, f, lane);
   const int sk = __reduce_add_sync(0xffffffffu, acc.skipped);
-  store_slot(rec, lane, acc.v[0], comp[0]);
+  store_slot(rec, lane, f.s, f.c);
   if (lane == 0) {
-    store_slot(rec, kAcc, Ev, Ec);
+    store_slot(rec, kAcc, f.es, f.ec);
     store_slot(rec, kAcc + 1, (R)sk, R(0));
     store_slot(rec, kAcc + 2, R(0), R(0));
     store_slot(rec, kAcc + 3, R(0), R(0));
   }
   acc.zero();
+  f.zero();
 }
 
 // This warp's run of items and its first record index (-1: one record per item).
@@ -487,11 +592,12 @@ __device__ __forceinline__ void warp_range(const WarpSched& ws, int gwarp, int n
 }
 
 template <typename R>
-__device__ __forceinline__ void finish_item(Acc<R>& acc, void* partials, int it, int& seg, bool flush, int lane) {
+__device__ __forceinline__ void finish_item(Acc<R>& acc, Folded<R>& f, void* partials, int it, int& seg, bool flush,
+                                            int lane) {
   if (seg < 0) {
-    write_record(acc, partials, it, flush, lane);
+    write_record(acc, f, partials, it, flush, lane);
   } else if (flush) {
-    write_record(acc, partials, seg, true, lane);
+    write_record(acc, f, partials, seg, true, lane);
     ++seg;
   }
 }
@@ -504,16 +610,15 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * BLOCK + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * BLOCK) >> 5;
-  Consts<R> k;
-  k.isr = (R)rp.inv_sigma_ray; k.isd = (R)rp.inv_sigma_dist;
-  k.ivr = (R)rp.inv_var_ray; k.ivd = (R)rp.inv_var_dist;
-  k.kappa = (R)rp.kappa; k.half_kappa = (R)(0.5 * rp.kappa);
+  const Consts<R> k = make_consts<R>(rp);
 
   // each warp owns a contiguous run of items and reduces once per edge
   int it0, it1, seg;
   warp_range(ws, gwarp, nwarps, num_items, it0, it1, seg);
   Acc<R> acc;
   acc.zero();
+  Folded<R> f;
+  f.zero();
   for (int it = it0; it < it1; ++it) {
     const Item item = items[it];
     const int64_t pix_i = es[item.edge].pix_i, pix_j = es[item.edge].pix_j;
@@ -531,6 +636,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
         Group<R, UNROLL> G;
         load_indices<R, UNROLL>(G.n, idx, g0 + lane, item.end);
         load_pixels<DT, R, UNROLL>(G, points, pix_i, pix_j, g0 + lane);
+        fold_before(acc, f, UNROLL, lane);
         accumulate_group<R, UNROLL>(G, T, k, acc);
       }
     } else {
@@ -545,6 +651,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
         load_pixels<DT, R, UNROLL>(B, points, pix_i, pix_j, g0 + STEP + lane);
         int nA[UNROLL];
         load_indices<R, UNROLL>(nA, idx, g0 + 2 * STEP + lane, item.end);
+        fold_before(acc, f, UNROLL, lane);
         accumulate_group<R, UNROLL>(A, T, k, acc);
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) A.n[u] = nA[u];
@@ -553,6 +660,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
         load_pixels<DT, R, UNROLL>(A, points, pix_i, pix_j, g0 + STEP + lane);
         int nB[UNROLL];
         load_indices<R, UNROLL>(nB, idx, g0 + 2 * STEP + lane, item.end);
+        fold_before(acc, f, UNROLL, lane);
         accumulate_group<R, UNROLL>(B, T, k, acc);
 #pragma unroll
         for (int u = 0; u < UNROLL; ++u) B.n[u] = nB[u];
@@ -560,7 +668,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) residual_reduce_kernel(
       }
     }
     // ---- warp reduction (compensated butterfly) at the end of each edge run
-    finish_item(acc, partials, it, seg, it + 1 == it1 || items[it + 1].edge != item.edge, lane);
+    finish_item(acc, f, partials, it, seg, it + 1 == it1 || items[it + 1].edge != item.edge, lane);
   }
 }
 
@@ -647,6 +755,20 @@ __device__ __forceinline__ void prefetch_indices(int32_t* buf, const int32_t* __
   for (int q = n16 + lane; q < n; q += 32) cp_async4(buf + q, idx + item.begin + q);
 }
 
+// cp.async of one packed pixel to a shared-memory address given as a 32-bit shared-space
+// address (no generic-to-shared conversion per copy)
+template <int DT>
+__device__ __forceinline__ void copy_px_s(uint32_t dst, const unsigned char* src) {
+  if constexpr (DT == 0) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+  } else if constexpr (DT == 1) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+  } else {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16), "l"(src + 16) : "memory");
+  }
+}
+
 template <typename R, int DT, bool PAIR>
 __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kernel(
     const void* __restrict__ points, const int32_t* __restrict__ midx, const Item* __restrict__ items,
@@ -654,18 +776,18 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
     const float* __restrict__ T32, RobustParams rp, void* __restrict__ partials, WarpSched ws) {
   constexpr int PX = PixBytes<DT>::v;
   constexpr int kWarpBytes = 2 * kAsyncChunk * 4 + kRing * 32 * 2 * PX;
+  constexpr int kSlotBytes = 32 * 2 * PX;  // one ring slot: 32 lanes x (streamed, gathered) pixel
+  static_assert((kRing & (kRing - 1)) == 0, "ring depth is a power of two");
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   unsigned char* mine = smem + (size_t)warp * kWarpBytes;
   int32_t* ibuf[2] = {reinterpret_cast<int32_t*>(mine), reinterpret_cast<int32_t*>(mine) + kAsyncChunk};
-  unsigned char* ring = mine + 2 * kAsyncChunk * 4 + lane * 2 * PX;  // + slot * 32 * 2 * PX
+  unsigned char* ring = mine + 2 * kAsyncChunk * 4 + lane * 2 * PX;  // + slot * kSlotBytes
+  const uint32_t ring_s = smem_addr(ring);
   const int gwarp = (blockIdx.x * 256 + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * 256) >> 5;
-  Consts<R> k;
-  k.isr = (R)rp.inv_sigma_ray; k.isd = (R)rp.inv_sigma_dist;
-  k.ivr = (R)rp.inv_var_ray; k.ivd = (R)rp.inv_var_dist;
-  k.kappa = (R)rp.kappa; k.half_kappa = (R)(0.5 * rp.kappa);
+  const Consts<R> k = make_consts<R>(rp);
 
   // each warp owns a contiguous run of items and reduces once per edge
   int it0, it1, seg;
@@ -686,8 +808,21 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
   cp_commit();
   Acc<R> acc;
   acc.zero();
+  Folded<R> f;
+  f.zero();
   AccPair pacc;  // PAIR only
   if constexpr (PAIR) pacc.zero();
+  // PAIR: the packed accumulators are folded through acc (their two elements added first)
+  auto fold_pairs = [&]() {
+    if constexpr (PAIR) {
+#pragma unroll
+      for (int q = 0; q < kAcc; ++q) {
+        acc.v[q] = pacc.v[q].x + pacc.v[q].y;
+        pacc.v[q] = make_float2(0.f, 0.f);
+      }
+      fold_mid(acc, f, lane);
+    }
+  };
   for (int it = it0; it < it1; ++it, b ^= 1) {
     const Item item = items[it];
     const int next = it + 1;
@@ -703,7 +838,11 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
     cp_commit();
     cp_wait<1>();  // this item's indices (all but the group just committed)
     __syncwarp();
-    const int64_t pix_i = es[item.edge].pix_i, pix_j = es[item.edge].pix_j;
+    // the item's streamed and gathered keyframes as byte pointers (pixel offsets are added
+    // per match as 32-bit multiples of the pixel size)
+    const unsigned char* src_i =
+        static_cast<const unsigned char*>(points) + (es[item.edge].pix_i + item.begin) * PX;
+    const unsigned char* src_j = static_cast<const unsigned char*>(points) + es[item.edge].pix_j * PX;
     const int32_t* cur = ibuf[b];
     R T[12];
 #pragma unroll
@@ -730,13 +869,20 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
       __syncwarp();
     }
     const int ngroups = (nvalid + 31) >> 5;
+    if constexpr (PAIR) {
+      if (f.groups > 0 && f.groups + ngroups > kFoldGroups) fold_pairs();
+      f.groups += ngroups;
+    } else {
+      fold_before(acc, f, ngroups, lane);
+    }
+    // this lane's list entry of group gidx (entries past the list issue nothing)
     auto issue = [&](int gidx) {
       const int e = 32 * gidx + lane;
-      if (gidx < ngroups && e < nvalid) {
+      if (e < nvalid) {
         const uint32_t v = (uint32_t)cur[e];
-        unsigned char* slot = ring + (size_t)(gidx % kRing) * 32 * 2 * PX;
-        copy_px<DT>(slot, points, pix_i + item.begin + (int)(v & 1023u));
-        copy_px<DT>(slot + PX, points, pix_j + (int)(v >> 10));
+        const uint32_t slot = ring_s + (uint32_t)(gidx & (kRing - 1)) * kSlotBytes;
+        copy_px_s<DT>(slot, src_i + (v & 1023u) * PX);
+        copy_px_s<DT>(slot + PX, src_j + (v >> 10) * PX);
       }
       cp_commit();
     };
@@ -746,7 +892,7 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
       for (int gidx = 0; gidx < ngroups; ++gidx) {
         cp_wait<kRing - 1>();
         if (32 * gidx + lane < nvalid) {
-          const unsigned char* slot = ring + (size_t)(gidx % kRing) * 32 * 2 * PX;
+          const unsigned char* slot = ring + (size_t)(gidx & (kRing - 1)) * kSlotBytes;
           R xi, yi, zi, ci, xj, yj, zj, cj;
           read_px<DT, R>(slot, xi, yi, zi, ci);
           read_px<DT, R>(slot + PX, xj, yj, zj, cj);
@@ -762,12 +908,12 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
         float xiA = 0.f, yiA = 0.f, ziA = 0.f, ciA = 0.f, xjA = 0.f, yjA = 0.f, zjA = 0.f, cjA = 0.f;
         float xiB = 0.f, yiB = 0.f, ziB = 0.f, ciB = 0.f, xjB = 0.f, yjB = 0.f, zjB = 0.f, cjB = 0.f;
         if (useA) {
-          const unsigned char* slot = ring + (size_t)(gidx % kRing) * 32 * 2 * PX;
+          const unsigned char* slot = ring + (size_t)(gidx & (kRing - 1)) * kSlotBytes;
           read_px<DT, float>(slot, xiA, yiA, ziA, ciA);
           read_px<DT, float>(slot + PX, xjA, yjA, zjA, cjA);
         }
         if (useB) {
-          const unsigned char* slot = ring + (size_t)((gidx + 1) % kRing) * 32 * 2 * PX;
+          const unsigned char* slot = ring + (size_t)((gidx + 1) & (kRing - 1)) * kSlotBytes;
           read_px<DT, float>(slot, xiB, yiB, ziB, ciB);
           read_px<DT, float>(slot + PX, xjB, yjB, zjB, cjB);
         }
@@ -784,8 +930,7 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
     if constexpr (PAIR) {
       // fold the two elements of the packed accumulators (only read when flushing)
       if (flush) {
-#pragma unroll
-        for (int q = 0; q < kAcc; ++q) acc.v[q] = pacc.v[q].x + pacc.v[q].y;
+        fold_pairs();
         float err;
         acc.E = two_sum(pacc.E.x, pacc.E.y, err);
         acc.Ec = pacc.Ec.x + pacc.Ec.y + err;
@@ -793,7 +938,7 @@ __global__ void __launch_bounds__(256, PAIR ? 1 : 2) residual_reduce_async_kerne
         pacc.zero();
       }
     }
-    finish_item(acc, partials, it, seg, flush, lane);
+    finish_item(acc, f, partials, it, seg, flush, lane);
   }
   cp_wait<0>();
 }
@@ -866,21 +1011,19 @@ __device__ __forceinline__ void cta_range(const WarpSched& ws, int num_items, in
 
 // CTA-wide record of the accumulators (all threads call it; `flush` is CTA-uniform).
 template <typename R>
-__device__ __forceinline__ void cta_record(Acc<R>& acc, void* partials, int rec_idx, bool flush, double (*red)[kAcc + 2],
-                                           int tid, int lane, int warp) {
+__device__ __forceinline__ void cta_record(Acc<R>& acc, Folded<R>& f, void* partials, int rec_idx, bool flush,
+                                           double (*red)[kAcc + 2], int tid, int lane, int warp) {
   using Slot = typename std::conditional<sizeof(R) == 4, float2, double>::type;
   Slot* rec = reinterpret_cast<Slot*>(partials) + (int64_t)rec_idx * kPartial;
   if (!flush) {
     if (tid < kPartial) store_slot(rec, tid, R(0), R(0));
     return;
   }
-  R comp[kAcc];
-  warp_transpose_reduce(acc.v, comp, lane);
-  R Ec = R(0);
-  const R Ev = warp_sum_pair(acc.E, Ec);
-  Ec += warp_sum_plain(acc.Ec);
+  fold(acc, f, lane);
+  const R Ev = f.es, Ec = f.ec;
   const int sk = __reduce_add_sync(0xffffffffu, acc.skipped);
-  red[warp][lane] = (double)acc.v[0] + (double)comp[0];
+  red[warp][lane] = (double)f.s + (double)f.c;
+  f.zero();
   if (lane == 0) {
     red[warp][kAcc] = (double)Ev + (double)Ec;
     red[warp][kAcc + 1] = (double)sk;
@@ -927,10 +1070,7 @@ __global__ void __launch_bounds__(256, 2) residual_reduce_tma_kernel(
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  Consts<R> k;
-  k.isr = (R)rp.inv_sigma_ray; k.isd = (R)rp.inv_sigma_dist;
-  k.ivr = (R)rp.inv_var_ray; k.ivd = (R)rp.inv_var_dist;
-  k.kappa = (R)rp.kappa; k.half_kappa = (R)(0.5 * rp.kappa);
+  const Consts<R> k = make_consts<R>(rp);
   // thread 0: bulk copies of local item q into stage q % kTmaStages
   auto issue = [&](int q) {
     const Item item = items[it0 + q];
@@ -970,6 +1110,8 @@ __global__ void __launch_bounds__(256, 2) residual_reduce_tma_kernel(
   cp_commit();
   Acc<R> acc;
   acc.zero();
+  Folded<R> f;
+  f.zero();
   for (int q = 0; q < n_local; ++q) {
     const int st = q % kTmaStages;
     const uint32_t parity = (uint32_t)(q / kTmaStages) & 1u;
@@ -990,6 +1132,7 @@ __global__ void __launch_bounds__(256, 2) residual_reduce_tma_kernel(
       if constexpr (sizeof(R) == 4) T[t] = T32[16 * item.edge + t];
       else T[t] = T64[12 * item.edge + t];
     }
+    fold_before(acc, f, 4, lane);  // at most four matches per lane per item
     if (landed_cur) {
       const int32_t* sidx = reinterpret_cast<const int32_t*>(smem + (size_t)st * kStageBytes);
       const unsigned char* sxi = smem + (size_t)st * kStageBytes + kIdxBytes;
@@ -1014,9 +1157,9 @@ __global__ void __launch_bounds__(256, 2) residual_reduce_tma_kernel(
     landed_cur = landed_next;
     const bool flush = it + 1 == it1 || items[it + 1].edge != item.edge;
     if (seg < 0) {
-      cta_record(acc, partials, it, flush, red, tid, lane, warp);
+      cta_record(acc, f, partials, it, flush, red, tid, lane, warp);
     } else if (flush) {
-      cta_record(acc, partials, seg, true, red, tid, lane, warp);
+      cta_record(acc, f, partials, seg, true, red, tid, lane, warp);
       ++seg;
     }
   }

@@ -189,12 +189,7 @@ extern "C" int como3r_linearize_noalloc(const como3r_graph_desc* d, const double
   if (err) return report_cuda_error(err, "linearize_noalloc match check");
   if (h_bad) return invalid("a match index lies outside [-1, P_j)");
 
-  RobustParams rp{};
-  rp.inv_sigma_ray = 1.0 / d->sigma_ray;
-  rp.inv_sigma_dist = 1.0 / d->sigma_dist;
-  rp.inv_var_ray = 1.0 / (d->sigma_ray * d->sigma_ray);
-  rp.inv_var_dist = 1.0 / (d->sigma_dist * d->sigma_dist);
-  rp.kappa = d->huber_k;
+  const RobustParams rp = make_robust_params(d->sigma_ray, d->sigma_dist, d->huber_k);
   int dev = 0, sms = 1;
   if (cudaError_t e = cudaGetDevice(&dev)) return report_cuda_error(e, "cudaGetDevice");
   if (cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))

@@ -7,7 +7,9 @@ derivation with the hand-written reverse pass.  Comparisons: the directional der
 along dense random directions (all pixels at once) and single-pixel derivatives.
 Tolerances: the all-FP64 form differs from the oracle only by its FP32 output rounding
 (2^-24 relative per element), so 1e-6 relative; the mixed form evaluates every match in
-FP32 and accumulates pixel gradients with FP32 atomics, so 2e-3 relative.
+FP32 (hardware reciprocal and square-root approximations, ~2 ulp) and accumulates pixel
+gradients with FP32 atomics, which agree with the oracle to ~1e-6 relative on these
+problems, so 1e-5 relative.
 """
 import dataclasses
 
@@ -19,7 +21,7 @@ from synth import make_problem, make_workload
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-6, 1: 2e-3}  # by mode: PLAIN_FP64, MIXED
+TOL = {0: 1e-6, 1: 1e-5}  # by mode: PLAIN_FP64, MIXED
 
 
 @pytest.fixture(scope="module")
@@ -84,13 +86,16 @@ def test_vjp_single_pixels_match_complex_step(C, small, mode):
     gl, gc, _, _, _ = gpu_grads(C, small, mode, iters, C.VJP_UNROLLED)
     pix = touched_pixels(small)
     scale_l, scale_c = np.abs(gl).max(), np.abs(gc).max()
+    # a pixel's derivative can be a small difference of large per-match terms, whose FP32
+    # rounding scales with the problem's gradients: relative to max(|ref|, 1 % of the largest)
+    floor = 1e-3 if mode == 0 else 1e-2
     for p in pix[np.linspace(0, len(pix) - 1, 6).astype(int)]:
         v = np.zeros(gl.size)
         v[p] = 1.0
         rl = O.refined_cost_derivative(small, small.poses_init, iters, v, None)
         rc = O.refined_cost_derivative(small, small.poses_init, iters, None, v)
-        assert abs(gl[p] - rl) <= TOL[mode] * max(abs(rl), 1e-3 * scale_l), (p, gl[p], rl)
-        assert abs(gc[p] - rc) <= TOL[mode] * max(abs(rc), 1e-3 * scale_c), (p, gc[p], rc)
+        assert abs(gl[p] - rl) <= TOL[mode] * max(abs(rl), floor * scale_l), (p, gl[p], rl)
+        assert abs(gc[p] - rc) <= TOL[mode] * max(abs(rc), floor * scale_c), (p, gc[p], rc)
 
 
 def test_vjp_untouched_pixels_have_zero_gradient(C, small):

@@ -306,7 +306,10 @@ def test_multi_sm_solve_matches_oracle(C, tiny, mid, ctas, monkeypatch):
     np.testing.assert_allclose(trace, to, rtol=FP64_TOL)
     for v in ("COMO3R_K1_CFG", "COMO3R_K1_CHUNK", "COMO3R_K1_WEIGHTS"):  # the mixed batch: autotuned
         monkeypatch.delenv(v)
-    batch = make_problem(22, agents=2, n_kf=4, H=24, W=32, f=25.0, n_inter=1, num_graphs=3, name="batch3")
+    # a batch of three 2-agent graphs at 64x48 (at 32x24 with one inter-agent edge the second
+    # agent's gauge is so weakly tied that FP32 summation order alone moves the converged
+    # poses by up to ~1.4e-5, depending on the residual kernel's configuration)
+    batch = make_problem(22, agents=2, n_kf=4, H=48, W=64, f=50.0, n_inter=2, num_graphs=3, name="batch3-64x48")
     poses = torch_poses(batch.poses_init)
     with C.Graph(batch, mode=C.MIXED) as g:
         st, trace, info = g.solve(poses, 6)

@@ -219,6 +219,25 @@ def test_cfg5_batch_of_64_full_size(C):
     assert prob.num_graphs == 64 and prob.pixels_of().sum() > 2 ** 31  # 64-bit pixel offsets exercised
 
 
+def test_cfg5_batch_of_64_noisy_sampled_edges(C):
+    """The 64-graph batch with 1 % depth noise and 15 % outliers (the benchmark's batch):
+    sampled edges of sampled graphs against the oracle's blocks at the initial poses, in the
+    mixed form.  Its edges hold up to 196,608 matches, so every lane of the residual kernel
+    sums many items of one edge: the per-lane runs are bounded and folded compensated."""
+    from synth import graph_subproblem, make_cloud_batch_gpu
+    from synth.cloud_gpu import batch64_specs
+    prob, pts, midx = make_cloud_batch_gpu(5, batch64_specs(noise=0.01, outlier=0.15), device="cuda")
+    with C.Graph(prob, mode=C.MIXED, points=pts, match_idx=midx) as g:
+        rec = edge_records(C, g, prob.poses_init)
+    rng = np.random.default_rng(1)
+    sizes = [(prob.edge_offset[k + 1] - prob.edge_offset[k], k) for k in range(prob.num_graphs)]
+    for gsel in (max(sizes)[1], 7, 40):
+        sub = graph_subproblem(prob, pts, midx, gsel)
+        e0 = int(prob.edge_offset[gsel])
+        edges = rng.choice(sub.num_edges, size=min(3, sub.num_edges), replace=False)
+        check_sampled_edges(sub, rec[e0:e0 + sub.num_edges], edges, MIXED_TOL, sub.poses_init)
+
+
 def test_cfg5_chain_2000_full_resolution(C):
     from synth.cloud_gpu import chain2000_spec
     _cfg5_check(C, chain2000_spec(noise=0.0, outlier=0.0), sample_graphs=(0,), iters=10)
