@@ -55,10 +55,13 @@ def parse_args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-sample-edges", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["all", "mixed", "gauge", "depth", "cfg5", "front"], default="all",
-                    help="mixed: time only the resident mixed form; gauge / depth / cfg5 / front: only the "
-                         "gauge synchronisation / the structure refinement / the 64-graph batch and the "
-                         "2,000-keyframe chain / the front-end kernels (profiling runs)")
+    ap.add_argument("--only", choices=["all", "mixed", "gauge", "depth", "cfg5", "front", "team", "adjoint4"],
+                    default="all",
+                    help="mixed: time only the resident mixed form; gauge / depth / cfg5 / front / team / "
+                         "adjoint4: only the gauge synchronisation / the structure refinement / the 64-graph "
+                         "batch and the 2,000-keyframe chain / the front-end kernels / the 4 x 150 FP16 team / "
+                         "the 4 x 30 adjoint workload (profiling runs)")
+    ap.add_argument("--no-team", action="store_true", help="skip the 4 x 150 FP16 team and the 4 x 30 adjoint")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-graph batch and the 2,000-keyframe chain (per-graph latency)")
     ap.add_argument("--batch-reps", type=int, default=3)
@@ -413,40 +416,261 @@ def measure_front(C, torch, reps: int = 20) -> dict:
                                          "frac": packed_gbs / peak, "algorithmic_bytes_per_launch": 48 * nk * P}}}
 
 
-def oracle_sample(prob, n_edges: int, offset: int = 0):
+_SAMPLE = None
+
+
+def _sample_init(path):
+    """Worker of the oracle legs: the sampled edges and the solve's system loaded once (the
+    parent spawned it with one BLAS / OpenMP thread)."""
+    global _SAMPLE
+    z = np.load(path, allow_pickle=True)
+    _SAMPLE = (z["edges"].tolist(), z["solve"].item())
+
+
+def _sample_edge(k):
+    from oracle import como3r_oracle as O
+    Ti, Tj, Pi, Pj, params = _SAMPLE[0][k]
+    O.linearize_edge(Ti, Tj, Pi, Pj, params)
+    return k
+
+
+def _sample_solve(_):
+    from oracle import como3r_oracle as O
+    s = _SAMPLE[1]
+    t = time.perf_counter()
+    tau, _, _ = O.damped_solve(s["H"], s["g"], s["anchor"], s["lam"], s["eps0"], s["max_attempts"])
+    O.retract(s["poses"], 1e-3 * tau)
+    return time.perf_counter() - t
+
+
+def _oracle_pool(n, path):
+    """n spawned workers, each single-threaded (BLAS / OpenMP thread counts set in the
+    environment they start with), loaded with the sample."""
+    import multiprocessing as mp
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        pool = mp.get_context("spawn").Pool(n, initializer=_sample_init, initargs=(path,))
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    pool.map(_sample_edge, [0] * n, chunksize=1)  # every worker up and loaded
+    return pool
+
+
+def oracle_sample(prob, n_edges: int, offset: int = 0, all_cores: bool = True):
     """Time the FP64 oracle on a bounded sample of one iteration and extrapolate.
 
     Sample: `n_edges` edges (evenly spread) linearised with dense per-match Jacobians,
     plus the dense damped Cholesky solve and retraction of a system of the full size 7N.
-    One iteration = sampled edge time x E / n_edges + solve + retraction.
+    One iteration = sampled edge time x E / n_edges + solve + retraction.  Timed on one core
+    (one single-threaded spawned process runs the oracle's own serial loop) and on all of
+    the host's cores (one single-threaded spawned process per core takes the sampled edges;
+    the solve stays serial), the core count from os.cpu_count().
     """
     from oracle import como3r_oracle as O
     arrs = O.problem_arrays(prob)
     T = [O.pose_to_matrix(p) for p in prob.poses_init]
     sel = np.unique(np.linspace(0, prob.num_edges - 1, n_edges).astype(int) + offset) % prob.num_edges
-    c0 = time.process_time()
-    t0 = time.perf_counter()
+    edges = []
     for e in sel:
         i, j, m, n, Pi, Pj = O.edge_matches(prob, arrs, int(e))
-        O.linearize_edge(T[i], T[j], Pi, Pj, prob.params())
-    t_edges = time.perf_counter() - t0
+        edges.append((T[i], T[j], Pi, Pj, prob.params()))
     rng = np.random.default_rng(0)
     n7 = 7 * prob.num_kf
     B = rng.normal(size=(n7, n7))
-    Hs = B @ B.T / n7 + np.eye(n7)
-    gs = rng.normal(size=n7)
-    t1 = time.perf_counter()
-    tau, _, _ = O.damped_solve(Hs, gs, int(prob.anchor[0]), prob.lam, prob.eps0, prob.max_attempts)
-    O.retract(prob.poses_init, 1e-3 * tau)
-    t_solve = time.perf_counter() - t1
-    cpu_s = time.process_time() - c0
-    t_iter = t_edges * prob.num_edges / len(sel) + t_solve
-    # threads actually used: CPU time over wall time of the sample (numpy / BLAS threads)
-    threads = max(1, round(cpu_s / max(t_edges + t_solve, 1e-9)))
-    return {"value": 1.0 / t_iter, "unit": UNIT, "cores": int(threads), "kind": "oracle",
-            "sample": (f"{len(sel)} of {prob.num_edges} edges linearised + full {n7}x{n7} dense solve and "
-                       f"retraction ({t_edges + t_solve:.1f} s CPU), extrapolated to one GN iteration"),
-            "seconds_per_iteration": t_iter}
+    solve = dict(H=B @ B.T / n7 + np.eye(n7), g=rng.normal(size=n7), anchor=int(prob.anchor[0]), lam=prob.lam,
+                 eps0=prob.eps0, max_attempts=prob.max_attempts, poses=prob.poses_init)
+    cores = os.cpu_count() or 1
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "sample.npz")
+        blob = np.empty(len(edges), dtype=object)
+        blob[:] = edges
+        np.savez(path, edges=blob, solve=np.array(solve, dtype=object))
+        with _oracle_pool(1, path) as pool:
+            t0 = time.perf_counter()
+            pool.map(_sample_edge, range(len(edges)), chunksize=len(edges))
+            t_edges = time.perf_counter() - t0
+            t_solve = pool.map(_sample_solve, [0])[0]
+        t_iter = t_edges * prob.num_edges / len(sel) + t_solve
+        out = {"value": 1.0 / t_iter, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"{len(sel)} of {prob.num_edges} edges linearised + full {n7}x{n7} dense solve and "
+                          f"retraction ({t_edges + t_solve:.1f} s on one core), extrapolated to one GN iteration"),
+               "seconds_per_iteration": t_iter}
+        if all_cores and cores > 1:
+            with _oracle_pool(cores, path) as pool:
+                t0 = time.perf_counter()
+                pool.map(_sample_edge, range(len(edges)), chunksize=1)
+                t_par = time.perf_counter() - t0
+            t_iter_all = t_par * prob.num_edges / len(sel) + t_solve
+            out = dict(out, value=1.0 / t_iter_all, cores=cores, seconds_per_iteration=t_iter_all,
+                       sample=(f"{len(sel)} of {prob.num_edges} edges linearised on {cores} cores ({t_par:.1f} s, "
+                               f"one single-threaded spawned process per core) + the full {n7}x{n7} dense solve and "
+                               f"retraction on one core ({t_solve:.1f} s), extrapolated to one GN iteration"),
+                       one_core={"value": 1.0 / t_iter, "unit": UNIT, "cores": 1, "seconds_per_iteration": t_iter})
+    return out
+
+
+def error_vs_golden(C, torch, prob, gold, iters: int) -> dict:
+    """Both forms against a stored FP64 oracle golden of the same inputs: the assembled H and
+    g at the initial poses (when stored) and the poses and final cost after `iters`
+    iterations (rotation angle, translation relative to max(|t|, trajectory RMS radius),
+    scale ratio, as the parity tests measure them)."""
+    from tests.gpu_helpers import pose_err
+    out = {}
+    N = prob.num_kf
+    for name, mode in (("mixed", C.MIXED), ("fp64", C.PLAIN_FP64)):
+        r = {}
+        poses = torch.tensor(prob.poses_init, dtype=torch.float64, device="cuda")
+        g = C.Graph(prob, mode=mode)
+        if "H_blocks" in gold:
+            H = torch.zeros((7 * N, 7 * N), dtype=torch.float64, device="cuda")
+            gv = torch.zeros(7 * N, dtype=torch.float64, device="cuda")
+            g.gn_step(poses.clone(), H, gv)
+            Ho = np.zeros((7 * N, 7 * N))
+            for (rr, cc), blk in zip(gold["H_block_rc"].astype(int), gold["H_blocks"]):
+                Ho[7 * rr:7 * rr + 7, 7 * cc:7 * cc + 7] = blk.reshape(7, 7)
+                if rr != cc:
+                    Ho[7 * cc:7 * cc + 7, 7 * rr:7 * rr + 7] = blk.reshape(7, 7).T
+            Hg = H.cpu().numpy()
+            r["hessian_rel"] = float(np.linalg.norm(Hg - Ho) / np.linalg.norm(Ho))
+            r["gradient_rel"] = float(np.linalg.norm(gv.cpu().numpy() - gold["g"]) / np.linalg.norm(gold["g"]))
+        st, trace, info = g.solve(poses, iters)
+        g.close()
+        err = pose_err(poses.cpu().numpy(), gold["poses"])
+        r.update({"rotation_rad": err["rot"], "translation_rel": err["trans"], "scale_rel": err["scale"],
+                  "final_cost_rel": float(abs(trace[-1, 0] / gold["trace"][-1] - 1.0)), "iters": iters})
+        out[name] = r
+    return out
+
+
+def measure_team(C, torch, args) -> dict:
+    """The batched mixed-precision workload: 4 agents x 150 keyframes at 512x384 with FP16
+    storage (points and confidence), 952 edges (60 inter-agent), each edge's valid matches
+    restricted to a column band covering U[0.2, 1] of the image (uneven edge sizes), 1 %
+    depth noise, 15 % outliers; one persistent residual launch per iteration, the
+    iterations replayed from a CUDA graph, the residual kernel autotuned.  Inputs:
+    shared-canvas generator, seed 31 (about a minute on the host)."""
+    from tests.golden import fullsize as F
+    t = time.time()
+    prob = F.problem("team_4x150_f16")
+    gen_s = time.time() - t
+    iters = F.ITERS["team_4x150_f16"]
+    pts = torch.from_numpy(np.ascontiguousarray(prob.points)).cuda()
+    idx = torch.from_numpy(np.ascontiguousarray(prob.match_idx)).cuda()
+    poses0 = torch.tensor(prob.poses_init, dtype=torch.float64, device="cuda")
+    work = torch.empty_like(poses0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {"workload": "4 agents x 150 kf, 512x384 FP16, column-band masks U[0.2,1]", "keyframes": prob.num_kf,
+           "edges": prob.num_edges, "valid_matches_per_iter": prob.valid_matches(), "iters_per_step": iters,
+           "generate_s": gen_s}
+    for name, mode, steps in (("mixed", C.MIXED, 5), ("fp64", C.PLAIN_FP64, 1)):
+        g = C.Graph(prob, mode=mode, points=pts, match_idx=idx)
+        work.copy_(poses0)
+        g.solve(work, 2, trace=False)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(steps):
+            work.copy_(poses0)
+            g.solve(work, iters, trace=False)
+        ev1.record()
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        st = g.time_stages(poses0, reps=3)
+        stats = g.stats()
+        g.close()
+        v = iters / (ms / 1e3)
+        res[name] = {"gn_iters_per_s": v, "mresiduals_per_s": v * prob.valid_matches() / 1e6, "ms_per_step": ms,
+                     "stages_ms": st, "k1_config": stats["block"] % 100, "solve_ctas": stats["solve_ctas"]}
+    res["mixed_over_fp64"] = res["mixed"]["gn_iters_per_s"] / res["fp64"]["gn_iters_per_s"]
+    peak, _ = measured_hbm_peak()
+    bytes_alg = algorithmic_bytes(prob)
+    k1_ms = res["mixed"]["stages_ms"]["residual_reduce"]
+    ach = bytes_alg / (k1_ms / 1e3) / 1e9
+    res["roofline"] = {"kernel": "residual_reduce (K1, mixed, FP16 storage)", "bound": "hbm", "achieved": ach,
+                       "peak": peak, "unit": "GB/s", "frac": ach / peak, "algorithmic_bytes_per_launch": bytes_alg,
+                       "k1_ms_per_launch": k1_ms}
+    if os.path.exists(F.PATHS["team_4x150_f16"]):
+        gold = F.load("team_4x150_f16")
+        F.check_fingerprint(prob, gold)
+        res["error_vs_oracle"] = error_vs_golden(C, torch, prob, gold, iters)
+    del pts, idx
+    torch.cuda.empty_cache()
+    return res
+
+
+def measure_adjoint_4x30(C, torch) -> dict:
+    """The adjoint workload: 4 agents x 30 keyframes at 512x384 FP32 (180 edges), the refined
+    cost after 8 iterations differentiated w.r.t. per-pixel log-range and confidence:
+    unrolled vjp timing in both forms, the per-match adjoint kernel's roofline, and the
+    gradients against the stored FP64 oracle golden (complex-step directional derivatives
+    along two seeded directions, envelope derivatives and central differences of 64
+    seeded pixels)."""
+    from tests.golden import fullsize as F
+    t = time.time()
+    prob = F.problem("adjoint_4x30")
+    gen_s = time.time() - t
+    iters = F.ITERS["adjoint_4x30"]
+    poses0 = torch.tensor(prob.poses_init, dtype=torch.float64, device="cuda")
+    res = {"workload": "4 agents x 30 kf, 512x384 FP32", "edges": prob.num_edges, "iters": iters,
+           "valid_matches_per_iter": prob.valid_matches(), "generate_s": gen_s}
+    peak, _ = measured_hbm_peak()
+    valid = prob.valid_matches()
+    adj_bytes = algorithmic_bytes(prob) + 16 * valid
+    grads = {}
+    for name, mode in (("mixed", C.MIXED), ("fp64", C.PLAIN_FP64)):
+        g = C.Graph(prob, mode=mode)
+        parts = g.time_vjp(poses0, iters, reps=2)
+        t_fwd = g.time_stages(poses0, reps=3)["iteration"] * iters
+        for vm, vname in ((C.VJP_UNROLLED, "unrolled"), (C.VJP_ENVELOPE, "envelope")):
+            st, gl, gc, loss = g.vjp(poses0, iters, vm)
+            grads[(name, vname)] = (gl.double().cpu().numpy(), gc.double().cpu().numpy(), float(loss.sum()))
+        g.close()
+        adj_ms = parts["adjoint_match"] / max(iters, 1)
+        res[name] = {"vjp_ms": parts["forward"] + parts["envelope"] + parts["backward"], "parts_ms": parts,
+                     "forward_iterations_ms": t_fwd,
+                     "match_kernel": {"bound": "hbm", "ms_per_launch": adj_ms,
+                                      "achieved": adj_bytes / (adj_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                                      "frac": adj_bytes / (adj_ms / 1e3) / 1e9 / peak,
+                                      "algorithmic_bytes_per_launch": int(adj_bytes)}}
+    if os.path.exists(F.PATHS["adjoint_4x30"]):
+        gold = F.load("adjoint_4x30")
+        F.check_fingerprint(prob, gold)
+        err = {}
+        pix = gold["pixels"].astype(np.int64)
+        for (name, vname), (gl, gc, loss) in grads.items():
+            e = {"loss_rel": abs(loss / gold["loss"][0] - 1.0)}
+            ref = gold["dir_unrolled"] if vname == "unrolled" else gold["dir_envelope"]
+            dirs = []
+            for seed, r in zip(gold["dir_seeds"], ref):
+                rng = np.random.default_rng(int(seed))
+                vl, vc = rng.normal(size=gl.size), rng.normal(size=gl.size)
+                got = float(gl @ vl + gc @ vc)
+                mag = float(np.abs(gl * vl).sum() + np.abs(gc * vc).sum())
+                dirs.append(abs(got - r) / mag)
+            e["directional_rel_max"] = max(dirs)  # relative to sum |g_p v_p|
+            if vname == "envelope":
+                env = gold["envelope"]
+                scale = np.abs(env).max(axis=0)
+                e["pixels_rel_max"] = float(max(np.abs(gl[pix] - env[:, 0]).max() / scale[0],
+                                                np.abs(gc[pix] - env[:, 1]).max() / scale[1]))
+            else:
+                g_at = np.where(gold["fd_which"] == 0, gl[pix], gc[pix])
+                keep = gold["fd_excluded"] == 0
+                e["central_difference"] = {
+                    "pixels": int(len(pix)), "excluded_huber_branch": int((~keep).sum()),
+                    "step": 1e-4, "rel_dev_median": float(np.median(np.abs(g_at - gold["fd"])[keep] /
+                                                                   np.abs(gold["fd"])[keep])),
+                    "fd_error_vs_exact": float(np.abs(gold["fd"][gold["exact_idx"].astype(int)] -
+                                                      gold["exact"]).max())}
+            err[f"{name}_{vname}"] = e
+        res["error_vs_oracle"] = err
+    return res
 
 
 # ----------------------------------------------------------------------------- arms
@@ -460,11 +684,11 @@ def run_reference(args):
     # list, plus the full dense solve), sized so that the whole run stays within minutes
     n_edges = 1 if args.steps + args.warmup > 24 else 4
     for w in range(args.warmup):
-        oracle_sample(prob, n_edges, offset=w)
+        oracle_sample(prob, n_edges, offset=w, all_cores=False)
     t0 = time.perf_counter()
     its, cores = [], []
     for k in range(args.steps):
-        r = oracle_sample(prob, n_edges, offset=args.warmup + k)
+        r = oracle_sample(prob, n_edges, offset=args.warmup + k, all_cores=False)
         its.append(r["seconds_per_iteration"])
         cores.append(r["cores"])
     wall = time.perf_counter() - t0
@@ -508,6 +732,11 @@ def run_ours(args):
         if rank == 0:
             cfg5 = measure_cfg5(C, torch, torch.device("cuda", local_rank), args.batch_reps)
             print(json.dumps({"cfg5": cfg5, "note": "profiling run (--only cfg5)"}), flush=True)
+        return
+    if args.only in ("team", "adjoint4"):
+        if rank == 0:
+            r = measure_team(C, torch, args) if args.only == "team" else measure_adjoint_4x30(C, torch)
+            print(json.dumps({args.only: r, "note": f"profiling run (--only {args.only})"}), flush=True)
         return
     if args.only == "gauge":
         if rank == 0:
@@ -635,6 +864,15 @@ def run_ours(args):
     gauge = None if args.no_batch else measure_gauge(C, torch, dev)
     depth = measure_depth(C, torch, prob)
     front = measure_front(C, torch)
+    # the mixed and FP64 forms against the stored FP64 oracle golden of this workload
+    from tests.golden import fullsize as F
+    golden_err = None
+    if args.workload == "two_agent_40kf_512x384" and args.seed == 0 and os.path.exists(F.PATHS["two_agent_40kf"]):
+        gold = F.load("two_agent_40kf")
+        F.check_fingerprint(prob, gold)
+        golden_err = error_vs_golden(C, torch, prob, gold, iters)
+    team = None if args.no_team else measure_team(C, torch, args)
+    adj4 = None if args.no_team else measure_adjoint_4x30(C, torch)
 
     clocks.stop()
     if rank != 0:
@@ -703,6 +941,13 @@ def run_ours(args):
         out["gauge_sync"] = gauge
     out["depth_refine"] = depth
     out["front_end"] = front
+    if golden_err is not None:
+        out["mixed_error_vs_oracle"] = dict(golden_err, reference="FP64 oracle golden (tests/golden), same inputs",
+                                            targets={"fp64": 1e-9, "mixed": 1e-5})
+    if team is not None:
+        out["cfg3_team_f16"] = team
+    if adj4 is not None:
+        out["cfg4_adjoint"] = adj4
     if cpu is not None:
         out["cpu_baseline"] = cpu
     print(json.dumps(out), flush=True)

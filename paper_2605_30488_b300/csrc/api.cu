@@ -658,8 +658,10 @@ int como3r_depth_refine(como3r_graph_t g, const double* poses, double* eta, int3
   const HostPlan& p = g->plan;
   CK(launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, g->stream), "edge_prep");
   g->last_launches = 1 + 2 * ((int64_t)iters + 1) + (points_out ? 1 : 0);
-  return depth_run(g->depth, p, g->d_items, g->num_items, g->d_es, g->midx, g->d_T64, g->d_T32, g->rp.kappa, g->sms,
-                   eta, iters, cost_trace, points_out, g->points, match_ms, g->stream);
+  const bool lists = g->k1_compact && g->k1_chunk <= kCompactSlot;
+  return depth_run(g->depth, p, g->d_items, g->num_items, g->d_es, g->midx, lists ? g->d_counts : nullptr,
+                   lists ? g->d_compact : nullptr, g->d_T64, g->d_T32, g->rp.kappa, g->sms, eta, iters, cost_trace,
+                   points_out, g->points, match_ms, g->stream);
 }
 
 int como3r_linearize(como3r_graph_t g, const double* poses, double* edge_out, double* cost_out) {

@@ -144,13 +144,18 @@ struct Slots {
   }
 };
 
-template <typename R>
+// LIST: the items' precompacted valid-match lists of the residual kernel (entry
+// (n << 10) | pixel offset in the item, in pixel order) replace the index rows, so every
+// lane takes matches only (a lane's four entries are consecutive, so its streamed pixels
+// are still mostly one segment) and the index rows are not read.
+template <typename R, bool LIST>
 __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
     const typename Rec<R>::T* __restrict__ rec, const int32_t* __restrict__ seg,
     const int32_t* __restrict__ midx, const Item* __restrict__ items, int num_items,
     const EdgeStatic* __restrict__ es, const double* __restrict__ T64, const float* __restrict__ T32,
     const R* __restrict__ scale, double kscale, double kappa_d, double* __restrict__ gsum,
-    double* __restrict__ hsum, double* __restrict__ cost) {
+    double* __restrict__ hsum, double* __restrict__ cost, const int32_t* __restrict__ counts,
+    const uint32_t* __restrict__ compact) {
   const int lane = threadIdx.x & 31;
   const int w0 = (blockIdx.x * kDepthThreads + threadIdx.x) >> 5;
   const int nw = (gridDim.x * kDepthThreads) >> 5;
@@ -168,37 +173,68 @@ __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
       else T[q] = T64[12 * item.edge + q];
     }
     const int32_t* idx = midx + e.idx_off;
-    // a lane's match indices of one chunk: one 16-byte load when the four are in range and
-    // aligned, else one by one (-1 past the item)
-    auto load_idx = [&](int mb, int (&nn)[kDepthUnroll]) {
-      if constexpr (kDepthUnroll == 4) {
-        if (mb + 3 < item.end && (reinterpret_cast<uintptr_t>(idx + mb) & 15u) == 0) {
-          const int4 v = __ldg(reinterpret_cast<const int4*>(idx + mb));
-          nn[0] = v.x; nn[1] = v.y; nn[2] = v.z; nn[3] = v.w;
+    // the item's entries: pixels (index rows) or valid matches (lists)
+    const uint32_t* list = LIST ? compact + (int64_t)it * kCompactSlot : nullptr;
+    const int q_begin = LIST ? 0 : item.begin, q_end = LIST ? counts[it] : item.end;
+    // a lane's entries of one chunk: one 16-byte load when the four are in range and
+    // aligned, else one by one (-1 past the end); mm = the streamed pixel (offset from the
+    // keyframe's first pixel), nn = the gathered one
+    auto load_idx = [&](int qb, int (&mm)[kDepthUnroll], int (&nn)[kDepthUnroll]) {
+      if constexpr (LIST) {
+        if (qb + 3 < q_end) {  // list slots start 16-byte aligned
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(list + qb));
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int u = 0; u < kDepthUnroll; ++u) {
+            mm[u] = item.begin + (int)(w[u] & 1023u);
+            nn[u] = (int)(w[u] >> 10);
+          }
           return;
         }
+#pragma unroll
+        for (int u = 0; u < kDepthUnroll; ++u) {
+          const uint32_t w = qb + u < q_end ? __ldg(list + qb + u) : 0u;
+          mm[u] = item.begin + (int)(w & 1023u);
+          nn[u] = qb + u < q_end ? (int)(w >> 10) : -1;
+        }
+      } else {
+        if constexpr (kDepthUnroll == 4) {
+          if (qb + 3 < q_end && (reinterpret_cast<uintptr_t>(idx + qb) & 15u) == 0) {
+            const int4 v = __ldg(reinterpret_cast<const int4*>(idx + qb));
+            nn[0] = v.x; nn[1] = v.y; nn[2] = v.z; nn[3] = v.w;
+#pragma unroll
+            for (int u = 0; u < kDepthUnroll; ++u) mm[u] = qb + u;
+            return;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kDepthUnroll; ++u) {
+          mm[u] = qb + u;
+          nn[u] = qb + u < q_end ? __ldg(idx + qb + u) : -1;
+        }
       }
-#pragma unroll
-      for (int u = 0; u < kDepthUnroll; ++u) nn[u] = mb + u < item.end ? __ldg(idx + mb + u) : -1;
     };
-    // each lane takes kDepthUnroll consecutive pixels of the item (streamed loads of a lane
-    // are contiguous; its pixels mostly share one segment, so they add up in the lane); the
-    // next chunk's indices are in flight while this chunk's records are gathered and used
-    int nxt[kDepthUnroll];
-    load_idx(item.begin + kDepthUnroll * lane, nxt);
-    for (int m0 = item.begin; m0 < item.end; m0 += 32 * kDepthUnroll) {
-      const int mb = m0 + kDepthUnroll * lane;
-      int nn[kDepthUnroll];
+    // each lane takes kDepthUnroll consecutive entries of the item (streamed loads of a lane
+    // are (nearly) contiguous; its pixels mostly share one segment, so they add up in the
+    // lane); the next chunk's entries are in flight while this chunk's records are gathered
+    int nxt_m[kDepthUnroll], nxt_n[kDepthUnroll];
+    load_idx(q_begin + kDepthUnroll * lane, nxt_m, nxt_n);
+    for (int q0 = q_begin; q0 < q_end; q0 += 32 * kDepthUnroll) {
+      const int qb = q0 + kDepthUnroll * lane;
+      int mm[kDepthUnroll], nn[kDepthUnroll];
 #pragma unroll
-      for (int u = 0; u < kDepthUnroll; ++u) nn[u] = nxt[u];
-      if (m0 + 32 * kDepthUnroll < item.end) load_idx(mb + 32 * kDepthUnroll, nxt);
+      for (int u = 0; u < kDepthUnroll; ++u) {
+        mm[u] = nxt_m[u];
+        nn[u] = nxt_n[u];
+      }
+      if (q0 + 32 * kDepthUnroll < q_end) load_idx(qb + 32 * kDepthUnroll, nxt_m, nxt_n);
       typename Rec<R>::T ri[kDepthUnroll], rj[kDepthUnroll];
       int si[kDepthUnroll], sj[kDepthUnroll];
 #pragma unroll
       for (int u = 0; u < kDepthUnroll; ++u) {
         si[u] = sj[u] = -1;
         if (nn[u] >= 0) {
-          const int64_t pi = e.pix_i + mb + u, pj = e.pix_j + nn[u];
+          const int64_t pi = e.pix_i + mm[u], pj = e.pix_j + nn[u];
           ri[u] = rec[pi];
           rj[u] = rec[pj];
           si[u] = __ldg(seg + pi);
@@ -538,9 +574,9 @@ int depth_setup(const HostPlan& p, const void* points, int dtype, int mode, cons
 }
 
 int depth_run(DepthState* st, const HostPlan& p, const Item* items, int num_items, const EdgeStatic* es,
-              const int32_t* midx, const double* T64, const float* T32, double kappa, int sms, double* eta_io,
-              int iters, double* cost_trace, void* points_out, const void* points_src, float* match_ms,
-              cudaStream_t s) {
+              const int32_t* midx, const int32_t* counts, const uint32_t* compact, const double* T64,
+              const float* T32, double kappa, int sms, double* eta_io, int iters, double* cost_trace,
+              void* points_out, const void* points_src, float* match_ms, cudaStream_t s) {
   const int M = st->M;
   cudaError_t e = cudaSuccess;
   if (M) e = cudaMemcpyAsync(st->eta[0], eta_io, sizeof(double) * M, cudaMemcpyDefault, s);
@@ -562,14 +598,19 @@ int depth_run(DepthState* st, const HostPlan& p, const Item* items, int num_item
     e = cudaMemsetAsync(st->cost, 0, sizeof(double), s);
     if (!e && match_ms) e = cudaEventRecord(e0, s);
     if (!e) {
-      if (st->mode == COMO3R_MIXED)
-        depth_match_kernel<float><<<grid, kDepthThreads, 0, s>>>(
-            static_cast<const float4*>(st->rec), st->seg, midx, items, num_items, es, T64, T32, st->sc32[cur],
-            kscale, kappa, st->gsum, st->hsum, st->cost);
-      else
-        depth_match_kernel<double><<<grid, kDepthThreads, 0, s>>>(
-            static_cast<const double4*>(st->rec), st->seg, midx, items, num_items, es, T64, T32, st->sc64[cur],
-            kscale, kappa, st->gsum, st->hsum, st->cost);
+      const bool list = counts && compact;
+#define COMO3R_DEPTH(R, V, SC, LIST)                                                                          \
+  depth_match_kernel<R, LIST><<<grid, kDepthThreads, 0, s>>>(static_cast<const V*>(st->rec), st->seg, midx,   \
+                                                              items, num_items, es, T64, T32, SC, kscale, kappa, \
+                                                              st->gsum, st->hsum, st->cost, counts, compact)
+      if (st->mode == COMO3R_MIXED) {
+        if (list) COMO3R_DEPTH(float, float4, st->sc32[cur], true);
+        else COMO3R_DEPTH(float, float4, st->sc32[cur], false);
+      } else {
+        if (list) COMO3R_DEPTH(double, double4, st->sc64[cur], true);
+        else COMO3R_DEPTH(double, double4, st->sc64[cur], false);
+      }
+#undef COMO3R_DEPTH
       e = cudaGetLastError();
     }
     if (!e && match_ms) e = cudaEventRecord(e1, s);

@@ -64,10 +64,11 @@ void plan_stats(const HostPlan& p, int64_t* stats);
 struct DepthState;
 int depth_setup(const HostPlan& p, const void* points, int dtype, int mode, const int32_t* labels,
                 const como3r_depth_desc* d, cudaStream_t s, DepthState** out, int64_t* num_segments);
+// counts / compact: the residual kernel's valid-match lists of the items (both NULL: none)
 int depth_run(DepthState* st, const HostPlan& p, const Item* items, int num_items, const EdgeStatic* es,
-              const int32_t* midx, const double* T64, const float* T32, double kappa, int sms, double* eta,
-              int iters, double* cost_trace, void* points_out, const void* points_src, float* match_ms,
-              cudaStream_t s);
+              const int32_t* midx, const int32_t* counts, const uint32_t* compact, const double* T64,
+              const float* T32, double kappa, int sms, double* eta, int iters, double* cost_trace,
+              void* points_out, const void* points_src, float* match_ms, cudaStream_t s);
 void depth_free(DepthState* st);
 
 }  // namespace como3r
