@@ -516,6 +516,68 @@ def oracle_sample(prob, n_edges: int, offset: int = 0, all_cores: bool = True):
     return out
 
 
+def measure_small(C, torch) -> dict:
+    """The oracle-sized workload (2 agents x 6 keyframes, 64x48, FP64 storage, 14 edges, 10 %
+    outliers, 10 iterations, seed 0): both GPU forms (launch-bound at this size) and the
+    FP64 oracle's whole 10-iteration solve on one core (one single-threaded spawned
+    process), with the GPU poses' error against it."""
+    import multiprocessing as mp
+    from synth import make_workload
+    prob = make_workload("two_agent_6kf_64x48", seed=0)
+    iters = prob.iters
+    res = {"workload": "two_agent_6kf_64x48", "edges": prob.num_edges, "valid_matches_per_iter": prob.valid_matches(),
+           "iters_per_step": iters}
+    poses0 = torch.tensor(prob.poses_init, dtype=torch.float64, device="cuda")
+    work = torch.empty_like(poses0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    finals = {}
+    for name, mode in (("mixed", C.MIXED), ("fp64", C.PLAIN_FP64)):
+        g = C.Graph(prob, mode=mode)
+        for _ in range(3):
+            work.copy_(poses0)
+            g.solve(work, iters, trace=False)
+        torch.cuda.synchronize()
+        steps = 50
+        ev0.record()
+        for _ in range(steps):
+            work.copy_(poses0)
+            g.solve(work, iters, trace=False)
+        ev1.record()
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        finals[name] = work.cpu().numpy()
+        g.close()
+        res[name] = {"gn_iters_per_s": iters / (ms / 1e3), "ms_per_step": ms}
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(1) as pool:
+            po, t = pool.apply(_small_oracle_solve, (iters,))
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    res["oracle_one_core"] = {"gn_iters_per_s": iters / t, "seconds": t, "cores": 1}
+    from tests.gpu_helpers import pose_err
+    for name in ("mixed", "fp64"):
+        e = pose_err(finals[name], po)
+        res[name]["error_vs_oracle"] = {"rotation_rad": e["rot"], "translation_rel": e["trans"], "scale_rel": e["scale"]}
+    return res
+
+
+def _small_oracle_solve(iters):
+    from oracle import como3r_oracle as O
+    from synth import make_workload
+    prob = make_workload("two_agent_6kf_64x48", seed=0)
+    t = time.perf_counter()
+    po, _ = O.gn_solve(prob, prob.poses_init, iters)
+    return po, time.perf_counter() - t
+
+
 def error_vs_golden(C, torch, prob, gold, iters: int) -> dict:
     """Both forms against a stored FP64 oracle golden of the same inputs: the assembled H and
     g at the initial poses (when stored) and the poses and final cost after `iters`
@@ -871,6 +933,7 @@ def run_ours(args):
         gold = F.load("two_agent_40kf")
         F.check_fingerprint(prob, gold)
         golden_err = error_vs_golden(C, torch, prob, gold, iters)
+    small = measure_small(C, torch)
     team = None if args.no_team else measure_team(C, torch, args)
     adj4 = None if args.no_team else measure_adjoint_4x30(C, torch)
 
@@ -944,6 +1007,7 @@ def run_ours(args):
     if golden_err is not None:
         out["mixed_error_vs_oracle"] = dict(golden_err, reference="FP64 oracle golden (tests/golden), same inputs",
                                             targets={"fp64": 1e-9, "mixed": 1e-5})
+    out["cfg1_small"] = small
     if team is not None:
         out["cfg3_team_f16"] = team
     if adj4 is not None:

@@ -142,7 +142,12 @@ struct SolverPlan {
 // Every CTA of a graph lays out its shared memory identically up to the blocks (column
 // scratch for kCNColMax columns first, then the blocks), so a remote column or block is
 // found at the same offset as a local one.
-enum ClusterMeta { kCSched, kCNSched, kCU, kCNU, kCT, kCNT, kCLvl, kCNSlot, kCNCol, kCOwn, kCNColMax, kCMetaCount };
+// kCTopLocal: the lowest level from which on every level's columns are all owned by rank 0
+// (the narrow top of the elimination tree): the back substitution of those levels needs no
+// cluster barrier between them (only rank 0 works, and only rank 0 reads their solutions).
+enum ClusterMeta {
+  kCSched, kCNSched, kCU, kCNU, kCT, kCNT, kCLvl, kCNSlot, kCNCol, kCOwn, kCNColMax, kCTopLocal, kCMetaCount
+};
 struct ClusterPlan {
   int C;                    // CTAs per graph
   const int32_t* cmeta;     // [G * C][kCMetaCount]

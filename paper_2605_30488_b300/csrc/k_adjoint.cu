@@ -115,8 +115,10 @@ __device__ __forceinline__ void adjoint_one(R xi, R yi, R zi, R ci, R xj, R yj, 
                                             R tz, R out_scale, R* __restrict__ gl, R* __restrict__ gc, int64_t pi,
                                             int64_t pj, R (&F)[kAdjRec]) {
   const R inf = inf_of<R>(), th2 = R(1e-24);
-  const V3<R> sx = v3(T[0] * xj + T[1] * yj + T[2] * zj, T[3] * xj + T[4] * yj + T[5] * zj,
-                      T[6] * xj + T[7] * yj + T[8] * zj);  // sR X_j = dx / dl_j
+  // sR X_j = dx / dl_j (the FP32 copy of the transform holds sR - I: X_j added back)
+  V3<R> sx = v3(T[0] * xj + T[1] * yj + T[2] * zj, T[3] * xj + T[4] * yj + T[5] * zj,
+                T[6] * xj + T[7] * yj + T[8] * zj);
+  if constexpr (sizeof(R) == 4) sx = v3(sx.x + xj, sx.y + yj, sx.z + zj);
   const V3<R> x = v3(sx.x + T[9], sx.y + T[10], sx.z + T[11]);
   const R d2 = dot(x, x), di2 = xi * xi + yi * yi + zi * zi, cc = ci * cj;
   const bool ok = (fmin(d2, di2) > th2) & (fmax(fmax(d2, di2), cc) < inf) & (cc >= R(0));

@@ -909,10 +909,17 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
     }
   }
   if (ok) {
+    // levels from kCTopLocal up hold rank 0's columns only: between them rank 0 needs a CTA
+    // barrier, the other ranks nothing; from the level below on, one cluster barrier per level
+    const int top_local = cm[kCTopLocal];
     for (int l = nlev - 1; l >= 0; --l) {
       const int* L0 = lv + 4 * l;
       for (int x = L0[0] + warp; x < L0[4]; x += kClusterWarps) backward_column<true>(C, cs[x], lane);
-      cl.sync();  // this level's solutions are read by the columns below it
+      if (l > top_local) {
+        if (rank == 0) __syncthreads();  // the next level is rank 0's too
+      } else {
+        cl.sync();  // this level's solutions are read by the columns below it, on any rank
+      }
     }
     for (int x = tid; x < 7 * ncl; x += kClusterThreads)
       tau[7 * col_kf[cs[x / 7]] + x % 7] = y_of<true>(C, cs[x / 7])[x % 7];

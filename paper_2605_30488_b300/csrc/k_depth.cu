@@ -250,9 +250,15 @@ __global__ void __launch_bounds__(kDepthThreads, 2) depth_match_kernel(
         const R dj = sj[u] >= 0 ? __ldg(scale + sj[u]) : R(1);
         const R xi0 = di * ri[u].x, xi1 = di * ri[u].y, xi2 = di * ri[u].z;
         const R xj0 = dj * rj[u].x, xj1 = dj * rj[u].y, xj2 = dj * rj[u].z;
-        const R a0 = fma(T[0], xj0, fma(T[1], xj1, T[2] * xj2));  // s R X_j
-        const R a1 = fma(T[3], xj0, fma(T[4], xj1, T[5] * xj2));
-        const R a2 = fma(T[6], xj0, fma(T[7], xj1, T[8] * xj2));
+        // s R X_j (the FP32 copy of the transform holds sR - I: X_j added back)
+        R a0 = fma(T[0], xj0, fma(T[1], xj1, T[2] * xj2));
+        R a1 = fma(T[3], xj0, fma(T[4], xj1, T[5] * xj2));
+        R a2 = fma(T[6], xj0, fma(T[7], xj1, T[8] * xj2));
+        if constexpr (sizeof(R) == 4) {
+          a0 += xj0;
+          a1 += xj1;
+          a2 += xj2;
+        }
         const R y0 = a0 + T[9], y1 = a1 + T[10], y2 = a2 + T[11];
         const R cc = ri[u].w * rj[u].w;
         const R nx2 = fma(xi0, xi0, fma(xi1, xi1, xi2 * xi2)), ny2 = fma(y0, y0, fma(y1, y1, y2 * y2));

@@ -129,12 +129,26 @@ __device__ __forceinline__ void add_cost(float& E, float& Ec, float x) {
 __device__ __forceinline__ void add_cost(double& E, double&, double x) { E += x; }
 
 // One match: residual, robust weights, Jacobian rows, accumulation (see file header).
+// x = sR X_j + t from the edge's transform: FP64 holds sR itself, the FP32 copy sR - I (its
+// entries small for the near-identity relative poses of neighbouring keyframes, so their
+// rounding, shared by all of the edge's matches, is small), with X_j added back.
+template <typename R>
+__device__ __forceinline__ void transform_point(const R* T, R xj, R yj, R zj, R& x0, R& x1, R& x2) {
+  x0 = fma(T[0], xj, fma(T[1], yj, fma(T[2], zj, T[9])));
+  x1 = fma(T[3], xj, fma(T[4], yj, fma(T[5], zj, T[10])));
+  x2 = fma(T[6], xj, fma(T[7], yj, fma(T[8], zj, T[11])));
+  if constexpr (sizeof(R) == 4) {
+    x0 += xj;
+    x1 += yj;
+    x2 += zj;
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void accumulate(R xi, R yi, R zi, R ci, R xj, R yj, R zj, R cj, const R* T,
                                            const Consts<R>& k, Acc<R>& acc) {
-  const R x0 = fma(T[0], xj, fma(T[1], yj, fma(T[2], zj, T[9])));
-  const R x1 = fma(T[3], xj, fma(T[4], yj, fma(T[5], zj, T[10])));
-  const R x2 = fma(T[6], xj, fma(T[7], yj, fma(T[8], zj, T[11])));
+  R x0, x1, x2;
+  transform_point<R>(T, xj, yj, zj, x0, x1, x2);
   const R d2 = fma(x0, x0, fma(x1, x1, x2 * x2));
   const R di2 = fma(xi, xi, fma(yi, yi, zi * zi));
   const R cc = ci * cj;
@@ -249,9 +263,10 @@ __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y
 __device__ __forceinline__ void accumulate_pair(float2 xi, float2 yi, float2 zi, float2 ci, float2 xj, float2 yj,
                                                 float2 zj, float2 cj, bool useA, bool useB, const float* T,
                                                 const Consts<float>& k, AccPair& acc) {
-  const float2 x0 = fma2(f2(T[0]), xj, fma2(f2(T[1]), yj, fma2(f2(T[2]), zj, f2(T[9]))));
-  const float2 x1 = fma2(f2(T[3]), xj, fma2(f2(T[4]), yj, fma2(f2(T[5]), zj, f2(T[10]))));
-  const float2 x2 = fma2(f2(T[6]), xj, fma2(f2(T[7]), yj, fma2(f2(T[8]), zj, f2(T[11]))));
+  // T holds sR - I (see transform_point): X_j added back
+  const float2 x0 = add2(xj, fma2(f2(T[0]), xj, fma2(f2(T[1]), yj, fma2(f2(T[2]), zj, f2(T[9])))));
+  const float2 x1 = add2(yj, fma2(f2(T[3]), xj, fma2(f2(T[4]), yj, fma2(f2(T[5]), zj, f2(T[10])))));
+  const float2 x2 = add2(zj, fma2(f2(T[6]), xj, fma2(f2(T[7]), yj, fma2(f2(T[8]), zj, f2(T[11])))));
   float2 d2 = fma2(x0, x0, fma2(x1, x1, mul2(x2, x2)));
   float2 di2 = fma2(xi, xi, fma2(yi, yi, mul2(zi, zi)));
   float2 cc = mul2(ci, cj);

@@ -49,7 +49,11 @@ __global__ void edge_prep_kernel(const double* __restrict__ poses, const EdgeSta
     }
     const double v = f * fma(Ri[r], b0, fma(Ri[3 + r], b1, Ri[6 + r] * b2));
     T64[12 * e + lane] = v;
-    T32[16 * e + lane] = (float)v;
+    // the FP32 copy holds sR_ij - I: relative poses of neighbouring keyframes are close to
+    // the identity, so its entries are small and their rounding error (the only error of
+    // the transform shared by all of an edge's matches) is roughly ten times smaller than
+    // that of sR_ij itself; the kernels add X_j back in FP32
+    T32[16 * e + lane] = (float)(lane < 9 && lane % 4 == 0 ? v - 1.0 : v);
   } else if (lane < 16) {
     T32[16 * e + lane] = 0.f;
   }

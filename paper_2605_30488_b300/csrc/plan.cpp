@@ -534,13 +534,26 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
     const int* lvl = p.llvl.data() + 4 * m[kMetaLvlBase];
     const int* colslot = p.lcol_slot.data() + cbase + g;
     const int* sched = p.lsched.data() + cbase;
-    // owners: round robin over the columns of each level from rank 0, so that the narrow
-    // top of the elimination tree (one column per level) stays on one CTA and its near
-    // updates read local shared memory; the far updates are spread below
+    // owners: per level, each column (largest first: 1 + its off-diagonal blocks, the
+    // factorisation and off-diagonal solve work) to the CTA with the least work of the level
+    // so far, lowest rank on ties -- so the narrow top of the elimination tree (one column
+    // per level) stays on rank 0 and its near updates read local shared memory, and the
+    // wide bottom levels end together; the far updates are spread below
     std::vector<int> owner(ncol, 0), clocal(ncol, 0), slocal(nslot, 0), shome(nslot, 0);
     std::vector<std::vector<int>> own_cols(C), own_slots(C);
-    for (int l = 0; l < nlev; ++l)
-      for (int q = lvl[4 * l]; q < lvl[4 * (l + 1)]; ++q) owner[sched[q]] = (q - lvl[4 * l]) % C;
+    for (int l = 0; l < nlev; ++l) {
+      std::vector<int> cols(sched + lvl[4 * l], sched + lvl[4 * (l + 1)]);
+      auto cost = [&](int c) { return colslot[c + 1] - colslot[c]; };
+      std::stable_sort(cols.begin(), cols.end(), [&](int a, int b) { return cost(a) > cost(b); });
+      std::vector<int> load(C, 0);
+      for (int c : cols) {
+        int best = 0;
+        for (int r = 1; r < C; ++r)
+          if (load[r] < load[best]) best = r;
+        owner[c] = best;
+        load[best] += cost(c);
+      }
+    }
     for (int q = 0; q < ncol; ++q) {  // level order
       const int c = sched[q], r = owner[c];
       clocal[c] = (int)own_cols[r].size();
@@ -552,14 +565,25 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
       }
     }
     for (int c = 0; c < ncol; ++c) cp.col_home[cbase + c] = (owner[c] << 24) | clocal[c];
+    // the top run of levels whose columns are all rank 0's
+    int top_local = nlev;
+    while (top_local > 0) {
+      bool all0 = true;
+      for (int q = lvl[4 * (top_local - 1)]; q < lvl[4 * top_local]; ++q) all0 = all0 && owner[sched[q]] == 0;
+      if (!all0) break;
+      --top_local;
+    }
     int ncol_max = 0;
     for (int r = 0; r < C; ++r) ncol_max = std::max(ncol_max, (int)own_cols[r].size());
     for (int sl = 0; sl < nslot; ++sl) cp.slot_home[sbase + sl] = (shome[sl] << 24) | slocal[sl];
     // Executors of the far update tasks of level l (they run during level l + 1's diagonal
-    // factorisations): when level l + 1 has fewer columns than CTAs, the CTAs that own none
-    // of them, round robin (writing the destinations through the cluster window) -- on
+    // factorisations, writing their destinations through the cluster window when remote):
+    // when level l + 1 has fewer columns than CTAs, the CTAs that own none of them -- on
     // this GPU an SM's FP64 pipe is narrow, and updates run beside a critical
-    // factorisation delay it; otherwise the destination's owner.
+    // factorisation delay it; otherwise every CTA.  Each task goes to the candidate with
+    // the least update work so far at this level (work = the task's triplets), so the
+    // wide bottom levels, whose far updates mostly land in the top columns, do not pile
+    // them on those columns' owner.
     std::vector<int> far_exec(std::max(lvl[4 * nlev + 1], 0), -1);
     for (int l = 0; l < nlev; ++l) {
       std::vector<char> busy(C, 0);
@@ -570,13 +594,17 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
             busy[owner[sched[q]]] = 1;
             ++nbusy;
           }
-      std::vector<int> idle;
+      std::vector<int> cand;
       for (int r = 0; r < C; ++r)
-        if (!busy[r]) idle.push_back(r);
-      int k = 0;
+        if (nbusy == C || !busy[r]) cand.push_back(r);
+      std::vector<long long> load(C, 0);
       for (int u = lvl[4 * l + 2]; u < lvl[4 * (l + 1) + 1]; ++u) {
         const int4 t = p.lutask[ubase + u];
-        far_exec[u] = (nbusy < C && !idle.empty()) ? idle[k++ % (int)idle.size()] : shome[t.x];
+        int best = cand[0];
+        for (int r : cand)
+          if (load[r] < load[best]) best = r;
+        far_exec[u] = best;
+        load[best] += std::max(1, t.z - t.y);
       }
     }
     for (int r = 0; r < C; ++r) {
@@ -618,7 +646,7 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
       for (int sl : own_slots[r]) cp.own_slot.push_back(sl);
       const int nsl = (int)own_slots[r].size(), ncl = (int)own_cols[r].size();
       cp.cmeta.insert(cp.cmeta.end(), {s0, (int)cp.csched.size() - s0, u0, (int)cp.cutask.size() - u0, t0,
-                                       (int)cp.cttask.size() - t0, l0, nsl, ncl, o0, ncol_max});
+                                       (int)cp.cttask.size() - t0, l0, nsl, ncl, o0, ncol_max, top_local});
       cp.max_cta_smem = std::max(cp.max_cta_smem,
                                  cluster_smem_bytes(nsl, ncl, ncol_max, ntri, (int)cp.cutask.size() - u0,
                                                     (int)cp.cttask.size() - t0, nlev, nslot, ncol));
