@@ -189,12 +189,16 @@ int como3r_linearize(como3r_graph_t graph, const double* poses, double* edge_out
  *   grad_logdepth, grad_conf  device float [sum_k P_k], pixels in the packed order of
  *             points_conf: upstream * dL/dl_p and upstream * dL/dc_p (overwritten).
  *   poses_out [N][8] (host or device) or NULL: T^K.   loss_out host [G] or NULL: E_g(T^K).
- * The forward iterations are recomputed inside the call; only the poses, steps and solve
- * outcomes of each iteration are kept (checkpoints of 7N + 8N doubles per iteration), and
- * each backward step re-linearises from its pose checkpoint and re-factorises with the
- * recorded eps.  Pixel gradients are accumulated with atomics (FP32 in the MIXED form, so
- * bitwise results can vary between runs; FP64 then rounded once in the PLAIN form).  A
- * match with c_i c_j = 0 contributes no confidence gradient.  Synchronises the stream.
+ * The forward iterations are recomputed inside the call and keep, per iteration, the poses,
+ * the step, the solve outcome and the damped factor (7N + 8N doubles and 49 per factor
+ * block + 63 per unknown keyframe); each backward step solves its adjoint system with the
+ * kept factor of its iteration (the system is not linearised or factorised again).  The
+ * kept-factor solve holds its working vector and plan in shared memory when the largest
+ * graph's fit (about 100 bytes per keyframe and 12 per factor block), else in global
+ * memory (COMO3R_SUBSTITUTE_SMEM=0 at create forces the latter, a test setting).  Pixel gradients are accumulated with atomics (FP32
+ * in the MIXED form, so bitwise results can vary between runs; FP64 then rounded once in
+ * the PLAIN form).  A match with c_i c_j = 0 contributes no confidence gradient.
+ * Synchronises the stream.
  * Returns OK or the warning bitmask of the forward iterations, or an error. */
 typedef enum { COMO3R_VJP_UNROLLED = 0, COMO3R_VJP_ENVELOPE = 1 } como3r_vjp_mode;
 int como3r_vjp(como3r_graph_t graph, const double* poses_init, int32_t iters, int32_t mode, double upstream,

@@ -115,10 +115,12 @@ struct como3r_graph {
   // adjoint workspaces (allocated by the first como3r_vjp call, grown with iters)
   int vjp_iters_cap = -1;
   double *d_ckpt = nullptr, *d_tau_hist = nullptr;
-  GraphInfoDev *d_ginfo_hist = nullptr, *d_ginfo_bwd = nullptr, *d_ginfo_final = nullptr;
+  GraphInfoDev *d_ginfo_hist = nullptr, *d_ginfo_final = nullptr;
   double *d_adj_a = nullptr, *d_adj_a2 = nullptr, *d_adj_rhs = nullptr, *d_adj_u = nullptr;
   double *d_evec = nullptr, *d_adj_rec = nullptr, *d_edge_adj = nullptr, *d_gacc = nullptr;
-  int* d_warn_bwd = nullptr;
+  // the factor of every forward iteration (blocks, column scratch), solved again backwards
+  double *d_keep_L = nullptr, *d_keep_S = nullptr, *d_sub_z = nullptr;
+  size_t sub_smem = 0;  // shared memory of the kept-factor substitution (0: d_sub_z)
 };
 
 namespace {
@@ -211,21 +213,22 @@ int enqueue_linearize(como3r_graph* g, cudaStream_t s, double* cost_hist, const 
 
 // The damped factorisation and solve of every graph: the grid-wide or the multi-SM
 // variant when one was chosen at create, else one CTA per graph.
+// `keep` (the vjp's forward iterations): where a successful factorisation also leaves L.
 cudaError_t launch_solver(como3r_graph* g, const double* gvec, double* tau, GraphInfoDev* ginfo, int* warn,
-                          cudaStream_t s, const GraphInfoDev* fixed = nullptr) {
+                          cudaStream_t s, FactorKeep keep = {}) {
   if (g->grid_ctas > 0)
     return launch_factor_solve_grid(g->grid_ctas, g->sp, g->d_A, g->d_L, g->d_colscratch, gvec, tau, g->lambda,
-                                    g->eps0, g->max_attempts, ginfo, warn, g->d_gsync, s, fixed, g->grid_extra);
+                                    g->eps0, g->max_attempts, ginfo, warn, g->d_gsync, s, keep, g->grid_extra);
   if (g->cluster_ctas > 0)
     return launch_factor_solve_cluster(g->plan.G, g->sp, g->cp, g->cluster_smem, g->d_A, gvec, tau, g->lambda,
-                                       g->eps0, g->max_attempts, ginfo, warn, s, fixed);
+                                       g->eps0, g->max_attempts, ginfo, warn, s, keep);
   return launch_factor_solve(g->plan.G, g->sp, g->smem_solve, g->solve_smem, g->d_A, g->d_L, g->d_colscratch, gvec,
-                             tau, g->lambda, g->eps0, g->max_attempts, ginfo, warn, s, fixed);
+                             tau, g->lambda, g->eps0, g->max_attempts, ginfo, warn, s, keep);
 }
 
-int enqueue_solve(como3r_graph* g, cudaStream_t s, int* iter) {
+int enqueue_solve(como3r_graph* g, cudaStream_t s, int* iter, FactorKeep keep = {}) {
   const HostPlan& p = g->plan;
-  CK(launch_solver(g, g->d_gvec, g->d_tau, g->d_ginfo, g->d_warn, s), "factor_solve");
+  CK(launch_solver(g, g->d_gvec, g->d_tau, g->d_ginfo, g->d_warn, s, keep), "factor_solve");
   CK(launch_retract(g->d_tau, g->d_poses, g->d_frozen, p.N, iter, s), "retract");
   return COMO3R_OK;
 }
@@ -331,15 +334,16 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
       (rc = dalloc(g, &g->d_poses, (size_t)N * 8)) || (rc = dalloc(g, &g->d_bad, 1)))
     return rc;
   // solver plan
-  int32_t *meta, *col_kf, *lcol_slot, *lslot_row, *lsched, *llvl;
+  int32_t *meta, *col_kf, *lcol_slot, *lslot_row, *lsched, *llvl, *lrow_off;
   int4 *ltri, *lutask;
-  int2* lttask;
+  int2 *lttask, *lrow_ent;
   if ((rc = upload(g, &meta, p.meta)) || (rc = upload(g, &col_kf, p.col_kf)) ||
       (rc = upload(g, &lcol_slot, p.lcol_slot)) || (rc = upload(g, &lslot_row, p.lslot_row)) ||
       (rc = upload(g, &lsched, p.lsched)) || (rc = upload(g, &ltri, p.ltri)) || (rc = upload(g, &lutask, p.lutask)) ||
-      (rc = upload(g, &lttask, p.lttask)) || (rc = upload(g, &llvl, p.llvl)))
+      (rc = upload(g, &lttask, p.lttask)) || (rc = upload(g, &llvl, p.llvl)) ||
+      (rc = upload(g, &lrow_off, p.lrow_off)) || (rc = upload(g, &lrow_ent, p.lrow_ent)))
     return rc;
-  g->sp = SolverPlan{meta, col_kf, lcol_slot, lslot_row, lsched, ltri, lutask, lttask, llvl};
+  g->sp = SolverPlan{meta, col_kf, lcol_slot, lslot_row, lsched, ltri, lutask, lttask, llvl, lrow_off, lrow_ent};
   // test setting COMO3R_TEST_DIAG_SHIFT=<s0>,<s1>,...: graph g's assembled diagonal is
   // lowered by s_g before every solve (missing entries 0), which makes the first epsilon
   // attempts fail by construction; off unless the variable is set
@@ -406,6 +410,18 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   if (g->smem_solve) {
     g->solve_smem = p.max_graph_smem;
     CK(factor_solve_prepare(g->solve_smem), "solver smem attribute");
+  }
+  {  // the kept-factor substitution of the vjp: its vector and plan in shared memory if they fit
+    size_t z = 16;
+    for (int k = 0; k < G; ++k) {
+      const int32_t* m = p.meta.data() + kMetaCount * k;
+      z = std::max(z, substitute_smem_bytes(m[kMetaNSlot], m[kMetaNCol], m[kMetaNLvl]));
+    }
+    const char* e = getenv("COMO3R_SUBSTITUTE_SMEM");  // test setting: 0 forces global memory
+    if (z <= factor_solve_max_smem() && !(e && atoi(e) == 0)) {
+      g->sub_smem = z;
+      CK(factor_substitute_prepare(g->sub_smem), "substitute smem attribute");
+    }
   }
   // match index check and valid counts
   CK(cudaMemsetAsync(g->d_bad, 0, sizeof(unsigned long long), g->stream), "memset");
@@ -701,19 +717,22 @@ int vjp_impl(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t 
   const int N = p.N, E = p.E, G = p.G;
   const int64_t P = p.total_px;
   int rc;
+  const size_t keep_L = (size_t)p.slot_begin.back() * 49, keep_S = (size_t)p.col_begin.back() * kColScratch;
   if (iters > g->vjp_iters_cap) {
     const int cap = std::max<int>(iters, 8);
     CK(cudaStreamSynchronize(g->stream), "sync");
     if ((rc = dalloc(g, &g->d_ckpt, (size_t)(cap + 1) * 8 * N)) || (rc = dalloc(g, &g->d_tau_hist, (size_t)cap * 7 * N)) ||
-        (rc = dalloc(g, &g->d_ginfo_hist, (size_t)cap * G)))
+        (rc = dalloc(g, &g->d_ginfo_hist, (size_t)cap * G)) || (rc = dalloc(g, &g->d_keep_L, (size_t)cap * keep_L)) ||
+        (rc = dalloc(g, &g->d_keep_S, (size_t)cap * keep_S)))
       return rc;
     if (g->vjp_iters_cap < 0 &&
-        ((rc = dalloc(g, &g->d_ginfo_bwd, G)) || (rc = dalloc(g, &g->d_ginfo_final, G)) ||
+        ((rc = dalloc(g, &g->d_ginfo_final, G)) ||
+         (g->sub_smem == 0 && (rc = dalloc(g, &g->d_sub_z, (size_t)7 * p.col_begin.back()))) ||
          (rc = dalloc(g, &g->d_adj_a, (size_t)7 * N)) ||
          (rc = dalloc(g, &g->d_adj_a2, (size_t)7 * N)) || (rc = dalloc(g, &g->d_adj_rhs, (size_t)7 * N)) ||
          (rc = dalloc(g, &g->d_adj_u, (size_t)7 * N)) || (rc = dalloc(g, &g->d_evec, (size_t)16 * E)) ||
          (rc = dalloc(g, &g->d_adj_rec, (size_t)kAdjointRecord * std::max(g->max_items, 1))) ||
-         (rc = dalloc(g, &g->d_edge_adj, (size_t)14 * E)) || (rc = dalloc(g, &g->d_warn_bwd, 1)) ||
+         (rc = dalloc(g, &g->d_edge_adj, (size_t)14 * E)) ||
          (p.mode == COMO3R_PLAIN_FP64 && (rc = dalloc(g, &g->d_gacc, (size_t)2 * P)))))
       return rc;
     g->vjp_iters_cap = cap;
@@ -722,11 +741,13 @@ int vjp_impl(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t 
   cudaStream_t s = g->stream;
   int64_t launches = 0;
   CK(mark(0), "event");
-  // forward with checkpoints: T^k, tau_k and the solve outcome of every iteration
+  // forward with checkpoints: T^k, tau_k, the solve outcome and the factor of every iteration
+  auto keep_of = [&](int k) { return FactorKeep{g->d_keep_L + (size_t)k * keep_L, g->d_keep_S + (size_t)k * keep_S}; };
   for (int k = 0; k < iters; ++k) {
     CK(cudaMemcpyAsync(g->d_ckpt + (size_t)k * 8 * N, g->d_poses, sizeof(double) * 8 * N, cudaMemcpyDeviceToDevice, s),
        "checkpoint");
-    if ((rc = enqueue_linearize(g, s, nullptr, nullptr, nullptr)) || (rc = enqueue_solve(g, s, nullptr))) return rc;
+    if ((rc = enqueue_linearize(g, s, nullptr, nullptr, nullptr)) || (rc = enqueue_solve(g, s, nullptr, keep_of(k))))
+      return rc;
     CK(cudaMemcpyAsync(g->d_tau_hist + (size_t)k * 7 * N, g->d_tau, sizeof(double) * 7 * N, cudaMemcpyDeviceToDevice,
                        s),
        "checkpoint");
@@ -766,9 +787,11 @@ int vjp_impl(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t 
       CK(cudaMemcpyAsync(g->d_poses, g->d_ckpt + (size_t)k * 8 * N, sizeof(double) * 8 * N, cudaMemcpyDeviceToDevice,
                          s),
          "restore");
-      if ((rc = enqueue_linearize(g, s, nullptr, nullptr, nullptr))) return rc;
+      // the edge transforms at T^k; H(T^k) is not formed again: its factor was kept
+      CK(launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, s), "edge_prep");
       CK(cudaMemsetAsync(g->d_adj_u, 0, sizeof(double) * 7 * N, s), "memset");
-      CK(launch_solver(g, g->d_adj_rhs, g->d_adj_u, g->d_ginfo_bwd, g->d_warn_bwd, s, g->d_ginfo_hist + (size_t)k * G),
+      CK(launch_factor_substitute(G, g->sp, keep_of(k), g->d_ginfo_hist + (size_t)k * G, g->d_adj_rhs, g->d_adj_u,
+                                  g->sub_smem, g->d_sub_z, s),
          "adjoint solve");
       CK(launch_adjoint_edge_prep(p.mode, g->d_es, E, g->d_Ad, g->d_adj_u, tau_k, g->d_evec, s), "adjoint edge prep");
       CK(mark(4 + 2 * k), "event");
@@ -781,7 +804,7 @@ int vjp_impl(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t 
       CK(launch_adjoint_gather(g->d_adj_a2, g->d_edge_adj, g->d_kf_contrib_off, g->d_kf_contrib, g->d_frozen, N,
                                nullptr, 1.0, g->d_adj_a, s),
          "adjoint gather");
-      launches += 4 + 6;
+      launches += 7;
     }
     CK(cudaMemcpyAsync(g->d_poses, g->d_ckpt + (size_t)iters * 8 * N, sizeof(double) * 8 * N,
                        cudaMemcpyDeviceToDevice, s),

@@ -130,6 +130,8 @@ struct SolverPlan {
   const int2* ttask;        // (slot, col), at t_base
   const int32_t* lvl;       // per graph (nlev+1) x 4: level offsets in sched, utask (near), utask (far), ttask;
                             // at 4 * lvl_base
+  const int32_t* row_off;   // per graph ncol+1 offsets of each block row's entries, at col_base + g
+  const int2* row_ent;      // (slot of L_rj, j) by block row r, j ascending, at slot_base - col_base
 };
 
 // Multi-SM solve: one thread-block cluster of `C` CTAs per graph.  Every column has an
@@ -167,6 +169,14 @@ inline size_t solver_smem_bytes(int nslot, int ncol, int ntri, int nu, int nt, i
   b += r16(16 * (size_t)ntri) + r16(16 * (size_t)nu) + r16(8 * (size_t)nt);
   b += r16(4 * (size_t)(ncol + 1)) + r16(4 * (size_t)nslot) + r16(4 * (size_t)ncol) + r16(16 * (size_t)(nlev + 1));
   return b;
+}
+
+// Bytes of shared memory of the kept-factor substitution of one graph: its working vector,
+// block-row entries and offsets, column-slot offsets, slot rows, schedule and levels.
+inline size_t substitute_smem_bytes(int nslot, int ncol, int nlev) {
+  auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+  return r16(8 * 7 * (size_t)ncol) + r16(8 * (size_t)(nslot - ncol)) + 2 * r16(4 * (size_t)(ncol + 1)) +
+         r16(4 * (size_t)nslot) + r16(4 * (size_t)ncol) + r16(16 * (size_t)(nlev + 1));
 }
 
 // Bytes of shared memory of one CTA of the multi-SM solve: its blocks and column scratch,
@@ -218,6 +228,13 @@ cudaError_t launch_export_dense(int num_slots, const int32_t* slot_kf_r, const i
                                 cudaStream_t s);
 // Workspace doubles per column (outside the slots): 7 Dinv + 7 rhs/solution + 49 L_cc^{-1}.
 constexpr int kColScratch = 63;
+// A factorisation kept for later solves: the graph's blocks of L at L + 49 (slot_base + s)
+// and its column scratch at S + kColScratch (col_base + c), written by a solve that
+// succeeded when L is not NULL.
+struct FactorKeep {
+  double* L;
+  double* S;
+};
 // Panel levels of the factorisation: at most this many columns, each with at most this
 // many off-diagonal blocks (7 diagonal rows + the right-hand side + 7 rows per block fit a
 // warp's 32 lanes).
@@ -227,13 +244,22 @@ constexpr int kPanelBlocks = 3;
 cudaError_t launch_factor_solve_cluster(int G, const SolverPlan& plan, const ClusterPlan& cp, size_t smem_bytes,
                                         const double* A, const double* gvec, double* tau, double lambda, double eps0,
                                         int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s,
-                                        const GraphInfoDev* fixed = nullptr);
+                                        FactorKeep keep = {});
 cudaError_t factor_solve_cluster_prepare(size_t smem_bytes, int C);
 cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t smem_bytes, const double* A,
                                 double* L, double* colscratch, const double* gvec, double* tau, double lambda,
                                 double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s,
-                                const GraphInfoDev* fixed = nullptr);
+                                FactorKeep keep = {});
 size_t factor_solve_max_smem();
+// out = -(L L^T)^{-1} rhs with the factor a successful solve kept (the adjoint systems of
+// the unrolled vjp), per graph; zero on the columns of a graph whose recorded solve
+// (rec[g].solved) failed.  rhs / out are [N][7] by keyframe; anchors are not written.
+// One CTA per graph; the working vector and the plan arrays live in shared memory
+// (smem = the largest graph's substitute_smem_bytes, set up by factor_substitute_prepare)
+// or, with smem == 0, in global memory (zwork: [total columns][7] doubles).
+cudaError_t factor_substitute_prepare(size_t smem_bytes);
+cudaError_t launch_factor_substitute(int G, const SolverPlan& plan, FactorKeep keep, const GraphInfoDev* rec,
+                                     const double* rhs, double* out, size_t smem_bytes, double* zwork, cudaStream_t s);
 // Test setting only (COMO3R_TEST_DIAG_SHIFT): A_gg -= shift[g] I on every graph's
 // assembled diagonal, launched after the assembly when the setting is given at create.
 cudaError_t launch_diag_shift(int G, const SolverPlan& plan, double* A, const double* shift, cudaStream_t s);
@@ -256,7 +282,7 @@ int factor_solve_grid_ctas();  // CTAs of the grid solve on this GPU (one per SM
 cudaError_t launch_factor_solve_grid(int ctas, const SolverPlan& plan, const double* A, double* L, double* colscratch,
                                      const double* gvec, double* tau, double lambda, double eps0, int max_attempts,
                                      GraphInfoDev* ginfo, int* warn, GridSync* sync, cudaStream_t s,
-                                     const GraphInfoDev* fixed = nullptr, unsigned extra_arrivals = 0);
+                                     FactorKeep keep = {}, unsigned extra_arrivals = 0);
 cudaError_t launch_retract(const double* tau, double* poses, const uint8_t* frozen, int N, int* iter_counter,
                            cudaStream_t s);
 // ---- adjoint of the refined cost (k_adjoint.cu)

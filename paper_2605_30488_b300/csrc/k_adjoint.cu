@@ -383,41 +383,49 @@ __global__ void adjoint_edge_kernel(const double* __restrict__ rec, const int32_
   }
 }
 
-// C = A B for 7x7 row-major matrices in shared memory, one warp: lane l computes entries
-// l and l + 32 (7 FMA each).  Reads A, B and writes C after a warp barrier.
-__device__ __forceinline__ void warp_mat7_mul(const double* A, const double* B, double* C, int lane) {
-  double c0 = 0.0, c1 = 0.0;
-  const int r0 = lane / 7, q0 = lane % 7, e1 = lane + 32, r1 = e1 / 7, q1 = e1 % 7;
+// C = A B for 7x7 row-major matrices in shared memory, one entry per thread of a 64-thread
+// block (entries 49..63 idle): every FP64 instruction holds its SM sub-partition's FP64
+// unit for ~80 cycles, so two warps (two sub-partitions) halve the product's time on one
+// warp.  C may alias A or B; all 64 threads call it.
+__device__ __forceinline__ void block_mat7_mul(const double* A, const double* B, double* C, int tid) {
+  double c = 0.0;
+  if (tid < 49) {
+    const int r = tid / 7, q = tid % 7;
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    c0 = fma(A[7 * r0 + k], B[7 * k + q0], c0);
-    if (e1 < 49) c1 = fma(A[7 * r1 + k], B[7 * k + q1], c1);
+    for (int k = 0; k < 7; ++k) c = fma(A[7 * r + k], B[7 * k + q], c);
   }
-  __syncwarp();
-  C[lane] = c0;
-  if (e1 < 49) C[e1] = c1;
-  __syncwarp();
+  __syncthreads();
+  if (tid < 49) C[tid] = c;
+  __syncthreads();
 }
 
-// Per keyframe (one warp): a' = exp(ad_tau)^T a and rhs = -phi1(ad_tau)^T a (so the solve
+// Terms of the phi1 series below: with ||X||_inf <= 1/2 the remainder after X^14 / 15! is
+// below (1/2)^15 / 16! ~ 1.5e-18, under FP64 rounding.
+constexpr int kPhiTerms = 14;
+
+// Per keyframe (two warps): a' = exp(ad_tau)^T a and rhs = -phi1(ad_tau)^T a (so the solve
 // returns u = A^{-1} tau_bar); frozen keyframes get zeros.  exp and phi1 of X = ad_tau by
-// scaling and squaring (Higham, 2005): X / 2^s with ||X / 2^s||_inf <= 1/2, a 20-term
-// Taylor series of phi1 (Horner), exp = I + X phi1, then s doublings
+// scaling and squaring (Higham, 2005): X / 2^s with ||X / 2^s||_inf <= 1/2, the Taylor
+// series of phi1 to X^14 / 15! (Horner), exp = I + X phi1, then s doublings
 // phi1(2X) = phi1(X)(exp(X) + I)/2, exp(2X) = exp(X)^2.
-__global__ void adjoint_keyframe_kernel(const double* __restrict__ a, const double* __restrict__ tau,
-                                        const uint8_t* __restrict__ frozen, int N, double* __restrict__ a_out,
-                                        double* __restrict__ rhs) {
-  __shared__ double X[49], P[49], E[49], T[49];
-  const int kf = blockIdx.x, lane = threadIdx.x;
+__global__ void __launch_bounds__(64) adjoint_keyframe_kernel(const double* __restrict__ a,
+                                                              const double* __restrict__ tau,
+                                                              const uint8_t* __restrict__ frozen, int N,
+                                                              double* __restrict__ a_out, double* __restrict__ rhs) {
+  __shared__ double X[49], P[49], E[49];
+  __shared__ int s_sq;
+  const int kf = blockIdx.x, tid = threadIdx.x;
   if (kf >= N) return;
   if (frozen[kf]) {
-    if (lane < 7) a_out[7 * kf + lane] = rhs[7 * kf + lane] = 0.0;
+    if (tid < 7) a_out[7 * kf + tid] = rhs[7 * kf + tid] = 0.0;
     return;
   }
   const double* t = tau + 7 * kf;
+  const bool ent = tid < 49;
+  const int r = tid / 7, c = tid % 7;
+  const double id = (ent && r == c) ? 1.0 : 0.0;
   // ad_tau = [[w^ + z I, v^, -v], [0, w^, 0], [0, 0, 0]]
-  for (int x = lane; x < 49; x += 32) {
-    const int r = x / 7, c = x % 7;
+  if (ent) {
     auto skew = [&](const double* w, int i, int k) -> double {
       if (i == k) return 0.0;
       if (i == 0) return k == 1 ? -w[2] : w[1];
@@ -429,57 +437,62 @@ __global__ void adjoint_keyframe_kernel(const double* __restrict__ a, const doub
     else if (r < 3 && c < 6) v = skew(t, r, c - 3);
     else if (r < 3) v = -t[r];
     else if (r < 6 && c >= 3 && c < 6) v = skew(t + 3, r - 3, c - 3);
-    X[x] = v;
+    X[tid] = v;
   }
-  __syncwarp();
-  // infinity norm (max row sum), the same value in every lane
-  double rs = 0.0;
-  if (lane < 7)
+  __syncthreads();
+  // infinity norm (max row sum) in warp 0, then the number of halvings
+  if (tid < 32) {
+    double rs = 0.0;
+    if (tid < 7)
 #pragma unroll
-    for (int c = 0; c < 7; ++c) rs += fabs(X[7 * lane + c]);
+      for (int k = 0; k < 7; ++k) rs += fabs(X[7 * tid + k]);
 #pragma unroll
-  for (int off = 4; off > 0; off >>= 1) rs = fmax(rs, __shfl_xor_sync(0xffffffffu, rs, off));
-  rs = __shfl_sync(0xffffffffu, rs, 0);
-  int sq = 0;
-  while (rs > 0.5 && sq < 64) {
-    rs *= 0.5;
-    ++sq;
+    for (int off = 4; off > 0; off >>= 1) rs = fmax(rs, __shfl_xor_sync(0xffffffffu, rs, off));
+    if (tid == 0) {
+      int sq = 0;
+      while (rs > 0.5 && sq < 64) {
+        rs *= 0.5;
+        ++sq;
+      }
+      s_sq = sq;
+    }
   }
-  const double f = ldexp(1.0, -sq);
-  for (int x = lane; x < 49; x += 32) {
-    X[x] *= f;
-    P[x] = (x % 8 == 0) ? 1.0 : 0.0;
+  __syncthreads();
+  const int sq = s_sq;
+  if (ent) {
+    X[tid] *= ldexp(1.0, -sq);
+    P[tid] = id;
   }
-  __syncwarp();
-  for (int n = 20; n >= 1; --n) {  // P <- I + X P / (n + 1)
-    warp_mat7_mul(X, P, T, lane);
-    const double inv = 1.0 / (double)(n + 1);
-    for (int x = lane; x < 49; x += 32) P[x] = ((x % 8 == 0) ? 1.0 : 0.0) + T[x] * inv;
-    __syncwarp();
+  __syncthreads();
+#pragma unroll
+  for (int n = kPhiTerms; n >= 1; --n) {  // P <- I + X P / (n + 1)
+    block_mat7_mul(X, P, P, tid);
+    if (ent) P[tid] = fma(P[tid], 1.0 / (double)(n + 1), id);
+    __syncthreads();
   }
-  warp_mat7_mul(X, P, E, lane);
-  if (lane < 7) E[8 * lane] += 1.0;
-  __syncwarp();
+  block_mat7_mul(X, P, E, tid);
+  if (ent) E[tid] += id;
+  __syncthreads();
   for (int s2 = 0; s2 < sq; ++s2) {
-    if (lane < 7) E[8 * lane] += 1.0;  // E + I
-    __syncwarp();
-    warp_mat7_mul(P, E, T, lane);
-    if (lane < 7) E[8 * lane] -= 1.0;
-    for (int x = lane; x < 49; x += 32) P[x] = 0.5 * T[x];
-    __syncwarp();
-    warp_mat7_mul(E, E, T, lane);
-    for (int x = lane; x < 49; x += 32) E[x] = T[x];
-    __syncwarp();
+    if (ent) E[tid] += id;  // E + I
+    __syncthreads();
+    block_mat7_mul(P, E, P, tid);
+    if (ent) {
+      P[tid] *= 0.5;
+      E[tid] -= id;
+    }
+    __syncthreads();
+    block_mat7_mul(E, E, E, tid);
   }
   const double* ak = a + 7 * kf;
-  if (lane < 14) {
-    const int c = lane % 7;
-    const double* M = lane < 7 ? E : P;
+  if (tid < 14) {
+    const int q = tid % 7;
+    const double* M = tid < 7 ? E : P;
     double acc = 0.0;
 #pragma unroll
-    for (int r = 0; r < 7; ++r) acc = fma(M[7 * r + c], ak[r], acc);
-    if (lane < 7) a_out[7 * kf + c] = acc;
-    else rhs[7 * kf + c] = -acc;
+    for (int k = 0; k < 7; ++k) acc = fma(M[7 * k + q], ak[k], acc);
+    if (tid < 7) a_out[7 * kf + q] = acc;
+    else rhs[7 * kf + q] = -acc;
   }
 }
 
@@ -618,7 +631,7 @@ cudaError_t launch_adjoint_edge(const double* rec, const int32_t* item_off, int 
 cudaError_t launch_adjoint_keyframe(const double* a, const double* tau, const uint8_t* frozen, int N, double* a_out,
                                     double* rhs, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  adjoint_keyframe_kernel<<<N, 32, 0, s>>>(a, tau, frozen, N, a_out, rhs);
+  adjoint_keyframe_kernel<<<N, 64, 0, s>>>(a, tau, frozen, N, a_out, rhs);
   return cudaGetLastError();
 }
 

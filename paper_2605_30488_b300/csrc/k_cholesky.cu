@@ -436,7 +436,7 @@ template <bool SMEM>
 __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
     SolverPlan P, const double* __restrict__ A, double* Lg, double* Sg, const double* __restrict__ gvec,
     double* __restrict__ tau, double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
-    const GraphInfoDev* __restrict__ fixed) {
+    FactorKeep keep) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ int s_fail;
   __shared__ double s_xbuf[kPanelXchg];
@@ -488,18 +488,10 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
   const double* Ag = A + (int64_t)sbase * 49;
   const int* col_kf = P.col_kf + cbase;
 
-  // `fixed` (adjoint re-solves): exactly the attempt that succeeded in the recorded
-  // forward solve, or a zero result where that solve failed
-  int attempt = 0, last = max_attempts;
-  if (fixed) {
-    if (!fixed[g].solved) last = 0;
-    attempt = fixed[g].attempts - 1;
-    if (last) last = attempt + 1;
-  }
+  int attempt = 0;
   bool ok = false;
   double pow100 = 1.0;  // 100^attempt, exact in FP64
-  for (int r = 0; r < attempt; ++r) pow100 *= 100.0;
-  for (; attempt < last; ++attempt, pow100 *= 100.0) {
+  for (; attempt < max_attempts; ++attempt, pow100 *= 100.0) {
     const double eps = eps0 * pow100;
     if (SMEM) {
       stage(C.L, Ag, (int64_t)nslot * 49, tid);
@@ -572,6 +564,11 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_kernel(
       __syncthreads();
     }
     for (int x = tid; x < 7 * ncol; x += kSolveThreads) tau[7 * col_kf[x / 7] + x % 7] = y_of<false>(C, x / 7)[x % 7];
+    if (keep.L) {
+      for (int64_t x = tid; x < (int64_t)nslot * 49; x += kSolveThreads) keep.L[(int64_t)sbase * 49 + x] = C.L[x];
+      for (int64_t x = tid; x < (int64_t)ncol * kColScratch; x += kSolveThreads)
+        keep.S[(int64_t)cbase * kColScratch + x] = C.S[x];
+    }
   } else {
     for (int x = tid; x < 7 * ncol; x += kSolveThreads) tau[7 * col_kf[x / 7] + x % 7] = 0.0;
   }
@@ -629,7 +626,7 @@ __device__ bool grid_barrier(GridSync* gs, int* s_ok, unsigned extra) {
 __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
     SolverPlan P, const double* __restrict__ A, double* Lg, double* Sg, const double* __restrict__ gvec,
     double* __restrict__ tau, double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
-    const GraphInfoDev* __restrict__ fixed, GridSync* gs, unsigned extra) {
+    FactorKeep keep, GridSync* gs, unsigned extra) {
   __shared__ double s_xbuf[kPanelXchg];
   __shared__ int s_ok;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -664,16 +661,10 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
   const int* col_kf = P.col_kf + cbase;
   volatile int* vfail = gs->fail;
 
-  int attempt = 0, last = max_attempts;
-  if (fixed) {
-    if (!fixed[0].solved) last = 0;
-    attempt = fixed[0].attempts - 1;
-    if (last) last = attempt + 1;
-  }
+  int attempt = 0;
   bool ok = false, alive = true;
   double pow100 = 1.0;
-  for (int r = 0; r < attempt; ++r) pow100 *= 100.0;
-  for (; attempt < last && alive; ++attempt, pow100 *= 100.0) {
+  for (; attempt < max_attempts && alive; ++attempt, pow100 *= 100.0) {
     const double eps = eps0 * pow100;
     for (int64_t x = gt; x < (int64_t)nslot * 49; x += GT) C.L[x] = Ag[x];
     if (gt == 0) vfail[0] = 0;
@@ -744,6 +735,10 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
   }
   bool solved = ok && alive;
   for (int x = gt; x < 7 * ncol; x += GT) tau[7 * col_kf[x / 7] + x % 7] = solved ? y_of<false>(C, x / 7)[x % 7] : 0.0;
+  if (solved && keep.L) {  // (the back substitution's last barrier ordered every write before these reads)
+    for (int64_t x = gt; x < (int64_t)nslot * 49; x += GT) keep.L[(int64_t)sbase * 49 + x] = C.L[x];
+    for (int64_t x = gt; x < (int64_t)ncol * kColScratch; x += GT) keep.S[(int64_t)cbase * kColScratch + x] = C.S[x];
+  }
   // every CTA's tau is written before the stamp; a CTA whose last wait ran out zeroes its
   // part again (the others then run out too, or had already given up and written zeros)
   if (alive) alive = grid_barrier(gs, &s_ok, extra);
@@ -775,7 +770,7 @@ constexpr int kClusterWarps = kClusterThreads / 32;
 __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kernel(
     SolverPlan P, ClusterPlan CP, const double* __restrict__ A, const double* __restrict__ gvec,
     double* __restrict__ tau, double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
-    const GraphInfoDev* __restrict__ fixed) {
+    FactorKeep keep) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char dyn[];
@@ -831,16 +826,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
   const double* Ag = A + (int64_t)sbase * 49;
   const int* col_kf = P.col_kf + cbase;
 
-  int attempt = 0, last = max_attempts;
-  if (fixed) {
-    if (!fixed[g].solved) last = 0;
-    attempt = fixed[g].attempts - 1;
-    if (last) last = attempt + 1;
-  }
+  int attempt = 0;
   bool ok = false;
   double pow100 = 1.0;
-  for (int r = 0; r < attempt; ++r) pow100 *= 100.0;
-  for (; attempt < last; ++attempt, pow100 *= 100.0) {
+  for (; attempt < max_attempts; ++attempt, pow100 *= 100.0) {
     const double eps = eps0 * pow100;
     // this CTA's blocks of A (gathered by slot), damping and the forward right-hand side
     for (int64_t x = tid; x < (int64_t)nsl * 49; x += kClusterThreads) {
@@ -923,6 +912,15 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
     }
     for (int x = tid; x < 7 * ncl; x += kClusterThreads)
       tau[7 * col_kf[cs[x / 7]] + x % 7] = y_of<true>(C, cs[x / 7])[x % 7];
+    if (keep.L) {  // this CTA's blocks and columns (its own shared memory only)
+      for (int64_t x = tid; x < (int64_t)nsl * 49; x += kClusterThreads)
+        keep.L[(int64_t)(sbase + own[x / 49]) * 49 + x % 49] = C.L[x];
+      for (int x = tid; x < ncl * kColScratch; x += kClusterThreads) {
+        const int col = cs[x / kColScratch];
+        keep.S[(int64_t)(cbase + col) * kColScratch + x % kColScratch] =
+            C.S[(int64_t)(ch[col] & 0xffffff) * kColScratch + x % kColScratch];
+      }
+    }
   } else {
     for (int x = tid; x < 7 * ncl; x += kClusterThreads) tau[7 * col_kf[cs[x / 7]] + x % 7] = 0.0;
   }
@@ -933,6 +931,261 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
   }
   cl.sync();  // no CTA leaves while another may still read its shared memory
   if (tid == 0 && rank == 0) ginfo[g].done_ns = globaltimer_ns();  // every CTA's tau is written
+}
+
+// ---- solves with a kept factor ----------------------------------------------------------
+// z = -(L L^T)^{-1} rhs with the blocks of L and the L_cc^{-1} a successful factorisation
+// kept: the forward substitution level by level from the leaves, each column gathering
+// its block row (z_c = L_cc^{-1} (z_c - sum_j L_cj z_j), j ascending), then the back
+// substitution from the root (z_c = L_cc^{-T} (z_c - sum_r L_rc^T z_r)).  One CTA per
+// graph with a CTA barrier between levels; the plan arrays and the working vector in
+// shared memory when they fit, the factor read through the L2 (a kept factor is small).
+// FP64 instructions occupy an SM sub-partition's FP64 unit for ~80 cycles each, so a level
+// with more than kSubSpread columns packs four columns per warp (8 lanes each, one row per
+// lane, the blocks of a column in sequence: ~9 FP64 instructions per column), and a narrow
+// level gives each column a warp of its own (the row blocks four abreast, a shorter
+// dependent chain of ~20 instructions).
+constexpr int kSubSpread = 8;
+constexpr int kSubAhead = 4;  // blocks whose loads a packed column issues before their FMAs
+
+// one column per warp: lanes 7 b + i (b < 4) take row i of every fourth block of the row,
+// the four partial sums meet by shuffles, lane q < 7 forms z_c[q] with row q of L_cc^{-1}
+__device__ void substitute_forward_spread(const double* Lb, const double* Sb, const int* row_off, const int2* row_ent,
+                                          double* Z, int col, int lane) {
+  const int grp = lane / 7, i = lane % 7;
+  const int r0 = row_off[col], nr = row_off[col + 1] - r0;
+  double part = 0.0;
+  if (grp < 4) {
+    for (int b = grp; b < nr; b += 4) {
+      const int2 e = row_ent[r0 + b];
+      const double* B = Lb + (int64_t)e.x * 49 + 7 * i;
+      const double* zj = Z + 7 * e.y;
+      double p0 = B[0] * zj[0];
+      double p1 = B[1] * zj[1];
+      p0 = fma(B[2], zj[2], p0);
+      p1 = fma(B[3], zj[3], p1);
+      p0 = fma(B[4], zj[4], p0);
+      p1 = fma(B[5], zj[5], p1);
+      p0 = fma(B[6], zj[6], p0);
+      part += p0 + p1;
+    }
+  }
+  const double o1 = __shfl_sync(kFull, part, (i + 7) & 31);
+  const double o2 = __shfl_sync(kFull, part, (i + 14) & 31);
+  const double o3 = __shfl_sync(kFull, part, (i + 21) & 31);
+  double* zc = Z + 7 * col;
+  const double t = (lane < 7) ? zc[i] - ((part + o1) + (o2 + o3)) : 0.0;
+  const double* X = Sb + (int64_t)col * kColScratch + 14;  // L_cc^{-1}, row-major
+  double yq = 0.0;
+#pragma unroll
+  for (int r = 0; r < 7; ++r) {
+    const double tr = __shfl_sync(kFull, t, r);
+    if (lane < 7 && r <= i) yq = fma(X[7 * i + r], tr, yq);
+  }
+  __syncwarp();
+  if (lane < 7) zc[i] = yq;
+}
+
+// the back substitution of one column per warp: the arithmetic of backward_column
+__device__ void substitute_backward_spread(const double* Lb, const double* Sb, const int* col_slot,
+                                           const int* slot_row, double* Z, int col, int lane) {
+  const int grp = lane / 7, q = lane % 7;
+  const int s_begin = col_slot[col] + 1, nb = col_slot[col + 1] - s_begin;
+  double part = 0.0;
+  if (grp < 4) {
+    for (int b = grp; b < nb; b += 4) {
+      const double* B = Lb + (int64_t)(s_begin + b) * 49;
+      const double* xr = Z + 7 * slot_row[s_begin + b];
+      double p0 = B[q] * xr[0];
+      double p1 = B[7 + q] * xr[1];
+      p0 = fma(B[14 + q], xr[2], p0);
+      p1 = fma(B[21 + q], xr[3], p1);
+      p0 = fma(B[28 + q], xr[4], p0);
+      p1 = fma(B[35 + q], xr[5], p1);
+      p0 = fma(B[42 + q], xr[6], p0);
+      part += p0 + p1;
+    }
+  }
+  const double o1 = __shfl_sync(kFull, part, (q + 7) & 31);
+  const double o2 = __shfl_sync(kFull, part, (q + 14) & 31);
+  const double o3 = __shfl_sync(kFull, part, (q + 21) & 31);
+  double* zc = Z + 7 * col;
+  const double t = (lane < 7) ? zc[q] - ((part + o1) + (o2 + o3)) : 0.0;
+  const double* X = Sb + (int64_t)col * kColScratch + 14;
+  double xq = 0.0;
+#pragma unroll
+  for (int r = 0; r < 7; ++r) {
+    const double tr = __shfl_sync(kFull, t, r);
+    if (lane < 7 && r >= q) xq = fma(X[7 * r + q], tr, xq);
+  }
+  __syncwarp();
+  if (lane < 7) zc[q] = xq;
+}
+
+// four columns per warp: segment s = lane / 8 takes column cols[s] (s < ncols), its lane
+// i < 7 row i.  s = sum_j L_cj z_j - z_c accumulates in one chain (so t = -s), then
+// z_c = -L_cc^{-1} s with the segment's s_r by shuffles.
+__device__ void substitute_forward_packed(const double* Lb, const double* Sb, const int* row_off, const int2* row_ent,
+                                          double* Z, const int* cols, int ncols, int lane) {
+  const int seg = lane >> 3, i = lane & 7;
+  const bool act = seg < ncols && i < 7;
+  const int col = cols[seg < ncols ? seg : 0];
+  const double* X = Sb + (int64_t)col * kColScratch + 14 + 7 * i;
+  double xr[7];  // row i of L_cc^{-1}, loaded ahead of the chain
+#pragma unroll
+  for (int r = 0; r < 7; ++r) xr[r] = act && r <= i ? X[r] : 0.0;
+  double sacc = 0.0;
+  if (act) {
+    sacc = -Z[7 * col + i];
+    const int r0 = row_off[col], r1 = row_off[col + 1];
+    for (int b0 = r0; b0 < r1; b0 += kSubAhead) {  // the loads of kSubAhead blocks, then their FMAs
+      double bv[kSubAhead][7];
+      int zo[kSubAhead];
+#pragma unroll
+      for (int u = 0; u < kSubAhead; ++u) {
+        const int2 e = b0 + u < r1 ? row_ent[b0 + u] : make_int2(0, -1);
+        zo[u] = 7 * e.y;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) bv[u][q] = e.y >= 0 ? Lb[(int64_t)e.x * 49 + 7 * i + q] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kSubAhead; ++u)
+        if (zo[u] >= 0)
+#pragma unroll
+          for (int q = 0; q < 7; ++q) sacc = fma(bv[u][q], Z[zo[u] + q], sacc);
+    }
+  }
+  double y = 0.0;
+#pragma unroll
+  for (int r = 0; r < 7; ++r) {
+    const double sr = __shfl_sync(kFull, sacc, (lane & ~7) | r);
+    if (act && r <= i) y = fma(xr[r], sr, y);
+  }
+  __syncwarp();
+  if (act) Z[7 * col + i] = -y;
+}
+
+__device__ void substitute_backward_packed(const double* Lb, const double* Sb, const int* col_slot,
+                                           const int* slot_row, double* Z, const int* cols, int ncols, int lane) {
+  const int seg = lane >> 3, q = lane & 7;
+  const bool act = seg < ncols && q < 7;
+  const int col = cols[seg < ncols ? seg : 0];
+  const double* X = Sb + (int64_t)col * kColScratch + 14 + q;
+  double xc[7];  // column q of L_cc^{-1}, loaded ahead of the chain
+#pragma unroll
+  for (int r = 0; r < 7; ++r) xc[r] = act && r >= q ? X[7 * r] : 0.0;
+  double sacc = 0.0;
+  if (act) {
+    sacc = -Z[7 * col + q];
+    const int s0 = col_slot[col] + 1, s1 = col_slot[col + 1];
+    for (int b0 = s0; b0 < s1; b0 += kSubAhead) {
+      double bv[kSubAhead][7];
+      int zo[kSubAhead];
+#pragma unroll
+      for (int u = 0; u < kSubAhead; ++u) {
+        const bool has = b0 + u < s1;
+        zo[u] = has ? 7 * slot_row[b0 + u] : -1;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) bv[u][i] = has ? Lb[(int64_t)(b0 + u) * 49 + 7 * i + q] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kSubAhead; ++u)
+        if (zo[u] >= 0)
+#pragma unroll
+          for (int i = 0; i < 7; ++i) sacc = fma(bv[u][i], Z[zo[u] + i], sacc);
+    }
+  }
+  double x = 0.0;
+#pragma unroll
+  for (int r = 0; r < 7; ++r) {
+    const double sr = __shfl_sync(kFull, sacc, (lane & ~7) | r);
+    if (act && r >= q) x = fma(xc[r], sr, x);
+  }
+  __syncwarp();
+  if (act) Z[7 * col + q] = -x;
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(kSolveThreads) factor_substitute_kernel(SolverPlan P, FactorKeep keep,
+                                                                          const GraphInfoDev* __restrict__ rec,
+                                                                          const double* __restrict__ rhs,
+                                                                          double* __restrict__ out, double* zwork) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const int g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int* m = P.meta + kMetaCount * g;
+  const int cbase = m[kMetaColBase], ncol = m[kMetaNCol], sbase = m[kMetaSlotBase], nslot = m[kMetaNSlot];
+  const int nlev = m[kMetaNLvl];
+  if (ncol == 0) return;
+  const int* col_kf = P.col_kf + cbase;
+  if (!rec[g].solved) {
+    for (int x = tid; x < 7 * ncol; x += kSolveThreads) out[7 * col_kf[x / 7] + x % 7] = 0.0;
+    return;
+  }
+  const double* Lb = keep.L + (int64_t)sbase * 49;
+  const double* Sb = keep.S + (int64_t)cbase * kColScratch;
+  const int* col_slot = P.col_slot + cbase + g;
+  const int* slot_row = P.slot_row + sbase;
+  const int* row_off = P.row_off + cbase + g;
+  const int2* row_ent = P.row_ent + (sbase - cbase);
+  const int* sched = P.sched + cbase;
+  const int* lvl = P.lvl + 4 * m[kMetaLvlBase];
+  // the kept factor was written iterations ago and has left the L2 since: bring all of it
+  // back at once (one prefetch per 128-byte line) instead of level by level
+  {
+    const char* l0 = reinterpret_cast<const char*>(Lb);
+    const char* s0 = reinterpret_cast<const char*>(Sb);
+    const int64_t nl = ((int64_t)nslot * 49 * 8 + 127) / 128, ns = ((int64_t)ncol * kColScratch * 8 + 127) / 128;
+    for (int64_t x = tid; x < nl + ns; x += kSolveThreads) {
+      const char* p = x < nl ? l0 + 128 * x : s0 + 128 * (x - nl);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+    }
+  }
+  double* Z;
+  if (SMEM) {  // the layout of substitute_smem_bytes
+    unsigned char* q = dyn;
+    Z = carve<double>(q, (size_t)7 * ncol);
+    int2* re = carve<int2>(q, nslot - ncol);
+    int* ro = carve<int>(q, ncol + 1);
+    int* cs = carve<int>(q, ncol + 1);
+    int* sr = carve<int>(q, nslot);
+    int* sc = carve<int>(q, ncol);
+    int* lv = carve<int>(q, 4 * (nlev + 1));
+    stage(re, row_ent, nslot - ncol, tid);
+    stage(ro, row_off, ncol + 1, tid);
+    stage(cs, col_slot, ncol + 1, tid);
+    stage(sr, slot_row, nslot, tid);
+    stage(sc, sched, ncol, tid);
+    stage(lv, lvl, 4 * (nlev + 1), tid);
+    row_ent = re; row_off = ro; col_slot = cs; slot_row = sr; sched = sc; lvl = lv;
+  } else {
+    Z = zwork + (int64_t)cbase * 7;
+  }
+  for (int x = tid; x < 7 * ncol; x += kSolveThreads) Z[x] = -rhs[7 * col_kf[x / 7] + x % 7];
+  async_wait_all();
+  __syncthreads();
+  for (int lv = 0; lv < nlev; ++lv) {
+    const int q0 = lvl[4 * lv], n = lvl[4 * lv + 4] - q0;
+    if (n <= kSubSpread) {
+      for (int q = warp; q < n; q += kSolveWarps)
+        substitute_forward_spread(Lb, Sb, row_off, row_ent, Z, sched[q0 + q], lane);
+    } else {
+      for (int q = 4 * warp; q < n; q += 4 * kSolveWarps)
+        substitute_forward_packed(Lb, Sb, row_off, row_ent, Z, sched + q0 + q, min(4, n - q), lane);
+    }
+    __syncthreads();
+  }
+  for (int lv = nlev - 1; lv >= 0; --lv) {
+    const int q0 = lvl[4 * lv], n = lvl[4 * lv + 4] - q0;
+    if (n <= kSubSpread) {
+      for (int q = warp; q < n; q += kSolveWarps)
+        substitute_backward_spread(Lb, Sb, col_slot, slot_row, Z, sched[q0 + q], lane);
+    } else {
+      for (int q = 4 * warp; q < n; q += 4 * kSolveWarps)
+        substitute_backward_packed(Lb, Sb, col_slot, slot_row, Z, sched + q0 + q, min(4, n - q), lane);
+    }
+    __syncthreads();
+  }
+  for (int x = tid; x < 7 * ncol; x += kSolveThreads) out[7 * col_kf[x / 7] + x % 7] = Z[x];
 }
 
 }  // namespace
@@ -960,7 +1213,7 @@ int factor_solve_grid_ctas() {
 cudaError_t launch_factor_solve_grid(int ctas, const SolverPlan& plan, const double* A, double* L, double* colscratch,
                                      const double* gvec, double* tau, double lambda, double eps0, int max_attempts,
                                      GraphInfoDev* ginfo, int* warn, GridSync* sync, cudaStream_t s,
-                                     const GraphInfoDev* fixed, unsigned extra_arrivals) {
+                                     FactorKeep keep, unsigned extra_arrivals) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)ctas);
   cfg.blockDim = dim3(kSolveThreads);
@@ -972,7 +1225,7 @@ cudaError_t launch_factor_solve_grid(int ctas, const SolverPlan& plan, const dou
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, factor_solve_grid_kernel, plan, A, L, colscratch, gvec, tau, lambda, eps0,
-                            max_attempts, ginfo, warn, fixed, sync, extra_arrivals);
+                            max_attempts, ginfo, warn, keep, sync, extra_arrivals);
 }
 
 // Test setting only: subtracts shift[g] from every diagonal entry of graph g's assembled
@@ -996,6 +1249,22 @@ cudaError_t launch_diag_shift(int G, const SolverPlan& plan, double* A, const do
   return cudaGetLastError();
 }
 
+cudaError_t factor_substitute_prepare(size_t smem_bytes) {
+  return cudaFuncSetAttribute(factor_substitute_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_bytes);
+}
+
+cudaError_t launch_factor_substitute(int G, const SolverPlan& plan, FactorKeep keep, const GraphInfoDev* rec,
+                                     const double* rhs, double* out, size_t smem_bytes, double* zwork, cudaStream_t s) {
+  if (G <= 0) return cudaSuccess;
+  if (!keep.L || !keep.S || (smem_bytes == 0 && !zwork)) return cudaErrorInvalidValue;
+  if (smem_bytes)
+    factor_substitute_kernel<true><<<G, kSolveThreads, smem_bytes, s>>>(plan, keep, rec, rhs, out, nullptr);
+  else
+    factor_substitute_kernel<false><<<G, kSolveThreads, 0, s>>>(plan, keep, rec, rhs, out, zwork);
+  return cudaGetLastError();
+}
+
 cudaError_t factor_solve_prepare(size_t smem_bytes) {
   return cudaFuncSetAttribute(factor_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
@@ -1003,14 +1272,14 @@ cudaError_t factor_solve_prepare(size_t smem_bytes) {
 cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t smem_bytes, const double* A,
                                 double* L, double* colscratch, const double* gvec, double* tau, double lambda,
                                 double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s,
-                                const GraphInfoDev* fixed) {
+                                FactorKeep keep) {
   if (G <= 0) return cudaSuccess;
   if (smem) {
     factor_solve_kernel<true><<<G, kSolveThreads, smem_bytes, s>>>(plan, A, L, colscratch, gvec, tau, lambda, eps0,
-                                                                   max_attempts, ginfo, warn, fixed);
+                                                                   max_attempts, ginfo, warn, keep);
   } else {
     factor_solve_kernel<false><<<G, kSolveThreads, 0, s>>>(plan, A, L, colscratch, gvec, tau, lambda, eps0,
-                                                           max_attempts, ginfo, warn, fixed);
+                                                           max_attempts, ginfo, warn, keep);
   }
   return cudaGetLastError();
 }
@@ -1030,7 +1299,7 @@ cudaError_t factor_solve_cluster_prepare(size_t smem_bytes, int C) {
 cudaError_t launch_factor_solve_cluster(int G, const SolverPlan& plan, const ClusterPlan& cp, size_t smem_bytes,
                                         const double* A, const double* gvec, double* tau, double lambda, double eps0,
                                         int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s,
-                                        const GraphInfoDev* fixed) {
+                                        FactorKeep keep) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(G * cp.C));
   cfg.blockDim = dim3(kClusterThreads);
@@ -1044,7 +1313,7 @@ cudaError_t launch_factor_solve_cluster(int G, const SolverPlan& plan, const Clu
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, factor_solve_cluster_kernel, plan, cp, A, gvec, tau, lambda, eps0, max_attempts,
-                            ginfo, warn, fixed);
+                            ginfo, warn, keep);
 }
 
 }  // namespace como3r

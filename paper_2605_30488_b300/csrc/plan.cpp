@@ -363,6 +363,20 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
       const auto it = std::lower_bound(rows[c].begin(), rows[c].end(), r);
       return slot_base[c] + 1 + (int)(it - rows[c].begin());
     };
+    // blocks of L by block row (the left-looking forward substitution with a kept factor):
+    // row r lists (slot of L_rj, j) for j < r in ascending j
+    {
+      std::vector<int> cnt(n + 1, 0);
+      for (int k = 0; k < n; ++k)
+        for (int r : rows[k]) ++cnt[r + 1];
+      for (int r = 0; r < n; ++r) cnt[r + 1] += cnt[r];
+      const size_t e0 = p.lrow_ent.size();
+      p.lrow_ent.resize(e0 + (size_t)cnt[n]);
+      std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+      for (int k = 0; k < n; ++k)
+        for (int r : rows[k]) p.lrow_ent[e0 + (size_t)fill[r]++] = make_int2(slot_of(r, k), k);
+      p.lrow_off.insert(p.lrow_off.end(), cnt.begin(), cnt.end());
+    }
     for (int k = 0; k < n; ++k) {
       const int kc = p.col_kf[cbase + k];
       p.slot_kf_r.push_back(kc);

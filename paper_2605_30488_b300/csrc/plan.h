@@ -28,6 +28,10 @@ struct HostPlan {
   std::vector<int32_t> meta, lcol_slot, lslot_row, lsched, llvl;
   std::vector<int4> ltri, lutask;
   std::vector<int2> lttask;
+  // blocks of L by block row: per graph ncol + 1 offsets (at col_begin[g] + g) into
+  // (local slot, column) entries (graph g's at slot_begin[g] - col_begin[g])
+  std::vector<int32_t> lrow_off;
+  std::vector<int2> lrow_ent;
   std::vector<int8_t> order_kind;  // per graph: 0 minimum degree, 1 nested dissection
   std::vector<int32_t> slot_kf_r, slot_kf_c;
   // assembly (entries edge * 2 + negate, in edge order)

@@ -241,12 +241,28 @@ def test_vjp_full_size_mixed_matches_fp64(C, adjoint_workload):
             assert abs(float(a[k] @ v - b[k] @ v)) <= tol * mag, (vjp_mode, iters, k)
 
 
-def test_vjp_with_multi_sm_solve(C, mid, monkeypatch):
-    """The adjoint's recorded-eps re-solves through the multi-SM factorisation."""
-    monkeypatch.setenv("COMO3R_SOLVE_CLUSTER", "4")
+@pytest.mark.parametrize("setting", [("COMO3R_SOLVE_CLUSTER", "4"), ("COMO3R_SOLVE_GRID", "1"),
+                                     ("COMO3R_SUBSTITUTE_SMEM", "0")])
+def test_vjp_with_each_kept_factor(C, mid, monkeypatch, setting):
+    """The adjoint systems solved with the factor kept by the multi-SM (cluster) and the
+    grid-wide factorisations, and with the substitution's working vector in global memory."""
+    monkeypatch.setenv(*setting)
     gl, gc, _, _, _ = gpu_grads(C, mid, 0, 2, C.VJP_UNROLLED)
     rng = np.random.default_rng(7)
     vl, vc = rng.normal(size=gl.size), rng.normal(size=gl.size)
     ref = O.refined_cost_derivative(mid, mid.poses_init, 2, vl, vc)
+    mag = float(np.abs(gl * vl).sum() + np.abs(gc * vc).sum())
+    assert abs(float(gl @ vl + gc @ vc) - ref) <= TOL[0] * mag
+
+
+def test_vjp_batch_of_graphs_matches_complex_step(C):
+    """Three graphs of different sizes in one handle: every graph's adjoint systems are
+    solved with its own kept factor (one CTA per graph)."""
+    specs = [dict(n_kf=3), dict(n_kf=4), dict(n_kf=2)]
+    prob = make_problem(11, H=24, W=32, f=25.0, n_inter=1, iters=3, graph_specs=specs)
+    gl, gc, _, _, _ = gpu_grads(C, prob, 0, 3, C.VJP_UNROLLED)
+    rng = np.random.default_rng(3)
+    vl, vc = rng.normal(size=gl.size), rng.normal(size=gl.size)
+    ref = O.refined_cost_derivative(prob, prob.poses_init, 3, vl, vc)
     mag = float(np.abs(gl * vl).sum() + np.abs(gc * vc).sum())
     assert abs(float(gl @ vl + gc @ vc) - ref) <= TOL[0] * mag
