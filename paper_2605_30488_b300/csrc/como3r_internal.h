@@ -240,6 +240,14 @@ struct FactorKeep {
 // warp's 32 lanes).
 constexpr int kPanelCols = 4;
 constexpr int kPanelBlocks = 3;
+// A level (or a CTA's part of a level in the multi-SM solve) with a single column is a
+// panel when that column has at most this many off-diagonal blocks: four warps eliminate
+// its first 32 rows and then solve the last four of its 8 + 7 x 4 = 36 against L_cc.
+constexpr int kPanel4Blocks = 4;
+// A CTA of the multi-SM solve (8 warps) factors up to this many of its columns of a level
+// as whole panels, one warp each (a fifth column would otherwise turn the CTA's level into
+// diagonal factorisations followed by off-diagonal solves, about twice the dependent chain).
+constexpr int kClusterPanelCols = 8;
 // The multi-SM solve (same arguments; `cp` adds the cluster plan; smem_bytes per CTA).
 cudaError_t launch_factor_solve_cluster(int G, const SolverPlan& plan, const ClusterPlan& cp, size_t smem_bytes,
                                         const double* A, const double* gvec, double* tau, double lambda, double eps0,

@@ -259,16 +259,21 @@ __device__ void panel_factor(const SolveCtx& C, int col, int lane, int* fail) {
 // pivot, so it is never rewritten within a column) across one named barrier of the four
 // warps (barrier 1; all four warps call this together and pass every barrier).  Every
 // entry sees the operations of panel_factor in the same order: bitwise the same factor.
+// A column with kPanel4Blocks off-diagonal blocks has 36 rows: rows 32..35 (block 3, rows
+// 3..6) stay out of the elimination (any instruction for them in the pivot loop would
+// lengthen every column's chain) and are solved afterwards against the finished L_cc by
+// lanes 0..3 of warp 0, with the operations of the off-diagonal solve: bitwise what the
+// elimination would give them.
 __device__ __forceinline__ void panel_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 template <bool CL>
 __device__ void panel_factor4(const SolveCtx& C, int col, int warp, int lane, double* xbuf, int* fail) {
   const int dslot = C.col_slot[col], nb = C.col_slot[col + 1] - dslot - 1;
-  if (nb > kPanelBlocks) {  // never planned; the same decision in all four warps
+  if (nb > kPanel4Blocks) {  // never planned; the same decision in all four warps
     if (warp == 0 && lane == 0) raise_fail<CL>(C, fail);
     return;
   }
-  const int rows = 8 + 7 * nb;  // <= 29
+  const int rows = min(8 + 7 * nb, 32);
   const bool has = lane < rows;
   double* D = blk<CL>(C, dslot);
   double* row = nullptr;
@@ -320,6 +325,25 @@ __device__ void panel_factor4(const SolveCtx& C, int col, int warp, int lane, do
   }
   if (lane < 7 && (lane & 3) == warp) dinv_of<CL>(C, col)[lane] = myinv;
   if (__any_sync(kFull, bad) && lane == 0) raise_fail<CL>(C, fail);
+  if (nb == kPanel4Blocks) {  // rows 32..35 (the same decision in all four warps)
+    panel_barrier();           // L_cc and its pivot inverses are in place
+    if (warp == 0 && lane < 4) {
+      const double* Lc = D;
+      const double* dv = dinv_of<CL>(C, col);
+      double* B = blk<CL>(C, dslot + kPanel4Blocks) + 7 * (3 + lane);
+      double sr[7];
+#pragma unroll
+      for (int c = 0; c < 7; ++c) sr[c] = B[c];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        sr[q] *= dv[q];
+#pragma unroll
+        for (int c = q + 1; c < 7; ++c) sr[c] = fma(-Lc[7 * c + q], sr[q], sr[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 7; ++c) B[c] = sr[c];
+    }
+  }
 }
 
 // T: item x < 7 * nt: row (x % 7) of off-diagonal block ttask[t0 + x / 7]; items from

@@ -432,9 +432,10 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
       int qe = q, max_nb = 0;
       for (; qe < n && level[byl[qe]] == lv; ++qe) max_nb = std::max(max_nb, (int)rows[byl[qe]].size());
       // a narrow level (at most kPanelCols columns, each with at most kPanelBlocks
-      // off-diagonal blocks) is factored as whole column panels: its off-diagonal rows ride
-      // along in the diagonal elimination, so it gets no off-diagonal solve tasks
-      const bool panel = qe - q <= kPanelCols && max_nb <= kPanelBlocks;
+      // off-diagonal blocks, or one column with at most kPanel4Blocks) is factored as whole
+      // column panels: its off-diagonal rows ride along in the diagonal elimination, so it
+      // gets no off-diagonal solve tasks
+      const bool panel = (qe - q <= kPanelCols && max_nb <= kPanelBlocks) || (qe - q == 1 && max_nb <= kPanel4Blocks);
       for (; q < qe; ++q) {
         const int k = byl[q];
         p.lsched.push_back(k);
@@ -640,15 +641,18 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
           if (far_exec[u] == r) cp.cutask.push_back(p.lutask[ubase + u]);
         const int tt = (int)cp.cttask.size() - t0;
         // this CTA factors its columns of the level as whole panels (no off-diagonal solve
-        // tasks) when it owns at most kPanelCols of them, each with at most kPanelBlocks
-        // off-diagonal blocks: one warp per column on separate SM sub-partitions
+        // tasks) when it owns at most kClusterPanelCols of them, each with at most
+        // kPanelBlocks off-diagonal blocks (one warp per column), or a single one with at
+        // most kPanel4Blocks (four warps)
         int n_own = 0, max_nb = 0;
         for (int q = lvl[4 * l]; q < lvl[4 * (l + 1)]; ++q)
           if (owner[sched[q]] == r) {
             ++n_own;
             max_nb = std::max(max_nb, colslot[sched[q] + 1] - colslot[sched[q]] - 1);
           }
-        if (n_own > kPanelCols || max_nb > kPanelBlocks)
+        const bool panel_cta = (n_own <= kClusterPanelCols && max_nb <= kPanelBlocks) ||
+                               (n_own == 1 && max_nb <= kPanel4Blocks);
+        if (!panel_cta)
           for (int x = lvl[4 * l + 3]; x < lvl[4 * (l + 1) + 3]; ++x) {
             const int2 t = p.lttask[tbase + x];
             if (shome[t.x] == r) cp.cttask.push_back(t);
