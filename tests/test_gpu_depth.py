@@ -42,8 +42,12 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("mode", ["mixed", "plain"])
-def test_depth_refine_matches_oracle(C, mode):
+@pytest.mark.parametrize("chunk", ["1024", "2048"])
+def test_depth_refine_matches_oracle(C, mode, chunk, monkeypatch):
+    """Work items of 1024 pixels have the residual kernel's valid-match lists, which the
+    match pass walks; items of 2048 pixels have none, and it reads the index rows."""
     import torch
+    monkeypatch.setenv("COMO3R_K1_CHUNK", chunk)
     dtype = np.float32 if mode == "mixed" else np.float64
     p, lab = case(dtype=dtype)
     m = C.MIXED if mode == "mixed" else C.PLAIN_FP64
