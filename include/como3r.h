@@ -114,7 +114,10 @@ typedef struct {
  * CTAs per graph, COMO3R_SOLVE_CLUSTER=<C> forcing C CTAs or 0 none; for one graph whose
  * factor fits neither one SM nor a cluster, a grid-wide solve over one CTA per SM (a
  * cooperative launch), COMO3R_SOLVE_GRID=1 forcing it for any one-graph plan, 0 disabling
- * it), allocate workspaces, check every match index on the
+ * it; for a batch too large for one cluster per graph, one launch of CTA groups when the
+ * planner's estimates favour it: the slowest graphs each solved by a cluster of 8 CTAs, the
+ * others packed onto single CTAs, factors in global memory, COMO3R_SOLVE_GROUPS=<k> forcing k
+ * cluster-solved graphs or 0 none), allocate workspaces, check every match index on the
  * device (-1 <= n < P_j) and autotune the residual kernel's work-item size and launch
  * configuration on this graph's data (a few milliseconds of timed trial launches; the
  * environment variables COMO3R_K1_CFG=<n>, COMO3R_K1_CHUNK=<pixels> and
@@ -263,9 +266,10 @@ int64_t como3r_last_launch_count(como3r_graph_t graph);
 #define COMO3R_STAT_SMEM_SOLVE 13    /* 1 if the factor of every graph fits in shared memory */
 #define COMO3R_STAT_ND_GRAPHS 14     /* graphs ordered by nested dissection (others: minimum degree) */
 #define COMO3R_STAT_K1_STALLS 15     /* bounded waits of the TMA-staged K1 that gave up (process-wide; 0 = healthy) */
-#define COMO3R_STAT_SOLVE_CTAS 16    /* CTAs per graph of the factorisation: 1, the cluster of the multi-SM solve, or the grid of the grid-wide solve of one large graph */
+#define COMO3R_STAT_SOLVE_CTAS 16    /* CTAs per graph of the factorisation: 1, the cluster of the multi-SM solve, the grid of the grid-wide solve of one large graph, or the cluster of a batch's CTA groups */
 #define COMO3R_STAT_SOLVE_FLOPS 17   /* FP64 operations of one factorisation + solve, all graphs (FMA = 2) */
-#define COMO3R_STAT_COUNT 18
+#define COMO3R_STAT_SOLVE_GROUPS 18  /* graphs of a batch solved by a whole cluster (CTA-group solve), 0 if none */
+#define COMO3R_STAT_COUNT 19
 int como3r_graph_stats(como3r_graph_t graph, int64_t* stats /* [COMO3R_STAT_COUNT] */);
 
 /* Plan a description on the host only (no device memory touched): fills the same stats

@@ -27,7 +27,8 @@ PLAIN_FP64, MIXED = 0, 1
 VJP_UNROLLED, VJP_ENVELOPE = 0, 1
 EDGE_RECORD = 64
 STAT_NAMES = ["graphs", "keyframes", "edges", "items", "columns", "blocks", "fill", "updates", "levels",
-              "valid", "chunk", "block", "grid", "smem_solve", "nd_graphs", "k1_stalls", "solve_ctas", "solve_flops"]
+              "valid", "chunk", "block", "grid", "smem_solve", "nd_graphs", "k1_stalls", "solve_ctas", "solve_flops",
+              "solve_groups"]
 
 STAGE_NAMES = ["edge_prep", "residual_reduce", "edge_reduce", "assemble", "factor_solve", "retract", "iteration"]
 

@@ -104,6 +104,12 @@ struct como3r_graph {
   int cluster_ctas = 0;
   // grid-wide solve of a single large graph (grid_ctas co-resident CTAs), when chosen
   int grid_ctas = 0;
+  // batches with large graphs: one launch of CTA groups (group_ctas CTAs, group_big graphs
+  // solved by a whole cluster), when chosen
+  int group_ctas = 0, group_big = 0;
+  int4* d_gtask = nullptr;
+  int32_t* d_glist = nullptr;
+  int* d_gfail = nullptr;
   GridSync* d_gsync = nullptr;
   unsigned grid_extra = 0;  // COMO3R_GRID_BARRIER_EXTRA: test of the barrier's wait limit
   double* d_diag_shift = nullptr;  // COMO3R_TEST_DIAG_SHIFT: per-graph diagonal shift (tests only)
@@ -216,6 +222,9 @@ int enqueue_linearize(como3r_graph* g, cudaStream_t s, double* cost_hist, const 
 // `keep` (the vjp's forward iterations): where a successful factorisation also leaves L.
 cudaError_t launch_solver(como3r_graph* g, const double* gvec, double* tau, GraphInfoDev* ginfo, int* warn,
                           cudaStream_t s, FactorKeep keep = {}) {
+  if (g->group_ctas > 0)
+    return launch_factor_solve_group(g->group_ctas, g->sp, g->d_gtask, g->d_glist, g->d_A, g->d_L, g->d_colscratch,
+                                     gvec, tau, g->lambda, g->eps0, g->max_attempts, ginfo, warn, g->d_gfail, s, keep);
   if (g->grid_ctas > 0)
     return launch_factor_solve_grid(g->grid_ctas, g->sp, g->d_A, g->d_L, g->d_colscratch, gvec, tau, g->lambda,
                                     g->eps0, g->max_attempts, ginfo, warn, g->d_gsync, s, keep, g->grid_extra);
@@ -274,6 +283,28 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   if (rc) return set_error(rc, p.error);
   CK(cudaGetDevice(&g->device), "cudaGetDevice");
   CK(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device), "attribute");
+  // a batch too large for one cluster per graph: CTA groups when they beat one CTA per graph
+  // (COMO3R_SOLVE_GROUPS=<k> puts the k slowest graphs on clusters, 0 disables them); a graph
+  // solved by a cluster may take the other ordering, and the plan is built again with it
+  GroupPlan gp;
+  {
+    int force = -1;
+    bool want = p.G > 1 && kGroupCTAs * p.G > g->sms;
+    if (const char* e = getenv("COMO3R_SOLVE_GROUPS")) {
+      force = std::max(0, atoi(e));
+      want = force > 0 && p.G > 1;
+    }
+    if (want) build_group_plan(p, g->sms, force, gp);
+    if (gp.ctas > 0) {
+      bool changed = false;
+      for (int k = 0; k < p.G; ++k) changed = changed || (gp.order[k] >= 0 && gp.order[k] != p.order_kind[k]);
+      if (changed) {
+        HostPlan p2;
+        if ((rc = build_plan(d, p2, &gp.order))) return set_error(rc, p2.error);
+        p = std::move(p2);
+      }
+    }
+  }
   CK(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking), "stream create");
   g->rp = make_robust_params(d->sigma_ray, d->sigma_dist, d->huber_k);
   g->lambda = d->lambda;
@@ -366,9 +397,17 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
   // shared-memory factor when every graph fits
   const size_t smax = factor_solve_max_smem();
   g->smem_solve = p.max_graph_smem <= smax;
+  if (gp.ctas > 0) {
+    if ((rc = upload(g, &g->d_gtask, gp.gtask)) || (rc = upload(g, &g->d_glist, gp.glist)) ||
+        (rc = dalloc(g, &g->d_gfail, (size_t)2 * p.G)))
+      return rc;
+    CK(cudaMemsetAsync(g->d_gfail, 0, sizeof(int) * 2 * (size_t)p.G, g->stream), "memset");
+    g->group_ctas = gp.ctas;
+    g->group_big = gp.big;
+  }
   // multi-SM solve for a few large graphs (it needs the graphs' clusters to fit on the GPU);
   // COMO3R_SOLVE_CLUSTER=<C> forces C CTAs per graph, 0 disables it
-  {
+  if (g->group_ctas == 0) {
     int C = 0, max_col = 0;
     for (int k = 0; k < p.G; ++k) max_col = std::max(max_col, p.col_begin[k + 1] - p.col_begin[k]);
     if (max_col >= 32 && 8 * p.G <= g->sms) C = 8;
@@ -973,7 +1012,10 @@ int como3r_graph_stats(como3r_graph_t g, int64_t* stats) {
   stats[COMO3R_STAT_BLOCK] = residual_reduce_block() * 100 + g->k1_cfg;
   stats[COMO3R_STAT_GRID] = g->k1_grid;
   stats[COMO3R_STAT_SMEM_SOLVE] = g->smem_solve ? 1 : 0;
-  stats[COMO3R_STAT_SOLVE_CTAS] = g->grid_ctas > 0 ? g->grid_ctas : (g->cluster_ctas > 0 ? g->cluster_ctas : 1);
+  stats[COMO3R_STAT_SOLVE_CTAS] = g->grid_ctas > 0 ? g->grid_ctas
+                                 : g->cluster_ctas > 0 ? g->cluster_ctas
+                                 : g->group_ctas > 0 ? kGroupCTAs : 1;
+  stats[COMO3R_STAT_SOLVE_GROUPS] = g->group_big;
   stats[COMO3R_STAT_K1_STALLS] = residual_reduce_stalls();
   return COMO3R_OK;
 }

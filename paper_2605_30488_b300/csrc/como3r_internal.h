@@ -291,6 +291,17 @@ cudaError_t launch_factor_solve_grid(int ctas, const SolverPlan& plan, const dou
                                      const double* gvec, double* tau, double lambda, double eps0, int max_attempts,
                                      GraphInfoDev* ginfo, int* warn, GridSync* sync, cudaStream_t s,
                                      FactorKeep keep = {}, unsigned extra_arrivals = 0);
+// Batches with large graphs: one launch of clusters of kGroupCTAs CTAs (factor in global
+// memory, L/colscratch as for the one-CTA kernel).  gtask[b] = (offset in glist, count,
+// rank, group size) for CTA b: a cluster whose CTAs all name one graph with group size
+// kGroupCTAs solves it together (cluster barriers); a CTA with group size 1 solves its
+// graphs in turn.  Every CTA of the launch has an entry (count 0: idle).  gfail: 2 ints per
+// graph.  ctas is a multiple of kGroupCTAs.
+constexpr int kGroupCTAs = 8;
+cudaError_t launch_factor_solve_group(int ctas, const SolverPlan& plan, const int4* gtask, const int32_t* glist,
+                                      const double* A, double* L, double* colscratch, const double* gvec, double* tau,
+                                      double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
+                                      int* gfail, cudaStream_t s, FactorKeep keep = {});
 cudaError_t launch_retract(const double* tau, double* poses, const uint8_t* frozen, int N, int* iter_counter,
                            cudaStream_t s);
 // ---- adjoint of the refined cost (k_adjoint.cu)

@@ -647,30 +647,34 @@ __device__ bool grid_barrier(GridSync* gs, int* s_ok, unsigned extra) {
   return *s_ok != 0;
 }
 
-__global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
-    SolverPlan P, const double* __restrict__ A, double* Lg, double* Sg, const double* __restrict__ gvec,
-    double* __restrict__ tau, double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
-    FactorKeep keep, GridSync* gs, unsigned extra) {
-  __shared__ double s_xbuf[kPanelXchg];
-  __shared__ int s_ok;
+// The global-memory solve of graph g by a group of `gsize` CTAs (this one is `grank`): the
+// task lists of factor_solve_kernel spread over every warp of the group, with bar.sync()
+// wherever that kernel has a CTA barrier, so the factor is bitwise the same.  `fail` is the
+// graph's pair of level failure flags in global memory.  bar.sync() returns false when a
+// bounded wait gave up (the grid barrier only): the graph then gets the zero update.
+template <class Bar>
+__device__ void solve_graph_global(const SolverPlan& P, int g, const double* __restrict__ A, double* Lg, double* Sg,
+                                   const double* __restrict__ gvec, double* __restrict__ tau, double lambda,
+                                   double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn, FactorKeep keep,
+                                   int* fail2, int grank, int gsize, Bar& bar, double* s_xbuf) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int gw = blockIdx.x * kSolveWarps + warp, GW = gridDim.x * kSolveWarps;
-  const int gt = blockIdx.x * kSolveThreads + tid, GT = gridDim.x * kSolveThreads;
-  const int* m = P.meta;  // graph 0
+  const int gw = grank * kSolveWarps + warp, GW = gsize * kSolveWarps;
+  const int gt = grank * kSolveThreads + tid, GT = gsize * kSolveThreads;
+  const int* m = P.meta + kMetaCount * g;
   const int cbase = m[kMetaColBase], ncol = m[kMetaNCol], sbase = m[kMetaSlotBase], nslot = m[kMetaNSlot];
   const int nlev = m[kMetaNLvl];
-  if (ncol == 0) {  // the same in every CTA
+  if (ncol == 0) {  // the same in every CTA of the group
     if (gt == 0) {
-      ginfo[0].attempts = 1;
-      ginfo[0].solved = 1;
-      ginfo[0].done_ns = globaltimer_ns();
+      ginfo[g].attempts = 1;
+      ginfo[g].solved = 1;
+      ginfo[g].done_ns = globaltimer_ns();
     }
     return;
   }
   SolveCtx C;
   C.L = Lg + (int64_t)sbase * 49;
   C.S = Sg + (int64_t)cbase * kColScratch;
-  C.col_slot = P.col_slot + cbase;
+  C.col_slot = P.col_slot + cbase + g;
   C.slot_row = P.slot_row + sbase;
   C.sched = P.sched + cbase;
   C.tri = P.tri + m[kMetaTriBase];
@@ -683,7 +687,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
   C.nranks = 1;
   const double* Ag = A + (int64_t)sbase * 49;
   const int* col_kf = P.col_kf + cbase;
-  volatile int* vfail = gs->fail;
+  volatile int* vfail = fail2;
 
   int attempt = 0;
   bool ok = false, alive = true;
@@ -692,14 +696,14 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
     const double eps = eps0 * pow100;
     for (int64_t x = gt; x < (int64_t)nslot * 49; x += GT) C.L[x] = Ag[x];
     if (gt == 0) vfail[0] = 0;
-    if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
+    if (!(alive = bar.sync())) break;
     for (int x = gt; x < 7 * ncol; x += GT) {
       const int col = x / 7, k = x % 7;
       const int ds = C.col_slot[col];
       blk<false>(C, ds)[8 * k] += lambda * Ag[(int64_t)ds * 49 + 8 * k] + eps;
       y_of<false>(C, col)[k] = -gvec[7 * col_kf[col] + k];
     }
-    if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
+    if (!(alive = bar.sync())) break;
     bool failed = false;
     for (int lv = 0; lv < nlev; ++lv) {
       const int* L0 = C.lvl + 4 * lv;
@@ -707,9 +711,9 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
       const bool panel = nt == 0;
       const int nd = panel ? ncl : (ncl + 3) / 4;
       const int f0 = lv > 0 ? C.lvl[4 * (lv - 1) + 2] : 0, nf = lv > 0 ? L0[1] - f0 : 0;
-      int* fail = gs->fail + (lv & 1);
+      int* fail = fail2 + (lv & 1);
       if (panel && ncl == 1) {
-        if (blockIdx.x == 0 && warp < 4) {
+        if (grank == 0 && warp < 4) {
           panel_factor4<false>(C, C.sched[L0[0]], warp, lane, s_xbuf, fail);
         } else {
           for (int i = gw - 4; i < 2 * nf; i += GW - 4) update_half<false>(C, C.utask[f0 + i / 2], i & 1, lane);
@@ -724,28 +728,28 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
       // the next level's flag: its last readers passed the previous barrier, its writers
       // start after this one
       if (gt == 0) vfail[(lv + 1) & 1] = 0;
-      if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
+      if (!(alive = bar.sync())) break;
       if (vfail[lv & 1]) {
         // every CTA has read the flag before any can reset it for the next attempt
         failed = true;
-        alive = grid_barrier(gs, &s_ok, extra);
+        alive = bar.sync();
         break;
       }
       if (!panel) {
         for (int x = gt; x < 7 * nt; x += GT) trsm_or_inverse<false>(C, L0[3], nt, 7 * nt, L0[0], x);
-        if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
+        if (!(alive = bar.sync())) break;
       }
       for (int x = gw; x < 2 * (L0[2] - L0[1]); x += GW) update_half<false>(C, C.utask[L0[1] + x / 2], x & 1, lane);
       // L_cc^{-1} of the level's columns (read only by the back substitution): the last
-      // threads of the grid, which the update tasks leave idle first
+      // threads of the group, which the update tasks leave idle first
       for (int x = GT - 1 - gt; x < 7 * ncl; x += GT) trsm_or_inverse<false>(C, 0, 0, 0, L0[0], x);
-      if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
+      if (!(alive = bar.sync())) break;
     }
     if (!alive) break;
     if (!failed) {
       const int* L0 = C.lvl + 4 * (nlev - 1);  // far updates of the last level (none in an elimination tree)
       for (int x = gw; x < 2 * (L0[5] - L0[2]); x += GW) update_half<false>(C, C.utask[L0[2] + x / 2], x & 1, lane);
-      if (!(alive = grid_barrier(gs, &s_ok, extra))) break;
+      if (!(alive = bar.sync())) break;
       ok = true;
       break;
     }
@@ -754,7 +758,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
     for (int lv = nlev - 1; lv >= 0 && alive; --lv) {
       const int* L0 = C.lvl + 4 * lv;
       for (int q = L0[0] + gw; q < L0[4]; q += GW) backward_column<false>(C, C.sched[q], lane);
-      alive = grid_barrier(gs, &s_ok, extra);
+      alive = bar.sync();
     }
   }
   bool solved = ok && alive;
@@ -765,16 +769,73 @@ __global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
   }
   // every CTA's tau is written before the stamp; a CTA whose last wait ran out zeroes its
   // part again (the others then run out too, or had already given up and written zeros)
-  if (alive) alive = grid_barrier(gs, &s_ok, extra);
+  if (alive) alive = bar.sync();
   if (solved && !alive) {
     solved = false;
     for (int x = gt; x < 7 * ncol; x += GT) tau[7 * col_kf[x / 7] + x % 7] = 0.0;
   }
   if (gt == 0) {
-    ginfo[0].attempts = solved ? attempt + 1 : max_attempts;
-    ginfo[0].solved = solved ? 1 : 0;
-    ginfo[0].done_ns = globaltimer_ns();
+    ginfo[g].attempts = solved ? attempt + 1 : max_attempts;
+    ginfo[g].solved = solved ? 1 : 0;
+    ginfo[g].done_ns = globaltimer_ns();
     if (!solved) atomicOr(warn, 1);
+  }
+}
+
+struct GridBar {  // the bounded grid barrier of a cooperative launch
+  GridSync* gs;
+  int* s_ok;
+  unsigned extra;
+  __device__ bool sync() { return grid_barrier(gs, s_ok, extra); }
+};
+struct ClusterBar {  // the thread-block cluster's hardware barrier
+  __device__ bool sync() {
+    cooperative_groups::this_cluster().sync();
+    return true;
+  }
+};
+struct CtaBar {
+  __device__ bool sync() {
+    __syncthreads();
+    return true;
+  }
+};
+
+__global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_grid_kernel(
+    SolverPlan P, const double* __restrict__ A, double* Lg, double* Sg, const double* __restrict__ gvec,
+    double* __restrict__ tau, double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
+    FactorKeep keep, GridSync* gs, unsigned extra) {
+  __shared__ double s_xbuf[kPanelXchg];
+  __shared__ int s_ok;
+  GridBar bar{gs, &s_ok, extra};
+  solve_graph_global(P, 0, A, Lg, Sg, gvec, tau, lambda, eps0, max_attempts, ginfo, warn, keep, gs->fail,
+                     (int)blockIdx.x, (int)gridDim.x, bar, s_xbuf);
+}
+
+// ---- batches with large graphs: cluster groups (factor in global memory) ------------------
+// One launch of clusters of kGroupCTAs CTAs.  CTA b runs the graphs gtask[b] = (list offset,
+// count, rank in group, group size) of the list glist: a cluster whose CTAs all list the
+// same large graph solves it together (group size kGroupCTAs, cluster barriers); any other
+// CTA solves its own graphs one after the other (group size 1, CTA barriers).  Per graph
+// two failure flags in gfail.
+__global__ void __launch_bounds__(kSolveThreads, 1) factor_solve_group_kernel(
+    SolverPlan P, const int4* __restrict__ gtask, const int32_t* __restrict__ glist, const double* __restrict__ A,
+    double* Lg, double* Sg, const double* __restrict__ gvec, double* __restrict__ tau, double lambda, double eps0,
+    int max_attempts, GraphInfoDev* ginfo, int* warn, FactorKeep keep, int* gfail) {
+  __shared__ double s_xbuf[kPanelXchg];
+  const int4 t = gtask[blockIdx.x];
+  for (int k = 0; k < t.y; ++k) {
+    const int g = glist[t.x + k];
+    if (t.w > 1) {
+      ClusterBar bar;
+      solve_graph_global(P, g, A, Lg, Sg, gvec, tau, lambda, eps0, max_attempts, ginfo, warn, keep, gfail + 2 * g,
+                         t.z, t.w, bar, s_xbuf);
+    } else {
+      CtaBar bar;
+      solve_graph_global(P, g, A, Lg, Sg, gvec, tau, lambda, eps0, max_attempts, ginfo, warn, keep, gfail + 2 * g,
+                         0, 1, bar, s_xbuf);
+      __syncthreads();  // the next graph reuses the hand-over buffer
+    }
   }
 }
 
@@ -1271,6 +1332,27 @@ cudaError_t launch_diag_shift(int G, const SolverPlan& plan, double* A, const do
   if (G <= 0) return cudaSuccess;
   diag_shift_kernel<<<G, 256, 0, s>>>(plan, A, shift);
   return cudaGetLastError();
+}
+
+cudaError_t launch_factor_solve_group(int ctas, const SolverPlan& plan, const int4* gtask, const int32_t* glist,
+                                      const double* A, double* L, double* colscratch, const double* gvec, double* tau,
+                                      double lambda, double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn,
+                                      int* gfail, cudaStream_t s, FactorKeep keep) {
+  if (ctas <= 0 || ctas % kGroupCTAs) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3(kSolveThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)kGroupCTAs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, factor_solve_group_kernel, plan, gtask, glist, A, L, colscratch, gvec, tau, lambda,
+                            eps0, max_attempts, ginfo, warn, keep, gfail);
 }
 
 cudaError_t factor_substitute_prepare(size_t smem_bytes) {

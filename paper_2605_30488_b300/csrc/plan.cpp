@@ -197,7 +197,7 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 }  // namespace
 
-int build_plan(const como3r_graph_desc* d, HostPlan& p) {
+int build_plan(const como3r_graph_desc* d, HostPlan& p, const std::vector<int8_t>* force_order) {
   auto fail = [&](const std::string& msg) {
     p.error = msg;
     return COMO3R_ERR_INVALID_ARG;
@@ -336,7 +336,12 @@ int build_plan(const como3r_graph_desc* d, HostPlan& p) {
     Symbolic S_nd = symbolic(adj, nd.order);
     const std::vector<int> md_order = min_degree_order(adj);
     Symbolic S_md = symbolic(adj, md_order);
-    const bool use_md = order_cost(S_md) <= order_cost(S_nd);
+    const int forced = force_order && g < (int)force_order->size() ? (*force_order)[g] : -1;
+    const bool use_md = forced >= 0 ? forced == 0 : order_cost(S_md) <= order_cost(S_nd);
+    p.nlev_md.push_back(S_md.nlev);
+    p.nlev_nd.push_back(S_nd.nlev);
+    p.upd_md.push_back(S_md.updates);
+    p.upd_nd.push_back(S_nd.updates);
     const std::vector<int>& order = use_md ? md_order : nd.order;
     Symbolic& S = use_md ? S_md : S_nd;
     p.order_kind.push_back(use_md ? 0 : 1);
@@ -534,6 +539,7 @@ void plan_stats(const HostPlan& p, int64_t* s) {
     if (t.w >= 0) rhs_tri += t.z - t.y;
   s[COMO3R_STAT_SOLVE_FLOPS] = cols * (140 + 49 + 114 + 56) + offdiag * (343 + 98) +
                                (int64_t)p.ltri.size() * 686 + rhs_tri * 98;
+  s[COMO3R_STAT_SOLVE_GROUPS] = 0;  // the device's choice (como3r_graph_stats)
 }
 
 
@@ -670,6 +676,82 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
                                                     (int)cp.cttask.size() - t0, nlev, nslot, ncol));
     }
   }
+}
+
+}  // namespace como3r
+
+namespace como3r {
+
+// Estimated solve times (microseconds), measured orders of magnitude on this GPU: one CTA
+// with the factor in global memory pays ~9.4 us per elimination level (a 7x7 factorisation
+// chain with L2 round trips) and ~0.14 us per block update (14 FP64 warp instructions on
+// one SM's four sub-partitions); a cluster of kGroupCTAs pays ~10 us per level (cluster
+// barriers) and spreads the updates over its SMs.
+void build_group_plan(const HostPlan& p, int sms, int force_big, GroupPlan& gp) {
+  gp = GroupPlan();
+  const int G = p.G;
+  if (G < 2 || sms < kGroupCTAs) return;
+  auto one = [&](int g) {
+    const bool md = 3.0 * p.nlev_md[g] + 0.15 * (double)p.upd_md[g] <= 3.0 * p.nlev_nd[g] + 0.15 * (double)p.upd_nd[g];
+    return md ? 9.4 * p.nlev_md[g] + 0.14 * (double)p.upd_md[g] : 9.4 * p.nlev_nd[g] + 0.14 * (double)p.upd_nd[g];
+  };
+  auto group = [&](int g, int* order) {
+    const double md = 10.0 * p.nlev_md[g] + 0.14 / kGroupCTAs * (double)p.upd_md[g];
+    const double nd = 10.0 * p.nlev_nd[g] + 0.14 / kGroupCTAs * (double)p.upd_nd[g];
+    if (order) *order = md <= nd ? 0 : 1;
+    return md <= nd ? md : nd;
+  };
+  std::vector<int> idx(G);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::vector<double> e1(G);
+  for (int g = 0; g < G; ++g) e1[g] = one(g);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return e1[a] > e1[b]; });
+  gp.single_us = e1[idx[0]];
+  // the remaining graphs, largest first, each onto the least-loaded of m CTAs
+  auto pack = [&](int k, int m, std::vector<std::vector<int>>* bins) {
+    std::vector<double> load(m, 0.0);
+    if (bins) bins->assign(m, {});
+    for (int q = k; q < G; ++q) {
+      const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      load[b] += e1[idx[q]];
+      if (bins) (*bins)[b].push_back(idx[q]);
+    }
+    return m ? *std::max_element(load.begin(), load.end()) : 0.0;
+  };
+  int best_k = -1, best_m = 0;
+  double best = 0.8 * gp.single_us;  // a group solve must gain at least a fifth
+  const int kmax = std::min(G, sms / kGroupCTAs);
+  for (int k = 1; k <= kmax; ++k) {
+    if (force_big >= 0 && k != force_big) continue;
+    const int m = ((sms - kGroupCTAs * k) / kGroupCTAs) * kGroupCTAs;
+    if (k < G && m == 0) continue;
+    double mk = pack(k, m, nullptr);
+    for (int q = 0; q < k; ++q) mk = std::max(mk, group(idx[q], nullptr));
+    if (force_big >= 0 || mk < best) {
+      best = mk;
+      best_k = k;
+      best_m = m;
+    }
+  }
+  if (best_k < 1) return;
+  gp.big = best_k;
+  gp.makespan_us = best;
+  gp.order.assign(G, -1);
+  for (int q = 0; q < best_k; ++q) {
+    int o = 0;
+    group(idx[q], &o);
+    gp.order[idx[q]] = (int8_t)o;
+    const int off = (int)gp.glist.size();
+    gp.glist.push_back(idx[q]);
+    for (int r = 0; r < kGroupCTAs; ++r) gp.gtask.push_back(make_int4(off, 1, r, kGroupCTAs));
+  }
+  std::vector<std::vector<int>> bins;
+  pack(best_k, best_m, &bins);
+  for (const auto& b : bins) {
+    gp.gtask.push_back(make_int4((int)gp.glist.size(), (int)b.size(), 0, 1));
+    for (int g : b) gp.glist.push_back(g);
+  }
+  gp.ctas = (int)gp.gtask.size();
 }
 
 }  // namespace como3r

@@ -33,6 +33,10 @@ struct HostPlan {
   std::vector<int32_t> lrow_off;
   std::vector<int2> lrow_ent;
   std::vector<int8_t> order_kind;  // per graph: 0 minimum degree, 1 nested dissection
+  // per graph, both candidate orderings: elimination-tree levels and block updates
+  // (minimum degree, nested dissection), for the CTA-group assignment of batched solves
+  std::vector<int32_t> nlev_md, nlev_nd;
+  std::vector<int64_t> upd_md, upd_nd;
   std::vector<int32_t> slot_kf_r, slot_kf_c;
   // assembly (entries edge * 2 + negate, in edge order)
   std::vector<int32_t> slot_contrib_off, slot_contrib, kf_contrib_off, kf_contrib;
@@ -55,7 +59,22 @@ struct HostClusterPlan {
 void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp);
 
 // Validates `d` and fills `p`; returns COMO3R_OK or COMO3R_ERR_INVALID_ARG (message in p.error).
-int build_plan(const como3r_graph_desc* d, HostPlan& p);
+// order (optional, per graph): 0 minimum degree, 1 nested dissection, -1 the cheaper one for
+// one SM (the default).
+int build_plan(const como3r_graph_desc* d, HostPlan& p, const std::vector<int8_t>* order = nullptr);
+
+// CTA groups of a batched solve (factor_solve_group_kernel): per graph the estimated time
+// (microseconds) of one CTA with its one-SM ordering, and of a cluster of kGroupCTAs with the
+// better ordering for it; the assignment minimising the estimated makespan on `sms` SMs.
+struct GroupPlan {
+  int ctas = 0;                    // multiple of kGroupCTAs; 0: no group solve
+  int big = 0;                     // graphs solved by a whole cluster
+  double makespan_us = 0.0, single_us = 0.0;  // estimates: grouped, and one CTA per graph
+  std::vector<int4> gtask;         // per CTA (list offset, count, rank, group size)
+  std::vector<int32_t> glist;
+  std::vector<int8_t> order;       // per graph, for build_plan
+};
+void build_group_plan(const HostPlan& p, int sms, int force_big, GroupPlan& gp);
 
 // Splits every edge's streamed pixels into items of at most `chunk` pixels.
 void build_items(const HostPlan& p, int chunk, std::vector<Item>& items, std::vector<int32_t>& item_off);

@@ -116,7 +116,10 @@ def torch_poses(p):
 
 VARIANTS = {"cta": dict(COMO3R_SOLVE_CLUSTER="0", COMO3R_SOLVE_GRID="0"),
             "cluster": dict(COMO3R_SOLVE_CLUSTER="4", COMO3R_SOLVE_GRID="0"),
-            "grid": dict(COMO3R_SOLVE_CLUSTER="0", COMO3R_SOLVE_GRID="1")}
+            "grid": dict(COMO3R_SOLVE_CLUSTER="0", COMO3R_SOLVE_GRID="1"),
+            # batches: one graph by a cluster of the CTA-group launch, or every graph
+            "group1": dict(COMO3R_SOLVE_GROUPS="1"),
+            "group3": dict(COMO3R_SOLVE_GROUPS="3")}
 
 
 def set_variant(monkeypatch, variant, shifts):
@@ -126,7 +129,11 @@ def set_variant(monkeypatch, variant, shifts):
 
 
 def check_variant(C, g, variant):
-    ctas = g.stats()["solve_ctas"]
+    st = g.stats()
+    ctas = st["solve_ctas"]
+    if variant.startswith("group"):
+        assert ctas == 8 and st["solve_groups"] == int(variant[5:]), (variant, st)
+        return
     assert (ctas == 1) if variant == "cta" else (ctas == 4 if variant == "cluster" else ctas > 4), (variant, ctas)
 
 
@@ -183,7 +190,7 @@ def test_retry_succeeds_mixed(C, tiny, monkeypatch):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("variant", ["cta", "cluster"])
+@pytest.mark.parametrize("variant", ["cta", "cluster", "group1", "group3"])
 def test_retry_in_one_graph_of_a_batch(C, batch3, variant, monkeypatch):
     """Three graphs in one launch, only graph 1 shifted: graphs 0 and 2 solve at the first
     attempt, graph 1 at its fourth; every graph's step equals the oracle's."""

@@ -223,6 +223,28 @@ def test_batched_graphs_match_individual(C):
     np.testing.assert_allclose(trace, to, rtol=FP64_TOL)
 
 
+@pytest.mark.parametrize("groups", ["1", "2", "3"])
+def test_group_solve_matches_oracle(C, groups, monkeypatch):
+    """A batch solved by one launch of CTA groups (COMO3R_SOLVE_GROUPS=k: the k slowest
+    graphs each by a cluster of 8 CTAs with cluster barriers, the others each by one CTA,
+    factors in global memory; a cluster-solved graph may take the other ordering): the
+    oracle's FP64 poses and cost trace after six iterations."""
+    specs = [dict(agents=2, n_kf=5, H=48, W=64, f=50.0), dict(agents=1, n_kf=7, H=60, W=80, f=60.0),
+             dict(agents=3, n_kf=4, H=48, W=64, f=50.0, n_inter=3)]
+    batch = make_problem(21, noise=0.005, outlier=0.1, exact=True, graph_specs=specs, name="batch",
+                         dtype=np.float32)
+    monkeypatch.setenv("COMO3R_SOLVE_GROUPS", groups)
+    poses = torch_poses(batch.poses_init)
+    with C.Graph(batch, mode=C.PLAIN_FP64) as g:
+        st = g.stats()
+        assert st["solve_groups"] == int(groups) and st["solve_ctas"] == 8, st
+        st, trace, info = g.solve(poses, 6)
+    assert all(x["solved"] for x in info)
+    po, to = O.gn_solve(batch, batch.poses_init, 6)
+    assert max(pose_err(poses.cpu().numpy(), po).values()) <= FP64_TOL
+    np.testing.assert_allclose(trace, to, rtol=FP64_TOL)
+
+
 @pytest.mark.parametrize("cfg", [0, 1, 2, 3, 4, 5, 6])
 def test_every_residual_kernel_configuration(C, mid, tiny, cfg, monkeypatch):
     """Each launch configuration the autotuner may choose gives the oracle's edge blocks
