@@ -255,9 +255,12 @@ def test_vjp_with_each_kept_factor(C, mid, monkeypatch, setting):
     assert abs(float(gl @ vl + gc @ vc) - ref) <= TOL[0] * mag
 
 
-def test_vjp_batch_of_graphs_matches_complex_step(C):
+@pytest.mark.parametrize("groups", ["0", "2"])
+def test_vjp_batch_of_graphs_matches_complex_step(C, groups, monkeypatch):
     """Three graphs of different sizes in one handle: every graph's adjoint systems are
-    solved with its own kept factor (one CTA per graph)."""
+    solved with its own kept factor (kept by one CTA per graph, or by the CTA-group solve
+    with two graphs on clusters)."""
+    monkeypatch.setenv("COMO3R_SOLVE_GROUPS", groups)
     specs = [dict(n_kf=3), dict(n_kf=4), dict(n_kf=2)]
     prob = make_problem(11, H=24, W=32, f=25.0, n_inter=1, iters=3, graph_specs=specs)
     gl, gc, _, _, _ = gpu_grads(C, prob, 0, 3, C.VJP_UNROLLED)
