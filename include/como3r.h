@@ -196,9 +196,10 @@ int como3r_linearize(como3r_graph_t graph, const double* poses, double* edge_out
  * the step, the solve outcome and the damped factor (7N + 8N doubles and 49 per factor
  * block + 63 per unknown keyframe); each backward step solves its adjoint system with the
  * kept factor of its iteration (the system is not linearised or factorised again).  The
- * kept-factor solve holds its working vector and plan in shared memory when the largest
- * graph's fit (about 100 bytes per keyframe and 12 per factor block), else in global
- * memory (COMO3R_SUBSTITUTE_SMEM=0 at create forces the latter, a test setting).  Pixel gradients are accumulated with atomics (FP32
+ * kept-factor solve holds its working vector, plan and the kept factor in shared memory when
+ * the largest graph's fit (about 500 bytes per keyframe and 400 per factor block), else the
+ * vector and plan alone (about 100 and 12), else global memory (COMO3R_SUBSTITUTE_SMEM=1 / 0
+ * at create force the second / the third, test settings).  Pixel gradients are accumulated with atomics (FP32
  * in the MIXED form, so bitwise results can vary between runs; FP64 then rounded once in
  * the PLAIN form).  A match with c_i c_j = 0 contributes no confidence gradient.
  * Synchronises the stream.

@@ -127,6 +127,7 @@ struct como3r_graph {
   // the factor of every forward iteration (blocks, column scratch), solved again backwards
   double *d_keep_L = nullptr, *d_keep_S = nullptr, *d_sub_z = nullptr;
   size_t sub_smem = 0;  // shared memory of the kept-factor substitution (0: d_sub_z)
+  bool sub_fsmem = false;  // ... the kept factor staged into it as well
 };
 
 namespace {
@@ -450,17 +451,26 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
     g->solve_smem = p.max_graph_smem;
     CK(factor_solve_prepare(g->solve_smem), "solver smem attribute");
   }
-  {  // the kept-factor substitution of the vjp: its vector and plan in shared memory if they fit
-    size_t z = 16;
+  {  // the kept-factor substitution of the vjp: its vector, plan and (if they fit) the kept
+     // factor in shared memory
+    size_t z = 16, zf = 16;
     for (int k = 0; k < G; ++k) {
       const int32_t* m = p.meta.data() + kMetaCount * k;
-      z = std::max(z, substitute_smem_bytes(m[kMetaNSlot], m[kMetaNCol], m[kMetaNLvl]));
+      const size_t b = substitute_smem_bytes(m[kMetaNSlot], m[kMetaNCol], m[kMetaNLvl]);
+      z = std::max(z, b);
+      zf = std::max(zf, b + substitute_factor_bytes(m[kMetaNSlot], m[kMetaNCol]));
     }
-    const char* e = getenv("COMO3R_SUBSTITUTE_SMEM");  // test setting: 0 forces global memory
-    if (z <= factor_solve_max_smem() && !(e && atoi(e) == 0)) {
+    // test setting: 0 forces global memory, 1 keeps the factor out of shared memory
+    const char* e = getenv("COMO3R_SUBSTITUTE_SMEM");
+    const int want = e ? atoi(e) : 2;
+    const size_t smax = factor_solve_max_smem();
+    if (want >= 2 && zf <= smax) {
+      g->sub_smem = zf;
+      g->sub_fsmem = true;
+    } else if (want >= 1 && z <= smax) {
       g->sub_smem = z;
-      CK(factor_substitute_prepare(g->sub_smem), "substitute smem attribute");
     }
+    if (g->sub_smem) CK(factor_substitute_prepare(g->sub_smem, g->sub_fsmem), "substitute smem attribute");
   }
   // match index check and valid counts
   CK(cudaMemsetAsync(g->d_bad, 0, sizeof(unsigned long long), g->stream), "memset");
@@ -830,7 +840,7 @@ int vjp_impl(como3r_graph_t g, const double* poses_init, int32_t iters, int32_t 
       CK(launch_edge_prep(g->d_poses, g->d_es, p.E, g->d_T64, g->d_T32, g->d_Ad, s), "edge_prep");
       CK(cudaMemsetAsync(g->d_adj_u, 0, sizeof(double) * 7 * N, s), "memset");
       CK(launch_factor_substitute(G, g->sp, keep_of(k), g->d_ginfo_hist + (size_t)k * G, g->d_adj_rhs, g->d_adj_u,
-                                  g->sub_smem, g->d_sub_z, s),
+                                  g->sub_smem, g->d_sub_z, s, g->sub_fsmem),
          "adjoint solve");
       CK(launch_adjoint_edge_prep(p.mode, g->d_es, E, g->d_Ad, g->d_adj_u, tau_k, g->d_evec, s), "adjoint edge prep");
       CK(mark(4 + 2 * k), "event");

@@ -179,6 +179,12 @@ inline size_t substitute_smem_bytes(int nslot, int ncol, int nlev) {
          r16(4 * (size_t)nslot) + r16(4 * (size_t)ncol) + r16(16 * (size_t)(nlev + 1));
 }
 
+// ... and of its kept blocks and L_cc^{-1} when those are staged as well.
+inline size_t substitute_factor_bytes(int nslot, int ncol) {
+  auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+  return r16(8 * 49 * (size_t)nslot) + r16(8 * 49 * (size_t)ncol);
+}
+
 // Bytes of shared memory of one CTA of the multi-SM solve: its blocks and column scratch,
 // the graph's triplets, its task lists and the graph's home / column-slot / row maps.
 inline size_t cluster_smem_bytes(int nslot_loc, int ncol_loc, int ncol_max, int ntri, int nu, int nt, int nlev,
@@ -265,9 +271,12 @@ size_t factor_solve_max_smem();
 // One CTA per graph; the working vector and the plan arrays live in shared memory
 // (smem = the largest graph's substitute_smem_bytes, set up by factor_substitute_prepare)
 // or, with smem == 0, in global memory (zwork: [total columns][7] doubles).
-cudaError_t factor_substitute_prepare(size_t smem_bytes);
+// factor_in_smem: the kept blocks and L_cc^{-1} are staged into shared memory too (smem then
+// includes substitute_factor_bytes of the largest graph).
+cudaError_t factor_substitute_prepare(size_t smem_bytes, bool factor_in_smem);
 cudaError_t launch_factor_substitute(int G, const SolverPlan& plan, FactorKeep keep, const GraphInfoDev* rec,
-                                     const double* rhs, double* out, size_t smem_bytes, double* zwork, cudaStream_t s);
+                                     const double* rhs, double* out, size_t smem_bytes, double* zwork, cudaStream_t s,
+                                     bool factor_in_smem);
 // Test setting only (COMO3R_TEST_DIAG_SHIFT): A_gg -= shift[g] I on every graph's
 // assembled diagonal, launched after the assembly when the setting is given at create.
 cudaError_t launch_diag_shift(int G, const SolverPlan& plan, double* A, const double* shift, cudaStream_t s);

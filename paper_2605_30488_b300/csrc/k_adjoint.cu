@@ -341,25 +341,55 @@ __global__ void adjoint_edge_prep_kernel(const EdgeStatic* __restrict__ es, int 
   }
 }
 
-// Per edge (one warp): fixed-order FP64 sum of the item records (lane q sums slot q), then
-// the keyframe terms out[e][0..6] = dF/dd_i, out[e][7..13] = dF/dd_j.
-__global__ void adjoint_edge_kernel(const double* __restrict__ rec, const int32_t* __restrict__ item_off, int E,
-                                    const EdgeStatic* __restrict__ es, const double* __restrict__ Ad,
-                                    const double* __restrict__ u, const double* __restrict__ tau,
-                                    double* __restrict__ out) {
-  __shared__ double F[kAdjRec], y[kAdjRec], d[14];
-  const int e = blockIdx.x, lane = threadIdx.x;
+// Component k of ad_transpose_apply(xi, y).
+__device__ __forceinline__ double ad_transpose_component(const double* xi, const double* y, int k) {
+  const double v0 = xi[0], v1 = xi[1], v2 = xi[2], w0 = xi[3], w1 = xi[4], w2 = xi[5], z = xi[6];
+  const double y0 = y[0], y1 = y[1], y2 = y[2], q0 = y[3], q1 = y[4], q2 = y[5];
+  switch (k) {
+    case 0: return (y1 * w2 - y2 * w1) + z * y0;
+    case 1: return (y2 * w0 - y0 * w2) + z * y1;
+    case 2: return (y0 * w1 - y1 * w0) + z * y2;
+    case 3: return (y1 * v2 - y2 * v1) + (q1 * w2 - q2 * w1);
+    case 4: return (y2 * v0 - y0 * v2) + (q2 * w0 - q0 * w2);
+    case 5: return (y0 * v1 - y1 * v0) + (q0 * w1 - q1 * w0);
+    default: return -(v0 * y0 + v1 * y1 + v2 * y2);
+  }
+}
+
+// Per edge (kAdjEdgeThreads threads): FP64 sum of the item records in a fixed order (warp w
+// sums items w, w + 4, ... of slot `lane`, four loads ahead; the four partial sums are then
+// added pairwise), then the keyframe terms out[e][0..6] = dF/dd_i, out[e][7..13] = dF/dd_j,
+// one component per lane (an FP64 instruction holds its SM sub-partition ~80 cycles
+// however few lanes it uses, so a component per lane is a short chain).
+constexpr int kAdjEdgeThreads = 128;
+__global__ void __launch_bounds__(kAdjEdgeThreads) adjoint_edge_kernel(
+    const double* __restrict__ rec, const int32_t* __restrict__ item_off, int E, const EdgeStatic* __restrict__ es,
+    const double* __restrict__ Ad, const double* __restrict__ u, const double* __restrict__ tau,
+    double* __restrict__ out) {
+  constexpr int W = kAdjEdgeThreads / 32;
+  __shared__ double part[W][kAdjRec], F[kAdjRec], y[kAdjRec], d[14], pq[14];
+  const int e = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (e >= E) return;
   const int i = es[e].i, j = es[e].j;
   if (lane < kAdjRec) {
+    const int i0 = item_off[e] + warp, i1 = item_off[e + 1];
     double f = 0.0;
-    for (int it = item_off[e]; it < item_off[e + 1]; ++it) f += rec[(int64_t)it * kAdjRec + lane];
-    F[lane] = f;
-  } else if (lane - kAdjRec < 7) {
+    int it = i0;
+    for (; it + 3 * W < i1; it += 4 * W) {
+      const double r0 = rec[(int64_t)it * kAdjRec + lane], r1 = rec[(int64_t)(it + W) * kAdjRec + lane];
+      const double r2 = rec[(int64_t)(it + 2 * W) * kAdjRec + lane], r3 = rec[(int64_t)(it + 3 * W) * kAdjRec + lane];
+      f = (((f + r0) + r1) + r2) + r3;
+    }
+    for (; it < i1; it += W) f += rec[(int64_t)it * kAdjRec + lane];
+    part[warp][lane] = f;
+  } else if (warp == 0 && lane - kAdjRec < 7) {
     const int k = lane - kAdjRec;
     d[k] = u[7 * j + k] - u[7 * i + k];
   }
-  if (lane < 7) d[7 + lane] = tau[7 * j + lane] - tau[7 * i + lane];
+  if (warp == 1 && lane < 7) d[7 + lane] = tau[7 * j + lane] - tau[7 * i + lane];
+  __syncthreads();
+  if (warp != 0) return;
+  if (lane < kAdjRec) F[lane] = (part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]);
   __syncwarp();
   // y = [Ad^T F_xi, Ad^T F_u~, Ad^T F_tau~]
   if (lane < kAdjRec) {
@@ -371,15 +401,12 @@ __global__ void adjoint_edge_kernel(const double* __restrict__ rec, const int32_
     y[lane] = acc;
   }
   __syncwarp();
-  if (lane == 0) {
-    double pu[7], pt[7];
-    ad_transpose_apply(d, y + 7, pu);
-    ad_transpose_apply(d + 7, y + 14, pt);
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      out[14 * e + k] = -y[k] + pu[k] + pt[k];
-      out[14 * e + 7 + k] = y[k];
-    }
+  // ad_(u~_j - u~_i)^T y_u~ (lanes 0..6) and ad_(tau_j - tau_i)^T y_tau~ (lanes 7..13)
+  if (lane < 14) pq[lane] = lane < 7 ? ad_transpose_component(d, y + 7, lane) : ad_transpose_component(d + 7, y + 14, lane - 7);
+  __syncwarp();
+  if (lane < 7) {
+    out[14 * e + lane] = -y[lane] + pq[lane] + pq[7 + lane];
+    out[14 * e + 7 + lane] = y[lane];
   }
 }
 
@@ -624,7 +651,7 @@ cudaError_t launch_adjoint_edge_prep(int mode, const EdgeStatic* es, int E, cons
 cudaError_t launch_adjoint_edge(const double* rec, const int32_t* item_off, int E, const EdgeStatic* es,
                                 const double* Ad, const double* u, const double* tau, double* out, cudaStream_t s) {
   if (E == 0) return cudaSuccess;
-  adjoint_edge_kernel<<<E, 32, 0, s>>>(rec, item_off, E, es, Ad, u, tau, out);
+  adjoint_edge_kernel<<<E, kAdjEdgeThreads, 0, s>>>(rec, item_off, E, es, Ad, u, tau, out);
   return cudaGetLastError();
 }
 

@@ -1035,7 +1035,7 @@ constexpr int kSubAhead = 4;  // blocks whose loads a packed column issues befor
 
 // one column per warp: lanes 7 b + i (b < 4) take row i of every fourth block of the row,
 // the four partial sums meet by shuffles, lane q < 7 forms z_c[q] with row q of L_cc^{-1}
-__device__ void substitute_forward_spread(const double* Lb, const double* Sb, const int* row_off, const int2* row_ent,
+__device__ void substitute_forward_spread(const double* Lb, const double* Xb, int xs, const int* row_off, const int2* row_ent,
                                           double* Z, int col, int lane) {
   const int grp = lane / 7, i = lane % 7;
   const int r0 = row_off[col], nr = row_off[col + 1] - r0;
@@ -1060,7 +1060,7 @@ __device__ void substitute_forward_spread(const double* Lb, const double* Sb, co
   const double o3 = __shfl_sync(kFull, part, (i + 21) & 31);
   double* zc = Z + 7 * col;
   const double t = (lane < 7) ? zc[i] - ((part + o1) + (o2 + o3)) : 0.0;
-  const double* X = Sb + (int64_t)col * kColScratch + 14;  // L_cc^{-1}, row-major
+  const double* X = Xb + (int64_t)col * xs;  // L_cc^{-1}, row-major
   double yq = 0.0;
 #pragma unroll
   for (int r = 0; r < 7; ++r) {
@@ -1072,7 +1072,7 @@ __device__ void substitute_forward_spread(const double* Lb, const double* Sb, co
 }
 
 // the back substitution of one column per warp: the arithmetic of backward_column
-__device__ void substitute_backward_spread(const double* Lb, const double* Sb, const int* col_slot,
+__device__ void substitute_backward_spread(const double* Lb, const double* Xb, int xs, const int* col_slot,
                                            const int* slot_row, double* Z, int col, int lane) {
   const int grp = lane / 7, q = lane % 7;
   const int s_begin = col_slot[col] + 1, nb = col_slot[col + 1] - s_begin;
@@ -1096,7 +1096,7 @@ __device__ void substitute_backward_spread(const double* Lb, const double* Sb, c
   const double o3 = __shfl_sync(kFull, part, (q + 21) & 31);
   double* zc = Z + 7 * col;
   const double t = (lane < 7) ? zc[q] - ((part + o1) + (o2 + o3)) : 0.0;
-  const double* X = Sb + (int64_t)col * kColScratch + 14;
+  const double* X = Xb + (int64_t)col * xs;
   double xq = 0.0;
 #pragma unroll
   for (int r = 0; r < 7; ++r) {
@@ -1110,12 +1110,12 @@ __device__ void substitute_backward_spread(const double* Lb, const double* Sb, c
 // four columns per warp: segment s = lane / 8 takes column cols[s] (s < ncols), its lane
 // i < 7 row i.  s = sum_j L_cj z_j - z_c accumulates in one chain (so t = -s), then
 // z_c = -L_cc^{-1} s with the segment's s_r by shuffles.
-__device__ void substitute_forward_packed(const double* Lb, const double* Sb, const int* row_off, const int2* row_ent,
+__device__ void substitute_forward_packed(const double* Lb, const double* Xb, int xs, const int* row_off, const int2* row_ent,
                                           double* Z, const int* cols, int ncols, int lane) {
   const int seg = lane >> 3, i = lane & 7;
   const bool act = seg < ncols && i < 7;
   const int col = cols[seg < ncols ? seg : 0];
-  const double* X = Sb + (int64_t)col * kColScratch + 14 + 7 * i;
+  const double* X = Xb + (int64_t)col * xs + 7 * i;
   double xr[7];  // row i of L_cc^{-1}, loaded ahead of the chain
 #pragma unroll
   for (int r = 0; r < 7; ++r) xr[r] = act && r <= i ? X[r] : 0.0;
@@ -1150,12 +1150,12 @@ __device__ void substitute_forward_packed(const double* Lb, const double* Sb, co
   if (act) Z[7 * col + i] = -y;
 }
 
-__device__ void substitute_backward_packed(const double* Lb, const double* Sb, const int* col_slot,
+__device__ void substitute_backward_packed(const double* Lb, const double* Xb, int xs, const int* col_slot,
                                            const int* slot_row, double* Z, const int* cols, int ncols, int lane) {
   const int seg = lane >> 3, q = lane & 7;
   const bool act = seg < ncols && q < 7;
   const int col = cols[seg < ncols ? seg : 0];
-  const double* X = Sb + (int64_t)col * kColScratch + 14 + q;
+  const double* X = Xb + (int64_t)col * xs + q;
   double xc[7];  // column q of L_cc^{-1}, loaded ahead of the chain
 #pragma unroll
   for (int r = 0; r < 7; ++r) xc[r] = act && r >= q ? X[7 * r] : 0.0;
@@ -1190,7 +1190,8 @@ __device__ void substitute_backward_packed(const double* Lb, const double* Sb, c
   if (act) Z[7 * col + q] = -x;
 }
 
-template <bool SMEM>
+// FSMEM (with SMEM): the kept blocks and L_cc^{-1} staged into shared memory as well.
+template <bool SMEM, bool FSMEM>
 __global__ void __launch_bounds__(kSolveThreads) factor_substitute_kernel(SolverPlan P, FactorKeep keep,
                                                                           const GraphInfoDev* __restrict__ rec,
                                                                           const double* __restrict__ rhs,
@@ -1208,6 +1209,8 @@ __global__ void __launch_bounds__(kSolveThreads) factor_substitute_kernel(Solver
   }
   const double* Lb = keep.L + (int64_t)sbase * 49;
   const double* Sb = keep.S + (int64_t)cbase * kColScratch;
+  const double* Xb = Sb + 14;  // L_cc^{-1} of column c at Xb + xs c
+  int xs = kColScratch;
   const int* col_slot = P.col_slot + cbase + g;
   const int* slot_row = P.slot_row + sbase;
   const int* row_off = P.row_off + cbase + g;
@@ -1242,6 +1245,19 @@ __global__ void __launch_bounds__(kSolveThreads) factor_substitute_kernel(Solver
     stage(sc, sched, ncol, tid);
     stage(lv, lvl, 4 * (nlev + 1), tid);
     row_ent = re; row_off = ro; col_slot = cs; slot_row = sr; sched = sc; lvl = lv;
+    if (FSMEM) {
+      double* Ls = carve<double>(q, (size_t)nslot * 49);
+      double* Xs = carve<double>(q, (size_t)ncol * 49);
+      stage(Ls, Lb, (int64_t)nslot * 49, tid);
+      for (int x = tid; x < 49 * ncol; x += kSolveThreads) {
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(Xs + x);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(Xb + (int64_t)(x / 49) * kColScratch + x % 49)
+                     : "memory");
+      }
+      Lb = Ls;
+      Xb = Xs;
+      xs = 49;
+    }
   } else {
     Z = zwork + (int64_t)cbase * 7;
   }
@@ -1252,10 +1268,10 @@ __global__ void __launch_bounds__(kSolveThreads) factor_substitute_kernel(Solver
     const int q0 = lvl[4 * lv], n = lvl[4 * lv + 4] - q0;
     if (n <= kSubSpread) {
       for (int q = warp; q < n; q += kSolveWarps)
-        substitute_forward_spread(Lb, Sb, row_off, row_ent, Z, sched[q0 + q], lane);
+        substitute_forward_spread(Lb, Xb, xs, row_off, row_ent, Z, sched[q0 + q], lane);
     } else {
       for (int q = 4 * warp; q < n; q += 4 * kSolveWarps)
-        substitute_forward_packed(Lb, Sb, row_off, row_ent, Z, sched + q0 + q, min(4, n - q), lane);
+        substitute_forward_packed(Lb, Xb, xs, row_off, row_ent, Z, sched + q0 + q, min(4, n - q), lane);
     }
     __syncthreads();
   }
@@ -1263,10 +1279,10 @@ __global__ void __launch_bounds__(kSolveThreads) factor_substitute_kernel(Solver
     const int q0 = lvl[4 * lv], n = lvl[4 * lv + 4] - q0;
     if (n <= kSubSpread) {
       for (int q = warp; q < n; q += kSolveWarps)
-        substitute_backward_spread(Lb, Sb, col_slot, slot_row, Z, sched[q0 + q], lane);
+        substitute_backward_spread(Lb, Xb, xs, col_slot, slot_row, Z, sched[q0 + q], lane);
     } else {
       for (int q = 4 * warp; q < n; q += 4 * kSolveWarps)
-        substitute_backward_packed(Lb, Sb, col_slot, slot_row, Z, sched + q0 + q, min(4, n - q), lane);
+        substitute_backward_packed(Lb, Xb, xs, col_slot, slot_row, Z, sched + q0 + q, min(4, n - q), lane);
     }
     __syncthreads();
   }
@@ -1355,19 +1371,25 @@ cudaError_t launch_factor_solve_group(int ctas, const SolverPlan& plan, const in
                             eps0, max_attempts, ginfo, warn, keep, gfail);
 }
 
-cudaError_t factor_substitute_prepare(size_t smem_bytes) {
-  return cudaFuncSetAttribute(factor_substitute_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+cudaError_t factor_substitute_prepare(size_t smem_bytes, bool factor_in_smem) {
+  if (factor_in_smem)
+    return cudaFuncSetAttribute(factor_substitute_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes);
+  return cudaFuncSetAttribute(factor_substitute_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem_bytes);
 }
 
 cudaError_t launch_factor_substitute(int G, const SolverPlan& plan, FactorKeep keep, const GraphInfoDev* rec,
-                                     const double* rhs, double* out, size_t smem_bytes, double* zwork, cudaStream_t s) {
+                                     const double* rhs, double* out, size_t smem_bytes, double* zwork, cudaStream_t s,
+                                     bool factor_in_smem) {
   if (G <= 0) return cudaSuccess;
   if (!keep.L || !keep.S || (smem_bytes == 0 && !zwork)) return cudaErrorInvalidValue;
-  if (smem_bytes)
-    factor_substitute_kernel<true><<<G, kSolveThreads, smem_bytes, s>>>(plan, keep, rec, rhs, out, nullptr);
+  if (smem_bytes && factor_in_smem)
+    factor_substitute_kernel<true, true><<<G, kSolveThreads, smem_bytes, s>>>(plan, keep, rec, rhs, out, nullptr);
+  else if (smem_bytes)
+    factor_substitute_kernel<true, false><<<G, kSolveThreads, smem_bytes, s>>>(plan, keep, rec, rhs, out, nullptr);
   else
-    factor_substitute_kernel<false><<<G, kSolveThreads, 0, s>>>(plan, keep, rec, rhs, out, zwork);
+    factor_substitute_kernel<false, false><<<G, kSolveThreads, 0, s>>>(plan, keep, rec, rhs, out, zwork);
   return cudaGetLastError();
 }
 

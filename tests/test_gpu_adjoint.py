@@ -242,10 +242,12 @@ def test_vjp_full_size_mixed_matches_fp64(C, adjoint_workload):
 
 
 @pytest.mark.parametrize("setting", [("COMO3R_SOLVE_CLUSTER", "4"), ("COMO3R_SOLVE_GRID", "1"),
-                                     ("COMO3R_SUBSTITUTE_SMEM", "0")])
+                                     ("COMO3R_SUBSTITUTE_SMEM", "1"), ("COMO3R_SUBSTITUTE_SMEM", "0")])
 def test_vjp_with_each_kept_factor(C, mid, monkeypatch, setting):
     """The adjoint systems solved with the factor kept by the multi-SM (cluster) and the
-    grid-wide factorisations, and with the substitution's working vector in global memory."""
+    grid-wide factorisations, and by the substitution with the factor read through the L2
+    (its plan and vector in shared memory) or with everything in global memory (the default
+    stages the factor into shared memory)."""
     monkeypatch.setenv(*setting)
     gl, gc, _, _, _ = gpu_grads(C, mid, 0, 2, C.VJP_UNROLLED)
     rng = np.random.default_rng(7)
