@@ -723,7 +723,8 @@ void build_group_plan(const HostPlan& p, int sms, int force_big, GroupPlan& gp) 
   const int kmax = std::min(G, sms / kGroupCTAs);
   for (int k = 1; k <= kmax; ++k) {
     if (force_big >= 0 && k != force_big) continue;
-    const int m = ((sms - kGroupCTAs * k) / kGroupCTAs) * kGroupCTAs;
+    // the CTAs left for the other graphs, whole clusters (none when every graph is clustered)
+    const int m = k < G ? ((sms - kGroupCTAs * k) / kGroupCTAs) * kGroupCTAs : 0;
     if (k < G && m == 0) continue;
     double mk = pack(k, m, nullptr);
     for (int q = 0; q < k; ++q) mk = std::max(mk, group(idx[q], nullptr));
