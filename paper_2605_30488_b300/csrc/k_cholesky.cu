@@ -908,6 +908,9 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
   // landed (and be visible to every thread) before any address is formed from it
   async_wait_all();
   __syncthreads();
+  // launched as a programmatic dependent of the assembly: the system is complete and
+  // visible once the preceding grid has finished (returns at once without such a grid)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const double* Ag = A + (int64_t)sbase * 49;
   const int* col_kf = P.col_kf + cbase;
 
@@ -1433,13 +1436,17 @@ cudaError_t launch_factor_solve_cluster(int G, const SolverPlan& plan, const Clu
   cfg.blockDim = dim3(kClusterThreads);
   cfg.dynamicSmemBytes = smem_bytes;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)cp.C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  // may start before the preceding kernel (the assembly) finishes: it stages its plan
+  // meanwhile and waits for that kernel before reading the system
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   return cudaLaunchKernelEx(&cfg, factor_solve_cluster_kernel, plan, cp, A, gvec, tau, lambda, eps0, max_attempts,
                             ginfo, warn, keep);
 }

@@ -192,6 +192,9 @@ __global__ void __launch_bounds__(64) assemble_kernel(int num_slots, const int32
                                                       const double* __restrict__ edge_cost,
                                                       const double* __restrict__ edge_skip, GraphInfoDev* ginfo,
                                                       double* cost_hist, const int* iter_counter, int* warn) {
+  // the solver launched after this kernel may start now: it stages its static plan and
+  // waits for this grid's completion (griddepcontrol.wait) before it reads A or g
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int b = blockIdx.x, t = threadIdx.x;
   if (b < num_slots) {
     if (t >= 49) return;
