@@ -682,22 +682,23 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
 
 namespace como3r {
 
-// Estimated solve times (microseconds), measured orders of magnitude on this GPU: one CTA
-// with the factor in global memory pays ~9.4 us per elimination level (a 7x7 factorisation
-// chain with L2 round trips) and ~0.14 us per block update (14 FP64 warp instructions on
-// one SM's four sub-partitions); a cluster of kGroupCTAs pays ~10 us per level (cluster
-// barriers) and spreads the updates over its SMs.
+// Estimated solve times (microseconds), fitted to one-CTA solves of the 64-graph batch on
+// this GPU (per-graph completion stamps): one CTA with the factor in global memory pays
+// ~40 us per graph (staging, the first attempt's set-up), ~6.3 us per elimination level (a
+// 7x7 factorisation chain with L2 round trips) and ~0.26 us per block update (14 FP64 warp
+// instructions on one SM's four sub-partitions, with their loads); a cluster of kGroupCTAs
+// pays ~10 us per level (cluster barriers) and spreads the updates over its SMs.
 void build_group_plan(const HostPlan& p, int sms, int force_big, GroupPlan& gp) {
   gp = GroupPlan();
   const int G = p.G;
   if (G < 2 || sms < kGroupCTAs) return;
   auto one = [&](int g) {
     const bool md = 3.0 * p.nlev_md[g] + 0.15 * (double)p.upd_md[g] <= 3.0 * p.nlev_nd[g] + 0.15 * (double)p.upd_nd[g];
-    return md ? 9.4 * p.nlev_md[g] + 0.14 * (double)p.upd_md[g] : 9.4 * p.nlev_nd[g] + 0.14 * (double)p.upd_nd[g];
+    return 40.0 + (md ? 6.3 * p.nlev_md[g] + 0.26 * (double)p.upd_md[g] : 6.3 * p.nlev_nd[g] + 0.26 * (double)p.upd_nd[g]);
   };
   auto group = [&](int g, int* order) {
-    const double md = 10.0 * p.nlev_md[g] + 0.14 / kGroupCTAs * (double)p.upd_md[g];
-    const double nd = 10.0 * p.nlev_nd[g] + 0.14 / kGroupCTAs * (double)p.upd_nd[g];
+    const double md = 10.0 * p.nlev_md[g] + 0.26 / kGroupCTAs * (double)p.upd_md[g];
+    const double nd = 10.0 * p.nlev_nd[g] + 0.26 / kGroupCTAs * (double)p.upd_nd[g];
     if (order) *order = md <= nd ? 0 : 1;
     return md <= nd ? md : nd;
   };
