@@ -406,26 +406,37 @@ int create_impl(como3r_graph* g, const como3r_graph_desc* d) {
     g->group_ctas = gp.ctas;
     g->group_big = gp.big;
   }
-  // multi-SM solve for a few large graphs (it needs the graphs' clusters to fit on the GPU);
+  // multi-SM solve for a few large graphs (it needs the graphs' clusters to fit on the GPU):
+  // eight CTAs per graph, or sixteen (a non-portable cluster size) when a factor does not fit
+  // eight CTAs' shared memory and the GPU can schedule such a cluster;
   // COMO3R_SOLVE_CLUSTER=<C> forces C CTAs per graph, 0 disables it
   if (g->group_ctas == 0) {
     int C = 0, max_col = 0;
     for (int k = 0; k < p.G; ++k) max_col = std::max(max_col, p.col_begin[k + 1] - p.col_begin[k]);
     if (max_col >= 32 && 8 * p.G <= g->sms) C = 8;
-    if (const char* e = getenv("COMO3R_SOLVE_CLUSTER")) C = std::max(0, std::min(16, atoi(e)));
+    const char* force_c = getenv("COMO3R_SOLVE_CLUSTER");
+    if (force_c) C = std::max(0, std::min(16, atoi(force_c)));
     if (C > 1) {
       HostClusterPlan hc;
       build_cluster_plan(p, C, hc);
+      if (!force_c && hc.max_cta_smem > smax && 16 * p.G <= g->sms) {
+        HostClusterPlan h16;
+        build_cluster_plan(p, 16, h16);
+        if (h16.max_cta_smem <= smax && factor_solve_cluster_max_active(h16.max_cta_smem, 16) > 0) {
+          hc = std::move(h16);
+          C = 16;
+        }
+      }
       if (hc.max_cta_smem <= smax) {
         int32_t *cmeta, *csched, *clvl, *own, *shome, *chome;
-        int4* cut;
+        int4 *cut, *ctri;
         int2* ctt;
         if ((rc = upload(g, &cmeta, hc.cmeta)) || (rc = upload(g, &csched, hc.csched)) ||
             (rc = upload(g, &clvl, hc.clvl)) || (rc = upload(g, &own, hc.own_slot)) ||
             (rc = upload(g, &shome, hc.slot_home)) || (rc = upload(g, &chome, hc.col_home)) ||
-            (rc = upload(g, &cut, hc.cutask)) || (rc = upload(g, &ctt, hc.cttask)))
+            (rc = upload(g, &cut, hc.cutask)) || (rc = upload(g, &ctt, hc.cttask)) || (rc = upload(g, &ctri, hc.ctri)))
           return rc;
-        g->cp = ClusterPlan{C, cmeta, csched, cut, ctt, clvl, own, shome, chome};
+        g->cp = ClusterPlan{C, cmeta, csched, cut, ctt, clvl, own, shome, chome, ctri};
         g->cluster_smem = hc.max_cta_smem;
         CK(factor_solve_cluster_prepare(g->cluster_smem, C), "cluster solver attributes");
         g->cluster_ctas = C;

@@ -147,8 +147,12 @@ struct SolverPlan {
 // kCTopLocal: the lowest level from which on every level's columns are all owned by rank 0
 // (the narrow top of the elimination tree): the back substitution of those levels needs no
 // cluster barrier between them (only rank 0 works, and only rank 0 reads their solutions).
+// kCTri / kCNTri: the CTA's own triplet list (the triplets of the update tasks it runs, in
+// task order; its tasks' triplet ranges index into it), so that a CTA stages only what it
+// reads, not the whole graph's list.
 enum ClusterMeta {
-  kCSched, kCNSched, kCU, kCNU, kCT, kCNT, kCLvl, kCNSlot, kCNCol, kCOwn, kCNColMax, kCTopLocal, kCMetaCount
+  kCSched, kCNSched, kCU, kCNU, kCT, kCNT, kCLvl, kCNSlot, kCNCol, kCOwn, kCNColMax, kCTopLocal, kCTri, kCNTri,
+  kCMetaCount
 };
 struct ClusterPlan {
   int C;                    // CTAs per graph
@@ -160,6 +164,7 @@ struct ClusterPlan {
   const int32_t* own_slot;  // graph-local slot of each local slot, per (graph, rank)
   const int32_t* slot_home; // per slot (at slot_base)
   const int32_t* col_home;  // per column (at col_base)
+  const int4* ctri;         // triplets of each (graph, rank)'s update tasks
 };
 
 // Bytes of shared memory one graph's factor, per-column scratch and plan occupy.
@@ -186,7 +191,8 @@ inline size_t substitute_factor_bytes(int nslot, int ncol) {
 }
 
 // Bytes of shared memory of one CTA of the multi-SM solve: its blocks and column scratch,
-// the graph's triplets, its task lists and the graph's home / column-slot / row maps.
+// the triplets of its update tasks, its task lists and the graph's home / column-slot / row
+// maps.
 inline size_t cluster_smem_bytes(int nslot_loc, int ncol_loc, int ncol_max, int ntri, int nu, int nt, int nlev,
                                  int nslot, int ncol) {
   auto r16 = [](size_t x) { return (x + 15) & ~size_t(15); };
@@ -265,6 +271,9 @@ cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t
                                 double eps0, int max_attempts, GraphInfoDev* ginfo, int* warn, cudaStream_t s,
                                 FactorKeep keep = {});
 size_t factor_solve_max_smem();
+// Clusters of C CTAs (with smem_bytes each) of the multi-SM solver that the GPU can hold at
+// once (0: none, e.g. a cluster size it cannot schedule); sets the kernel's attributes.
+int factor_solve_cluster_max_active(size_t smem_bytes, int C);
 // out = -(L L^T)^{-1} rhs with the factor a successful solve kept (the adjoint systems of
 // the unrolled vjp), per graph; zero on the columns of a graph whose recorded solve
 // (rec[g].solved) failed.  rhs / out are [N][7] by keyframe; anchors are not written.

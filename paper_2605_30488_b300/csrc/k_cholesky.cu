@@ -867,7 +867,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
   const int* m = P.meta + kMetaCount * g;
   const int* cm = CP.cmeta + kCMetaCount * (g * CP.C + rank);
   const int cbase = m[kMetaColBase], ncol = m[kMetaNCol], sbase = m[kMetaSlotBase], nslot = m[kMetaNSlot];
-  const int nlev = m[kMetaNLvl], ntri = m[kMetaNTri];
+  const int nlev = m[kMetaNLvl], ntri = cm[kCNTri];
   if (ncol == 0) {  // the whole cluster returns here (same graph)
     if (tid == 0 && rank == 0) {
       ginfo[g].attempts = 1;
@@ -892,7 +892,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1) factor_solve_cluster_kerne
   int* ch = carve<int>(q, ncol);
   int* colslot = carve<int>(q, ncol + 1);
   int* srow = carve<int>(q, nslot);
-  stage(tri, P.tri + m[kMetaTriBase], ntri, tid, kClusterThreads);
+  stage(tri, CP.ctri + cm[kCTri], ntri, tid, kClusterThreads);
   stage(ut, CP.cutask + cm[kCU], nu, tid, kClusterThreads);
   stage(tt, CP.cttask + cm[kCT], nt, tid, kClusterThreads);
   stage(cs, CP.csched + cm[kCSched], ncl, tid, kClusterThreads);
@@ -1425,6 +1425,27 @@ cudaError_t factor_solve_cluster_prepare(size_t smem_bytes, int C) {
   if (e == cudaSuccess && C > 8)
     e = cudaFuncSetAttribute(factor_solve_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
+}
+
+int factor_solve_cluster_max_active(size_t smem_bytes, int C) {
+  if (factor_solve_cluster_prepare(smem_bytes, C) != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)C);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, factor_solve_cluster_kernel, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 cudaError_t launch_factor_solve_cluster(int G, const SolverPlan& plan, const ClusterPlan& cp, size_t smem_bytes,

@@ -551,7 +551,7 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
   for (int g = 0; g < p.G; ++g) {
     const int* m = p.meta.data() + kMetaCount * g;
     const int cbase = m[kMetaColBase], ncol = m[kMetaNCol], sbase = m[kMetaSlotBase], nslot = m[kMetaNSlot];
-    const int ubase = m[kMetaUBase], tbase = m[kMetaTBase], nlev = m[kMetaNLvl], ntri = m[kMetaNTri];
+    const int ubase = m[kMetaUBase], tbase = m[kMetaTBase], nlev = m[kMetaNLvl], tribase = m[kMetaTriBase];
     const int* lvl = p.llvl.data() + 4 * m[kMetaLvlBase];
     const int* colslot = p.lcol_slot.data() + cbase + g;
     const int* sched = p.lsched.data() + cbase;
@@ -667,12 +667,22 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
       }
       cp.clvl.insert(cp.clvl.end(), {(int)cp.csched.size() - s0, (int)cp.cutask.size() - u0,
                                      (int)cp.cutask.size() - u0, (int)cp.cttask.size() - t0});
+      // this CTA's triplets, in the order of its tasks, which are re-pointed at them
+      const int r0 = (int)cp.ctri.size();
+      for (size_t u = u0; u < cp.cutask.size(); ++u) {
+        int4& t = cp.cutask[u];
+        const int b = (int)cp.ctri.size() - r0;
+        cp.ctri.insert(cp.ctri.end(), p.ltri.begin() + tribase + t.y, p.ltri.begin() + tribase + t.z);
+        t.z = b + (t.z - t.y);
+        t.y = b;
+      }
+      const int nrt = (int)cp.ctri.size() - r0;
       for (int sl : own_slots[r]) cp.own_slot.push_back(sl);
       const int nsl = (int)own_slots[r].size(), ncl = (int)own_cols[r].size();
       cp.cmeta.insert(cp.cmeta.end(), {s0, (int)cp.csched.size() - s0, u0, (int)cp.cutask.size() - u0, t0,
-                                       (int)cp.cttask.size() - t0, l0, nsl, ncl, o0, ncol_max, top_local});
+                                       (int)cp.cttask.size() - t0, l0, nsl, ncl, o0, ncol_max, top_local, r0, nrt});
       cp.max_cta_smem = std::max(cp.max_cta_smem,
-                                 cluster_smem_bytes(nsl, ncl, ncol_max, ntri, (int)cp.cutask.size() - u0,
+                                 cluster_smem_bytes(nsl, ncl, ncol_max, nrt, (int)cp.cutask.size() - u0,
                                                     (int)cp.cttask.size() - t0, nlev, nslot, ncol));
     }
   }

@@ -50,7 +50,7 @@ struct HostPlan {
 struct HostClusterPlan {
   int C = 0;
   std::vector<int32_t> cmeta, csched, clvl, own_slot, slot_home, col_home;
-  std::vector<int4> cutask;
+  std::vector<int4> cutask, ctri;
   std::vector<int2> cttask;
   size_t max_cta_smem = 0;  // shared memory of the largest (graph, rank) CTA
 };

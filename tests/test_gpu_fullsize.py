@@ -205,3 +205,22 @@ def test_adjoint_4x30_envelope_matches_oracle(C, adjoint, mode_name):
         got = float(gl @ vl + gc @ vc)
         mag = float(np.abs(gl * vl).sum() + np.abs(gc * vc).sum())
         assert abs(got - ref) <= tol * mag, (seed, got, ref, mag)
+
+
+def test_adjoint_4x30_unrolled_mixed_matches_oracle(C, adjoint):
+    """The mixed form's unrolled gradient through the 8 iterations (FP32 per-match
+    arithmetic, FP64 solves and sums) against the oracle's complex-step directional
+    derivatives and single-pixel derivatives, at the mixed form's 1e-5."""
+    p, gold = adjoint
+    gl, gc, loss = vjp(C, p, C.MIXED, C.VJP_UNROLLED)
+    assert abs(loss / gold["loss"][0] - 1) <= MIXED_TOL
+    for seed, ref in zip(gold["dir_seeds"], gold["dir_unrolled"]):
+        vl, vc = directions(seed, gl.size)
+        got = float(gl @ vl + gc @ vc)
+        mag = float(np.abs(gl * vl).sum() + np.abs(gc * vc).sum())
+        assert abs(got - ref) <= MIXED_GRAD_TOL * mag, (seed, got, ref, mag)
+    pix = gold["pixels"].astype(np.int64)
+    g_at = np.where(gold["fd_which"] == 0, gl[pix], gc[pix])
+    scale = np.abs(g_at).max()
+    for k, ex in zip(gold["exact_idx"].astype(int), gold["exact"]):
+        assert abs(g_at[k] - ex) <= MIXED_GRAD_TOL * max(abs(ex), 1e-3 * scale), (k, g_at[k], ex)

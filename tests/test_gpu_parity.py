@@ -300,7 +300,7 @@ def test_batched_tracking(C):
         assert all(x["solved"] for x in info)
 
 
-@pytest.mark.parametrize("ctas", [2, 4, 8])
+@pytest.mark.parametrize("ctas", [2, 4, 8, 16])
 def test_multi_sm_solve_matches_oracle(C, tiny, mid, ctas, monkeypatch):
     """The multi-SM factorisation (one cluster of `ctas` CTAs per graph, columns spread over
     them) gives the oracle's FP64 steps and solves, alone and for a batch of graphs."""
