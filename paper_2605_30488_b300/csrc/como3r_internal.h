@@ -254,8 +254,9 @@ constexpr int kPanelCols = 4;
 constexpr int kPanelBlocks = 3;
 // A level (or a CTA's part of a level in the multi-SM solve) with a single column is a
 // panel when that column has at most this many off-diagonal blocks: four warps eliminate
-// its first 32 rows and then solve the last four of its 8 + 7 x 4 = 36 against L_cc.
-constexpr int kPanel4Blocks = 4;
+// its first 32 rows and then solve the rest of its 8 + 7 nb rows against L_cc, one row per
+// thread of the four warps (8 + 7 x 20 - 32 = 116 <= 128).
+constexpr int kPanel4Blocks = 20;
 // A CTA of the multi-SM solve (8 warps) factors up to this many of its columns of a level
 // as whole panels, one warp each (a fifth column would otherwise turn the CTA's level into
 // diagonal factorisations followed by off-diagonal solves, about twice the dependent chain).

@@ -259,17 +259,19 @@ __device__ void panel_factor(const SolveCtx& C, int col, int lane, int* fail) {
 // pivot, so it is never rewritten within a column) across one named barrier of the four
 // warps (barrier 1; all four warps call this together and pass every barrier).  Every
 // entry sees the operations of panel_factor in the same order: bitwise the same factor.
-// A column with kPanel4Blocks off-diagonal blocks has 36 rows: rows 32..35 (block 3, rows
-// 3..6) stay out of the elimination (any instruction for them in the pivot loop would
-// lengthen every column's chain) and are solved afterwards against the finished L_cc by
-// lanes 0..3 of warp 0, with the operations of the off-diagonal solve: bitwise what the
-// elimination would give them.
+// A column with nb >= 4 off-diagonal blocks has 8 + 7 nb > 32 rows: rows 32 and up stay
+// out of the elimination (any instruction for them in the pivot loop would lengthen every
+// column's chain) and are solved afterwards against the finished L_cc with the operations
+// of the off-diagonal solve (bitwise what the elimination would give them): in the narrow
+// form (nb <= kPanel4Narrow) rows 32..35 by lanes 0..3 of warp 0, in the wide form row
+// 32 + t by thread t of the four warps.
 __device__ __forceinline__ void panel_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+constexpr int kPanel4Narrow = 4;
 
-template <bool CL>
-__device__ void panel_factor4(const SolveCtx& C, int col, int warp, int lane, double* xbuf, int* fail) {
+template <bool CL, bool WIDE>
+__device__ void panel_factor4_impl(const SolveCtx& C, int col, int warp, int lane, double* xbuf, int* fail) {
   const int dslot = C.col_slot[col], nb = C.col_slot[col + 1] - dslot - 1;
-  if (nb > kPanel4Blocks) {  // never planned; the same decision in all four warps
+  if (nb > (WIDE ? kPanel4Blocks : kPanel4Narrow)) {  // never planned; the same decision in all four warps
     if (warp == 0 && lane == 0) raise_fail<CL>(C, fail);
     return;
   }
@@ -325,12 +327,15 @@ __device__ void panel_factor4(const SolveCtx& C, int col, int warp, int lane, do
   }
   if (lane < 7 && (lane & 3) == warp) dinv_of<CL>(C, col)[lane] = myinv;
   if (__any_sync(kFull, bad) && lane == 0) raise_fail<CL>(C, fail);
-  if (nb == kPanel4Blocks) {  // rows 32..35 (the same decision in all four warps)
-    panel_barrier();           // L_cc and its pivot inverses are in place
-    if (warp == 0 && lane < 4) {
+  const int ntail = 8 + 7 * nb - 32;
+  if (ntail > 0) {    // rows 32.. (the same decision in all four warps)
+    panel_barrier();  // L_cc and its pivot inverses are in place
+    const int t = WIDE ? 32 * warp + lane : (warp == 0 ? lane : 32);
+    if (t < ntail) {
       const double* Lc = D;
       const double* dv = dinv_of<CL>(C, col);
-      double* B = blk<CL>(C, dslot + kPanel4Blocks) + 7 * (3 + lane);
+      double* B = WIDE ? blk<CL>(C, dslot + 1 + (24 + t) / 7) + 7 * ((24 + t) % 7)
+                       : blk<CL>(C, dslot + kPanel4Narrow) + 7 * (3 + lane);
       double sr[7];
 #pragma unroll
       for (int c = 0; c < 7; ++c) sr[c] = B[c];
@@ -344,6 +349,18 @@ __device__ void panel_factor4(const SolveCtx& C, int col, int warp, int lane, do
       for (int c = 0; c < 7; ++c) B[c] = sr[c];
     }
   }
+}
+
+// Four-warp panel of a single column: the narrow form (at most kPanel4Narrow off-diagonal
+// blocks, most single-column levels) and the wide form are separate copies; one copy for
+// both made every narrow panel ~0.14 us slower.
+template <bool CL>
+__device__ __forceinline__ void panel_factor4(const SolveCtx& C, int col, int warp, int lane, double* xbuf,
+                                              int* fail) {
+  if (C.col_slot[col + 1] - C.col_slot[col] - 1 <= kPanel4Narrow)
+    panel_factor4_impl<CL, false>(C, col, warp, lane, xbuf, fail);
+  else
+    panel_factor4_impl<CL, true>(C, col, warp, lane, xbuf, fail);
 }
 
 // T: item x < 7 * nt: row (x % 7) of off-diagonal block ttask[t0 + x / 7]; items from

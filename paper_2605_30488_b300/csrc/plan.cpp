@@ -599,30 +599,28 @@ void build_cluster_plan(const HostPlan& p, int C, HostClusterPlan& cp) {
     for (int sl = 0; sl < nslot; ++sl) cp.slot_home[sbase + sl] = (shome[sl] << 24) | slocal[sl];
     // Executors of the far update tasks of level l (they run during level l + 1's diagonal
     // factorisations, writing their destinations through the cluster window when remote):
-    // when level l + 1 has fewer columns than CTAs, the CTAs that own none of them -- on
-    // this GPU an SM's FP64 pipe is narrow, and updates run beside a critical
-    // factorisation delay it; otherwise every CTA.  Each task goes to the candidate with
-    // the least update work so far at this level (work = the task's triplets), so the
-    // wide bottom levels, whose far updates mostly land in the top columns, do not pile
-    // them on those columns' owner.
+    // each task (work = its triplets) goes to the CTA with the least estimated work so far,
+    // where a CTA that factors columns of level l + 1 starts from that factorisation's time
+    // (kFarBusyBase triplets' worth per round of up to kClusterPanelCols columns: on this GPU
+    // an SM's FP64 pipe is narrow, and updates run beside a critical factorisation delay it)
+    // and an idle CTA from zero; ties go to the highest rank (rank 0 owns the critical top
+    // of the tree).  So the idle CTAs take the far work first, and it spreads over every CTA
+    // only where it would outlast the factorisations (a wide level under a level with one
+    // idle CTA).
+    constexpr long long kFarBusyBase = 24;
     std::vector<int> far_exec(std::max(lvl[4 * nlev + 1], 0), -1);
     for (int l = 0; l < nlev; ++l) {
-      std::vector<char> busy(C, 0);
-      int nbusy = 0;
-      if (l + 1 < nlev)
-        for (int q = lvl[4 * (l + 1)]; q < lvl[4 * (l + 2)]; ++q)
-          if (!busy[owner[sched[q]]]) {
-            busy[owner[sched[q]]] = 1;
-            ++nbusy;
-          }
-      std::vector<int> cand;
-      for (int r = 0; r < C; ++r)
-        if (nbusy == C || !busy[r]) cand.push_back(r);
       std::vector<long long> load(C, 0);
+      if (l + 1 < nlev) {
+        std::vector<int> nown(C, 0);
+        for (int q = lvl[4 * (l + 1)]; q < lvl[4 * (l + 2)]; ++q) ++nown[owner[sched[q]]];
+        for (int r = 0; r < C; ++r)
+          if (nown[r]) load[r] = kFarBusyBase * ((nown[r] + kClusterPanelCols - 1) / kClusterPanelCols);
+      }
       for (int u = lvl[4 * l + 2]; u < lvl[4 * (l + 1) + 1]; ++u) {
         const int4 t = p.lutask[ubase + u];
-        int best = cand[0];
-        for (int r : cand)
+        int best = C - 1;
+        for (int r = C - 2; r >= 0; --r)
           if (load[r] < load[best]) best = r;
         far_exec[u] = best;
         load[best] += std::max(1, t.z - t.y);
