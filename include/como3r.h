@@ -111,8 +111,10 @@ typedef struct {
 
 /* Validate the description, plan the solve (fill-reducing ordering, symbolic block
  * factorisation, work lists; for a few large graphs a multi-SM solve with one cluster of 8
- * CTAs per graph, COMO3R_SOLVE_CLUSTER=<C> forcing C CTAs or 0 none; for one graph whose
- * factor fits neither one SM nor a cluster, a grid-wide solve over one CTA per SM (a
+ * CTAs per graph (16 when a factor does not fit eight CTAs' shared memory and the device
+ * can schedule a 16-CTA cluster), COMO3R_SOLVE_CLUSTER=<C> forcing C CTAs or 0 none; for
+ * one graph whose factor fits neither one SM nor a cluster, a grid-wide solve over one CTA
+ * per SM (a
  * cooperative launch), COMO3R_SOLVE_GRID=1 forcing it for any one-graph plan, 0 disabling
  * it; for a batch too large for one cluster per graph, one launch of CTA groups when the
  * planner's estimates favour it: the slowest graphs each solved by a cluster of 8 CTAs, the
