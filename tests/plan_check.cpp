@@ -1,0 +1,220 @@
+// Host-side checks of the multi-SM solver's plan (build_cluster_plan), compiled and run by
+// tests/test_plan_host.py.  For synthetic pose-graph topologies and cluster sizes 2..16:
+//   * every update task of the graph's plan is run exactly once per level: a near task by
+//     the CTA that owns its destination, a far task by one executor;
+//   * a CTA's tasks index its own triplet list, and the triplets they reach there are the
+//     triplets of the same task in the graph's list, in the same order;
+//   * far tasks are assigned greedily by estimated work: a CTA's last far task of a level
+//     went to it while its estimated work was the least of all CTAs;
+//   * the shared memory reported covers every CTA's blocks, scratch, triplets and lists.
+// Prints "OK <checks>" on success, "FAIL <reason>" otherwise.
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+
+using namespace como3r;
+
+namespace {
+
+int g_checks = 0;
+#define CHECK(cond, ...)                 \
+  do {                                   \
+    ++g_checks;                          \
+    if (!(cond)) {                       \
+      std::printf("FAIL ");              \
+      std::printf(__VA_ARGS__);          \
+      std::printf("\n");                 \
+      std::exit(1);                      \
+    }                                    \
+  } while (0)
+
+struct Topo {
+  std::string name;
+  std::vector<int32_t> kf_offset, height, width, agent_of, edge_offset, edge_i, edge_j, anchor;
+};
+
+// Graphs of `agents` chains of n keyframes each: consecutive edges, skip edges every
+// second keyframe, loop closures every `loop` keyframes and `inter` edges between agents.
+void add_graph(Topo& t, int agents, int n, int loop, int inter, unsigned seed) {
+  const int base = t.kf_offset.back();
+  for (int a = 0; a < agents; ++a)
+    for (int k = 0; k < n; ++k) t.agent_of.push_back(a);
+  auto kf = [&](int a, int k) { return base + a * n + k; };
+  for (int a = 0; a < agents; ++a) {
+    for (int k = 0; k + 1 < n; ++k) t.edge_i.push_back(kf(a, k)), t.edge_j.push_back(kf(a, k + 1));
+    for (int k = 0; k + 2 < n; k += 2) t.edge_i.push_back(kf(a, k)), t.edge_j.push_back(kf(a, k + 2));
+    if (loop > 0)
+      for (int k = loop; k < n; k += loop) t.edge_i.push_back(kf(a, k - loop)), t.edge_j.push_back(kf(a, k));
+  }
+  unsigned s = seed;
+  auto rnd = [&](int m) { s = s * 1664525u + 1013904223u; return (int)((s >> 8) % (unsigned)m); };
+  for (int q = 0; q < inter && agents > 1; ++q) {
+    const int a = rnd(agents), b = (a + 1 + rnd(agents - 1)) % agents;
+    t.edge_i.push_back(kf(a, rnd(n)));
+    t.edge_j.push_back(kf(b, rnd(n)));
+  }
+  t.kf_offset.push_back(base + agents * n);
+  t.height.push_back(48);
+  t.width.push_back(64);
+  t.edge_offset.push_back((int32_t)t.edge_i.size());
+  t.anchor.push_back(base);
+}
+
+void check_topology(const Topo& t) {
+  const int G = (int)t.height.size();
+  float dummy[4] = {0, 0, 0, 0};
+  int32_t midx[1] = {-1};
+  como3r_graph_desc d{};
+  d.num_graphs = G;
+  d.kf_offset = t.kf_offset.data();
+  d.height = t.height.data();
+  d.width = t.width.data();
+  d.agent_of = t.agent_of.data();
+  d.points_conf = dummy;
+  d.dtype = COMO3R_F32;
+  d.edge_offset = t.edge_offset.data();
+  d.edge_i = t.edge_i.data();
+  d.edge_j = t.edge_j.data();
+  d.match_idx = midx;
+  d.anchor = t.anchor.data();
+  d.sigma_ray = 0.003;
+  d.sigma_dist = 10;
+  d.huber_k = 1.345;
+  d.eps0 = 1e-6;
+  d.max_attempts = 6;
+  d.mode = COMO3R_MIXED;
+  HostPlan p;
+  CHECK(build_plan(&d, p) == COMO3R_OK, "%s: build_plan: %s", t.name.c_str(), p.error.c_str());
+  for (int C : {2, 4, 8, 16}) {
+    HostClusterPlan cp;
+    build_cluster_plan(p, C, cp);
+    for (int g = 0; g < G; ++g) {
+      const int* m = p.meta.data() + kMetaCount * g;
+      const int nlev = m[kMetaNLvl], ubase = m[kMetaUBase], tribase = m[kMetaTriBase], sbase = m[kMetaSlotBase];
+      const int cbase = m[kMetaColBase];
+      const int* lvl = p.llvl.data() + 4 * m[kMetaLvlBase];
+      const int* colslot = p.lcol_slot.data() + cbase + g;
+      // per level: global tasks by destination slot
+      for (int l = 0; l < nlev; ++l) {
+        std::map<int, int> seen;  // destination -> times run
+        std::vector<long long> load(C, 0), last_w(C, 0);
+        std::vector<int> nown_next(C, 0);
+        for (int r = 0; r < C; ++r) {
+          const int32_t* cm = cp.cmeta.data() + kCMetaCount * (g * C + r);
+          const int32_t* L = cp.clvl.data() + cm[kCLvl];
+          if (l + 1 < nlev) nown_next[r] = L[4 * (l + 1) + 4] - L[4 * (l + 1)];
+          const int4* ut = cp.cutask.data() + cm[kCU];
+          const int4* ct = cp.ctri.data() + cm[kCTri];
+          // near tasks of level l: [L[4l+1], L[4l+2]); far: [L[4l+2], L[4(l+1)+1])
+          for (int u = L[4 * l + 1]; u < L[4 * (l + 1) + 1]; ++u) {
+            const int4 tk = ut[u];
+            const bool near = u < L[4 * l + 2];
+            CHECK(tk.y >= 0 && tk.y <= tk.z && tk.z <= cm[kCNTri], "%s C=%d rank %d: task %d triplets [%d,%d) "
+                  "outside its list of %d", t.name.c_str(), C, r, u, tk.y, tk.z, cm[kCNTri]);
+            // the same destination among the graph's tasks of this level
+            int found = -1;
+            for (int v = lvl[4 * l + 1]; v < lvl[4 * (l + 1) + 1]; ++v)
+              if (p.lutask[ubase + v].x == tk.x) found = v;
+            CHECK(found >= 0, "%s C=%d rank %d level %d: destination %d not a task of the level", t.name.c_str(), C,
+                  r, l, tk.x);
+            const int4 gt = p.lutask[ubase + found];
+            CHECK(near == (found < lvl[4 * l + 2]), "%s C=%d: near/far kind changed for destination %d",
+                  t.name.c_str(), C, tk.x);
+            CHECK(gt.w == tk.w && gt.z - gt.y == tk.z - tk.y, "%s C=%d: task of destination %d changed",
+                  t.name.c_str(), C, tk.x);
+            for (int q = 0; q < tk.z - tk.y; ++q) {
+              const int4 a = ct[tk.y + q], b = p.ltri[tribase + gt.y + q];
+              CHECK(a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w, "%s C=%d rank %d: triplet %d of "
+                    "destination %d differs from the graph's", t.name.c_str(), C, r, q, tk.x);
+            }
+            if (near) {
+              const int h = cp.slot_home[sbase + tk.x];
+              CHECK((h >> 24) == r, "%s C=%d: near task of destination %d run by rank %d, owned by rank %d",
+                    t.name.c_str(), C, tk.x, r, h >> 24);
+            } else {
+              const long long w = std::max(1, tk.z - tk.y);
+              load[r] += w;
+              last_w[r] = w;
+            }
+            ++seen[tk.x];
+          }
+        }
+        for (int v = lvl[4 * l + 1]; v < lvl[4 * (l + 1) + 1]; ++v) {
+          const int dst = p.lutask[ubase + v].x;
+          CHECK(seen[dst] == 1, "%s C=%d level %d: destination %d run %d times", t.name.c_str(), C, l, dst,
+                seen[dst]);
+        }
+        // greedy far assignment: the last far task of each executor went to it while its
+        // estimated work (a factorising CTA's base + far work so far) was the least
+        std::vector<long long> total(C);
+        for (int r = 0; r < C; ++r) {
+          const long long base = nown_next[r] ? 24LL * ((nown_next[r] + kClusterPanelCols - 1) / kClusterPanelCols) : 0;
+          total[r] = base + load[r];
+        }
+        for (int r = 0; r < C; ++r) {
+          if (last_w[r] == 0) continue;
+          for (int q = 0; q < C; ++q)
+            CHECK(total[r] - last_w[r] <= total[q], "%s C=%d level %d: rank %d's last far task taken at work %lld "
+                  "while rank %d ends at %lld", t.name.c_str(), C, l, r, total[r] - last_w[r], q, total[q]);
+        }
+      }
+      // shared memory of every CTA within the reported maximum; triplets partitioned
+      long long tri_sum = 0, tri_tasks = 0;
+      for (int v = 0; v < m[kMetaNU]; ++v) tri_tasks += p.lutask[ubase + v].z - p.lutask[ubase + v].y;
+      for (int r = 0; r < C; ++r) {
+        const int32_t* cm = cp.cmeta.data() + kCMetaCount * (g * C + r);
+        tri_sum += cm[kCNTri];
+        const size_t b = cluster_smem_bytes(cm[kCNSlot], cm[kCNCol], cm[kCNColMax], cm[kCNTri], cm[kCNU], cm[kCNT],
+                                            nlev, m[kMetaNSlot], m[kMetaNCol]);
+        CHECK(b <= cp.max_cta_smem, "%s C=%d rank %d: %zu bytes above the reported %zu", t.name.c_str(), C, r, b,
+              cp.max_cta_smem);
+      }
+      CHECK(tri_sum == tri_tasks, "%s C=%d: %lld triplets staged for %lld in tasks", t.name.c_str(), C, tri_sum,
+            tri_tasks);
+      (void)colslot;
+    }
+  }
+}
+
+}  // namespace
+
+int main() {
+  std::vector<Topo> topos;
+  {
+    Topo t{"two_agents_40"};
+    t.kf_offset = {0};
+    t.edge_offset = {0};
+    add_graph(t, 2, 40, 10, 6, 7u);
+    topos.push_back(t);
+  }
+  {
+    Topo t{"four_agents_150"};
+    t.kf_offset = {0};
+    t.edge_offset = {0};
+    add_graph(t, 4, 150, 0, 60, 11u);
+    topos.push_back(t);
+  }
+  {
+    Topo t{"chain_400"};
+    t.kf_offset = {0};
+    t.edge_offset = {0};
+    add_graph(t, 1, 400, 50, 0, 3u);
+    topos.push_back(t);
+  }
+  {
+    Topo t{"batch_3"};
+    t.kf_offset = {0};
+    t.edge_offset = {0};
+    add_graph(t, 2, 12, 4, 2, 5u);
+    add_graph(t, 3, 30, 10, 8, 9u);
+    add_graph(t, 1, 60, 20, 0, 13u);
+    topos.push_back(t);
+  }
+  for (const Topo& t : topos) check_topology(t);
+  std::printf("OK %d\n", g_checks);
+  return 0;
+}
