@@ -32,6 +32,7 @@
 #include <cooperative_groups.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "como3r_internal.h"
 
@@ -1391,12 +1392,24 @@ cudaError_t launch_factor_solve_group(int ctas, const SolverPlan& plan, const in
                             eps0, max_attempts, ginfo, warn, keep, gfail);
 }
 
+// The dynamic shared memory limit of a solver kernel only grows: graphs alive at the same
+// time plan different sizes, and each launch asks for its own graph's, which must stay
+// within the limit whichever graph was created last.  Per kernel, the largest size set so
+// far (one process-wide value; setting a larger limit than a launch uses costs nothing).
+static std::mutex g_smem_attr_mu;
+template <typename K>
+cudaError_t grow_smem_limit(K kernel, size_t& largest, size_t smem_bytes) {
+  std::lock_guard<std::mutex> lock(g_smem_attr_mu);
+  if (smem_bytes <= largest) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e == cudaSuccess) largest = smem_bytes;
+  return e;
+}
+static size_t g_smem_substitute_f = 0, g_smem_substitute = 0, g_smem_solve = 0, g_smem_cluster = 0;
+
 cudaError_t factor_substitute_prepare(size_t smem_bytes, bool factor_in_smem) {
-  if (factor_in_smem)
-    return cudaFuncSetAttribute(factor_substitute_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes);
-  return cudaFuncSetAttribute(factor_substitute_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_bytes);
+  if (factor_in_smem) return grow_smem_limit(factor_substitute_kernel<true, true>, g_smem_substitute_f, smem_bytes);
+  return grow_smem_limit(factor_substitute_kernel<true, false>, g_smem_substitute, smem_bytes);
 }
 
 cudaError_t launch_factor_substitute(int G, const SolverPlan& plan, FactorKeep keep, const GraphInfoDev* rec,
@@ -1414,7 +1427,7 @@ cudaError_t launch_factor_substitute(int G, const SolverPlan& plan, FactorKeep k
 }
 
 cudaError_t factor_solve_prepare(size_t smem_bytes) {
-  return cudaFuncSetAttribute(factor_solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  return grow_smem_limit(factor_solve_kernel<true>, g_smem_solve, smem_bytes);
 }
 
 cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t smem_bytes, const double* A,
@@ -1437,8 +1450,7 @@ cudaError_t launch_factor_solve(int G, const SolverPlan& plan, bool smem, size_t
 namespace como3r {
 
 cudaError_t factor_solve_cluster_prepare(size_t smem_bytes, int C) {
-  cudaError_t e = cudaFuncSetAttribute(factor_solve_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes);
+  cudaError_t e = grow_smem_limit(factor_solve_cluster_kernel, g_smem_cluster, smem_bytes);
   if (e == cudaSuccess && C > 8)
     e = cudaFuncSetAttribute(factor_solve_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;

@@ -300,6 +300,26 @@ def test_batched_tracking(C):
         assert all(x["solved"] for x in info)
 
 
+@pytest.mark.parametrize("ctas", ["0", "4"])
+def test_graphs_of_different_sizes_alive_together(C, tiny, mid, ctas, monkeypatch):
+    """A graph created after a larger one plans less shared memory for its solver; the
+    larger graph's solves (and vjp substitutions) still launch and give the oracle's steps."""
+    monkeypatch.setenv("COMO3R_SOLVE_CLUSTER", ctas)
+    po, to = O.gn_solve(mid, mid.poses_init, 3)
+    with C.Graph(mid, mode=C.PLAIN_FP64) as big:
+        with C.Graph(tiny, mode=C.PLAIN_FP64) as small:
+            assert big.stats()["solve_ctas"] == small.stats()["solve_ctas"] == max(int(ctas), 1)
+            poses_s = torch_poses(tiny.poses_init)
+            small.solve(poses_s, 2)
+            poses = torch_poses(mid.poses_init)
+            st, trace, info = big.solve(poses, 3)
+            assert all(x["solved"] for x in info)
+            st, gl, gc, loss = big.vjp(torch_poses(mid.poses_init), 2, C.VJP_UNROLLED)
+            assert np.isfinite(gl.double().cpu().numpy()).all()
+    assert max(pose_err(poses.cpu().numpy(), po).values()) <= FP64_TOL
+    np.testing.assert_allclose(trace, to, rtol=FP64_TOL)
+
+
 @pytest.mark.parametrize("ctas", [2, 4, 8, 16])
 def test_multi_sm_solve_matches_oracle(C, tiny, mid, ctas, monkeypatch):
     """The multi-SM factorisation (one cluster of `ctas` CTAs per graph, columns spread over
