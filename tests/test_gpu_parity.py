@@ -397,6 +397,39 @@ def test_grid_solve_matches_single_cta(C, tiny, mid, monkeypatch):
     np.testing.assert_allclose(res["tiny"][1], to, rtol=FP64_TOL)
 
 
+@pytest.fixture(scope="module")
+def wide_top():
+    # 2 agents x 12 keyframes with skips up to 3 and 16 inter-agent edges: the top of its
+    # elimination tree has a one-column level with five off-diagonal blocks (8 + 35 rows),
+    # factored as a wide four-warp panel whose rows beyond 32 are solved afterwards
+    return make_problem(5, agents=2, n_kf=12, H=24, W=32, f=25.0, n_inter=16, skip_max=3, name="wide-top")
+
+
+def test_wide_panels_match_oracle_in_every_solver(C, wide_top, monkeypatch):
+    """The wide four-warp panel gives the same factor in the one-CTA, cluster (4 and 8 CTAs)
+    and grid-wide solves (bitwise: the same operations per entry in the same order) and the
+    oracle's FP64 steps."""
+    pin_residual_kernel(monkeypatch)
+    out = {}
+    for name, env in (("cta", dict(COMO3R_SOLVE_CLUSTER="0", COMO3R_SOLVE_GRID="0")),
+                      ("cluster4", dict(COMO3R_SOLVE_CLUSTER="4", COMO3R_SOLVE_GRID="0")),
+                      ("cluster8", dict(COMO3R_SOLVE_CLUSTER="8", COMO3R_SOLVE_GRID="0")),
+                      ("grid", dict(COMO3R_SOLVE_CLUSTER="0", COMO3R_SOLVE_GRID="1"))):
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        poses = torch_poses(wide_top.poses_init)
+        with C.Graph(wide_top, mode=C.PLAIN_FP64) as g:
+            st, trace, info = g.solve(poses, 5)
+        assert all(x["solved"] for x in info), name
+        out[name] = (poses.cpu().numpy(), trace)
+    for name in ("cluster4", "cluster8", "grid"):
+        np.testing.assert_array_equal(out[name][0], out["cta"][0])
+        np.testing.assert_array_equal(out[name][1], out["cta"][1])
+    po, to = O.gn_solve(wide_top, wide_top.poses_init, 5)
+    assert max(pose_err(out["cta"][0], po).values()) <= FP64_TOL
+    np.testing.assert_allclose(out["cta"][1], to, rtol=FP64_TOL)
+
+
 def test_grid_solve_failure_gives_zero_update(C, tiny, monkeypatch):
     """Every attempt fails in the grid-wide solve too (all CTAs take the decision from the
     same flag after a grid barrier): the update is zero and the warning is set; the next
