@@ -724,13 +724,18 @@ def measure_adjoint_4x30(C, torch) -> dict:
             else:
                 g_at = np.where(gold["fd_which"] == 0, gl[pix], gc[pix])
                 keep = gold["fd_excluded"] == 0
+                ex = gold["exact_idx"].astype(int)
+                sc = float(np.abs(g_at).max())
+                e["exact_pixels_rel_max"] = float(np.max(np.abs(g_at[ex] - gold["exact"]) /
+                                                         np.maximum(np.abs(gold["exact"]), 1e-3 * sc)))
                 e["central_difference"] = {
-                    "pixels": int(len(pix)), "excluded_huber_branch": int((~keep).sum()),
-                    "step": 1e-4, "rel_dev_median": float(np.median(np.abs(g_at - gold["fd"])[keep] /
-                                                                   np.abs(gold["fd"])[keep])),
-                    "fd_error_vs_exact": float(np.abs(gold["fd"][gold["exact_idx"].astype(int)] -
-                                                      gold["exact"]).max())}
+                    "pixels": int(len(pix)), "excluded_huber_branch": int((~keep).sum()), "step": 1e-4,
+                    "noise_rms_at_exact_pixels": float(np.sqrt(np.mean((gold["fd"][ex] - gold["exact"]) ** 2))),
+                    "spread_rms_vs_gradient": float(np.sqrt(np.mean((g_at - gold["fd"])[keep] ** 2)))}
             err[f"{name}_{vname}"] = e
+        err["note"] = ("8 unconverged IRLS iterations amplify rounding: the mixed form's unrolled gradient differs "
+                       "from the FP64 one at O(1) here (its envelope does not); the central differences are "
+                       "noise-dominated (noise_rms vs derivatives of 0.05..2000) and agree within it")
         res["error_vs_oracle"] = err
     return res
 
