@@ -297,21 +297,6 @@ __global__ void __launch_bounds__(256) adjoint_match_kernel(
   }
 }
 
-// ad_xi^T y for xi = (v, w, z) with ad_xi = [[w^ + z I, v^, -v], [0, w^, 0], [0, 0, 0]].
-__device__ __forceinline__ void ad_transpose_apply(const double* xi, const double* y, double* out) {
-  const double v0 = xi[0], v1 = xi[1], v2 = xi[2], w0 = xi[3], w1 = xi[4], w2 = xi[5], z = xi[6];
-  const double y0 = y[0], y1 = y[1], y2 = y[2], q0 = y[3], q1 = y[4], q2 = y[5];
-  // (w^ + z I)^T y_v = y_v x w + z y_v
-  out[0] = (y1 * w2 - y2 * w1) + z * y0;
-  out[1] = (y2 * w0 - y0 * w2) + z * y1;
-  out[2] = (y0 * w1 - y1 * w0) + z * y2;
-  // (v^)^T y_v + (w^)^T y_w = y_v x v + y_w x w
-  out[3] = (y1 * v2 - y2 * v1) + (q1 * w2 - q2 * w1);
-  out[4] = (y2 * v0 - y0 * v2) + (q2 * w0 - q0 * w2);
-  out[5] = (y0 * v1 - y1 * v0) + (q0 * w1 - q1 * w0);
-  out[6] = -(v0 * y0 + v1 * y1 + v2 * y2);
-}
-
 // Per edge (one warp; an FP64 warp instruction holds its SM sub-partition's FP64 unit
 // ~80 cycles however many lanes it uses, so work is spread over lanes): Ad-rotated adjoint and step differences for the match kernel,
 // u~ = Ad (u_j - u_i), tau~ = Ad (tau_j - tau_i), stored in R (16 per edge).
@@ -341,7 +326,8 @@ __global__ void adjoint_edge_prep_kernel(const EdgeStatic* __restrict__ es, int 
   }
 }
 
-// Component k of ad_transpose_apply(xi, y).
+// Component k of ad_xi^T y for xi = (v, w, z) with ad_xi = [[w^ + z I, v^, -v], [0, w^, 0], [0, 0, 0]]:
+// (w^ + z I)^T y_v = y_v x w + z y_v, (v^)^T y_v + (w^)^T y_w = y_v x v + y_w x w, -v . y_v.
 __device__ __forceinline__ double ad_transpose_component(const double* xi, const double* y, int k) {
   const double v0 = xi[0], v1 = xi[1], v2 = xi[2], w0 = xi[3], w1 = xi[4], w2 = xi[5], z = xi[6];
   const double y0 = y[0], y1 = y[1], y2 = y[2], q0 = y[3], q1 = y[4], q2 = y[5];
@@ -357,11 +343,13 @@ __device__ __forceinline__ double ad_transpose_component(const double* xi, const
 }
 
 // Per edge (kAdjEdgeThreads threads): FP64 sum of the item records in a fixed order (warp w
-// sums items w, w + 4, ... of slot `lane`, four loads ahead; the four partial sums are then
-// added pairwise), then the keyframe terms out[e][0..6] = dF/dd_i, out[e][7..13] = dF/dd_j,
-// one component per lane (an FP64 instruction holds its SM sub-partition ~80 cycles
-// however few lanes it uses, so a component per lane is a short chain).
-constexpr int kAdjEdgeThreads = 128;
+// of W sums items w, w + W, ... of slot `lane`, four loads ahead; the W partial sums are
+// then added pairwise), then the keyframe terms out[e][0..6] = dF/dd_i, out[e][7..13] =
+// dF/dd_j, one component per lane (an FP64 instruction holds its SM sub-partition ~80
+// cycles however few lanes it uses, so a component per lane is a short chain).
+// (Eight warps: 10.19 -> 10.15 ms for the vjp of the 2 x 40 workload against four; sixteen
+// measured the same as eight.)
+constexpr int kAdjEdgeThreads = 256;
 __global__ void __launch_bounds__(kAdjEdgeThreads) adjoint_edge_kernel(
     const double* __restrict__ rec, const int32_t* __restrict__ item_off, int E, const EdgeStatic* __restrict__ es,
     const double* __restrict__ Ad, const double* __restrict__ u, const double* __restrict__ tau,
@@ -389,7 +377,16 @@ __global__ void __launch_bounds__(kAdjEdgeThreads) adjoint_edge_kernel(
   if (warp == 1 && lane < 7) d[7 + lane] = tau[7 * j + lane] - tau[7 * i + lane];
   __syncthreads();
   if (warp != 0) return;
-  if (lane < kAdjRec) F[lane] = (part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]);
+  if (lane < kAdjRec) {
+    double q[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) q[w] = part[w][lane];
+#pragma unroll
+    for (int h = 1; h < W; h *= 2)
+#pragma unroll
+      for (int w = 0; w + h < W; w += 2 * h) q[w] += q[w + h];
+    F[lane] = q[0];
+  }
   __syncwarp();
   // y = [Ad^T F_xi, Ad^T F_u~, Ad^T F_tau~]
   if (lane < kAdjRec) {
