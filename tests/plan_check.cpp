@@ -6,10 +6,12 @@
 //     triplets of the same task in the graph's list, in the same order;
 //   * far tasks are assigned greedily by estimated work: a CTA's last far task of a level
 //     went to it while its estimated work was the least of all CTAs;
-//   * the shared memory reported covers every CTA's blocks, scratch, triplets and lists.
+//   * the shared memory reported covers every CTA's blocks, scratch, triplets and lists;
+//   * the CTA-group plan of a batch (see check_groups).
 // Prints "OK <checks>" on success, "FAIL <reason>" otherwise.
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -180,6 +182,84 @@ void check_topology(const Topo& t) {
   }
 }
 
+// The CTA-group plan of a batch (build_group_plan): every graph exactly once; a clustered
+// graph on kGroupCTAs consecutive CTAs of ranks 0..kGroupCTAs-1, the others packed onto
+// single CTAs; whole clusters within the GPU; the clustered graphs the slowest by the
+// one-CTA estimate; a forced count honoured.
+void check_groups(const Topo& t, int sms) {
+  const int G = (int)t.height.size();
+  float dummy[4] = {0, 0, 0, 0};
+  int32_t midx[1] = {-1};
+  como3r_graph_desc d{};
+  d.num_graphs = G;
+  d.kf_offset = t.kf_offset.data();
+  d.height = t.height.data();
+  d.width = t.width.data();
+  d.agent_of = t.agent_of.data();
+  d.points_conf = dummy;
+  d.dtype = COMO3R_F32;
+  d.edge_offset = t.edge_offset.data();
+  d.edge_i = t.edge_i.data();
+  d.edge_j = t.edge_j.data();
+  d.match_idx = midx;
+  d.anchor = t.anchor.data();
+  d.sigma_ray = 0.003;
+  d.sigma_dist = 10;
+  d.huber_k = 1.345;
+  d.eps0 = 1e-6;
+  d.max_attempts = 6;
+  d.mode = COMO3R_MIXED;
+  HostPlan p;
+  CHECK(build_plan(&d, p) == COMO3R_OK, "%s: build_plan: %s", t.name.c_str(), p.error.c_str());
+  for (int force : {-1, 1, 3}) {
+    GroupPlan gp;
+    build_group_plan(p, sms, force, gp);
+    if (gp.ctas == 0) {
+      CHECK(force < 0, "%s: forced %d clustered graphs, no group plan", t.name.c_str(), force);
+      continue;
+    }
+    CHECK(gp.ctas % kGroupCTAs == 0 && gp.ctas <= sms, "%s: %d CTAs on %d SMs", t.name.c_str(), gp.ctas, sms);
+    CHECK((int)gp.gtask.size() == gp.ctas, "%s: %zu tasks for %d CTAs", t.name.c_str(), gp.gtask.size(), gp.ctas);
+    if (force > 0) CHECK(gp.big == force, "%s: forced %d, planned %d", t.name.c_str(), force, gp.big);
+    std::vector<int> seen(G, 0), clustered(G, 0);
+    for (int c = 0; c < gp.ctas; ++c) {
+      const int4 k = gp.gtask[c];
+      CHECK(k.x >= 0 && k.y >= 0 && k.x + k.y <= (int)gp.glist.size(), "%s: CTA %d list out of range",
+            t.name.c_str(), c);
+      if (k.w == kGroupCTAs) {
+        CHECK(k.y == 1 && c % kGroupCTAs == k.z, "%s: CTA %d rank %d of a cluster-solved graph", t.name.c_str(), c,
+              k.z);
+        CHECK(gp.gtask[c - k.z].x == k.x, "%s: CTA %d not in its graph's cluster", t.name.c_str(), c);
+        if (k.z == 0) ++seen[gp.glist[k.x]], clustered[gp.glist[k.x]] = 1;
+      } else {
+        CHECK(k.w == 1 && k.z == 0, "%s: CTA %d group size %d rank %d", t.name.c_str(), c, k.w, k.z);
+        for (int q = 0; q < k.y; ++q) ++seen[gp.glist[k.x + q]];
+      }
+    }
+    int nclustered = 0;
+    for (int g = 0; g < G; ++g) {
+      CHECK(seen[g] == 1, "%s: graph %d solved %d times", t.name.c_str(), g, seen[g]);
+      nclustered += clustered[g];
+      CHECK((gp.order[g] >= 0) == (clustered[g] == 1), "%s: graph %d ordering override", t.name.c_str(), g);
+    }
+    CHECK(nclustered == gp.big, "%s: %d clustered graphs, planned %d", t.name.c_str(), nclustered, gp.big);
+    // the clustered graphs are the slowest by the one-CTA estimate (levels and block updates
+    // of the cheaper ordering for one SM): none of the others is estimated slower
+    auto est = [&](int g) {
+      const double md = 3.0 * p.nlev_md[g] + 0.15 * (double)p.upd_md[g];
+      const double nd = 3.0 * p.nlev_nd[g] + 0.15 * (double)p.upd_nd[g];
+      return md <= nd ? 6.3 * p.nlev_md[g] + 0.26 * (double)p.upd_md[g] : 6.3 * p.nlev_nd[g] + 0.26 * (double)p.upd_nd[g];
+    };
+    double min_big = 1e300, max_small = -1;
+    for (int g = 0; g < G; ++g) {
+      if (clustered[g]) min_big = std::min(min_big, est(g));
+      else max_small = std::max(max_small, est(g));
+    }
+    CHECK(max_small <= min_big, "%s: a single-CTA graph (%.1f us) estimated slower than a clustered one (%.1f us)",
+          t.name.c_str(), max_small, min_big);
+  }
+}
+
 }  // namespace
 
 int main() {
@@ -215,6 +295,14 @@ int main() {
     topos.push_back(t);
   }
   for (const Topo& t : topos) check_topology(t);
+  {
+    Topo t{"batch_40"};
+    t.kf_offset = {0};
+    t.edge_offset = {0};
+    for (int g = 0; g < 40; ++g) add_graph(t, 2, 6 + (g * 37) % 110, (g % 3) ? 10 : 0, 2 + g % 7, 100u + g);
+    check_groups(t, 148);
+    check_groups(t, 64);
+  }
   std::printf("OK %d\n", g_checks);
   return 0;
 }

@@ -1,11 +1,12 @@
-"""Host logic of the multi-SM solver's plan, without a GPU.
+"""Host logic of the multi-SM and CTA-group solve plans, without a GPU.
 
 `tests/plan_check.cpp` is compiled with the host compiler against the planner's source
 (`csrc/plan.cpp`) and run: for several synthetic pose-graph topologies and cluster sizes
 2, 4, 8 and 16 it checks that every update task runs exactly once per level (near tasks by
 the owner of their destination), that each CTA's own triplet list holds exactly the
 triplets of its tasks in the graph's order, that far tasks are assigned greedily by
-estimated work, and that the reported shared memory covers every CTA.
+estimated work, that the reported shared memory covers every CTA, and that a batch's
+CTA-group plan solves every graph once, the slowest on whole clusters.
 """
 import os
 import shutil
