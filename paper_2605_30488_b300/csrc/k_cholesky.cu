@@ -1394,18 +1394,24 @@ cudaError_t launch_factor_solve_group(int ctas, const SolverPlan& plan, const in
 
 // The dynamic shared memory limit of a solver kernel only grows: graphs alive at the same
 // time plan different sizes, and each launch asks for its own graph's, which must stay
-// within the limit whichever graph was created last.  Per kernel, the largest size set so
-// far (one process-wide value; setting a larger limit than a launch uses costs nothing).
+// within the limit whichever graph was created last.  Per kernel and device, the largest
+// size set so far (setting a larger limit than a launch uses costs nothing).
+constexpr int kMaxDevices = 64;
 static std::mutex g_smem_attr_mu;
 template <typename K>
-cudaError_t grow_smem_limit(K kernel, size_t& largest, size_t smem_bytes) {
+cudaError_t grow_smem_limit(K kernel, size_t (&largest)[kMaxDevices], size_t smem_bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_smem_attr_mu);
-  if (smem_bytes <= largest) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-  if (e == cudaSuccess) largest = smem_bytes;
+  size_t* cur = (dev >= 0 && dev < kMaxDevices) ? &largest[dev] : nullptr;
+  if (cur && smem_bytes <= *cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e == cudaSuccess && cur) *cur = smem_bytes;
   return e;
 }
-static size_t g_smem_substitute_f = 0, g_smem_substitute = 0, g_smem_solve = 0, g_smem_cluster = 0;
+static size_t g_smem_substitute_f[kMaxDevices], g_smem_substitute[kMaxDevices], g_smem_solve[kMaxDevices],
+    g_smem_cluster[kMaxDevices];
 
 cudaError_t factor_substitute_prepare(size_t smem_bytes, bool factor_in_smem) {
   if (factor_in_smem) return grow_smem_limit(factor_substitute_kernel<true, true>, g_smem_substitute_f, smem_bytes);
