@@ -7,6 +7,7 @@
 //   * far tasks are assigned greedily by estimated work: a CTA's last far task of a level
 //     went to it while its estimated work was the least of all CTAs;
 //   * the shared memory reported covers every CTA's blocks, scratch, triplets and lists;
+//   * the symbolic factorisation, levels and update triplets (see check_symbolic);
 //   * the CTA-group plan of a batch (see check_groups).
 // Prints "OK <checks>" on success, "FAIL <reason>" otherwise.
 #include <cstdio>
@@ -182,6 +183,137 @@ void check_topology(const Topo& t) {
   }
 }
 
+// The symbolic block factorisation and its level schedule, from first principles: in the
+// plan's column order, eliminating a column connects all its later neighbours (fill), so
+// column c's off-diagonal block rows must be exactly its later neighbours at that point;
+// a column's level is above the levels of all columns that update it; the update triplets
+// of a level are exactly (L_rj, L_kj -> block (r, k)) for its columns j and every pair
+// r >= k of j's rows, grouped into one task per destination; a near task is one whose
+// destination column is factored at the next level.
+void check_symbolic(const Topo& t, int order) {
+  const int G = (int)t.height.size();
+  float dummy[4] = {0, 0, 0, 0};
+  int32_t midx[1] = {-1};
+  como3r_graph_desc d{};
+  d.num_graphs = G;
+  d.kf_offset = t.kf_offset.data();
+  d.height = t.height.data();
+  d.width = t.width.data();
+  d.agent_of = t.agent_of.data();
+  d.points_conf = dummy;
+  d.dtype = COMO3R_F32;
+  d.edge_offset = t.edge_offset.data();
+  d.edge_i = t.edge_i.data();
+  d.edge_j = t.edge_j.data();
+  d.match_idx = midx;
+  d.anchor = t.anchor.data();
+  d.sigma_ray = 0.003;
+  d.sigma_dist = 10;
+  d.huber_k = 1.345;
+  d.eps0 = 1e-6;
+  d.max_attempts = 6;
+  d.mode = COMO3R_MIXED;
+  HostPlan p;
+  std::vector<int8_t> ord(G, (int8_t)order);
+  CHECK(build_plan(&d, p, &ord) == COMO3R_OK, "%s: build_plan: %s", t.name.c_str(), p.error.c_str());
+  for (int g = 0; g < G; ++g) {
+    const int* m = p.meta.data() + kMetaCount * g;
+    const int cbase = m[kMetaColBase], n = m[kMetaNCol], sbase = m[kMetaSlotBase], nslot = m[kMetaNSlot];
+    const int nlev = m[kMetaNLvl], ubase = m[kMetaUBase], tribase = m[kMetaTriBase];
+    const int* lvl = p.llvl.data() + 4 * m[kMetaLvlBase];
+    const int* colslot = p.lcol_slot.data() + cbase + g;
+    CHECK(colslot[n] == nslot, "%s: column slots end at %d, %d slots", t.name.c_str(), colslot[n], nslot);
+    // columns <-> keyframes: every unfixed keyframe of the graph exactly once
+    std::map<int, int> col_of_kf;
+    for (int c = 0; c < n; ++c) {
+      const int kf = p.col_kf[cbase + c];
+      CHECK(kf >= t.kf_offset[g] && kf < t.kf_offset[g + 1] && !p.frozen[kf] && !col_of_kf.count(kf),
+            "%s: column %d keyframe %d", t.name.c_str(), c, kf);
+      col_of_kf[kf] = c;
+    }
+    int unfixed = 0;
+    for (int kf = t.kf_offset[g]; kf < t.kf_offset[g + 1]; ++kf) unfixed += !p.frozen[kf];
+    CHECK(unfixed == n, "%s: %d unfixed keyframes, %d columns", t.name.c_str(), unfixed, n);
+    // elimination graph in column order
+    std::vector<std::vector<char>> adj(n, std::vector<char>(n, 0));
+    for (int e = t.edge_offset[g]; e < t.edge_offset[g + 1]; ++e) {
+      const auto a = col_of_kf.find(t.edge_i[e]), b = col_of_kf.find(t.edge_j[e]);
+      if (a == col_of_kf.end() || b == col_of_kf.end()) continue;
+      adj[a->second][b->second] = adj[b->second][a->second] = 1;
+    }
+    std::vector<std::vector<int>> rows(n);
+    for (int c = 0; c < n; ++c) {
+      for (int r = c + 1; r < n; ++r)
+        if (adj[c][r]) rows[c].push_back(r);
+      for (int a : rows[c])
+        for (int b : rows[c])
+          if (a != b) adj[a][b] = 1;
+    }
+    std::map<std::pair<int, int>, int> slot;  // (row, column) -> local slot
+    for (int c = 0; c < n; ++c) {
+      const int s0 = colslot[c], nb = colslot[c + 1] - s0 - 1;
+      CHECK(p.lslot_row[sbase + s0] == c, "%s: column %d's first slot is not its diagonal", t.name.c_str(), c);
+      CHECK(nb == (int)rows[c].size(), "%s order %d: column %d has %d off-diagonal blocks, elimination gives %zu",
+            t.name.c_str(), order, c, nb, rows[c].size());
+      slot[{c, c}] = s0;
+      for (int b = 0; b < nb; ++b) {
+        CHECK(p.lslot_row[sbase + s0 + 1 + b] == rows[c][b], "%s order %d: column %d block %d row %d, expected %d",
+              t.name.c_str(), order, c, b, p.lslot_row[sbase + s0 + 1 + b], rows[c][b]);
+        slot[{rows[c][b], c}] = s0 + 1 + b;
+      }
+    }
+    // levels
+    std::vector<int> level(n, -1);
+    for (int l = 0; l < nlev; ++l)
+      for (int q = lvl[4 * l]; q < lvl[4 * (l + 1)]; ++q) {
+        const int c = p.lsched[cbase + q];
+        CHECK(c >= 0 && c < n && level[c] < 0, "%s: column %d scheduled twice", t.name.c_str(), c);
+        level[c] = l;
+      }
+    for (int c = 0; c < n; ++c) {
+      CHECK(level[c] >= 0, "%s: column %d never scheduled", t.name.c_str(), c);
+      for (int r : rows[c])
+        CHECK(level[r] > level[c], "%s: column %d (level %d) updates column %d at level %d", t.name.c_str(), c,
+              level[c], r, level[r]);
+    }
+    // update triplets per level
+    for (int l = 0; l < nlev; ++l) {
+      std::map<std::vector<int>, int> want, got;
+      for (int j = 0; j < n; ++j) {
+        if (level[j] != l) continue;
+        for (size_t a = 0; a < rows[j].size(); ++a)
+          for (size_t b = 0; b <= a; ++b) {
+            const int r = rows[j][a], k = rows[j][b];
+            ++want[{slot[{r, j}], slot[{k, j}], slot[{r, k}], j}];
+          }
+      }
+      for (int v = lvl[4 * l + 1]; v < lvl[4 * (l + 1) + 1]; ++v) {
+        const int4 tk = p.lutask[ubase + v];
+        const bool diag = p.lslot_row[sbase + tk.x] == [&] {
+          for (int c = 0; c < n; ++c)
+            if (tk.x >= colslot[c] && tk.x < colslot[c + 1]) return c;
+          return -1;
+        }();
+        CHECK(tk.w == (diag ? p.lslot_row[sbase + tk.x] : -1), "%s: task of slot %d right-hand-side column %d",
+              t.name.c_str(), tk.x, tk.w);
+        int dst_col = -1;
+        for (int c = 0; c < n; ++c)
+          if (tk.x >= colslot[c] && tk.x < colslot[c + 1]) dst_col = c;
+        const bool near = v < lvl[4 * l + 2];
+        CHECK(near == (level[dst_col] == l + 1), "%s: task of slot %d (column level %d) near=%d at level %d",
+              t.name.c_str(), tk.x, level[dst_col], (int)near, l);
+        for (int q = tk.y; q < tk.z; ++q) {
+          const int4 tr = p.ltri[tribase + q];
+          CHECK(tr.z == tk.x, "%s: triplet of slot %d in the task of slot %d", t.name.c_str(), tr.z, tk.x);
+          ++got[{tr.x, tr.y, tr.z, tr.w}];
+        }
+      }
+      CHECK(want == got, "%s order %d level %d: %zu distinct update triplets planned, %zu expected", t.name.c_str(),
+            order, l, got.size(), want.size());
+    }
+  }
+}
+
 // The CTA-group plan of a batch (build_group_plan): every graph exactly once; a clustered
 // graph on kGroupCTAs consecutive CTAs of ranks 0..kGroupCTAs-1, the others packed onto
 // single CTAs; whole clusters within the GPU; the clustered graphs the slowest by the
@@ -294,7 +426,11 @@ int main() {
     add_graph(t, 1, 60, 20, 0, 13u);
     topos.push_back(t);
   }
-  for (const Topo& t : topos) check_topology(t);
+  for (const Topo& t : topos) {
+    check_topology(t);
+    check_symbolic(t, 0);
+    check_symbolic(t, 1);
+  }
   {
     Topo t{"batch_40"};
     t.kf_offset = {0};
