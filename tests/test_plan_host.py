@@ -1,15 +1,16 @@
 """Host logic of the multi-SM and CTA-group solve plans, without a GPU.
 
 `tests/plan_check.cpp` is compiled with the host compiler against the planner's source
-(`csrc/plan.cpp`) and run.  For several synthetic pose-graph topologies, in both fill-
-reducing orderings, it re-derives the symbolic block factorisation by eliminating the
-columns in the plan's order and checks the planned block rows, the level schedule (a
-column above every column that updates it) and the update triplets of every level against
-it.  For cluster sizes 2, 4, 8 and 16 it checks that every update task runs exactly once per level (near tasks by
-the owner of their destination), that each CTA's own triplet list holds exactly the
-triplets of its tasks in the graph's order, that far tasks are assigned greedily by
-estimated work, that the reported shared memory covers every CTA, and that a batch's
-CTA-group plan solves every graph once, the slowest on whole clusters.
+(`csrc/plan.cpp`) and run.  For several synthetic pose-graph topologies, in both
+fill-reducing orderings, it re-derives the symbolic block factorisation by eliminating the
+columns in the plan's order and checks against it the planned block rows, the level
+schedule (a column above every column that updates it) and the update triplets of every
+level.  For cluster sizes 2, 4, 8 and 16 it checks that every update task runs exactly
+once per level (near tasks by the owner of their destination), that each CTA's own
+triplet list holds exactly the triplets of its tasks in the graph's order, that far tasks
+are assigned greedily by estimated work and that the reported shared memory covers every
+CTA; and that a batch's CTA-group plan solves every graph once, the slowest on whole
+clusters.
 """
 import os
 import shutil
