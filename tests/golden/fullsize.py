@@ -15,7 +15,10 @@ Workloads (all synthetic, seeded; the stand-ins for the paper's 512 x 384 pointm
                      generator: exact correspondences, generated in about a minute);
 * adjoint_4x30    -- 4 agents x 30 keyframes, 512 x 384 FP32, 180 edges, 8 iterations,
                      the refined cost differentiated w.r.t. per-pixel log-range and
-                     confidence.
+                     confidence;
+* two_agent_6kf   -- the small configuration: 2 agents x 6 keyframes, 64 x 48 FP64, 14
+                     edges, 10 iterations (seconds of the oracle; stored so that the bench
+                     reads its errors against the oracle instead of running it).
 
 A fingerprint of the inputs (valid match count, sum of the match indices, sums of the
 stored point values) is stored with each golden, so a test can tell a changed input from
@@ -34,8 +37,9 @@ PATHS = {
     "two_agent_40kf": os.path.join(HERE, "fullsize_two_agent_40kf.txt"),
     "team_4x150_f16": os.path.join(HERE, "fullsize_team_4x150_f16.txt"),
     "adjoint_4x30": os.path.join(HERE, "fullsize_adjoint_4x30.txt"),
+    "two_agent_6kf": os.path.join(HERE, "fullsize_two_agent_6kf.txt"),
 }
-ITERS = {"two_agent_40kf": 15, "team_4x150_f16": 10, "adjoint_4x30": 8}
+ITERS = {"two_agent_40kf": 15, "team_4x150_f16": 10, "adjoint_4x30": 8, "two_agent_6kf": 10}
 
 
 def problem(name: str):
@@ -49,6 +53,8 @@ def problem(name: str):
         return make_cloud_problem(31, [spec], dtype=np.float16, iters=ITERS[name], name="team-4x150-f16-band")
     if name == "adjoint_4x30":
         return make_workload("four_agent_30kf_512x384", seed=0)
+    if name == "two_agent_6kf":
+        return make_workload("two_agent_6kf_64x48", seed=0)
     raise KeyError(name)
 
 

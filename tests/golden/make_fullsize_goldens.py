@@ -1,6 +1,7 @@
 """Writes the full-size oracle goldens (fullsize_*.txt beside this file).
 
-Usage (from the repository root; each takes minutes to hours of CPU):
+Usage (from the repository root; the full-size ones take minutes to hours of CPU):
+    python -m tests.golden.make_fullsize_goldens two_agent_6kf      (seconds)
     python -m tests.golden.make_fullsize_goldens two_agent_40kf
     python -m tests.golden.make_fullsize_goldens team_4x150_f16
     python -m tests.golden.make_fullsize_goldens adjoint_4x30 [--workers 6]
@@ -90,6 +91,18 @@ def make_two_agent_40kf():
         "H_fro: its Frobenius norm (both triangles); g: the gradient (fixed keyframes zero).",
         f"poses / trace: {F.ITERS[name]} Gauss-Newton iterations from the initial poses (trace[k] = cost before",
         f"iteration k, trace[{F.ITERS[name]}] after the last). CPU time {time.time() - t0:.0f} s."]), ent)
+
+
+def make_two_agent_6kf():
+    name = "two_agent_6kf"
+    prob = F.problem(name)
+    t0 = time.time()
+    poses, trace = O.gn_solve(prob, prob.poses_init, F.ITERS[name])
+    ent = _fp_entries(prob)
+    ent.update(poses=poses, trace=trace[:, 0])
+    F.write(F.PATHS[name], _header(name, prob, [
+        f"poses / trace: {F.ITERS[name]} Gauss-Newton iterations from the initial poses (trace[k] = cost before",
+        f"iteration k, trace[{F.ITERS[name]}] after the last). CPU time {time.time() - t0:.1f} s."]), ent)
 
 
 def make_team_4x150_f16():
@@ -292,6 +305,8 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.which == "two_agent_40kf":
         make_two_agent_40kf()
+    elif a.which == "two_agent_6kf":
+        make_two_agent_6kf()
     elif a.which == "team_4x150_f16":
         make_team_4x150_f16()
     else:
